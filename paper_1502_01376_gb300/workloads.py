@@ -1,0 +1,172 @@
+"""Seeded synthetic inputs for the hybrid Yee-FFT field advance.
+
+This module holds none of the method's arithmetic: it draws random
+band-limited fields and particle positions/velocities, and moves particles
+ballistically (x^{n+1} = x^n + v dt) to give the deposit its start and end
+points.  Both the CUDA path's tests and the oracle's tests take their inputs
+from here, so the two sides see bit-identical inputs.
+
+Workloads (shapes and distributions follow Table 1 and the drifting-plasma
+setup of Sec. 3; c = 1, k_p = omega_p = 1):
+
+  vacuum_beam      2D 128 x 64, dx = 0.1, dt = 0.05, FP64 state, 100 steps;
+                   band-limited random E, B (|k| < 0.5 pi/dx, rms 1e-3 per
+                   component); 4096 beam particles of charge -0.01 at
+                   v1 = 0.99, uniform in the box, linear shapes, no filter.
+  drift_plasma     2D 4096 x 1024, dx = 0.2, dt = 0.1, FP32 state; electrons
+                   and positive particles (q/m = -1, +1), 8 per cell each,
+                   uniform positions, u1 = gamma beta with gamma = 50 and a
+                   Gaussian spread 1e-4 in u; density n/n_p = 100; quadratic
+                   shapes; J1 correction + k1 low-pass filter at kc = 0.5 of
+                   Nyquist, width 0.2 of Nyquist.
+  drift_plasma_3d  3D 1024 x 256 x 256, dx = 0.2, dt = 0.08, gamma = 30,
+                   2 particles per cell per species.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    dims: int
+    n1: int
+    n2: int
+    n3: int = 1
+    dx1: float = 0.1
+    dx2: float = 0.1
+    dx3: float = 0.1
+    dt: float = 0.05
+    precision: int = 64
+    steps: int = 100
+    correct_j1: bool = True
+    filt_kc: float = 0.0
+    filt_w: float = 0.0
+    shape_order: int = 1
+    seed: int = 1
+    # particles
+    kind: str = "beam"            # "beam" | "plasma"
+    n_particles: int = 4096       # beam only
+    beam_q: float = -0.01
+    beam_v1: float = 0.99
+    ppc: int = 8                  # plasma: particles per cell per species
+    gamma: float = 50.0
+    u_th: float = 1e-4
+    density: float = 100.0        # n / n_p
+    field_amp: float = 1e-3
+    field_kfrac: float = 0.5
+
+    @property
+    def shape(self):
+        return (self.n3, self.n2, self.n1) if self.dims == 3 else (self.n2, self.n1)
+
+    @property
+    def cells(self) -> int:
+        return self.n1 * self.n2 * (self.n3 if self.dims == 3 else 1)
+
+    def scaled(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+VACUUM_BEAM = Workload("vacuum_beam_2d_128x64_f64", 2, 128, 64, dx1=0.1, dx2=0.1, dt=0.05,
+                       precision=64, steps=100, seed=1, kind="beam", n_particles=4096,
+                       shape_order=1)
+DRIFT_PLASMA = Workload("drift_plasma_2d_4096x1024_f32", 2, 4096, 1024, dx1=0.2, dx2=0.2, dt=0.1,
+                        precision=32, steps=1000, filt_kc=0.5, filt_w=0.2, shape_order=2, seed=2,
+                        kind="plasma", ppc=8, gamma=50.0)
+DRIFT_PLASMA_3D = Workload("drift_plasma_3d_1024x256x256_f32", 3, 1024, 256, 256, dx1=0.2, dx2=0.2,
+                           dx3=0.2, dt=0.08, precision=32, steps=100, filt_kc=0.5, filt_w=0.2,
+                           shape_order=2, seed=4, kind="plasma", ppc=2, gamma=30.0)
+
+WORKLOADS = {w.name: w for w in (VACUUM_BEAM, DRIFT_PLASMA, DRIFT_PLASMA_3D)}
+
+
+# ---------------------------------------------------------------------------
+def band_limited_fields(w: Workload, rng: np.random.Generator | None = None):
+    """Six real random fields (E1,E2,E3,B1,B2,B3) whose Fourier content is
+    confined to |k| < kfrac * pi/dx (radially, in grid wavenumbers), with
+    uniform random phases, each scaled to rms field_amp.  FP64."""
+    rng = rng or np.random.default_rng(w.seed)
+    shp = w.shape
+    out = []
+    # normalised wavenumbers in units of the Nyquist number of each axis
+    axes = [np.fft.fftfreq(n) * 2.0 for n in shp[:-1]] + [np.fft.rfftfreq(shp[-1]) * 2.0]
+    grids = np.meshgrid(*axes, indexing="ij")
+    kr = np.sqrt(sum(g * g for g in grids))
+    mask = (kr < w.field_kfrac)
+    for _ in range(6):
+        amp = rng.standard_normal(mask.shape)
+        ph = rng.uniform(0.0, 2.0 * np.pi, mask.shape)
+        spec = np.where(mask, amp * np.exp(1j * ph), 0.0)
+        f = np.fft.irfftn(spec, s=shp, axes=tuple(range(len(shp))))
+        rms = np.sqrt(np.mean(f * f))
+        out.append(np.ascontiguousarray(f * (w.field_amp / rms if rms > 0 else 0.0)))
+    return out[:3], out[3:]
+
+
+@dataclass
+class Particles:
+    """Positions in cell units (x / dx per axis, FP64), velocities, charges."""
+    x: np.ndarray          # [np, dims]
+    v: np.ndarray          # [np, 3]  (v1, v2, v3)
+    q: np.ndarray          # [np]
+
+    @property
+    def count(self) -> int:
+        return self.q.size
+
+
+def make_particles(w: Workload, rng: np.random.Generator | None = None) -> Particles:
+    rng = rng or np.random.default_rng(w.seed + 1000)
+    d = w.dims
+    ext = np.array([w.n1, w.n2, w.n3][:d], dtype=np.float64)
+    if w.kind == "beam":
+        n = w.n_particles
+        x = rng.uniform(0.0, 1.0, (n, d)) * ext
+        v = np.zeros((n, 3))
+        v[:, 0] = w.beam_v1
+        q = np.full(n, w.beam_q)
+        return Particles(x, v, q)
+    # drifting plasma: two species, ppc each, q/m = -1 and +1
+    ncell = w.cells
+    n = ncell * w.ppc
+    dV = w.dx1 * w.dx2 * (w.dx3 if d == 3 else 1.0)
+    rho0 = w.density / (4.0 * np.pi)            # 4 pi rho0 = omega_p^2 = n/n_p
+    xs, vs, qs = [], [], []
+    for sign in (-1.0, +1.0):
+        x = rng.uniform(0.0, 1.0, (n, d)) * ext
+        u = rng.standard_normal((n, 3)) * w.u_th
+        u[:, 0] += np.sqrt(w.gamma ** 2 - 1.0)
+        gam = np.sqrt(1.0 + np.sum(u * u, axis=1))
+        xs.append(x)
+        vs.append(u / gam[:, None])
+        qs.append(np.full(n, sign * rho0 * dV / w.ppc))
+    return Particles(np.concatenate(xs), np.concatenate(vs), np.concatenate(qs))
+
+
+def ballistic_move(w: Workload, p: Particles, step: int, real=np.float64):
+    """Start/end points of step `step` (x^n -> x^{n+1}, ballistic), as the
+    deposit interface takes them: integer cell of x^n per axis (periodic),
+    offset of x^n and of x^{n+1} from that cell, in cell units, rounded to
+    `real`.  Also returns v3 (the out-of-plane velocity in 2D)."""
+    d = w.dims
+    dxs = np.array([w.dx1, w.dx2, w.dx3][:d])
+    ext = np.array([w.n1, w.n2, w.n3][:d], dtype=np.float64)
+    x0 = np.mod(p.x + step * p.v[:, :d] * w.dt / dxs, ext)
+    cell = np.floor(x0)
+    off0 = x0 - cell
+    off1 = off0 + p.v[:, :d] * w.dt / dxs
+    cell = np.mod(cell, ext).astype(np.int32)
+    off0 = np.ascontiguousarray(off0.astype(real))
+    off1 = np.ascontiguousarray(off1.astype(real))
+    v3 = np.ascontiguousarray(p.v[:, 2].astype(real))
+    return np.ascontiguousarray(cell), off0, off1, v3
+
+
+def position_at(w: Workload, p: Particles, step: int, real=np.float64):
+    """Integer cell and offset of x^step (for charge densities)."""
+    cell, off0, _, _ = ballistic_move(w, p, step, real)
+    return cell, off0

@@ -1,0 +1,415 @@
+"""Pins of the oracle's hybrid field advance against what the paper and the
+mathematics fix (none of these retypes the oracle's own per-mode formulae):
+
+* exact calculus: a single x1 Fourier mode (and the Nyquist cosine) is
+  differentiated exactly by the hybrid x1 operator, at the staggered points;
+* the vacuum numerical dispersion relation of Sec. 2.2 with [k]1 = k1
+  (Eq. emdispersion, Courant derivation), measured from plane-wave runs;
+* the Courant limit of Sec. 2.2 and its 0.537 value for square cells;
+* Yee recovery (Sec. 2.1, last sentence): with the finite-difference symbol the
+  k-space step equals a direct real-space Yee step (Eqs. yee2db1-yee2de3);
+* div B stays at its initial value (curl structure of Eqs. hybrid2db1-db3);
+* Gauss's law residual is constant in time with the corrected current and
+  drifts without it (Sec. 2.3);
+* numerical Cerenkov radiation of a 0.99c particle is suppressed relative to
+  the Yee solver (abstract, Sec. 1).
+"""
+import numpy as np
+import pytest
+
+from paper_1502_01376_gb300 import workloads as wl
+
+
+def zeros(g, orc):
+    s = orc.field_shape(g)
+    return [np.zeros(s) for _ in range(3)], [np.zeros(s) for _ in range(3)], [np.zeros(s) for _ in range(3)]
+
+
+# ---------------------------------------------------------------- calculus pins
+@pytest.mark.parametrize("kappa", [0, 1, 3, 7, 15, 16])
+def test_sigma_plus_is_exact_derivative_at_half_points(orc, kappa):
+    n1, n2, dx1, dx2, dt = 32, 8, 0.3, 0.25, 0.05
+    g = orc.grid(n1=n1, n2=n2, dx1=dx1, dx2=dx2, dt=dt)
+    E, B, J = zeros(g, orc)
+    rng = np.random.default_rng(kappa)
+    h = rng.standard_normal(n2)[:, None]
+    i1 = np.arange(n1)[None, :]
+    k = 2 * np.pi * kappa / (n1 * dx1)
+    phi = 0.3 if kappa not in (0, n1 // 2) else 0.0
+    E[2][:] = np.cos(k * i1 * dx1 + phi) * h            # E3 at integer x1
+    E[1][:] = np.sin(k * i1 * dx1 + phi) * h            # E2 at integer x1
+    E2_0, E3_0 = E[1].copy(), E[2].copy()
+    orc.step(g, E, B, J)
+    # derivative of the band-limited interpolant at x1 = (i1+1/2) dx1; for the
+    # Nyquist mode the interpolant is cos(pi x/dx1) (sin term vanishes on the grid)
+    xh = (i1 + 0.5) * dx1
+    dE3 = -k * np.sin(k * xh + phi) * h
+    dE2 = k * np.cos(k * xh + phi) * h if kappa != n1 // 2 else 0.0 * h
+    assert np.allclose(B[1], dt * dE3, atol=1e-13)                 # B2 += c dt d1 E3
+    d2E1 = 0.0
+    assert np.allclose(B[2], -dt * dE2 + d2E1, atol=1e-13)         # B3 -= c dt d1 E2
+    d2E3 = (np.roll(E3_0, -1, axis=0) - E3_0) / dx2
+    assert np.allclose(B[0], -dt * d2E3, atol=1e-13)               # B1 -= c dt d2 E3
+
+
+@pytest.mark.parametrize("kappa", [0, 1, 5, 15, 16])
+def test_sigma_minus_is_exact_derivative_at_integer_points(orc, kappa):
+    n1, n2, dx1, dx2, dt = 32, 8, 0.2, 0.3, 0.04
+    g = orc.grid(n1=n1, n2=n2, dx1=dx1, dx2=dx2, dt=dt)
+    E, B, J = zeros(g, orc)
+    rng = np.random.default_rng(50 + kappa)
+    h = rng.standard_normal(n2)[:, None]
+    i1 = np.arange(n1)[None, :]
+    k = 2 * np.pi * kappa / (n1 * dx1)
+    phi = 0.7 if kappa not in (0, n1 // 2) else 0.0
+    xh = (i1 + 0.5) * dx1
+    # B2, B3 sit at half-integer x1; for Nyquist the samples are cos(pi (x - dx/2)/dx)
+    if kappa == n1 // 2:
+        B[1][:] = np.cos(np.pi * i1) * h
+        B[2][:] = np.cos(np.pi * i1) * h
+        dB = (np.pi / dx1) * np.cos(np.pi * i1) * h          # d/dx cos(pi(x-dx/2)/dx) at x = i dx
+    else:
+        B[1][:] = np.cos(k * xh + phi) * h
+        B[2][:] = np.cos(k * xh + phi) * h
+        dB = -k * np.sin(k * i1 * dx1 + phi) * h
+    B1_0 = B[0].copy()
+    B3_0 = B[2].copy()
+    orc.step(g, E, B, J)          # E = 0, so B^{n+1/2} = B^{n-1/2}
+    assert np.allclose(E[2], dt * dB, atol=1e-13)                     # E3 += c dt d1 B2
+    assert np.allclose(E[1], -dt * dB, atol=1e-13)                    # E2 -= c dt d1 B3
+    d2B3 = (B3_0 - np.roll(B3_0, 1, axis=0)) / dx2
+    assert np.allclose(E[0], dt * d2B3, atol=1e-13)                   # E1 += c dt d2 B3
+    assert np.allclose(B1_0, 0.0)
+
+
+# ------------------------------------------------------------ dispersion pins
+def _mode_ls_cos(series):
+    a = np.asarray(series)
+    num = np.sum((a[2:] + a[:-2]) * a[1:-1])
+    den = 2.0 * np.sum(a[1:-1] ** 2)
+    return num / den
+
+
+def _run_series(orc, g, init, pick, nsteps=10):
+    E, B, J = zeros(g, orc)
+    pat = init(E, B)
+    out = [np.sum(pick(E, B) * pat)]
+    for _ in range(nsteps):
+        orc.step(g, E, B, J)
+        out.append(np.sum(pick(E, B) * pat))
+    return out
+
+
+def _hybrid_cos_omega_dt(dt, dx2, k1, k2, dx3=None, k3=None):
+    kb2 = np.sin(k2 * dx2 / 2) / (dx2 / 2)
+    K2 = k1 ** 2 + kb2 ** 2
+    if k3 is not None:
+        K2 += (np.sin(k3 * dx3 / 2) / (dx3 / 2)) ** 2
+    # [omega]^2 = K^2  <=>  sin^2(w dt/2) = (dt/2)^2 K^2  <=>  cos(w dt) = 1 - 2 (dt/2)^2 K^2
+    return 1.0 - 2.0 * (dt / 2) ** 2 * K2
+
+
+@pytest.mark.parametrize("k1i,k2i", [(1, 0), (3, 2), (8, 4), (16, 0), (16, 8), (5, 7), (0, 3)])
+@pytest.mark.parametrize("pol", ["TE", "TM"])
+def test_vacuum_dispersion_2d(orc, k1i, k2i, pol):
+    n1, n2, dx1, dx2 = 32, 16, 0.2, 0.25
+    g0 = orc.grid(n1=n1, n2=n2, dx1=dx1, dx2=dx2)
+    dt = 0.9 * orc.courant(g0)
+    g = orc.grid(n1=n1, n2=n2, dx1=dx1, dx2=dx2, dt=dt)
+    k1 = 2 * np.pi * k1i / (n1 * dx1)
+    k2 = 2 * np.pi * k2i / (n2 * dx2)
+    i1 = np.arange(n1)[None, :]
+    i2 = np.arange(n2)[:, None]
+    if pol == "TE":      # E3, B1, B2
+        def init(E, B):
+            pat = np.cos(k1 * i1 * dx1 + k2 * i2 * dx2)
+            E[2][:] = pat
+            return pat
+        pick = lambda E, B: E[2]
+    else:                # E1, E2, B3; B3 at (i1+1/2, i2+1/2)
+        def init(E, B):
+            # any phase of the mode will do; this one keeps the Nyquist cosines
+            # non-zero at the half-integer points
+            pat = np.cos(k1 * i1 * dx1 + k2 * i2 * dx2)
+            B[2][:] = pat
+            return pat
+        pick = lambda E, B: B[2]
+    series = _run_series(orc, g, init, pick)
+    got = _mode_ls_cos(series)
+    want = _hybrid_cos_omega_dt(dt, dx2, k1, k2)
+    assert abs(got - want) < 1e-12, (got, want)
+    # phase velocity along x1 is superluminal (no numerical Cerenkov resonance)
+    if k2i == 0 and k1i > 0:
+        w = np.arccos(np.clip(got, -1, 1)) / dt
+        assert w >= k1 * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("comp,k", [(2, (1, 1, 0)), (2, (8, 4, 0)), (1, (4, 0, 3)), (1, (8, 0, 4)),
+                                    (0, (0, 2, 1)), (0, (0, 4, 4))])
+def test_vacuum_dispersion_3d(orc, comp, k):
+    """A single divergence-free E mode (E_c with k_c = 0) obeys the 3D hybrid
+    relation [omega]^2 = k1^2 + [k]2^2 + [k]3^2."""
+    n1, n2, n3, dx1, dx2, dx3 = 16, 8, 8, 0.2, 0.25, 0.3
+    g0 = orc.grid(dims=3, n1=n1, n2=n2, n3=n3, dx1=dx1, dx2=dx2, dx3=dx3)
+    dt = 0.8 * orc.courant(g0)
+    g = orc.grid(dims=3, n1=n1, n2=n2, n3=n3, dx1=dx1, dx2=dx2, dx3=dx3, dt=dt)
+    k1 = 2 * np.pi * k[0] / (n1 * dx1)
+    k2 = 2 * np.pi * k[1] / (n2 * dx2)
+    k3 = 2 * np.pi * k[2] / (n3 * dx3)
+    i1 = np.arange(n1)[None, None, :]
+    i2 = np.arange(n2)[None, :, None]
+    i3 = np.arange(n3)[:, None, None]
+
+    def init(E, B):
+        pat = np.cos(k1 * i1 * dx1 + k2 * i2 * dx2 + k3 * i3 * dx3)
+        E[comp][:] = pat
+        return pat
+    series = _run_series(orc, g, init, lambda E, B: E[comp], nsteps=12)
+    got = _mode_ls_cos(series)
+    want = _hybrid_cos_omega_dt(dt, dx2, k1, k2, dx3, k3)
+    assert abs(got - want) < 1e-12, (got, want)
+
+
+# ---------------------------------------------------------------- Courant pins
+def test_courant_closed_form(orc):
+    for dx1, dx2 in [(0.2, 0.2), (0.1, 0.3), (1.0, 0.5)]:
+        g = orc.grid(dx1=dx1, dx2=dx2)
+        assert orc.courant(g) == pytest.approx(2 / np.sqrt(np.pi ** 2 / dx1 ** 2 + 4 / dx2 ** 2), rel=1e-15)
+    g = orc.grid(dx1=1.0, dx2=1.0)
+    assert round(orc.courant(g), 3) == 0.537         # "dt <= 0.537 dx1" for square cells
+
+
+@pytest.mark.parametrize("factor,grows", [(1.02, True), (0.98, False)])
+def test_courant_stability(orc, factor, grows):
+    n1, n2, dx = 16, 8, 0.2
+    g0 = orc.grid(n1=n1, n2=n2, dx1=dx, dx2=dx)
+    g = orc.grid(n1=n1, n2=n2, dx1=dx, dx2=dx, dt=factor * orc.courant(g0))
+    E, B, J = zeros(g, orc)
+    rng = np.random.default_rng(11)
+    for f in E + B:
+        f[:] = rng.standard_normal(f.shape)
+    m0 = max(np.max(np.abs(f)) for f in E + B)
+    orc.step(g, E, B, J, nsteps=60)
+    m1 = max(np.max(np.abs(f)) for f in E + B)
+    if grows:
+        assert m1 > 1e3 * m0
+    else:
+        assert m1 < 30 * m0
+
+
+# ---------------------------------------------------------------- Yee recovery
+def yee_step_2d(E, B, J, dt, dx1, dx2, ampere=4 * np.pi):
+    """Direct real-space Yee step, Eqs. yee2db1-yee2de3 (axis 0 = x2, axis 1 = x1)."""
+    E1, E2, E3 = E
+    B1, B2, B3 = B
+    fwd = lambda f, ax: np.roll(f, -1, axis=ax) - f
+    bwd = lambda f, ax: f - np.roll(f, 1, axis=ax)
+    B1 -= dt * fwd(E3, 0) / dx2
+    B2 += dt * fwd(E3, 1) / dx1
+    B3 += -dt * fwd(E2, 1) / dx1 + dt * fwd(E1, 0) / dx2
+    E1 += -ampere * dt * J[0] + dt * bwd(B3, 0) / dx2
+    E2 += -ampere * dt * J[1] - dt * bwd(B3, 1) / dx1
+    E3 += -ampere * dt * J[2] + dt * bwd(B2, 1) / dx1 - dt * bwd(B1, 0) / dx2
+
+
+def yee_step_3d(E, B, J, dt, dx, ampere=4 * np.pi):
+    """Standard 3D Yee step (axis 0 = x3, 1 = x2, 2 = x1)."""
+    E1, E2, E3 = E
+    B1, B2, B3 = B
+    ax = {1: 2, 2: 1, 3: 0}
+    fwd = lambda f, d: (np.roll(f, -1, axis=ax[d]) - f) / dx[d - 1]
+    bwd = lambda f, d: (f - np.roll(f, 1, axis=ax[d])) / dx[d - 1]
+    B1 -= dt * (fwd(E3, 2) - fwd(E2, 3))
+    B2 -= dt * (fwd(E1, 3) - fwd(E3, 1))
+    B3 -= dt * (fwd(E2, 1) - fwd(E1, 2))
+    E1 += dt * (bwd(B3, 2) - bwd(B2, 3)) - ampere * dt * J[0]
+    E2 += dt * (bwd(B1, 3) - bwd(B3, 1)) - ampere * dt * J[1]
+    E3 += dt * (bwd(B2, 1) - bwd(B1, 2)) - ampere * dt * J[2]
+
+
+def test_yee_recovery_2d(orc):
+    n1, n2, dx1, dx2, dt = 32, 12, 0.2, 0.15, 0.05
+    g = orc.grid(n1=n1, n2=n2, dx1=dx1, dx2=dx2, dt=dt, yee_mode=True)
+    rng = np.random.default_rng(5)
+    E = [rng.standard_normal((n2, n1)) for _ in range(3)]
+    B = [rng.standard_normal((n2, n1)) for _ in range(3)]
+    J = [rng.standard_normal((n2, n1)) for _ in range(3)]
+    Ey = [f.copy() for f in E]
+    By = [f.copy() for f in B]
+    for _ in range(3):
+        orc.step(g, E, B, J)
+        yee_step_2d(Ey, By, J, dt, dx1, dx2)
+    for a, b in zip(E + B, Ey + By):
+        assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(b))
+
+
+def test_yee_recovery_3d(orc):
+    n1, n2, n3 = 16, 6, 5
+    dx = (0.2, 0.15, 0.25)
+    dt = 0.04
+    g = orc.grid(dims=3, n1=n1, n2=n2, n3=n3, dx1=dx[0], dx2=dx[1], dx3=dx[2], dt=dt, yee_mode=True)
+    rng = np.random.default_rng(6)
+    shp = (n3, n2, n1)
+    E = [rng.standard_normal(shp) for _ in range(3)]
+    B = [rng.standard_normal(shp) for _ in range(3)]
+    J = [rng.standard_normal(shp) for _ in range(3)]
+    Ey = [f.copy() for f in E]
+    By = [f.copy() for f in B]
+    for _ in range(2):
+        orc.step(g, E, B, J)
+        yee_step_3d(Ey, By, J, dt, dx)
+    for a, b in zip(E + B, Ey + By):
+        assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(b))
+
+
+def test_hybrid_differs_from_yee(orc):
+    """Negative control for the recovery pin: the hybrid symbol is not Yee's."""
+    n1, n2 = 32, 8
+    g = orc.grid(n1=n1, n2=n2, dx1=0.2, dx2=0.2, dt=0.05)
+    rng = np.random.default_rng(9)
+    E = [rng.standard_normal((n2, n1)) for _ in range(3)]
+    B = [rng.standard_normal((n2, n1)) for _ in range(3)]
+    J = [np.zeros((n2, n1)) for _ in range(3)]
+    Ey = [f.copy() for f in E]
+    By = [f.copy() for f in B]
+    orc.step(g, E, B, J)
+    yee_step_2d(Ey, By, J, 0.05, 0.2, 0.2)
+    assert np.max(np.abs(B[1] - By[1])) > 1e-3
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("dims", [2, 3])
+def test_div_b_constant(orc, dims):
+    if dims == 2:
+        g = orc.grid(n1=64, n2=32, dx1=0.1, dx2=0.1, dt=0.05)
+    else:
+        g = orc.grid(dims=3, n1=32, n2=8, n3=8, dx1=0.1, dx2=0.12, dx3=0.11, dt=0.04)
+    rng = np.random.default_rng(21)
+    shp = orc.field_shape(g)
+    E = [rng.standard_normal(shp) for _ in range(3)]
+    B = [rng.standard_normal(shp) for _ in range(3)]
+    J = [rng.standard_normal(shp) for _ in range(3)]
+    d0 = orc.divb(g, B)
+    scale = np.max(np.abs(d0))
+    for _ in range(5):
+        orc.step(g, E, B, J, nsteps=10)
+        d = orc.divb(g, B)
+        assert np.max(np.abs(d - d0)) < 1e-11 * scale
+
+
+def _gauss_run(orc, g, w, nsteps, order):
+    E, B = wl.band_limited_fields(w)
+    p = wl.make_particles(w)
+    cell, off0 = wl.position_at(w, p, 0)
+    rho = orc.charge(g, cell, off0, p.q, order)
+    G0 = orc.gauss(g, E, rho)
+    scale = g.ampere * np.max(np.abs(rho))
+    per_step, total = [], []
+    for n in range(nsteps):
+        cell, off0, off1, v3 = wl.ballistic_move(w, p, n)
+        Gn = orc.gauss(g, E, orc.charge(g, cell, off0, p.q, order))
+        J = orc.deposit(g, cell, off0, off1, v3, p.q, order)
+        orc.step(g, E, B, J)
+        Gn1 = orc.gauss(g, E, orc.charge(g, cell, off1, p.q, order))
+        per_step.append(np.max(np.abs(Gn1 - Gn)) / scale)
+    cell, off0 = wl.position_at(w, p, nsteps)
+    total = np.max(np.abs(orc.gauss(g, E, orc.charge(g, cell, off0, p.q, order)) - G0)) / scale
+    return max(per_step), total
+
+
+@pytest.mark.parametrize("filt", [False, True])
+def test_gauss_law_invariant_with_correction(orc, filt):
+    w = wl.VACUUM_BEAM.scaled(n1=32, n2=16, n_particles=48, filt_kc=0.5 if filt else 0.0, filt_w=0.2)
+    g = orc.grid(n1=w.n1, n2=w.n2, dx1=w.dx1, dx2=w.dx2, dt=w.dt, correct_j1=True,
+                 filt_kc=w.filt_kc, filt_w=w.filt_w)
+    per, tot = _gauss_run(orc, g, w, 25, 1)
+    assert per < 1e-13
+    assert tot < 1e-11
+
+
+def test_gauss_law_drifts_without_correction(orc):
+    w = wl.VACUUM_BEAM.scaled(n1=32, n2=16, n_particles=48)
+    g = orc.grid(n1=w.n1, n2=w.n2, dx1=w.dx1, dx2=w.dx2, dt=w.dt, correct_j1=False)
+    per, tot = _gauss_run(orc, g, w, 10, 1)
+    assert per > 1e-4
+    assert tot > 1e-3
+
+
+def test_gauss_law_3d(orc):
+    w = wl.Workload("t3", 3, 16, 8, 8, dx1=0.2, dx2=0.2, dx3=0.2, dt=0.08, kind="beam",
+                    n_particles=16, shape_order=2, seed=3)
+    g = orc.grid(dims=3, n1=16, n2=8, n3=8, dx1=0.2, dx2=0.2, dx3=0.2, dt=0.08)
+    E, B = wl.band_limited_fields(w)
+    p = wl.make_particles(w)
+    for n in range(3):
+        cell, off0, off1, v3 = wl.ballistic_move(w, p, n)
+        G0 = orc.gauss(g, E, orc.charge(g, cell, off0, p.q, 2))
+        J = orc.deposit(g, cell, off0, off1, v3, p.q, 2)
+        orc.step(g, E, B, J)
+        G1 = orc.gauss(g, E, orc.charge(g, cell, off1, p.q, 2))
+        assert np.max(np.abs(G1 - G0)) < 1e-12 * np.max(np.abs(G0))
+
+
+# ---------------------------------------------------------------- tables
+def test_correction_and_filter_special_values(orc):
+    n1 = 64
+    g = orc.grid(n1=n1, n2=4, dx1=0.2, dx2=0.2, dt=0.05, filt_kc=0.5, filt_w=0.2)
+    keff, corr, filt = orc.mode_tables(g)
+    assert corr[0] == 1.0
+    assert corr[-1] == pytest.approx(2 / np.pi, rel=1e-15)         # Nyquist: sin(pi/2)/(pi/2)
+    k = 2 * np.pi * np.arange(n1 // 2 + 1) / (n1 * 0.2)
+    assert np.allclose(keff, k, rtol=1e-15)
+    assert filt[0] == 1.0
+    assert filt[n1 // 4] == pytest.approx(0.5, abs=1e-15)          # F(kc) = 1/2 at kc = pi/(2 dx)
+    assert filt[-1] == 0.0
+    assert np.all(np.diff(filt) <= 1e-15)
+    gy = orc.grid(n1=n1, n2=4, dx1=0.2, dx2=0.2, dt=0.05, yee_mode=True)
+    keff_y, corr_y, _ = orc.mode_tables(gy)
+    assert np.allclose(corr_y, 1.0)
+    assert keff_y[-1] == pytest.approx(2 / 0.2)
+
+
+def test_dispersion_bump_table(orc):
+    """Sec. 4: [k]1 = k1 + dk_max cos^2(...) on [k1l, k1u], peak dk_max at k1m."""
+    n1, dx = 1000, 0.2
+    g = orc.grid(n1=n1, n2=4, dx1=dx, dx2=dx, dt=0.05, kmod_l=0.15, kmod_u=0.26, kmod_max=0.01)
+    keff, corr, _ = orc.mode_tables(g)
+    kg = 2 * np.pi / dx
+    k = kg * np.arange(n1 // 2 + 1) / n1
+    dk = keff - k
+    assert np.all(np.abs(dk[(k < 0.15 * kg) | (k > 0.26 * kg)]) < 1e-12 * kg)
+    im = np.argmin(np.abs(k - 0.205 * kg))
+    assert dk[im] == pytest.approx(0.01 * kg, rel=1e-12)
+    assert np.all(dk >= -1e-12 * kg)
+
+
+# ---------------------------------------------------------------- Cerenkov
+def _single_particle_wake(orc, yee):
+    n1, n2, dx, dt = 256, 64, 0.1, 0.045
+    w = wl.Workload("cer", 2, n1, n2, dx1=dx, dx2=dx, dt=dt, kind="beam", n_particles=1, beam_v1=0.99,
+                    beam_q=-0.01, shape_order=2)
+    g = orc.grid(n1=n1, n2=n2, dx1=dx, dx2=dx, dt=dt, yee_mode=yee)
+    p = wl.Particles(np.array([[10.0, n2 / 2]]), np.array([[0.99, 0.0, 0.0]]), np.array([-0.01]))
+    E = [np.zeros((n2, n1)) for _ in range(3)]
+    B = [np.zeros((n2, n1)) for _ in range(3)]
+    nsteps = 300
+    hist = []
+    for n in range(nsteps):
+        cell, off0, off1, v3 = wl.ballistic_move(w, p, n)
+        J = orc.deposit(g, cell, off0, off1, v3, p.q, 2)
+        orc.step(g, E, B, J)
+        if n >= nsteps - 40:
+            hist.append(E[1].copy())
+    # fields that change shape in the particle frame: remove the co-moving part by
+    # comparing with the field one step later shifted by the particle motion is
+    # impractical on a grid, so measure E2 energy well behind the particle
+    x_end = (10.0 + nsteps * 0.99 * dt / dx) % n1
+    i_end = int(x_end)
+    behind = [(i_end - 20 - j) % n1 for j in range(60)]
+    return float(np.sum(hist[-1][:, behind] ** 2))
+
+
+def test_no_numerical_cerenkov_in_hybrid(orc):
+    e_yee = _single_particle_wake(orc, True)
+    e_hyb = _single_particle_wake(orc, False)
+    assert e_yee > 20.0 * e_hyb, (e_yee, e_hyb)
