@@ -1,0 +1,158 @@
+/*
+ * hyb.h -- C ABI of libhyb.so, the GB300 (sm_103a) implementation of the
+ * hybrid Yee-FFT Maxwell field advance of Yu et al., arXiv:1502.01376
+ * ("Mitigation of numerical Cerenkov radiation and instability using a hybrid
+ * finite difference-FFT Maxwell solver and a local charge conserving current
+ * deposit").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Fields are real arrays of the grid's precision (float for precision 32,
+ * double for 64), row-major [n3][n2][n1] (n3 = 1 in 2D), x1 contiguous,
+ * 16-byte aligned, resident in this process's current CUDA device memory
+ * unless a call says "host".  A half-integer position i+1/2 is stored at
+ * index i (Yee staggering, Sec. 2.1): E1(i1+1/2,i2), E2(i1,i2+1/2), E3(i1,i2),
+ * B1(i1,i2+1/2), B2(i1+1/2,i2), B3(i1+1/2,i2+1/2), j like E, rho at integer
+ * points; 3D adds the standard Yee offsets in x3 (Sec. 2.4).  All boundaries
+ * are periodic.  Units: c = 1; Ampere's law carries `ampere` (4 pi) times j.
+ *
+ * Ownership: field, current, charge and particle memory belongs to the
+ * caller; the library borrows the pointers given to hyb_bind_fields until the
+ * next bind or hyb_destroy_grid.  The library owns its mode tables and its
+ * scratch, allocated in hyb_create_grid.
+ *
+ * Streams: every call is enqueued on the grid's stream and returns without
+ * waiting, except hyb_diag, hyb_advance_host, hyb_check and
+ * hyb_destroy_grid, which synchronise that stream.
+ *
+ * Errors: no call throws, exits or aborts.  A non-zero hyb_status is
+ * returned and hyb_last_error() gives a one-line message (thread-local).
+ * Kernels that detect bad input at run time (a particle moving a cell or more
+ * in one step) record it in a device flag that hyb_check reports.
+ */
+#ifndef HYB_H_
+#define HYB_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HYB_API __attribute__((visibility("default")))
+#else
+#define HYB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hyb_grid hyb_grid;   /* opaque */
+
+typedef enum {
+    HYB_OK = 0,
+    HYB_EINVAL = 1,     /* bad argument, size or unsupported combination */
+    HYB_ECOURANT = 2,   /* dt above the Courant limit of Sec. 2.2 */
+    HYB_EALIGN = 3,     /* pointer not 16-byte aligned */
+    HYB_ECUDA = 4,      /* a CUDA runtime call failed */
+    HYB_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    HYB_ESTATE = 6,     /* call out of order (e.g. fields not bound) */
+    HYB_ENOMEM = 7,     /* device allocation failed */
+    HYB_EDATA = 8       /* a kernel rejected input data (see hyb_check) */
+} hyb_status;
+
+typedef struct {
+    int dims;             /* 2 or 3 */
+    int n1, n2, n3;       /* grid points along x1 (FFT, even, power of two), x2, x3 (FD); n3 ignored in 2D */
+    double dx1, dx2, dx3; /* cell sizes */
+    double dt;            /* time step; must satisfy the Courant limit of Sec. 2.2 */
+    int precision;        /* 32 (float fields) or 64 (double fields) */
+    int correct_j1;       /* 1: apply Eq. currentcorrection to j1 inside hyb_advance */
+    double filt_kc;       /* k1 low-pass filter of Sec. 4 on j: centre, fraction of pi/dx1; on iff 0 < filt_kc < 1 */
+    double filt_w;        /* filter transition width, fraction of pi/dx1 (raised cosine, F(kc) = 1/2) */
+    double kmod_l, kmod_u;/* dispersion bump of Sec. 4: k1 range, fractions of k_g1 = 2 pi/dx1 */
+    double kmod_max;      /* bump height, fraction of k_g1; 0 = off */
+    int yee_mode;         /* 1: [k]1 = sin(k1 dx1/2)/(dx1/2) (recovers the Yee solver, Sec. 2.1) */
+    double ampere;        /* coefficient of j in Ampere's law; 0 selects 4 pi */
+    int path;             /* 0: fastest available; 1: three-pass (FFT, update, inverse FFT);
+                             2: fused single-pass (precision 32, dims 2, n1 in 512..4096) */
+} hyb_grid_desc;
+
+/* Courant limit dt_max = 2 / sqrt(pi^2/dx1^2 + 4/dx2^2 [+ 4/dx3^2]) of Sec. 2.2. */
+HYB_API double hyb_courant_limit(const hyb_grid_desc* desc);
+
+/* Validates desc (sizes, Courant limit -> HYB_ECOURANT, precision/path
+ * combination), computes the per-mode tables of Eqs. currentcorrection and
+ * hybrid2db1-hybrid2de3 and the Sec. 4 filter/bump in FP64 on the host, rounds
+ * them once to the run precision, uploads them and allocates scratch on the
+ * current device.  stream is a cudaStream_t (NULL = legacy default stream). */
+HYB_API hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** out);
+
+/* Replaces the stream later calls are enqueued on. */
+HYB_API hyb_status hyb_set_stream(hyb_grid* g, void* stream);
+
+/* Borrows the caller's device arrays: E[3], B[3], J[3] (required, each
+ * n1*n2*n3 elements of the grid's precision) and rho (nullable; used only by
+ * hyb_diag's Gauss residual).  Checks 16-byte alignment (HYB_EALIGN). */
+HYB_API hyb_status hyb_bind_fields(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3], void* rho);
+
+/* Sec. 2.3 charge-conserving (Esirkepov-form) deposit of j^{n+1/2} into the
+ * bound J (zeroed first) for np particles moving from x^n to x^{n+1}:
+ *   cell    int32 [np][dims]: integer cell of x^n along each axis (0 <= c < n);
+ *   off_old real  [np][dims]: x^n  - cell, in cell units, in [0, 1);
+ *   off_new real  [np][dims]: x^{n+1} - cell, in cell units, |off_new - off_old| < 1;
+ *   v3      real  [np] (2D only, nullable): out-of-plane velocity for j3;
+ *   q       real  [np]: macro-particle charge;
+ *   shape_order 1 (linear), 2 (quadratic) or 3 (cubic) B-spline.
+ * Real arrays are of the grid's precision, device resident.  Particles that
+ * break the range conditions are skipped and flagged (hyb_check -> HYB_EDATA). */
+HYB_API hyb_status hyb_deposit(hyb_grid* g, const int32_t* cell, const void* off_old, const void* off_new,
+                       const void* v3, const void* q, int64_t np, int shape_order);
+
+/* Eq. currentcorrection alone, in place on the bound J1:
+ * j1 <- IFFT_x1[ sin(k1 dx1/2)/(k1 dx1/2) FFT_x1[j1] ]. */
+HYB_API hyb_status hyb_correct_current(hyb_grid* g);
+
+/* The Sec. 4 k1 low-pass form factor alone, in place on all three bound J components. */
+HYB_API hyb_status hyb_filter(hyb_grid* g);
+
+/* nsteps of the hybrid advance, Eqs. hybrid2db1-hybrid2de3 (3D: Sec. 2.4),
+ * in place on the bound fields: on entry E = E^n, B = B^{n-1/2}, J = j^{n+1/2}
+ * (the same J for every step); on exit E = E^{n+nsteps}, B = B^{n+nsteps-1/2}.
+ * Per step: FFT along x1 of E, B, j; correction of j1 (if correct_j1) and the
+ * filter of j (if on) in k1 space; Faraday then Ampere per k1 mode with
+ * finite differences in x2 (and x3); inverse FFT. */
+HYB_API hyb_status hyb_advance(hyb_grid* g, int nsteps);
+
+/* The same as hyb_advance, but E, B, J are HOST arrays (pinned memory
+ * recommended): they are copied into the bound device arrays, advanced, and
+ * E, B are copied back.  Synchronises the grid's stream. */
+HYB_API hyb_status hyb_advance_host(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3], int nsteps);
+
+/* FP64 diagnostics of the bound fields, synchronous:
+ *   out[0..5]  sum f^2 dV / (8 pi) of E1, E2, E3, B1, B2, B3;
+ *   out[6]     max |div B|, div B = sigma+ B1 + d2+ B2 [+ d3+ B3] at the B-cell corners;
+ *   out[7]     max |G|, G = sigma- E1 + d2- E2 [+ d3- E3] - ampere F rho (Sec. 2.3; F the
+ *              current filter, rho taken as 0 if not bound);
+ *   out[8]     rms of G. */
+HYB_API hyb_status hyb_diag(hyb_grid* g, double out[9]);
+
+/* Synchronises the grid's stream and reports (and clears) the device-side data
+ * flag set by hyb_deposit for out-of-range particles: HYB_OK or HYB_EDATA. */
+HYB_API hyb_status hyb_check(hyb_grid* g);
+
+/* Frees the grid's tables and scratch (not the caller's arrays). NULL is a no-op. */
+HYB_API hyb_status hyb_destroy_grid(hyb_grid* g);
+
+/* Message for the last failing call on this thread ("" if none). */
+HYB_API const char* hyb_last_error(void);
+
+/* Which advance path a grid runs: 1 three-pass, 2 fused. */
+HYB_API int hyb_grid_path(const hyb_grid* g);
+
+/* Number of kernel launches one hyb_advance step of this grid issues. */
+HYB_API int hyb_launches_per_step(const hyb_grid* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYB_H_ */

@@ -1,0 +1,284 @@
+// generic.cu -- three-pass hybrid advance for any precision, 2D or 3D:
+//   (1) batched real FFT along x1 of E, B, j into a spectral scratch,
+//   (2) per-k1-mode Faraday then Ampere updates with finite differences in
+//       x2 (and x3) (Eqs. hybrid2db1-hybrid2de3; Sec. 2.4 for 3D),
+//   (3) batched inverse real FFT of E, B back in place.
+// It also provides the row FFTs used by the standalone current processing and
+// the diagnostics.  The x1 transform is a shared-memory Stockham radix-2 FFT
+// of the n1/2-point complex sequence z[j] = x[2j] + i x[2j+1] followed by the
+// standard even/odd split into the n1/2+1 real-input coefficients.
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+constexpr int kRowThreads = 256;
+
+template <typename C>
+__device__ __forceinline__ void stockham_radix2(C*& src, C*& dst, int M, const C* __restrict__ twM, bool inverse) {
+    // natural-order in, natural-order out; one __syncthreads per stage
+    for (int Ns = 1; Ns < M; Ns <<= 1) {
+        const int tstride = M / (2 * Ns);
+        for (int j = threadIdx.x; j < (M >> 1); j += blockDim.x) {
+            const int k = j & (Ns - 1);
+            C a = src[j], b = src[j + (M >> 1)];
+            C w = twM[k * tstride];
+            b = inverse ? cmulc(b, w) : cmul(b, w);
+            const int o = ((j - k) << 1) + k;
+            dst[o] = cadd(a, b);
+            dst[o + Ns] = csub(a, b);
+        }
+        __syncthreads();
+        C* t = src; src = dst; dst = t;
+    }
+}
+
+struct RowPtrs { const void* p[9]; };
+struct RowPtrsW { void* p[9]; };
+
+// X[k] = 1/2 (Z[k] + Z*[M-k]) - i/2 W_N^k (Z[k] - Z*[M-k]),  k = 0..M
+template <typename Tin, typename T>
+__global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* __restrict__ out, int n1, int64_t rows,
+                                                           const cplx<T>* __restrict__ twM, const cplx<T>* __restrict__ twN) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = n1 >> 1;
+    C* src = reinterpret_cast<C*>(smem_raw);
+    C* dst = src + M;
+    const int64_t row = blockIdx.x;
+    const int f = blockIdx.y;
+    const Tin* x = reinterpret_cast<const Tin*>(in.p[f]) + row * n1;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) src[j] = mkc<C>((T)x[2 * j], (T)x[2 * j + 1]);
+    __syncthreads();
+    stockham_radix2(src, dst, M, twM, false);
+    C* X = out + ((int64_t)f * rows + row) * (M + 1);
+    for (int k = threadIdx.x; k <= M; k += blockDim.x) {
+        C zk = src[k == M ? 0 : k];
+        C zm = src[k == 0 ? 0 : M - k];
+        C zmc = cconj(zm);
+        C e = cscale(cadd(zk, zmc), (T)0.5);
+        C d = csub(zk, zmc);
+        C w = (k < M) ? twN[k] : mkc<C>((T)-1, (T)0);
+        C wd = cmul(w, d);
+        X[k] = mkc<C>(e.x + (T)0.5 * wd.y, e.y - (T)0.5 * wd.x);
+    }
+}
+
+// inverse of the above: Z[k] = E + i O, E = (X[k] + X*[M-k])/2, O = conj(W_N^k)(X[k] - X*[M-k])/2,
+// z = IDFT_M(Z) / M, x[2j] = Re z[j], x[2j+1] = Im z[j].  DC/Nyquist imaginary parts are dropped.
+template <typename T, typename Tout>
+__global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __restrict__ in, RowPtrsW out, int n1, int64_t rows,
+                                                            const cplx<T>* __restrict__ twM, const cplx<T>* __restrict__ twN,
+                                                            int in_field0) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = n1 >> 1;
+    C* src = reinterpret_cast<C*>(smem_raw);
+    C* dst = src + M;
+    const int64_t row = blockIdx.x;
+    const int f = blockIdx.y;
+    const C* X = in + ((int64_t)(in_field0 + f) * rows + row) * (M + 1);
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        C xk = X[k], xm = X[M - k];
+        if (k == 0) { xk.y = 0; xm.y = 0; }
+        C xmc = cconj(xm);
+        C e = cscale(cadd(xk, xmc), (T)0.5);
+        C o = cscale(cmulc(csub(xk, xmc), twN[k]), (T)0.5);
+        src[k] = mkc<C>(e.x - o.y, e.y + o.x);
+    }
+    __syncthreads();
+    stockham_radix2(src, dst, M, twM, true);
+    Tout* x = reinterpret_cast<Tout*>(out.p[f]) + row * n1;
+    const T inv = (T)1 / (T)M;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        x[2 * j] = (Tout)(src[j].x * inv);
+        x[2 * j + 1] = (Tout)(src[j].y * inv);
+    }
+}
+
+template <typename Tin, typename T>
+static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
+    size_t smem = sizeof(cplx<T>) * (size_t)n1;   // 2 * M complex
+    auto kern = k_rfft_rows<Tin, T>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)rows, nf);
+    kern<<<grid, kRowThreads, smem, s>>>(p, out, n1, rows, t.twM, t.twN);
+    return cudaGetLastError();
+}
+
+template <typename T, typename Tout>
+static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, int nf, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
+    size_t smem = sizeof(cplx<T>) * (size_t)n1;
+    auto kern = k_irfft_rows<T, Tout>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)rows, nf);
+    kern<<<grid, kRowThreads, smem, s>>>(in, p, n1, rows, t.twM, t.twN, f0);
+    return cudaGetLastError();
+}
+
+template <typename Tin, typename T>
+cudaError_t rfft_rows(const Tin* in, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
+    RowPtrs p{};
+    p.p[0] = in;
+    return launch_rfft<Tin, T>(p, 1, out, n1, rows, t, s);
+}
+
+template <typename T, typename Tout>
+cudaError_t irfft_rows(const cplx<T>* in, Tout* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
+    RowPtrsW p{};
+    p.p[0] = out;
+    return launch_irfft<T, Tout>(in, 0, p, 1, n1, rows, t, s);
+}
+
+template cudaError_t rfft_rows<float, float>(const float*, float2*, int, int64_t, const ModeTables<float>&, cudaStream_t);
+template cudaError_t rfft_rows<double, double>(const double*, double2*, int, int64_t, const ModeTables<double>&, cudaStream_t);
+template cudaError_t rfft_rows<float, double>(const float*, double2*, int, int64_t, const ModeTables<double>&, cudaStream_t);
+template cudaError_t irfft_rows<float, float>(const float2*, float*, int, int64_t, const ModeTables<float>&, cudaStream_t);
+template cudaError_t irfft_rows<double, double>(const double2*, double*, int, int64_t, const ModeTables<double>&, cudaStream_t);
+
+// ----------------------------------------------------------------------------
+// per-mode updates; spec layout [9][rows][nk], fields E1 E2 E3 B1 B2 B3 J1 J2 J3,
+// row = i3 * n2 + i2.
+// Faraday:  B1 -= a2 d2+E3 - a3 d3+E2;  B2 -= a3 d3+E1 - S E3;  B3 -= S E2 - a2 d2+E1
+template <typename T, bool D3>
+__global__ void __launch_bounds__(kRowThreads) k_faraday(cplx<T>* __restrict__ spec, int nk, int n2, int n3, int64_t rows,
+                                                         const cplx<T>* __restrict__ S, T a2, T a3) {
+    using C = cplx<T>;
+    const int64_t r = blockIdx.x;
+    const int i2 = (int)(r % n2), i3 = (int)(r / n2);
+    const int64_t rp2 = (int64_t)i3 * n2 + (i2 + 1 == n2 ? 0 : i2 + 1);
+    const int64_t rp3 = D3 ? (int64_t)(i3 + 1 == n3 ? 0 : i3 + 1) * n2 + i2 : r;
+    const int64_t fs = rows * nk;
+    C* E1 = spec; C* E2 = spec + fs; C* E3 = spec + 2 * fs;
+    C* B1 = spec + 3 * fs; C* B2 = spec + 4 * fs; C* B3 = spec + 5 * fs;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        const int64_t i = r * nk + k, ip2 = rp2 * nk + k, ip3 = rp3 * nk + k;
+        C e1 = E1[i], e2 = E2[i], e3 = E3[i], s = S[k];
+        C d2e3 = cscale(csub(E3[ip2], e3), a2);
+        C d2e1 = cscale(csub(E1[ip2], e1), a2);
+        C b1 = B1[i], b2 = B2[i], b3 = B3[i];
+        b1 = csub(b1, d2e3);
+        b2 = cadd(b2, cmul(s, e3));
+        b3 = csub(b3, csub(cmul(s, e2), d2e1));
+        if (D3) {
+            C d3e2 = cscale(csub(E2[ip3], e2), a3);
+            C d3e1 = cscale(csub(E1[ip3], e1), a3);
+            b1 = cadd(b1, d3e2);
+            b2 = csub(b2, d3e1);
+        }
+        B1[i] = b1; B2[i] = b2; B3[i] = b3;
+    }
+}
+
+// Ampere (Sm = c dt sigma- = -conj(S)):
+//   E1 += a2 d2-B3 - a3 d3-B2 - cj1 J1;  E2 += a3 d3-B1 - Sm B3 - cj J2;  E3 += Sm B2 - a2 d2-B1 - cj J3
+template <typename T, bool D3>
+__global__ void __launch_bounds__(kRowThreads) k_ampere(cplx<T>* __restrict__ spec, int nk, int n2, int n3, int64_t rows,
+                                                        const cplx<T>* __restrict__ S, const T* __restrict__ cj1,
+                                                        const T* __restrict__ cj, T a2, T a3) {
+    using C = cplx<T>;
+    const int64_t r = blockIdx.x;
+    const int i2 = (int)(r % n2), i3 = (int)(r / n2);
+    const int64_t rm2 = (int64_t)i3 * n2 + (i2 == 0 ? n2 - 1 : i2 - 1);
+    const int64_t rm3 = D3 ? (int64_t)(i3 == 0 ? n3 - 1 : i3 - 1) * n2 + i2 : r;
+    const int64_t fs = rows * nk;
+    C* E1 = spec; C* E2 = spec + fs; C* E3 = spec + 2 * fs;
+    const C* B1 = spec + 3 * fs; const C* B2 = spec + 4 * fs; const C* B3 = spec + 5 * fs;
+    const C* J1 = spec + 6 * fs; const C* J2 = spec + 7 * fs; const C* J3 = spec + 8 * fs;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        const int64_t i = r * nk + k, im2 = rm2 * nk + k, im3 = rm3 * nk + k;
+        C s = S[k];
+        C sm = mkc<C>(-s.x, s.y);          // -conj(S)
+        C b1 = B1[i], b2 = B2[i], b3 = B3[i];
+        C d2b3 = cscale(csub(b3, B3[im2]), a2);
+        C d2b1 = cscale(csub(b1, B1[im2]), a2);
+        C e1 = cadd(E1[i], d2b3);
+        C e2 = csub(E2[i], cmul(sm, b3));
+        C e3 = csub(cadd(E3[i], cmul(sm, b2)), d2b1);
+        if (D3) {
+            C d3b2 = cscale(csub(b2, B2[im3]), a3);
+            C d3b1 = cscale(csub(b1, B1[im3]), a3);
+            e1 = csub(e1, d3b2);
+            e2 = cadd(e2, d3b1);
+        }
+        const T c1 = cj1[k], c = cj[k];
+        E1[i] = csub(e1, cscale(J1[i], c1));
+        E2[i] = csub(e2, cscale(J2[i], c));
+        E3[i] = csub(e3, cscale(J3[i], c));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRowThreads) k_scale_rows(cplx<T>* __restrict__ spec, int nk, int64_t rows, const T* __restrict__ fac) {
+    const int64_t r = blockIdx.x;
+    cplx<T>* X = spec + ((int64_t)blockIdx.y * rows + r) * nk;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) X[k] = cscale(X[k], fac[k]);
+}
+
+template <typename T> static const ModeTables<T>& tables(hyb_grid* g);
+template <> const ModeTables<float>& tables<float>(hyb_grid* g) { return g->tf; }
+template <> const ModeTables<double>& tables<double>(hyb_grid* g) { return g->td; }
+
+template <typename T>
+hyb_status generic_advance(hyb_grid* g, int nsteps) {
+    using C = cplx<T>;
+    const ModeTables<T>& t = tables<T>(g);
+    const int n1 = g->d.n1, nk = g->nk;
+    const int64_t rows = g->rows;
+    C* spec = reinterpret_cast<C*>(g->spec);
+    RowPtrs fin{};
+    for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; fin.p[6 + c] = g->J[c]; }
+    RowPtrsW fout{};
+    for (int c = 0; c < 3; c++) { fout.p[c] = g->E[c]; fout.p[3 + c] = g->B[c]; }
+    const T a2 = (T)(g->d.dt / g->d.dx2);
+    const T a3 = (T)(g->d.dims == 3 ? g->d.dt / g->d.dx3 : 0.0);
+    const bool d3 = g->d.dims == 3;
+    for (int s = 0; s < nsteps; s++) {
+        HYB_CUDA_TRY((launch_rfft<T, T>(fin, 9, spec, n1, rows, t, g->stream)));
+        if (d3) {
+            k_faraday<T, true><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
+            k_ampere<T, true><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, t.cj1, t.cj, a2, a3);
+        } else {
+            k_faraday<T, false><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, a2, a3);
+            k_ampere<T, false><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, t.cj1, t.cj, a2, a3);
+        }
+        HYB_CUDA_TRY(cudaGetLastError());
+        HYB_CUDA_TRY((launch_irfft<T, T>(spec, 0, fout, 6, n1, rows, t, g->stream)));
+    }
+    return HYB_OK;
+}
+
+template <typename T>
+hyb_status generic_process_current(hyb_grid* g, bool corr, bool filt) {
+    using C = cplx<T>;
+    const ModeTables<T>& t = tables<T>(g);
+    const int n1 = g->d.n1, nk = g->nk;
+    const int64_t rows = g->rows;
+    C* spec = reinterpret_cast<C*>(g->spec);
+    int nf = filt ? 3 : 1;
+    RowPtrs fin{};
+    RowPtrsW fout{};
+    for (int c = 0; c < nf; c++) { fin.p[c] = g->J[c]; fout.p[c] = g->J[c]; }
+    HYB_CUDA_TRY((launch_rfft<T, T>(fin, nf, spec, n1, rows, t, g->stream)));
+    if (filt) {
+        dim3 grid((unsigned)rows, 3);
+        k_scale_rows<T><<<grid, kRowThreads, 0, g->stream>>>(spec, nk, rows, t.filt);
+    }
+    if (corr) {
+        dim3 grid((unsigned)rows, 1);
+        k_scale_rows<T><<<grid, kRowThreads, 0, g->stream>>>(spec, nk, rows, t.corr);
+    }
+    HYB_CUDA_TRY(cudaGetLastError());
+    HYB_CUDA_TRY((launch_irfft<T, T>(spec, 0, fout, nf, n1, rows, t, g->stream)));
+    return HYB_OK;
+}
+
+hyb_status generic_launches_per_step() { return (hyb_status)4; }
+
+template hyb_status generic_advance<float>(hyb_grid*, int);
+template hyb_status generic_advance<double>(hyb_grid*, int);
+template hyb_status generic_process_current<float>(hyb_grid*, bool, bool);
+template hyb_status generic_process_current<double>(hyb_grid*, bool, bool);
+
+}  // namespace hyb

@@ -1,0 +1,312 @@
+// hyb_api.cu -- C ABI of libhyb.so (declared in include/hyb.h): validation,
+// FP64 host computation of the per-mode tables, scratch ownership and
+// dispatch to the three-pass or fused advance.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+hyb_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HYB_ENOMEM : HYB_ECUDA;
+}
+
+static const double kPi = 3.14159265358979323846;
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static double courant_limit(const hyb_grid_desc& d) {
+    double s = kPi * kPi / (d.dx1 * d.dx1) + 4.0 / (d.dx2 * d.dx2);
+    if (d.dims == 3) s += 4.0 / (d.dx3 * d.dx3);
+    return 2.0 / sqrt(s);
+}
+
+// FP64 per-mode quantities for kappa = 0..n1/2
+struct HostModes {
+    std::vector<double> keff, corr, filt, sgp_re, sgp_im;
+};
+
+static HostModes host_modes(const hyb_grid_desc& d) {
+    const int M = d.n1 / 2;
+    HostModes h;
+    h.keff.resize(M + 1); h.corr.resize(M + 1); h.filt.resize(M + 1);
+    h.sgp_re.resize(M + 1); h.sgp_im.resize(M + 1);
+    const double kn = kPi / d.dx1, kg = 2.0 * kPi / d.dx1;
+    const bool filt_on = d.filt_kc > 0.0 && d.filt_kc < 1.0;
+    for (int k = 0; k <= M; k++) {
+        const double k1 = kg * (double)k / (double)d.n1;               // 2 pi kappa / (n1 dx1)
+        const double kfd = sin(0.5 * k1 * d.dx1) / (0.5 * d.dx1);        // Yee symbol [k]1
+        double ke = k1;                                                  // hybrid: [k]1 -> k1
+        if (d.yee_mode) {
+            ke = kfd;
+        } else if (d.kmod_max != 0.0) {                                  // Sec. 4 bump
+            const double kl = d.kmod_l * kg, ku = d.kmod_u * kg, km = 0.5 * (kl + ku);
+            if (k1 >= kl && k1 <= ku) {
+                const double c = cos(0.5 * kPi * (k1 - km) / (kl - km));
+                ke += d.kmod_max * kg * c * c;
+            }
+        }
+        h.keff[k] = ke;
+        h.corr[k] = (k == 0) ? 1.0 : kfd / ke;                           // Eq. currentcorrection
+        double f = 1.0;
+        if (filt_on) {
+            const double kc = d.filt_kc * kn, w = d.filt_w * kn, a = fabs(k1);
+            if (w <= 0.0) f = a <= kc ? 1.0 : 0.0;
+            else if (a <= kc - 0.5 * w) f = 1.0;
+            else if (a >= kc + 0.5 * w) f = 0.0;
+            else { const double c = cos(0.5 * kPi * (a - kc + 0.5 * w) / w); f = c * c; }
+        }
+        h.filt[k] = f;
+        const double ph = 0.5 * k1 * d.dx1;                              // half-cell shift
+        h.sgp_re[k] = -ke * sin(ph);                                      // i ke exp(+i ph)
+        h.sgp_im[k] = ke * cos(ph);
+    }
+    return h;
+}
+
+template <typename T>
+static hyb_status upload_tables(hyb_grid* g, const HostModes& h, ModeTables<T>& t) {
+    using C = cplx<T>;
+    const hyb_grid_desc& d = g->d;
+    const int M = d.n1 / 2, nk = M + 1;
+    const double dt = d.dt, A = d.ampere;
+    std::vector<C> S(nk), sgp(nk), twM(M), twN(M);
+    std::vector<T> cj1(nk), cj(nk), corr(nk), filt(nk);
+    for (int k = 0; k < nk; k++) {
+        S[k] = mkc<C>((T)(dt * h.sgp_re[k]), (T)(dt * h.sgp_im[k]));
+        sgp[k] = mkc<C>((T)h.sgp_re[k], (T)h.sgp_im[k]);
+        const double c1 = d.correct_j1 ? h.corr[k] : 1.0;
+        cj1[k] = (T)(A * dt * h.filt[k] * c1);
+        cj[k] = (T)(A * dt * h.filt[k]);
+        corr[k] = (T)h.corr[k];
+        filt[k] = (T)h.filt[k];
+    }
+    for (int j = 0; j < M; j++) {
+        const double a = -2.0 * kPi * (double)j / (double)M;
+        twM[j] = mkc<C>((T)cos(a), (T)sin(a));
+        const double b = -2.0 * kPi * (double)j / (double)d.n1;
+        twN[j] = mkc<C>((T)cos(b), (T)sin(b));
+    }
+    const size_t bytes = sizeof(C) * (4 * (size_t)nk + 2 * (size_t)M) + sizeof(T) * 4 * (size_t)nk + 256;
+    char* base = nullptr;
+    HYB_CUDA_TRY(cudaMalloc(&base, bytes));
+    char* p = base;
+    auto take = [&](size_t n) { char* r = p; p += (n + 15) & ~(size_t)15; return r; };
+    t.S = (C*)take(sizeof(C) * nk);
+    t.sgp = (C*)take(sizeof(C) * nk);
+    t.twM = (C*)take(sizeof(C) * M);
+    t.twN = (C*)take(sizeof(C) * M);
+    t.cj1 = (T*)take(sizeof(T) * nk);
+    t.cj = (T*)take(sizeof(T) * nk);
+    t.corr = (T*)take(sizeof(T) * nk);
+    t.filt = (T*)take(sizeof(T) * nk);
+    HYB_CUDA_TRY(cudaMemcpy(t.S, S.data(), sizeof(C) * nk, cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMemcpy(t.sgp, sgp.data(), sizeof(C) * nk, cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMemcpy(t.twM, twM.data(), sizeof(C) * M, cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMemcpy(t.twN, twN.data(), sizeof(C) * M, cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMemcpy(t.cj1, cj1.data(), sizeof(T) * nk, cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMemcpy(t.cj, cj.data(), sizeof(T) * nk, cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMemcpy(t.corr, corr.data(), sizeof(T) * nk, cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMemcpy(t.filt, filt.data(), sizeof(T) * nk, cudaMemcpyHostToDevice));
+    return HYB_OK;
+}
+
+static void free_tables_f(ModeTables<float>& t) { if (t.S) cudaFree(t.S); t = ModeTables<float>(); }
+static void free_tables_d(ModeTables<double>& t) { if (t.S) cudaFree(t.S); t = ModeTables<double>(); }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace hyb
+
+using namespace hyb;
+
+extern "C" {
+
+const char* hyb_last_error(void) { return hyb::g_err; }
+
+double hyb_courant_limit(const hyb_grid_desc* desc) {
+    if (!desc) return 0.0;
+    return courant_limit(*desc);
+}
+
+hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** out) {
+    set_error("");
+    if (!desc || !out) { set_error("hyb_create_grid: null argument"); return HYB_EINVAL; }
+    *out = nullptr;
+    hyb_grid_desc d = *desc;
+    if (d.dims != 2 && d.dims != 3) { set_error("dims must be 2 or 3 (got %d)", d.dims); return HYB_EINVAL; }
+    if (d.dims == 2) { d.n3 = 1; d.dx3 = d.dx3 > 0 ? d.dx3 : 1.0; }
+    if (!is_pow2(d.n1) || d.n1 < 8 || d.n1 > 8192) { set_error("n1 must be a power of two in [8, 8192] (got %d)", d.n1); return HYB_EINVAL; }
+    if (d.n2 < 2 || (d.dims == 3 && d.n3 < 2)) { set_error("n2 (and n3 in 3D) must be >= 2"); return HYB_EINVAL; }
+    if ((int64_t)d.n2 * d.n3 > (int64_t)1 << 30) { set_error("too many rows"); return HYB_EINVAL; }
+    if (!(d.dx1 > 0 && d.dx2 > 0 && (d.dims == 2 || d.dx3 > 0) && d.dt > 0)) { set_error("cell sizes and dt must be positive"); return HYB_EINVAL; }
+    if (d.precision != 32 && d.precision != 64) { set_error("precision must be 32 or 64 (got %d)", d.precision); return HYB_EINVAL; }
+    if (d.ampere == 0.0) d.ampere = 4.0 * kPi;
+    const double cl = courant_limit(d);
+    if (d.dt > cl * (1.0 + 1e-12)) {
+        set_error("dt = %.17g exceeds the Courant limit %.17g of the hybrid solver", d.dt, cl);
+        return HYB_ECOURANT;
+    }
+    if (d.path < 0 || d.path > 2) { set_error("path must be 0, 1 or 2"); return HYB_EINVAL; }
+    const bool fused_ok = fused_supported(d);
+    if (d.path == 2 && !fused_ok) {
+        set_error("fused path needs precision 32, dims 2, n1 in [512, 4096] and n2 >= 4");
+        return HYB_EINVAL;
+    }
+    hyb_grid* g = new hyb_grid();
+    g->d = d;
+    g->stream = (cudaStream_t)stream;
+    g->path = (d.path == 0) ? (fused_ok ? 2 : 1) : d.path;
+    g->rows = (int64_t)d.n2 * d.n3;
+    g->cells = g->rows * d.n1;
+    g->nk = d.n1 / 2 + 1;
+    hyb_status st = HYB_OK;
+    cudaError_t ce = cudaGetDevice(&g->device);
+    if (ce != cudaSuccess) { st = cuda_fail(ce, "cudaGetDevice"); hyb_destroy_grid(g); return st; }
+    HostModes h = host_modes(d);
+    st = upload_tables<double>(g, h, g->td);
+    if (st == HYB_OK && d.precision == 32) st = upload_tables<float>(g, h, g->tf);
+    if (st == HYB_OK) {
+        ce = cudaMalloc(&g->diag_acc, 16 * sizeof(double));
+        if (ce == cudaSuccess) ce = cudaMalloc(&g->dflag, sizeof(int));
+        if (ce == cudaSuccess) ce = cudaMemset(g->dflag, 0, sizeof(int));
+        if (ce != cudaSuccess) st = cuda_fail(ce, "cudaMalloc(accumulators)");
+    }
+    if (st == HYB_OK) {
+        const size_t csz = d.precision == 32 ? sizeof(float2) : sizeof(double2);
+        const int nf = (g->path == 1) ? 9 : 3;
+        g->spec_bytes = (size_t)nf * g->rows * g->nk * csz;
+        ce = cudaMalloc(&g->spec, g->spec_bytes);
+        if (ce != cudaSuccess) { g->spec = nullptr; st = cuda_fail(ce, "cudaMalloc(spectral scratch)"); }
+    }
+    if (st == HYB_OK && g->path == 2) st = fused_create(g);
+    if (st != HYB_OK) { hyb_destroy_grid(g); return st; }
+    *out = g;
+    return HYB_OK;
+}
+
+hyb_status hyb_set_stream(hyb_grid* g, void* stream) {
+    if (!g) { set_error("null grid"); return HYB_EINVAL; }
+    g->stream = (cudaStream_t)stream;
+    return HYB_OK;
+}
+
+hyb_status hyb_bind_fields(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3], void* rho) {
+    if (!g || !E || !B || !J) { set_error("hyb_bind_fields: null argument"); return HYB_EINVAL; }
+    for (int c = 0; c < 3; c++) {
+        if (!E[c] || !B[c] || !J[c]) { set_error("hyb_bind_fields: null field pointer"); return HYB_EINVAL; }
+        if (!aligned16(E[c]) || !aligned16(B[c]) || !aligned16(J[c])) { set_error("hyb_bind_fields: field not 16-byte aligned"); return HYB_EALIGN; }
+    }
+    if (rho && !aligned16(rho)) { set_error("hyb_bind_fields: rho not 16-byte aligned"); return HYB_EALIGN; }
+    for (int c = 0; c < 3; c++) { g->E[c] = E[c]; g->B[c] = B[c]; g->J[c] = J[c]; }
+    g->rho = rho;
+    g->bound = true;
+    return HYB_OK;
+}
+
+hyb_status hyb_deposit(hyb_grid* g, const int32_t* cell, const void* off_old, const void* off_new,
+                       const void* v3, const void* q, int64_t np, int shape_order) {
+    if (!g) { set_error("null grid"); return HYB_EINVAL; }
+    if (!g->bound) { set_error("hyb_deposit: fields not bound"); return HYB_ESTATE; }
+    if (np < 0 || shape_order < 1 || shape_order > 3) { set_error("hyb_deposit: bad np or shape_order"); return HYB_EINVAL; }
+    if (np > 0 && (!cell || !off_old || !off_new || !q)) { set_error("hyb_deposit: null particle array"); return HYB_EINVAL; }
+    if (g->d.precision == 32)
+        return deposit<float>(g, cell, (const float*)off_old, (const float*)off_new, (const float*)v3, (const float*)q, np, shape_order);
+    return deposit<double>(g, cell, (const double*)off_old, (const double*)off_new, (const double*)v3, (const double*)q, np, shape_order);
+}
+
+hyb_status hyb_correct_current(hyb_grid* g) {
+    if (!g) { set_error("null grid"); return HYB_EINVAL; }
+    if (!g->bound) { set_error("fields not bound"); return HYB_ESTATE; }
+    return g->d.precision == 32 ? generic_process_current<float>(g, true, false) : generic_process_current<double>(g, true, false);
+}
+
+hyb_status hyb_filter(hyb_grid* g) {
+    if (!g) { set_error("null grid"); return HYB_EINVAL; }
+    if (!g->bound) { set_error("fields not bound"); return HYB_ESTATE; }
+    return g->d.precision == 32 ? generic_process_current<float>(g, false, true) : generic_process_current<double>(g, false, true);
+}
+
+hyb_status hyb_advance(hyb_grid* g, int nsteps) {
+    if (!g) { set_error("null grid"); return HYB_EINVAL; }
+    if (!g->bound) { set_error("hyb_advance: fields not bound"); return HYB_ESTATE; }
+    if (nsteps < 0) { set_error("nsteps < 0"); return HYB_EINVAL; }
+    if (nsteps == 0) return HYB_OK;
+    if (g->path == 2) return fused_advance(g, nsteps);
+    return g->d.precision == 32 ? generic_advance<float>(g, nsteps) : generic_advance<double>(g, nsteps);
+}
+
+hyb_status hyb_advance_host(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3], int nsteps) {
+    if (!g || !E || !B || !J) { set_error("hyb_advance_host: null argument"); return HYB_EINVAL; }
+    if (!g->bound) { set_error("hyb_advance_host: device fields not bound"); return HYB_ESTATE; }
+    const size_t bytes = (size_t)g->cells * (g->d.precision == 32 ? 4 : 8);
+    for (int c = 0; c < 3; c++) {
+        HYB_CUDA_TRY(cudaMemcpyAsync(g->E[c], E[c], bytes, cudaMemcpyHostToDevice, g->stream));
+        HYB_CUDA_TRY(cudaMemcpyAsync(g->B[c], B[c], bytes, cudaMemcpyHostToDevice, g->stream));
+        HYB_CUDA_TRY(cudaMemcpyAsync(g->J[c], J[c], bytes, cudaMemcpyHostToDevice, g->stream));
+    }
+    hyb_status st = hyb_advance(g, nsteps);
+    if (st != HYB_OK) return st;
+    for (int c = 0; c < 3; c++) {
+        HYB_CUDA_TRY(cudaMemcpyAsync(E[c], g->E[c], bytes, cudaMemcpyDeviceToHost, g->stream));
+        HYB_CUDA_TRY(cudaMemcpyAsync(B[c], g->B[c], bytes, cudaMemcpyDeviceToHost, g->stream));
+    }
+    HYB_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return HYB_OK;
+}
+
+hyb_status hyb_diag(hyb_grid* g, double out[9]) {
+    if (!g || !out) { set_error("null argument"); return HYB_EINVAL; }
+    if (!g->bound) { set_error("fields not bound"); return HYB_ESTATE; }
+    return g->d.precision == 32 ? diag<float>(g, out) : diag<double>(g, out);
+}
+
+hyb_status hyb_check(hyb_grid* g) {
+    if (!g) { set_error("null grid"); return HYB_EINVAL; }
+    int h = 0;
+    HYB_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    HYB_CUDA_TRY(cudaMemcpy(&h, g->dflag, sizeof(int), cudaMemcpyDeviceToHost));
+    HYB_CUDA_TRY(cudaMemset(g->dflag, 0, sizeof(int)));
+    if (h & 1) { set_error("hyb_deposit skipped particles outside the documented offset ranges"); return HYB_EDATA; }
+    if (h & 2) { set_error("a bounded device-side wait gave up"); return HYB_ETIMEOUT; }
+    return HYB_OK;
+}
+
+hyb_status hyb_destroy_grid(hyb_grid* g) {
+    if (!g) return HYB_OK;
+    if (g->stream) cudaStreamSynchronize(g->stream); else cudaDeviceSynchronize();
+    if (g->fused) fused_destroy(g);
+    free_tables_f(g->tf);
+    free_tables_d(g->td);
+    if (g->spec) cudaFree(g->spec);
+    if (g->diag_work) cudaFree(g->diag_work);
+    if (g->diag_acc) cudaFree(g->diag_acc);
+    if (g->dflag) cudaFree(g->dflag);
+    delete g;
+    return HYB_OK;
+}
+
+int hyb_grid_path(const hyb_grid* g) { return g ? g->path : 0; }
+
+int hyb_launches_per_step(const hyb_grid* g) {
+    if (!g) return 0;
+    return g->path == 2 ? fused_launches_per_step(g) : (int)generic_launches_per_step();
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of libhyb.so (C ABI: include/hyb.h).
+
+Argument marshalling only: every step of the hybrid advance, the deposit and
+the diagnostics runs in the library's CUDA kernels.  PyTorch supplies device
+memory and the current stream.  There is no CPU fallback: if the library is
+missing or cannot load, ``lib()`` raises.
+
+Module-level functions carry the C names (``hyb_create_grid``, ...); ``Grid``
+wraps them for tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhyb.so")
+
+HYB_OK, HYB_EINVAL, HYB_ECOURANT, HYB_EALIGN, HYB_ECUDA, HYB_ETIMEOUT, HYB_ESTATE, HYB_ENOMEM, HYB_EDATA = range(9)
+STATUS_NAMES = ["HYB_OK", "HYB_EINVAL", "HYB_ECOURANT", "HYB_EALIGN", "HYB_ECUDA", "HYB_ETIMEOUT",
+                "HYB_ESTATE", "HYB_ENOMEM", "HYB_EDATA"]
+
+
+class HybError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int),
+        ("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int),
+        ("dx1", ctypes.c_double), ("dx2", ctypes.c_double), ("dx3", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("correct_j1", ctypes.c_int),
+        ("filt_kc", ctypes.c_double), ("filt_w", ctypes.c_double),
+        ("kmod_l", ctypes.c_double), ("kmod_u", ctypes.c_double), ("kmod_max", ctypes.c_double),
+        ("yee_mode", ctypes.c_int),
+        ("ampere", ctypes.c_double),
+        ("path", ctypes.c_int),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+_V = ctypes.c_void_p
+_P3 = ctypes.c_void_p * 3
+
+
+def lib():
+    """Load libhyb.so (build it first with paper_1502_01376_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: run paper_1502_01376_gb300/build.py "
+                                  "(there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            S = ctypes.c_int
+            D = ctypes.POINTER(GridDesc)
+            L.hyb_courant_limit.argtypes = [D]
+            L.hyb_courant_limit.restype = ctypes.c_double
+            L.hyb_create_grid.argtypes = [D, _V, ctypes.POINTER(_V)]
+            L.hyb_create_grid.restype = S
+            L.hyb_set_stream.argtypes = [_V, _V]
+            L.hyb_set_stream.restype = S
+            L.hyb_bind_fields.argtypes = [_V, _P3, _P3, _P3, _V]
+            L.hyb_bind_fields.restype = S
+            L.hyb_deposit.argtypes = [_V, _V, _V, _V, _V, _V, ctypes.c_int64, ctypes.c_int]
+            L.hyb_deposit.restype = S
+            for fn in ("hyb_correct_current", "hyb_filter", "hyb_check", "hyb_destroy_grid"):
+                getattr(L, fn).argtypes = [_V]
+                getattr(L, fn).restype = S
+            L.hyb_advance.argtypes = [_V, ctypes.c_int]
+            L.hyb_advance.restype = S
+            L.hyb_advance_host.argtypes = [_V, _P3, _P3, _P3, ctypes.c_int]
+            L.hyb_advance_host.restype = S
+            L.hyb_diag.argtypes = [_V, ctypes.POINTER(ctypes.c_double)]
+            L.hyb_diag.restype = S
+            L.hyb_last_error.argtypes = []
+            L.hyb_last_error.restype = ctypes.c_char_p
+            L.hyb_grid_path.argtypes = [_V]
+            L.hyb_grid_path.restype = ctypes.c_int
+            L.hyb_launches_per_step.argtypes = [_V]
+            L.hyb_launches_per_step.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != HYB_OK:
+        raise HybError(st, lib().hyb_last_error().decode())
+
+
+def make_desc(dims=2, n1=128, n2=64, n3=1, dx1=0.1, dx2=0.1, dx3=0.1, dt=0.05, precision=64,
+              correct_j1=True, filt_kc=0.0, filt_w=0.0, kmod_l=0.0, kmod_u=0.0, kmod_max=0.0,
+              yee_mode=False, ampere=0.0, path=0) -> GridDesc:
+    return GridDesc(dims, n1, n2, n3, dx1, dx2, dx3, dt, precision, int(bool(correct_j1)), filt_kc, filt_w,
+                    kmod_l, kmod_u, kmod_max, int(bool(yee_mode)), ampere, path)
+
+
+def desc_from_workload(w, **over) -> GridDesc:
+    kw = dict(dims=w.dims, n1=w.n1, n2=w.n2, n3=w.n3, dx1=w.dx1, dx2=w.dx2, dx3=w.dx3, dt=w.dt,
+              precision=w.precision, correct_j1=w.correct_j1, filt_kc=w.filt_kc, filt_w=w.filt_w)
+    kw.update(over)
+    return make_desc(**kw)
+
+
+# ---- C-named thin wrappers ---------------------------------------------------
+def hyb_courant_limit(desc: GridDesc) -> float:
+    return lib().hyb_courant_limit(ctypes.byref(desc))
+
+
+def hyb_create_grid(desc: GridDesc, stream: int = 0) -> int:
+    h = _V()
+    _check(lib().hyb_create_grid(ctypes.byref(desc), _V(stream), ctypes.byref(h)))
+    return h.value
+
+
+def hyb_set_stream(g: int, stream: int):
+    _check(lib().hyb_set_stream(_V(g), _V(stream)))
+
+
+def hyb_bind_fields(g: int, E, B, J, rho=0):
+    _check(lib().hyb_bind_fields(_V(g), _P3(*E), _P3(*B), _P3(*J), _V(rho or 0)))
+
+
+def hyb_deposit(g: int, cell: int, off_old: int, off_new: int, v3: int, q: int, np_: int, order: int):
+    _check(lib().hyb_deposit(_V(g), _V(cell), _V(off_old), _V(off_new), _V(v3 or 0), _V(q), np_, order))
+
+
+def hyb_correct_current(g: int):
+    _check(lib().hyb_correct_current(_V(g)))
+
+
+def hyb_filter(g: int):
+    _check(lib().hyb_filter(_V(g)))
+
+
+def hyb_advance(g: int, nsteps: int):
+    _check(lib().hyb_advance(_V(g), nsteps))
+
+
+def hyb_advance_host(g: int, E, B, J, nsteps: int):
+    _check(lib().hyb_advance_host(_V(g), _P3(*E), _P3(*B), _P3(*J), nsteps))
+
+
+def hyb_diag(g: int) -> np.ndarray:
+    out = (ctypes.c_double * 9)()
+    _check(lib().hyb_diag(_V(g), out))
+    return np.array(list(out))
+
+
+def hyb_check(g: int):
+    _check(lib().hyb_check(_V(g)))
+
+
+def hyb_destroy_grid(g: int):
+    _check(lib().hyb_destroy_grid(_V(g)))
+
+
+def hyb_last_error() -> str:
+    return lib().hyb_last_error().decode()
+
+
+def hyb_grid_path(g: int) -> int:
+    return lib().hyb_grid_path(_V(g))
+
+
+def hyb_launches_per_step(g: int) -> int:
+    return lib().hyb_launches_per_step(_V(g))
+
+
+# ---- tensor convenience ----------------------------------------------------------
+def _ptr(t):
+    return 0 if t is None else int(t.data_ptr())
+
+
+class Grid:
+    """A grid bound to torch CUDA tensors E, B, J (lists of 3) and optional rho."""
+
+    def __init__(self, desc: GridDesc, stream=None):
+        import torch
+        self.desc = desc
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = hyb_create_grid(desc, self.stream.cuda_stream)
+        self.dtype = torch.float32 if desc.precision == 32 else torch.float64
+        self.tensors = None
+
+    @property
+    def shape(self):
+        d = self.desc
+        return (d.n3, d.n2, d.n1) if d.dims == 3 else (d.n2, d.n1)
+
+    def _chk(self, t):
+        assert t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and tuple(t.shape) == self.shape, \
+            (t.device, t.dtype, tuple(t.shape), self.shape)
+
+    def bind(self, E, B, J, rho=None):
+        for t in list(E) + list(B) + list(J) + ([rho] if rho is not None else []):
+            self._chk(t)
+        self.tensors = (list(E), list(B), list(J), rho)
+        hyb_bind_fields(self.h, [_ptr(t) for t in E], [_ptr(t) for t in B], [_ptr(t) for t in J], _ptr(rho))
+        return self
+
+    def deposit(self, cell, off_old, off_new, v3, q, order):
+        n = q.numel()
+        hyb_deposit(self.h, _ptr(cell), _ptr(off_old), _ptr(off_new), _ptr(v3), _ptr(q), n, order)
+
+    def correct_current(self):
+        hyb_correct_current(self.h)
+
+    def filter(self):
+        hyb_filter(self.h)
+
+    def advance(self, nsteps=1):
+        hyb_advance(self.h, nsteps)
+
+    def advance_host(self, E, B, J, nsteps=1):
+        """E, B, J: pinned CPU tensors of the grid's dtype (E, B updated in place)."""
+        hyb_advance_host(self.h, [_ptr(t) for t in E], [_ptr(t) for t in B], [_ptr(t) for t in J], nsteps)
+
+    def diag(self):
+        return hyb_diag(self.h)
+
+    def check(self):
+        hyb_check(self.h)
+
+    @property
+    def path(self):
+        return hyb_grid_path(self.h)
+
+    @property
+    def launches_per_step(self):
+        return hyb_launches_per_step(self.h)
+
+    def close(self):
+        if self.h:
+            hyb_destroy_grid(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

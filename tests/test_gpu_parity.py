@@ -1,0 +1,274 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: 1e-12 relative per field for the FP64 GPU path, 1e-5 for FP32
+(relative L2 error ||gpu - oracle|| / ||oracle|| per field)."""
+import numpy as np
+import pytest
+
+from paper_1502_01376_gb300 import workloads as wl
+
+from gpu_util import hyb_module, need_gpu, orc_grid, rel_err, to_dev, to_np, torch
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 1e-5}
+
+
+def _setup(hyb, w, path=0, **over):
+    dt = torch.float64 if w.precision == 64 else torch.float32
+    desc = hyb.desc_from_workload(w, path=path, **over)
+    g = hyb.Grid(desc)
+    E0, B0 = wl.band_limited_fields(w)
+    E = [to_dev(a, dt) for a in E0]
+    B = [to_dev(a, dt) for a in B0]
+    J = [torch.zeros(w.shape, device="cuda", dtype=dt) for _ in range(3)]
+    g.bind(E, B, J)
+    return g, E0, B0, E, B, J
+
+
+def _compare(E, B, Eo, Bo, tol, tag=""):
+    errs = [rel_err(to_np(a), b) for a, b in zip(E + B, Eo + Bo)]
+    assert max(errs) < tol, (tag, errs)
+    return errs
+
+
+@pytest.mark.parametrize("path", [1, 0])
+def test_vacuum_beam_workload_fp64_100_steps(orc, path):
+    """Config: 2D 128x64 FP64, beam of 4096 particles at 0.99c, deposit each step, 100 steps."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.VACUUM_BEAM
+    g, E0, B0, E, B, J = _setup(hyb, w, path=path)
+    go = orc_grid(orc, w)
+    p = wl.make_particles(w)
+    Eo = [a.copy() for a in E0]
+    Bo = [a.copy() for a in B0]
+    for n in range(w.steps):
+        cell, off0, off1, v3 = wl.ballistic_move(w, p, n)
+        Jo = orc.deposit(go, cell, off0, off1, v3, p.q, w.shape_order)
+        orc.step(go, Eo, Bo, Jo)
+        g.deposit(torch.from_numpy(cell).cuda(), to_dev(off0, torch.float64), to_dev(off1, torch.float64),
+                  to_dev(v3, torch.float64), to_dev(p.q, torch.float64), w.shape_order)
+        g.advance(1)
+        if n in (0, 9):
+            _compare(E, B, Eo, Bo, TOL[64], f"step {n}")
+    g.check()
+    _compare(E, B, Eo, Bo, TOL[64], "final")
+
+
+@pytest.mark.parametrize("n1,n2", [(64, 37), (256, 12), (1024, 5)])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_three_pass_random_fields(orc, n1, n2, prec):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("t", 2, n1, n2, dx1=0.2, dx2=0.25, dt=0.08, precision=prec, filt_kc=0.5, filt_w=0.2, seed=3)
+    g, E0, B0, E, B, J = _setup(hyb, w, path=1)
+    rng = np.random.default_rng(4)
+    J0 = [rng.standard_normal(w.shape) * 1e-3 for _ in range(3)]
+    dt = torch.float64 if prec == 64 else torch.float32
+    for c in range(3):
+        J[c].copy_(to_dev(J0[c], dt))
+    rnd = (lambda a: a) if prec == 64 else (lambda a: a.astype(np.float32).astype(np.float64))
+    Jin = [rnd(a) for a in J0]               # inputs rounded on the host exactly as the GPU sees them
+    Ein = [rnd(a) for a in E0]
+    Bin = [rnd(a) for a in B0]
+    go = orc_grid(orc, w)
+    nst = 10
+    orc.step(go, Ein, Bin, Jin, nsteps=nst)
+    g.advance(nst)
+    _compare(E, B, Ein, Bin, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_three_pass_3d(orc, prec):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("t3", 3, 64, 12, 10, dx1=0.2, dx2=0.2, dx3=0.25, dt=0.06, precision=prec,
+                    filt_kc=0.6, filt_w=0.2, seed=5)
+    g, E0, B0, E, B, J = _setup(hyb, w, path=1)
+    rng = np.random.default_rng(6)
+    dt = torch.float64 if prec == 64 else torch.float32
+    J0 = [rng.standard_normal(w.shape) * 1e-3 for _ in range(3)]
+    for c in range(3):
+        J[c].copy_(to_dev(J0[c], dt))
+    rnd = (lambda a: a) if prec == 64 else (lambda a: a.astype(np.float32).astype(np.float64))
+    Jin = [rnd(a) for a in J0]
+    Ein = [rnd(a) for a in E0]
+    Bin = [rnd(a) for a in B0]
+    go = orc_grid(orc, w)
+    orc.step(go, Ein, Bin, Jin, nsteps=5)
+    g.advance(5)
+    _compare(E, B, Ein, Bin, TOL[prec])
+
+
+@pytest.mark.parametrize("yee", [True, False])
+def test_yee_mode_and_bump(orc, yee):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("ty", 2, 128, 16, dx1=0.2, dx2=0.2, dt=0.08, precision=64, seed=8)
+    over = dict(yee_mode=True) if yee else dict(kmod_l=0.15, kmod_u=0.26, kmod_max=0.01)
+    g, E0, B0, E, B, J = _setup(hyb, w, path=1, **over)
+    go = orc_grid(orc, w, **over)
+    Eo, Bo = [a.copy() for a in E0], [a.copy() for a in B0]
+    Jo = [np.zeros(w.shape) for _ in range(3)]
+    orc.step(go, Eo, Bo, Jo, nsteps=4)
+    g.advance(4)
+    _compare(E, B, Eo, Bo, TOL[64])
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("dims", [2, 3])
+def test_deposit_matches_oracle(orc, prec, order, dims):
+    need_gpu()
+    hyb = hyb_module()
+    if dims == 2:
+        w = wl.Workload("td", 2, 64, 24, dx1=0.2, dx2=0.3, dt=0.07, precision=prec, kind="plasma", ppc=2,
+                        gamma=3.0, u_th=0.3, shape_order=order, seed=9)
+    else:
+        w = wl.Workload("td3", 3, 16, 8, 6, dx1=0.2, dx2=0.3, dx3=0.25, dt=0.05, precision=prec, kind="plasma",
+                        ppc=1, gamma=2.0, u_th=0.3, shape_order=order, seed=10)
+    real = np.float64 if prec == 64 else np.float32
+    dt = torch.float64 if prec == 64 else torch.float32
+    g, E0, B0, E, B, J = _setup(hyb, w, path=1)
+    p = wl.make_particles(w)
+    cell, off0, off1, v3 = wl.ballistic_move(w, p, 2, real=real)
+    q = p.q.astype(real)
+    g.deposit(torch.from_numpy(cell).cuda(), to_dev(off0, dt), to_dev(off1, dt),
+              to_dev(v3, dt) if dims == 2 else None, to_dev(q, dt), order)
+    g.check()
+    go = orc_grid(orc, w)
+    Jo = orc.deposit(go, cell, off0.astype(np.float64), off1.astype(np.float64),
+                     v3.astype(np.float64), q.astype(np.float64), order)
+    tol = 1e-12 if prec == 64 else 1e-5
+    for a, b in zip(J, Jo):
+        assert rel_err(to_np(a), b) < tol
+
+
+def test_deposit_flags_bad_particles():
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("tb", 2, 16, 8, dx1=0.2, dx2=0.2, dt=0.05, precision=64)
+    g, E0, B0, E, B, J = _setup(hyb, w, path=1)
+    cell = torch.tensor([[2, 3], [4, 4]], dtype=torch.int32, device="cuda")
+    off0 = torch.tensor([[0.5, 0.5], [0.5, 0.5]], dtype=torch.float64, device="cuda")
+    off1 = torch.tensor([[0.6, 0.5], [1.7, 0.5]], dtype=torch.float64, device="cuda")   # second moves > 1 cell
+    q = torch.ones(2, dtype=torch.float64, device="cuda")
+    g.deposit(cell, off0, off1, None, q, 1)
+    with pytest.raises(hyb.HybError) as e:
+        g.check()
+    assert e.value.status == hyb.HYB_EDATA
+    g.check()        # flag cleared
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_standalone_correction_and_filter(orc, prec):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("tc", 2, 256, 10, dx1=0.2, dx2=0.2, dt=0.08, precision=prec, filt_kc=0.45, filt_w=0.3, seed=11)
+    g, E0, B0, E, B, J = _setup(hyb, w, path=1)
+    dt = torch.float64 if prec == 64 else torch.float32
+    rng = np.random.default_rng(12)
+    J0 = [rng.standard_normal(w.shape) for _ in range(3)]
+    for c in range(3):
+        J[c].copy_(to_dev(J0[c], dt))
+    rnd = (lambda a: a) if prec == 64 else (lambda a: a.astype(np.float32).astype(np.float64))
+    Jo = [rnd(a) for a in J0]
+    go = orc_grid(orc, w)
+    g.correct_current()
+    orc.process_current(go, Jo, True, False)
+    g.filter()
+    orc.process_current(go, Jo, False, True)
+    for a, b in zip(J, Jo):
+        assert rel_err(to_np(a), b) < (1e-13 if prec == 64 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_diag_matches_oracle(orc, prec):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.VACUUM_BEAM.scaled(n1=64, n2=20, n_particles=32, precision=prec, filt_kc=0.5, filt_w=0.2)
+    dt = torch.float64 if prec == 64 else torch.float32
+    desc = hyb.desc_from_workload(w, path=1)
+    g = hyb.Grid(desc)
+    E0, B0 = wl.band_limited_fields(w)
+    E = [to_dev(a, dt) for a in E0]
+    B = [to_dev(a, dt) for a in B0]
+    J = [torch.zeros(w.shape, device="cuda", dtype=dt) for _ in range(3)]
+    p = wl.make_particles(w)
+    go = orc_grid(orc, w)
+    cell, off0 = wl.position_at(w, p, 0)
+    rho_np = orc.charge(go, cell, off0, p.q, 1)
+    rho = to_dev(rho_np, dt)
+    g.bind(E, B, J, rho)
+    got = g.diag()
+    rnd = (lambda a: a) if prec == 64 else (lambda a: a.astype(np.float32).astype(np.float64))
+    want = orc.diag(go, [rnd(a) for a in E0], [rnd(a) for a in B0], rnd(rho_np))
+    tol = 1e-11 if prec == 64 else 1e-5
+    assert np.allclose(got[:6], want[:6], rtol=tol, atol=0)
+    assert got[6] == pytest.approx(want[6], rel=1e-6 if prec == 32 else 1e-9)
+    assert got[7] == pytest.approx(want[7], rel=1e-6 if prec == 32 else 1e-9)
+    assert got[8] == pytest.approx(want[8], rel=1e-6 if prec == 32 else 1e-9)
+
+
+def test_gauss_invariant_on_gpu(orc):
+    """Gauss residual from the GPU's own diagnostic stays constant with the correction (Sec. 2.3)."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.VACUUM_BEAM.scaled(n1=64, n2=32, n_particles=128)
+    desc = hyb.desc_from_workload(w)
+    g = hyb.Grid(desc)
+    E0, B0 = wl.band_limited_fields(w)
+    E = [to_dev(a, torch.float64) for a in E0]
+    B = [to_dev(a, torch.float64) for a in B0]
+    J = [torch.zeros(w.shape, device="cuda", dtype=torch.float64) for _ in range(3)]
+    rho = torch.zeros(w.shape, device="cuda", dtype=torch.float64)
+    g.bind(E, B, J, rho)
+    p = wl.make_particles(w)
+    go = orc_grid(orc, w)
+    for n in range(20):
+        cell, off0, off1, v3 = wl.ballistic_move(w, p, n)
+        rho.copy_(to_dev(orc.charge(go, cell, off0, p.q, 1), torch.float64))
+        g0 = g.diag()
+        g.deposit(torch.from_numpy(cell).cuda(), to_dev(off0, torch.float64), to_dev(off1, torch.float64),
+                  to_dev(v3, torch.float64), to_dev(p.q, torch.float64), 1)
+        g.advance(1)
+        rho.copy_(to_dev(orc.charge(go, cell, off1, p.q, 1), torch.float64))
+        g1 = g.diag()
+        assert abs(g1[8] - g0[8]) < 1e-11 * max(g0[8], 1.0)
+
+
+def test_advance_host_matches_device(orc):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("th", 2, 128, 16, dx1=0.2, dx2=0.2, dt=0.08, precision=64, seed=13)
+    g, E0, B0, E, B, J = _setup(hyb, w, path=1)
+    Eh = [torch.from_numpy(a.copy()).pin_memory() for a in E0]
+    Bh = [torch.from_numpy(a.copy()).pin_memory() for a in B0]
+    Jh = [torch.zeros(w.shape, dtype=torch.float64).pin_memory() for _ in range(3)]
+    g.advance_host(Eh, Bh, Jh, 3)
+    g.advance(0)
+    Eo, Bo = [a.copy() for a in E0], [a.copy() for a in B0]
+    orc.step(orc_grid(orc, w), Eo, Bo, [np.zeros(w.shape)] * 3, nsteps=3)
+    for a, b in zip(Eh + Bh, Eo + Bo):
+        assert rel_err(a.numpy(), b) < 1e-12
+
+
+def test_courant_rejected_and_alignment():
+    need_gpu()
+    hyb = hyb_module()
+    d = hyb.make_desc(n1=64, n2=16, dx1=0.2, dx2=0.2, dt=0.2)
+    with pytest.raises(hyb.HybError) as e:
+        hyb.Grid(d)
+    assert e.value.status == hyb.HYB_ECOURANT
+    d = hyb.make_desc(n1=64, n2=16, dx1=0.2, dx2=0.2, dt=0.05, precision=64)
+    g = hyb.Grid(d)
+    base = torch.zeros(64 * 16 + 1, dtype=torch.float64, device="cuda")
+    ok = [torch.zeros(64 * 16, dtype=torch.float64, device="cuda") for _ in range(8)]
+    ptrs = [int(t.data_ptr()) for t in ok]
+    with pytest.raises(hyb.HybError) as e:
+        hyb.hyb_bind_fields(g.h, [int(base.data_ptr()) + 8] + ptrs[:2], ptrs[2:5], ptrs[5:8])
+    assert e.value.status == hyb.HYB_EALIGN
+    with pytest.raises(hyb.HybError) as e:
+        g.advance(1)
+    assert e.value.status == hyb.HYB_ESTATE
