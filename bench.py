@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the hybrid Yee-FFT field advance on GB300.
+
+Workload: the 2D drifting-plasma grid, 4096 x 1024 cells, FP32 fields,
+dx = 0.2, dt = 0.1, J1 correction + k1 low-pass filter (kc = 0.5 of Nyquist);
+J deposited once (charge-conserving, quadratic shapes) from 8 + 8 particles
+per cell drifting at gamma = 50, before timing.  A step is one hyb_advance
+(FFT of E, B, J along x1, J1 correction, filter, Faraday + Ampere per k1 mode,
+inverse FFT).  Metric: cell-steps/s.  L2 is flushed (256 MB write) between
+timed steps; each step is timed with CUDA events on the grid's stream.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on the
+host cores on bounded samples of the same workload.  With torchrun (N > 1)
+every rank runs an independent replica (the path does not shard across
+GPUs here); value = N * cells / max-over-ranks step time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hybrid-solver cell-steps/s on 1 GB300 at <=1e-5 rel err vs FP64; % HBM roofline"
+UNIT = "cell-steps/s"
+BYTES_PER_CELL_STEP = 60          # read E, B, J (9 words) + write E, B (6 words), FP32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and fp64 comparison")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fused2d.cu", "hyb_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1502_01376_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(cells):
+    """dram bytes per launch of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "fused2d_drift_plasma_4096x1024.md")
+    if not os.path.exists(path):
+        return None
+    src_hash, per_cell = None, None
+    for line in open(path):
+        if line.startswith("kernel_source_hash:"):
+            src_hash = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_cell:"):
+            per_cell = float(line.split(":", 1)[1].strip())
+    if src_hash != kernel_source_hash() or per_cell is None:
+        return None
+    return per_cell * cells
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def mark(self, begin):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        inside = [r for t, r in self.rows if self.t0 and self.t1 and self.t0 <= t <= self.t1]
+        use = inside if inside else [r for _, r in self.rows]
+        sm = [float(r[0]) for r in use if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in use if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i in range(4) if len(r) > 4 + i and r[4 + i] == "Active"})
+        pw = [float(r[2]) for r in use if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(use), "in_timed_region": bool(inside),
+                "power_w_max": max(pw) if pw else None}
+
+
+def cpu_baseline_sample(workload, budget_s=15.0):
+    """The oracle as it stands on a bounded sample of the workload: the full
+    4096-point x1 rows on a 4096 x R periodic strip, timed on the host cores."""
+    import numpy as np
+    import oracle
+    from paper_1502_01376_gb300 import workloads as wl
+    rows = 64
+    w = workload.scaled(n2=rows)
+    g = oracle.grid(n1=w.n1, n2=w.n2, dx1=w.dx1, dx2=w.dx2, dt=w.dt, filt_kc=w.filt_kc, filt_w=w.filt_w)
+    E, B = wl.band_limited_fields(w)
+    rng = np.random.default_rng(0)
+    J = [rng.standard_normal(w.shape) * 1e-3 for _ in range(3)]
+    oracle.step(g, E, B, J, 1)                 # warm
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.step(g, E, B, J, 1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 200:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": w.cells * n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} oracle steps of a {w.n1} x {rows} periodic strip of the workload ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    from paper_1502_01376_gb300 import workloads as wl
+    w = wl.DRIFT_PLASMA
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    oracle.build()
+    rows = 4
+    ws_ = w.scaled(n2=rows)
+    g = oracle.grid(n1=ws_.n1, n2=ws_.n2, dx1=ws_.dx1, dx2=ws_.dx2, dt=ws_.dt, filt_kc=ws_.filt_kc, filt_w=ws_.filt_w)
+    E, B = wl.band_limited_fields(ws_)
+    rng = np.random.default_rng(0)
+    J = [rng.standard_normal(ws_.shape) * 1e-3 for _ in range(3)]
+    for _ in range(args.warmup):
+        oracle.step(g, E, B, J, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.step(g, E, B, J, 1)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = ws_.cells / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample_rows": rows, "n1": w.n1, "n2_full": w.n2},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"each step: one oracle step of a {ws_.n1} x {rows} periodic strip of the workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1502_01376_gb300 import build, hyb, workloads as wl
+    if rank == 0 or ws == 1:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    w = wl.DRIFT_PLASMA
+    stream = torch.cuda.current_stream()
+    grid = hyb.Grid(hyb.desc_from_workload(w, path=0), stream)
+    E0, B0 = wl.band_limited_fields(w)
+    E = [torch.from_numpy(a.astype(np.float32)).to(dev) for a in E0]
+    B = [torch.from_numpy(a.astype(np.float32)).to(dev) for a in B0]
+    J = [torch.zeros(w.shape, dtype=torch.float32, device=dev) for _ in range(3)]
+    grid.bind(E, B, J)
+    # J^{n+1/2} of the drifting plasma, deposited once (not part of the timed step)
+    cell, off0, off1, v3, q = wl.plasma_move_torch(w, dev)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    grid.deposit(cell, off0, off1, v3, q, w.shape_order)
+    t1.record()
+    grid.check()
+    deposit_ms = t0.elapsed_time(t1)
+    n_particles = int(q.numel())
+    del cell, off0, off1, v3, q
+    torch.cuda.empty_cache()
+
+    cells = w.cells
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    for _ in range(args.warmup):
+        grid.advance(1)
+    torch.cuda.synchronize()
+    K = args.steps
+    ek = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.5)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark(True)
+    wall0 = time.perf_counter()
+    for i in range(K):
+        flush.zero_()
+        grid.set_kernel_events(*ek[i])
+        es[i][0].record(stream)
+        grid.advance(1)
+        es[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        torch.distributed.barrier()
+    if sampler:
+        sampler.mark(False)
+        sampler.stop()
+    grid.set_kernel_events(None, None)
+    step_ms = [a.elapsed_time(b) for a, b in es]
+    kern_ms = [a.elapsed_time(b) for a, b in ek]
+    ms = statistics.mean(step_ms)
+    kms = statistics.mean(kern_ms)
+    if ws > 1:
+        t = torch.tensor([ms, kms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, kms = float(t[0]), float(t[1])
+    value = ws * cells / (ms / 1e3)
+    launches = grid.launches_per_step * K
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # accuracy of the FP32 step against the FP64 GPU path from identical inputs
+        g64 = hyb.Grid(hyb.desc_from_workload(w, precision=64, path=1), stream)
+        E64 = [t.double() for t in E]
+        B64 = [t.double() for t in B]
+        J64 = [t.double() for t in J]
+        g64.bind(E64, B64, J64)
+        Ec = [t.clone() for t in E]
+        Bc = [t.clone() for t in B]
+        g32 = hyb.Grid(hyb.desc_from_workload(w, path=0), stream)
+        g32.bind(Ec, Bc, J)
+        nacc = 10
+        g32.advance(nacc)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g64.advance(nacc)
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / nacc
+        errs = []
+        for a, b in zip(Ec + Bc, E64 + B64):
+            errs.append(float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b)))
+        extras["accuracy"] = {"steps": nacc, "max_rel_err_vs_fp64_gpu_path": max(errs),
+                              "per_field": dict(zip(["E1", "E2", "E3", "B1", "B2", "B3"], errs))}
+        extras["fp64_gpu_path"] = {"value": cells / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64}
+        g64.close()
+        g32.close()
+        del E64, B64, J64, Ec, Bc
+        # end to end through the public API with host buffers (pinned)
+        Eh = [t.cpu().pin_memory() for t in E]
+        Bh = [t.cpu().pin_memory() for t in B]
+        Jh = [t.cpu().pin_memory() for t in J]
+        grid.advance_host(Eh, Bh, Jh, 1)
+        ne = 10
+        tt = time.perf_counter()
+        for _ in range(ne):
+            grid.advance_host(Eh, Bh, Jh, 1)
+        e2e_s = (time.perf_counter() - tt) / ne
+        extras["e2e"] = {"value": cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 9 * 4 * cells,
+                         "d2h_bytes_per_step": 6 * 4 * cells, "ms_per_step": 1e3 * e2e_s}
+        if ws == 1:
+            extras["cpu_baseline"] = cpu_baseline_sample(w)
+    if rank == 0:
+        peak, src = peaks()
+        achieved = BYTES_PER_CELL_STEP * cells / (kms / 1e3) / 1e9
+        traffic = profiled_traffic(cells)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n1": w.n1, "n2": w.n2, "dx": w.dx1, "dt": w.dt,
+                       "correct_j1": True, "filter_kc": w.filt_kc, "filter_w": w.filt_w,
+                       "particles_deposited": n_particles, "deposit_ms": deposit_ms,
+                       "path": "fused" if grid.path == 2 else "three-pass",
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+                         "kernel": "k_fused2d<4096>" if grid.path == 2 else "three-pass step",
+                         "kernel_ms": kms, "bytes_per_launch": BYTES_PER_CELL_STEP * cells},
+            "gpu_launches": launches,
+            "wall_s_timed": wall,
+        }
+        if sampler:
+            line["clocks"] = sampler.summary()
+        if "e2e" in extras:
+            line["e2e"] = extras.pop("e2e")
+        if "cpu_baseline" in extras:
+            line["cpu_baseline"] = extras.pop("cpu_baseline")
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

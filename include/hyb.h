@@ -145,6 +145,13 @@ HYB_API hyb_status hyb_destroy_grid(hyb_grid* g);
 /* Message for the last failing call on this thread ("" if none). */
 HYB_API const char* hyb_last_error(void);
 
+/* Instrumentation: start and stop are cudaEvent_t handles (NULL disables).
+ * While set, every step of hyb_advance records start immediately before and
+ * stop immediately after the launch of its dominant kernel (the fused kernel
+ * on path 2; the whole step on path 1), on the grid's stream, so a caller can
+ * time that kernel alone.  The events are borrowed, not owned. */
+HYB_API hyb_status hyb_set_kernel_events(hyb_grid* g, void* start, void* stop);
+
 /* Which advance path a grid runs: 1 three-pass, 2 fused. */
 HYB_API int hyb_grid_path(const hyb_grid* g);
 

@@ -1,11 +1,708 @@
-// fused2d.cu -- placeholder until the single-pass FP32 kernel lands.
+// fused2d.cu -- single-pass FP32 hybrid advance for 2D grids with
+// n1 in {512, 1024, 2048, 4096}: one kernel reads E^n, B^{n-1/2}, j^{n+1/2}
+// once from HBM and writes E^{n+1}, B^{n+1/2} once (15 words per cell).
+//
+// Work decomposition.  The Faraday/Ampere updates of Eqs. hybrid2db1-de3 are
+// pointwise in the x1 mode kappa and couple only neighbouring x2 rows, so each
+// CTA sweeps a strip of consecutive x2 rows, keeping the k1-space lines it
+// still needs in shared memory ("slots"): E1, E3 of rows p and p+1, E2 of row
+// p, B1, B3 of rows p-1 and p, B2 of row p (10 lines).  Rows just outside the
+// strip (E, B1, B3 of row p0-1; E1, E3 of row p1) are copied each step by a
+// small kernel into a halo buffer before any CTA overwrites them.
+//
+// The CTA has three thread groups of T = n1/32 threads; in every "round" each
+// group performs one real FFT of one row (forward or inverse), so the three
+// groups run in lock-step and share __syncthreads:
+//   R1  FFT E1(p+1), E3(p+1), E2(p)                            -> slots
+//   R2  FFT B1(p), B2(p), B3(p); Faraday update                 -> slots
+//   R3  FFT j1(p), j2(p), j3(p); j1 correction, filter, Ampere  -> E slots
+//   R4  inverse FFT E1(p), E2(p), E3(p)                         -> HBM
+//   R5  inverse FFT B1(p), B2(p), B3(p)                         -> HBM
+//
+// Real FFT of n1 = N points: the N/2 = M-point complex FFT of
+// z[j] = x[2j] + i x[2j+1], factored M = 16 * 16 * P3 (P3 = T/16):
+//   stage 1: thread n_a = t holds z[t + T n_b], 16-point DFT over n_b, twiddle W_M^{t k_b};
+//   stage 2: thread (k_b, m_a) gathers 16 values over m_b from shared memory,
+//            16-point DFT, twiddle W_T^{m_a l_b};
+//   stage 3: thread gathers P3 values of a column c = k_b + 16 l_b, P3-point DFT
+//            -> Z[c + 256 l_a].
+// Each thread owns column pairs {c, 256 - c}, so the even/odd split that turns
+// Z into the N/2+1 real-input coefficients X (it pairs kappa with M - kappa)
+// happens in registers; a thread owns the same set of kappa for every line,
+// so the per-mode updates are thread-local reads and writes of slots.  The
+// DC and Nyquist coefficients (both real) are packed into one complex slot.
+#include <math.h>
+
+#include <vector>
+
 #include "hyb_internal.cuh"
 
 namespace hyb {
-struct FusedPlan {};
-bool fused_supported(const hyb_grid_desc&) { return false; }
-hyb_status fused_create(hyb_grid*) { set_error("fused path unavailable"); return HYB_EINVAL; }
-void fused_destroy(hyb_grid* g) { delete g->fused; g->fused = nullptr; }
-hyb_status fused_advance(hyb_grid*, int) { set_error("fused path unavailable"); return HYB_EINVAL; }
-int fused_launches_per_step(const hyb_grid*) { return 0; }
+
+struct FusedPlan {
+    int n_strips = 0;
+    int* strip0 = nullptr;        // [n_strips + 1] first row of each strip (device)
+    float* halo = nullptr;        // [n_strips][7][n1]
+    float4* sym = nullptr;        // [M + 1] {Re S, Im S, cj1, cj}, S = c dt sigma+
+    float2* twM = nullptr;        // [M] W_M^j
+    float2* twC = nullptr;        // [256] W_N^c
+    size_t smem = 0;
+    int threads = 0;
+};
+
+// ------------------------------------------------------------------ complex
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return f2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
+__device__ __forceinline__ float2 mulc(float2 a, float2 b) { return f2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y)); }  // a conj(b)
+__device__ __forceinline__ float2 scl(float2 a, float s) { return f2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return f2(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV> __device__ __forceinline__ float2 rot(float2 a) { return INV ? f2(-a.y, a.x) : f2(a.y, -a.x); }
+
+// W_R^k as compile-time constants (forward sign); INV conjugates
+template <int R, int K, bool INV>
+__device__ __forceinline__ float2 wconst() {
+    constexpr double PI = 3.14159265358979323846;
+    constexpr int k = ((K % R) + R) % R;
+    // cos/sin of 2 pi k / R for the few R used here (exact table of constants)
+    constexpr double c = (R == 1 || k == 0) ? 1.0
+        : (4 * k == R) ? 0.0 : (2 * k == R) ? -1.0 : (4 * k == 3 * R) ? 0.0
+        : (R == 8 && (k == 1 || k == 7)) ? 0.70710678118654752440 : (R == 8) ? -0.70710678118654752440
+        : (R == 16) ? ((k == 1 || k == 15) ? 0.92387953251128675613 : (k == 2 || k == 14) ? 0.70710678118654752440
+                      : (k == 3 || k == 13) ? 0.38268343236508977173 : (k == 5 || k == 11) ? -0.38268343236508977173
+                      : (k == 6 || k == 10) ? -0.70710678118654752440 : -0.92387953251128675613)
+        : 0.0;
+    constexpr double s = (R == 1 || k == 0 || 2 * k == R) ? 0.0
+        : (4 * k == R) ? 1.0 : (4 * k == 3 * R) ? -1.0
+        : (R == 8) ? ((k < 4) ? 0.70710678118654752440 : -0.70710678118654752440)
+        : (R == 16) ? ((k == 1 || k == 7) ? 0.38268343236508977173 : (k == 2 || k == 6) ? 0.70710678118654752440
+                      : (k == 3 || k == 5) ? 0.92387953251128675613 : (k == 9 || k == 15) ? -0.38268343236508977173
+                      : (k == 10 || k == 14) ? -0.70710678118654752440 : -0.92387953251128675613)
+        : 0.0;
+    (void)PI;
+    // W_R^k = exp(-2 pi i k / R) = c - i s
+    return INV ? f2((float)c, (float)s) : f2((float)c, (float)-s);
+}
+
+// W_R^k for R | 16 with k known after unrolling (folds to a constant)
+__device__ __forceinline__ float2 wr(int R, int k) {
+    const int j = ((k * (16 / R)) % 16 + 16) % 16;      // angle in units of 2 pi / 16
+    const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h = 0.70710678118654752440f;
+    switch (j) {
+    case 0: return f2(1.f, 0.f);
+    case 1: return f2(c1, -s1);
+    case 2: return f2(h, -h);
+    case 3: return f2(s1, -c1);
+    case 4: return f2(0.f, -1.f);
+    case 5: return f2(-s1, -c1);
+    case 6: return f2(-h, -h);
+    case 7: return f2(-c1, -s1);
+    case 8: return f2(-1.f, 0.f);
+    case 9: return f2(-c1, s1);
+    case 10: return f2(-h, h);
+    case 11: return f2(-s1, c1);
+    case 12: return f2(0.f, 1.f);
+    case 13: return f2(s1, c1);
+    case 14: return f2(h, h);
+    default: return f2(c1, s1);
+    }
+}
+
+// ------------------------------------------------------------------ small DFTs (natural order in/out)
+template <bool INV> __device__ __forceinline__ void dft2(float2& a, float2& b) { float2 t = a; a = add(t, b); b = sub(t, b); }
+
+template <bool INV> __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+    float2 a = add(x0, x2), b = sub(x0, x2), c = add(x1, x3), d = rot<INV>(sub(x1, x3));
+    x0 = add(a, c); x2 = sub(a, c); x1 = add(b, d); x3 = sub(b, d);
+}
+
+template <int R, bool INV> struct Dft;
+template <bool INV> struct Dft<1, INV> { template <typename A> __device__ static void run(A&) {} };
+template <bool INV> struct Dft<2, INV> { template <typename A> __device__ static void run(A& x) { dft2<INV>(x[0], x[1]); } };
+template <bool INV> struct Dft<4, INV> { template <typename A> __device__ static void run(A& x) { dft4<INV>(x[0], x[1], x[2], x[3]); } };
+template <bool INV> struct Dft<8, INV> {
+    template <typename A> __device__ static void run(A& x) {
+        // n = 2 n1 + n2, k = k1 + 4 k2
+        float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+        float2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+        dft4<INV>(e0, e1, e2, e3);
+        dft4<INV>(o0, o1, o2, o3);
+        o1 = mul(o1, wconst<8, 1, INV>());
+        o2 = rot<INV>(o2);
+        o3 = mul(o3, wconst<8, 3, INV>());
+        x[0] = add(e0, o0); x[4] = sub(e0, o0);
+        x[1] = add(e1, o1); x[5] = sub(e1, o1);
+        x[2] = add(e2, o2); x[6] = sub(e2, o2);
+        x[3] = add(e3, o3); x[7] = sub(e3, o3);
+    }
+};
+template <bool INV> struct Dft<16, INV> {
+    template <typename A> __device__ static void run(A& x) {
+        // n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W16^{n2 k1}, DFT4 over n2
+        float2 y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; n2++) {
+            y[n2][0] = x[n2]; y[n2][1] = x[4 + n2]; y[n2][2] = x[8 + n2]; y[n2][3] = x[12 + n2];
+            dft4<INV>(y[n2][0], y[n2][1], y[n2][2], y[n2][3]);
+        }
+        y[1][1] = mul(y[1][1], wconst<16, 1, INV>());
+        y[1][2] = mul(y[1][2], wconst<16, 2, INV>());
+        y[1][3] = mul(y[1][3], wconst<16, 3, INV>());
+        y[2][1] = mul(y[2][1], wconst<16, 2, INV>());
+        y[2][2] = rot<INV>(y[2][2]);
+        y[2][3] = mul(y[2][3], wconst<16, 6, INV>());
+        y[3][1] = mul(y[3][1], wconst<16, 3, INV>());
+        y[3][2] = mul(y[3][2], wconst<16, 6, INV>());
+        y[3][3] = mul(y[3][3], wconst<16, 9, INV>());
+#pragma unroll
+        for (int k1 = 0; k1 < 4; k1++) {
+            float2 a = y[0][k1], b = y[1][k1], c = y[2][k1], d = y[3][k1];
+            dft4<INV>(a, b, c, d);
+            x[k1] = a; x[k1 + 4] = b; x[k1 + 8] = c; x[k1 + 12] = d;
+        }
+    }
+};
+
+// ------------------------------------------------------------------ kernel args
+struct FusedArgs {
+    float* E[3];
+    float* B[3];
+    const float* J[3];
+    const float* halo;
+    const int* strip0;
+    const float4* sym;
+    const float2* twM;
+    const float2* twC;
+    float a2;           // c dt / dx2
+};
+
+__device__ __forceinline__ float2 ldg_stream(const float2* p) {
+    float2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void stg_stream(float2* p, float2 v) {
+    asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// job kinds
+enum : int { J_IDLE = 0, J_FWD = 1, J_INV = 2 };
+// epilogues of forward jobs
+enum : int { X_STORE = 0, X_B1, X_B2, X_B3, X_J1, X_J2, X_J3 };
+
+struct Job {
+    int kind;
+    int epi;          // forward epilogue
+    int slot;         // destination slot (forward) or source slot (inverse)
+    int row;          // the row p the epilogue refers to
+    const float* src; // forward: global source row
+    float* dst;       // inverse: global destination row
+};
+
+// slot numbers
+__device__ __forceinline__ int sE1(int r) { return 0 + (r & 1); }
+__device__ __forceinline__ int sE3(int r) { return 2 + (r & 1); }
+constexpr int sE2 = 4;
+__device__ __forceinline__ int sB1(int r) { return 5 + (r & 1); }
+__device__ __forceinline__ int sB3(int r) { return 7 + (r & 1); }
+constexpr int sB2 = 9;
+constexpr int kSlots = 10;
+
+template <int N>
+struct Geo {
+    static constexpr int M = N / 2;
+    static constexpr int T = M / 16;
+    static constexpr int P3 = T / 16;
+    static constexpr int Q = 16 / P3;       // columns per thread
+    static constexpr int NT = 3 * T;
+    static constexpr int XB = M + 16;       // exchange buffer (float2) per group
+};
+
+// job of group g in round index ri of a strip [p0, p1)
+__device__ __forceinline__ Job job_of(const FusedArgs& a, int N, int strip, int p0, int p1, int ri, int g) {
+    Job j{J_IDLE, X_STORE, 0, 0, nullptr, nullptr};
+    const float* halo = a.halo + (size_t)strip * 7 * N;
+    const int h = p0 - 1;
+    if (ri < 3) {
+        if (ri == 0) {
+            j.kind = J_FWD; j.epi = X_STORE;
+            if (g == 0) { j.src = a.E[0] + (size_t)p0 * N; j.slot = sE1(p0); }
+            else if (g == 1) { j.src = a.E[2] + (size_t)p0 * N; j.slot = sE3(p0); }
+            else { j.src = halo + 1 * N; j.slot = sE2; }
+        } else if (ri == 1) {
+            if (g == 0) { j.kind = J_FWD; j.epi = X_STORE; j.src = halo + 0 * N; j.slot = sE1(h); }
+            else if (g == 1) { j.kind = J_FWD; j.epi = X_STORE; j.src = halo + 2 * N; j.slot = sE3(h); }
+        } else {
+            if (g == 0) { j.kind = J_FWD; j.epi = X_B1; j.src = halo + 3 * N; j.slot = sB1(h); j.row = h; }
+            else if (g == 2) { j.kind = J_FWD; j.epi = X_B3; j.src = halo + 4 * N; j.slot = sB3(h); j.row = h; }
+        }
+        return j;
+    }
+    const int r = (ri - 3) % 5;
+    const int p = p0 + (ri - 3) / 5;
+    if (p >= p1) return j;
+    j.row = p;
+    switch (r) {
+    case 0:
+        j.kind = J_FWD; j.epi = X_STORE;
+        if (g == 0) { j.src = (p + 1 < p1) ? a.E[0] + (size_t)(p + 1) * N : halo + 5 * N; j.slot = sE1(p + 1); }
+        else if (g == 1) { j.src = (p + 1 < p1) ? a.E[2] + (size_t)(p + 1) * N : halo + 6 * N; j.slot = sE3(p + 1); }
+        else { j.src = a.E[1] + (size_t)p * N; j.slot = sE2; }
+        break;
+    case 1:
+        j.kind = J_FWD;
+        if (g == 0) { j.epi = X_B1; j.src = a.B[0] + (size_t)p * N; j.slot = sB1(p); }
+        else if (g == 1) { j.epi = X_B2; j.src = a.B[1] + (size_t)p * N; j.slot = sB2; }
+        else { j.epi = X_B3; j.src = a.B[2] + (size_t)p * N; j.slot = sB3(p); }
+        break;
+    case 2:
+        j.kind = J_FWD;
+        if (g == 0) { j.epi = X_J1; j.src = a.J[0] + (size_t)p * N; j.slot = sE1(p); }
+        else if (g == 1) { j.epi = X_J2; j.src = a.J[1] + (size_t)p * N; j.slot = sE2; }
+        else { j.epi = X_J3; j.src = a.J[2] + (size_t)p * N; j.slot = sE3(p); }
+        break;
+    case 3:
+        j.kind = J_INV;
+        if (g == 0) { j.slot = sE1(p); j.dst = a.E[0] + (size_t)p * N; }
+        else if (g == 1) { j.slot = sE2; j.dst = a.E[1] + (size_t)p * N; }
+        else { j.slot = sE3(p); j.dst = a.E[2] + (size_t)p * N; }
+        break;
+    default:
+        j.kind = J_INV;
+        if (g == 0) { j.slot = sB1(p); j.dst = a.B[0] + (size_t)p * N; }
+        else if (g == 1) { j.slot = sB2; j.dst = a.B[1] + (size_t)p * N; }
+        else { j.slot = sB3(p); j.dst = a.B[2] + (size_t)p * N; }
+        break;
+    }
+    return j;
+}
+
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::NT, 1) k_fused2d(FusedArgs a) {
+    using G = Geo<N>;
+    constexpr int M = G::M, T = G::T, P3 = G::P3, Q = G::Q, XB = G::XB;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* slots = smem;
+    const int g = threadIdx.x / T, t = threadIdx.x % T;
+    float2* xb = smem + kSlots * M + g * XB;
+    const int strip = blockIdx.x;
+    const int p0 = a.strip0[strip], p1 = a.strip0[strip + 1];
+    const int nrounds = 3 + 5 * (p1 - p0);
+
+    // per-thread twiddles (exact FP64-rounded values from tables)
+    float2 tw1[16], tw2[16];
+    const int kb = t & 15, ma = t >> 4;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        tw1[k] = a.twM[t * k];                     // W_M^{t k}, t k < M
+        tw2[k] = a.twM[16 * ma * k];               // W_T^{ma k} = W_M^{16 ma k}
+    }
+    // column pairs owned by this thread
+    int cA[Q / 2];
+    float2 wA[Q / 2];
+#pragma unroll
+    for (int p = 0; p < Q / 2; p++) {
+        const int pi = t + T * p;
+        cA[p] = pi;
+        wA[p] = a.twC[pi];                         // W_N^{cA}
+    }
+    const float2 w128 = a.twC[128];
+    auto colB = [&](int p) { return cA[p] == 0 ? 128 : 256 - cA[p]; };
+    const float inv2M = 0.5f / (float)M;
+
+    float2 pf[16];
+    bool pf_ok = false;
+    auto prefetch = [&](int from_ri) {
+        pf_ok = false;
+        for (int rr = from_ri; rr < nrounds && rr < from_ri + 5; rr++) {
+            Job nj = job_of(a, N, strip, p0, p1, rr, g);
+            if (nj.kind == J_FWD) {
+                const float2* s = reinterpret_cast<const float2*>(nj.src);
+#pragma unroll
+                for (int nb = 0; nb < 16; nb++) pf[nb] = ldg_stream(s + t + T * nb);
+                pf_ok = true;
+                return;
+            }
+        }
+    };
+    prefetch(0);
+
+    float2 x[16];
+    for (int ri = 0; ri < nrounds; ri++) {
+        const Job j = job_of(a, N, strip, p0, p1, ri, g);
+        if (j.kind == J_FWD) {
+            // ---------------- forward real FFT of one row
+#pragma unroll
+            for (int nb = 0; nb < 16; nb++) x[nb] = pf[nb];
+            prefetch(ri + 1);
+            Dft<16, false>::run(x);
+#pragma unroll
+            for (int k = 1; k < 16; k++) x[k] = mul(x[k], tw1[k]);
+#pragma unroll
+            for (int k = 0; k < 16; k++) xb[k * (T + 1) + t] = x[k];
+        } else if (j.kind == J_INV) {
+            // ---------------- inverse: slot -> pre-processing -> stage 3 inverse
+#pragma unroll
+            for (int e = 0; e < 16; e++) x[e] = slots[j.slot * M + e * T + t];
+            // pair pre-processing: Z[k] = E + iO, Z[M-k] = conj(E - iO)
+#pragma unroll
+            for (int p = 0; p < Q / 2; p++) {
+#pragma unroll
+                for (int l = 0; l < P3; l++) {
+                    const int ea = (2 * p) * P3 + l;
+                    if (cA[p] != 0) {
+                        const int eb = (2 * p + 1) * P3 + (P3 - 1 - l);
+                        const float2 w = mul(wA[p], wr(2 * P3, l));
+                        const float2 xa = x[ea], xbv = x[eb];
+                        const float2 E = scl(add(xa, conjf2(xbv)), inv2M);
+                        const float2 O = scl(mulc(sub(xa, conjf2(xbv)), w), inv2M);
+                        const float2 v = f2(-O.y, O.x);
+                        x[ea] = add(E, v);
+                        x[eb] = conjf2(sub(E, v));
+                    }
+                }
+            }
+            if (t == 0) {
+                // column 0: l = 0 packs (X0, XM); pairs l <-> P3 - l
+                {
+                    const float X0 = x[0].x, XM = x[0].y;
+                    const float e = (X0 + XM) * inv2M, o = (X0 - XM) * inv2M;
+                    x[0] = f2(e, o);
+                }
+#pragma unroll
+                for (int l = 1; l < P3; l++) {
+                    if (l <= P3 - l) {
+                        const int ea = l, eb = P3 - l;
+                        const float2 w = wr(2 * P3, l);
+                        const float2 xa = x[ea], xbv = x[eb];
+                        const float2 E = scl(add(xa, conjf2(xbv)), inv2M);
+                        const float2 O = scl(mulc(sub(xa, conjf2(xbv)), w), inv2M);
+                        const float2 v = f2(-O.y, O.x);
+                        x[ea] = add(E, v);
+                        if (eb != ea) x[eb] = conjf2(sub(E, v));
+                    }
+                }
+                // column 128 (elements P3 .. 2P3-1): pairs l <-> P3 - 1 - l
+#pragma unroll
+                for (int l = 0; l < P3; l++) {
+                    if (l <= P3 - 1 - l) {
+                        const int ea = P3 + l, eb = P3 + (P3 - 1 - l);
+                        const float2 w = mul(w128, wr(2 * P3, l));
+                        const float2 xa = x[ea], xbv = x[eb];
+                        const float2 E = scl(add(xa, conjf2(xbv)), inv2M);
+                        const float2 O = scl(mulc(sub(xa, conjf2(xbv)), w), inv2M);
+                        const float2 v = f2(-O.y, O.x);
+                        x[ea] = add(E, v);
+                        if (eb != ea) x[eb] = conjf2(sub(E, v));
+                    }
+                }
+            }
+            // stage 3 inverse: per column, P3-point inverse DFT over l_a -> m_a
+#pragma unroll
+            for (int p = 0; p < Q / 2; p++) {
+#pragma unroll
+                for (int s = 0; s < 2; s++) {
+                    float2 w[P3];
+#pragma unroll
+                    for (int l = 0; l < P3; l++) w[l] = x[(2 * p + s) * P3 + l];
+                    Dft<P3, true>::run(w);
+                    const int c = s == 0 ? cA[p] : colB(p);
+#pragma unroll
+                    for (int m = 0; m < P3; m++) xb[m * 256 + c] = w[m];
+                }
+            }
+        }
+        __syncthreads();
+        // ---------------- stage 2 (forward) / stage 2 inverse (x is dead here and reused)
+        if (j.kind == J_FWD) {
+#pragma unroll
+            for (int mb = 0; mb < 16; mb++) x[mb] = xb[kb * (T + 1) + ma + P3 * mb];
+        } else if (j.kind == J_INV) {
+#pragma unroll
+            for (int l = 0; l < 16; l++) x[l] = xb[ma * 256 + l * 16 + kb];
+        }
+        __syncthreads();
+        if (j.kind == J_FWD) {
+            Dft<16, false>::run(x);
+#pragma unroll
+            for (int l = 1; l < 16; l++) x[l] = mul(x[l], tw2[l]);
+#pragma unroll
+            for (int l = 0; l < 16; l++) xb[ma * 256 + l * 16 + kb] = x[l];
+        } else if (j.kind == J_INV) {
+#pragma unroll
+            for (int l = 1; l < 16; l++) x[l] = mulc(x[l], tw2[l]);
+            Dft<16, true>::run(x);
+#pragma unroll
+            for (int mb = 0; mb < 16; mb++) xb[kb * (T + 1) + ma + P3 * mb] = x[mb];
+        }
+        __syncthreads();
+        if (j.kind == J_FWD) {
+            // ---------------- stage 3 forward: columns, then pair post-processing
+#pragma unroll
+            for (int p = 0; p < Q / 2; p++) {
+#pragma unroll
+                for (int s = 0; s < 2; s++) {
+                    const int c = s == 0 ? cA[p] : colB(p);
+                    float2 w[P3];
+#pragma unroll
+                    for (int m = 0; m < P3; m++) w[m] = xb[m * 256 + c];
+                    Dft<P3, false>::run(w);
+#pragma unroll
+                    for (int l = 0; l < P3; l++) x[(2 * p + s) * P3 + l] = w[l];
+                }
+            }
+            // X[k] = e - u, X[M-k] = conj(e + u), e = (a + conj b)/2, u = (i/2) W_N^k (a - conj b)
+#pragma unroll
+            for (int p = 0; p < Q / 2; p++) {
+#pragma unroll
+                for (int l = 0; l < P3; l++) {
+                    if (cA[p] != 0) {
+                        const int ea = (2 * p) * P3 + l, eb = (2 * p + 1) * P3 + (P3 - 1 - l);
+                        const float2 w = mul(wA[p], wr(2 * P3, l));
+                        const float2 av = x[ea], bv = x[eb];
+                        const float2 e = scl(add(av, conjf2(bv)), 0.5f);
+                        const float2 wd = mul(w, sub(av, conjf2(bv)));
+                        const float2 u = f2(-0.5f * wd.y, 0.5f * wd.x);
+                        x[ea] = sub(e, u);
+                        x[eb] = conjf2(add(e, u));
+                    }
+                }
+            }
+            if (t == 0) {
+                {
+                    const float2 z0 = x[0];
+                    x[0] = f2(z0.x + z0.y, z0.x - z0.y);     // (X0, X_M) packed
+                }
+#pragma unroll
+                for (int l = 1; l < P3; l++) {
+                    if (l <= P3 - l) {
+                        const int ea = l, eb = P3 - l;
+                        const float2 w = wr(2 * P3, l);
+                        const float2 av = x[ea], bv = x[eb];
+                        const float2 e = scl(add(av, conjf2(bv)), 0.5f);
+                        const float2 wd = mul(w, sub(av, conjf2(bv)));
+                        const float2 u = f2(-0.5f * wd.y, 0.5f * wd.x);
+                        x[ea] = sub(e, u);
+                        if (eb != ea) x[eb] = conjf2(add(e, u));
+                    }
+                }
+#pragma unroll
+                for (int l = 0; l < P3; l++) {
+                    if (l <= P3 - 1 - l) {
+                        const int ea = P3 + l, eb = P3 + (P3 - 1 - l);
+                        const float2 w = mul(w128, wr(2 * P3, l));
+                        const float2 av = x[ea], bv = x[eb];
+                        const float2 e = scl(add(av, conjf2(bv)), 0.5f);
+                        const float2 wd = mul(w, sub(av, conjf2(bv)));
+                        const float2 u = f2(-0.5f * wd.y, 0.5f * wd.x);
+                        x[ea] = sub(e, u);
+                        if (eb != ea) x[eb] = conjf2(add(e, u));
+                    }
+                }
+            }
+            // ---------------- epilogue: per-mode updates on thread-owned kappa
+            const int p = j.row;
+            const float a2 = a.a2;
+            float2* Sl = slots;
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                const int pp = e / (2 * P3), s = (e / P3) & 1, l = e % P3;
+                const int c = s == 0 ? cA[pp] : colB(pp);
+                const int kap = c + 256 * l;
+                const bool packed = (t == 0 && e == 0);
+                const int o = e * T + t;
+                float4 sy = a.sym[kap];
+                float2 S = f2(sy.x, sy.y);
+                float cj1 = sy.z, cj = sy.w;
+                if (packed) {                                   // DC in .x, Nyquist in .y: both real
+                    const float4 sn = a.sym[M];
+                    S = f2(sy.x, sn.x);
+                    cj1 = 0.f; cj = 0.f;
+                    (void)cj1; (void)cj;
+                }
+                const float2 X = x[e];
+                float2 out = X;
+                switch (j.epi) {
+                case X_STORE: break;
+                case X_B1: {      // B1 -= a2 (E3(p+1) - E3(p))
+                    const float2 d = sub(Sl[sE3(p + 1) * M + o], Sl[sE3(p) * M + o]);
+                    out = sub(X, scl(d, a2));
+                } break;
+                case X_B2: {      // B2 += S E3(p)
+                    const float2 e3 = Sl[sE3(p) * M + o];
+                    out = packed ? f2(X.x + S.x * e3.x, X.y + S.y * e3.y) : add(X, mul(S, e3));
+                } break;
+                case X_B3: {      // B3 += a2 (E1(p+1) - E1(p)) - S E2(p)
+                    const float2 d = sub(Sl[sE1(p + 1) * M + o], Sl[sE1(p) * M + o]);
+                    const float2 e2 = Sl[sE2 * M + o];
+                    const float2 se2 = packed ? f2(S.x * e2.x, S.y * e2.y) : mul(S, e2);
+                    out = sub(add(X, scl(d, a2)), se2);
+                } break;
+                case X_J1: {      // E1 += a2 (B3(p) - B3(p-1)) - cj1 j1
+                    const float2 d = sub(Sl[sB3(p) * M + o], Sl[sB3(p - 1) * M + o]);
+                    const float2 e1 = Sl[sE1(p) * M + o];
+                    const float2 cjv = packed ? f2(sy.z, a.sym[M].z) : f2(cj1, cj1);
+                    out = f2(e1.x + a2 * d.x - cjv.x * X.x, e1.y + a2 * d.y - cjv.y * X.y);
+                } break;
+                case X_J2: {      // E2 += conj(S) B3(p) - cj j2
+                    const float2 b3 = Sl[sB3(p) * M + o];
+                    const float2 e2 = Sl[sE2 * M + o];
+                    const float2 cjv = packed ? f2(sy.w, a.sym[M].w) : f2(cj, cj);
+                    const float2 sb = packed ? f2(S.x * b3.x, S.y * b3.y) : mulc(b3, S);
+                    out = f2(e2.x + sb.x - cjv.x * X.x, e2.y + sb.y - cjv.y * X.y);
+                } break;
+                default: {        // X_J3: E3 += -conj(S) B2(p) - a2 (B1(p) - B1(p-1)) - cj j3
+                    const float2 b2 = Sl[sB2 * M + o];
+                    const float2 d = sub(Sl[sB1(p) * M + o], Sl[sB1(p - 1) * M + o]);
+                    const float2 e3 = Sl[sE3(p) * M + o];
+                    const float2 cjv = packed ? f2(sy.w, a.sym[M].w) : f2(cj, cj);
+                    const float2 sb = packed ? f2(S.x * b2.x, S.y * b2.y) : mulc(b2, S);
+                    out = f2(e3.x - sb.x - a2 * d.x - cjv.x * X.x, e3.y - sb.y - a2 * d.y - cjv.y * X.y);
+                } break;
+                }
+                Sl[j.slot * M + o] = out;
+            }
+        } else if (j.kind == J_INV) {
+            // ---------------- stage 1 inverse: gather over k_b, twiddle, 16-point inverse DFT, store
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = xb[k * (T + 1) + t];
+#pragma unroll
+            for (int k = 1; k < 16; k++) x[k] = mulc(x[k], tw1[k]);
+            Dft<16, true>::run(x);
+            float2* d = reinterpret_cast<float2*>(j.dst);
+#pragma unroll
+            for (int nb = 0; nb < 16; nb++) stg_stream(d + t + T * nb, x[nb]);
+        }
+        __syncthreads();
+    }
+}
+
+// copies the 7 halo rows of every strip: E1,E2,E3,B1,B3 of row p0-1 and E1,E3 of row p1
+__global__ void k_halo(const float* __restrict__ E1, const float* __restrict__ E2, const float* __restrict__ E3,
+                       const float* __restrict__ B1, const float* __restrict__ B3, const int* __restrict__ strip0,
+                       int n_strips, int n1, int n2, float* __restrict__ halo) {
+    const int s = blockIdx.x, k = blockIdx.y;
+    const int p0 = strip0[s], p1 = strip0[s + 1];
+    const int rl = (p0 - 1 + n2) % n2, rn = p1 % n2;
+    const float* src;
+    switch (k) {
+    case 0: src = E1 + (size_t)rl * n1; break;
+    case 1: src = E2 + (size_t)rl * n1; break;
+    case 2: src = E3 + (size_t)rl * n1; break;
+    case 3: src = B1 + (size_t)rl * n1; break;
+    case 4: src = B3 + (size_t)rl * n1; break;
+    case 5: src = E1 + (size_t)rn * n1; break;
+    default: src = E3 + (size_t)rn * n1; break;
+    }
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(halo + ((size_t)s * 7 + k) * n1);
+    for (int i = threadIdx.x; i < n1 / 4; i += blockDim.x) d4[i] = s4[i];
+}
+
+// ------------------------------------------------------------------ host side
+bool fused_supported(const hyb_grid_desc& d) {
+    return d.precision == 32 && d.dims == 2 && (d.n1 == 512 || d.n1 == 1024 || d.n1 == 2048 || d.n1 == 4096) && d.n2 >= 4;
+}
+
+template <int N>
+static size_t fused_smem() { return sizeof(float2) * ((size_t)kSlots * Geo<N>::M + 3 * (size_t)Geo<N>::XB); }
+
+template <int N>
+static hyb_status prep(hyb_grid* g, FusedPlan* P) {
+    const size_t smem = fused_smem<N>();
+    HYB_CUDA_TRY(cudaFuncSetAttribute(k_fused2d<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    HYB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused2d<N>, Geo<N>::NT, smem));
+    if (occ < 1) { set_error("fused kernel does not fit on an SM"); return HYB_EINVAL; }
+    int sms = 0;
+    HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+    const int n2 = g->d.n2;
+    int ns = sms * occ;
+    if (ns > n2 / 2) ns = n2 / 2;
+    if (ns < 1) ns = 1;
+    P->n_strips = ns;
+    P->smem = smem;
+    P->threads = Geo<N>::NT;
+    return HYB_OK;
+}
+
+hyb_status fused_create(hyb_grid* g) {
+    FusedPlan* P = new FusedPlan();
+    g->fused = P;
+    const int N = g->d.n1, M = N / 2;
+    hyb_status st;
+    switch (N) {
+    case 512: st = prep<512>(g, P); break;
+    case 1024: st = prep<1024>(g, P); break;
+    case 2048: st = prep<2048>(g, P); break;
+    default: st = prep<4096>(g, P); break;
+    }
+    if (st != HYB_OK) return st;
+    const int ns = P->n_strips, n2 = g->d.n2;
+    std::vector<int> s0(ns + 1);
+    for (int s = 0; s <= ns; s++) s0[s] = (int)(((int64_t)s * n2) / ns);
+    HYB_CUDA_TRY(cudaMalloc(&P->strip0, sizeof(int) * (ns + 1)));
+    HYB_CUDA_TRY(cudaMemcpy(P->strip0, s0.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMalloc(&P->halo, sizeof(float) * (size_t)ns * 7 * N));
+    // symbol table and twiddles, from the FP64 host values already rounded into g->tf
+    std::vector<float2> S(M + 1);
+    std::vector<float> cj1(M + 1), cj(M + 1);
+    HYB_CUDA_TRY(cudaMemcpy(S.data(), g->tf.S, sizeof(float2) * (M + 1), cudaMemcpyDeviceToHost));
+    HYB_CUDA_TRY(cudaMemcpy(cj1.data(), g->tf.cj1, sizeof(float) * (M + 1), cudaMemcpyDeviceToHost));
+    HYB_CUDA_TRY(cudaMemcpy(cj.data(), g->tf.cj, sizeof(float) * (M + 1), cudaMemcpyDeviceToHost));
+    std::vector<float4> sym(M + 1);
+    for (int k = 0; k <= M; k++) sym[k] = make_float4(S[k].x, S[k].y, cj1[k], cj[k]);
+    HYB_CUDA_TRY(cudaMalloc(&P->sym, sizeof(float4) * (M + 1)));
+    HYB_CUDA_TRY(cudaMemcpy(P->sym, sym.data(), sizeof(float4) * (M + 1), cudaMemcpyHostToDevice));
+    std::vector<float2> twC(256);
+    const double pi = 3.14159265358979323846;
+    for (int c = 0; c < 256; c++) { const double ang = -2.0 * pi * c / N; twC[c] = make_float2((float)cos(ang), (float)sin(ang)); }
+    HYB_CUDA_TRY(cudaMalloc(&P->twC, sizeof(float2) * 256));
+    HYB_CUDA_TRY(cudaMemcpy(P->twC, twC.data(), sizeof(float2) * 256, cudaMemcpyHostToDevice));
+    P->twM = g->tf.twM;
+    return HYB_OK;
+}
+
+void fused_destroy(hyb_grid* g) {
+    FusedPlan* P = g->fused;
+    if (!P) return;
+    if (P->strip0) cudaFree(P->strip0);
+    if (P->halo) cudaFree(P->halo);
+    if (P->sym) cudaFree(P->sym);
+    if (P->twC) cudaFree(P->twC);
+    delete P;
+    g->fused = nullptr;
+}
+
+hyb_status fused_advance(hyb_grid* g, int nsteps) {
+    FusedPlan* P = g->fused;
+    FusedArgs a;
+    for (int c = 0; c < 3; c++) { a.E[c] = (float*)g->E[c]; a.B[c] = (float*)g->B[c]; a.J[c] = (const float*)g->J[c]; }
+    a.halo = P->halo;
+    a.strip0 = P->strip0;
+    a.sym = P->sym;
+    a.twM = P->twM;
+    a.twC = P->twC;
+    a.a2 = (float)(g->d.dt / g->d.dx2);
+    const int N = g->d.n1;
+    for (int s = 0; s < nsteps; s++) {
+        k_halo<<<dim3(P->n_strips, 7), 256, 0, g->stream>>>(a.E[0], a.E[1], a.E[2], a.B[0], a.B[2], P->strip0,
+                                                            P->n_strips, N, g->d.n2, P->halo);
+        if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
+        switch (N) {
+        case 512: k_fused2d<512><<<P->n_strips, P->threads, P->smem, g->stream>>>(a); break;
+        case 1024: k_fused2d<1024><<<P->n_strips, P->threads, P->smem, g->stream>>>(a); break;
+        case 2048: k_fused2d<2048><<<P->n_strips, P->threads, P->smem, g->stream>>>(a); break;
+        default: k_fused2d<4096><<<P->n_strips, P->threads, P->smem, g->stream>>>(a); break;
+        }
+        HYB_CUDA_TRY(cudaGetLastError());
+        if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
+    }
+    return HYB_OK;
+}
+
+int fused_launches_per_step(const hyb_grid*) { return 2; }
+
 }  // namespace hyb

@@ -235,6 +235,7 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
     const T a3 = (T)(g->d.dims == 3 ? g->d.dt / g->d.dx3 : 0.0);
     const bool d3 = g->d.dims == 3;
     for (int s = 0; s < nsteps; s++) {
+        if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
         HYB_CUDA_TRY((launch_rfft<T, T>(fin, 9, spec, n1, rows, t, g->stream)));
         if (d3) {
             k_faraday<T, true><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
@@ -245,6 +246,7 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
         }
         HYB_CUDA_TRY(cudaGetLastError());
         HYB_CUDA_TRY((launch_irfft<T, T>(spec, 0, fout, 6, n1, rows, t, g->stream)));
+        if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
     }
     return HYB_OK;
 }

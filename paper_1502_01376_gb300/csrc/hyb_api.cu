@@ -302,6 +302,14 @@ hyb_status hyb_destroy_grid(hyb_grid* g) {
     return HYB_OK;
 }
 
+hyb_status hyb_set_kernel_events(hyb_grid* g, void* start, void* stop) {
+    if (!g) { set_error("null grid"); return HYB_EINVAL; }
+    if ((start == nullptr) != (stop == nullptr)) { set_error("set both events or neither"); return HYB_EINVAL; }
+    g->ev_start = (cudaEvent_t)start;
+    g->ev_stop = (cudaEvent_t)stop;
+    return HYB_OK;
+}
+
 int hyb_grid_path(const hyb_grid* g) { return g ? g->path : 0; }
 
 int hyb_launches_per_step(const hyb_grid* g) {

@@ -67,6 +67,7 @@ struct hyb_grid {
     double* diag_acc = nullptr;    // 16 FP64 accumulators
     int* dflag = nullptr;          // device data-error flag
     hyb::FusedPlan* fused = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional kernel timing events
 };
 
 namespace hyb {

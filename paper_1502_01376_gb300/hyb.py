@@ -87,6 +87,8 @@ def lib():
             L.hyb_last_error.restype = ctypes.c_char_p
             L.hyb_grid_path.argtypes = [_V]
             L.hyb_grid_path.restype = ctypes.c_int
+            L.hyb_set_kernel_events.argtypes = [_V, _V, _V]
+            L.hyb_set_kernel_events.restype = S
             L.hyb_launches_per_step.argtypes = [_V]
             L.hyb_launches_per_step.restype = ctypes.c_int
             _lib = L
@@ -169,6 +171,10 @@ def hyb_last_error() -> str:
     return lib().hyb_last_error().decode()
 
 
+def hyb_set_kernel_events(g: int, start: int, stop: int):
+    _check(lib().hyb_set_kernel_events(_V(g), _V(start), _V(stop)))
+
+
 def hyb_grid_path(g: int) -> int:
     return lib().hyb_grid_path(_V(g))
 
@@ -232,6 +238,11 @@ class Grid:
 
     def check(self):
         hyb_check(self.h)
+
+    def set_kernel_events(self, start=None, stop=None):
+        """torch.cuda.Event pair (created with enable_timing=True) or None."""
+        hyb_set_kernel_events(self.h, start.cuda_event if start is not None else 0,
+                              stop.cuda_event if stop is not None else 0)
 
     @property
     def path(self):

@@ -170,3 +170,38 @@ def position_at(w: Workload, p: Particles, step: int, real=np.float64):
     """Integer cell and offset of x^step (for charge densities)."""
     cell, off0, _, _ = ballistic_move(w, p, step, real)
     return cell, off0
+
+
+def plasma_move_torch(w: Workload, device, seed: int | None = None, step: int = 0):
+    """Drifting-plasma particles drawn directly on a CUDA device (seeded
+    torch generator; same distributions as make_particles), returned as the
+    deposit interface takes them for step `step`: int32 cell [np, dims],
+    float32 offsets of x^n and x^{n+1}, float32 v3 and q."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(w.seed + 2000 if seed is None else seed)
+    d = w.dims
+    ext = torch.tensor([w.n1, w.n2, w.n3][:d], dtype=torch.float64, device=device)
+    dxs = torch.tensor([w.dx1, w.dx2, w.dx3][:d], dtype=torch.float64, device=device)
+    n = w.cells * w.ppc
+    dV = w.dx1 * w.dx2 * (w.dx3 if d == 3 else 1.0)
+    rho0 = w.density / (4.0 * np.pi)
+    cells, off0s, off1s, v3s, qs = [], [], [], [], []
+    for sign in (-1.0, +1.0):
+        x = torch.rand(n, d, generator=gen, device=device, dtype=torch.float64) * ext
+        u = torch.randn(n, 3, generator=gen, device=device, dtype=torch.float64) * w.u_th
+        u[:, 0] += np.sqrt(w.gamma ** 2 - 1.0)
+        v = u / torch.sqrt(1.0 + (u * u).sum(1, keepdim=True))
+        del u
+        x = torch.remainder(x + step * v[:, :d] * w.dt / dxs, ext)
+        c = torch.floor(x)
+        o0 = x - c
+        o1 = o0 + v[:, :d] * w.dt / dxs
+        cells.append(torch.remainder(c, ext).to(torch.int32))
+        off0s.append(o0.to(torch.float32))
+        off1s.append(o1.to(torch.float32))
+        v3s.append(v[:, 2].to(torch.float32))
+        qs.append(torch.full((n,), sign * rho0 * dV / w.ppc, device=device, dtype=torch.float32))
+        del x, v, c, o0, o1
+    return (torch.cat(cells).contiguous(), torch.cat(off0s).contiguous(), torch.cat(off1s).contiguous(),
+            torch.cat(v3s).contiguous(), torch.cat(qs).contiguous())

@@ -272,3 +272,69 @@ def test_courant_rejected_and_alignment():
     with pytest.raises(hyb.HybError) as e:
         g.advance(1)
     assert e.value.status == hyb.HYB_ESTATE
+
+
+# ------------------------------------------------------------------ fused FP32 path
+def _fused_case(orc, hyb, n1, n2, nsteps, filt=True, seed=21, amp_j=1e-3):
+    w = wl.Workload("tf", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.1, precision=32,
+                    filt_kc=0.5 if filt else 0.0, filt_w=0.2, seed=seed)
+    g, E0, B0, E, B, J = _setup(hyb, w, path=2)
+    assert g.path == 2
+    rng = np.random.default_rng(seed + 1)
+    J0 = [rng.standard_normal(w.shape) * amp_j for _ in range(3)]
+    for c in range(3):
+        J[c].copy_(to_dev(J0[c], torch.float32))
+    rnd = lambda a: a.astype(np.float32).astype(np.float64)
+    Eo, Bo, Jo = [rnd(a) for a in E0], [rnd(a) for a in B0], [rnd(a) for a in J0]
+    orc.step(orc_grid(orc, w), Eo, Bo, Jo, nsteps=nsteps)
+    g.advance(nsteps)
+    return _compare(E, B, Eo, Bo, TOL[32], f"fused {n1}x{n2}")
+
+
+@pytest.mark.parametrize("n1,n2", [(512, 8), (512, 37), (1024, 21), (2048, 13), (4096, 9), (4096, 64)])
+def test_fused_matches_oracle(orc, n1, n2):
+    need_gpu()
+    hyb = hyb_module()
+    _fused_case(orc, hyb, n1, n2, 10)
+
+
+def test_fused_without_filter_and_correction(orc):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("tf", 2, 1024, 16, dx1=0.2, dx2=0.2, dt=0.1, precision=32, correct_j1=False, seed=3)
+    g, E0, B0, E, B, J = _setup(hyb, w, path=2)
+    rng = np.random.default_rng(5)
+    J0 = [rng.standard_normal(w.shape) * 1e-3 for _ in range(3)]
+    for c in range(3):
+        J[c].copy_(to_dev(J0[c], torch.float32))
+    rnd = lambda a: a.astype(np.float32).astype(np.float64)
+    Eo, Bo, Jo = [rnd(a) for a in E0], [rnd(a) for a in B0], [rnd(a) for a in J0]
+    orc.step(orc_grid(orc, w), Eo, Bo, Jo, nsteps=5)
+    g.advance(5)
+    _compare(E, B, Eo, Bo, TOL[32])
+
+
+def test_fused_matches_three_pass_fp32():
+    """Same arithmetic problem through the two FP32 paths."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("tf", 2, 2048, 40, dx1=0.2, dx2=0.2, dt=0.1, precision=32, filt_kc=0.5, filt_w=0.2, seed=9)
+    ga, E0, B0, Ea, Ba, Ja = _setup(hyb, w, path=2)
+    gb, _, _, Eb, Bb, Jb = _setup(hyb, w, path=1)
+    rng = np.random.default_rng(10)
+    for c in range(3):
+        j = to_dev(rng.standard_normal(w.shape) * 1e-3, torch.float32)
+        Ja[c].copy_(j)
+        Jb[c].copy_(j)
+    ga.advance(20)
+    gb.advance(20)
+    for a, b in zip(Ea + Ba, Eb + Bb):
+        assert rel_err(to_np(a), to_np(b)) < 1e-5
+
+
+def test_fused_full_size_drift_plasma_grid(orc):
+    """The 4096 x 1024 grid in the launch configuration the benchmark times, 3 steps."""
+    need_gpu()
+    hyb = hyb_module()
+    errs = _fused_case(orc, hyb, 4096, 1024, 3, seed=31)
+    assert max(errs) < 1e-5
