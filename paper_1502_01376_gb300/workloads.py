@@ -159,9 +159,17 @@ def ballistic_move(w: Workload, p: Particles, step: int, real=np.float64):
     cell = np.floor(x0)
     off0 = x0 - cell
     off1 = off0 + p.v[:, :d] * w.dt / dxs
+    off0r = off0.astype(real)
+    off1r = off1.astype(real)
+    # an offset just below 1 can round to 1 in the target precision: move it
+    # to the next cell so that the rounded offset stays in [0, 1)
+    up = off0r >= 1
+    cell = np.where(up, cell + 1, cell)
+    off0r = np.where(up, real(0), off0r).astype(real)
+    off1r = np.where(up, (off1 - 1.0).astype(real), off1r).astype(real)
     cell = np.mod(cell, ext).astype(np.int32)
-    off0 = np.ascontiguousarray(off0.astype(real))
-    off1 = np.ascontiguousarray(off1.astype(real))
+    off0 = np.ascontiguousarray(off0r)
+    off1 = np.ascontiguousarray(off1r)
     v3 = np.ascontiguousarray(p.v[:, 2].astype(real))
     return np.ascontiguousarray(cell), off0, off1, v3
 
@@ -197,8 +205,13 @@ def plasma_move_torch(w: Workload, device, seed: int | None = None, step: int = 
         c = torch.floor(x)
         o0 = x - c
         o1 = o0 + v[:, :d] * w.dt / dxs
+        o0f = o0.to(torch.float32)
+        up = o0f >= 1                      # rounding to FP32 reached 1: move to the next cell
+        c = torch.where(up, c + 1, c)
+        o1 = torch.where(up, o1 - 1.0, o1)
+        o0f = torch.where(up, torch.zeros_like(o0f), o0f)
         cells.append(torch.remainder(c, ext).to(torch.int32))
-        off0s.append(o0.to(torch.float32))
+        off0s.append(o0f)
         off1s.append(o1.to(torch.float32))
         v3s.append(v[:, 2].to(torch.float32))
         qs.append(torch.full((n,), sign * rho0 * dV / w.ppc, device=device, dtype=torch.float32))
