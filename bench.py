@@ -259,6 +259,9 @@ def main():
     torch.cuda.synchronize()
     K = args.steps
     ek = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in ek:          # torch creates the CUDA event on first record; the library records them later
+        a.record(stream)
+        b.record(stream)
     es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:

@@ -240,7 +240,8 @@ class Grid:
         hyb_check(self.h)
 
     def set_kernel_events(self, start=None, stop=None):
-        """torch.cuda.Event pair (created with enable_timing=True) or None."""
+        """torch.cuda.Event pair (created with enable_timing=True and recorded
+        once, so that the CUDA event exists) or None."""
         hyb_set_kernel_events(self.h, start.cuda_event if start is not None else 0,
                               stop.cuda_event if stop is not None else 0)
 
