@@ -152,6 +152,40 @@ HYB_API const char* hyb_last_error(void);
  * time that kernel alone.  The events are borrowed, not owned. */
 HYB_API hyb_status hyb_set_kernel_events(hyb_grid* g, void* start, void* stop);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent grids advanced together (the paper applies the
+ * solver to many grid geometries; batching them is this library's design).
+ * Grids on the fused path are grouped by n1 into one persistent launch per
+ * group over a table of (grid, strip) work items; one step of all grids is
+ * captured once in a CUDA graph and replayed by hyb_batch_advance.
+ * ------------------------------------------------------------------------- */
+typedef struct hyb_batch hyb_batch;   /* opaque */
+
+/* Creates n grids (each as hyb_create_grid would, on the same stream). */
+HYB_API hyb_status hyb_batch_create(const hyb_grid_desc* descs, int n, void* stream, hyb_batch** out);
+
+/* Binds grid i of the batch to caller device arrays (as hyb_bind_fields; no rho). */
+HYB_API hyb_status hyb_batch_bind(hyb_batch* b, int i, void* const E[3], void* const B[3], void* const J[3]);
+
+/* Autotuner: for each group, times `trials` steps for each candidate strip
+ * height (rows per work item) on scratch fields it allocates and frees, and
+ * keeps the fastest.  Bound fields are not touched.  Synchronises. */
+HYB_API hyb_status hyb_batch_tune(hyb_batch* b, int trials);
+
+/* nsteps of every grid of the batch, one CUDA-graph launch per step, with the
+ * same state contract as hyb_advance.  The graph is (re)captured on the first
+ * call after a bind or a tune. */
+HYB_API hyb_status hyb_batch_advance(hyb_batch* b, int nsteps);
+
+/* Tuned rows per strip of the group with this n1 (0 if none). */
+HYB_API int hyb_batch_rows_per_strip(const hyb_batch* b, int n1);
+
+/* Kernel launches in one step of the batch (the nodes of its graph). */
+HYB_API int hyb_batch_launches_per_step(const hyb_batch* b);
+
+/* Frees the batch and its grids (not the caller's arrays). */
+HYB_API hyb_status hyb_batch_destroy(hyb_batch* b);
+
 /* Which advance path a grid runs: 1 three-pass, 2 fused. */
 HYB_API int hyb_grid_path(const hyb_grid* g);
 

@@ -1,0 +1,252 @@
+// batch.cu -- many independent grids advanced together, one CUDA-graph launch
+// per step.  Grids that run the fused FP32 kernel are grouped by n1; each
+// group is one persistent launch of k_fused2d<n1> over a table of work items
+// (grid, strip, first row, end row) from all its grids, preceded by one halo
+// launch.  Other grids (FP64, 3D, unsupported n1) run their three-pass step.
+// Groups are forked onto side streams inside the captured graph so that they
+// overlap.  hyb_batch_tune times candidate strip heights per group on scratch
+// fields and keeps the fastest (the autotuner).
+#include <algorithm>
+#include <vector>
+
+#include "fused_api.cuh"
+
+struct hyb_batch {
+    std::vector<hyb_grid*> grids;
+    cudaStream_t stream = nullptr;
+    struct Group {
+        int n1 = 0;
+        std::vector<int> members;          // indices into grids
+        int rows_per_strip = 8;            // tuned
+        int4* items = nullptr;             // device work items
+        int n_items = 0;
+        int grid = 0;
+        cudaStream_t side = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
+    };
+    std::vector<Group> groups;
+    std::vector<int> others;               // grids on the three-pass path
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool dirty = true;
+    int launches_per_step = 0;
+};
+
+namespace hyb {
+
+static hyb_status group_plan(hyb_batch* b, hyb_batch::Group& G) {
+    std::vector<int4> items;
+    for (size_t k = 0; k < G.members.size(); k++) {
+        hyb_grid* g = b->grids[G.members[k]];
+        int ns = (g->d.n2 + G.rows_per_strip - 1) / G.rows_per_strip;
+        if (ns > g->d.n2 / 2) ns = g->d.n2 / 2;
+        if (ns < 1) ns = 1;
+        hyb_status st = fused_set_strips(g, ns);
+        if (st != HYB_OK) return st;
+        std::vector<int4> it = fused_items((int)k, g->d.n2, ns);
+        items.insert(items.end(), it.begin(), it.end());
+    }
+    // longest items first, so that the persistent CTAs finish together
+    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& c) { return (a.w - a.z) > (c.w - c.z); });
+    if (G.items) { cudaFree(G.items); G.items = nullptr; }
+    HYB_CUDA_TRY(cudaMalloc(&G.items, sizeof(int4) * items.size()));
+    HYB_CUDA_TRY(cudaMemcpy(G.items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    G.n_items = (int)items.size();
+    int occ = 0, sms = 0;
+    HYB_CUDA_TRY(fused_occupancy(G.n1, &occ));
+    HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->grids[0]->device));
+    G.grid = std::min(G.n_items, sms * occ);
+    b->dirty = true;
+    return HYB_OK;
+}
+
+static FusedBatch group_args(hyb_batch* b, const hyb_batch::Group& G) {
+    FusedBatch fb;
+    for (size_t k = 0; k < G.members.size(); k++) fb.inst[k] = fused_inst(b->grids[G.members[k]]);
+    fb.items = G.items;
+    fb.n_items = G.n_items;
+    return fb;
+}
+
+// enqueue one step of every group (forked onto side streams) and of the others
+static hyb_status enqueue_step(hyb_batch* b, cudaStream_t s) {
+    for (auto& G : b->groups) {
+        HYB_CUDA_TRY(cudaEventRecord(G.fork, s));
+        HYB_CUDA_TRY(cudaStreamWaitEvent(G.side, G.fork, 0));
+        HYB_CUDA_TRY(fused_launch(G.n1, group_args(b, G), G.grid, G.side, nullptr, nullptr));
+        HYB_CUDA_TRY(cudaEventRecord(G.join, G.side));
+    }
+    for (int i : b->others) {
+        hyb_grid* g = b->grids[i];
+        cudaStream_t keep = g->stream;
+        g->stream = s;
+        hyb_status st = g->d.precision == 32 ? generic_advance<float>(g, 1) : generic_advance<double>(g, 1);
+        g->stream = keep;
+        if (st != HYB_OK) return st;
+    }
+    for (auto& G : b->groups) HYB_CUDA_TRY(cudaStreamWaitEvent(s, G.join, 0));
+    return HYB_OK;
+}
+
+static hyb_status capture(hyb_batch* b) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    cudaStream_t cs = nullptr;
+    HYB_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    HYB_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    hyb_status st = enqueue_step(b, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (st != HYB_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    b->graph = graph;
+    HYB_CUDA_TRY(cudaGraphInstantiate(&b->exec, graph, 0));
+    b->dirty = false;
+    return HYB_OK;
+}
+
+}  // namespace hyb
+
+using namespace hyb;
+
+extern "C" {
+
+hyb_status hyb_batch_create(const hyb_grid_desc* descs, int n, void* stream, hyb_batch** out) {
+    if (!descs || !out || n < 1) { set_error("hyb_batch_create: bad arguments"); return HYB_EINVAL; }
+    *out = nullptr;
+    hyb_batch* b = new hyb_batch();
+    b->stream = (cudaStream_t)stream;
+    for (int i = 0; i < n; i++) {
+        hyb_grid* g = nullptr;
+        hyb_status st = hyb_create_grid(&descs[i], stream, &g);
+        if (st != HYB_OK) { hyb_batch_destroy(b); return st; }
+        b->grids.push_back(g);
+    }
+    for (int i = 0; i < n; i++) {
+        hyb_grid* g = b->grids[i];
+        if (g->path != 2) { b->others.push_back(i); continue; }
+        auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const hyb_batch::Group& G) { return G.n1 == g->d.n1; });
+        if (it == b->groups.end()) {
+            b->groups.emplace_back();
+            b->groups.back().n1 = g->d.n1;
+            it = b->groups.end() - 1;
+        }
+        if ((int)it->members.size() >= kMaxInst) { set_error("more than %d fused grids with the same n1", kMaxInst); hyb_batch_destroy(b); return HYB_EINVAL; }
+        it->members.push_back(i);
+    }
+    for (auto& G : b->groups) {
+        cudaError_t e = cudaStreamCreateWithFlags(&G.side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) { hyb_status st = cuda_fail(e, "stream/event creation"); hyb_batch_destroy(b); return st; }
+        hyb_status st = group_plan(b, G);
+        if (st != HYB_OK) { hyb_batch_destroy(b); return st; }
+    }
+    b->launches_per_step = 2 * (int)b->groups.size() + 4 * (int)b->others.size();
+    *out = b;
+    return HYB_OK;
+}
+
+hyb_status hyb_batch_bind(hyb_batch* b, int i, void* const E[3], void* const B[3], void* const J[3]) {
+    if (!b || i < 0 || i >= (int)b->grids.size()) { set_error("hyb_batch_bind: bad index"); return HYB_EINVAL; }
+    hyb_status st = hyb_bind_fields(b->grids[i], E, B, J, nullptr);
+    if (st == HYB_OK) b->dirty = true;
+    return st;
+}
+
+hyb_status hyb_batch_advance(hyb_batch* b, int nsteps) {
+    if (!b || nsteps < 0) { set_error("hyb_batch_advance: bad arguments"); return HYB_EINVAL; }
+    for (auto* g : b->grids) if (!g->bound) { set_error("hyb_batch_advance: a grid is not bound"); return HYB_ESTATE; }
+    if (b->dirty) { hyb_status st = capture(b); if (st != HYB_OK) return st; }
+    for (int s = 0; s < nsteps; s++) HYB_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+    return HYB_OK;
+}
+
+hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
+    if (!b) { set_error("null batch"); return HYB_EINVAL; }
+    if (trials < 1) trials = 3;
+    static const int cand[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
+    cudaEvent_t e0, e1;
+    HYB_CUDA_TRY(cudaEventCreate(&e0));
+    HYB_CUDA_TRY(cudaEventCreate(&e1));
+    hyb_status result = HYB_OK;
+    for (auto& G : b->groups) {
+        // scratch fields: timing does not depend on the values
+        std::vector<void*> bufs;
+        bool fail = false;
+        for (int m : G.members) {
+            hyb_grid* g = b->grids[m];
+            void* p = nullptr;
+            if (cudaMalloc(&p, (size_t)9 * g->cells * sizeof(float)) != cudaSuccess) { fail = true; break; }
+            cudaMemset(p, 0, (size_t)9 * g->cells * sizeof(float));
+            bufs.push_back(p);
+        }
+        if (fail) { for (void* p : bufs) cudaFree(p); result = cuda_fail(cudaErrorMemoryAllocation, "hyb_batch_tune scratch"); break; }
+        float best = 1e30f;
+        int best_h = G.rows_per_strip;
+        for (int h : cand) {
+            G.rows_per_strip = h;
+            hyb_status st = group_plan(b, G);
+            if (st != HYB_OK) { result = st; break; }
+            FusedBatch fb;
+            for (size_t k = 0; k < G.members.size(); k++) {
+                hyb_grid* g = b->grids[G.members[k]];
+                FusedInst a = fused_inst(g);
+                float* base = (float*)bufs[k];
+                for (int c = 0; c < 3; c++) {
+                    a.E[c] = base + (size_t)c * g->cells;
+                    a.B[c] = base + (size_t)(3 + c) * g->cells;
+                    a.J[c] = base + (size_t)(6 + c) * g->cells;
+                }
+                fb.inst[k] = a;
+            }
+            fb.items = G.items;
+            fb.n_items = G.n_items;
+            fused_launch(G.n1, fb, G.grid, b->stream, nullptr, nullptr);       // warm
+            cudaEventRecord(e0, b->stream);
+            for (int t = 0; t < trials; t++) fused_launch(G.n1, fb, G.grid, b->stream, nullptr, nullptr);
+            cudaEventRecord(e1, b->stream);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { result = cuda_fail(e, "hyb_batch_tune"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_h = h; }
+        }
+        for (void* p : bufs) cudaFree(p);
+        if (result != HYB_OK) break;
+        G.rows_per_strip = best_h;
+        result = group_plan(b, G);
+        if (result != HYB_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->dirty = true;
+    return result;
+}
+
+int hyb_batch_rows_per_strip(const hyb_batch* b, int n1) {
+    if (!b) return 0;
+    for (auto& G : b->groups) if (G.n1 == n1) return G.rows_per_strip;
+    return 0;
+}
+
+int hyb_batch_launches_per_step(const hyb_batch* b) { return b ? b->launches_per_step : 0; }
+
+hyb_status hyb_batch_destroy(hyb_batch* b) {
+    if (!b) return HYB_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto& G : b->groups) {
+        if (G.items) cudaFree(G.items);
+        if (G.side) cudaStreamDestroy(G.side);
+        if (G.fork) cudaEventDestroy(G.fork);
+        if (G.join) cudaEventDestroy(G.join);
+    }
+    for (auto* g : b->grids) hyb_destroy_grid(g);
+    delete b;
+    return HYB_OK;
+}
+
+}  // extern "C"

@@ -35,20 +35,11 @@
 
 #include <vector>
 
-#include "hyb_internal.cuh"
+#include "fused_api.cuh"
 
 namespace hyb {
 
-struct FusedPlan {
-    int n_strips = 0;
-    int* strip0 = nullptr;        // [n_strips + 1] first row of each strip (device)
-    float* halo = nullptr;        // [n_strips][7][n1]
-    float4* sym = nullptr;        // [M + 1] {Re S, Im S, cj1, cj}, S = c dt sigma+
-    float2* twM = nullptr;        // [M] W_M^j
-    float2* twC = nullptr;        // [256] W_N^c
-    size_t smem = 0;
-    int threads = 0;
-};
+
 
 // ------------------------------------------------------------------ complex
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -166,17 +157,7 @@ template <bool INV> struct Dft<16, INV> {
 };
 
 // ------------------------------------------------------------------ kernel args
-struct FusedArgs {
-    float* E[3];
-    float* B[3];
-    const float* J[3];
-    const float* halo;
-    const int* strip0;
-    const float4* sym;
-    const float2* twM;
-    const float2* twC;
-    float a2;           // c dt / dx2
-};
+
 
 __device__ __forceinline__ float2 ldg_stream(const float2* p) {
     float2 v;
@@ -218,10 +199,11 @@ struct Geo {
     static constexpr int Q = 16 / P3;       // columns per thread
     static constexpr int NT = 3 * T;
     static constexpr int XB = M + 16;       // exchange buffer (float2) per group
+    static constexpr int MINB = (N == 4096) ? 1 : (N == 2048) ? 2 : (N == 1024) ? 4 : 6;   // CTAs per SM to fit
 };
 
 // job of group g in round index ri of a strip [p0, p1)
-__device__ __forceinline__ Job job_of(const FusedArgs& a, int N, int strip, int p0, int p1, int ri, int g) {
+__device__ __forceinline__ Job job_of(const FusedInst& a, int N, int strip, int p0, int p1, int ri, int g) {
     Job j{J_IDLE, X_STORE, 0, 0, nullptr, nullptr};
     const float* halo = a.halo + (size_t)strip * 7 * N;
     const int h = p0 - 1;
@@ -280,24 +262,23 @@ __device__ __forceinline__ Job job_of(const FusedArgs& a, int N, int strip, int 
 }
 
 template <int N>
-__global__ void __launch_bounds__(Geo<N>::NT, 1) k_fused2d(FusedArgs a) {
+__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch fb) {
     using G = Geo<N>;
     constexpr int M = G::M, T = G::T, P3 = G::P3, Q = G::Q, XB = G::XB;
     extern __shared__ __align__(16) float2 smem[];
     float2* slots = smem;
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* xb = smem + kSlots * M + g * XB;
-    const int strip = blockIdx.x;
-    const int p0 = a.strip0[strip], p1 = a.strip0[strip + 1];
-    const int nrounds = 3 + 5 * (p1 - p0);
+    if ((int)blockIdx.x >= fb.n_items) return;
 
-    // per-thread twiddles (exact FP64-rounded values from tables)
+    // per-thread twiddles (exact FP64-rounded values; identical for every instance with this n1)
+    const FusedInst& i0 = fb.inst[fb.items[blockIdx.x].x];
     float2 tw1[16], tw2[16];
     const int kb = t & 15, ma = t >> 4;
 #pragma unroll
     for (int k = 0; k < 16; k++) {
-        tw1[k] = a.twM[t * k];                     // W_M^{t k}, t k < M
-        tw2[k] = a.twM[16 * ma * k];               // W_T^{ma k} = W_M^{16 ma k}
+        tw1[k] = i0.twM[t * k];                    // W_M^{t k}, t k < M
+        tw2[k] = i0.twM[16 * ma * k];              // W_T^{ma k} = W_M^{16 ma k}
     }
     // column pairs owned by this thread
     int cA[Q / 2];
@@ -306,11 +287,17 @@ __global__ void __launch_bounds__(Geo<N>::NT, 1) k_fused2d(FusedArgs a) {
     for (int p = 0; p < Q / 2; p++) {
         const int pi = t + T * p;
         cA[p] = pi;
-        wA[p] = a.twC[pi];                         // W_N^{cA}
+        wA[p] = i0.twC[pi];                        // W_N^{cA}
     }
-    const float2 w128 = a.twC[128];
+    const float2 w128 = i0.twC[128];
     auto colB = [&](int p) { return cA[p] == 0 ? 128 : 256 - cA[p]; };
     const float inv2M = 0.5f / (float)M;
+
+  for (int item = blockIdx.x; item < fb.n_items; item += gridDim.x) {
+    const int4 it = fb.items[item];
+    const FusedInst a = fb.inst[it.x];
+    const int strip = it.y, p0 = it.z, p1 = it.w;
+    const int nrounds = 3 + 5 * (p1 - p0);
 
     float2 pf[16];
     bool pf_ok = false;
@@ -577,27 +564,28 @@ __global__ void __launch_bounds__(Geo<N>::NT, 1) k_fused2d(FusedArgs a) {
         }
         __syncthreads();
     }
+  }
 }
 
-// copies the 7 halo rows of every strip: E1,E2,E3,B1,B3 of row p0-1 and E1,E3 of row p1
-__global__ void k_halo(const float* __restrict__ E1, const float* __restrict__ E2, const float* __restrict__ E3,
-                       const float* __restrict__ B1, const float* __restrict__ B3, const int* __restrict__ strip0,
-                       int n_strips, int n1, int n2, float* __restrict__ halo) {
-    const int s = blockIdx.x, k = blockIdx.y;
-    const int p0 = strip0[s], p1 = strip0[s + 1];
+// copies the 7 halo rows of every work item: E1,E2,E3,B1,B3 of row p0-1 and E1,E3 of row p1
+__global__ void k_halo(FusedBatch fb, int n1) {
+    const int4 it = fb.items[blockIdx.x];
+    const FusedInst& a = fb.inst[it.x];
+    const int k = blockIdx.y;
+    const int n2 = a.n2, p0 = it.z, p1 = it.w;
     const int rl = (p0 - 1 + n2) % n2, rn = p1 % n2;
     const float* src;
     switch (k) {
-    case 0: src = E1 + (size_t)rl * n1; break;
-    case 1: src = E2 + (size_t)rl * n1; break;
-    case 2: src = E3 + (size_t)rl * n1; break;
-    case 3: src = B1 + (size_t)rl * n1; break;
-    case 4: src = B3 + (size_t)rl * n1; break;
-    case 5: src = E1 + (size_t)rn * n1; break;
-    default: src = E3 + (size_t)rn * n1; break;
+    case 0: src = a.E[0] + (size_t)rl * n1; break;
+    case 1: src = a.E[1] + (size_t)rl * n1; break;
+    case 2: src = a.E[2] + (size_t)rl * n1; break;
+    case 3: src = a.B[0] + (size_t)rl * n1; break;
+    case 4: src = a.B[2] + (size_t)rl * n1; break;
+    case 5: src = a.E[0] + (size_t)rn * n1; break;
+    default: src = a.E[2] + (size_t)rn * n1; break;
     }
     const float4* s4 = reinterpret_cast<const float4*>(src);
-    float4* d4 = reinterpret_cast<float4*>(halo + ((size_t)s * 7 + k) * n1);
+    float4* d4 = reinterpret_cast<float4*>(const_cast<float*>(a.halo) + ((size_t)it.y * 7 + k) * n1);
     for (int i = threadIdx.x; i < n1 / 4; i += blockDim.x) d4[i] = s4[i];
 }
 
@@ -609,44 +597,58 @@ bool fused_supported(const hyb_grid_desc& d) {
 template <int N>
 static size_t fused_smem() { return sizeof(float2) * ((size_t)kSlots * Geo<N>::M + 3 * (size_t)Geo<N>::XB); }
 
-template <int N>
-static hyb_status prep(hyb_grid* g, FusedPlan* P) {
-    const size_t smem = fused_smem<N>();
-    HYB_CUDA_TRY(cudaFuncSetAttribute(k_fused2d<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int occ = 0;
-    HYB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused2d<N>, Geo<N>::NT, smem));
-    if (occ < 1) { set_error("fused kernel does not fit on an SM"); return HYB_EINVAL; }
-    int sms = 0;
-    HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
-    const int n2 = g->d.n2;
-    int ns = sms * occ;
-    if (ns > n2 / 2) ns = n2 / 2;
-    if (ns < 1) ns = 1;
-    P->n_strips = ns;
-    P->smem = smem;
-    P->threads = Geo<N>::NT;
-    return HYB_OK;
+size_t fused_smem_bytes(int n1) {
+    switch (n1) {
+    case 512: return fused_smem<512>();
+    case 1024: return fused_smem<1024>();
+    case 2048: return fused_smem<2048>();
+    default: return fused_smem<4096>();
+    }
 }
 
-hyb_status fused_create(hyb_grid* g) {
-    FusedPlan* P = new FusedPlan();
-    g->fused = P;
-    const int N = g->d.n1, M = N / 2;
-    hyb_status st;
-    switch (N) {
-    case 512: st = prep<512>(g, P); break;
-    case 1024: st = prep<1024>(g, P); break;
-    case 2048: st = prep<2048>(g, P); break;
-    default: st = prep<4096>(g, P); break;
+int fused_threads(int n1) { return 3 * (n1 / 32); }
+
+template <int N>
+static cudaError_t fused_attr(int* occ) {
+    const size_t smem = fused_smem<N>();
+    cudaError_t e = cudaFuncSetAttribute(k_fused2d<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_fused2d<N>, Geo<N>::NT, smem);
+}
+
+// resident CTAs per SM of the fused kernel for n1
+cudaError_t fused_occupancy(int n1, int* occ) {
+    switch (n1) {
+    case 512: return fused_attr<512>(occ);
+    case 1024: return fused_attr<1024>(occ);
+    case 2048: return fused_attr<2048>(occ);
+    default: return fused_attr<4096>(occ);
     }
-    if (st != HYB_OK) return st;
-    const int ns = P->n_strips, n2 = g->d.n2;
-    std::vector<int> s0(ns + 1);
-    for (int s = 0; s <= ns; s++) s0[s] = (int)(((int64_t)s * n2) / ns);
-    HYB_CUDA_TRY(cudaMalloc(&P->strip0, sizeof(int) * (ns + 1)));
-    HYB_CUDA_TRY(cudaMemcpy(P->strip0, s0.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
-    HYB_CUDA_TRY(cudaMalloc(&P->halo, sizeof(float) * (size_t)ns * 7 * N));
-    // symbol table and twiddles, from the FP64 host values already rounded into g->tf
+}
+
+// one step for the work items of a launch: halo copy, then the persistent fused kernel
+cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+    k_halo<<<dim3(fb.n_items, 7), 256, 0, s>>>(fb, n1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev0) { e = cudaEventRecord(ev0, s); if (e != cudaSuccess) return e; }
+    const size_t smem = fused_smem_bytes(n1);
+    const int thr = fused_threads(n1);
+    switch (n1) {
+    case 512: k_fused2d<512><<<grid, thr, smem, s>>>(fb); break;
+    case 1024: k_fused2d<1024><<<grid, thr, smem, s>>>(fb); break;
+    case 2048: k_fused2d<2048><<<grid, thr, smem, s>>>(fb); break;
+    default: k_fused2d<4096><<<grid, thr, smem, s>>>(fb); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev1) e = cudaEventRecord(ev1, s);
+    return e;
+}
+
+// per-grid tables of the fused kernel (symbols, W_N^c) and its halo buffer
+hyb_status fused_tables(hyb_grid* g, int n_strips, FusedPlan* P) {
+    const int N = g->d.n1, M = N / 2;
     std::vector<float2> S(M + 1);
     std::vector<float> cj1(M + 1), cj(M + 1);
     HYB_CUDA_TRY(cudaMemcpy(S.data(), g->tf.S, sizeof(float2) * (M + 1), cudaMemcpyDeviceToHost));
@@ -662,13 +664,76 @@ hyb_status fused_create(hyb_grid* g) {
     HYB_CUDA_TRY(cudaMalloc(&P->twC, sizeof(float2) * 256));
     HYB_CUDA_TRY(cudaMemcpy(P->twC, twC.data(), sizeof(float2) * 256, cudaMemcpyHostToDevice));
     P->twM = g->tf.twM;
+    HYB_CUDA_TRY(cudaMalloc(&P->halo, sizeof(float) * (size_t)n_strips * 7 * N));
+    P->n_strips = n_strips;
+    return HYB_OK;
+}
+
+// re-plans a fused grid for n_strips strips (halo buffer and single-grid items)
+hyb_status fused_set_strips(hyb_grid* g, int n_strips) {
+    FusedPlan* P = g->fused;
+    if (n_strips < 1) n_strips = 1;
+    if (n_strips > g->d.n2) n_strips = g->d.n2;
+    if (P->halo) { cudaFree(P->halo); P->halo = nullptr; }
+    HYB_CUDA_TRY(cudaMalloc(&P->halo, sizeof(float) * (size_t)n_strips * 7 * g->d.n1));
+    P->n_strips = n_strips;
+    std::vector<int4> it = fused_items(0, g->d.n2, n_strips);
+    if (P->items) { cudaFree(P->items); P->items = nullptr; }
+    HYB_CUDA_TRY(cudaMalloc(&P->items, sizeof(int4) * it.size()));
+    HYB_CUDA_TRY(cudaMemcpy(P->items, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
+    P->n_items = (int)it.size();
+    int occ = 0, sms = 0;
+    HYB_CUDA_TRY(fused_occupancy(g->d.n1, &occ));
+    HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+    P->grid = P->n_items < sms * occ ? P->n_items : sms * occ;
+    return HYB_OK;
+}
+
+// rows split into n_strips nearly equal strips: items {inst, strip, p0, p1}
+std::vector<int4> fused_items(int inst, int n2, int n_strips) {
+    std::vector<int4> it(n_strips);
+    for (int s = 0; s < n_strips; s++)
+        it[s] = make_int4(inst, s, (int)(((int64_t)s * n2) / n_strips), (int)(((int64_t)(s + 1) * n2) / n_strips));
+    return it;
+}
+
+FusedInst fused_inst(const hyb_grid* g) {
+    FusedInst a;
+    const FusedPlan* P = g->fused;
+    for (int c = 0; c < 3; c++) { a.E[c] = (float*)g->E[c]; a.B[c] = (float*)g->B[c]; a.J[c] = (const float*)g->J[c]; }
+    a.halo = P->halo;
+    a.sym = P->sym;
+    a.twM = P->twM;
+    a.twC = P->twC;
+    a.a2 = (float)(g->d.dt / g->d.dx2);
+    a.n2 = g->d.n2;
+    return a;
+}
+
+hyb_status fused_create(hyb_grid* g) {
+    FusedPlan* P = new FusedPlan();
+    g->fused = P;
+    int occ = 0, sms = 0;
+    HYB_CUDA_TRY(fused_occupancy(g->d.n1, &occ));
+    if (occ < 1) { set_error("fused kernel does not fit on an SM"); return HYB_EINVAL; }
+    HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+    int ns = sms * occ;
+    if (ns > g->d.n2 / 2) ns = g->d.n2 / 2;
+    if (ns < 1) ns = 1;
+    hyb_status st = fused_tables(g, ns, P);
+    if (st != HYB_OK) return st;
+    std::vector<int4> it = fused_items(0, g->d.n2, ns);
+    HYB_CUDA_TRY(cudaMalloc(&P->items, sizeof(int4) * it.size()));
+    HYB_CUDA_TRY(cudaMemcpy(P->items, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
+    P->n_items = (int)it.size();
+    P->grid = (int)it.size();
     return HYB_OK;
 }
 
 void fused_destroy(hyb_grid* g) {
     FusedPlan* P = g->fused;
     if (!P) return;
-    if (P->strip0) cudaFree(P->strip0);
+    if (P->items) cudaFree(P->items);
     if (P->halo) cudaFree(P->halo);
     if (P->sym) cudaFree(P->sym);
     if (P->twC) cudaFree(P->twC);
@@ -678,28 +743,12 @@ void fused_destroy(hyb_grid* g) {
 
 hyb_status fused_advance(hyb_grid* g, int nsteps) {
     FusedPlan* P = g->fused;
-    FusedArgs a;
-    for (int c = 0; c < 3; c++) { a.E[c] = (float*)g->E[c]; a.B[c] = (float*)g->B[c]; a.J[c] = (const float*)g->J[c]; }
-    a.halo = P->halo;
-    a.strip0 = P->strip0;
-    a.sym = P->sym;
-    a.twM = P->twM;
-    a.twC = P->twC;
-    a.a2 = (float)(g->d.dt / g->d.dx2);
-    const int N = g->d.n1;
-    for (int s = 0; s < nsteps; s++) {
-        k_halo<<<dim3(P->n_strips, 7), 256, 0, g->stream>>>(a.E[0], a.E[1], a.E[2], a.B[0], a.B[2], P->strip0,
-                                                            P->n_strips, N, g->d.n2, P->halo);
-        if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
-        switch (N) {
-        case 512: k_fused2d<512><<<P->n_strips, P->threads, P->smem, g->stream>>>(a); break;
-        case 1024: k_fused2d<1024><<<P->n_strips, P->threads, P->smem, g->stream>>>(a); break;
-        case 2048: k_fused2d<2048><<<P->n_strips, P->threads, P->smem, g->stream>>>(a); break;
-        default: k_fused2d<4096><<<P->n_strips, P->threads, P->smem, g->stream>>>(a); break;
-        }
-        HYB_CUDA_TRY(cudaGetLastError());
-        if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
-    }
+    FusedBatch fb;
+    fb.inst[0] = fused_inst(g);
+    fb.items = P->items;
+    fb.n_items = P->n_items;
+    for (int s = 0; s < nsteps; s++)
+        HYB_CUDA_TRY(fused_launch(g->d.n1, fb, P->grid, g->stream, g->ev_start, g->ev_stop));
     return HYB_OK;
 }
 

@@ -1,0 +1,47 @@
+// fused_api.cuh -- host-side interface of the fused FP32 2D kernel shared by
+// the single-grid path (fused2d.cu) and the batched launch (batch.cu).
+#pragma once
+#include <vector>
+
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+struct FusedInst {
+    float* E[3];
+    float* B[3];
+    const float* J[3];
+    const float* halo;   // [strips][7][n1] of this instance
+    const float4* sym;   // per-mode {Re S, Im S, cj1, cj}
+    const float2* twM;
+    const float2* twC;
+    float a2;            // c dt / dx2
+    int n2;
+};
+constexpr int kMaxInst = 24;
+struct FusedBatch {
+    FusedInst inst[kMaxInst];
+    const int4* items;   // {instance, strip, p0, p1}
+    int n_items;
+};
+
+struct FusedPlan {
+    int n_strips = 0;
+    int4* items = nullptr;        // [n_items] {instance 0, strip, p0, p1} (device)
+    int n_items = 0;
+    int grid = 0;                 // CTAs of the persistent launch
+    float* halo = nullptr;        // [n_strips][7][n1]
+    float4* sym = nullptr;        // [M + 1] {Re S, Im S, cj1, cj}, S = c dt sigma+
+    float2* twM = nullptr;        // [M] W_M^j (the grid's FP32 table)
+    float2* twC = nullptr;        // [256] W_N^c
+};
+
+size_t fused_smem_bytes(int n1);
+int fused_threads(int n1);
+cudaError_t fused_occupancy(int n1, int* occ);
+cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+std::vector<int4> fused_items(int inst, int n2, int n_strips);
+FusedInst fused_inst(const hyb_grid* g);
+hyb_status fused_set_strips(hyb_grid* g, int n_strips);
+
+}  // namespace hyb

@@ -38,7 +38,7 @@ struct ModeTables {
     cplx<T>* sgp = nullptr;   // sigma+ (without c dt), for diagnostics
 };
 
-struct FusedPlan;   // defined in fused2d.cu
+struct FusedPlan;   // defined in fused_api.cuh
 
 }  // namespace hyb
 

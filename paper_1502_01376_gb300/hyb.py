@@ -89,6 +89,20 @@ def lib():
             L.hyb_grid_path.restype = ctypes.c_int
             L.hyb_set_kernel_events.argtypes = [_V, _V, _V]
             L.hyb_set_kernel_events.restype = S
+            L.hyb_batch_create.argtypes = [D, ctypes.c_int, _V, ctypes.POINTER(_V)]
+            L.hyb_batch_create.restype = S
+            L.hyb_batch_bind.argtypes = [_V, ctypes.c_int, _P3, _P3, _P3]
+            L.hyb_batch_bind.restype = S
+            L.hyb_batch_tune.argtypes = [_V, ctypes.c_int]
+            L.hyb_batch_tune.restype = S
+            L.hyb_batch_advance.argtypes = [_V, ctypes.c_int]
+            L.hyb_batch_advance.restype = S
+            L.hyb_batch_rows_per_strip.argtypes = [_V, ctypes.c_int]
+            L.hyb_batch_rows_per_strip.restype = ctypes.c_int
+            L.hyb_batch_launches_per_step.argtypes = [_V]
+            L.hyb_batch_launches_per_step.restype = ctypes.c_int
+            L.hyb_batch_destroy.argtypes = [_V]
+            L.hyb_batch_destroy.restype = S
             L.hyb_launches_per_step.argtypes = [_V]
             L.hyb_launches_per_step.restype = ctypes.c_int
             _lib = L
@@ -183,6 +197,37 @@ def hyb_launches_per_step(g: int) -> int:
     return lib().hyb_launches_per_step(_V(g))
 
 
+def hyb_batch_create(descs, stream: int = 0) -> int:
+    arr = (GridDesc * len(descs))(*descs)
+    h = _V()
+    _check(lib().hyb_batch_create(arr, len(descs), _V(stream), ctypes.byref(h)))
+    return h.value
+
+
+def hyb_batch_bind(b: int, i: int, E, B, J):
+    _check(lib().hyb_batch_bind(_V(b), i, _P3(*E), _P3(*B), _P3(*J)))
+
+
+def hyb_batch_tune(b: int, trials: int = 3):
+    _check(lib().hyb_batch_tune(_V(b), trials))
+
+
+def hyb_batch_advance(b: int, nsteps: int):
+    _check(lib().hyb_batch_advance(_V(b), nsteps))
+
+
+def hyb_batch_rows_per_strip(b: int, n1: int) -> int:
+    return lib().hyb_batch_rows_per_strip(_V(b), n1)
+
+
+def hyb_batch_launches_per_step(b: int) -> int:
+    return lib().hyb_batch_launches_per_step(_V(b))
+
+
+def hyb_batch_destroy(b: int):
+    _check(lib().hyb_batch_destroy(_V(b)))
+
+
 # ---- tensor convenience ----------------------------------------------------------
 def _ptr(t):
     return 0 if t is None else int(t.data_ptr())
@@ -256,6 +301,45 @@ class Grid:
     def close(self):
         if self.h:
             hyb_destroy_grid(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several grids advanced together (one CUDA-graph launch per step)."""
+
+    def __init__(self, descs, stream=None):
+        import torch
+        self.descs = list(descs)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = hyb_batch_create(self.descs, self.stream.cuda_stream)
+        self.bound = {}
+
+    def bind(self, i, E, B, J):
+        self.bound[i] = (list(E), list(B), list(J))
+        hyb_batch_bind(self.h, i, [_ptr(t) for t in E], [_ptr(t) for t in B], [_ptr(t) for t in J])
+
+    def tune(self, trials=3):
+        hyb_batch_tune(self.h, trials)
+
+    def advance(self, nsteps=1):
+        hyb_batch_advance(self.h, nsteps)
+
+    def rows_per_strip(self, n1):
+        return hyb_batch_rows_per_strip(self.h, n1)
+
+    @property
+    def launches_per_step(self):
+        return hyb_batch_launches_per_step(self.h)
+
+    def close(self):
+        if self.h:
+            hyb_batch_destroy(self.h)
             self.h = 0
 
     def __del__(self):
