@@ -111,6 +111,21 @@ HYB_API hyb_status hyb_deposit(hyb_grid* g, const int32_t* cell, const void* off
  * j1 <- IFFT_x1[ sin(k1 dx1/2)/(k1 dx1/2) FFT_x1[j1] ]. */
 HYB_API hyb_status hyb_correct_current(hyb_grid* g);
 
+/* The same j1 correction as hyb_correct_current, for callers that cannot
+ * allocate device memory (the paper has no counterpart; this is a library
+ * convenience).  It needs no grid: desc gives the sizes and cell size (dims,
+ * n1, n2, n3, dx1, precision, yee_mode and the Sec. 4 bump are read), j1 is
+ * the caller's device array (in place), stream a cudaStream_t.  It allocates
+ * nothing: its tables and the k1-space copy of a block of rows live in one
+ * static 8 MiB device array of the library, which every GPU that loads the
+ * library keeps until the process exits.  Rows are processed in blocks that
+ * fit the array; an n1 whose single row does not fit is rejected with
+ * HYB_EINVAL.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call reuses the same array, so calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race: serialise them. */
+HYB_API hyb_status hyb_correct_current_noalloc(const hyb_grid_desc* desc, void* j1, void* stream);
+
 /* The Sec. 4 k1 low-pass form factor alone, in place on all three bound J components. */
 HYB_API hyb_status hyb_filter(hyb_grid* g);
 

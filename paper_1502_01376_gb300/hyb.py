@@ -103,6 +103,8 @@ def lib():
             L.hyb_batch_launches_per_step.restype = ctypes.c_int
             L.hyb_batch_destroy.argtypes = [_V]
             L.hyb_batch_destroy.restype = S
+            L.hyb_correct_current_noalloc.argtypes = [D, _V, _V]
+            L.hyb_correct_current_noalloc.restype = S
             L.hyb_launches_per_step.argtypes = [_V]
             L.hyb_launches_per_step.restype = ctypes.c_int
             _lib = L
@@ -153,6 +155,12 @@ def hyb_deposit(g: int, cell: int, off_old: int, off_new: int, v3: int, q: int, 
 
 def hyb_correct_current(g: int):
     _check(lib().hyb_correct_current(_V(g)))
+
+
+def hyb_correct_current_noalloc(desc: GridDesc, j1: int, stream: int = 0):
+    """j1 correction without any device allocation (working memory is a
+    static array of the library); for callers that cannot allocate."""
+    _check(lib().hyb_correct_current_noalloc(ctypes.byref(desc), _V(j1), _V(stream)))
 
 
 def hyb_filter(g: int):
