@@ -253,6 +253,10 @@ def main():
         torch.cuda.empty_cache()
 
     cells = w.cells
+    # the accuracy check starts from this initial state (the timed loop keeps
+    # driving the fields with the same current, which is not a physical run)
+    E_init = [t.clone() for t in E] if not args.no_extras else None
+    B_init = [t.clone() for t in B] if not args.no_extras else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     for _ in range(args.warmup):
         grid.advance(1)
@@ -302,12 +306,12 @@ def main():
     if rank == 0 and not args.no_extras:
         # accuracy of the FP32 step against the FP64 GPU path from identical inputs
         g64 = hyb.Grid(hyb.desc_from_workload(w, precision=64, path=1), stream)
-        E64 = [t.double() for t in E]
-        B64 = [t.double() for t in B]
+        E64 = [t.double() for t in E_init]
+        B64 = [t.double() for t in B_init]
         J64 = [t.double() for t in J]
         g64.bind(E64, B64, J64)
-        Ec = [t.clone() for t in E]
-        Bc = [t.clone() for t in B]
+        Ec = [t.clone() for t in E_init]
+        Bc = [t.clone() for t in B_init]
         g32 = hyb.Grid(hyb.desc_from_workload(w, path=0), stream)
         g32.bind(Ec, Bc, J)
         nacc = 10
@@ -322,7 +326,8 @@ def main():
         errs = []
         for a, b in zip(Ec + Bc, E64 + B64):
             errs.append(float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b)))
-        extras["accuracy"] = {"steps": nacc, "max_rel_err_vs_fp64_gpu_path": max(errs),
+        extras["accuracy"] = {"steps": nacc, "from": "initial state, same FP32-rounded inputs and J",
+                              "max_rel_err_vs_fp64_gpu_path": max(errs),
                               "per_field": dict(zip(["E1", "E2", "E3", "B1", "B2", "B3"], errs))}
         extras["fp64_gpu_path"] = {"value": cells / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64}
         g64.close()
