@@ -201,6 +201,26 @@ HYB_API int hyb_batch_launches_per_step(const hyb_batch* b);
 /* Frees the batch and its grids (not the caller's arrays). */
 HYB_API hyb_status hyb_batch_destroy(hyb_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * NCI analysis (Sec. 3 and the Appendix): growth rate of the numerical
+ * Cerenkov instability of a cold plasma drifting along x1 on the hybrid
+ * solver's grid, from the roots of the numerical dispersion relation
+ * (Eq. 2dmodesres with its coupling term; hybrid operators [k]E1 = [k]B1 = k1,
+ * [k]E2 = [k]B2 = sin(k2 dx2/2)/(dx2/2)), seeded by the roots of the cubic
+ * Eq. asym1 and refined by Newton's method, in FP64 on the GPU.
+ *   samples  device double [n][9]: dt, dx1, dx2, gamma, wp2 (plasma frequency^2,
+ *            n/n_p), filt_kc, filt_w (current filter, fractions of pi/dx1;
+ *            kc outside (0,1) = off), k1, k2;
+ *   order    particle shape order l (1..3), momentum-conserving interpolation;
+ *   correct_j1  1: the Eq. currentcorrection factor multiplies S_j1;
+ *   alias    device int [n_alias][2]: (mu, nu1) pairs;
+ *   growth   device double [n][n_alias]: max Im(omega) over the refined roots
+ *            of that alias (0 if none grows);
+ *   root     device double [n][n_alias][2] (nullable): the root that gives it.
+ * Asynchronous on stream. */
+HYB_API hyb_status hyb_nci_growth(const double* samples, int64_t n, int order, int correct_j1,
+                                  const int* alias, int n_alias, double* growth, double* root, void* stream);
+
 /* Which advance path a grid runs: 1 three-pass, 2 fused. */
 HYB_API int hyb_grid_path(const hyb_grid* g);
 

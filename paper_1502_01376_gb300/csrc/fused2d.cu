@@ -261,6 +261,28 @@ __device__ __forceinline__ Job job_of(const FusedInst& a, int N, int strip, int 
     return j;
 }
 
+// source row of the idx-th forward transform of group g in a work item
+// (prologue: P1 all groups, P2 groups 0 and 1, P3 groups 0 and 2; then R1, R2, R3 per row)
+__device__ __forceinline__ const float* fwd_src(const FusedInst& a, int N, int strip, int p0, int p1, int g, int idx) {
+    const float* halo = a.halo + (size_t)strip * 7 * N;
+    const int npro = (g == 0) ? 3 : 2;
+    if (idx < npro) {
+        if (idx == 0) return g == 0 ? a.E[0] + (size_t)p0 * N : g == 1 ? a.E[2] + (size_t)p0 * N : halo + 1 * N;
+        if (idx == 1) return g == 0 ? halo + 0 * N : g == 1 ? halo + 2 * N : halo + 4 * N;
+        return halo + 3 * N;                                            // g == 0, P3
+    }
+    const int q = idx - npro;
+    const int p = p0 + q / 3, r = q % 3;
+    if (p >= p1) return nullptr;
+    if (r == 0) {
+        if (g == 2) return a.E[1] + (size_t)p * N;
+        const int c = g == 0 ? 0 : 2;
+        return (p + 1 < p1) ? a.E[c] + (size_t)(p + 1) * N : halo + (g == 0 ? 5 : 6) * N;
+    }
+    if (r == 1) return a.B[g] + (size_t)p * N;
+    return a.J[g] + (size_t)p * N;
+}
+
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch fb) {
     using G = Geo<N>;
@@ -269,17 +291,16 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
     float2* slots = smem;
     const int g = threadIdx.x / T, t = threadIdx.x % T;
     float2* xb = smem + kSlots * M + g * XB;
+    float2* s_tw2 = smem + kSlots * M + 3 * XB;                     // [P3][16] W_T^{ma l}
     if ((int)blockIdx.x >= fb.n_items) return;
 
-    // per-thread twiddles (exact FP64-rounded values; identical for every instance with this n1)
+    // twiddles: exact FP64-rounded values, identical for every instance with this n1
     const FusedInst& i0 = fb.inst[fb.items[blockIdx.x].x];
-    float2 tw1[16], tw2[16];
+    float2 tw1[16];
     const int kb = t & 15, ma = t >> 4;
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-        tw1[k] = i0.twM[t * k];                    // W_M^{t k}, t k < M
-        tw2[k] = i0.twM[16 * ma * k];              // W_T^{ma k} = W_M^{16 ma k}
-    }
+    for (int k = 0; k < 16; k++) tw1[k] = i0.twM[t * k];         // W_M^{t k}, t k < M
+    for (int i = threadIdx.x; i < P3 * 16; i += blockDim.x) s_tw2[i] = i0.twM[16 * (i >> 4) * (i & 15)];
     // column pairs owned by this thread
     int cA[Q / 2];
     float2 wA[Q / 2];
@@ -287,43 +308,42 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
     for (int p = 0; p < Q / 2; p++) {
         const int pi = t + T * p;
         cA[p] = pi;
-        wA[p] = i0.twC[pi];                        // W_N^{cA}
+        wA[p] = i0.twC[pi];                                          // W_N^{cA}
     }
     const float2 w128 = i0.twC[128];
     auto colB = [&](int p) { return cA[p] == 0 ? 128 : 256 - cA[p]; };
     const float inv2M = 0.5f / (float)M;
+    __syncthreads();
 
   for (int item = blockIdx.x; item < fb.n_items; item += gridDim.x) {
     const int4 it = fb.items[item];
-    const FusedInst a = fb.inst[it.x];
+    const FusedInst& a = fb.inst[it.x];
     const int strip = it.y, p0 = it.z, p1 = it.w;
     const int nrounds = 3 + 5 * (p1 - p0);
+    const float a2 = a.a2;
 
     float2 pf[16];
-    bool pf_ok = false;
-    auto prefetch = [&](int from_ri) {
-        pf_ok = false;
-        for (int rr = from_ri; rr < nrounds && rr < from_ri + 5; rr++) {
-            Job nj = job_of(a, N, strip, p0, p1, rr, g);
-            if (nj.kind == J_FWD) {
-                const float2* s = reinterpret_cast<const float2*>(nj.src);
+    int fidx = 0;
+    {
+        const float2* s0 = reinterpret_cast<const float2*>(fwd_src(a, N, strip, p0, p1, g, 0));
 #pragma unroll
-                for (int nb = 0; nb < 16; nb++) pf[nb] = ldg_stream(s + t + T * nb);
-                pf_ok = true;
-                return;
-            }
-        }
-    };
-    prefetch(0);
+        for (int nb = 0; nb < 16; nb++) pf[nb] = ldg_stream(s0 + t + T * nb);
+    }
 
     float2 x[16];
     for (int ri = 0; ri < nrounds; ri++) {
         const Job j = job_of(a, N, strip, p0, p1, ri, g);
         if (j.kind == J_FWD) {
-            // ---------------- forward real FFT of one row
+            // ---------------- stage 1: 16-point DFT of z[t + T n_b] from the prefetched row
 #pragma unroll
             for (int nb = 0; nb < 16; nb++) x[nb] = pf[nb];
-            prefetch(ri + 1);
+            {
+                const float2* nsrc = reinterpret_cast<const float2*>(fwd_src(a, N, strip, p0, p1, g, ++fidx));
+                if (nsrc) {
+#pragma unroll
+                    for (int nb = 0; nb < 16; nb++) pf[nb] = ldg_stream(nsrc + t + T * nb);
+                }
+            }
             Dft<16, false>::run(x);
 #pragma unroll
             for (int k = 1; k < 16; k++) x[k] = mul(x[k], tw1[k]);
@@ -339,31 +359,33 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
 #pragma unroll
                 for (int l = 0; l < P3; l++) {
                     const int ea = (2 * p) * P3 + l;
-                    if (cA[p] != 0) {
-                        const int eb = (2 * p + 1) * P3 + (P3 - 1 - l);
-                        const float2 w = mul(wA[p], wr(2 * P3, l));
-                        const float2 xa = x[ea], xbv = x[eb];
-                        const float2 E = scl(add(xa, conjf2(xbv)), inv2M);
-                        const float2 O = scl(mulc(sub(xa, conjf2(xbv)), w), inv2M);
-                        const float2 v = f2(-O.y, O.x);
-                        x[ea] = add(E, v);
-                        x[eb] = conjf2(sub(E, v));
-                    }
+                    const int eb = (2 * p + 1) * P3 + (P3 - 1 - l);
+                    const float2 w = mul(wA[p], wr(2 * P3, l));
+                    const float2 xa = x[ea], xbv = x[eb];
+                    const float2 E = scl(add(xa, conjf2(xbv)), inv2M);
+                    const float2 O = scl(mulc(sub(xa, conjf2(xbv)), w), inv2M);
+                    const float2 v = f2(-O.y, O.x);
+                    x[ea] = add(E, v);
+                    x[eb] = conjf2(sub(E, v));
                 }
             }
             if (t == 0) {
-                // column 0: l = 0 packs (X0, XM); pairs l <-> P3 - l
+                // the general formula above paired column 0 with itself wrongly: recompute
+                // column 0 (l = 0 packs (X0, XM); pairs l <-> P3 - l) and column 128 (l <-> P3-1-l)
+                float2 c0[P3], c1[P3];
+                const float2* sl = slots + j.slot * M + t;
+#pragma unroll
+                for (int l = 0; l < P3; l++) { c0[l] = sl[l * T]; c1[l] = sl[(P3 + l) * T]; }
                 {
-                    const float X0 = x[0].x, XM = x[0].y;
-                    const float e = (X0 + XM) * inv2M, o = (X0 - XM) * inv2M;
-                    x[0] = f2(e, o);
+                    const float X0 = c0[0].x, XM = c0[0].y;
+                    x[0] = f2((X0 + XM) * inv2M, (X0 - XM) * inv2M);
                 }
 #pragma unroll
                 for (int l = 1; l < P3; l++) {
                     if (l <= P3 - l) {
                         const int ea = l, eb = P3 - l;
                         const float2 w = wr(2 * P3, l);
-                        const float2 xa = x[ea], xbv = x[eb];
+                        const float2 xa = c0[ea], xbv = c0[eb];
                         const float2 E = scl(add(xa, conjf2(xbv)), inv2M);
                         const float2 O = scl(mulc(sub(xa, conjf2(xbv)), w), inv2M);
                         const float2 v = f2(-O.y, O.x);
@@ -371,18 +393,17 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
                         if (eb != ea) x[eb] = conjf2(sub(E, v));
                     }
                 }
-                // column 128 (elements P3 .. 2P3-1): pairs l <-> P3 - 1 - l
 #pragma unroll
                 for (int l = 0; l < P3; l++) {
                     if (l <= P3 - 1 - l) {
-                        const int ea = P3 + l, eb = P3 + (P3 - 1 - l);
+                        const int ea = l, eb = P3 - 1 - l;
                         const float2 w = mul(w128, wr(2 * P3, l));
-                        const float2 xa = x[ea], xbv = x[eb];
+                        const float2 xa = c1[ea], xbv = c1[eb];
                         const float2 E = scl(add(xa, conjf2(xbv)), inv2M);
                         const float2 O = scl(mulc(sub(xa, conjf2(xbv)), w), inv2M);
                         const float2 v = f2(-O.y, O.x);
-                        x[ea] = add(E, v);
-                        if (eb != ea) x[eb] = conjf2(sub(E, v));
+                        x[P3 + ea] = add(E, v);
+                        if (eb != ea) x[P3 + eb] = conjf2(sub(E, v));
                     }
                 }
             }
@@ -414,12 +435,12 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
         if (j.kind == J_FWD) {
             Dft<16, false>::run(x);
 #pragma unroll
-            for (int l = 1; l < 16; l++) x[l] = mul(x[l], tw2[l]);
+            for (int l = 1; l < 16; l++) x[l] = mul(x[l], s_tw2[ma * 16 + l]);
 #pragma unroll
             for (int l = 0; l < 16; l++) xb[ma * 256 + l * 16 + kb] = x[l];
         } else if (j.kind == J_INV) {
 #pragma unroll
-            for (int l = 1; l < 16; l++) x[l] = mulc(x[l], tw2[l]);
+            for (int l = 1; l < 16; l++) x[l] = mulc(x[l], s_tw2[ma * 16 + l]);
             Dft<16, true>::run(x);
 #pragma unroll
             for (int mb = 0; mb < 16; mb++) xb[kb * (T + 1) + ma + P3 * mb] = x[mb];
@@ -440,34 +461,34 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
                     for (int l = 0; l < P3; l++) x[(2 * p + s) * P3 + l] = w[l];
                 }
             }
+            float2 z0[P3], z1[P3];                  // column 0 and 128 of thread 0, kept for the fix-up
+            if (t == 0) {
+#pragma unroll
+                for (int l = 0; l < P3; l++) { z0[l] = x[l]; z1[l] = x[P3 + l]; }
+            }
             // X[k] = e - u, X[M-k] = conj(e + u), e = (a + conj b)/2, u = (i/2) W_N^k (a - conj b)
 #pragma unroll
             for (int p = 0; p < Q / 2; p++) {
 #pragma unroll
                 for (int l = 0; l < P3; l++) {
-                    if (cA[p] != 0) {
-                        const int ea = (2 * p) * P3 + l, eb = (2 * p + 1) * P3 + (P3 - 1 - l);
-                        const float2 w = mul(wA[p], wr(2 * P3, l));
-                        const float2 av = x[ea], bv = x[eb];
-                        const float2 e = scl(add(av, conjf2(bv)), 0.5f);
-                        const float2 wd = mul(w, sub(av, conjf2(bv)));
-                        const float2 u = f2(-0.5f * wd.y, 0.5f * wd.x);
-                        x[ea] = sub(e, u);
-                        x[eb] = conjf2(add(e, u));
-                    }
+                    const int ea = (2 * p) * P3 + l, eb = (2 * p + 1) * P3 + (P3 - 1 - l);
+                    const float2 w = mul(wA[p], wr(2 * P3, l));
+                    const float2 av = x[ea], bv = x[eb];
+                    const float2 e = scl(add(av, conjf2(bv)), 0.5f);
+                    const float2 wd = mul(w, sub(av, conjf2(bv)));
+                    const float2 u = f2(-0.5f * wd.y, 0.5f * wd.x);
+                    x[ea] = sub(e, u);
+                    x[eb] = conjf2(add(e, u));
                 }
             }
             if (t == 0) {
-                {
-                    const float2 z0 = x[0];
-                    x[0] = f2(z0.x + z0.y, z0.x - z0.y);     // (X0, X_M) packed
-                }
+                x[0] = f2(z0[0].x + z0[0].y, z0[0].x - z0[0].y);     // (X0, X_M) packed
 #pragma unroll
                 for (int l = 1; l < P3; l++) {
                     if (l <= P3 - l) {
                         const int ea = l, eb = P3 - l;
                         const float2 w = wr(2 * P3, l);
-                        const float2 av = x[ea], bv = x[eb];
+                        const float2 av = z0[ea], bv = z0[eb];
                         const float2 e = scl(add(av, conjf2(bv)), 0.5f);
                         const float2 wd = mul(w, sub(av, conjf2(bv)));
                         const float2 u = f2(-0.5f * wd.y, 0.5f * wd.x);
@@ -478,78 +499,123 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
 #pragma unroll
                 for (int l = 0; l < P3; l++) {
                     if (l <= P3 - 1 - l) {
-                        const int ea = P3 + l, eb = P3 + (P3 - 1 - l);
+                        const int ea = l, eb = P3 - 1 - l;
                         const float2 w = mul(w128, wr(2 * P3, l));
-                        const float2 av = x[ea], bv = x[eb];
+                        const float2 av = z1[ea], bv = z1[eb];
                         const float2 e = scl(add(av, conjf2(bv)), 0.5f);
                         const float2 wd = mul(w, sub(av, conjf2(bv)));
                         const float2 u = f2(-0.5f * wd.y, 0.5f * wd.x);
-                        x[ea] = sub(e, u);
-                        if (eb != ea) x[eb] = conjf2(add(e, u));
+                        x[P3 + ea] = sub(e, u);
+                        if (eb != ea) x[P3 + eb] = conjf2(add(e, u));
                     }
                 }
             }
             // ---------------- epilogue: per-mode updates on thread-owned kappa
             const int p = j.row;
-            const float a2 = a.a2;
-            float2* Sl = slots;
-#pragma unroll
-            for (int e = 0; e < 16; e++) {
+            float2* Sl = slots + t;
+            float2* dst = Sl + j.slot * M;
+            const float4* sym = a.sym;
+            auto kap_of = [&](int e) {
                 const int pp = e / (2 * P3), s = (e / P3) & 1, l = e % P3;
-                const int c = s == 0 ? cA[pp] : colB(pp);
-                const int kap = c + 256 * l;
-                const bool packed = (t == 0 && e == 0);
-                const int o = e * T + t;
-                float4 sy = a.sym[kap];
-                float2 S = f2(sy.x, sy.y);
-                float cj1 = sy.z, cj = sy.w;
-                if (packed) {                                   // DC in .x, Nyquist in .y: both real
-                    const float4 sn = a.sym[M];
-                    S = f2(sy.x, sn.x);
-                    cj1 = 0.f; cj = 0.f;
-                    (void)cj1; (void)cj;
+                return (s == 0 ? cA[pp] : colB(pp)) + 256 * l;
+            };
+            switch (j.epi) {
+            case X_STORE:
+#pragma unroll
+                for (int e = 0; e < 16; e++) dst[e * T] = x[e];
+                break;
+            case X_B1: {        // B1 -= a2 (E3(p+1) - E3(p))
+                const float2* u = Sl + sE3(p + 1) * M;
+                const float2* v = Sl + sE3(p) * M;
+#pragma unroll
+                for (int e = 0; e < 16; e++) dst[e * T] = sub(x[e], scl(sub(u[e * T], v[e * T]), a2));
+            } break;
+            case X_B2: {        // B2 += S E3(p)
+                const float2* v = Sl + sE3(p) * M;
+                float2 S[16];
+#pragma unroll
+                for (int e = 0; e < 16; e++) { const float4 q = sym[kap_of(e)]; S[e] = f2(q.x, q.y); }
+#pragma unroll
+                for (int e = 0; e < 16; e++)
+                    if (e != 0 || t != 0) dst[e * T] = add(x[e], mul(S[e], v[e * T]));
+                if (t == 0) {                     // packed DC/Nyquist element: two real updates
+                    const float sd = sym[0].x, sn = sym[M].x;
+                    const float2 e3 = v[0];
+                    dst[0] = f2(x[0].x + sd * e3.x, x[0].y + sn * e3.y);
                 }
-                const float2 X = x[e];
-                float2 out = X;
-                switch (j.epi) {
-                case X_STORE: break;
-                case X_B1: {      // B1 -= a2 (E3(p+1) - E3(p))
-                    const float2 d = sub(Sl[sE3(p + 1) * M + o], Sl[sE3(p) * M + o]);
-                    out = sub(X, scl(d, a2));
-                } break;
-                case X_B2: {      // B2 += S E3(p)
-                    const float2 e3 = Sl[sE3(p) * M + o];
-                    out = packed ? f2(X.x + S.x * e3.x, X.y + S.y * e3.y) : add(X, mul(S, e3));
-                } break;
-                case X_B3: {      // B3 += a2 (E1(p+1) - E1(p)) - S E2(p)
-                    const float2 d = sub(Sl[sE1(p + 1) * M + o], Sl[sE1(p) * M + o]);
-                    const float2 e2 = Sl[sE2 * M + o];
-                    const float2 se2 = packed ? f2(S.x * e2.x, S.y * e2.y) : mul(S, e2);
-                    out = sub(add(X, scl(d, a2)), se2);
-                } break;
-                case X_J1: {      // E1 += a2 (B3(p) - B3(p-1)) - cj1 j1
-                    const float2 d = sub(Sl[sB3(p) * M + o], Sl[sB3(p - 1) * M + o]);
-                    const float2 e1 = Sl[sE1(p) * M + o];
-                    const float2 cjv = packed ? f2(sy.z, a.sym[M].z) : f2(cj1, cj1);
-                    out = f2(e1.x + a2 * d.x - cjv.x * X.x, e1.y + a2 * d.y - cjv.y * X.y);
-                } break;
-                case X_J2: {      // E2 += conj(S) B3(p) - cj j2
-                    const float2 b3 = Sl[sB3(p) * M + o];
-                    const float2 e2 = Sl[sE2 * M + o];
-                    const float2 cjv = packed ? f2(sy.w, a.sym[M].w) : f2(cj, cj);
-                    const float2 sb = packed ? f2(S.x * b3.x, S.y * b3.y) : mulc(b3, S);
-                    out = f2(e2.x + sb.x - cjv.x * X.x, e2.y + sb.y - cjv.y * X.y);
-                } break;
-                default: {        // X_J3: E3 += -conj(S) B2(p) - a2 (B1(p) - B1(p-1)) - cj j3
-                    const float2 b2 = Sl[sB2 * M + o];
-                    const float2 d = sub(Sl[sB1(p) * M + o], Sl[sB1(p - 1) * M + o]);
-                    const float2 e3 = Sl[sE3(p) * M + o];
-                    const float2 cjv = packed ? f2(sy.w, a.sym[M].w) : f2(cj, cj);
-                    const float2 sb = packed ? f2(S.x * b2.x, S.y * b2.y) : mulc(b2, S);
-                    out = f2(e3.x - sb.x - a2 * d.x - cjv.x * X.x, e3.y - sb.y - a2 * d.y - cjv.y * X.y);
-                } break;
+            } break;
+            case X_B3: {        // B3 += a2 (E1(p+1) - E1(p)) - S E2(p)
+                const float2* u = Sl + sE1(p + 1) * M;
+                const float2* v = Sl + sE1(p) * M;
+                const float2* w2 = Sl + sE2 * M;
+                float2 S[16];
+#pragma unroll
+                for (int e = 0; e < 16; e++) { const float4 q = sym[kap_of(e)]; S[e] = f2(q.x, q.y); }
+#pragma unroll
+                for (int e = 0; e < 16; e++)
+                    if (e != 0 || t != 0)
+                        dst[e * T] = sub(add(x[e], scl(sub(u[e * T], v[e * T]), a2)), mul(S[e], w2[e * T]));
+                if (t == 0) {
+                    const float sd = sym[0].x, sn = sym[M].x;
+                    const float2 d = sub(u[0], v[0]), e2 = w2[0];
+                    dst[0] = f2(x[0].x + a2 * d.x - sd * e2.x, x[0].y + a2 * d.y - sn * e2.y);
                 }
-                Sl[j.slot * M + o] = out;
+            } break;
+            case X_J1: {        // E1 += a2 (B3(p) - B3(p-1)) - cj1 j1
+                const float2* u = Sl + sB3(p) * M;
+                const float2* v = Sl + sB3(p - 1) * M;
+                float cj1[16];
+#pragma unroll
+                for (int e = 0; e < 16; e++) cj1[e] = sym[kap_of(e)].z;
+                if (t == 0) cj1[0] = sym[0].z;                    // DC; the Nyquist half below
+                const float cjn = (t == 0) ? sym[M].z : 0.f;
+#pragma unroll
+                for (int e = 0; e < 16; e++) {
+                    const float2 d = sub(u[e * T], v[e * T]), e1 = dst[e * T];
+                    const float cy = (e == 0 && t == 0) ? cjn : cj1[e];
+                    dst[e * T] = f2(e1.x + a2 * d.x - cj1[e] * x[e].x, e1.y + a2 * d.y - cy * x[e].y);
+                }
+            } break;
+            case X_J2: {        // E2 += conj(S) B3(p) - cj j2
+                const float2* u = Sl + sB3(p) * M;
+                float4 q[16];
+#pragma unroll
+                for (int e = 0; e < 16; e++) q[e] = sym[kap_of(e)];
+#pragma unroll
+                for (int e = 0; e < 16; e++) {
+                    if (e != 0 || t != 0) {
+                        const float2 sb = mulc(u[e * T], f2(q[e].x, q[e].y)), e2 = dst[e * T];
+                        dst[e * T] = f2(e2.x + sb.x - q[e].w * x[e].x, e2.y + sb.y - q[e].w * x[e].y);
+                    }
+                }
+                if (t == 0) {                     // real symbols at DC and Nyquist
+                    const float4 qd = sym[0], qn = sym[M];
+                    const float2 b3 = u[0], e2 = dst[0];
+                    dst[0] = f2(e2.x + qd.x * b3.x - qd.w * x[0].x, e2.y + qn.x * b3.y - qn.w * x[0].y);
+                }
+            } break;
+            default: {          // X_J3: E3 += -conj(S) B2(p) - a2 (B1(p) - B1(p-1)) - cj j3
+                const float2* b2p = Sl + sB2 * M;
+                const float2* u = Sl + sB1(p) * M;
+                const float2* v = Sl + sB1(p - 1) * M;
+                float4 q[16];
+#pragma unroll
+                for (int e = 0; e < 16; e++) q[e] = sym[kap_of(e)];
+#pragma unroll
+                for (int e = 0; e < 16; e++) {
+                    if (e != 0 || t != 0) {
+                        const float2 sb = mulc(b2p[e * T], f2(q[e].x, q[e].y));
+                        const float2 d = sub(u[e * T], v[e * T]), e3 = dst[e * T];
+                        dst[e * T] = f2(e3.x - sb.x - a2 * d.x - q[e].w * x[e].x, e3.y - sb.y - a2 * d.y - q[e].w * x[e].y);
+                    }
+                }
+                if (t == 0) {
+                    const float4 qd = sym[0], qn = sym[M];
+                    const float2 b2 = b2p[0], d = sub(u[0], v[0]), e3 = dst[0];
+                    dst[0] = f2(e3.x - qd.x * b2.x - a2 * d.x - qd.w * x[0].x,
+                                e3.y - qn.x * b2.y - a2 * d.y - qn.w * x[0].y);
+                }
+            } break;
             }
         } else if (j.kind == J_INV) {
             // ---------------- stage 1 inverse: gather over k_b, twiddle, 16-point inverse DFT, store
@@ -595,7 +661,7 @@ bool fused_supported(const hyb_grid_desc& d) {
 }
 
 template <int N>
-static size_t fused_smem() { return sizeof(float2) * ((size_t)kSlots * Geo<N>::M + 3 * (size_t)Geo<N>::XB); }
+static size_t fused_smem() { return sizeof(float2) * ((size_t)kSlots * Geo<N>::M + 3 * (size_t)Geo<N>::XB + 16 * Geo<N>::P3); }
 
 size_t fused_smem_bytes(int n1) {
     switch (n1) {

@@ -105,6 +105,8 @@ def lib():
             L.hyb_batch_destroy.restype = S
             L.hyb_correct_current_noalloc.argtypes = [D, _V, _V]
             L.hyb_correct_current_noalloc.restype = S
+            L.hyb_nci_growth.argtypes = [_V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _V, ctypes.c_int, _V, _V, _V]
+            L.hyb_nci_growth.restype = S
             L.hyb_launches_per_step.argtypes = [_V]
             L.hyb_launches_per_step.restype = ctypes.c_int
             _lib = L
@@ -234,6 +236,29 @@ def hyb_batch_launches_per_step(b: int) -> int:
 
 def hyb_batch_destroy(b: int):
     _check(lib().hyb_batch_destroy(_V(b)))
+
+
+def hyb_nci_growth(samples: int, n: int, order: int, correct_j1: bool, alias: int, n_alias: int,
+                   growth: int, root: int = 0, stream: int = 0):
+    _check(lib().hyb_nci_growth(_V(samples), n, order, int(bool(correct_j1)), _V(alias), n_alias,
+                                _V(growth), _V(root or 0), _V(stream)))
+
+
+def nci_growth(samples, aliases=((0, -1), (0, 0), (0, 1)), order=2, correct_j1=True, want_roots=False):
+    """samples: CUDA float64 tensor [n, 9]; returns growth [n, n_alias] (and roots [n, n_alias] complex)."""
+    import torch
+    assert samples.is_cuda and samples.dtype == torch.float64 and samples.shape[1] == 9
+    samples = samples.contiguous()
+    n = samples.shape[0]
+    al = torch.tensor(list(aliases), dtype=torch.int32, device=samples.device).contiguous()
+    g = torch.empty((n, len(aliases)), dtype=torch.float64, device=samples.device)
+    r = torch.empty((n, len(aliases), 2), dtype=torch.float64, device=samples.device) if want_roots else None
+    hyb_nci_growth(int(samples.data_ptr()), n, order, correct_j1, int(al.data_ptr()), len(aliases),
+                   int(g.data_ptr()), int(r.data_ptr()) if r is not None else 0,
+                   torch.cuda.current_stream().cuda_stream)
+    if want_roots:
+        return g, torch.view_as_complex(r)
+    return g
 
 
 # ---- tensor convenience ----------------------------------------------------------
