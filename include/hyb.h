@@ -221,6 +221,35 @@ HYB_API hyb_status hyb_batch_destroy(hyb_batch* b);
 HYB_API hyb_status hyb_nci_growth(const double* samples, int64_t n, int order, int correct_j1,
                                   const int* alias, int n_alias, double* growth, double* root, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * NCI surrogate: a small MLP (n_in -> width x depth tanh layers -> 1) trained
+ * on the root solver's growth rates to pick the filter cutoff and time step
+ * before a run.  Forward, backward and Adam are this library's kernels: BF16
+ * weights and activations as tensor-core operands (mma m16n8k16), FP32
+ * accumulation, FP32 master weights.  Parameters are laid out per layer as
+ * W[out][in] then b[out] (FP32).  x is device FP32 [B][n_in]; targets, outputs
+ * device FP32 [B].
+ * ------------------------------------------------------------------------- */
+typedef struct hyb_mlp hyb_mlp;   /* opaque */
+
+/* init_params: host FP32 [hyb_mlp_num_params] (NULL = zeros). Synchronous. */
+HYB_API hyb_status hyb_mlp_create(int n_in, int width, int depth, const float* init_params, hyb_mlp** out);
+HYB_API int64_t hyb_mlp_num_params(const hyb_mlp* m);
+HYB_API hyb_status hyb_mlp_set_params(hyb_mlp* m, const float* params_host);
+HYB_API hyb_status hyb_mlp_get_params(hyb_mlp* m, float* params_host);
+/* y = network(x), asynchronous on stream. */
+HYB_API hyb_status hyb_mlp_forward(hyb_mlp* m, const float* x, int64_t B, float* y, void* stream);
+/* Gradient of the mean-squared error sum_b (y_b - t_b)^2 / B with respect to
+ * every parameter (host FP32 [num_params], nullable) and the loss (host,
+ * nullable); synchronises stream.  Used to check the backward kernels. */
+HYB_API hyb_status hyb_mlp_gradients(hyb_mlp* m, const float* x, const float* target, int64_t B, float* grad_host,
+                                     float* loss_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean-squared error;
+ * the loss before the step is written to loss_dev (device FP32, nullable). */
+HYB_API hyb_status hyb_mlp_train_step(hyb_mlp* m, const float* x, const float* target, int64_t B, float lr, float* loss_dev,
+                                      void* stream);
+HYB_API hyb_status hyb_mlp_destroy(hyb_mlp* m);
+
 /* Which advance path a grid runs: 1 three-pass, 2 fused. */
 HYB_API int hyb_grid_path(const hyb_grid* g);
 

@@ -65,6 +65,10 @@ static FusedBatch group_args(hyb_batch* b, const hyb_batch::Group& G) {
     for (size_t k = 0; k < G.members.size(); k++) fb.inst[k] = fused_inst(b->grids[G.members[k]]);
     fb.items = G.items;
     fb.n_items = G.n_items;
+    fb.flags = nullptr;                  // halo-buffer mode (work items may outnumber CTAs)
+    fb.epoch = 0;
+    fb.n_strips = 0;
+    fb.err = nullptr;
     return fb;
 }
 
@@ -203,6 +207,10 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
             }
             fb.items = G.items;
             fb.n_items = G.n_items;
+            fb.flags = nullptr;
+            fb.epoch = 0;
+            fb.n_strips = 0;
+            fb.err = nullptr;
             fused_launch(G.n1, fb, G.grid, b->stream, nullptr, nullptr);       // warm
             cudaEventRecord(e0, b->stream);
             for (int t = 0; t < trials; t++) fused_launch(G.n1, fb, G.grid, b->stream, nullptr, nullptr);

@@ -161,8 +161,24 @@ template <bool INV> struct Dft<16, INV> {
 
 __device__ __forceinline__ float2 ldg_stream(const float2* p) {
     float2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
     return v;
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+// bounded wait of one thread for flag >= epoch; on time-out sets bit 2 of *err and gives up
+__device__ __forceinline__ void wait_flag(const int* f, int epoch, int* err) {
+    const long long t0 = clock64();
+    while (ld_acquire(f) < epoch) {
+        if (clock64() - t0 > 4000000000LL) { atomicOr(err, 2); return; }
+        __nanosleep(256);
+    }
 }
 __device__ __forceinline__ void stg_stream(float2* p, float2 v) {
     asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(v.x), "f"(v.y) : "memory");
@@ -262,14 +278,24 @@ __device__ __forceinline__ Job job_of(const FusedInst& a, int N, int strip, int 
 }
 
 // source row of the idx-th forward transform of group g in a work item
-// (prologue: P1 all groups, P2 groups 0 and 1, P3 groups 0 and 2; then R1, R2, R3 per row)
-__device__ __forceinline__ const float* fwd_src(const FusedInst& a, int N, int strip, int p0, int p1, int g, int idx) {
+// (prologue: P1 all groups, P2 groups 0 and 1, P3 groups 0 and 2; then R1, R2, R3 per row).
+// Halo-buffer mode: rows outside the strip come from the buffer filled by k_halo.
+// Flag mode: the row before the strip is read from the fields directly, and the
+// row after it (E1, E3 only) from the copy published by the next strip.
+__device__ __forceinline__ const float* fwd_src(const FusedInst& a, int N, int strip, int p0, int p1, int g, int idx,
+                                                bool fm, int next) {
     const float* halo = a.halo + (size_t)strip * 7 * N;
     const int npro = (g == 0) ? 3 : 2;
     if (idx < npro) {
+        if (fm) {
+            const int h = (p0 - 1 + a.n2) % a.n2;
+            if (idx == 0) return g == 0 ? a.E[0] + (size_t)p0 * N : g == 1 ? a.E[2] + (size_t)p0 * N : a.E[1] + (size_t)h * N;
+            if (idx == 1) return g == 0 ? a.E[0] + (size_t)h * N : g == 1 ? a.E[2] + (size_t)h * N : a.B[2] + (size_t)h * N;
+            return a.B[0] + (size_t)h * N;                                  // g == 0, P3
+        }
         if (idx == 0) return g == 0 ? a.E[0] + (size_t)p0 * N : g == 1 ? a.E[2] + (size_t)p0 * N : halo + 1 * N;
         if (idx == 1) return g == 0 ? halo + 0 * N : g == 1 ? halo + 2 * N : halo + 4 * N;
-        return halo + 3 * N;                                            // g == 0, P3
+        return halo + 3 * N;                                                // g == 0, P3
     }
     const int q = idx - npro;
     const int p = p0 + q / 3, r = q % 3;
@@ -277,7 +303,9 @@ __device__ __forceinline__ const float* fwd_src(const FusedInst& a, int N, int s
     if (r == 0) {
         if (g == 2) return a.E[1] + (size_t)p * N;
         const int c = g == 0 ? 0 : 2;
-        return (p + 1 < p1) ? a.E[c] + (size_t)(p + 1) * N : halo + (g == 0 ? 5 : 6) * N;
+        if (p + 1 < p1) return a.E[c] + (size_t)(p + 1) * N;
+        if (fm) return a.halo + (size_t)next * 7 * N + (g == 0 ? 0 : 1) * N;
+        return halo + (g == 0 ? 5 : 6) * N;
     }
     if (r == 1) return a.B[g] + (size_t)p * N;
     return a.J[g] + (size_t)p * N;
@@ -293,6 +321,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
     float2* xb = smem + kSlots * M + g * XB;
     float2* s_tw2 = smem + kSlots * M + 3 * XB;                     // [P3][16] W_T^{ma l}
     if ((int)blockIdx.x >= fb.n_items) return;
+    const bool fm = fb.flags != nullptr;
 
     // twiddles: exact FP64-rounded values, identical for every instance with this n1
     const FusedInst& i0 = fb.inst[fb.items[blockIdx.x].x];
@@ -313,32 +342,65 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
     const float2 w128 = i0.twC[128];
     auto colB = [&](int p) { return cA[p] == 0 ? 128 : 256 - cA[p]; };
     const float inv2M = 0.5f / (float)M;
+    // Barriers: the three exchanges of a row FFT stay inside a group (named barrier
+    // 1 + g over its T threads); the whole CTA synchronises only where slots pass
+    // between groups: after P2, P3 (and P1 in flag mode), and after R1, R2, R5.
+    auto gsync = [&]() {
+        if (T >= 32) asm volatile("bar.sync %0, %1;" :: "r"(1 + g), "r"(T) : "memory");
+        else __syncthreads();
+    };
+    // slot layout: element pairs (e, e+1) of a thread are adjacent (one 16-byte access)
+    auto sidx = [&](int sl, int e) { return sl * M + (e >> 1) * (2 * T) + 2 * t + (e & 1); };
+    auto ld1 = [&](int sl, int e) { return slots[sidx(sl, e)]; };
+    auto ld2 = [&](int sl, int e) { return *reinterpret_cast<const float4*>(slots + sidx(sl, e)); };
+    auto st2 = [&](int sl, int e, float2 u, float2 v) {
+        *reinterpret_cast<float4*>(slots + sidx(sl, e)) = make_float4(u.x, u.y, v.x, v.y);
+    };
     __syncthreads();
 
   for (int item = blockIdx.x; item < fb.n_items; item += gridDim.x) {
     const int4 it = fb.items[item];
     const FusedInst& a = fb.inst[it.x];
     const int strip = it.y, p0 = it.z, p1 = it.w;
-    const int nrounds = 3 + 5 * (p1 - p0);
+    const int H = p1 - p0;
+    const int nrounds = 3 + 5 * H;
     const float a2 = a.a2;
+    const int next = fm ? (strip + 1) % fb.n_strips : 0;
+    const int ri_wait_halo = 3 + 5 * (H - 2) + 2;                  // round that prefetches the next strip's copy
+    const int ri_wait_read = 3 + 5 * (H - 1) + 3;                  // first write of the last row
+    auto cta_sync_after = [&](int ri) {
+        if (ri < 3) return ri >= 1 || fm;
+        const int r = (ri - 3) % 5;
+        return r == 0 || r == 1 || r == 4;
+    };
 
     float2 pf[16];
     int fidx = 0;
     {
-        const float2* s0 = reinterpret_cast<const float2*>(fwd_src(a, N, strip, p0, p1, g, 0));
+        const float2* s0 = reinterpret_cast<const float2*>(fwd_src(a, N, strip, p0, p1, g, 0, fm, next));
 #pragma unroll
         for (int nb = 0; nb < 16; nb++) pf[nb] = ldg_stream(s0 + t + T * nb);
     }
 
     float2 x[16];
     for (int ri = 0; ri < nrounds; ri++) {
+        if (fm && (ri == ri_wait_halo || ri == ri_wait_read)) {
+            if (threadIdx.x == 0) wait_flag(fb.flags + 2 * next + (ri == ri_wait_read ? 1 : 0), fb.epoch, fb.err);
+            __syncthreads();
+        }
         const Job j = job_of(a, N, strip, p0, p1, ri, g);
         if (j.kind == J_FWD) {
             // ---------------- stage 1: 16-point DFT of z[t + T n_b] from the prefetched row
 #pragma unroll
             for (int nb = 0; nb < 16; nb++) x[nb] = pf[nb];
+            if (fm && ri == 0 && g < 2) {
+                // publish E1 (g = 0) or E3 (g = 1) of the strip's first row for the previous strip
+                float2* h = reinterpret_cast<float2*>(const_cast<float*>(a.halo) + ((size_t)strip * 7 + g) * N);
+#pragma unroll
+                for (int nb = 0; nb < 16; nb++) h[t + T * nb] = x[nb];
+            }
             {
-                const float2* nsrc = reinterpret_cast<const float2*>(fwd_src(a, N, strip, p0, p1, g, ++fidx));
+                const float2* nsrc = reinterpret_cast<const float2*>(fwd_src(a, N, strip, p0, p1, g, ++fidx, fm, next));
                 if (nsrc) {
 #pragma unroll
                     for (int nb = 0; nb < 16; nb++) pf[nb] = ldg_stream(nsrc + t + T * nb);
@@ -352,7 +414,11 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
         } else if (j.kind == J_INV) {
             // ---------------- inverse: slot -> pre-processing -> stage 3 inverse
 #pragma unroll
-            for (int e = 0; e < 16; e++) x[e] = slots[j.slot * M + e * T + t];
+            for (int e = 0; e < 16; e += 2) {
+                const float4 v = ld2(j.slot, e);
+                x[e] = f2(v.x, v.y);
+                x[e + 1] = f2(v.z, v.w);
+            }
             // pair pre-processing: Z[k] = E + iO, Z[M-k] = conj(E - iO)
 #pragma unroll
             for (int p = 0; p < Q / 2; p++) {
@@ -373,9 +439,8 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
                 // the general formula above paired column 0 with itself wrongly: recompute
                 // column 0 (l = 0 packs (X0, XM); pairs l <-> P3 - l) and column 128 (l <-> P3-1-l)
                 float2 c0[P3], c1[P3];
-                const float2* sl = slots + j.slot * M + t;
 #pragma unroll
-                for (int l = 0; l < P3; l++) { c0[l] = sl[l * T]; c1[l] = sl[(P3 + l) * T]; }
+                for (int l = 0; l < P3; l++) { c0[l] = ld1(j.slot, l); c1[l] = ld1(j.slot, P3 + l); }
                 {
                     const float X0 = c0[0].x, XM = c0[0].y;
                     x[0] = f2((X0 + XM) * inv2M, (X0 - XM) * inv2M);
@@ -422,7 +487,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
                 }
             }
         }
-        __syncthreads();
+        gsync();
         // ---------------- stage 2 (forward) / stage 2 inverse (x is dead here and reused)
         if (j.kind == J_FWD) {
 #pragma unroll
@@ -431,7 +496,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
 #pragma unroll
             for (int l = 0; l < 16; l++) x[l] = xb[ma * 256 + l * 16 + kb];
         }
-        __syncthreads();
+        gsync();
         if (j.kind == J_FWD) {
             Dft<16, false>::run(x);
 #pragma unroll
@@ -445,7 +510,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
 #pragma unroll
             for (int mb = 0; mb < 16; mb++) xb[kb * (T + 1) + ma + P3 * mb] = x[mb];
         }
-        __syncthreads();
+        gsync();
         if (j.kind == J_FWD) {
             // ---------------- stage 3 forward: columns, then pair post-processing
 #pragma unroll
@@ -510,110 +575,100 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
                     }
                 }
             }
-            // ---------------- epilogue: per-mode updates on thread-owned kappa
+            // ---------------- epilogue: per-mode updates on thread-owned kappa (pairs of elements)
             const int p = j.row;
-            float2* Sl = slots + t;
-            float2* dst = Sl + j.slot * M;
+            const int ds = j.slot;
             const float4* sym = a.sym;
             auto kap_of = [&](int e) {
                 const int pp = e / (2 * P3), s = (e / P3) & 1, l = e % P3;
                 return (s == 0 ? cA[pp] : colB(pp)) + 256 * l;
             };
+            auto lo = [](float4 v) { return f2(v.x, v.y); };
+            auto hi = [](float4 v) { return f2(v.z, v.w); };
             switch (j.epi) {
             case X_STORE:
 #pragma unroll
-                for (int e = 0; e < 16; e++) dst[e * T] = x[e];
+                for (int e = 0; e < 16; e += 2) st2(ds, e, x[e], x[e + 1]);
                 break;
             case X_B1: {        // B1 -= a2 (E3(p+1) - E3(p))
-                const float2* u = Sl + sE3(p + 1) * M;
-                const float2* v = Sl + sE3(p) * M;
 #pragma unroll
-                for (int e = 0; e < 16; e++) dst[e * T] = sub(x[e], scl(sub(u[e * T], v[e * T]), a2));
+                for (int e = 0; e < 16; e += 2) {
+                    const float4 u = ld2(sE3(p + 1), e), v = ld2(sE3(p), e);
+                    st2(ds, e, sub(x[e], scl(sub(lo(u), lo(v)), a2)), sub(x[e + 1], scl(sub(hi(u), hi(v)), a2)));
+                }
             } break;
             case X_B2: {        // B2 += S E3(p)
-                const float2* v = Sl + sE3(p) * M;
-                float2 S[16];
+                const float2 e30 = ld1(sE3(p), 0);
 #pragma unroll
-                for (int e = 0; e < 16; e++) { const float4 q = sym[kap_of(e)]; S[e] = f2(q.x, q.y); }
-#pragma unroll
-                for (int e = 0; e < 16; e++)
-                    if (e != 0 || t != 0) dst[e * T] = add(x[e], mul(S[e], v[e * T]));
+                for (int e = 0; e < 16; e += 2) {
+                    const float4 qa = sym[kap_of(e)], qb = sym[kap_of(e + 1)];
+                    const float4 v = ld2(sE3(p), e);
+                    st2(ds, e, add(x[e], mul(f2(qa.x, qa.y), lo(v))), add(x[e + 1], mul(f2(qb.x, qb.y), hi(v))));
+                }
                 if (t == 0) {                     // packed DC/Nyquist element: two real updates
                     const float sd = sym[0].x, sn = sym[M].x;
-                    const float2 e3 = v[0];
-                    dst[0] = f2(x[0].x + sd * e3.x, x[0].y + sn * e3.y);
+                    slots[sidx(ds, 0)] = f2(x[0].x + sd * e30.x, x[0].y + sn * e30.y);
                 }
             } break;
             case X_B3: {        // B3 += a2 (E1(p+1) - E1(p)) - S E2(p)
-                const float2* u = Sl + sE1(p + 1) * M;
-                const float2* v = Sl + sE1(p) * M;
-                const float2* w2 = Sl + sE2 * M;
-                float2 S[16];
 #pragma unroll
-                for (int e = 0; e < 16; e++) { const float4 q = sym[kap_of(e)]; S[e] = f2(q.x, q.y); }
-#pragma unroll
-                for (int e = 0; e < 16; e++)
-                    if (e != 0 || t != 0)
-                        dst[e * T] = sub(add(x[e], scl(sub(u[e * T], v[e * T]), a2)), mul(S[e], w2[e * T]));
+                for (int e = 0; e < 16; e += 2) {
+                    const float4 qa = sym[kap_of(e)], qb = sym[kap_of(e + 1)];
+                    const float4 u = ld2(sE1(p + 1), e), v = ld2(sE1(p), e), w2 = ld2(sE2, e);
+                    st2(ds, e, sub(add(x[e], scl(sub(lo(u), lo(v)), a2)), mul(f2(qa.x, qa.y), lo(w2))),
+                        sub(add(x[e + 1], scl(sub(hi(u), hi(v)), a2)), mul(f2(qb.x, qb.y), hi(w2))));
+                }
                 if (t == 0) {
                     const float sd = sym[0].x, sn = sym[M].x;
-                    const float2 d = sub(u[0], v[0]), e2 = w2[0];
-                    dst[0] = f2(x[0].x + a2 * d.x - sd * e2.x, x[0].y + a2 * d.y - sn * e2.y);
+                    const float2 d = sub(ld1(sE1(p + 1), 0), ld1(sE1(p), 0)), e2 = ld1(sE2, 0);
+                    slots[sidx(ds, 0)] = f2(x[0].x + a2 * d.x - sd * e2.x, x[0].y + a2 * d.y - sn * e2.y);
                 }
             } break;
             case X_J1: {        // E1 += a2 (B3(p) - B3(p-1)) - cj1 j1
-                const float2* u = Sl + sB3(p) * M;
-                const float2* v = Sl + sB3(p - 1) * M;
                 float cj1[16];
 #pragma unroll
                 for (int e = 0; e < 16; e++) cj1[e] = sym[kap_of(e)].z;
-                if (t == 0) cj1[0] = sym[0].z;                    // DC; the Nyquist half below
-                const float cjn = (t == 0) ? sym[M].z : 0.f;
+                const float cjn = (t == 0) ? sym[M].z : cj1[0];   // Nyquist half of the packed element
 #pragma unroll
-                for (int e = 0; e < 16; e++) {
-                    const float2 d = sub(u[e * T], v[e * T]), e1 = dst[e * T];
-                    const float cy = (e == 0 && t == 0) ? cjn : cj1[e];
-                    dst[e * T] = f2(e1.x + a2 * d.x - cj1[e] * x[e].x, e1.y + a2 * d.y - cy * x[e].y);
+                for (int e = 0; e < 16; e += 2) {
+                    const float4 u = ld2(sB3(p), e), v = ld2(sB3(p - 1), e), d0 = ld2(ds, e);
+                    const float2 da = sub(lo(u), lo(v)), db = sub(hi(u), hi(v));
+                    const float cy = (e == 0) ? cjn : cj1[e];
+                    st2(ds, e, f2(d0.x + a2 * da.x - cj1[e] * x[e].x, d0.y + a2 * da.y - cy * x[e].y),
+                        f2(d0.z + a2 * db.x - cj1[e + 1] * x[e + 1].x, d0.w + a2 * db.y - cj1[e + 1] * x[e + 1].y));
                 }
             } break;
             case X_J2: {        // E2 += conj(S) B3(p) - cj j2
-                const float2* u = Sl + sB3(p) * M;
-                float4 q[16];
+                const float2 b30 = ld1(sB3(p), 0), e20 = ld1(ds, 0);
 #pragma unroll
-                for (int e = 0; e < 16; e++) q[e] = sym[kap_of(e)];
-#pragma unroll
-                for (int e = 0; e < 16; e++) {
-                    if (e != 0 || t != 0) {
-                        const float2 sb = mulc(u[e * T], f2(q[e].x, q[e].y)), e2 = dst[e * T];
-                        dst[e * T] = f2(e2.x + sb.x - q[e].w * x[e].x, e2.y + sb.y - q[e].w * x[e].y);
-                    }
+                for (int e = 0; e < 16; e += 2) {
+                    const float4 qa = sym[kap_of(e)], qb = sym[kap_of(e + 1)];
+                    const float4 u = ld2(sB3(p), e), d0 = ld2(ds, e);
+                    const float2 sa = mulc(lo(u), f2(qa.x, qa.y)), sb = mulc(hi(u), f2(qb.x, qb.y));
+                    st2(ds, e, f2(d0.x + sa.x - qa.w * x[e].x, d0.y + sa.y - qa.w * x[e].y),
+                        f2(d0.z + sb.x - qb.w * x[e + 1].x, d0.w + sb.y - qb.w * x[e + 1].y));
                 }
                 if (t == 0) {                     // real symbols at DC and Nyquist
                     const float4 qd = sym[0], qn = sym[M];
-                    const float2 b3 = u[0], e2 = dst[0];
-                    dst[0] = f2(e2.x + qd.x * b3.x - qd.w * x[0].x, e2.y + qn.x * b3.y - qn.w * x[0].y);
+                    slots[sidx(ds, 0)] = f2(e20.x + qd.x * b30.x - qd.w * x[0].x, e20.y + qn.x * b30.y - qn.w * x[0].y);
                 }
             } break;
             default: {          // X_J3: E3 += -conj(S) B2(p) - a2 (B1(p) - B1(p-1)) - cj j3
-                const float2* b2p = Sl + sB2 * M;
-                const float2* u = Sl + sB1(p) * M;
-                const float2* v = Sl + sB1(p - 1) * M;
-                float4 q[16];
+                const float2 b20 = ld1(sB2, 0), e30 = ld1(ds, 0);
+                const float2 dd0 = sub(ld1(sB1(p), 0), ld1(sB1(p - 1), 0));
 #pragma unroll
-                for (int e = 0; e < 16; e++) q[e] = sym[kap_of(e)];
-#pragma unroll
-                for (int e = 0; e < 16; e++) {
-                    if (e != 0 || t != 0) {
-                        const float2 sb = mulc(b2p[e * T], f2(q[e].x, q[e].y));
-                        const float2 d = sub(u[e * T], v[e * T]), e3 = dst[e * T];
-                        dst[e * T] = f2(e3.x - sb.x - a2 * d.x - q[e].w * x[e].x, e3.y - sb.y - a2 * d.y - q[e].w * x[e].y);
-                    }
+                for (int e = 0; e < 16; e += 2) {
+                    const float4 qa = sym[kap_of(e)], qb = sym[kap_of(e + 1)];
+                    const float4 b2 = ld2(sB2, e), u = ld2(sB1(p), e), v = ld2(sB1(p - 1), e), d0 = ld2(ds, e);
+                    const float2 sa = mulc(lo(b2), f2(qa.x, qa.y)), sb = mulc(hi(b2), f2(qb.x, qb.y));
+                    const float2 da = sub(lo(u), lo(v)), db = sub(hi(u), hi(v));
+                    st2(ds, e, f2(d0.x - sa.x - a2 * da.x - qa.w * x[e].x, d0.y - sa.y - a2 * da.y - qa.w * x[e].y),
+                        f2(d0.z - sb.x - a2 * db.x - qb.w * x[e + 1].x, d0.w - sb.y - a2 * db.y - qb.w * x[e + 1].y));
                 }
                 if (t == 0) {
                     const float4 qd = sym[0], qn = sym[M];
-                    const float2 b2 = b2p[0], d = sub(u[0], v[0]), e3 = dst[0];
-                    dst[0] = f2(e3.x - qd.x * b2.x - a2 * d.x - qd.w * x[0].x,
-                                e3.y - qn.x * b2.y - a2 * d.y - qn.w * x[0].y);
+                    slots[sidx(ds, 0)] = f2(e30.x - qd.x * b20.x - a2 * dd0.x - qd.w * x[0].x,
+                                            e30.y - qn.x * b20.y - a2 * dd0.y - qn.w * x[0].y);
                 }
             } break;
             }
@@ -628,7 +683,11 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
 #pragma unroll
             for (int nb = 0; nb < 16; nb++) stg_stream(d + t + T * nb, x[nb]);
         }
-        __syncthreads();
+        if (cta_sync_after(ri)) __syncthreads(); else gsync();
+        if (fm && threadIdx.x == 0) {
+            if (ri == 0) { __threadfence(); st_release(fb.flags + 2 * strip, fb.epoch); }
+            if (ri == 2) st_release(fb.flags + 2 * strip + 1, fb.epoch);
+        }
     }
   }
 }
@@ -692,21 +751,33 @@ cudaError_t fused_occupancy(int n1, int* occ) {
     }
 }
 
-// one step for the work items of a launch: halo copy, then the persistent fused kernel
-cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
-    k_halo<<<dim3(fb.n_items, 7), 256, 0, s>>>(fb, n1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (ev0) { e = cudaEventRecord(ev0, s); if (e != cudaSuccess) return e; }
-    const size_t smem = fused_smem_bytes(n1);
-    const int thr = fused_threads(n1);
-    switch (n1) {
-    case 512: k_fused2d<512><<<grid, thr, smem, s>>>(fb); break;
-    case 1024: k_fused2d<1024><<<grid, thr, smem, s>>>(fb); break;
-    case 2048: k_fused2d<2048><<<grid, thr, smem, s>>>(fb); break;
-    default: k_fused2d<4096><<<grid, thr, smem, s>>>(fb); break;
+template <int N>
+static cudaError_t launch_n(const FusedBatch& fb, int grid, cudaStream_t s) {
+    const size_t smem = fused_smem<N>();
+    if (fb.flags) {          // all CTAs must be resident together: cooperative launch
+        void* args[] = {const_cast<FusedBatch*>(&fb)};
+        return cudaLaunchCooperativeKernel((const void*)k_fused2d<N>, dim3(grid), dim3(Geo<N>::NT), args, smem, s);
     }
-    e = cudaGetLastError();
+    k_fused2d<N><<<grid, Geo<N>::NT, smem, s>>>(fb);
+    return cudaGetLastError();
+}
+
+// one step for the work items of a launch: halo copy (unless the kernel exchanges
+// halos itself), then the persistent fused kernel
+cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+    cudaError_t e;
+    if (!fb.flags) {
+        k_halo<<<dim3(fb.n_items, 7), 256, 0, s>>>(fb, n1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (ev0) { e = cudaEventRecord(ev0, s); if (e != cudaSuccess) return e; }
+    switch (n1) {
+    case 512: e = launch_n<512>(fb, grid, s); break;
+    case 1024: e = launch_n<1024>(fb, grid, s); break;
+    case 2048: e = launch_n<2048>(fb, grid, s); break;
+    default: e = launch_n<4096>(fb, grid, s); break;
+    }
     if (e != cudaSuccess) return e;
     if (ev1) e = cudaEventRecord(ev1, s);
     return e;
@@ -752,6 +823,12 @@ hyb_status fused_set_strips(hyb_grid* g, int n_strips) {
     HYB_CUDA_TRY(fused_occupancy(g->d.n1, &occ));
     HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
     P->grid = P->n_items < sms * occ ? P->n_items : sms * occ;
+    if (P->flags) { cudaFree(P->flags); P->flags = nullptr; }
+    if (P->n_items <= sms * occ) {
+        HYB_CUDA_TRY(cudaMalloc(&P->flags, sizeof(int) * 2 * (size_t)n_strips));
+        HYB_CUDA_TRY(cudaMemset(P->flags, 0, sizeof(int) * 2 * (size_t)n_strips));
+        P->epoch = 0;
+    }
     return HYB_OK;
 }
 
@@ -793,6 +870,9 @@ hyb_status fused_create(hyb_grid* g) {
     HYB_CUDA_TRY(cudaMemcpy(P->items, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
     P->n_items = (int)it.size();
     P->grid = (int)it.size();
+    HYB_CUDA_TRY(cudaMalloc(&P->flags, sizeof(int) * 2 * (size_t)ns));
+    HYB_CUDA_TRY(cudaMemset(P->flags, 0, sizeof(int) * 2 * (size_t)ns));
+    P->epoch = 0;
     return HYB_OK;
 }
 
@@ -801,6 +881,7 @@ void fused_destroy(hyb_grid* g) {
     if (!P) return;
     if (P->items) cudaFree(P->items);
     if (P->halo) cudaFree(P->halo);
+    if (P->flags) cudaFree(P->flags);
     if (P->sym) cudaFree(P->sym);
     if (P->twC) cudaFree(P->twC);
     delete P;
@@ -813,11 +894,16 @@ hyb_status fused_advance(hyb_grid* g, int nsteps) {
     fb.inst[0] = fused_inst(g);
     fb.items = P->items;
     fb.n_items = P->n_items;
-    for (int s = 0; s < nsteps; s++)
+    fb.flags = P->flags;          // in-kernel halo exchange: one co-resident CTA per strip
+    fb.n_strips = P->n_strips;
+    fb.err = g->dflag;
+    for (int s = 0; s < nsteps; s++) {
+        fb.epoch = ++P->epoch;
         HYB_CUDA_TRY(fused_launch(g->d.n1, fb, P->grid, g->stream, g->ev_start, g->ev_stop));
+    }
     return HYB_OK;
 }
 
-int fused_launches_per_step(const hyb_grid*) { return 2; }
+int fused_launches_per_step(const hyb_grid* g) { return (g->fused && g->fused->flags) ? 1 : 2; }
 
 }  // namespace hyb

@@ -23,6 +23,14 @@ struct FusedBatch {
     FusedInst inst[kMaxInst];
     const int4* items;   // {instance, strip, p0, p1}
     int n_items;
+    // single-grid mode with in-kernel halo exchange (flags != nullptr): one
+    // work item per CTA, all CTAs co-resident; halo[s] holds E1, E3 of strip
+    // s's first row, published with flags[2 s] = epoch; flags[2 s + 1] = epoch
+    // says strip s has read the row before it.
+    int* flags;
+    int epoch;
+    int n_strips;
+    int* err;
 };
 
 struct FusedPlan {
@@ -31,6 +39,8 @@ struct FusedPlan {
     int n_items = 0;
     int grid = 0;                 // CTAs of the persistent launch
     float* halo = nullptr;        // [n_strips][7][n1]
+    int* flags = nullptr;         // [2 n_strips] in-kernel halo exchange
+    int epoch = 0;
     float4* sym = nullptr;        // [M + 1] {Re S, Im S, cj1, cj}, S = c dt sigma+
     float2* twM = nullptr;        // [M] W_M^j (the grid's FP32 table)
     float2* twC = nullptr;        // [256] W_N^c

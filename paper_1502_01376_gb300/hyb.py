@@ -107,6 +107,21 @@ def lib():
             L.hyb_correct_current_noalloc.restype = S
             L.hyb_nci_growth.argtypes = [_V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _V, ctypes.c_int, _V, _V, _V]
             L.hyb_nci_growth.restype = S
+            L.hyb_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _V, ctypes.POINTER(_V)]
+            L.hyb_mlp_create.restype = S
+            L.hyb_mlp_num_params.argtypes = [_V]
+            L.hyb_mlp_num_params.restype = ctypes.c_int64
+            for fn in ("hyb_mlp_set_params", "hyb_mlp_get_params"):
+                getattr(L, fn).argtypes = [_V, _V]
+                getattr(L, fn).restype = S
+            L.hyb_mlp_forward.argtypes = [_V, _V, ctypes.c_int64, _V, _V]
+            L.hyb_mlp_forward.restype = S
+            L.hyb_mlp_gradients.argtypes = [_V, _V, _V, ctypes.c_int64, _V, _V, _V]
+            L.hyb_mlp_gradients.restype = S
+            L.hyb_mlp_train_step.argtypes = [_V, _V, _V, ctypes.c_int64, ctypes.c_float, _V, _V]
+            L.hyb_mlp_train_step.restype = S
+            L.hyb_mlp_destroy.argtypes = [_V]
+            L.hyb_mlp_destroy.restype = S
             L.hyb_launches_per_step.argtypes = [_V]
             L.hyb_launches_per_step.restype = ctypes.c_int
             _lib = L
@@ -373,6 +388,75 @@ class Batch:
     def close(self):
         if self.h:
             hyb_batch_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mlp_init_params(n_in: int, width: int, depth: int, seed: int = 0) -> np.ndarray:
+    """Seeded Xavier-uniform weights, zero biases, in the library's layout."""
+    rng = np.random.default_rng(seed)
+    dims = [n_in] + [width] * depth + [1]
+    parts = []
+    for i in range(depth + 1):
+        fi, fo = dims[i], dims[i + 1]
+        lim = np.sqrt(6.0 / (fi + fo))
+        parts.append(rng.uniform(-lim, lim, (fo, fi)).ravel())
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts).astype(np.float32)
+
+
+class MLP:
+    """The NCI surrogate network (forward, backward and Adam in libhyb.so)."""
+
+    def __init__(self, n_in=6, width=256, depth=4, params=None, seed=0):
+        self.n_in, self.width, self.depth = n_in, width, depth
+        p = mlp_init_params(n_in, width, depth, seed) if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        h = _V()
+        _check(lib().hyb_mlp_create(n_in, width, depth, p.ctypes.data_as(_V), ctypes.byref(h)))
+        self.h = h.value
+        self.n_params = lib().hyb_mlp_num_params(_V(self.h))
+        assert self.n_params == p.size
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().hyb_mlp_get_params(_V(self.h), out.ctypes.data_as(_V)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().hyb_mlp_set_params(_V(self.h), p.ctypes.data_as(_V)))
+
+    def forward(self, x):
+        import torch
+        x = x.contiguous()
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        _check(lib().hyb_mlp_forward(_V(self.h), _V(int(x.data_ptr())), x.shape[0], _V(int(y.data_ptr())),
+                                     _V(torch.cuda.current_stream().cuda_stream)))
+        return y
+
+    def gradients(self, x, t):
+        import torch
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        _check(lib().hyb_mlp_gradients(_V(self.h), _V(int(x.data_ptr())), _V(int(t.data_ptr())), x.shape[0],
+                                       g.ctypes.data_as(_V), loss.ctypes.data_as(_V),
+                                       _V(torch.cuda.current_stream().cuda_stream)))
+        return g, float(loss[0])
+
+    def train_step(self, x, t, lr, loss_out=None):
+        import torch
+        _check(lib().hyb_mlp_train_step(_V(self.h), _V(int(x.data_ptr())), _V(int(t.data_ptr())), x.shape[0],
+                                        lr, _V(int(loss_out.data_ptr()) if loss_out is not None else 0),
+                                        _V(torch.cuda.current_stream().cuda_stream)))
+
+    def close(self):
+        if self.h:
+            _check(lib().hyb_mlp_destroy(_V(self.h)))
             self.h = 0
 
     def __del__(self):

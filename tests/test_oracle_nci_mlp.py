@@ -1,0 +1,81 @@
+"""Pins of the NCI dispersion oracle and of the surrogate-network oracle.
+
+NCI (Appendix): with the plasma frequency -> 0 the relation factorises into
+the vacuum hybrid modes [w]^2 = k1^2 + [k]2^2 and the beam resonance; the
+resonance roots move away as sqrt(wp2); the (0,0) modes grow far more slowly
+than the fastest (0,+-1) modes (Sec. 3, Sec. 6).  Quantitative growth rates of
+the paper live in absent figures, and the printed cubic (Eq. asym1) disagrees
+with the full relation in character for some modes (garbled coefficients), so
+parity of the growth values themselves is unpinned by the paper; the cubic is
+used only to seed Newton's method on the full relation.
+
+MLP: the FP64 backward pass equals central finite differences of the loss.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from oracle import nci
+
+
+def test_vacuum_limit_factorises():
+    P = nci.NciParams(dt=0.08, dx1=0.2, dx2=0.2, gamma=50, wp2=0.0)
+    k1, k2 = 7.0, 3.0
+    m = nci.symbols(P, k1, k2, 0, 0)
+    kb2 = math.sin(k2 * 0.1) / 0.1
+    K = math.sqrt(k1 * k1 + kb2 * kb2)
+    w_em = 2.0 / P.dt * math.asin(K * P.dt / 2.0)
+    assert abs(nci.F_of(P, m, w_em)) < 1e-9 * abs(nci.F_of(P, m, w_em * 1.01))
+    w_beam = k1 * P.v0
+    assert abs(nci.F_of(P, m, w_beam)) < 1e-12
+    assert nci.growth(P, k1, k2, 0, 0) == 0.0
+
+
+def test_resonance_roots_scale_with_plasma_frequency():
+    """The resonance roots of the full relation move away from w' = k1' v0 as
+    sqrt(wp2) (two-stream-like coupling of the beam mode)."""
+    k1, k2, nu = 12.0, 8.0, 1
+    sizes = []
+    for wp2 in (1e-2, 1e-4):
+        P = nci.NciParams(dt=0.08, dx1=0.2, dx2=0.2, gamma=50, wp2=wp2)
+        m = nci.symbols(P, k1, k2, 0, nu)
+        w_res = m.k1a * P.v0
+        near = [abs(w - w_res) for w in nci.roots(P, k1, k2, 0, nu) if abs(w - w_res) < 1.0]
+        sizes.append(max(near))
+    assert 0.07 < sizes[1] / sizes[0] < 0.14
+
+
+def test_zero_zero_modes_slower_than_pm1():
+    P = nci.NciParams(dt=0.08, dx1=0.2, dx2=0.2, gamma=50, wp2=100.0)
+    g00 = max(nci.growth_scan(P, 0, 0, 16, 16)[2].max(), 0.0)
+    gpm = max(nci.growth_scan(P, 0, -1, 16, 16)[2].max(), nci.growth_scan(P, 0, 1, 16, 16)[2].max())
+    assert gpm > 0.0
+    assert g00 < 0.5 * gpm
+
+
+@pytest.mark.parametrize("width,depth", [(8, 2), (16, 3)])
+def test_mlp_oracle_backprop_equals_finite_differences(width, depth):
+    rng = np.random.default_rng(width)
+    n_in, B = 6, 7
+    npar = omlp.num_params(n_in, width, depth)
+    p = rng.standard_normal(npar) * 0.3
+    x = rng.standard_normal((B, n_in))
+    t = rng.standard_normal(B)
+    g, loss = omlp.gradients(p, x, t, n_in, width, depth, rnd=False)
+    h = 1e-6
+    for i in rng.choice(npar, 25, replace=False):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        lp = np.mean((omlp.forward(pp, x, n_in, width, depth, rnd=False)[0] - t) ** 2)
+        lm = np.mean((omlp.forward(pm, x, n_in, width, depth, rnd=False)[0] - t) ** 2)
+        assert abs((lp - lm) / (2 * h) - g[i]) < 1e-7 * max(1.0, abs(g[i]))
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    # 1 + 2^-8 lies halfway between two BF16 values: ties go to the even mantissa (1.0)
+    assert omlp.bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert omlp.bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+    assert omlp.bf16(np.array([-3.0]))[0] == -3.0
