@@ -60,7 +60,7 @@ typedef enum {
 } hyb_status;
 
 typedef struct {
-    int dims;             /* 2 or 3 */
+    int dims;             /* 2, 3, or 20 for quasi-3D (one azimuthal mode; see azimuthal_m) */
     int n1, n2, n3;       /* grid points along x1 (FFT, even, power of two), x2, x3 (FD); n3 ignored in 2D */
     double dx1, dx2, dx3; /* cell sizes */
     double dt;            /* time step; must satisfy the Courant limit of Sec. 2.2 */
@@ -74,9 +74,16 @@ typedef struct {
     double ampere;        /* coefficient of j in Ampere's law; 0 selects 4 pi */
     int path;             /* 0: fastest available; 1: three-pass (FFT, update, inverse FFT);
                              2: fused single-pass (precision 32, dims 2, n1 in 512..4096) */
+    int azimuthal_m;      /* dims 20 only: azimuthal mode number m >= 0.  The grid is then
+                             (z, r) = (x1, x2) with n1 = nz, n2 = nr, dx1 = dz, dx2 = dr, a
+                             perfectly conducting wall at r = n2 dx2, the axis at r = 0, and
+                             every field and current is COMPLEX (interleaved re, im) of the
+                             grid's precision: the amplitude of exp(i m phi) (Sec. 5). */
 } hyb_grid_desc;
 
-/* Courant limit dt_max = 2 / sqrt(pi^2/dx1^2 + 4/dx2^2 [+ 4/dx3^2]) of Sec. 2.2. */
+/* Courant limit dt_max = 2 / sqrt(pi^2/dx1^2 + 4/dx2^2 [+ 4/dx3^2]) of Sec. 2.2;
+ * for a quasi-3D mode m, 4/dx2^2 is replaced by (4 m^2 + 6)/dx2^2, a bound on
+ * the largest eigenvalue of the cylindrical radial operator (at the axis). */
 HYB_API double hyb_courant_limit(const hyb_grid_desc* desc);
 
 /* Validates desc (sizes, Courant limit -> HYB_ECOURANT, precision/path

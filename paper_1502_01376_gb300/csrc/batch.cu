@@ -84,7 +84,8 @@ static hyb_status enqueue_step(hyb_batch* b, cudaStream_t s) {
         hyb_grid* g = b->grids[i];
         cudaStream_t keep = g->stream;
         g->stream = s;
-        hyb_status st = g->d.precision == 32 ? generic_advance<float>(g, 1) : generic_advance<double>(g, 1);
+        hyb_status st = g->d.dims == 20 ? quasi3d_advance(g, 1)
+                       : g->d.precision == 32 ? generic_advance<float>(g, 1) : generic_advance<double>(g, 1);
         g->stream = keep;
         if (st != HYB_OK) return st;
     }

@@ -13,25 +13,6 @@ namespace hyb {
 
 constexpr int kRowThreads = 256;
 
-template <typename C>
-__device__ __forceinline__ void stockham_radix2(C*& src, C*& dst, int M, const C* __restrict__ twM, bool inverse) {
-    // natural-order in, natural-order out; one __syncthreads per stage
-    for (int Ns = 1; Ns < M; Ns <<= 1) {
-        const int tstride = M / (2 * Ns);
-        for (int j = threadIdx.x; j < (M >> 1); j += blockDim.x) {
-            const int k = j & (Ns - 1);
-            C a = src[j], b = src[j + (M >> 1)];
-            C w = twM[k * tstride];
-            b = inverse ? cmulc(b, w) : cmul(b, w);
-            const int o = ((j - k) << 1) + k;
-            dst[o] = cadd(a, b);
-            dst[o + Ns] = csub(a, b);
-        }
-        __syncthreads();
-        C* t = src; src = dst; dst = t;
-    }
-}
-
 struct RowPtrs { const void* p[9]; };
 struct RowPtrsW { void* p[9]; };
 

@@ -31,8 +31,13 @@ static const double kPi = 3.14159265358979323846;
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// Sec. 2.2: dt <= 2 / sqrt(pi^2/dx1^2 + 4/dx2^2 [+ 4/dx3^2]).  Quasi-3D mode m:
+// the (i m / r) terms raise the radial operator's largest eigenvalue to at
+// most (4 m^2 + 6)/dr^2 (it sits at the axis), so 4/dx2^2 becomes (4 m^2 + 6)/dx2^2.
 static double courant_limit(const hyb_grid_desc& d) {
-    double s = kPi * kPi / (d.dx1 * d.dx1) + 4.0 / (d.dx2 * d.dx2);
+    double s = kPi * kPi / (d.dx1 * d.dx1);
+    if (d.dims == 20) s += (4.0 * d.azimuthal_m * d.azimuthal_m + 6.0) / (d.dx2 * d.dx2);
+    else s += 4.0 / (d.dx2 * d.dx2);
     if (d.dims == 3) s += 4.0 / (d.dx3 * d.dx3);
     return 2.0 / sqrt(s);
 }
@@ -150,8 +155,9 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
     if (!desc || !out) { set_error("hyb_create_grid: null argument"); return HYB_EINVAL; }
     *out = nullptr;
     hyb_grid_desc d = *desc;
-    if (d.dims != 2 && d.dims != 3) { set_error("dims must be 2 or 3 (got %d)", d.dims); return HYB_EINVAL; }
-    if (d.dims == 2) { d.n3 = 1; d.dx3 = d.dx3 > 0 ? d.dx3 : 1.0; }
+    if (d.dims != 2 && d.dims != 3 && d.dims != 20) { set_error("dims must be 2, 3 or 20 (got %d)", d.dims); return HYB_EINVAL; }
+    if (d.dims != 3) { d.n3 = 1; d.dx3 = d.dx3 > 0 ? d.dx3 : 1.0; }
+    if (d.dims == 20 && (d.azimuthal_m < 0 || d.azimuthal_m > 64)) { set_error("azimuthal_m must be in [0, 64]"); return HYB_EINVAL; }
     if (!is_pow2(d.n1) || d.n1 < 8 || d.n1 > 8192) { set_error("n1 must be a power of two in [8, 8192] (got %d)", d.n1); return HYB_EINVAL; }
     if (d.n2 < 2 || (d.dims == 3 && d.n3 < 2)) { set_error("n2 (and n3 in 3D) must be >= 2"); return HYB_EINVAL; }
     if ((int64_t)d.n2 * d.n3 > (int64_t)1 << 30) { set_error("too many rows"); return HYB_EINVAL; }
@@ -164,7 +170,8 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
         return HYB_ECOURANT;
     }
     if (d.path < 0 || d.path > 2) { set_error("path must be 0, 1 or 2"); return HYB_EINVAL; }
-    const bool fused_ok = fused_supported(d);
+    const bool fused_ok = d.dims != 20 && fused_supported(d);
+    if (d.dims == 20 && d.path == 2) { set_error("quasi-3D grids run the three-pass path"); return HYB_EINVAL; }
     if (d.path == 2 && !fused_ok) {
         set_error("fused path needs precision 32, dims 2, n1 in [512, 4096] and n2 >= 4");
         return HYB_EINVAL;
@@ -188,7 +195,8 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
         if (ce == cudaSuccess) ce = cudaMemset(g->dflag, 0, sizeof(int));
         if (ce != cudaSuccess) st = cuda_fail(ce, "cudaMalloc(accumulators)");
     }
-    if (st == HYB_OK) {
+    if (st == HYB_OK && d.dims == 20) st = quasi3d_create(g);
+    if (st == HYB_OK && d.dims != 20) {
         const size_t csz = d.precision == 32 ? sizeof(float2) : sizeof(double2);
         const int nf = (g->path == 1) ? 9 : 3;
         g->spec_bytes = (size_t)nf * g->rows * g->nk * csz;
@@ -226,6 +234,7 @@ hyb_status hyb_deposit(hyb_grid* g, const int32_t* cell, const void* off_old, co
     if (!g->bound) { set_error("hyb_deposit: fields not bound"); return HYB_ESTATE; }
     if (np < 0 || shape_order < 1 || shape_order > 3) { set_error("hyb_deposit: bad np or shape_order"); return HYB_EINVAL; }
     if (np > 0 && (!cell || !off_old || !off_new || !q)) { set_error("hyb_deposit: null particle array"); return HYB_EINVAL; }
+    if (g->d.dims == 20) { set_error("hyb_deposit: quasi-3D grids take their current from the caller"); return HYB_EINVAL; }
     if (g->d.precision == 32)
         return deposit<float>(g, cell, (const float*)off_old, (const float*)off_new, (const float*)v3, (const float*)q, np, shape_order);
     return deposit<double>(g, cell, (const double*)off_old, (const double*)off_new, (const double*)v3, (const double*)q, np, shape_order);
@@ -234,12 +243,14 @@ hyb_status hyb_deposit(hyb_grid* g, const int32_t* cell, const void* off_old, co
 hyb_status hyb_correct_current(hyb_grid* g) {
     if (!g) { set_error("null grid"); return HYB_EINVAL; }
     if (!g->bound) { set_error("fields not bound"); return HYB_ESTATE; }
+    if (g->d.dims == 20) { set_error("quasi-3D grids apply the correction inside hyb_advance only"); return HYB_EINVAL; }
     return g->d.precision == 32 ? generic_process_current<float>(g, true, false) : generic_process_current<double>(g, true, false);
 }
 
 hyb_status hyb_filter(hyb_grid* g) {
     if (!g) { set_error("null grid"); return HYB_EINVAL; }
     if (!g->bound) { set_error("fields not bound"); return HYB_ESTATE; }
+    if (g->d.dims == 20) { set_error("quasi-3D grids apply the filter inside hyb_advance only"); return HYB_EINVAL; }
     return g->d.precision == 32 ? generic_process_current<float>(g, false, true) : generic_process_current<double>(g, false, true);
 }
 
@@ -248,6 +259,7 @@ hyb_status hyb_advance(hyb_grid* g, int nsteps) {
     if (!g->bound) { set_error("hyb_advance: fields not bound"); return HYB_ESTATE; }
     if (nsteps < 0) { set_error("nsteps < 0"); return HYB_EINVAL; }
     if (nsteps == 0) return HYB_OK;
+    if (g->d.dims == 20) return quasi3d_advance(g, nsteps);
     if (g->path == 2) return fused_advance(g, nsteps);
     return g->d.precision == 32 ? generic_advance<float>(g, nsteps) : generic_advance<double>(g, nsteps);
 }
@@ -255,7 +267,7 @@ hyb_status hyb_advance(hyb_grid* g, int nsteps) {
 hyb_status hyb_advance_host(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3], int nsteps) {
     if (!g || !E || !B || !J) { set_error("hyb_advance_host: null argument"); return HYB_EINVAL; }
     if (!g->bound) { set_error("hyb_advance_host: device fields not bound"); return HYB_ESTATE; }
-    const size_t bytes = (size_t)g->cells * (g->d.precision == 32 ? 4 : 8);
+    const size_t bytes = (size_t)g->cells * (g->d.precision == 32 ? 4 : 8) * (g->d.dims == 20 ? 2 : 1);
     for (int c = 0; c < 3; c++) {
         HYB_CUDA_TRY(cudaMemcpyAsync(g->E[c], E[c], bytes, cudaMemcpyHostToDevice, g->stream));
         HYB_CUDA_TRY(cudaMemcpyAsync(g->B[c], B[c], bytes, cudaMemcpyHostToDevice, g->stream));
@@ -274,6 +286,7 @@ hyb_status hyb_advance_host(hyb_grid* g, void* const E[3], void* const B[3], voi
 hyb_status hyb_diag(hyb_grid* g, double out[9]) {
     if (!g || !out) { set_error("null argument"); return HYB_EINVAL; }
     if (!g->bound) { set_error("fields not bound"); return HYB_ESTATE; }
+    if (g->d.dims == 20) { set_error("hyb_diag: not available for quasi-3D grids"); return HYB_EINVAL; }
     return g->d.precision == 32 ? diag<float>(g, out) : diag<double>(g, out);
 }
 
@@ -292,6 +305,7 @@ hyb_status hyb_destroy_grid(hyb_grid* g) {
     if (!g) return HYB_OK;
     if (g->stream) cudaStreamSynchronize(g->stream); else cudaDeviceSynchronize();
     if (g->fused) fused_destroy(g);
+    if (g->qtab) quasi3d_destroy(g);
     free_tables_f(g->tf);
     free_tables_d(g->td);
     if (g->spec) cudaFree(g->spec);

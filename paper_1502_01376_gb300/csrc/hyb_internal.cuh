@@ -24,6 +24,27 @@ template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) { re
 template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mkc<C>(a.x, -a.y); }
 template <typename C> __host__ __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mkc<C>(a.x * s, a.y * s); }
 
+// ---------------------------------------------------------------- shared-memory radix-2 Stockham FFT
+template <typename C>
+__device__ __forceinline__ void stockham_radix2(C*& src, C*& dst, int M, const C* __restrict__ twM, bool inverse) {
+    // natural-order in, natural-order out; one __syncthreads per stage
+    for (int Ns = 1; Ns < M; Ns <<= 1) {
+        const int tstride = M / (2 * Ns);
+        for (int j = threadIdx.x; j < (M >> 1); j += blockDim.x) {
+            const int k = j & (Ns - 1);
+            C a = src[j], b = src[j + (M >> 1)];
+            C w = twM[k * tstride];
+            b = inverse ? cmulc(b, w) : cmul(b, w);
+            const int o = ((j - k) << 1) + k;
+            dst[o] = cadd(a, b);
+            dst[o + Ns] = csub(a, b);
+        }
+        __syncthreads();
+        C* t = src; src = dst; dst = t;
+    }
+}
+
+
 // ---------------------------------------------------------------- tables
 // Per-mode tables for kappa = 0..n1/2, computed in FP64 on the host and rounded once.
 template <typename T>
@@ -67,6 +88,7 @@ struct hyb_grid {
     double* diag_acc = nullptr;    // 16 FP64 accumulators
     int* dflag = nullptr;          // device data-error flag
     hyb::FusedPlan* fused = nullptr;
+    void* qtab = nullptr;          // quasi-3D per-mode tables (device)
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional kernel timing events
 };
 
@@ -99,6 +121,11 @@ hyb_status fused_create(hyb_grid* g);
 void fused_destroy(hyb_grid* g);
 hyb_status fused_advance(hyb_grid* g, int nsteps);
 int fused_launches_per_step(const hyb_grid* g);
+
+// quasi-3D azimuthal-mode path (quasi3d.cu)
+hyb_status quasi3d_create(hyb_grid* g);
+void quasi3d_destroy(hyb_grid* g);
+hyb_status quasi3d_advance(hyb_grid* g, int nsteps);
 
 // deposit (deposit.cu)
 template <typename T>

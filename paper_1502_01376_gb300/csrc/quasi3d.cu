@@ -1,0 +1,223 @@
+// quasi3d.cu -- hybrid solver for one azimuthal mode m of the quasi-3D
+// geometry (Sec. 5): complex fields F_m(r, z) (the amplitude of exp(i m phi)),
+// z (x1) spectral with the 2D solver's sigma+/- symbols and the j_z
+// correction, r (x2) by the Yee differences of the cylindrical curl
+//   (curl A)_r = (i m / r) A_z - dA_phi/dz,  (curl A)_phi = dA_r/dz - dA_z/dr,
+//   (curl A)_z = (1/r) d(r A_phi)/dr - (i m / r) A_r,
+// on the 2D staggering with x1 = z, x2 = r (E_z, E_r, E_phi, B_z, B_r, B_phi
+// in the E1..B3 slots), r_j = j dr.  Axis: E_z(0) from the circulation of
+// B_phi round a disc of radius dr/2 for m = 0, else 0; E_phi(0), B_r(0) only
+// for m = 1 (with dB_z/dr(0) = 2 B_z(dr/2)/dr and (i m/r) E_z -> i m E_z(dr)/dr),
+// else 0.  A perfect conductor at r = n_r dr.  Three passes per step: complex
+// FFT along z of the nine arrays, Faraday then Ampere per (r, k_z), inverse FFT.
+#include <math.h>
+
+#include <vector>
+
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+template <typename T>
+struct QTab {
+    cplx<T> sp;   // sigma+ = i k e^{+i k dz/2}
+    cplx<T> sm;   // sigma- = i k e^{-i k dz/2}
+    T cjz;        // ampere dt F corr
+    T cj;         // ampere dt F
+};
+
+template <typename T>
+struct QPlan {
+    QTab<T>* tab = nullptr;
+    cplx<T>* tw = nullptr;    // W_nz^j, j < nz
+    cplx<T>* spec = nullptr;  // [9][nr][nz]
+};
+
+struct QPtrs { void* p[9]; };
+
+constexpr int kQThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kQThreads) k_qfft_fwd(QPtrs in, cplx<T>* __restrict__ spec, int nz, int nr,
+                                                       const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* src = reinterpret_cast<C*>(smem_raw);
+    C* dst = src + nz;
+    const int row = blockIdx.x, f = blockIdx.y;
+    const C* x = reinterpret_cast<const C*>(in.p[f]) + (int64_t)row * nz;
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) src[j] = x[j];
+    __syncthreads();
+    stockham_radix2(src, dst, nz, tw, false);
+    C* X = spec + ((int64_t)f * nr + row) * nz;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) X[k] = src[k];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kQThreads) k_qfft_inv(const cplx<T>* __restrict__ spec, QPtrs out, int nz, int nr,
+                                                       const cplx<T>* __restrict__ tw) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* src = reinterpret_cast<C*>(smem_raw);
+    C* dst = src + nz;
+    const int row = blockIdx.x, f = blockIdx.y;
+    const C* X = spec + ((int64_t)f * nr + row) * nz;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) src[k] = X[k];
+    __syncthreads();
+    stockham_radix2(src, dst, nz, tw, true);
+    C* x = reinterpret_cast<C*>(out.p[f]) + (int64_t)row * nz;
+    const T inv = (T)1 / (T)nz;
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) x[j] = cscale(src[j], inv);
+}
+
+// i m / r times a
+template <typename C>
+__device__ __forceinline__ C imr(C a, decltype(C::x) m_over_r) { return mkc<C>(-m_over_r * a.y, m_over_r * a.x); }
+
+template <typename T>
+__global__ void __launch_bounds__(kQThreads) k_qfaraday(cplx<T>* __restrict__ spec, int nz, int nr, const QTab<T>* __restrict__ tab,
+                                                       T dt, T dr, int m) {
+    using C = cplx<T>;
+    const int j = blockIdx.x;
+    const int64_t fs = (int64_t)nr * nz;
+    C* Ez = spec; C* Er = spec + fs; C* Ep = spec + 2 * fs;
+    C* Bz = spec + 3 * fs; C* Br = spec + 4 * fs; C* Bp = spec + 5 * fs;
+    const T ri = (T)j * dr, rh = ((T)j + (T)0.5) * dr, rup = (T)(j + 1) * dr;
+    const T mT = (T)m;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        const int64_t i = (int64_t)j * nz + k, iu = i + nz;
+        const C sp = tab[k].sp;
+        const C ez = Ez[i], er = Er[i], ep = Ep[i];
+        const C ezu = (j + 1 < nr) ? Ez[iu] : mkc<C>((T)0, (T)0);       // wall: tangential E = 0
+        const C epu = (j + 1 < nr) ? Ep[iu] : mkc<C>((T)0, (T)0);
+        C cr;
+        if (j > 0) cr = csub(imr(ez, mT / ri), cmul(sp, ep));
+        else if (m == 1) cr = csub(imr(Ez[nz + k], mT / dr), cmul(sp, ep));
+        else cr = mkc<C>((T)0, (T)0);
+        const C cp = csub(cmul(sp, er), cscale(csub(ezu, ez), (T)1 / dr));
+        const C cz = csub(cscale(csub(cscale(epu, rup), cscale(ep, ri)), (T)1 / (rh * dr)), imr(er, mT / rh));
+        Bz[i] = csub(Bz[i], cscale(cz, dt));
+        Br[i] = (j == 0 && m != 1) ? mkc<C>((T)0, (T)0) : csub(Br[i], cscale(cr, dt));
+        Bp[i] = csub(Bp[i], cscale(cp, dt));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kQThreads) k_qampere(cplx<T>* __restrict__ spec, int nz, int nr, const QTab<T>* __restrict__ tab,
+                                                      T dt, T dr, int m) {
+    using C = cplx<T>;
+    const int j = blockIdx.x;
+    const int64_t fs = (int64_t)nr * nz;
+    C* Ez = spec; C* Er = spec + fs; C* Ep = spec + 2 * fs;
+    const C* Bz = spec + 3 * fs; const C* Br = spec + 4 * fs; const C* Bp = spec + 5 * fs;
+    const C* Jz = spec + 6 * fs; const C* Jr = spec + 7 * fs; const C* Jp = spec + 8 * fs;
+    const T ri = (T)j * dr, rh = ((T)j + (T)0.5) * dr, rd = ((T)j - (T)0.5) * dr;
+    const T mT = (T)m;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+        const int64_t i = (int64_t)j * nz + k, idn = i - nz;
+        const QTab<T> q = tab[k];
+        const C bz = Bz[i], br = Br[i], bp = Bp[i];
+        const C cr = csub(imr(bz, mT / rh), cmul(q.sm, bp));
+        C cp, cz;
+        if (j > 0) {
+            cp = csub(cmul(q.sm, br), cscale(csub(bz, Bz[idn]), (T)1 / dr));
+            cz = csub(cscale(csub(cscale(bp, rh), cscale(Bp[idn], rd)), (T)1 / (ri * dr)), imr(br, mT / ri));
+        } else {
+            cp = (m == 1) ? csub(cmul(q.sm, br), cscale(bz, (T)2 / dr)) : mkc<C>((T)0, (T)0);
+            cz = (m == 0) ? cscale(bp, (T)4 / dr) : mkc<C>((T)0, (T)0);
+        }
+        C er = csub(cadd(Er[i], cscale(cr, dt)), cscale(Jr[i], q.cj));
+        C ep = csub(cadd(Ep[i], cscale(cp, dt)), cscale(Jp[i], q.cj));
+        C ez = csub(cadd(Ez[i], cscale(cz, dt)), cscale(Jz[i], q.cjz));
+        if (j == 0 && m != 0) ez = mkc<C>((T)0, (T)0);
+        if (j == 0 && m != 1) ep = mkc<C>((T)0, (T)0);
+        Er[i] = er;
+        Ep[i] = ep;
+        Ez[i] = ez;
+    }
+}
+
+template <typename T>
+static hyb_status create_t(hyb_grid* g) {
+    using C = cplx<T>;
+    const hyb_grid_desc& d = g->d;
+    const int nz = d.n1, nr = d.n2;
+    QPlan<T>* P = new QPlan<T>();
+    g->qtab = P;
+    const double pi = 3.14159265358979323846;
+    std::vector<QTab<T>> tab(nz);
+    const bool filt_on = d.filt_kc > 0.0 && d.filt_kc < 1.0;
+    for (int k = 0; k < nz; k++) {
+        const int kap = (k <= nz / 2) ? k : k - nz;                  // Nyquist taken as +nz/2
+        const double kk = 2.0 * pi * kap / (nz * d.dx1);
+        const double ph = 0.5 * kk * d.dx1;
+        tab[k].sp = mkc<C>((T)(-kk * sin(ph)), (T)(kk * cos(ph)));
+        tab[k].sm = mkc<C>((T)(kk * sin(ph)), (T)(kk * cos(ph)));
+        const double corr = (kap == 0 || !d.correct_j1) ? 1.0 : sin(ph) / ph;
+        double F = 1.0;
+        if (filt_on) {
+            const double kn = pi / d.dx1, a = fabs(kk), kc = d.filt_kc * kn, w = d.filt_w * kn;
+            if (w <= 0.0) F = a <= kc ? 1.0 : 0.0;
+            else if (a <= kc - 0.5 * w) F = 1.0;
+            else if (a >= kc + 0.5 * w) F = 0.0;
+            else { const double c = cos(0.5 * pi * (a - kc + 0.5 * w) / w); F = c * c; }
+        }
+        tab[k].cjz = (T)(d.ampere * d.dt * F * corr);
+        tab[k].cj = (T)(d.ampere * d.dt * F);
+    }
+    std::vector<C> tw(nz);
+    for (int j = 0; j < nz; j++) { const double a = -2.0 * pi * j / nz; tw[j] = mkc<C>((T)cos(a), (T)sin(a)); }
+    HYB_CUDA_TRY(cudaMalloc(&P->tab, sizeof(QTab<T>) * nz));
+    HYB_CUDA_TRY(cudaMemcpy(P->tab, tab.data(), sizeof(QTab<T>) * nz, cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMalloc(&P->tw, sizeof(C) * nz));
+    HYB_CUDA_TRY(cudaMemcpy(P->tw, tw.data(), sizeof(C) * nz, cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMalloc(&P->spec, sizeof(C) * 9 * (size_t)nr * nz));
+    const size_t smem = sizeof(C) * 2 * (size_t)nz;
+    HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return HYB_OK;
+}
+
+template <typename T>
+static hyb_status advance_t(hyb_grid* g, int nsteps) {
+    using C = cplx<T>;
+    QPlan<T>* P = reinterpret_cast<QPlan<T>*>(g->qtab);
+    const hyb_grid_desc& d = g->d;
+    const int nz = d.n1, nr = d.n2;
+    const size_t smem = sizeof(C) * 2 * (size_t)nz;
+    QPtrs fin{}, fout{};
+    for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; fin.p[6 + c] = g->J[c]; }
+    for (int c = 0; c < 3; c++) { fout.p[c] = g->E[c]; fout.p[3 + c] = g->B[c]; }
+    for (int s = 0; s < nsteps; s++) {
+        if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
+        k_qfft_fwd<T><<<dim3(nr, 9), kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, P->tw);
+        k_qfaraday<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
+        k_qampere<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
+        k_qfft_inv<T><<<dim3(nr, 6), kQThreads, smem, g->stream>>>(P->spec, fout, nz, nr, P->tw);
+        HYB_CUDA_TRY(cudaGetLastError());
+        if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
+    }
+    return HYB_OK;
+}
+
+hyb_status quasi3d_create(hyb_grid* g) {
+    return g->d.precision == 32 ? create_t<float>(g) : create_t<double>(g);
+}
+
+void quasi3d_destroy(hyb_grid* g) {
+    if (!g->qtab) return;
+    if (g->d.precision == 32) {
+        QPlan<float>* P = reinterpret_cast<QPlan<float>*>(g->qtab);
+        cudaFree(P->tab); cudaFree(P->tw); cudaFree(P->spec); delete P;
+    } else {
+        QPlan<double>* P = reinterpret_cast<QPlan<double>*>(g->qtab);
+        cudaFree(P->tab); cudaFree(P->tw); cudaFree(P->spec); delete P;
+    }
+    g->qtab = nullptr;
+}
+
+hyb_status quasi3d_advance(hyb_grid* g, int nsteps) {
+    return g->d.precision == 32 ? advance_t<float>(g, nsteps) : advance_t<double>(g, nsteps);
+}
+
+}  // namespace hyb

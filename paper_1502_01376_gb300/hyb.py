@@ -44,6 +44,7 @@ class GridDesc(ctypes.Structure):
         ("yee_mode", ctypes.c_int),
         ("ampere", ctypes.c_double),
         ("path", ctypes.c_int),
+        ("azimuthal_m", ctypes.c_int),
     ]
 
 
@@ -135,9 +136,9 @@ def _check(st: int):
 
 def make_desc(dims=2, n1=128, n2=64, n3=1, dx1=0.1, dx2=0.1, dx3=0.1, dt=0.05, precision=64,
               correct_j1=True, filt_kc=0.0, filt_w=0.0, kmod_l=0.0, kmod_u=0.0, kmod_max=0.0,
-              yee_mode=False, ampere=0.0, path=0) -> GridDesc:
+              yee_mode=False, ampere=0.0, path=0, azimuthal_m=0) -> GridDesc:
     return GridDesc(dims, n1, n2, n3, dx1, dx2, dx3, dt, precision, int(bool(correct_j1)), filt_kc, filt_w,
-                    kmod_l, kmod_u, kmod_max, int(bool(yee_mode)), ampere, path)
+                    kmod_l, kmod_u, kmod_max, int(bool(yee_mode)), ampere, path, azimuthal_m)
 
 
 def desc_from_workload(w, **over) -> GridDesc:
@@ -290,7 +291,10 @@ class Grid:
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.h = hyb_create_grid(desc, self.stream.cuda_stream)
-        self.dtype = torch.float32 if desc.precision == 32 else torch.float64
+        if desc.dims == 20:
+            self.dtype = torch.complex64 if desc.precision == 32 else torch.complex128
+        else:
+            self.dtype = torch.float32 if desc.precision == 32 else torch.float64
         self.tensors = None
 
     @property

@@ -50,3 +50,19 @@ def test_axis_regularity_kept():
     J = [np.zeros((10, 16), complex) for _ in range(3)]
     q.step(g, E, B, J, 3)
     assert np.all(E[0][0] == 0) and np.all(E[2][0] == 0) and np.all(B[1][0] == 0)
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3, 5])
+def test_quasi3d_courant_bound(m):
+    """The radial operator's largest eigenvalue sits at the axis and is at most
+    (4 m^2 + 6)/dr^2: just below dt = 2/sqrt(pi^2/dz^2 + (4 m^2 + 6)/dr^2) every
+    mode is neutral; the 2D limit (4/dr^2) is not stable for m >= 1."""
+    dz, dr, nr, nz = 0.2, 0.15, 10, 8
+    dt = 0.995 * 2 / np.sqrt(np.pi ** 2 / dz ** 2 + (4 * m * m + 6) / dr ** 2)
+    g = q.QGrid(nz=nz, nr=nr, dz=dz, dr=dr, dt=dt, m=m)
+    worst = max(np.max(np.abs(np.linalg.eigvals(q.transfer_matrix(g, k)))) for k in range(nz))
+    assert worst < 1 + 1e-12
+    if m >= 1:
+        g2 = q.QGrid(nz=nz, nr=nr, dz=dz, dr=dr, dt=0.95 * 2 / np.sqrt(np.pi ** 2 / dz ** 2 + 4 / dr ** 2), m=m)
+        worst2 = max(np.max(np.abs(np.linalg.eigvals(q.transfer_matrix(g2, k)))) for k in range(nz))
+        assert worst2 > 1.01
