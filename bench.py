@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and fp64 comparison")
     ap.add_argument("--quick", action="store_true",
                     help="profiling mode: random band-limited J instead of the particle deposit, no extras")
+    ap.add_argument("--workload", default="drift_plasma",
+                    choices=["drift_plasma", "batched", "3d", "vacuum_beam"],
+                    help="drift_plasma (default, the headline): 2D 4096 x 1024 FP32; batched: 16 uneven 2D grids "
+                         "+ quasi-3D modes m = 0, 1, 2 (2048 x 512 complex) in one CUDA-graph step; 3d: 1024 x 256 x 256 "
+                         "FP32; vacuum_beam: 2D 128 x 64 FP64")
     return ap.parse_args()
 
 
@@ -145,6 +150,17 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None}
 
 
+def replica_aggregate(ms, kms, cells, world, device):
+    """Max-over-ranks step and kernel times of independent replicas, and the
+    whole-job value world * cells / max step time (cell-steps/s)."""
+    import torch
+    if world > 1:
+        t = torch.tensor([ms, kms], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, kms = float(t[0]), float(t[1])
+    return ms, kms, world * cells / (ms / 1e3)
+
+
 def cpu_baseline_sample(workload, budget_s=15.0):
     """The oracle as it stands on a bounded sample of the workload: the full
     4096-point x1 rows on a 4096 x R periodic strip, timed on the host cores."""
@@ -204,10 +220,131 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(step_fn, K, W, stream, flush, sampler):
+    """W untimed steps, then K steps each bracketed by CUDA events on `stream`,
+    with an L2 flush (256 MB write) before every timed step."""
+    import torch
+    for _ in range(W):
+        step_fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if sampler:
+        sampler.mark(True)
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step_fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark(False)
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def run_other(args):
+    """Measurement lines for the non-headline configurations (same JSON keys)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_1502_01376_gb300 import build, hyb, workloads as wl
+    build.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.5)
+    peak, src = peaks()
+    rng = np.random.default_rng(3)
+    extra = {}
+    if args.workload == "batched":
+        descs, bufs, cells, alg_bytes = [], [], 0, 0
+        sizes = [(int(rng.choice([512, 1024, 2048, 4096])), int(rng.choice([128, 256, 512, 1024]))) for _ in range(16)]
+        for i, (n1, n2) in enumerate(sizes):
+            w = wl.Workload(f"b{i}", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2,
+                            seed=100 + i)
+            descs.append(hyb.desc_from_workload(w))
+            E0, B0 = wl.band_limited_fields(w)
+            J0, _ = wl.band_limited_fields(w.scaled(seed=w.seed + 50))
+            mk = lambda arrs: [torch.from_numpy(a.astype(np.float32)).to(dev) for a in arrs]
+            bufs.append((mk(E0), mk(B0), mk(J0)))
+            cells += n1 * n2
+            alg_bytes += 60 * n1 * n2
+        nz, nr = 2048, 512
+        for m in (0, 1, 2):
+            dt = 0.9 * 2 / np.sqrt(np.pi ** 2 / 0.2 ** 2 + (4 * m * m + 6) / 0.2 ** 2)
+            descs.append(hyb.make_desc(dims=20, n1=nz, n2=nr, dx1=0.2, dx2=0.2, dt=min(0.08, dt), precision=32,
+                                       filt_kc=0.5, filt_w=0.2, azimuthal_m=m))
+            cf = lambda s_: [(torch.randn(nr, nz, device=dev) + 1j * torch.randn(nr, nz, device=dev)).to(torch.complex64) * s_
+                             for _ in range(3)]
+            bufs.append((cf(1e-3), cf(1e-3), cf(1e-3)))
+            cells += nz * nr
+            alg_bytes += 120 * nz * nr
+        b = hyb.Batch(descs, stream)
+        for i, (E, B, J) in enumerate(bufs):
+            b.bind(i, E, B, J)
+        t0 = time.perf_counter()
+        b.tune(3)
+        tune_s = time.perf_counter() - t0
+        ms = time_steps(lambda: b.advance(1), args.steps, args.warmup, stream, flush, sampler)
+        launches = b.launches_per_step * args.steps
+        extra["config"] = {"workload": "batched_16x2d_uneven_plus_quasi3d_m012_2048x512", "instances_2d": sizes,
+                           "quasi3d_modes": [0, 1, 2], "quasi3d_grid": [nz, nr], "autotune_s": tune_s,
+                           "rows_per_strip": {n1: b.rows_per_strip(n1) for n1 in (512, 1024, 2048, 4096)},
+                           "current": "band-limited random J (no deposit in the timed step)",
+                           "l2": "flushed between timed steps (256 MB write)"}
+        dtype = "f32"
+        b.close()
+    elif args.workload == "3d":
+        w = wl.DRIFT_PLASMA_3D
+        g = hyb.Grid(hyb.desc_from_workload(w), stream)
+        E0, B0 = wl.band_limited_fields(w)
+        J0, _ = wl.band_limited_fields(w.scaled(seed=w.seed + 50))
+        mk = lambda arrs: [torch.from_numpy(a.astype(np.float32)).to(dev) for a in arrs]
+        g.bind(mk(E0), mk(B0), mk(J0))
+        cells, alg_bytes = w.cells, 60 * w.cells
+        ms = time_steps(lambda: g.advance(1), args.steps, args.warmup, stream, flush, sampler)
+        launches = g.launches_per_step * args.steps
+        extra["config"] = {"workload": w.name, "path": "three-pass", "current": "band-limited random J",
+                           "l2": "flushed between timed steps (256 MB write)"}
+        dtype = "f32"
+        g.close()
+    else:
+        w = wl.VACUUM_BEAM
+        g = hyb.Grid(hyb.desc_from_workload(w), stream)
+        E0, B0 = wl.band_limited_fields(w)
+        mk = lambda arrs: [torch.from_numpy(a).to(dev) for a in arrs]
+        J = [torch.zeros(w.shape, dtype=torch.float64, device=dev) for _ in range(3)]
+        g.bind(mk(E0), mk(B0), J)
+        p = wl.make_particles(w)
+        cell, o0, o1, v3 = wl.ballistic_move(w, p, 0)
+        g.deposit(torch.from_numpy(cell).to(dev), torch.from_numpy(o0).to(dev), torch.from_numpy(o1).to(dev),
+                  torch.from_numpy(v3).to(dev), torch.from_numpy(p.q).to(dev), w.shape_order)
+        g.check()
+        cells, alg_bytes = w.cells, 120 * w.cells
+        ms = time_steps(lambda: g.advance(1), args.steps, args.warmup, stream, flush, sampler)
+        launches = g.launches_per_step * args.steps
+        extra["config"] = {"workload": w.name, "path": "three-pass FP64", "l2": "flushed between timed steps"}
+        dtype = "f64"
+        g.close()
+    sampler.stop()
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": cells / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": src, "kernel": "whole step", "bytes_per_launch": alg_bytes},
+            "gpu_launches": launches, "clocks": sampler.summary()}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "drift_plasma":
+        return run_other(args)
     import numpy as np
     import torch
     ws, rank, local = dist_env()
@@ -295,11 +432,7 @@ def main():
     kern_ms = [a.elapsed_time(b) for a, b in ek]
     ms = statistics.mean(step_ms)
     kms = statistics.mean(kern_ms)
-    if ws > 1:
-        t = torch.tensor([ms, kms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, kms = float(t[0]), float(t[1])
-    value = ws * cells / (ms / 1e3)
+    ms, kms, value = replica_aggregate(ms, kms, cells, ws, dev)
     launches = grid.launches_per_step * K
 
     extras = {}
