@@ -73,7 +73,10 @@ typedef struct {
     int yee_mode;         /* 1: [k]1 = sin(k1 dx1/2)/(dx1/2) (recovers the Yee solver, Sec. 2.1) */
     double ampere;        /* coefficient of j in Ampere's law; 0 selects 4 pi */
     int path;             /* 0: fastest available; 1: three-pass (FFT, update, inverse FFT);
-                             2: fused single-pass (precision 32, dims 2, n1 in 512..4096) */
+                             2: fused single-pass (precision 32, dims 2, n1 in 512..4096);
+                             3: three-pass with the x1 transform as a dense DFT matrix product on
+                                the tensor cores, FP32 split into BF16 hi + lo (3 products),
+                                FP32 accumulation (precision 32, dims 2 or 3, 16 <= n1 <= 1024) */
     int azimuthal_m;      /* dims 20 only: azimuthal mode number m >= 0.  The grid is then
                              (z, r) = (x1, x2) with n1 = nz, n2 = nr, dx1 = dz, dx2 = dr, a
                              perfectly conducting wall at r = n2 dx2, the axis at r = 0, and
@@ -257,7 +260,7 @@ HYB_API hyb_status hyb_mlp_train_step(hyb_mlp* m, const float* x, const float* t
                                       void* stream);
 HYB_API hyb_status hyb_mlp_destroy(hyb_mlp* m);
 
-/* Which advance path a grid runs: 1 three-pass, 2 fused. */
+/* Which advance path a grid runs: 1 three-pass, 2 fused, 3 three-pass with DFT-GEMM. */
 HYB_API int hyb_grid_path(const hyb_grid* g);
 
 /* Number of kernel launches one hyb_advance step of this grid issues. */

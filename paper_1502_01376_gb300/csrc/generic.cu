@@ -217,7 +217,14 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
     const bool d3 = g->d.dims == 3;
     for (int s = 0; s < nsteps; s++) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
-        HYB_CUDA_TRY((launch_rfft<T, T>(fin, 9, spec, n1, rows, t, g->stream)));
+        if (g->path == 3) {
+            const float* f9[9];
+            for (int c = 0; c < 9; c++) f9[c] = (const float*)fin.p[c];
+            hyb_status st = dftgemm_forward(g, f9, 9, reinterpret_cast<float2*>(spec));
+            if (st != HYB_OK) return st;
+        } else {
+            HYB_CUDA_TRY((launch_rfft<T, T>(fin, 9, spec, n1, rows, t, g->stream)));
+        }
         if (d3) {
             k_faraday<T, true><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
             k_ampere<T, true><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, t.cj1, t.cj, a2, a3);
@@ -226,7 +233,14 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
             k_ampere<T, false><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, t.cj1, t.cj, a2, a3);
         }
         HYB_CUDA_TRY(cudaGetLastError());
-        HYB_CUDA_TRY((launch_irfft<T, T>(spec, 0, fout, 6, n1, rows, t, g->stream)));
+        if (g->path == 3) {
+            float* f6[6];
+            for (int c = 0; c < 6; c++) f6[c] = (float*)fout.p[c];
+            hyb_status st = dftgemm_inverse(g, reinterpret_cast<const float2*>(spec), 6, f6);
+            if (st != HYB_OK) return st;
+        } else {
+            HYB_CUDA_TRY((launch_irfft<T, T>(spec, 0, fout, 6, n1, rows, t, g->stream)));
+        }
         if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
     }
     return HYB_OK;

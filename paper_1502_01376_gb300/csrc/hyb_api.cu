@@ -169,7 +169,11 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
         set_error("dt = %.17g exceeds the Courant limit %.17g of the hybrid solver", d.dt, cl);
         return HYB_ECOURANT;
     }
-    if (d.path < 0 || d.path > 2) { set_error("path must be 0, 1 or 2"); return HYB_EINVAL; }
+    if (d.path < 0 || d.path > 3) { set_error("path must be 0, 1, 2 or 3"); return HYB_EINVAL; }
+    if (d.path == 3 && !(d.precision == 32 && d.dims != 20 && d.n1 >= 16 && d.n1 <= 1024)) {
+        set_error("path 3 (DFT-GEMM) needs precision 32, dims 2 or 3 and 16 <= n1 <= 1024");
+        return HYB_EINVAL;
+    }
     const bool fused_ok = d.dims != 20 && fused_supported(d);
     if (d.dims == 20 && d.path == 2) { set_error("quasi-3D grids run the three-pass path"); return HYB_EINVAL; }
     if (d.path == 2 && !fused_ok) {
@@ -198,12 +202,13 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
     if (st == HYB_OK && d.dims == 20) st = quasi3d_create(g);
     if (st == HYB_OK && d.dims != 20) {
         const size_t csz = d.precision == 32 ? sizeof(float2) : sizeof(double2);
-        const int nf = (g->path == 1) ? 9 : 3;
+        const int nf = (g->path == 1 || g->path == 3) ? 9 : 3;
         g->spec_bytes = (size_t)nf * g->rows * g->nk * csz;
         ce = cudaMalloc(&g->spec, g->spec_bytes);
         if (ce != cudaSuccess) { g->spec = nullptr; st = cuda_fail(ce, "cudaMalloc(spectral scratch)"); }
     }
     if (st == HYB_OK && g->path == 2) st = fused_create(g);
+    if (st == HYB_OK && g->path == 3) st = dftgemm_create(g);
     if (st != HYB_OK) { hyb_destroy_grid(g); return st; }
     *out = g;
     return HYB_OK;
@@ -306,6 +311,7 @@ hyb_status hyb_destroy_grid(hyb_grid* g) {
     if (g->stream) cudaStreamSynchronize(g->stream); else cudaDeviceSynchronize();
     if (g->fused) fused_destroy(g);
     if (g->qtab) quasi3d_destroy(g);
+    if (g->dft) dftgemm_destroy(g);
     free_tables_f(g->tf);
     free_tables_d(g->td);
     if (g->spec) cudaFree(g->spec);

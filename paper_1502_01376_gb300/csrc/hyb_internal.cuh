@@ -89,6 +89,7 @@ struct hyb_grid {
     int* dflag = nullptr;          // device data-error flag
     hyb::FusedPlan* fused = nullptr;
     void* qtab = nullptr;          // quasi-3D per-mode tables (device)
+    void* dft = nullptr;           // path 3: DFT-GEMM matrices and buffers
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional kernel timing events
 };
 
@@ -126,6 +127,12 @@ int fused_launches_per_step(const hyb_grid* g);
 hyb_status quasi3d_create(hyb_grid* g);
 void quasi3d_destroy(hyb_grid* g);
 hyb_status quasi3d_advance(hyb_grid* g, int nsteps);
+
+// x1 transform as a split-BF16 DFT-GEMM on the tensor cores (dftgemm.cu)
+hyb_status dftgemm_create(hyb_grid* g);
+void dftgemm_destroy(hyb_grid* g);
+hyb_status dftgemm_forward(hyb_grid* g, const float* const* fields, int nf, float2* spec);
+hyb_status dftgemm_inverse(hyb_grid* g, const float2* spec, int nf, float* const* fields);
 
 // deposit (deposit.cu)
 template <typename T>

@@ -1,0 +1,72 @@
+"""Path 3: the x1 transform of the three-pass advance as a split-BF16 DFT
+matrix product on the tensor cores, checked field by field against the FP64
+oracle.  Each product keeps hi*hi + hi*lo + lo*hi of the BF16 split; the
+dropped lo*lo term and the BF16 rounding of lo leave about 2^-17 relative
+error per matrix entry, so after forward + inverse transforms over a few
+steps the per-field relative L2 error stays near 1e-5; the bound here is 1e-4."""
+import numpy as np
+import pytest
+
+from paper_1502_01376_gb300 import workloads as wl
+
+from gpu_util import hyb_module, need_gpu, orc_grid, rel_err, to_dev, to_np, torch
+
+pytestmark = pytest.mark.gpu
+
+TOL_DFT = 1e-4
+
+
+def _run(orc, w, path, nst):
+    hyb = hyb_module()
+    desc = hyb.desc_from_workload(w, path=path)
+    g = hyb.Grid(desc)
+    assert g.path == path
+    E0, B0 = wl.band_limited_fields(w)
+    rng = np.random.default_rng(7)
+    J0 = [rng.standard_normal(w.shape) * 1e-3 for _ in range(3)]
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    E = [to_dev(a, torch.float32) for a in E0]
+    B = [to_dev(a, torch.float32) for a in B0]
+    J = [to_dev(a, torch.float32) for a in J0]
+    g.bind(E, B, J)
+    g.advance(nst)
+    g.check()
+    Eo, Bo, Jo = [f32(a) for a in E0], [f32(a) for a in B0], [f32(a) for a in J0]
+    orc.step(orc_grid(orc, w), Eo, Bo, Jo, nsteps=nst)
+    return [rel_err(to_np(a), b) for a, b in zip(E + B, Eo + Bo)]
+
+
+@pytest.mark.parametrize("n1,n2", [(16, 9), (64, 37), (128, 20), (256, 33), (1024, 3)])
+def test_dftgemm_2d_per_field(orc, n1, n2):
+    need_gpu()
+    w = wl.Workload("t", 2, n1, n2, dx1=0.2, dx2=0.25, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2, seed=5)
+    errs = _run(orc, w, 3, 5)
+    assert max(errs) < TOL_DFT, errs
+
+
+def test_dftgemm_3d_per_field(orc):
+    need_gpu()
+    w = wl.Workload("t", 3, 64, 12, 10, dx1=0.2, dx2=0.25, dx3=0.3, dt=0.05, precision=32, filt_kc=0.6,
+                    filt_w=0.2, seed=6)
+    errs = _run(orc, w, 3, 4)
+    assert max(errs) < TOL_DFT, errs
+
+
+def test_dftgemm_tracks_radix_path(orc):
+    """Both FP32 paths on the same inputs: the DFT-GEMM error stays within a
+    small factor of the radix FFT's FP32 error plus the split-BF16 bound."""
+    need_gpu()
+    w = wl.Workload("t", 2, 128, 40, dx1=0.2, dx2=0.25, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2, seed=8)
+    e3 = _run(orc, w, 3, 8)
+    e1 = _run(orc, w, 1, 8)
+    assert max(e1) < 1e-5, e1
+    assert all(a < 10 * b + TOL_DFT for a, b in zip(e3, e1)), (e3, e1)
+
+
+def test_dftgemm_rejects_unsupported():
+    need_gpu()
+    hyb = hyb_module()
+    for bad in (dict(precision=64, n1=64), dict(precision=32, n1=2048), dict(precision=32, n1=8)):
+        w = wl.Workload("t", 2, bad["n1"], 8, dx1=0.2, dx2=0.25, dt=0.05, precision=bad["precision"], seed=1)
+        with pytest.raises(Exception):
+            hyb.Grid(hyb.desc_from_workload(w, path=3))
