@@ -46,10 +46,11 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="profiling mode: random band-limited J instead of the particle deposit, no extras")
     ap.add_argument("--workload", default="drift_plasma",
-                    choices=["drift_plasma", "batched", "3d", "vacuum_beam"],
+                    choices=["drift_plasma", "batched", "3d", "vacuum_beam", "x1_sweep"],
                     help="drift_plasma (default, the headline): 2D 4096 x 1024 FP32; batched: 16 uneven 2D grids "
                          "+ quasi-3D modes m = 0, 1, 2 (2048 x 512 complex) in one CUDA-graph step; 3d: 1024 x 256 x 256 "
-                         "FP32; vacuum_beam: 2D 128 x 64 FP64")
+                         "FP32, radix FFT vs DFT-GEMM x1 transform; vacuum_beam: 2D 128 x 64 FP64; x1_sweep: both x1 "
+                         "transforms for n1 = 16 .. 1024 at 2^25 cells")
     return ap.parse_args()
 
 
@@ -71,7 +72,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fused2d.cu", "hyb_internal.cuh"):
+    for f in ("fused2d.cu", "fused_api.cuh"):
         with open(os.path.join(ROOT, "paper_1502_01376_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -241,6 +242,34 @@ def time_steps(step_fn, K, W, stream, flush, sampler):
     return statistics.mean(a.elapsed_time(b) for a, b in ev)
 
 
+def x1_compare(hyb, w, arrs, stream, flush, sampler, args, dev):
+    """Time the three-pass advance with the radix x1 FFT (path 1) and with the
+    DFT-GEMM (path 3) on the same inputs; per-field relative L2 error of each
+    after 3 steps against the FP64 GPU path (parity-tested against the oracle)."""
+    import torch
+    out = {}
+    fin = {}
+    for path in (64, 1, 3):
+        prec = 64 if path == 64 else 32
+        dt = torch.float64 if prec == 64 else torch.float32
+        g = hyb.Grid(hyb.desc_from_workload(w, path=1 if path == 64 else path, precision=prec), stream)
+        F = [torch.from_numpy(a).to(device=dev, dtype=dt) for a in arrs]
+        g.bind(F[0:3], F[3:6], F[6:9])
+        g.advance(3)
+        torch.cuda.synchronize()
+        fin[path] = [f.double() if path != 64 else f for f in F[:6]]
+        if path != 64:
+            steps = args.steps if path == 1 else max(3, min(args.steps, 20))
+            out[f"ms_path{path}"] = time_steps(lambda: g.advance(1), steps, args.warmup, stream, flush, sampler)
+            out[f"launches_path{path}"] = g.launches_per_step
+        g.close()
+        del F
+    names = ("E1", "E2", "E3", "B1", "B2", "B3")
+    for path in (1, 3):
+        out[f"err_path{path}"] = {n: float((a - b).norm() / b.norm()) for n, a, b in zip(names, fin[path], fin[64])}
+    return out
+
+
 def run_other(args):
     """Measurement lines for the non-headline configurations (same JSON keys)."""
     import numpy as np
@@ -296,19 +325,40 @@ def run_other(args):
         dtype = "f32"
         b.close()
     elif args.workload == "3d":
+        # x1 transform as radix FFT (path 1) and as split-BF16 DFT-GEMM (path 3):
+        # both timed, per-field error of each after 3 steps against the FP64 GPU
+        # path from the same initial state, the faster one reported as the value
         w = wl.DRIFT_PLASMA_3D
-        g = hyb.Grid(hyb.desc_from_workload(w), stream)
         E0, B0 = wl.band_limited_fields(w)
         J0, _ = wl.band_limited_fields(w.scaled(seed=w.seed + 50))
-        mk = lambda arrs: [torch.from_numpy(a.astype(np.float32)).to(dev) for a in arrs]
-        g.bind(mk(E0), mk(B0), mk(J0))
         cells, alg_bytes = w.cells, 60 * w.cells
-        ms = time_steps(lambda: g.advance(1), args.steps, args.warmup, stream, flush, sampler)
-        launches = g.launches_per_step * args.steps
-        extra["config"] = {"workload": w.name, "path": "three-pass", "current": "band-limited random J",
+        x1 = x1_compare(hyb, w, list(E0) + list(B0) + list(J0), stream, flush, sampler, args, dev)
+        best = min((1, 3), key=lambda p_: x1[f"ms_path{p_}"])
+        ms = x1[f"ms_path{best}"]
+        launches = x1[f"launches_path{best}"] * args.steps
+        extra["config"] = {"workload": w.name, "path": {1: "three-pass radix FFT", 3: "three-pass DFT-GEMM"}[best],
+                           "x1_transform": x1, "current": "band-limited random J",
                            "l2": "flushed between timed steps (256 MB write)"}
         dtype = "f32"
-        g.close()
+    elif args.workload == "x1_sweep":
+        rows_out = []
+        for n1 in (16, 32, 64, 128, 256, 512, 1024):
+            n2 = (1 << 25) // n1
+            w = wl.Workload(f"sweep_{n1}", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.08, precision=32, filt_kc=0.5,
+                            filt_w=0.2, seed=3)
+            gen = np.random.default_rng(n1)
+            arrs = [gen.standard_normal(w.shape) * 1e-3 for _ in range(9)]
+            r = x1_compare(hyb, w, arrs, stream, flush, None, args, dev)
+            r["n1"], r["n2"] = n1, n2
+            rows_out.append(r)
+        best_row = rows_out[0]
+        best = min((1, 3), key=lambda p_: best_row[f"ms_path{p_}"])
+        cells, alg_bytes = 1 << 25, 60 << 25
+        ms = best_row[f"ms_path{best}"]
+        launches = best_row[f"launches_path{best}"] * args.steps
+        extra["config"] = {"workload": "x1_transform_sweep_2d_2^25_cells_f32", "value_at": "n1 = 16",
+                           "sweep": rows_out, "current": "random J", "l2": "flushed between timed steps"}
+        dtype = "f32"
     else:
         w = wl.VACUUM_BEAM
         g = hyb.Grid(hyb.desc_from_workload(w), stream)

@@ -334,7 +334,9 @@ int hyb_grid_path(const hyb_grid* g) { return g ? g->path : 0; }
 
 int hyb_launches_per_step(const hyb_grid* g) {
     if (!g) return 0;
-    return g->path == 2 ? fused_launches_per_step(g) : (int)generic_launches_per_step();
+    if (g->path == 2) return fused_launches_per_step(g);
+    if (g->path == 3) return 11;     // split + product (forward), Faraday, Ampere, split + 6 products (inverse)
+    return (int)generic_launches_per_step();
 }
 
 }  // extern "C"
