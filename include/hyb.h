@@ -72,7 +72,9 @@ typedef struct {
     double kmod_max;      /* bump height, fraction of k_g1; 0 = off */
     int yee_mode;         /* 1: [k]1 = sin(k1 dx1/2)/(dx1/2) (recovers the Yee solver, Sec. 2.1) */
     double ampere;        /* coefficient of j in Ampere's law; 0 selects 4 pi */
-    int path;             /* 0: fastest available; 1: three-pass (FFT, update, inverse FFT);
+    int path;             /* 0: fastest available, as measured on GB300 (fused where it applies,
+                                else path 3 for precision 32 with 16 <= n1 <= 64, else path 1);
+                             1: three-pass (FFT, update, inverse FFT);
                              2: fused single-pass (precision 32, dims 2, n1 in 512..4096);
                              3: three-pass with the x1 transform as a dense DFT matrix product on
                                 the tensor cores, FP32 split into BF16 hi + lo (3 products),
