@@ -72,7 +72,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fused2d.cu", "fused_api.cuh"):
+    for f in ("fused_tm.cu", "fused_dev.cuh", "fused_api.cuh"):
         with open(os.path.join(ROOT, "paper_1502_01376_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -545,7 +545,7 @@ def main():
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": src,
-                         "kernel": "k_fused2d<4096>" if grid.path == 2 else "three-pass step",
+                         "kernel": "k_fused_tm" if grid.path == 2 else "three-pass step",
                          "kernel_ms": kms, "bytes_per_launch": BYTES_PER_CELL_STEP * cells},
             "gpu_launches": launches,
             "wall_s_timed": wall,

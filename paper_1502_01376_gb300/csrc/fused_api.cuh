@@ -47,6 +47,10 @@ struct FusedPlan {
 };
 
 size_t fused_smem_bytes(int n1);
+// n1 = 4096: the TMEM/TMA kernel (fused_tm.cu)
+size_t fused_tm_smem_bytes();
+cudaError_t fused_tm_occupancy(int* occ);
+cudaError_t fused_tm_launch(const FusedBatch& fb, int grid, cudaStream_t s);
 int fused_threads(int n1);
 cudaError_t fused_occupancy(int n1, int* occ);
 cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
