@@ -15,7 +15,10 @@
 //     transform (one cp.async.bulk of 16 KB, completion on an mbarrier) and
 //     two exchange buffers that alternate between consecutive transforms, so
 //     a transform needs no barrier after its last exchange; plus the twiddle
-//     and per-mode symbol tables.
+//     tables; the per-mode symbols of a thread's modes sit in TMEM beside its
+//     slots;
+//   * of the three exchanges of a transform only the first and the last cross
+//     warps (group barrier); the middle one stays inside a warp.
 //
 // Real FFT of N = 4096 points: the M = 2048-point complex FFT of
 // z[j] = x[2j] + i x[2j+1], factored 8 x 8 x 8 x 4:
@@ -43,14 +46,16 @@ constexpr int N = 4096, M = 2048, T = 256, NT = 768;
 constexpr int XS = 64 * 34;                              // exchange buffer (float2): the S2 -> S3 layout is 64 x 34
 constexpr int OFF_STAGE = 0;                             // [3][M] float2
 constexpr int OFF_XB = OFF_STAGE + 3 * M * 8;            // [3][2][XS] float2
-constexpr int OFF_TW1 = OFF_XB + 3 * 2 * XS * 8;         // [7][256] float2  W_2048^{t k1}, k1 = 1..7
-constexpr int OFF_TW2 = OFF_TW1 + 7 * 256 * 8;           // [8][32] float2   W_256^{t0 k2}
-constexpr int OFF_TW3 = OFF_TW2 + 8 * 32 * 8;            // [8][4] float2    W_32^{u0 k3}
-constexpr int OFF_SYM = OFF_TW3 + 8 * 4 * 8;             // [M + 1] float4
-constexpr int OFF_BAR = (OFF_SYM + (M + 1) * 16 + 7) / 8 * 8;   // [3] mbarrier
+// twiddle tables as pairs: entry [m][i] = (W^{i (2m+1)}, W^{i (2m+2)}), m = 0..3 (k = 1..8, k = 8 unused)
+constexpr int OFF_TW1 = OFF_XB + 3 * 2 * XS * 8;         // [4][256] float4  W_2048^{t k1}
+constexpr int OFF_TW2 = OFF_TW1 + 4 * 256 * 16;          // [4][32] float4   W_256^{t0 k2}
+constexpr int OFF_TW3 = OFF_TW2 + 4 * 32 * 16;           // [4][4] float4    W_32^{u0 k3}
+constexpr int OFF_SYMN = OFF_TW3 + 4 * 4 * 16;           // float4: the Nyquist mode's symbols
+constexpr int OFF_BAR = OFF_SYMN + 16;                   // [3] mbarrier
 constexpr int OFF_MISC = OFF_BAR + 3 * 8;                // TMEM base address, abort flag
 constexpr int SMEM = OFF_MISC + 16;
-constexpr uint32_t TMEM_COLS = 512;                      // 2 x 160 used
+constexpr uint32_t TMEM_COLS = 512;                      // slots 2 x 160, symbols 2 x 32
+constexpr int SYM_COL = 320;                             // per-mode symbols: S (16 words), cj1 (8), cj (8)
 constexpr long long WAIT_CYCLES = 4000000000LL;          // about 2 s at 2 GHz
 }  // namespace tmk
 
@@ -80,6 +85,23 @@ __device__ __forceinline__ void tm_st8(uint32_t ta, const float (&r)[8]) {
                  :: "r"(ta), "r"(__float_as_uint(r[0])), "r"(__float_as_uint(r[1])), "r"(__float_as_uint(r[2])),
                     "r"(__float_as_uint(r[3])), "r"(__float_as_uint(r[4])), "r"(__float_as_uint(r[5])),
                     "r"(__float_as_uint(r[6])), "r"(__float_as_uint(r[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void tm_ld4(uint32_t ta, float (&r)[4]) {
+    uint32_t u[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]) : "r"(ta));
+#pragma unroll
+    for (int i = 0; i < 4; i++) r[i] = __uint_as_float(u[i]);
+}
+__device__ __forceinline__ void tm_st16(uint32_t ta, const float (&r)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+                 :: "r"(ta), "r"(__float_as_uint(r[0])), "r"(__float_as_uint(r[1])), "r"(__float_as_uint(r[2])),
+                    "r"(__float_as_uint(r[3])), "r"(__float_as_uint(r[4])), "r"(__float_as_uint(r[5])),
+                    "r"(__float_as_uint(r[6])), "r"(__float_as_uint(r[7])), "r"(__float_as_uint(r[8])),
+                    "r"(__float_as_uint(r[9])), "r"(__float_as_uint(r[10])), "r"(__float_as_uint(r[11])),
+                    "r"(__float_as_uint(r[12])), "r"(__float_as_uint(r[13])), "r"(__float_as_uint(r[14])),
+                    "r"(__float_as_uint(r[15]))
                  : "memory");
 }
 __device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -122,29 +144,121 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* er
     }
 }
 
-// exchange-buffer position of the S3 -> S4 value (column c, u0): XOR swizzle of
-// the low four bits keeps both access patterns free of bank conflicts
-__device__ __forceinline__ int x3sw(int c) { return c ^ ((c >> 3) & 7); }
-__device__ __forceinline__ int x3pos(int csw, int u0) { return u0 * 512 + (csw ^ ((u0 & 1) << 3)); }
+
+// ------------------------------------------------------------------ packed FP32 pairs (f32x2): one instruction
+// for the two components of a complex add, subtract or scale
+__device__ __forceinline__ unsigned long long pk(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+    return upk(r);
+}
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+    return upk(r);
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+    return upk(r);
+}
+// a * b + c per component
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+    return upk(r);
+}
+
+// 4-point DFT (natural order) with packed adds: the rotation by -i (+i for
+// the inverse) of the odd difference is folded into four scalar adds
+template <bool INV>
+__device__ __forceinline__ void dft4x(float2& x0, float2& x1, float2& x2, float2& x3) {
+    const float2 A = vadd(x0, x2), B = vsub(x0, x2), C = vadd(x1, x3), Y = vsub(x1, x3);
+    x0 = vadd(A, C);
+    x2 = vsub(A, C);
+    if (!INV) { x1 = f2(B.x + Y.y, B.y - Y.x); x3 = f2(B.x - Y.y, B.y + Y.x); }
+    else { x1 = f2(B.x - Y.y, B.y + Y.x); x3 = f2(B.x + Y.y, B.y - Y.x); }
+}
+// 8-point DFT (natural order): two 4-point DFTs, twiddles W_8^k, radix-2 combine
+template <bool INV>
+__device__ __forceinline__ void dft8x(float2 (&x)[8]) {
+    float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+    float2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+    dft4x<INV>(e0, e1, e2, e3);
+    dft4x<INV>(o0, o1, o2, o3);
+    const float h = 0.70710678118654752440f;
+    // o1 W_8^1 and o3 W_8^3 (conjugated for the inverse)
+    if (!INV) {
+        o1 = vmul(f2(o1.x + o1.y, o1.y - o1.x), f2(h, h));
+        o3 = vmul(f2(o3.y - o3.x, o3.x + o3.y), f2(h, -h));
+    } else {
+        o1 = vmul(f2(o1.x - o1.y, o1.x + o1.y), f2(h, h));
+        o3 = vmul(f2(o3.x + o3.y, o3.x - o3.y), f2(-h, h));
+    }
+    x[0] = vadd(e0, o0); x[4] = vsub(e0, o0);
+    x[1] = vadd(e1, o1); x[5] = vsub(e1, o1);
+    x[3] = vadd(e3, o3); x[7] = vsub(e3, o3);
+    // o2 times -i (forward) or +i (inverse)
+    if (!INV) { x[2] = f2(e2.x + o2.y, e2.y - o2.x); x[6] = f2(e2.x - o2.y, e2.y + o2.x); }
+    else { x[2] = f2(e2.x - o2.y, e2.y + o2.x); x[6] = f2(e2.x + o2.y, e2.y - o2.x); }
+}
+
+// exchange-buffer position of the S3 -> S4 value of column c = k1 + 8 k2 + 64 k3 and
+// u0: inside the 256-entry region k1, which is the region the S2 threads of warp
+// k1 read, so S2 -> S3 -> (region reuse) stays inside one warp; the XOR terms keep
+// the S3 writes and the S4 reads of column t free of bank conflicts.  The base
+// for even u0 is pos(0), for odd u0 pos(1); position(u0) = base + 64 u0.
+__device__ __forceinline__ int x3base(int k1, int k2, int k3, int u0odd) {
+    return k1 * 256 + 8 * (k3 ^ ((k2 ^ u0odd) & 1)) + (k2 ^ k1);
+}
+// the twiddles (W^{i k}, k = 1..7) of row i of a pair table: W^i .. W^{4i} are
+// read, W^{5i}, W^{6i}, W^{7i} are products with W^{4i} (a few ulp, far below
+// the path's error budget)
+__device__ __forceinline__ void tw_row(const float4* tab, int stride, int i, float2 (&w)[8]) {
+    const float4 q0 = tab[i], q1 = tab[stride + i];
+    w[1] = f2(q0.x, q0.y); w[2] = f2(q0.z, q0.w); w[3] = f2(q1.x, q1.y); w[4] = f2(q1.z, q1.w);
+    w[5] = mul(w[4], w[1]); w[6] = mul(w[4], w[2]); w[7] = mul(w[4], w[3]);
+}
+// all four pairs read from the table (for the small, broadcast-read tables)
+__device__ __forceinline__ void tw_row_full(const float4* tab, int stride, int i, float2 (&w)[8]) {
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const float4 q = tab[m * stride + i];
+        w[2 * m + 1] = f2(q.x, q.y);
+        if (m < 3) w[2 * m + 2] = f2(q.z, q.w);
+    }
+}
 
 // forward split of one pair: X[k] = e - u, X[M-k] = conj(e + u), e = (a + conj b)/2,
-// u = (i/2) w (a - conj b), w = W_N^k, a = Z[k], b = Z[M-k]
+// u = (i/2) w (a - conj b), w = W_N^k, a = Z[k], b = Z[M-k].  With
+// u' = (-wd.y/2, -wd.x/2), wd = w (a - conj b): X[k] = (e.x - u'.x, e.y + u'.y),
+// X[M-k] = (e.x + u'.x, u'.y - e.y).
 __device__ __forceinline__ void split_fwd(float2 av, float2 bv, float2 w, float2& xk, float2& xmk) {
-    const float2 e = scl(add(av, conjf2(bv)), 0.5f);
-    const float2 wd = mul(w, sub(av, conjf2(bv)));
-    const float2 u = f2(-0.5f * wd.y, 0.5f * wd.x);
-    xk = sub(e, u);
-    xmk = conjf2(add(e, u));
+    const float2 e = vfma(bv, f2(0.5f, -0.5f), vmul(av, f2(0.5f, 0.5f)));
+    const float2 wd = mul(w, vfma(bv, f2(-1.f, 1.f), av));
+    const float2 up = f2(-0.5f * wd.y, -0.5f * wd.x);
+    xk = vfma(up, f2(-1.f, 1.f), e);
+    xmk = vfma(e, f2(1.f, -1.f), up);
 }
-// inverse split of one pair (with the 1/M of the inverse transform folded in):
-// Z[k] = E + iO, Z[M-k] = conj(E - iO), E = (X[k] + conj X[M-k])/2M,
-// O = conj(w) (X[k] - conj X[M-k])/2M
+// inverse split of one pair (with the 1/M of the inverse transform folded in as s = 1/(2M)):
+// Z[k] = E + iO, Z[M-k] = conj(E - iO), E = s (X[k] + conj X[M-k]),
+// O = conj(w) s (X[k] - conj X[M-k])
 __device__ __forceinline__ void split_inv(float2 xa, float2 xbv, float2 w, float s, float2& zk, float2& zmk) {
-    const float2 E = scl(add(xa, conjf2(xbv)), s);
-    const float2 O = scl(mulc(sub(xa, conjf2(xbv)), w), s);
-    const float2 v = f2(-O.y, O.x);
-    zk = add(E, v);
-    zmk = conjf2(sub(E, v));
+    const float2 xs = vmul(xa, f2(s, s));
+    const float2 E = vfma(xbv, f2(s, -s), xs);
+    const float2 O = mulc(vfma(xbv, f2(-s, s), xs), w);
+    zk = f2(E.x - O.y, E.y + O.x);
+    zmk = f2(E.x + O.y, O.x - E.y);
 }
 
 __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
@@ -152,10 +266,10 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
     extern __shared__ __align__(128) unsigned char sm[];
     float2* stage = reinterpret_cast<float2*>(sm + OFF_STAGE);
     float2* xbuf = reinterpret_cast<float2*>(sm + OFF_XB);
-    float2* tw1 = reinterpret_cast<float2*>(sm + OFF_TW1);
-    float2* tw2 = reinterpret_cast<float2*>(sm + OFF_TW2);
-    float2* tw3 = reinterpret_cast<float2*>(sm + OFF_TW3);
-    float4* sym = reinterpret_cast<float4*>(sm + OFF_SYM);
+    float4* tw1 = reinterpret_cast<float4*>(sm + OFF_TW1);
+    float4* tw2 = reinterpret_cast<float4*>(sm + OFF_TW2);
+    float4* tw3 = reinterpret_cast<float4*>(sm + OFF_TW3);
+    float4* symN = reinterpret_cast<float4*>(sm + OFF_SYMN);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
     uint32_t* s_taddr = reinterpret_cast<uint32_t*>(sm + OFF_MISC);
     volatile int* s_abort = reinterpret_cast<volatile int*>(sm + OFF_MISC + 4);
@@ -176,9 +290,15 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
         *s_abort = 0;
     }
     const FusedInst& i0 = fb.inst[fb.items[blockIdx.x].x];
-    for (int i = tid; i < 7 * 256; i += NT) tw1[i] = i0.twM[(i & 255) * ((i >> 8) + 1)];
-    for (int i = tid; i < 8 * 32; i += NT) tw2[i] = i0.twM[8 * (i & 31) * (i >> 5)];
-    for (int i = tid; i < 8 * 4; i += NT) tw3[i] = i0.twM[64 * (i & 3) * (i >> 2)];
+    // W_2048^{j} for j < 2048; the k = 8 half of the last pair is never used (set to 1)
+    auto twp = [&](int step, int i, int m) {
+        const float2 lo = i0.twM[(step * i * (2 * m + 1)) & (M - 1)];
+        const float2 hi = (m < 3) ? i0.twM[(step * i * (2 * m + 2)) & (M - 1)] : f2(1.f, 0.f);
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    };
+    for (int q = tid; q < 4 * 256; q += NT) tw1[q] = twp(1, q & 255, q >> 8);
+    for (int q = tid; q < 4 * 32; q += NT) tw2[q] = twp(8, q & 31, q >> 5);
+    for (int q = tid; q < 4 * 4; q += NT) tw3[q] = twp(64, q & 3, q >> 2);
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
@@ -186,17 +306,24 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
     // this thread's TMEM words: lane t mod 128 (the warp's quarter), columns (t / 128) * 160 + 16 slot + ...
     const uint32_t tw = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((t >> 7) * 160);
     auto ta = [&](int slot, int chunk) { return tw + (uint32_t)(16 * slot + 8 * chunk); };
+    // symbols of this thread's modes: S of elements 4c..4c+3 at ts + 8c, cj1 at ts + 16 + 4c, cj at ts + 24 + 4c
+    const uint32_t ts = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(SYM_COL + (t >> 7) * 32);
 
     // modes owned by this thread
     const int cA = t, cB = (t == 0) ? 256 : 512 - t;
     const float2 wA = i0.twC[t];                                     // W_4096^{cA}
-    const int cAs = x3sw(cA), cBs = x3sw(cB);
+    const int qA0 = x3base(cA & 7, (cA >> 3) & 7, cA >> 6, 0), qA1 = x3base(cA & 7, (cA >> 3) & 7, cA >> 6, 1);
+    const int qB0 = x3base(cB & 7, (cB >> 3) & 7, cB >> 6, 0), qB1 = x3base(cB & 7, (cB >> 3) & 7, cB >> 6, 1);
     auto kap = [&](int e) { return (e & 1) ? cB + 512 * (3 - (e >> 1)) : cA + 512 * (e >> 1); };
     // stage thread maps
     const int s2_t0 = t & 31, s2_k1 = t >> 5;
     const int s3_k2 = t & 7, s3_u0 = (t >> 3) & 3, s3_k1 = t >> 5;
     const int s3_rd = (s3_k1 * 8 + s3_k2) * 34 + s3_u0;                   // + 4 u1
-    const int s3_wr = x3pos(x3sw(s3_k1 + 8 * s3_k2), s3_u0);             // + 64 k3
+    // S3 writes of k3: even k3 at s3_we + 16 (k3 / 2), odd k3 at s3_wo + 16 (k3 / 2)
+    const int s3_w0 = x3base(s3_k1, s3_k2, 0, s3_u0 & 1) + 64 * s3_u0;
+    const int s3_w1 = x3base(s3_k1, s3_k2, 1, s3_u0 & 1) + 64 * s3_u0;
+    auto s3_pos = [&](int k3) { return ((k3 & 1) ? s3_w1 : s3_w0) + 16 * (k3 >> 1); };
+    auto x3_pos = [&](int q0, int q1, int u0) { return ((u0 & 1) ? q1 : q0) + 64 * u0; };
     constexpr float inv2M = 0.5f / (float)M;
 
     const uint32_t bar = smem_addr(bars + g);
@@ -233,22 +360,37 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
         const int q = idx - npro;
         return (q % 3) == 0 && p0 + q / 3 + 1 == p1;
     };
-    if (it.x != cur_inst) {                                       // per-instance symbol table
+    if (it.x != cur_inst) {
+        // per-instance symbols of this thread's modes into TMEM (written once by group 0;
+        // the other groups' threads t own the same modes), the Nyquist entry into shared memory
+        tm_fence_before();
         __syncthreads();
-        for (int i = tid; i <= M; i += NT) sym[i] = a.sym[i];
+        tm_fence_after();
+        if (g == 0) {
+            float r[16];
+#pragma unroll
+            for (int e = 0; e < 8; e++) { const float4 q = a.sym[kap(e)]; r[2 * e] = q.x; r[2 * e + 1] = q.y; }
+            tm_st16(ts, r);
+#pragma unroll
+            for (int e = 0; e < 8; e++) { const float4 q = a.sym[kap(e)]; r[e] = q.z; r[8 + e] = q.w; }
+            tm_st16(ts + 16, r);
+            tm_wait_st();
+        }
+        if (tid == 0) *symN = a.sym[M];
+        tm_fence_before();
         __syncthreads();
+        tm_fence_after();
         cur_inst = it.x;
     }
     int fidx = 0;
-    // first staged row of this item
-    if (t == 0) {
-        const float* s0 = fwd_src(a, N, strip, p0, p1, g, 0, fm, next);
-        if (s0 && !is_direct(0)) {
-            mbar_expect_tx(bar, 4 * N);
-            bulk_load(stg_s, s0, 4 * N, bar);
-        }
+    // source of this group's next forward transform; the first one is staged now
+    const float* nsrc = fwd_src(a, N, strip, p0, p1, g, 0, fm, next);
+    bool ndirect = is_direct(0);
+    pending = nsrc != nullptr && !ndirect;
+    if (pending && t == 0) {
+        mbar_expect_tx(bar, 4 * N);
+        bulk_load(stg_s, nsrc, 4 * N, bar);
     }
-    pending = !is_direct(0) && fwd_src(a, N, strip, p0, p1, g, 0, fm, next) != nullptr;
 
     for (int ri = 0; ri < nrounds; ri++) {
         if (fm && (ri == ri_wait_halo || ri == ri_wait_read)) {
@@ -261,8 +403,8 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
         if (j.kind == J_FWD) {
             // ---------------- S1: 8-point DFT of z[t + 256 n]
             float2 v[8];
-            if (is_direct(fidx)) {
-                const float2* s = reinterpret_cast<const float2*>(fwd_src(a, N, strip, p0, p1, g, fidx, fm, next));
+            if (ndirect) {
+                const float2* s = reinterpret_cast<const float2*>(nsrc);
 #pragma unroll
                 for (int n = 0; n < 8; n++) v[n] = ldg_stream(s + t + 256 * n);
             } else {
@@ -278,48 +420,58 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
 #pragma unroll
                 for (int n = 0; n < 8; n++) h[t + 256 * n] = v[n];
             }
-            Dft<8, false>::run(v);
+            dft8x<false>(v);
+            {
+                float2 w[8];
+                tw_row(tw1, 256, t, w);
 #pragma unroll
-            for (int k = 1; k < 8; k++) v[k] = mul(v[k], tw1[(k - 1) * 256 + t]);
+                for (int k = 1; k < 8; k++) v[k] = mul(v[k], w[k]);
+            }
 #pragma unroll
             for (int k = 0; k < 8; k++) X[k * 256 + t] = v[k];
             gsync();
             fidx++;
             // the group's staging row is free: start the next forward's row
-            {
-                const float* ns = fwd_src(a, N, strip, p0, p1, g, fidx, fm, next);
-                const bool go = ns != nullptr && !is_direct(fidx);
-                if (go && t == 0) {
-                    fence_proxy_async_smem();
-                    mbar_expect_tx(bar, 4 * N);
-                    bulk_load(stg_s, ns, 4 * N, bar);
-                }
-                pending = go;
+            nsrc = fwd_src(a, N, strip, p0, p1, g, fidx, fm, next);
+            ndirect = is_direct(fidx);
+            pending = nsrc != nullptr && !ndirect;
+            if (pending && t == 0) {
+                fence_proxy_async_smem();
+                mbar_expect_tx(bar, 4 * N);
+                bulk_load(stg_s, nsrc, 4 * N, bar);
             }
             // ---------------- S2
 #pragma unroll
             for (int n = 0; n < 8; n++) v[n] = X[s2_k1 * 256 + s2_t0 + 32 * n];
-            Dft<8, false>::run(v);
+            dft8x<false>(v);
+            {
+                float2 w[8];
+                tw_row(tw2, 32, s2_t0, w);
 #pragma unroll
-            for (int k = 1; k < 8; k++) v[k] = mul(v[k], tw2[k * 32 + s2_t0]);
+                for (int k = 1; k < 8; k++) v[k] = mul(v[k], w[k]);
+            }
 #pragma unroll
             for (int k = 0; k < 8; k++) Y[(s2_k1 * 8 + k) * 34 + s2_t0] = v[k];
-            gsync();
+            __syncwarp();                     // S2 -> S3 stays inside the warp (k1 = warp)
             // ---------------- S3
 #pragma unroll
             for (int n = 0; n < 8; n++) v[n] = Y[s3_rd + 4 * n];
-            Dft<8, false>::run(v);
+            dft8x<false>(v);
+            {
+                float2 w[8];
+                tw_row_full(tw3, 4, s3_u0, w);
 #pragma unroll
-            for (int k = 1; k < 8; k++) v[k] = mul(v[k], tw3[k * 4 + s3_u0]);
+                for (int k = 1; k < 8; k++) v[k] = mul(v[k], w[k]);
+            }
 #pragma unroll
-            for (int k = 0; k < 8; k++) X[s3_wr + 64 * k] = v[k];
+            for (int k = 0; k < 8; k++) X[s3_pos(k)] = v[k];
             gsync();
             // ---------------- S4: columns cA, cB, 4-point DFT over u0
             float2 A[4], Bc[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) { A[u] = X[x3pos(cAs, u)]; Bc[u] = X[x3pos(cBs, u)]; }
-            Dft<4, false>::run(A);
-            Dft<4, false>::run(Bc);
+            for (int u = 0; u < 4; u++) { A[u] = X[x3_pos(qA0, qA1, u)]; Bc[u] = X[x3_pos(qB0, qB1, u)]; }
+            dft4x<false>(A[0], A[1], A[2], A[3]);
+            dft4x<false>(Bc[0], Bc[1], Bc[2], Bc[3]);
             tc++;
             // even/odd split into the real-input coefficients of this thread's modes
             float2 x[8];
@@ -359,87 +511,89 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
                     }
                 } break;
                 case X_B2: {        // B2 += S E3(p)
-                    float w[8];
+                    float w[8], S[8];
                     tm_ld8(ta(sE3(p), c), w);
+                    tm_ld8(ts + 8 * c, S);
                     tm_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
-                        const float4 q = sym[kap(e0 + i)];
-                        const float2 r = add(x[e0 + i], mul(f2(q.x, q.y), f2(w[2 * i], w[2 * i + 1])));
+                        const float2 r = add(x[e0 + i], mul(f2(S[2 * i], S[2 * i + 1]), f2(w[2 * i], w[2 * i + 1])));
                         o[2 * i] = r.x; o[2 * i + 1] = r.y;
                     }
                     if (c == 0 && t == 0) {   // packed DC/Nyquist: two real updates
-                        o[0] = x[0].x + sym[0].x * w[0];
-                        o[1] = x[0].y + sym[M].x * w[1];
+                        o[0] = x[0].x + S[0] * w[0];
+                        o[1] = x[0].y + symN->x * w[1];
                     }
                 } break;
                 case X_B3: {        // B3 += a2 (E1(p+1) - E1(p)) - S E2(p)
-                    float u[8], w[8], e2[8];
+                    float u[8], w[8], e2[8], S[8];
                     tm_ld8(ta(sE1(p + 1), c), u);
                     tm_ld8(ta(sE1(p), c), w);
                     tm_ld8(ta(sE2, c), e2);
+                    tm_ld8(ts + 8 * c, S);
                     tm_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
-                        const float4 q = sym[kap(e0 + i)];
-                        const float2 se = mul(f2(q.x, q.y), f2(e2[2 * i], e2[2 * i + 1]));
+                        const float2 se = mul(f2(S[2 * i], S[2 * i + 1]), f2(e2[2 * i], e2[2 * i + 1]));
                         o[2 * i] = x[e0 + i].x + a2 * (u[2 * i] - w[2 * i]) - se.x;
                         o[2 * i + 1] = x[e0 + i].y + a2 * (u[2 * i + 1] - w[2 * i + 1]) - se.y;
                     }
                     if (c == 0 && t == 0) {
-                        o[0] = x[0].x + a2 * (u[0] - w[0]) - sym[0].x * e2[0];
-                        o[1] = x[0].y + a2 * (u[1] - w[1]) - sym[M].x * e2[1];
+                        o[0] = x[0].x + a2 * (u[0] - w[0]) - S[0] * e2[0];
+                        o[1] = x[0].y + a2 * (u[1] - w[1]) - symN->x * e2[1];
                     }
                 } break;
                 case X_J1: {        // E1 += a2 (B3(p) - B3(p-1)) - cj1 j1
-                    float u[8], w[8], d[8];
+                    float u[8], w[8], d[8], cj1[4];
                     tm_ld8(ta(sB3(p), c), u);
                     tm_ld8(ta(sB3(p - 1), c), w);
                     tm_ld8(ta(ds, c), d);
+                    tm_ld4(ts + 16 + 4 * c, cj1);
                     tm_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
-                        const float cj1 = sym[kap(e0 + i)].z;
-                        o[2 * i] = d[2 * i] + a2 * (u[2 * i] - w[2 * i]) - cj1 * x[e0 + i].x;
-                        o[2 * i + 1] = d[2 * i + 1] + a2 * (u[2 * i + 1] - w[2 * i + 1]) - cj1 * x[e0 + i].y;
+                        o[2 * i] = d[2 * i] + a2 * (u[2 * i] - w[2 * i]) - cj1[i] * x[e0 + i].x;
+                        o[2 * i + 1] = d[2 * i + 1] + a2 * (u[2 * i + 1] - w[2 * i + 1]) - cj1[i] * x[e0 + i].y;
                     }
-                    if (c == 0 && t == 0) o[1] = d[1] + a2 * (u[1] - w[1]) - sym[M].z * x[0].y;
+                    if (c == 0 && t == 0) o[1] = d[1] + a2 * (u[1] - w[1]) - symN->z * x[0].y;
                 } break;
                 case X_J2: {        // E2 += conj(S) B3(p) - cj j2
-                    float u[8], d[8];
+                    float u[8], d[8], S[8], cj[4];
                     tm_ld8(ta(sB3(p), c), u);
                     tm_ld8(ta(ds, c), d);
+                    tm_ld8(ts + 8 * c, S);
+                    tm_ld4(ts + 24 + 4 * c, cj);
                     tm_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
-                        const float4 q = sym[kap(e0 + i)];
-                        const float2 sb = mulc(f2(u[2 * i], u[2 * i + 1]), f2(q.x, q.y));
-                        o[2 * i] = d[2 * i] + sb.x - q.w * x[e0 + i].x;
-                        o[2 * i + 1] = d[2 * i + 1] + sb.y - q.w * x[e0 + i].y;
+                        const float2 sb = mulc(f2(u[2 * i], u[2 * i + 1]), f2(S[2 * i], S[2 * i + 1]));
+                        o[2 * i] = d[2 * i] + sb.x - cj[i] * x[e0 + i].x;
+                        o[2 * i + 1] = d[2 * i + 1] + sb.y - cj[i] * x[e0 + i].y;
                     }
                     if (c == 0 && t == 0) {
-                        const float4 qd = sym[0], qn = sym[M];
-                        o[0] = d[0] + qd.x * u[0] - qd.w * x[0].x;
+                        const float4 qn = *symN;
+                        o[0] = d[0] + S[0] * u[0] - cj[0] * x[0].x;
                         o[1] = d[1] + qn.x * u[1] - qn.w * x[0].y;
                     }
                 } break;
                 default: {          // X_J3: E3 += -conj(S) B2(p) - a2 (B1(p) - B1(p-1)) - cj j3
-                    float b2[8], u[8], w[8], d[8];
+                    float b2[8], u[8], w[8], d[8], S[8], cj[4];
                     tm_ld8(ta(sB2, c), b2);
                     tm_ld8(ta(sB1(p), c), u);
                     tm_ld8(ta(sB1(p - 1), c), w);
                     tm_ld8(ta(ds, c), d);
+                    tm_ld8(ts + 8 * c, S);
+                    tm_ld4(ts + 24 + 4 * c, cj);
                     tm_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
-                        const float4 q = sym[kap(e0 + i)];
-                        const float2 sb = mulc(f2(b2[2 * i], b2[2 * i + 1]), f2(q.x, q.y));
-                        o[2 * i] = d[2 * i] - sb.x - a2 * (u[2 * i] - w[2 * i]) - q.w * x[e0 + i].x;
-                        o[2 * i + 1] = d[2 * i + 1] - sb.y - a2 * (u[2 * i + 1] - w[2 * i + 1]) - q.w * x[e0 + i].y;
+                        const float2 sb = mulc(f2(b2[2 * i], b2[2 * i + 1]), f2(S[2 * i], S[2 * i + 1]));
+                        o[2 * i] = d[2 * i] - sb.x - a2 * (u[2 * i] - w[2 * i]) - cj[i] * x[e0 + i].x;
+                        o[2 * i + 1] = d[2 * i + 1] - sb.y - a2 * (u[2 * i + 1] - w[2 * i + 1]) - cj[i] * x[e0 + i].y;
                     }
                     if (c == 0 && t == 0) {
-                        const float4 qd = sym[0], qn = sym[M];
-                        o[0] = d[0] - qd.x * b2[0] - a2 * (u[0] - w[0]) - qd.w * x[0].x;
+                        const float4 qn = *symN;
+                        o[0] = d[0] - S[0] * b2[0] - a2 * (u[0] - w[0]) - cj[0] * x[0].x;
                         o[1] = d[1] - qn.x * b2[1] - a2 * (u[1] - w[1]) - qn.w * x[0].y;
                     }
                 } break;
@@ -469,36 +623,48 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
                 split_inv(x[7], x[1], wconst<16, 1, false>(), inv2M, Bc[0], Bc[3]);
                 split_inv(x[5], x[3], wconst<16, 3, false>(), inv2M, Bc[1], Bc[2]);
             }
-            Dft<4, true>::run(A);
-            Dft<4, true>::run(Bc);
+            dft4x<true>(A[0], A[1], A[2], A[3]);
+            dft4x<true>(Bc[0], Bc[1], Bc[2], Bc[3]);
 #pragma unroll
-            for (int u = 0; u < 4; u++) { X[x3pos(cAs, u)] = A[u]; X[x3pos(cBs, u)] = Bc[u]; }
+            for (int u = 0; u < 4; u++) { X[x3_pos(qA0, qA1, u)] = A[u]; X[x3_pos(qB0, qB1, u)] = Bc[u]; }
             gsync();
             // ---------------- S3 inverse: twiddle, inverse 8-point DFT over k3 -> u1
             float2 v[8];
 #pragma unroll
-            for (int k = 0; k < 8; k++) v[k] = X[s3_wr + 64 * k];
+            for (int k = 0; k < 8; k++) v[k] = X[s3_pos(k)];
+            {
+                float2 w[8];
+                tw_row_full(tw3, 4, s3_u0, w);
 #pragma unroll
-            for (int k = 1; k < 8; k++) v[k] = mulc(v[k], tw3[k * 4 + s3_u0]);
-            Dft<8, true>::run(v);
+                for (int k = 1; k < 8; k++) v[k] = mulc(v[k], w[k]);
+            }
+            dft8x<true>(v);
 #pragma unroll
             for (int n = 0; n < 8; n++) Y[s3_rd + 4 * n] = v[n];
-            gsync();
+            __syncwarp();                     // S3 -> S2 inverse stays inside the warp
             // ---------------- S2 inverse: over k2 -> t1
 #pragma unroll
             for (int k = 0; k < 8; k++) v[k] = Y[(s2_k1 * 8 + k) * 34 + s2_t0];
+            {
+                float2 w[8];
+                tw_row(tw2, 32, s2_t0, w);
 #pragma unroll
-            for (int k = 1; k < 8; k++) v[k] = mulc(v[k], tw2[k * 32 + s2_t0]);
-            Dft<8, true>::run(v);
+                for (int k = 1; k < 8; k++) v[k] = mulc(v[k], w[k]);
+            }
+            dft8x<true>(v);
 #pragma unroll
             for (int n = 0; n < 8; n++) X[s2_k1 * 256 + s2_t0 + 32 * n] = v[n];
             gsync();
             // ---------------- S1 inverse: over k1 -> n, store the row
 #pragma unroll
             for (int k = 0; k < 8; k++) v[k] = X[k * 256 + t];
+            {
+                float2 w[8];
+                tw_row(tw1, 256, t, w);
 #pragma unroll
-            for (int k = 1; k < 8; k++) v[k] = mulc(v[k], tw1[(k - 1) * 256 + t]);
-            Dft<8, true>::run(v);
+                for (int k = 1; k < 8; k++) v[k] = mulc(v[k], w[k]);
+            }
+            dft8x<true>(v);
             float2* dst = reinterpret_cast<float2*>(j.dst);
 #pragma unroll
             for (int n = 0; n < 8; n++) stg_stream(dst + t + 256 * n, v[n]);
