@@ -4,7 +4,8 @@
 //       x2 (and x3) (Eqs. hybrid2db1-hybrid2de3; Sec. 2.4 for 3D),
 //   (3) batched inverse real FFT of E, B back in place.
 // It also provides the row FFTs used by the standalone current processing and
-// the diagnostics.  The x1 transform is a shared-memory Stockham radix-2 FFT
+// the diagnostics.  The x1 transform is a shared-memory Stockham FFT (radix 8,
+// then one radix-4 or radix-2 pass; several short rows per block)
 // of the n1/2-point complex sequence z[j] = x[2j] + i x[2j+1] followed by the
 // standard even/odd split into the n1/2+1 real-input coefficients.
 #include "hyb_internal.cuh"
@@ -16,31 +17,35 @@ constexpr int kRowThreads = 256;
 struct RowPtrs { const void* p[9]; };
 struct RowPtrsW { void* p[9]; };
 
-// X[k] = 1/2 (Z[k] + Z*[M-k]) - i/2 W_N^k (Z[k] - Z*[M-k]),  k = 0..M
+// X[k] = 1/2 (Z[k] + Z*[M-k]) - i/2 W_N^k (Z[k] - Z*[M-k]),  k = 0..M.
+// A block transforms RB = fft_rows_per_block(M) consecutive rows of one field.
 template <typename Tin, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* __restrict__ out, int n1, int64_t rows,
                                                            const cplx<T>* __restrict__ twM, const cplx<T>* __restrict__ twN) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = n1 >> 1;
+    const int M = n1 >> 1, RB = fft_rows_per_block(M);
     C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + M;
-    const int64_t row = blockIdx.x;
+    C* dst = src + (size_t)RB * M;
+    const int64_t row0 = (int64_t)blockIdx.x * RB;
+    const int nrow = (int)((rows - row0) < RB ? (rows - row0) : RB);
     const int f = blockIdx.y;
-    const Tin* x = reinterpret_cast<const Tin*>(in.p[f]) + row * n1;
-    for (int j = threadIdx.x; j < M; j += blockDim.x) src[j] = mkc<C>((T)x[2 * j], (T)x[2 * j + 1]);
+    const Tin* x = reinterpret_cast<const Tin*>(in.p[f]) + row0 * n1;
+    for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) src[q] = mkc<C>((T)x[2 * q], (T)x[2 * q + 1]);
     __syncthreads();
-    stockham_radix2(src, dst, M, twM, false);
-    C* X = out + ((int64_t)f * rows + row) * (M + 1);
-    for (int k = threadIdx.x; k <= M; k += blockDim.x) {
-        C zk = src[k == M ? 0 : k];
-        C zm = src[k == 0 ? 0 : M - k];
+    stockham_rows<C, false>(src, dst, M, nrow, twM);
+    C* X = out + ((int64_t)f * rows + row0) * (M + 1);
+    for (int q = threadIdx.x; q < nrow * (M + 1); q += blockDim.x) {
+        const int r = q / (M + 1), k = q - r * (M + 1);
+        const C* Z = src + (size_t)r * M;
+        C zk = Z[k == M ? 0 : k];
+        C zm = Z[k == 0 ? 0 : M - k];
         C zmc = cconj(zm);
         C e = cscale(cadd(zk, zmc), (T)0.5);
         C d = csub(zk, zmc);
         C w = (k < M) ? twN[k] : mkc<C>((T)-1, (T)0);
         C wd = cmul(w, d);
-        X[k] = mkc<C>(e.x + (T)0.5 * wd.y, e.y - (T)0.5 * wd.x);
+        X[q] = mkc<C>(e.x + (T)0.5 * wd.y, e.y - (T)0.5 * wd.x);
     }
 }
 
@@ -52,48 +57,59 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
                                                             int in_field0) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = n1 >> 1;
+    const int M = n1 >> 1, RB = fft_rows_per_block(M);
     C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + M;
-    const int64_t row = blockIdx.x;
+    C* dst = src + (size_t)RB * M;
+    const int64_t row0 = (int64_t)blockIdx.x * RB;
+    const int nrow = (int)((rows - row0) < RB ? (rows - row0) : RB);
     const int f = blockIdx.y;
-    const C* X = in + ((int64_t)(in_field0 + f) * rows + row) * (M + 1);
-    for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        C xk = X[k], xm = X[M - k];
+    const C* X = in + ((int64_t)(in_field0 + f) * rows + row0) * (M + 1);
+    for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) {
+        const int r = q / M, k = q - r * M;
+        const C* Xr = X + (size_t)r * (M + 1);
+        C xk = Xr[k], xm = Xr[M - k];
         if (k == 0) { xk.y = 0; xm.y = 0; }
         C xmc = cconj(xm);
         C e = cscale(cadd(xk, xmc), (T)0.5);
         C o = cscale(cmulc(csub(xk, xmc), twN[k]), (T)0.5);
-        src[k] = mkc<C>(e.x - o.y, e.y + o.x);
+        src[q] = mkc<C>(e.x - o.y, e.y + o.x);
     }
     __syncthreads();
-    stockham_radix2(src, dst, M, twM, true);
-    Tout* x = reinterpret_cast<Tout*>(out.p[f]) + row * n1;
+    stockham_rows<C, true>(src, dst, M, nrow, twM);
+    Tout* x = reinterpret_cast<Tout*>(out.p[f]) + row0 * n1;
     const T inv = (T)1 / (T)M;
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        x[2 * j] = (Tout)(src[j].x * inv);
-        x[2 * j + 1] = (Tout)(src[j].y * inv);
+    for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) {
+        x[2 * q] = (Tout)(src[q].x * inv);
+        x[2 * q + 1] = (Tout)(src[q].y * inv);
     }
+}
+
+template <typename T>
+static size_t row_fft_smem(int n1) {
+    const int M = n1 / 2;
+    return sizeof(cplx<T>) * 2 * (size_t)fft_rows_per_block(M) * M;
 }
 
 template <typename Tin, typename T>
 static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
-    size_t smem = sizeof(cplx<T>) * (size_t)n1;   // 2 * M complex
+    const size_t smem = row_fft_smem<T>(n1);
     auto kern = k_rfft_rows<Tin, T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)rows, nf);
+    const int RB = fft_rows_per_block(n1 / 2);
+    dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
     kern<<<grid, kRowThreads, smem, s>>>(p, out, n1, rows, t.twM, t.twN);
     return cudaGetLastError();
 }
 
 template <typename T, typename Tout>
 static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, int nf, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
-    size_t smem = sizeof(cplx<T>) * (size_t)n1;
+    const size_t smem = row_fft_smem<T>(n1);
     auto kern = k_irfft_rows<T, Tout>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)rows, nf);
+    const int RB = fft_rows_per_block(n1 / 2);
+    dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
     kern<<<grid, kRowThreads, smem, s>>>(in, p, n1, rows, t.twM, t.twN, f0);
     return cudaGetLastError();
 }

@@ -24,26 +24,92 @@ template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) { re
 template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mkc<C>(a.x, -a.y); }
 template <typename C> __host__ __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mkc<C>(a.x * s, a.y * s); }
 
-// ---------------------------------------------------------------- shared-memory radix-2 Stockham FFT
-template <typename C>
-__device__ __forceinline__ void stockham_radix2(C*& src, C*& dst, int M, const C* __restrict__ twM, bool inverse) {
-    // natural-order in, natural-order out; one __syncthreads per stage
-    for (int Ns = 1; Ns < M; Ns <<= 1) {
-        const int tstride = M / (2 * Ns);
-        for (int j = threadIdx.x; j < (M >> 1); j += blockDim.x) {
-            const int k = j & (Ns - 1);
-            C a = src[j], b = src[j + (M >> 1)];
-            C w = twM[k * tstride];
-            b = inverse ? cmulc(b, w) : cmul(b, w);
-            const int o = ((j - k) << 1) + k;
-            dst[o] = cadd(a, b);
-            dst[o + Ns] = csub(a, b);
+// ---------------------------------------------------------------- shared-memory Stockham FFT (radix 8, 4, 2)
+// Small DFTs in natural order; INV uses W = exp(+2 pi i / R) (no scaling).
+template <typename C, bool INV>
+__device__ __forceinline__ C rot_i(C a) { return INV ? mkc<C>(-a.y, a.x) : mkc<C>(a.y, -a.x); }   // times -i (fwd) / +i (inv)
+
+template <typename C, bool INV>
+__device__ __forceinline__ void sdft2(C* x) { const C t = x[0]; x[0] = cadd(t, x[1]); x[1] = csub(t, x[1]); }
+
+template <typename C, bool INV>
+__device__ __forceinline__ void sdft4(C& x0, C& x1, C& x2, C& x3) {
+    const C a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = rot_i<C, INV>(csub(x1, x3));
+    x0 = cadd(a, c); x2 = csub(a, c); x1 = cadd(b, d); x3 = csub(b, d);
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void sdft8(C* x) {
+    using T = decltype(C::x);
+    C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6], o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+    sdft4<C, INV>(e0, e1, e2, e3);
+    sdft4<C, INV>(o0, o1, o2, o3);
+    const T h = (T)0.70710678118654752440;
+    // o1 W8^1, o2 W8^2, o3 W8^3 (conjugate roots for the inverse)
+    o1 = INV ? mkc<C>(h * (o1.x - o1.y), h * (o1.x + o1.y)) : mkc<C>(h * (o1.x + o1.y), h * (o1.y - o1.x));
+    o2 = rot_i<C, INV>(o2);
+    o3 = INV ? mkc<C>(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : mkc<C>(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+    x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
+    x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
+    x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
+    x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
+}
+
+// One radix-R Stockham pass over nrow rows of M points (rows contiguous): butterfly j of a
+// row (0 <= j < M/R, k = j mod Ns) takes src[j + r M/R] W_{R Ns}^{r k}, r = 0..R-1, does an
+// R-point DFT over r and writes output r to dst[(j - k) R + k + r Ns].
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst, int M, int Ns, int nrow,
+                                              const C* __restrict__ tw) {
+    const int nb = M / R, ts = M / (R * Ns);
+    for (int q = threadIdx.x; q < nb * nrow; q += blockDim.x) {
+        const int row = q / nb, j = q - row * nb, k = j & (Ns - 1);
+        const C* s = src + (size_t)row * M;
+        C* d = dst + (size_t)row * M;
+        C x[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            x[r] = s[j + r * nb];
+            if (r > 0 && Ns > 1) {
+                const C w = tw[r * k * ts];
+                x[r] = INV ? cmulc(x[r], w) : cmul(x[r], w);
+            }
         }
+        if (R == 8) sdft8<C, INV>(x);
+        else if (R == 4) sdft4<C, INV>(x[0], x[1], x[2], x[3]);
+        else sdft2<C, INV>(x);
+        const int o = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; r++) d[o + r * Ns] = x[r];
+    }
+}
+
+// natural-order in, natural-order out FFT of nrow rows of M = 2^m points held in shared
+// memory (src); radix-8 passes then one radix-4 or radix-2 pass; one __syncthreads per pass.
+// On return src points at the result.  tw[j] = W_M^j, j < M.
+template <typename C, bool INV>
+__device__ __forceinline__ void stockham_rows(C*& src, C*& dst, int M, int nrow, const C* __restrict__ tw) {
+    int Ns = 1;
+    while (Ns * 8 <= M) {
+        stockham_pass<C, 8, INV>(src, dst, M, Ns, nrow, tw);
+        __syncthreads();
+        C* t = src; src = dst; dst = t;
+        Ns *= 8;
+    }
+    if (Ns * 4 <= M) {
+        stockham_pass<C, 4, INV>(src, dst, M, Ns, nrow, tw);
+        __syncthreads();
+        C* t = src; src = dst; dst = t;
+    } else if (Ns * 2 <= M) {
+        stockham_pass<C, 2, INV>(src, dst, M, Ns, nrow, tw);
         __syncthreads();
         C* t = src; src = dst; dst = t;
     }
 }
 
+// rows of M points one block of 256 threads transforms together (one radix-8 pass then
+// has about 256 butterflies)
+__host__ __device__ __forceinline__ int fft_rows_per_block(int M) { return M >= 2048 ? 1 : 2048 / M; }
 
 // ---------------------------------------------------------------- tables
 // Per-mode tables for kappa = 0..n1/2, computed in FP64 on the host and rounded once.

@@ -37,20 +37,23 @@ struct QPtrs { void* p[9]; };
 
 constexpr int kQThreads = 256;
 
+// complex transforms along z of RB = fft_rows_per_block(nz) rows per block
 template <typename T>
 __global__ void __launch_bounds__(kQThreads) k_qfft_fwd(QPtrs in, cplx<T>* __restrict__ spec, int nz, int nr,
                                                        const cplx<T>* __restrict__ tw) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int RB = fft_rows_per_block(nz);
     C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + nz;
-    const int row = blockIdx.x, f = blockIdx.y;
-    const C* x = reinterpret_cast<const C*>(in.p[f]) + (int64_t)row * nz;
-    for (int j = threadIdx.x; j < nz; j += blockDim.x) src[j] = x[j];
+    C* dst = src + (size_t)RB * nz;
+    const int row0 = blockIdx.x * RB, f = blockIdx.y;
+    const int nrow = (nr - row0) < RB ? (nr - row0) : RB;
+    const C* x = reinterpret_cast<const C*>(in.p[f]) + (int64_t)row0 * nz;
+    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) src[q] = x[q];
     __syncthreads();
-    stockham_radix2(src, dst, nz, tw, false);
-    C* X = spec + ((int64_t)f * nr + row) * nz;
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) X[k] = src[k];
+    stockham_rows<C, false>(src, dst, nz, nrow, tw);
+    C* X = spec + ((int64_t)f * nr + row0) * nz;
+    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) X[q] = src[q];
 }
 
 template <typename T>
@@ -58,16 +61,18 @@ __global__ void __launch_bounds__(kQThreads) k_qfft_inv(const cplx<T>* __restric
                                                        const cplx<T>* __restrict__ tw) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int RB = fft_rows_per_block(nz);
     C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + nz;
-    const int row = blockIdx.x, f = blockIdx.y;
-    const C* X = spec + ((int64_t)f * nr + row) * nz;
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) src[k] = X[k];
+    C* dst = src + (size_t)RB * nz;
+    const int row0 = blockIdx.x * RB, f = blockIdx.y;
+    const int nrow = (nr - row0) < RB ? (nr - row0) : RB;
+    const C* X = spec + ((int64_t)f * nr + row0) * nz;
+    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) src[q] = X[q];
     __syncthreads();
-    stockham_radix2(src, dst, nz, tw, true);
-    C* x = reinterpret_cast<C*>(out.p[f]) + (int64_t)row * nz;
+    stockham_rows<C, true>(src, dst, nz, nrow, tw);
+    C* x = reinterpret_cast<C*>(out.p[f]) + (int64_t)row0 * nz;
     const T inv = (T)1 / (T)nz;
-    for (int j = threadIdx.x; j < nz; j += blockDim.x) x[j] = cscale(src[j], inv);
+    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) x[q] = cscale(src[q], inv);
 }
 
 // i m / r times a
@@ -172,7 +177,7 @@ static hyb_status create_t(hyb_grid* g) {
     HYB_CUDA_TRY(cudaMalloc(&P->tw, sizeof(C) * nz));
     HYB_CUDA_TRY(cudaMemcpy(P->tw, tw.data(), sizeof(C) * nz, cudaMemcpyHostToDevice));
     HYB_CUDA_TRY(cudaMalloc(&P->spec, sizeof(C) * 9 * (size_t)nr * nz));
-    const size_t smem = sizeof(C) * 2 * (size_t)nz;
+    const size_t smem = sizeof(C) * 2 * (size_t)fft_rows_per_block(nz) * nz;
     HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return HYB_OK;
@@ -184,16 +189,17 @@ static hyb_status advance_t(hyb_grid* g, int nsteps) {
     QPlan<T>* P = reinterpret_cast<QPlan<T>*>(g->qtab);
     const hyb_grid_desc& d = g->d;
     const int nz = d.n1, nr = d.n2;
-    const size_t smem = sizeof(C) * 2 * (size_t)nz;
+    const size_t smem = sizeof(C) * 2 * (size_t)fft_rows_per_block(nz) * nz;
+    const int RB = fft_rows_per_block(nz), nblk = (nr + RB - 1) / RB;
     QPtrs fin{}, fout{};
     for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; fin.p[6 + c] = g->J[c]; }
     for (int c = 0; c < 3; c++) { fout.p[c] = g->E[c]; fout.p[3 + c] = g->B[c]; }
     for (int s = 0; s < nsteps; s++) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
-        k_qfft_fwd<T><<<dim3(nr, 9), kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, P->tw);
+        k_qfft_fwd<T><<<dim3(nblk, 9), kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, P->tw);
         k_qfaraday<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
         k_qampere<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
-        k_qfft_inv<T><<<dim3(nr, 6), kQThreads, smem, g->stream>>>(P->spec, fout, nz, nr, P->tw);
+        k_qfft_inv<T><<<dim3(nblk, 6), kQThreads, smem, g->stream>>>(P->spec, fout, nz, nr, P->tw);
         HYB_CUDA_TRY(cudaGetLastError());
         if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
     }
