@@ -73,7 +73,7 @@ typedef struct {
     int yee_mode;         /* 1: [k]1 = sin(k1 dx1/2)/(dx1/2) (recovers the Yee solver, Sec. 2.1) */
     double ampere;        /* coefficient of j in Ampere's law; 0 selects 4 pi */
     int path;             /* 0: fastest available, as measured on GB300 (fused where it applies,
-                                else path 3 for precision 32 with 16 <= n1 <= 64, else path 1);
+                                else path 1, faster than path 3 at every n1 measured);
                              1: three-pass (FFT, update, inverse FFT);
                              2: fused single-pass (precision 32, dims 2, n1 in 512..4096);
                              3: three-pass with the x1 transform as a dense DFT matrix product on

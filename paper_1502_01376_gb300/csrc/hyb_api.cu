@@ -183,10 +183,9 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
     hyb_grid* g = new hyb_grid();
     g->d = d;
     g->stream = (cudaStream_t)stream;
-    // auto: the fused single pass where it applies; otherwise the three-pass advance with
-    // the x1 transform that measured faster on GB300 (DFT-GEMM for FP32 n1 <= 64, radix FFT above)
-    const bool dft_auto = d.precision == 32 && d.dims != 20 && d.n1 >= 16 && d.n1 <= 64;
-    g->path = (d.path == 0) ? (fused_ok ? 2 : dft_auto ? 3 : 1) : d.path;
+    // auto: the fused single pass where it applies; otherwise the three-pass advance with the
+    // radix FFT, which measured faster on GB300 than the DFT-GEMM (path 3) at every n1 from 16 to 1024
+    g->path = (d.path == 0) ? (fused_ok ? 2 : 1) : d.path;
     g->rows = (int64_t)d.n2 * d.n3;
     g->cells = g->rows * d.n1;
     g->nk = d.n1 / 2 + 1;

@@ -73,11 +73,11 @@ def test_dftgemm_rejects_unsupported():
 
 
 def test_auto_path_picks_measured_transform():
-    """Path 0 takes the DFT-GEMM for FP32 n1 <= 64 (faster there on GB300) and
-    the radix FFT above; FP64 always takes the radix FFT."""
+    """Path 0 takes the radix FFT on the three-pass path (measured faster than the
+    DFT-GEMM at every n1 from 16 to 1024) and the fused kernel where it applies."""
     need_gpu()
     hyb = hyb_module()
-    for n1, prec, want in ((32, 32, 3), (64, 32, 3), (128, 32, 1), (32, 64, 1)):
+    for n1, prec, want in ((32, 32, 1), (64, 32, 1), (128, 32, 1), (32, 64, 1), (512, 32, 2)):
         w = wl.Workload("t", 2, n1, 8, dx1=0.2, dx2=0.25, dt=0.05, precision=prec, seed=1)
         g = hyb.Grid(hyb.desc_from_workload(w, path=0))
         assert g.path == want, (n1, prec, g.path)
