@@ -81,7 +81,7 @@ def kernel_source_hash():
 def profiled_traffic(cells):
     """dram bytes per launch of the fused kernel from the committed ncu summary,
     if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "fused2d_drift_plasma_4096x1024.md")
+    path = os.path.join(ROOT, "profiles", "fused_tm_drift_plasma_4096x1024.md")
     if not os.path.exists(path):
         return None
     src_hash, per_cell = None, None
@@ -162,7 +162,7 @@ def replica_aggregate(ms, kms, cells, world, device):
     return ms, kms, world * cells / (ms / 1e3)
 
 
-def cpu_baseline_sample(workload, budget_s=15.0):
+def cpu_baseline_sample(workload, budget_s=12.0):
     """The oracle as it stands on a bounded sample of the workload: the full
     4096-point x1 rows on a 4096 x R periodic strip, timed on the host cores."""
     import numpy as np
@@ -180,7 +180,7 @@ def cpu_baseline_sample(workload, budget_s=15.0):
     while True:
         oracle.step(g, E, B, J, 1)
         n += 1
-        if time.perf_counter() - t0 > budget_s or n >= 200:
+        if time.perf_counter() - t0 > budget_s or n >= 5000:
             break
     dt = time.perf_counter() - t0
     return {"value": w.cells * n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
