@@ -162,9 +162,22 @@ HYB_API hyb_status hyb_advance_host(hyb_grid* g, void* const E[3], void* const B
  *   out[8]     rms of G. */
 HYB_API hyb_status hyb_diag(hyb_grid* g, double out[9]);
 
-/* Synchronises the grid's stream and reports (and clears) the device-side data
- * flag set by hyb_deposit for out-of-range particles: HYB_OK or HYB_EDATA. */
+/* Synchronises the grid's stream and reports (and clears) the device-side flag:
+ * HYB_EDATA when hyb_deposit skipped out-of-range particles, HYB_ETIMEOUT when a
+ * bounded device wait of the fused advance (halo flag or row staging) gave up;
+ * otherwise HYB_OK. */
 HYB_API hyb_status hyb_check(hyb_grid* g);
+
+/* Self-test of the bounded device-side waits (the paper has no counterpart).
+ * Runs one probe kernel that waits on a condition nothing satisfies, with the
+ * same wait code the fused advance uses: which = 0, the release/acquire flag
+ * wait of the in-kernel halo exchange; which = 1, the mbarrier wait of the row
+ * staging.  The limit is `seconds` at the device's clock rate.  Returns
+ * HYB_ETIMEOUT when the wait gave up as designed (the expected result), HYB_OK
+ * if the condition was met, HYB_EINVAL for which not in {0, 1} or seconds not
+ * in (0, 10], HYB_ECUDA on a CUDA error.  Synchronous on `stream`; allocates
+ * and frees two ints of device memory. */
+HYB_API hyb_status hyb_wait_selftest(int which, double seconds, void* stream);
 
 /* Frees the grid's tables and scratch (not the caller's arrays). NULL is a no-op. */
 HYB_API hyb_status hyb_destroy_grid(hyb_grid* g);

@@ -138,11 +138,13 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
-// bounded wait of one thread for flag >= epoch; on time-out sets bit 2 of *err and gives up
-__device__ __forceinline__ void wait_flag(const int* f, int epoch, int* err) {
+// bounded wait of one thread for flag >= epoch; after `limit` clock cycles (about 2 s
+// by default) it sets bit 1 of *err and gives up
+constexpr long long kWaitCycles = 4000000000LL;
+__device__ __forceinline__ void wait_flag(const int* f, int epoch, int* err, long long limit = kWaitCycles) {
     const long long t0 = clock64();
     while (ld_acquire(f) < epoch) {
-        if (clock64() - t0 > 4000000000LL) { atomicOr(err, 2); return; }
+        if (clock64() - t0 > limit) { if (err) atomicOr(err, 2); return; }
         __nanosleep(256);
     }
 }

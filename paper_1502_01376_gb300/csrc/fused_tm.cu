@@ -56,7 +56,7 @@ constexpr int OFF_MISC = OFF_BAR + 3 * 8;                // TMEM base address, a
 constexpr int SMEM = OFF_MISC + 16;
 constexpr uint32_t TMEM_COLS = 512;                      // slots 2 x 160, symbols 2 x 32
 constexpr int SYM_COL = 320;                             // per-mode symbols: S (16 words), cj1 (8), cj (8)
-constexpr long long WAIT_CYCLES = 4000000000LL;          // about 2 s at 2 GHz
+constexpr long long WAIT_CYCLES = kWaitCycles;            // about 2 s at 2 GHz
 }  // namespace tmk
 
 // ------------------------------------------------------------------ TMEM, mbarrier and bulk-copy primitives
@@ -131,12 +131,13 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 
 // bounded wait for phase `parity` of an mbarrier; on time-out sets bit 1 of *err
 // and the CTA's abort flag (later waits then return at once)
-__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
+__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag,
+                                          long long limit = tmk::WAIT_CYCLES) {
     if (mbar_try_wait(bar, parity)) return;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return;
-        if (clock64() - t0 > tmk::WAIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             if (err) atomicOr(err, 2);
             *abort_flag = 1;
             return;
@@ -144,6 +145,65 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* er
     }
 }
 
+
+
+// ------------------------------------------------------------------ round schedule of this kernel
+// Group g owns component g of E and B: it transforms E_g and B_g, applies the
+// update of E_g (Ampere, with j_g) and of B_g (Faraday), and writes both back.
+// Rows outside the strip: h = p0 - 1 (from the fields in flag mode, else from the
+// halo buffer [E1, E2, E3, B1, B3 of h; E1, E3 of p1]).
+//   prologue  P1: g0 E1(p0), g1 E2(h), g2 E3(p0)   P2: g0 E1(h), g2 E3(h)
+//             P3: g0 B1(h) (Faraday), g2 B3(h) (Faraday)
+//   row p     R1: g0 E1(p+1), g1 E2(p), g2 E3(p+1)   R2: B_g(p), Faraday
+//             R3: j_g(p), Ampere into E_g(p)          R4: inverse E_g(p)   R5: inverse B_g(p)
+// Every slot is written by one group only, so the whole CTA synchronises only where
+// slots pass between groups: after R1 and R2 (and after the prologue rounds).
+__device__ __forceinline__ Job tm_job(const FusedInst& a, int N, int p0, int p1, int ri, int g) {
+    Job j{J_IDLE, X_STORE, 0, 0, nullptr, nullptr};
+    const int h = p0 - 1;
+    if (ri < 3) {
+        if (ri == 0) { j.kind = J_FWD; j.slot = (g == 0) ? sE1(p0) : (g == 1) ? sE2 : sE3(p0); }
+        else if (ri == 1) { if (g != 1) { j.kind = J_FWD; j.slot = (g == 0) ? sE1(h) : sE3(h); } }
+        else if (g != 1) { j.kind = J_FWD; j.epi = (g == 0) ? X_B1 : X_B3; j.slot = (g == 0) ? sB1(h) : sB3(h); j.row = h; }
+        return j;
+    }
+    const int r = (ri - 3) % 5, p = p0 + (ri - 3) / 5;
+    if (p >= p1) return j;
+    j.row = p;
+    const int sE = (g == 0) ? sE1(p) : (g == 1) ? sE2 : sE3(p);
+    const int sB = (g == 0) ? sB1(p) : (g == 1) ? sB2 : sB3(p);
+    if (r == 0) { j.kind = J_FWD; j.slot = (g == 0) ? sE1(p + 1) : (g == 1) ? sE2 : sE3(p + 1); }
+    else if (r == 1) { j.kind = J_FWD; j.epi = X_B1 + g; j.slot = sB; }
+    else if (r == 2) { j.kind = J_FWD; j.epi = X_J1 + g; j.slot = sE; }
+    else { j.kind = J_INV; j.slot = (r == 3) ? sE : sB; j.dst = ((r == 3) ? a.E[g] : a.B[g]) + (size_t)p * N; }
+    return j;
+}
+__device__ __forceinline__ int tm_npro(int g) { return g == 1 ? 1 : 3; }
+// source row of the idx-th forward transform of group g in a work item; *direct is set
+// when it is the next strip's published first row (read with plain loads after the flag)
+__device__ __forceinline__ const float* tm_src(const FusedInst& a, int N, int strip, int p0, int p1, int g, int idx,
+                                               bool fm, int next, bool* direct) {
+    *direct = false;
+    const float* halo = a.halo + (size_t)strip * 7 * N;
+    if (idx < tm_npro(g)) {
+        const int h = (p0 - 1 + a.n2) % a.n2;
+        if (g == 1) return fm ? a.E[1] + (size_t)h * N : halo + 1 * N;
+        const int c = (g == 0) ? 0 : 2;
+        if (idx == 0) return a.E[c] + (size_t)p0 * N;
+        if (idx == 1) return fm ? a.E[c] + (size_t)h * N : halo + c * N;
+        return fm ? a.B[c] + (size_t)h * N : halo + (g == 0 ? 3 : 4) * N;
+    }
+    const int q = idx - tm_npro(g);
+    const int p = p0 + q / 3, r = q % 3;
+    if (p >= p1) return nullptr;
+    if (r == 1) return a.B[g] + (size_t)p * N;
+    if (r == 2) return a.J[g] + (size_t)p * N;
+    if (g == 1) return a.E[1] + (size_t)p * N;
+    const int c = (g == 0) ? 0 : 2;
+    if (p + 1 < p1) return a.E[c] + (size_t)(p + 1) * N;
+    if (fm) { *direct = true; return a.halo + ((size_t)next * 7 + (g == 0 ? 0 : 1)) * N; }
+    return halo + (g == 0 ? 5 : 6) * N;
+}
 
 // ------------------------------------------------------------------ packed FP32 pairs (f32x2): one instruction
 // for the two components of a complex add, subtract or scale
@@ -350,15 +410,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
     auto cta_sync_after = [&](int ri) {
         if (ri < 3) return ri >= 1 || fm;
         const int r = (ri - 3) % 5;
-        return r == 0 || r == 1 || r == 4;
-    };
-    // the forward source read directly (not staged): the next strip's published copy
-    auto is_direct = [&](int idx) {
-        if (!fm) return false;
-        const int npro = (g == 0) ? 3 : 2;
-        if (idx < npro || g == 2) return false;
-        const int q = idx - npro;
-        return (q % 3) == 0 && p0 + q / 3 + 1 == p1;
+        return r == 0 || r == 1;
     };
     if (it.x != cur_inst) {
         // per-instance symbols of this thread's modes into TMEM (written once by group 0;
@@ -384,8 +436,8 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
     }
     int fidx = 0;
     // source of this group's next forward transform; the first one is staged now
-    const float* nsrc = fwd_src(a, N, strip, p0, p1, g, 0, fm, next);
-    bool ndirect = is_direct(0);
+    bool ndirect = false;
+    const float* nsrc = tm_src(a, N, strip, p0, p1, g, 0, fm, next, &ndirect);
     pending = nsrc != nullptr && !ndirect;
     if (pending && t == 0) {
         mbar_expect_tx(bar, 4 * N);
@@ -397,7 +449,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
             if (tid == 0) wait_flag(fb.flags + 2 * next + (ri == ri_wait_read ? 1 : 0), fb.epoch, fb.err);
             __syncthreads();
         }
-        const Job j = job_of(a, N, strip, p0, p1, ri, g);
+        const Job j = tm_job(a, N, p0, p1, ri, g);
         float2* X = xbuf + (g * 2 + (tc & 1)) * XS;
         float2* Y = xbuf + (g * 2 + ((tc & 1) ^ 1)) * XS;
         if (j.kind == J_FWD) {
@@ -414,9 +466,9 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
 #pragma unroll
                 for (int n = 0; n < 8; n++) v[n] = stg[t + 256 * n];
             }
-            if (fm && ri == 0 && g < 2) {
-                // publish E1 (g = 0) or E3 (g = 1) of the strip's first row for the previous strip
-                float2* h = reinterpret_cast<float2*>(const_cast<float*>(a.halo) + ((size_t)strip * 7 + g) * N);
+            if (fm && ri == 0 && g != 1) {
+                // publish E1 (g = 0) or E3 (g = 2) of the strip's first row for the previous strip
+                float2* h = reinterpret_cast<float2*>(const_cast<float*>(a.halo) + ((size_t)strip * 7 + (g == 0 ? 0 : 1)) * N);
 #pragma unroll
                 for (int n = 0; n < 8; n++) h[t + 256 * n] = v[n];
             }
@@ -432,8 +484,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
             gsync();
             fidx++;
             // the group's staging row is free: start the next forward's row
-            nsrc = fwd_src(a, N, strip, p0, p1, g, fidx, fm, next);
-            ndirect = is_direct(fidx);
+            nsrc = tm_src(a, N, strip, p0, p1, g, fidx, fm, next, &ndirect);
             pending = nsrc != nullptr && !ndirect;
             if (pending && t == 0) {
                 fence_proxy_async_smem();
@@ -686,6 +737,29 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
     __syncthreads();
     tm_fence_after();
     if (warp == 0) tm_dealloc(tbase, TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ self-test of the bounded waits
+// which = 0: the release/acquire flag wait of the halo exchange, on a flag nothing sets;
+// which = 1: the mbarrier wait of the row staging, on a phase nothing completes.
+// Both must give up after `limit` cycles and report through *err.
+__global__ void k_wait_probe(const int* flag, int* err, long long limit, int which) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    if (which == 0) {
+        wait_flag(flag, 1, err, limit);
+    } else {
+        mbar_init(smem_addr(&bar), 1);
+        mbar_fence_init();
+        abort_flag = 0;
+        mbar_wait(smem_addr(&bar), 0, err, &abort_flag, limit);
+    }
+}
+
+cudaError_t wait_probe(int* dflag, int* derr, long long limit, int which, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(dflag, derr, limit, which);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ host side

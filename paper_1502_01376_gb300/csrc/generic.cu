@@ -13,6 +13,7 @@
 namespace hyb {
 
 constexpr int kRowThreads = 256;
+constexpr int kModeRows = 8;          // per-mode kernels: blocks of 32 modes x 8 rows
 
 struct RowPtrs { const void* p[9]; };
 struct RowPtrsW { void* p[9]; };
@@ -21,10 +22,10 @@ struct RowPtrsW { void* p[9]; };
 // A block transforms RB = fft_rows_per_block(M) consecutive rows of one field.
 template <typename Tin, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* __restrict__ out, int n1, int64_t rows,
-                                                           const cplx<T>* __restrict__ twM, const cplx<T>* __restrict__ twN) {
+                                                           const cplx<T>* __restrict__ twM, const cplx<T>* __restrict__ twN, int RB) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = n1 >> 1, RB = fft_rows_per_block(M);
+    const int M = n1 >> 1;
     C* src = reinterpret_cast<C*>(smem_raw);
     C* dst = src + (size_t)RB * M;
     const int64_t row0 = (int64_t)blockIdx.x * RB;
@@ -54,10 +55,10 @@ __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* 
 template <typename T, typename Tout>
 __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __restrict__ in, RowPtrsW out, int n1, int64_t rows,
                                                             const cplx<T>* __restrict__ twM, const cplx<T>* __restrict__ twN,
-                                                            int in_field0) {
+                                                            int in_field0, int RB) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = n1 >> 1, RB = fft_rows_per_block(M);
+    const int M = n1 >> 1;
     C* src = reinterpret_cast<C*>(smem_raw);
     C* dst = src + (size_t)RB * M;
     const int64_t row0 = (int64_t)blockIdx.x * RB;
@@ -85,32 +86,29 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
 }
 
 template <typename T>
-static size_t row_fft_smem(int n1) {
-    const int M = n1 / 2;
-    return sizeof(cplx<T>) * 2 * (size_t)fft_rows_per_block(M) * M;
-}
+static size_t row_fft_smem(int n1, int RB) { return sizeof(cplx<T>) * 2 * (size_t)RB * (n1 / 2); }
 
 template <typename Tin, typename T>
 static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
-    const size_t smem = row_fft_smem<T>(n1);
+    const int RB = fft_rows_per_launch(n1 / 2, rows * nf);
+    const size_t smem = row_fft_smem<T>(n1, RB);
     auto kern = k_rfft_rows<Tin, T>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fft_smem<T>(n1, fft_rows_per_block(n1 / 2)));
     if (e != cudaSuccess) return e;
-    const int RB = fft_rows_per_block(n1 / 2);
     dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
-    kern<<<grid, kRowThreads, smem, s>>>(p, out, n1, rows, t.twM, t.twN);
+    kern<<<grid, kRowThreads, smem, s>>>(p, out, n1, rows, t.twM, t.twN, RB);
     return cudaGetLastError();
 }
 
 template <typename T, typename Tout>
 static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, int nf, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
-    const size_t smem = row_fft_smem<T>(n1);
+    const int RB = fft_rows_per_launch(n1 / 2, rows * nf);
+    const size_t smem = row_fft_smem<T>(n1, RB);
     auto kern = k_irfft_rows<T, Tout>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fft_smem<T>(n1, fft_rows_per_block(n1 / 2)));
     if (e != cudaSuccess) return e;
-    const int RB = fft_rows_per_block(n1 / 2);
     dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
-    kern<<<grid, kRowThreads, smem, s>>>(in, p, n1, rows, t.twM, t.twN, f0);
+    kern<<<grid, kRowThreads, smem, s>>>(in, p, n1, rows, t.twM, t.twN, f0, RB);
     return cudaGetLastError();
 }
 
@@ -142,14 +140,20 @@ template <typename T, bool D3>
 __global__ void __launch_bounds__(kRowThreads) k_faraday(cplx<T>* __restrict__ spec, int nk, int n2, int n3, int64_t rows,
                                                          const cplx<T>* __restrict__ S, T a2, T a3) {
     using C = cplx<T>;
-    const int64_t r = blockIdx.x;
-    const int i2 = (int)(r % n2), i3 = (int)(r / n2);
+    // block (32 modes) x (8 rows of one x3 plane); consecutive blocks walk the modes of a
+    // row group first: blockIdx.x = (i3 * g2 + i2 / 8) * nch + k / 32
+    const int g2 = (n2 + kModeRows - 1) / kModeRows, nch = (nk + 31) / 32;
+    const int rg = blockIdx.x / nch, ch = blockIdx.x - rg * nch;
+    const int i3 = rg / g2, i2 = (rg - i3 * g2) * kModeRows + threadIdx.y;
+    const int k = ch * 32 + threadIdx.x;
+    if (i2 >= n2 || k >= nk) return;
+    const int64_t r = (int64_t)i3 * n2 + i2;
     const int64_t rp2 = (int64_t)i3 * n2 + (i2 + 1 == n2 ? 0 : i2 + 1);
     const int64_t rp3 = D3 ? (int64_t)(i3 + 1 == n3 ? 0 : i3 + 1) * n2 + i2 : r;
     const int64_t fs = rows * nk;
     C* E1 = spec; C* E2 = spec + fs; C* E3 = spec + 2 * fs;
     C* B1 = spec + 3 * fs; C* B2 = spec + 4 * fs; C* B3 = spec + 5 * fs;
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    {
         const int64_t i = r * nk + k, ip2 = rp2 * nk + k, ip3 = rp3 * nk + k;
         C e1 = E1[i], e2 = E2[i], e3 = E3[i], s = S[k];
         C d2e3 = cscale(csub(E3[ip2], e3), a2);
@@ -175,15 +179,19 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(cplx<T>* __restrict__ sp
                                                         const cplx<T>* __restrict__ S, const T* __restrict__ cj1,
                                                         const T* __restrict__ cj, T a2, T a3) {
     using C = cplx<T>;
-    const int64_t r = blockIdx.x;
-    const int i2 = (int)(r % n2), i3 = (int)(r / n2);
+    const int g2 = (n2 + kModeRows - 1) / kModeRows, nch = (nk + 31) / 32;
+    const int rg = blockIdx.x / nch, ch = blockIdx.x - rg * nch;
+    const int i3 = rg / g2, i2 = (rg - i3 * g2) * kModeRows + threadIdx.y;
+    const int k = ch * 32 + threadIdx.x;
+    if (i2 >= n2 || k >= nk) return;
+    const int64_t r = (int64_t)i3 * n2 + i2;
     const int64_t rm2 = (int64_t)i3 * n2 + (i2 == 0 ? n2 - 1 : i2 - 1);
     const int64_t rm3 = D3 ? (int64_t)(i3 == 0 ? n3 - 1 : i3 - 1) * n2 + i2 : r;
     const int64_t fs = rows * nk;
     C* E1 = spec; C* E2 = spec + fs; C* E3 = spec + 2 * fs;
     const C* B1 = spec + 3 * fs; const C* B2 = spec + 4 * fs; const C* B3 = spec + 5 * fs;
     const C* J1 = spec + 6 * fs; const C* J2 = spec + 7 * fs; const C* J3 = spec + 8 * fs;
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    {
         const int64_t i = r * nk + k, im2 = rm2 * nk + k, im3 = rm3 * nk + k;
         C s = S[k];
         C sm = mkc<C>(-s.x, s.y);          // -conj(S)
@@ -241,12 +249,13 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
         } else {
             HYB_CUDA_TRY((launch_rfft<T, T>(fin, 9, spec, n1, rows, t, g->stream)));
         }
+        const dim3 mgrid((unsigned)((int64_t)g->d.n3 * ((g->d.n2 + kModeRows - 1) / kModeRows) * ((nk + 31) / 32))), mblk(32, kModeRows);
         if (d3) {
-            k_faraday<T, true><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
-            k_ampere<T, true><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, t.cj1, t.cj, a2, a3);
+            k_faraday<T, true><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
+            k_ampere<T, true><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, t.cj1, t.cj, a2, a3);
         } else {
-            k_faraday<T, false><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, a2, a3);
-            k_ampere<T, false><<<(unsigned)rows, kRowThreads, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, t.cj1, t.cj, a2, a3);
+            k_faraday<T, false><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, a2, a3);
+            k_ampere<T, false><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, t.cj1, t.cj, a2, a3);
         }
         HYB_CUDA_TRY(cudaGetLastError());
         if (g->path == 3) {

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "hyb_internal.cuh"
+#include "fused_api.cuh"
 
 namespace hyb {
 
@@ -304,6 +305,28 @@ hyb_status hyb_check(hyb_grid* g) {
     HYB_CUDA_TRY(cudaMemcpy(&h, g->dflag, sizeof(int), cudaMemcpyDeviceToHost));
     HYB_CUDA_TRY(cudaMemset(g->dflag, 0, sizeof(int)));
     if (h & 1) { set_error("hyb_deposit skipped particles outside the documented offset ranges"); return HYB_EDATA; }
+    if (h & 2) { set_error("a bounded device-side wait gave up"); return HYB_ETIMEOUT; }
+    return HYB_OK;
+}
+
+hyb_status hyb_wait_selftest(int which, double seconds, void* stream) {
+    if ((which != 0 && which != 1) || !(seconds > 0.0 && seconds <= 10.0)) {
+        set_error("hyb_wait_selftest: which must be 0 or 1 and seconds in (0, 10]");
+        return HYB_EINVAL;
+    }
+    int dev = 0, khz = 0;
+    HYB_CUDA_TRY(cudaGetDevice(&dev));
+    HYB_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    int* d = nullptr;
+    HYB_CUDA_TRY(cudaMalloc(&d, 2 * sizeof(int)));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = wait_probe(d, d + 1, (long long)(seconds * 1e3 * (double)khz), which, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "hyb_wait_selftest");
     if (h & 2) { set_error("a bounded device-side wait gave up"); return HYB_ETIMEOUT; }
     return HYB_OK;
 }

@@ -108,8 +108,14 @@ __device__ __forceinline__ void stockham_rows(C*& src, C*& dst, int M, int nrow,
 }
 
 // rows of M points one block of 256 threads transforms together (one radix-8 pass then
-// has about 256 butterflies)
+// has about 256 butterflies) ...
 __host__ __device__ __forceinline__ int fft_rows_per_block(int M) { return M >= 2048 ? 1 : 2048 / M; }
+// ... reduced for small launches so that there are at least about 600 blocks (4 per SM)
+__host__ __forceinline__ int fft_rows_per_launch(int M, int64_t total_rows) {
+    int rb = fft_rows_per_block(M);
+    while (rb > 1 && total_rows / rb < 600) rb >>= 1;
+    return rb;
+}
 
 // ---------------------------------------------------------------- tables
 // Per-mode tables for kappa = 0..n1/2, computed in FP64 on the host and rounded once.

@@ -40,10 +40,9 @@ constexpr int kQThreads = 256;
 // complex transforms along z of RB = fft_rows_per_block(nz) rows per block
 template <typename T>
 __global__ void __launch_bounds__(kQThreads) k_qfft_fwd(QPtrs in, cplx<T>* __restrict__ spec, int nz, int nr,
-                                                       const cplx<T>* __restrict__ tw) {
+                                                       const cplx<T>* __restrict__ tw, int RB) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int RB = fft_rows_per_block(nz);
     C* src = reinterpret_cast<C*>(smem_raw);
     C* dst = src + (size_t)RB * nz;
     const int row0 = blockIdx.x * RB, f = blockIdx.y;
@@ -58,10 +57,9 @@ __global__ void __launch_bounds__(kQThreads) k_qfft_fwd(QPtrs in, cplx<T>* __res
 
 template <typename T>
 __global__ void __launch_bounds__(kQThreads) k_qfft_inv(const cplx<T>* __restrict__ spec, QPtrs out, int nz, int nr,
-                                                       const cplx<T>* __restrict__ tw) {
+                                                       const cplx<T>* __restrict__ tw, int RB) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int RB = fft_rows_per_block(nz);
     C* src = reinterpret_cast<C*>(smem_raw);
     C* dst = src + (size_t)RB * nz;
     const int row0 = blockIdx.x * RB, f = blockIdx.y;
@@ -189,17 +187,17 @@ static hyb_status advance_t(hyb_grid* g, int nsteps) {
     QPlan<T>* P = reinterpret_cast<QPlan<T>*>(g->qtab);
     const hyb_grid_desc& d = g->d;
     const int nz = d.n1, nr = d.n2;
-    const size_t smem = sizeof(C) * 2 * (size_t)fft_rows_per_block(nz) * nz;
-    const int RB = fft_rows_per_block(nz), nblk = (nr + RB - 1) / RB;
+    const int RB = fft_rows_per_launch(nz, (int64_t)nr * 6), nblk = (nr + RB - 1) / RB;
+    const size_t smem = sizeof(C) * 2 * (size_t)RB * nz;
     QPtrs fin{}, fout{};
     for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; fin.p[6 + c] = g->J[c]; }
     for (int c = 0; c < 3; c++) { fout.p[c] = g->E[c]; fout.p[3 + c] = g->B[c]; }
     for (int s = 0; s < nsteps; s++) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
-        k_qfft_fwd<T><<<dim3(nblk, 9), kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, P->tw);
+        k_qfft_fwd<T><<<dim3(nblk, 9), kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, P->tw, RB);
         k_qfaraday<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
         k_qampere<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
-        k_qfft_inv<T><<<dim3(nblk, 6), kQThreads, smem, g->stream>>>(P->spec, fout, nz, nr, P->tw);
+        k_qfft_inv<T><<<dim3(nblk, 6), kQThreads, smem, g->stream>>>(P->spec, fout, nz, nr, P->tw, RB);
         HYB_CUDA_TRY(cudaGetLastError());
         if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
     }

@@ -125,6 +125,8 @@ def lib():
             L.hyb_mlp_destroy.restype = S
             L.hyb_launches_per_step.argtypes = [_V]
             L.hyb_launches_per_step.restype = ctypes.c_int
+            L.hyb_wait_selftest.argtypes = [ctypes.c_int, ctypes.c_double, _V]
+            L.hyb_wait_selftest.restype = S
             _lib = L
     return _lib
 
@@ -201,6 +203,11 @@ def hyb_diag(g: int) -> np.ndarray:
 
 def hyb_check(g: int):
     _check(lib().hyb_check(_V(g)))
+
+
+def hyb_wait_selftest(which: int, seconds: float, stream: int = 0) -> int:
+    """Status of the bounded-wait self-test (HYB_ETIMEOUT is the designed outcome)."""
+    return lib().hyb_wait_selftest(int(which), float(seconds), _V(stream))
 
 
 def hyb_destroy_grid(g: int):
