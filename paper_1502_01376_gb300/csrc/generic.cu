@@ -27,20 +27,19 @@ __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = n1 >> 1;
     C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + (size_t)RB * M;
+    C* dst = src + fpad_size((size_t)RB * M);
     const int64_t row0 = (int64_t)blockIdx.x * RB;
     const int nrow = (int)((rows - row0) < RB ? (rows - row0) : RB);
     const int f = blockIdx.y;
     const Tin* x = reinterpret_cast<const Tin*>(in.p[f]) + row0 * n1;
-    for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) src[q] = mkc<C>((T)x[2 * q], (T)x[2 * q + 1]);
+    for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) src[fpad(q)] = mkc<C>((T)x[2 * q], (T)x[2 * q + 1]);
     __syncthreads();
     stockham_rows<C, false>(src, dst, M, nrow, twM);
     C* X = out + ((int64_t)f * rows + row0) * (M + 1);
     for (int q = threadIdx.x; q < nrow * (M + 1); q += blockDim.x) {
         const int r = q / (M + 1), k = q - r * (M + 1);
-        const C* Z = src + (size_t)r * M;
-        C zk = Z[k == M ? 0 : k];
-        C zm = Z[k == 0 ? 0 : M - k];
+        C zk = src[fpad(r * M + (k == M ? 0 : k))];
+        C zm = src[fpad(r * M + (k == 0 ? 0 : M - k))];
         C zmc = cconj(zm);
         C e = cscale(cadd(zk, zmc), (T)0.5);
         C d = csub(zk, zmc);
@@ -60,7 +59,7 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = n1 >> 1;
     C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + (size_t)RB * M;
+    C* dst = src + fpad_size((size_t)RB * M);
     const int64_t row0 = (int64_t)blockIdx.x * RB;
     const int nrow = (int)((rows - row0) < RB ? (rows - row0) : RB);
     const int f = blockIdx.y;
@@ -73,20 +72,21 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
         C xmc = cconj(xm);
         C e = cscale(cadd(xk, xmc), (T)0.5);
         C o = cscale(cmulc(csub(xk, xmc), twN[k]), (T)0.5);
-        src[q] = mkc<C>(e.x - o.y, e.y + o.x);
+        src[fpad(q)] = mkc<C>(e.x - o.y, e.y + o.x);
     }
     __syncthreads();
     stockham_rows<C, true>(src, dst, M, nrow, twM);
     Tout* x = reinterpret_cast<Tout*>(out.p[f]) + row0 * n1;
     const T inv = (T)1 / (T)M;
     for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) {
-        x[2 * q] = (Tout)(src[q].x * inv);
-        x[2 * q + 1] = (Tout)(src[q].y * inv);
+        const C z = src[fpad(q)];
+        x[2 * q] = (Tout)(z.x * inv);
+        x[2 * q + 1] = (Tout)(z.y * inv);
     }
 }
 
 template <typename T>
-static size_t row_fft_smem(int n1, int RB) { return sizeof(cplx<T>) * 2 * (size_t)RB * (n1 / 2); }
+static size_t row_fft_smem(int n1, int RB) { return sizeof(cplx<T>) * 2 * fpad_size((size_t)RB * (n1 / 2)); }
 
 template <typename Tin, typename T>
 static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {

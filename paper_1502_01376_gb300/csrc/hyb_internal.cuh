@@ -55,6 +55,12 @@ __device__ __forceinline__ void sdft8(C* x) {
     x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
 }
 
+// Shared-memory position of element i of the FFT buffers: one padding element after every
+// eight, so that the stride-8 scatter of a radix-8 pass does not hit the same banks.
+__host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 3); }
+// elements of a padded buffer holding n values
+__host__ __device__ __forceinline__ size_t fpad_size(size_t n) { return n + n / 8 + 1; }
+
 // One radix-R Stockham pass over nrow rows of M points (rows contiguous): butterfly j of a
 // row (0 <= j < M/R, k = j mod Ns) takes src[j + r M/R] W_{R Ns}^{r k}, r = 0..R-1, does an
 // R-point DFT over r and writes output r to dst[(j - k) R + k + r Ns].
@@ -64,12 +70,11 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __re
     const int nb = M / R, ts = M / (R * Ns);
     for (int q = threadIdx.x; q < nb * nrow; q += blockDim.x) {
         const int row = q / nb, j = q - row * nb, k = j & (Ns - 1);
-        const C* s = src + (size_t)row * M;
-        C* d = dst + (size_t)row * M;
+        const int base = row * M;
         C x[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            x[r] = s[j + r * nb];
+            x[r] = src[fpad(base + j + r * nb)];
             if (r > 0 && Ns > 1) {
                 const C w = tw[r * k * ts];
                 x[r] = INV ? cmulc(x[r], w) : cmul(x[r], w);
@@ -78,15 +83,16 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __re
         if (R == 8) sdft8<C, INV>(x);
         else if (R == 4) sdft4<C, INV>(x[0], x[1], x[2], x[3]);
         else sdft2<C, INV>(x);
-        const int o = (j - k) * R + k;
+        const int o = base + (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; r++) d[o + r * Ns] = x[r];
+        for (int r = 0; r < R; r++) dst[fpad(o + r * Ns)] = x[r];
     }
 }
 
 // natural-order in, natural-order out FFT of nrow rows of M = 2^m points held in shared
-// memory (src); radix-8 passes then one radix-4 or radix-2 pass; one __syncthreads per pass.
-// On return src points at the result.  tw[j] = W_M^j, j < M.
+// memory (src, padded positions fpad(row * M + j)); radix-8 passes then one radix-4 or
+// radix-2 pass; one __syncthreads per pass.  On return src points at the result.
+// tw[j] = W_M^j, j < M.
 template <typename C, bool INV>
 __device__ __forceinline__ void stockham_rows(C*& src, C*& dst, int M, int nrow, const C* __restrict__ tw) {
     int Ns = 1;

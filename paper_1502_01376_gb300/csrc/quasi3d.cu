@@ -44,15 +44,15 @@ __global__ void __launch_bounds__(kQThreads) k_qfft_fwd(QPtrs in, cplx<T>* __res
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + (size_t)RB * nz;
+    C* dst = src + fpad_size((size_t)RB * nz);
     const int row0 = blockIdx.x * RB, f = blockIdx.y;
     const int nrow = (nr - row0) < RB ? (nr - row0) : RB;
     const C* x = reinterpret_cast<const C*>(in.p[f]) + (int64_t)row0 * nz;
-    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) src[q] = x[q];
+    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) src[fpad(q)] = x[q];
     __syncthreads();
     stockham_rows<C, false>(src, dst, nz, nrow, tw);
     C* X = spec + ((int64_t)f * nr + row0) * nz;
-    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) X[q] = src[q];
+    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) X[q] = src[fpad(q)];
 }
 
 template <typename T>
@@ -61,16 +61,16 @@ __global__ void __launch_bounds__(kQThreads) k_qfft_inv(const cplx<T>* __restric
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + (size_t)RB * nz;
+    C* dst = src + fpad_size((size_t)RB * nz);
     const int row0 = blockIdx.x * RB, f = blockIdx.y;
     const int nrow = (nr - row0) < RB ? (nr - row0) : RB;
     const C* X = spec + ((int64_t)f * nr + row0) * nz;
-    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) src[q] = X[q];
+    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) src[fpad(q)] = X[q];
     __syncthreads();
     stockham_rows<C, true>(src, dst, nz, nrow, tw);
     C* x = reinterpret_cast<C*>(out.p[f]) + (int64_t)row0 * nz;
     const T inv = (T)1 / (T)nz;
-    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) x[q] = cscale(src[q], inv);
+    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) x[q] = cscale(src[fpad(q)], inv);
 }
 
 // i m / r times a
@@ -175,7 +175,7 @@ static hyb_status create_t(hyb_grid* g) {
     HYB_CUDA_TRY(cudaMalloc(&P->tw, sizeof(C) * nz));
     HYB_CUDA_TRY(cudaMemcpy(P->tw, tw.data(), sizeof(C) * nz, cudaMemcpyHostToDevice));
     HYB_CUDA_TRY(cudaMalloc(&P->spec, sizeof(C) * 9 * (size_t)nr * nz));
-    const size_t smem = sizeof(C) * 2 * (size_t)fft_rows_per_block(nz) * nz;
+    const size_t smem = sizeof(C) * 2 * fpad_size((size_t)fft_rows_per_block(nz) * nz);
     HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return HYB_OK;
@@ -188,7 +188,7 @@ static hyb_status advance_t(hyb_grid* g, int nsteps) {
     const hyb_grid_desc& d = g->d;
     const int nz = d.n1, nr = d.n2;
     const int RB = fft_rows_per_launch(nz, (int64_t)nr * 6), nblk = (nr + RB - 1) / RB;
-    const size_t smem = sizeof(C) * 2 * (size_t)RB * nz;
+    const size_t smem = sizeof(C) * 2 * fpad_size((size_t)RB * nz);
     QPtrs fin{}, fout{};
     for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; fin.p[6 + c] = g->J[c]; }
     for (int c = 0; c < 3; c++) { fout.p[c] = g->E[c]; fout.p[3 + c] = g->B[c]; }
