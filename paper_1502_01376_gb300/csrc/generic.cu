@@ -8,6 +8,8 @@
 // then one radix-4 or radix-2 pass; several short rows per block)
 // of the n1/2-point complex sequence z[j] = x[2j] + i x[2j+1] followed by the
 // standard even/odd split into the n1/2+1 real-input coefficients.
+#include <type_traits>
+
 #include "hyb_internal.cuh"
 
 namespace hyb {
@@ -32,12 +34,20 @@ __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* 
     const int nrow = (int)((rows - row0) < RB ? (rows - row0) : RB);
     const int f = blockIdx.y;
     const Tin* x = reinterpret_cast<const Tin*>(in.p[f]) + row0 * n1;
-    for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) src[fpad(q)] = mkc<C>((T)x[2 * q], (T)x[2 * q + 1]);
+    if constexpr (std::is_same<Tin, T>::value) {           // (x[2q], x[2q+1]) as one complex load
+        const C* xc = reinterpret_cast<const C*>(x);
+        for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) src[fpad(q)] = xc[q];
+    } else {
+        for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) src[fpad(q)] = mkc<C>((T)x[2 * q], (T)x[2 * q + 1]);
+    }
     __syncthreads();
     stockham_rows<C, false>(src, dst, M, nrow, twM);
     C* X = out + ((int64_t)f * rows + row0) * (M + 1);
-    for (int q = threadIdx.x; q < nrow * (M + 1); q += blockDim.x) {
-        const int r = q / (M + 1), k = q - r * (M + 1);
+    const int lgM = 31 - __clz(M);
+    // modes k < M of all rows, then the Nyquist mode of each row
+    for (int q = threadIdx.x; q < (nrow << lgM) + nrow; q += blockDim.x) {
+        int r, k;
+        if (q < (nrow << lgM)) { r = q >> lgM; k = q & (M - 1); } else { r = q - (nrow << lgM); k = M; }
         C zk = src[fpad(r * M + (k == M ? 0 : k))];
         C zm = src[fpad(r * M + (k == 0 ? 0 : M - k))];
         C zmc = cconj(zm);
@@ -45,7 +55,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* 
         C d = csub(zk, zmc);
         C w = (k < M) ? twN[k] : mkc<C>((T)-1, (T)0);
         C wd = cmul(w, d);
-        X[q] = mkc<C>(e.x + (T)0.5 * wd.y, e.y - (T)0.5 * wd.x);
+        X[r * (M + 1) + k] = mkc<C>(e.x + (T)0.5 * wd.y, e.y - (T)0.5 * wd.x);
     }
 }
 
@@ -64,8 +74,9 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
     const int nrow = (int)((rows - row0) < RB ? (rows - row0) : RB);
     const int f = blockIdx.y;
     const C* X = in + ((int64_t)(in_field0 + f) * rows + row0) * (M + 1);
-    for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) {
-        const int r = q / M, k = q - r * M;
+    const int lgM = 31 - __clz(M);
+    for (int q = threadIdx.x; q < (nrow << lgM); q += blockDim.x) {
+        const int r = q >> lgM, k = q & (M - 1);
         const C* Xr = X + (size_t)r * (M + 1);
         C xk = Xr[k], xm = Xr[M - k];
         if (k == 0) { xk.y = 0; xm.y = 0; }
@@ -78,10 +89,15 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
     stockham_rows<C, true>(src, dst, M, nrow, twM);
     Tout* x = reinterpret_cast<Tout*>(out.p[f]) + row0 * n1;
     const T inv = (T)1 / (T)M;
-    for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) {
-        const C z = src[fpad(q)];
-        x[2 * q] = (Tout)(z.x * inv);
-        x[2 * q + 1] = (Tout)(z.y * inv);
+    if constexpr (std::is_same<Tout, T>::value) {
+        C* xc = reinterpret_cast<C*>(x);
+        for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) xc[q] = cscale(src[fpad(q)], inv);
+    } else {
+        for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) {
+            const C z = src[fpad(q)];
+            x[2 * q] = (Tout)(z.x * inv);
+            x[2 * q + 1] = (Tout)(z.y * inv);
+        }
     }
 }
 

@@ -56,27 +56,34 @@ __device__ __forceinline__ void sdft8(C* x) {
 }
 
 // Shared-memory position of element i of the FFT buffers: one padding element after every
-// eight, so that the stride-8 scatter of a radix-8 pass does not hit the same banks.
-__host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 3); }
+// sixteen, so that the stride-8 scatter of a radix-8 pass spreads over all banks while
+// contiguous accesses stay (nearly) conflict-free.
+__host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
 // elements of a padded buffer holding n values
-__host__ __device__ __forceinline__ size_t fpad_size(size_t n) { return n + n / 8 + 1; }
+__host__ __device__ __forceinline__ size_t fpad_size(size_t n) { return n + n / 16 + 1; }
 
 // One radix-R Stockham pass over nrow rows of M points (rows contiguous): butterfly j of a
 // row (0 <= j < M/R, k = j mod Ns) takes src[j + r M/R] W_{R Ns}^{r k}, r = 0..R-1, does an
 // R-point DFT over r and writes output r to dst[(j - k) R + k + r Ns].
 template <typename C, int R, bool INV>
-__device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst, int M, int Ns, int nrow,
+__device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst, int lgM, int lgNs, int nrow,
                                               const C* __restrict__ tw) {
-    const int nb = M / R, ts = M / (R * Ns);
-    for (int q = threadIdx.x; q < nb * nrow; q += blockDim.x) {
-        const int row = q / nb, j = q - row * nb, k = j & (Ns - 1);
+    constexpr int lgR = (R == 8) ? 3 : (R == 4) ? 2 : 1;
+    const int M = 1 << lgM, Ns = 1 << lgNs;
+    const int lgnb = lgM - lgR, nb = 1 << lgnb, lgts = lgM - lgR - lgNs;
+    // padded positions: when the element stride is a multiple of 16, fpad(a + r s) = fpad(a) + r (s + s / 16)
+    const bool rstride = (nb & 15) == 0, wstride = (Ns & 15) == 0;
+    const int nbp = nb + (nb >> 4), nsp = Ns + (Ns >> 4);
+    for (int q = threadIdx.x; q < (nrow << lgnb); q += blockDim.x) {
+        const int row = q >> lgnb, j = q & (nb - 1), k = j & (Ns - 1);
         const int base = row * M;
+        const int ra = fpad(base + j);
         C x[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            x[r] = src[fpad(base + j + r * nb)];
+            x[r] = src[rstride ? ra + r * nbp : fpad(base + j + r * nb)];
             if (r > 0 && Ns > 1) {
-                const C w = tw[r * k * ts];
+                const C w = tw[(r * k) << lgts];
                 x[r] = INV ? cmulc(x[r], w) : cmul(x[r], w);
             }
         }
@@ -84,8 +91,9 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __re
         else if (R == 4) sdft4<C, INV>(x[0], x[1], x[2], x[3]);
         else sdft2<C, INV>(x);
         const int o = base + (j - k) * R + k;
+        const int wa = fpad(o);
 #pragma unroll
-        for (int r = 0; r < R; r++) dst[fpad(o + r * Ns)] = x[r];
+        for (int r = 0; r < R; r++) dst[wstride ? wa + r * nsp : fpad(o + r * Ns)] = x[r];
     }
 }
 
@@ -95,19 +103,20 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __re
 // tw[j] = W_M^j, j < M.
 template <typename C, bool INV>
 __device__ __forceinline__ void stockham_rows(C*& src, C*& dst, int M, int nrow, const C* __restrict__ tw) {
-    int Ns = 1;
-    while (Ns * 8 <= M) {
-        stockham_pass<C, 8, INV>(src, dst, M, Ns, nrow, tw);
+    const int lgM = 31 - __clz(M);
+    int lgNs = 0;
+    while (lgNs + 3 <= lgM) {
+        stockham_pass<C, 8, INV>(src, dst, lgM, lgNs, nrow, tw);
         __syncthreads();
         C* t = src; src = dst; dst = t;
-        Ns *= 8;
+        lgNs += 3;
     }
-    if (Ns * 4 <= M) {
-        stockham_pass<C, 4, INV>(src, dst, M, Ns, nrow, tw);
+    if (lgNs + 2 <= lgM) {
+        stockham_pass<C, 4, INV>(src, dst, lgM, lgNs, nrow, tw);
         __syncthreads();
         C* t = src; src = dst; dst = t;
-    } else if (Ns * 2 <= M) {
-        stockham_pass<C, 2, INV>(src, dst, M, Ns, nrow, tw);
+    } else if (lgNs + 1 <= lgM) {
+        stockham_pass<C, 2, INV>(src, dst, lgM, lgNs, nrow, tw);
         __syncthreads();
         C* t = src; src = dst; dst = t;
     }
