@@ -46,11 +46,12 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="profiling mode: random band-limited J instead of the particle deposit, no extras")
     ap.add_argument("--workload", default="drift_plasma",
-                    choices=["drift_plasma", "batched", "3d", "vacuum_beam", "x1_sweep"],
+                    choices=["drift_plasma", "batched", "3d", "vacuum_beam", "x1_sweep", "surrogate"],
                     help="drift_plasma (default, the headline): 2D 4096 x 1024 FP32; batched: 16 uneven 2D grids "
                          "+ quasi-3D modes m = 0, 1, 2 (2048 x 512 complex) in one CUDA-graph step; 3d: 1024 x 256 x 256 "
                          "FP32, radix FFT vs DFT-GEMM x1 transform; vacuum_beam: 2D 128 x 64 FP64; x1_sweep: both x1 "
-                         "transforms for n1 = 16 .. 1024 at 2^25 cells")
+                         "transforms for n1 = 16 .. 1024 at 2^25 cells; surrogate: NCI surrogate trained on 200k "
+                         "root-solver samples, then the pick of cutoff and dt judged by the solver")
     return ap.parse_args()
 
 
@@ -196,7 +197,7 @@ def run_reference(args):
     import numpy as np
     import oracle
     oracle.build()
-    rows = 4
+    rows = 64                       # the same 4096 x 64 strip as the cpu_baseline sample
     ws_ = w.scaled(n2=rows)
     g = oracle.grid(n1=ws_.n1, n2=ws_.n2, dx1=ws_.dx1, dx2=ws_.dx2, dt=ws_.dt, filt_kc=ws_.filt_kc, filt_w=ws_.filt_w)
     E, B = wl.band_limited_fields(ws_)
@@ -268,6 +269,69 @@ def x1_compare(hyb, w, arrs, stream, flush, sampler, args, dev):
     for path in (1, 3):
         out[f"err_path{path}"] = {n: float((a - b).norm() / b.norm()) for n, a, b in zip(names, fin[path], fin[64])}
     return out
+
+
+def run_surrogate(args):
+    """The learned part: 200k (dt/dx1, dx2/dx1, gamma, kc, k1, k2) samples labelled by
+    the FP64 GPU root solver of the NCI dispersion relation, the MLP 6 -> 256 x 4 -> 1
+    trained by the library's own kernels, then the pick of filter cutoff and dt for
+    the drifting-plasma run (gamma 50, square cells), judged by the root solver."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1502_01376_gb300 import build, hyb, surrogate as sg
+    build.build()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, y, kept, n = sg.dataset(200000, seed=21)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    Xv, yv, _, _ = sg.dataset(20000, seed=22)
+    net = hyb.MLP(6, 256, 4, seed=5)
+    steps, batch = max(args.steps, 500), 8192
+    sg.train(net, X, y, steps=args.warmup, batch=batch, lr=2e-3, seed=0)       # warm-up steps (not timed)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark(True)
+    ev0.record()
+    hist = sg.train(net, X, y, steps=steps, batch=batch, lr=2e-3, seed=1)
+    ev1.record()
+    torch.cuda.synchronize()
+    sampler.mark(False)
+    train_ms = ev0.elapsed_time(ev1)
+    pred = net.forward(Xv)
+    mse = float(torch.mean((pred - yv) ** 2))
+    var = float(torch.var(yv))
+    dts = np.arange(0.2, 0.51, 0.05)
+    kcs = np.arange(0.3, 1.01, 0.1)
+    res = sg.pick(net, 50.0, 1.0, dts, kcs)
+    confirmed = float(sg.max_growth_solver([res["dt_dx1"]], [1.0], [50.0], [res["kc"]])[0])
+    unfiltered = float(sg.max_growth_solver([0.5], [1.0], [50.0], [1.0])[0])
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    solver_all = sg.max_growth_solver(res["all_dt"], np.ones(res["candidates"]), np.full(res["candidates"], 50.0),
+                                      res["all_kc"])
+    torch.cuda.synchronize()
+    t_solver = time.perf_counter() - t1
+    best_solver = float(np.min(solver_all))
+    sampler.stop()
+    net.close()
+    line = {"metric": "NCI surrogate training samples/s (MLP 6->256x4->1, BF16 operands, FP32 accumulation)",
+            "value": steps * batch / (train_ms / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": train_ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "gpu_launches": None, "clocks": sampler.summary(),
+            "config": {"workload": "nci_surrogate_200k", "samples": n, "kept_below_courant": kept,
+                       "label_seconds": t_data, "batch": batch, "loss_first": float(hist[:10].mean()),
+                       "loss_last": float(hist[-50:].mean()), "val_mse_over_var": mse / var,
+                       "pick": {"dt_dx1": res["dt_dx1"], "kc": res["kc"], "predicted": res["predicted"],
+                                "solver_at_pick": confirmed, "solver_best_candidate": best_solver,
+                                "solver_unfiltered_dt0.5": unfiltered, "candidates": res["candidates"],
+                                "surrogate_scan_s": res["seconds"], "solver_scan_s": t_solver}}}
+    print(json.dumps(line), flush=True)
 
 
 def run_other(args):
@@ -393,6 +457,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     if args.workload != "drift_plasma":
         return run_other(args)
     import numpy as np
