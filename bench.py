@@ -307,9 +307,14 @@ def run_surrogate(args):
     var = float(torch.var(yv))
     dts = np.arange(0.2, 0.51, 0.05)
     kcs = np.arange(0.3, 1.01, 0.1)
+    sg.pick(net, 50.0, 1.0, dts, kcs)                   # first call sizes the activation buffers
     res = sg.pick(net, 50.0, 1.0, dts, kcs)
     confirmed = float(sg.max_growth_solver([res["dt_dx1"]], [1.0], [50.0], [res["kc"]])[0])
+    # the surrogate prunes, the root solver judges the 8 most promising candidates
+    resv = sg.pick(net, 50.0, 1.0, dts, kcs, verify=8)
+    confirmed_v = float(sg.max_growth_solver([resv["dt_dx1"]], [1.0], [50.0], [resv["kc"]])[0])
     unfiltered = float(sg.max_growth_solver([0.5], [1.0], [50.0], [1.0])[0])
+    sg.max_growth_solver(res["all_dt"][:1], np.ones(1), np.full(1, 50.0), res["all_kc"][:1])   # warm
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     solver_all = sg.max_growth_solver(res["all_dt"], np.ones(res["candidates"]), np.full(res["candidates"], 50.0),
@@ -330,7 +335,10 @@ def run_surrogate(args):
                        "pick": {"dt_dx1": res["dt_dx1"], "kc": res["kc"], "predicted": res["predicted"],
                                 "solver_at_pick": confirmed, "solver_best_candidate": best_solver,
                                 "solver_unfiltered_dt0.5": unfiltered, "candidates": res["candidates"],
-                                "surrogate_scan_s": res["seconds"], "solver_scan_s": t_solver}}}
+                                "surrogate_scan_s": res["seconds"], "solver_scan_s": t_solver,
+                                "verified_pick": {"dt_dx1": resv["dt_dx1"], "kc": resv["kc"], "solver": confirmed_v,
+                                                  "candidates_solved": resv["verified"],
+                                                  "seconds": resv["seconds"] + resv["verify_seconds"]}}}}
     print(json.dumps(line), flush=True)
 
 

@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "hyb_internal.cuh"
@@ -44,10 +45,12 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
 }
 
 // C[m][n] (FP32) = sum_k A(m,k) B(k,n), A(m,k) = a[m*sam + k*sak], B(k,n) = b[k*sbk + n*sbn]
-// (BF16), M, N, K multiples of 16; accumulate into C if acc != 0.
+// (BF16), M, N, K multiples of 16; accumulate into C if acc != 0.  Split K: block z
+// handles k in [z*kchunk, (z+1)*kchunk) and, when gridDim.z > 1, adds its partial sums
+// atomically (C then holds the caller's zero or previous values).
 __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, int kmax, const __nv_bfloat16* __restrict__ a, int64_t sam, int64_t sak,
                                                    const __nv_bfloat16* __restrict__ b, int64_t sbk, int64_t sbn,
-                                                   float* __restrict__ c, int64_t scm, int acc) {
+                                                   float* __restrict__ c, int64_t scm, int acc, int kchunk) {
     __shared__ __nv_bfloat16 As[TM][TK + 8];
     __shared__ __nv_bfloat16 Bs[TN][TK + 8];      // stored as [n][k]
     const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
@@ -61,16 +64,19 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, int kmax
         for (int j = 0; j < 4; j++)
 #pragma unroll
             for (int r = 0; r < 4; r++) accf[i][j][r] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += TK) {
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    // tile fills walk the unit-stride index fastest (coalesced global reads)
+    const bool a_m_fast = (sam == 1), b_n_fast = (sbn == 1);
+    for (int k0 = kb; k0 < ke; k0 += TK) {
         for (int i = threadIdx.x; i < TM * TK; i += blockDim.x) {
-            const int r = i / TK, kk = i % TK;
+            const int r = a_m_fast ? i % TM : i / TK, kk = a_m_fast ? i / TM : i % TK;
             const int m = m0 + r, k = k0 + kk;
-            As[r][kk] = (m < M && k < kmax) ? a[m * sam + k * sak] : __float2bfloat16(0.f);
+            As[r][kk] = (m < M && k < kmax) ? a[(int64_t)m * sam + (int64_t)k * sak] : __float2bfloat16(0.f);
         }
         for (int i = threadIdx.x; i < TN * TK; i += blockDim.x) {
-            const int r = i / TK, kk = i % TK;
+            const int r = b_n_fast ? i % TN : i / TK, kk = b_n_fast ? i / TN : i % TK;
             const int n = n0 + r, k = k0 + kk;
-            Bs[r][kk] = (n < N && k < kmax) ? b[k * sbk + n * sbn] : __float2bfloat16(0.f);
+            Bs[r][kk] = (n < N && k < kmax) ? b[(int64_t)k * sbk + (int64_t)n * sbn] : __float2bfloat16(0.f);
         }
         __syncthreads();
         uint32_t af[2][4], bfr[4][2];
@@ -110,8 +116,9 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, int kmax
 #pragma unroll
                     for (int q = 0; q < 2; q++) {
                         if (cc + q < N) {
-                            float* p = c + rr * scm + cc + q;
-                            *p = acc ? *p + accf[i][j][2 * h + q] : accf[i][j][2 * h + q];
+                            float* p = c + (int64_t)rr * scm + cc + q;
+                            if (gridDim.z > 1) atomicAdd(p, accf[i][j][2 * h + q]);
+                            else *p = acc ? *p + accf[i][j][2 * h + q] : accf[i][j][2 * h + q];
                         }
                     }
                 }
@@ -120,10 +127,18 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, int kmax
 }
 
 // K is rounded up to 16 (the tile depth); entries with k >= K read as zero
+// Few output tiles and a long K (the weight gradients: K = batch) are split along K
+// over up to 64 blocks per tile, the partial sums added atomically into C.
 static void gemm(int M, int N, int K, const __nv_bfloat16* a, int64_t sam, int64_t sak, const __nv_bfloat16* b, int64_t sbk,
                  int64_t sbn, float* c, int64_t scm, int acc, cudaStream_t s) {
-    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-    k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, (K + 15) & ~15, K, a, sam, sak, b, sbk, sbn, c, scm, acc);
+    const int Kp = (K + 15) & ~15;
+    const int tiles = ((N + TN - 1) / TN) * ((M + TM - 1) / TM);
+    int split = 1;
+    while (split < 64 && tiles * split < 600 && Kp / (split * 2) >= 256) split *= 2;
+    const int kchunk = ((Kp / split + 15) & ~15);
+    if (split > 1 && !acc) cudaMemsetAsync(c, 0, sizeof(float) * (size_t)M * scm, s);   // rows of stride scm >= N
+    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, split);
+    k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, Kp, K, a, sam, sak, b, sbk, sbn, c, scm, acc, kchunk);
 }
 
 // x (FP32 [B][n_in]) -> BF16 [B][kin] with zero padding
@@ -239,7 +254,8 @@ static hyb_status ensure_cap(hyb_mlp* m, int64_t B) {
     if (B <= m->cap) return HYB_OK;
     if (m->act) { cudaFree(m->act); cudaFree(m->pre); cudaFree(m->dh); cudaFree(m->dhb); cudaFree(m->dx); }
     m->act = nullptr;
-    const int64_t cap = ((B + 63) / 64) * 64;
+    // at least 256 rows: dx also holds the weight gradient of a layer (up to 256 x 256)
+    const int64_t cap = std::max<int64_t>(256, ((B + 63) / 64) * 64);
     HYB_CUDA_TRY(cudaMalloc(&m->act, sizeof(__nv_bfloat16) * (size_t)(m->L + 1) * cap * 256));
     HYB_CUDA_TRY(cudaMalloc(&m->pre, sizeof(float) * (size_t)m->L * cap * 256));
     HYB_CUDA_TRY(cudaMalloc(&m->dh, sizeof(float) * (size_t)cap * 256));

@@ -142,10 +142,12 @@ def max_growth_solver(dt_dx1, dx2_dx1, gamma, kc, nk: int = 48) -> np.ndarray:
     return g.view(cands, nk * nk).max(dim=1).values.cpu().numpy()
 
 
-def pick(mlp, gamma: float, dx2_dx1: float, dt_grid, kc_grid, tol: float = 0.002, nk: int = 48):
+def pick(mlp, gamma: float, dx2_dx1: float, dt_grid, kc_grid, tol: float = 0.002, nk: int = 48, verify: int = 0):
     """Candidate (dt/dx1, kc) with the lowest predicted max growth, preferring
     the largest cutoff and then the largest time step among those within tol
-    of the lowest (keep the most physics bandwidth)."""
+    of the lowest (keep the most physics bandwidth).  With verify = k > 0 the
+    root solver, the surrogate's judge, re-scores the k candidates with the
+    lowest predicted growth and the pick is made among them on its values."""
     dts, kcs = np.meshgrid(np.asarray(dt_grid, float), np.asarray(kc_grid, float), indexing="ij")
     dts, kcs = dts.ravel(), kcs.ravel()
     ok = dts * DX1 <= courant_dt(DX1, dx2_dx1 * DX1)
@@ -153,8 +155,18 @@ def pick(mlp, gamma: float, dx2_dx1: float, dt_grid, kc_grid, tol: float = 0.002
     t0 = time.perf_counter()
     pred = max_growth_surrogate(mlp, dts, np.full(dts.size, dx2_dx1), np.full(dts.size, gamma), kcs, nk)
     t_pred = time.perf_counter() - t0
-    best = pred.min()
-    good = np.where(pred <= best + tol)[0]
+    score = pred
+    idx = np.arange(dts.size)
+    t_ver = 0.0
+    if verify > 0:
+        idx = np.argsort(pred)[:verify]
+        t1 = time.perf_counter()
+        score = np.full(dts.size, np.inf)
+        score[idx] = max_growth_solver(dts[idx], np.full(idx.size, dx2_dx1), np.full(idx.size, gamma), kcs[idx], nk)
+        t_ver = time.perf_counter() - t1
+    best = score[idx].min()
+    good = idx[score[idx] <= best + tol]
     i = good[np.lexsort((dts[good], kcs[good]))[-1]]
     return {"dt_dx1": float(dts[i]), "kc": float(kcs[i]), "predicted": float(pred[i]), "candidates": int(dts.size),
-            "seconds": t_pred, "all_dt": dts, "all_kc": kcs, "all_pred": pred}
+            "seconds": t_pred, "verify_seconds": t_ver, "verified": int(verify),
+            "all_dt": dts, "all_kc": kcs, "all_pred": pred}

@@ -77,6 +77,11 @@ def test_surrogate_trains_and_picks_settings_with_less_growth():
     confirmed = sg.max_growth_solver([res["dt_dx1"]], [1.0], [50.0], [res["kc"]])[0]
     unfiltered = sg.max_growth_solver([0.5], [1.0], [50.0], [1.0])[0]
     assert confirmed <= unfiltered
+    # pruned by the surrogate, judged by the root solver on the 8 most promising candidates
+    resv = sg.pick(net, 50.0, 1.0, dts, kcs, verify=8)
+    confirmed_v = sg.max_growth_solver([resv["dt_dx1"]], [1.0], [50.0], [resv["kc"]])[0]
+    assert confirmed_v <= unfiltered
+    assert confirmed_v <= confirmed + 2e-3
     t0 = time.perf_counter()
     sg.max_growth_solver(res["all_dt"], np.ones(res["candidates"]), np.full(res["candidates"], 50.0), res["all_kc"])
     t_solver = time.perf_counter() - t0
