@@ -1,0 +1,113 @@
+"""Edge cases of the boundary: the smallest and largest row lengths, the
+fewest rows, one-row-per-strip fused grids, ragged strips, an empty particle
+set, a batch of one grid, and the sizes the ABI rejects."""
+import numpy as np
+import pytest
+
+from paper_1502_01376_gb300 import workloads as wl
+
+from gpu_util import hyb_module, need_gpu, orc_grid, rel_err, to_dev, to_np, torch
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 1e-5}
+
+
+def _run(orc, hyb, w, path, nst=3, seed=5):
+    dt = torch.float64 if w.precision == 64 else torch.float32
+    g = hyb.Grid(hyb.desc_from_workload(w, path=path))
+    E0, B0 = wl.band_limited_fields(w)
+    rng = np.random.default_rng(seed)
+    J0 = [rng.standard_normal(w.shape) * 1e-3 for _ in range(3)]
+    rnd = (lambda a: a) if w.precision == 64 else (lambda a: a.astype(np.float32).astype(np.float64))
+    E = [to_dev(a, dt) for a in E0]
+    B = [to_dev(a, dt) for a in B0]
+    J = [to_dev(a, dt) for a in J0]
+    g.bind(E, B, J)
+    g.advance(nst)
+    g.check()
+    Eo, Bo, Jo = [rnd(a) for a in E0], [rnd(a) for a in B0], [rnd(a) for a in J0]
+    orc.step(orc_grid(orc, w), Eo, Bo, Jo, nsteps=nst)
+    errs = [rel_err(to_np(a), b) for a, b in zip(E + B, Eo + Bo)]
+    g.close()
+    return errs
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("n1,n2", [(8, 2), (8, 3), (16, 2), (8192, 3)])
+def test_three_pass_extreme_row_lengths(orc, prec, n1, n2):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("e", 2, n1, n2, dx1=0.2, dx2=0.25, dt=0.05, precision=prec, filt_kc=0.5, filt_w=0.2, seed=9)
+    errs = _run(orc, hyb, w, path=1)
+    assert max(errs) < TOL[prec], errs
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_three_pass_3d_two_planes(orc, prec):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("e3", 3, 32, 2, 2, dx1=0.2, dx2=0.25, dx3=0.3, dt=0.05, precision=prec, filt_kc=0.6, filt_w=0.2,
+                    seed=10)
+    errs = _run(orc, hyb, w, path=1)
+    assert max(errs) < TOL[prec], errs
+
+
+@pytest.mark.parametrize("n1,n2", [(4096, 4), (4096, 5), (512, 4), (2048, 7)])
+def test_fused_fewest_rows(orc, n1, n2):
+    """Strips of two or three rows (n2 / 2 strips), the smallest grids the fused path takes."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("ef", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.1, precision=32, filt_kc=0.5, filt_w=0.2, seed=11)
+    errs = _run(orc, hyb, w, path=2)
+    assert max(errs) < TOL[32], errs
+
+
+def test_deposit_without_particles_zeroes_j(orc):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("ed", 2, 64, 8, dx1=0.2, dx2=0.2, dt=0.05, precision=64, seed=12)
+    g = hyb.Grid(hyb.desc_from_workload(w, path=1))
+    E = [torch.zeros(w.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    B = [torch.zeros(w.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    J = [torch.ones(w.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    g.bind(E, B, J)
+    empty_i = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    empty_f = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
+    empty_v = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    empty_q = torch.zeros(0, dtype=torch.float64, device="cuda")
+    g.deposit(empty_i, empty_f, empty_f, empty_v, empty_q, 1)
+    g.check()
+    torch.cuda.synchronize()
+    assert all(float(j.abs().max()) == 0.0 for j in J)
+    g.close()
+
+
+def test_batch_of_one_grid_equals_single(orc):
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("eb", 2, 1024, 16, dx1=0.2, dx2=0.2, dt=0.1, precision=32, filt_kc=0.5, filt_w=0.2, seed=13)
+    E0, B0 = wl.band_limited_fields(w)
+    mk = lambda arrs: [to_dev(a, torch.float32) for a in arrs]
+    Jz = [np.zeros(w.shape) for _ in range(3)]
+    tb, ts = (mk(E0), mk(B0), mk(Jz)), (mk(E0), mk(B0), mk(Jz))
+    b = hyb.Batch([hyb.desc_from_workload(w)])
+    b.bind(0, *tb)
+    g = hyb.Grid(hyb.desc_from_workload(w))
+    g.bind(*ts)
+    b.advance(2)
+    g.advance(2)
+    torch.cuda.synchronize()
+    for x, y in zip(tb[0] + tb[1], ts[0] + ts[1]):
+        assert torch.equal(x, y)
+    b.close()
+    g.close()
+
+
+def test_sizes_the_abi_rejects():
+    need_gpu()
+    hyb = hyb_module()
+    for bad in (dict(n1=4, n2=8), dict(n1=16384, n2=4), dict(n1=96, n2=8), dict(n1=64, n2=1)):
+        w = wl.Workload("x", 2, bad["n1"], bad["n2"], dx1=0.2, dx2=0.2, dt=0.01, precision=64, seed=1)
+        with pytest.raises(Exception):
+            hyb.Grid(hyb.desc_from_workload(w))
