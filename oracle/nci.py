@@ -35,6 +35,14 @@ Readings of garbled or silent points (listed in the design doc):
 The cubic asym1 (expansion about w' = k1' v0 with v0 -> 1) gives seeds; each
 seed is refined by Newton's method on F(w) = D(w) (w' - k1' v0), whose only
 extra root, at the resonance itself, is rejected.
+
+Pins (tests/test_oracle_nci_mlp.py, tests/test_golden_paper_values.py): the
+vacuum limit factorises into the hybrid EM modes and the beam resonance; the
+resonance roots scale with sqrt(wp2); the (0,0) modes grow far more slowly
+than the (0,+-1) modes; and the value Sec. 4 prints: zero (0,0) growth at the
+Table 1 parameters with the printed k1 modification, positive growth without
+it.  The growth rates of other individual modes live in the paper's absent
+figures: beyond those properties their values are parity unpinned.
 """
 from __future__ import annotations
 

@@ -1,5 +1,6 @@
 // fused2d.cu -- single-pass FP32 hybrid advance for 2D grids with
-// n1 in {512, 1024, 2048, 4096}: one kernel reads E^n, B^{n-1/2}, j^{n+1/2}
+// n1 in {512, 1024, 2048} (n1 = 4096 runs the TMEM kernel of fused_tm.cu, which
+// shares the host side below): one kernel reads E^n, B^{n-1/2}, j^{n+1/2}
 // once from HBM and writes E^{n+1}, B^{n+1/2} once (15 words per cell).
 //
 // Work decomposition.  The Faraday/Ampere updates of Eqs. hybrid2db1-de3 are
@@ -7,8 +8,10 @@
 // CTA sweeps a strip of consecutive x2 rows, keeping the k1-space lines it
 // still needs in shared memory ("slots"): E1, E3 of rows p and p+1, E2 of row
 // p, B1, B3 of rows p-1 and p, B2 of row p (10 lines).  Rows just outside the
-// strip (E, B1, B3 of row p0-1; E1, E3 of row p1) are copied each step by a
-// small kernel into a halo buffer before any CTA overwrites them.
+// strip (E, B1, B3 of row p0-1; E1, E3 of row p1) are either exchanged inside
+// the kernel under release/acquire flags (one co-resident CTA per strip) or
+// copied each step by a small kernel into a halo buffer before any CTA
+// overwrites them (batches).
 //
 // The CTA has three thread groups of T = n1/32 threads; in every "round" each
 // group performs one real FFT of one row (forward or inverse), so the three
