@@ -43,19 +43,19 @@ __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* 
     __syncthreads();
     stockham_rows<C, false>(src, dst, M, nrow, twM);
     C* X = out + ((int64_t)f * rows + row0) * (M + 1);
-    const int lgM = 31 - __clz(M);
-    // modes k < M of all rows, then the Nyquist mode of each row
-    for (int q = threadIdx.x; q < (nrow << lgM) + nrow; q += blockDim.x) {
+    const int lgH = 31 - __clz(M) - 1, H = M >> 1;
+    // pairs (k, M - k) for k < M/2 of all rows (k = 0 gives X[0] and X[M]), then k = M/2 of each row:
+    // X[k] = e - u, X[M-k] = conj(e + u), e = (Z[k] + Z*[M-k])/2, u = (i/2) W_N^k (Z[k] - Z*[M-k])
+    for (int q = threadIdx.x; q < (nrow << lgH) + nrow; q += blockDim.x) {
         int r, k;
-        if (q < (nrow << lgM)) { r = q >> lgM; k = q & (M - 1); } else { r = q - (nrow << lgM); k = M; }
-        C zk = src[fpad(r * M + (k == M ? 0 : k))];
-        C zm = src[fpad(r * M + (k == 0 ? 0 : M - k))];
-        C zmc = cconj(zm);
-        C e = cscale(cadd(zk, zmc), (T)0.5);
-        C d = csub(zk, zmc);
-        C w = (k < M) ? twN[k] : mkc<C>((T)-1, (T)0);
-        C wd = cmul(w, d);
-        X[r * (M + 1) + k] = mkc<C>(e.x + (T)0.5 * wd.y, e.y - (T)0.5 * wd.x);
+        if (q < (nrow << lgH)) { r = q >> lgH; k = q & (H - 1); } else { r = q - (nrow << lgH); k = H; }
+        const C zk = src[fpad(r * M + k)];
+        const C zmc = cconj(src[fpad(r * M + ((M - k) & (M - 1)))]);
+        const C e = cscale(cadd(zk, zmc), (T)0.5);
+        const C wd = cmul(twN[k], csub(zk, zmc));
+        C* Xr = X + (size_t)r * (M + 1);
+        Xr[k] = mkc<C>(e.x + (T)0.5 * wd.y, e.y - (T)0.5 * wd.x);
+        if (k != H) Xr[M - k] = mkc<C>(e.x - (T)0.5 * wd.y, -(e.y + (T)0.5 * wd.x));
     }
 }
 
@@ -74,16 +74,20 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
     const int nrow = (int)((rows - row0) < RB ? (rows - row0) : RB);
     const int f = blockIdx.y;
     const C* X = in + ((int64_t)(in_field0 + f) * rows + row0) * (M + 1);
-    const int lgM = 31 - __clz(M);
-    for (int q = threadIdx.x; q < (nrow << lgM); q += blockDim.x) {
-        const int r = q >> lgM, k = q & (M - 1);
+    const int lgH = 31 - __clz(M) - 1, H = M >> 1;
+    // pairs (k, M - k) for k < M/2 (k = 0 reads X[0] and X[M]), then k = M/2 of each row:
+    // Z[k] = E + iO, Z[M-k] = conj(E - iO)
+    for (int q = threadIdx.x; q < (nrow << lgH) + nrow; q += blockDim.x) {
+        int r, k;
+        if (q < (nrow << lgH)) { r = q >> lgH; k = q & (H - 1); } else { r = q - (nrow << lgH); k = H; }
         const C* Xr = X + (size_t)r * (M + 1);
         C xk = Xr[k], xm = Xr[M - k];
         if (k == 0) { xk.y = 0; xm.y = 0; }
-        C xmc = cconj(xm);
-        C e = cscale(cadd(xk, xmc), (T)0.5);
-        C o = cscale(cmulc(csub(xk, xmc), twN[k]), (T)0.5);
-        src[fpad(q)] = mkc<C>(e.x - o.y, e.y + o.x);
+        const C xmc = cconj(xm);
+        const C e = cscale(cadd(xk, xmc), (T)0.5);
+        const C o = cscale(cmulc(csub(xk, xmc), twN[k]), (T)0.5);
+        src[fpad(r * M + k)] = mkc<C>(e.x - o.y, e.y + o.x);
+        if (k != 0 && k != H) src[fpad(r * M + M - k)] = mkc<C>(e.x + o.y, o.x - e.y);
     }
     __syncthreads();
     stockham_rows<C, true>(src, dst, M, nrow, twM);
