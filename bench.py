@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and fp64 comparison")
     ap.add_argument("--quick", action="store_true",
                     help="profiling mode: random band-limited J instead of the particle deposit, no extras")
+    ap.add_argument("--rows3d", type=int, default=256,
+                    help="3d workload: n2 = n3 = this (256 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--workload", default="drift_plasma",
                     choices=["drift_plasma", "batched", "3d", "vacuum_beam", "x1_sweep", "surrogate"],
                     help="drift_plasma (default, the headline): 2D 4096 x 1024 FP32; batched: 16 uneven 2D grids "
@@ -401,6 +403,8 @@ def run_other(args):
         # both timed, per-field error of each after 3 steps against the FP64 GPU
         # path from the same initial state, the faster one reported as the value
         w = wl.DRIFT_PLASMA_3D
+        if args.rows3d != w.n2:
+            w = w.scaled(n2=args.rows3d, n3=args.rows3d, name=f"drift_plasma_3d_1024x{args.rows3d}x{args.rows3d}_f32")
         E0, B0 = wl.band_limited_fields(w)
         J0, _ = wl.band_limited_fields(w.scaled(seed=w.seed + 50))
         cells, alg_bytes = w.cells, 60 * w.cells

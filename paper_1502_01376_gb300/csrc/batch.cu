@@ -190,7 +190,23 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
         if (fail) { for (void* p : bufs) cudaFree(p); result = cuda_fail(cudaErrorMemoryAllocation, "hyb_batch_tune scratch"); break; }
         float best = 1e30f;
         int best_h = G.rows_per_strip;
-        for (int h : cand) {
+        // candidates: a fixed ladder plus, for 1 to 3 waves of resident CTAs, the smallest
+        // strip height whose work items fill that many waves
+        std::vector<int> hs(cand, cand + sizeof(cand) / sizeof(cand[0]));
+        {
+            int occ = 1, sms = 1;
+            if (fused_occupancy(G.n1, &occ) != cudaSuccess || occ < 1) occ = 1;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->grids[0]->device) != cudaSuccess) sms = 1;
+            for (int w = 1; w <= 3; w++)
+                for (int h = 2; h <= 64; h++) {
+                    int64_t items = 0;
+                    for (int m : G.members) items += (b->grids[m]->d.n2 + h - 1) / h;
+                    if (items <= (int64_t)w * sms * occ) { hs.push_back(h); break; }
+                }
+            std::sort(hs.begin(), hs.end());
+            hs.erase(std::unique(hs.begin(), hs.end()), hs.end());
+        }
+        for (int h : hs) {
             G.rows_per_strip = h;
             hyb_status st = group_plan(b, G);
             if (st != HYB_OK) { result = st; break; }
