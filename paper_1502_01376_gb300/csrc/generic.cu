@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "hyb_internal.cuh"
+#include "packed_dev.cuh"
 
 namespace hyb {
 
@@ -105,11 +106,153 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
     }
 }
 
+// ---------------------------------------------------------------- n1 = 1024, FP32: register-resident row FFT
+// The 512-point complex FFT of z[j] = x[2j] + i x[2j+1], factored 8 x 8 x 8 over 64 threads per
+// row (8 points each), the exchanges through shared memory, then the real-input split in
+// (k, M - k) pairs:
+//   S1  thread t: z[t + 64 n], DFT8 over n -> k1, twiddle W_512^{t k1}          -> A[64 k1 + t]
+//   S2  (t0, k1) = (t & 7, t >> 3): A[64 k1 + t0 + 8 t1], DFT8 over t1 -> k2,
+//       twiddle W_64^{t0 k2}                                                  -> B[9 (8 k1 + k2) + t0]
+//   S3  (k1, k2) = (t >> 3, t & 7): B[9 (8 k1 + k2) + t0], DFT8 over t0 -> Z[k1 + 8 k2 + 64 k3]
+// Z is stored at k + k / 8 (padding against bank conflicts).  The inverse runs the stages
+// transposed with conjugate twiddles.  Four rows per block, one named barrier per row.
+constexpr int kRows1k = 4;
+constexpr int kBuf1k = 576;
+__device__ __forceinline__ int zp1k(int k) { return k + (k >> 3); }
+__device__ __forceinline__ float2 cm(float2 a, float2 b) { return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
+__device__ __forceinline__ float2 cmc(float2 a, float2 b) { return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y)); }
+
+__global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict__ out, int64_t rows,
+                                                  const float2* __restrict__ twM, const float2* __restrict__ twN) {
+    __shared__ float2 sbuf[kRows1k][2][kBuf1k];
+    const int L = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int64_t row = (int64_t)blockIdx.x * kRows1k + L;
+    const bool live = row < rows;
+    const int f = blockIdx.y;
+    float2* A = sbuf[L][0];
+    float2* B = sbuf[L][1];
+    auto lsync = [&]() { asm volatile("bar.sync %0, %1;" :: "r"(1 + L), "r"(64) : "memory"); };
+    float2 v[8];
+    {
+        const float2* z = reinterpret_cast<const float2*>(in.p[f]) + (live ? row : 0) * 512;
+#pragma unroll
+        for (int n = 0; n < 8; n++) v[n] = live ? z[t + 64 * n] : make_float2(0.f, 0.f);
+    }
+    dft8x<false>(v);
+#pragma unroll
+    for (int k = 1; k < 8; k++) v[k] = cm(v[k], twM[t * k]);
+#pragma unroll
+    for (int k = 0; k < 8; k++) A[64 * k + t] = v[k];
+    lsync();
+    {
+        const int t0 = t & 7, k1 = t >> 3;
+#pragma unroll
+        for (int n = 0; n < 8; n++) v[n] = A[64 * k1 + t0 + 8 * n];
+        dft8x<false>(v);
+#pragma unroll
+        for (int k = 1; k < 8; k++) v[k] = cm(v[k], twM[8 * t0 * k]);
+#pragma unroll
+        for (int k = 0; k < 8; k++) B[9 * (8 * k1 + k) + t0] = v[k];
+    }
+    lsync();
+    {
+        const int k1 = t >> 3, k2 = t & 7;
+#pragma unroll
+        for (int n = 0; n < 8; n++) v[n] = B[9 * (8 * k1 + k2) + n];
+        dft8x<false>(v);
+#pragma unroll
+        for (int k = 0; k < 8; k++) A[zp1k(k1 + 8 * k2 + 64 * k)] = v[k];
+    }
+    lsync();
+    if (live) {
+        float2* X = out + ((int64_t)f * rows + row) * 513;
+        // X[k] = e - u, X[M-k] = conj(e + u), e = (Z[k] + Z*[M-k])/2, u = (i/2) W_N^k (Z[k] - Z*[M-k])
+        auto pair = [&](int k) {
+            const float2 zk = A[zp1k(k)], zm = A[zp1k((512 - k) & 511)];
+            const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            const float2 wd = cm(twN[k], make_float2(zk.x - zm.x, zk.y + zm.y));
+            X[k] = make_float2(e.x + 0.5f * wd.y, e.y - 0.5f * wd.x);
+            if (k != 256) X[512 - k] = make_float2(e.x - 0.5f * wd.y, -(e.y + 0.5f * wd.x));
+        };
+#pragma unroll
+        for (int m = 0; m < 4; m++) pair(t + 64 * m);
+        if (t == 0) pair(256);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in, RowPtrsW out, int64_t rows,
+                                                   const float2* __restrict__ twM, const float2* __restrict__ twN,
+                                                   int in_field0) {
+    __shared__ float2 sbuf[kRows1k][2][kBuf1k];
+    const int L = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int64_t row = (int64_t)blockIdx.x * kRows1k + L;
+    const bool live = row < rows;
+    const int f = blockIdx.y;
+    float2* A = sbuf[L][0];
+    float2* B = sbuf[L][1];
+    auto lsync = [&]() { asm volatile("bar.sync %0, %1;" :: "r"(1 + L), "r"(64) : "memory"); };
+    {
+        const float2* X = in + ((int64_t)(in_field0 + f) * rows + (live ? row : 0)) * 513;
+        // Z[k] = E + iO, Z[M-k] = conj(E - iO), E = (X[k] + X*[M-k])/2, O = conj(W_N^k)(X[k] - X*[M-k])/2;
+        // the imaginary parts of X[0] and X[M] are dropped
+        auto pair = [&](int k) {
+            float2 xk = X[k], xm = X[512 - k];
+            if (k == 0) { xk.y = 0.f; xm.y = 0.f; }
+            const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y - xm.y));
+            const float2 o = cmc(make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y + xm.y)), twN[k]);
+            A[zp1k(k)] = make_float2(e.x - o.y, e.y + o.x);
+            if (k != 0 && k != 256) A[zp1k(512 - k)] = make_float2(e.x + o.y, o.x - e.y);
+        };
+#pragma unroll
+        for (int m = 0; m < 4; m++) pair(t + 64 * m);
+        if (t == 0) pair(256);
+    }
+    lsync();
+    float2 v[8];
+    {
+        const int k1 = t >> 3, k2 = t & 7;
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = A[zp1k(k1 + 8 * k2 + 64 * k)];
+        dft8x<true>(v);
+#pragma unroll
+        for (int n = 0; n < 8; n++) B[9 * (8 * k1 + k2) + n] = v[n];
+    }
+    lsync();
+    {
+        const int t0 = t & 7, k1 = t >> 3;
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = B[9 * (8 * k1 + k) + t0];
+#pragma unroll
+        for (int k = 1; k < 8; k++) v[k] = cmc(v[k], twM[8 * t0 * k]);
+        dft8x<true>(v);
+#pragma unroll
+        for (int n = 0; n < 8; n++) A[64 * k1 + t0 + 8 * n] = v[n];
+    }
+    lsync();
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = A[64 * k + t];
+#pragma unroll
+    for (int k = 1; k < 8; k++) v[k] = cmc(v[k], twM[t * k]);
+    dft8x<true>(v);
+    if (live) {
+        float2* z = reinterpret_cast<float2*>(out.p[f]) + row * 512;
+        const float inv = 1.f / 512.f;
+#pragma unroll
+        for (int n = 0; n < 8; n++) z[t + 64 * n] = make_float2(v[n].x * inv, v[n].y * inv);
+    }
+}
+
 template <typename T>
 static size_t row_fft_smem(int n1, int RB) { return sizeof(cplx<T>) * 2 * fpad_size((size_t)RB * (n1 / 2)); }
 
 template <typename Tin, typename T>
 static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
+    if constexpr (std::is_same<Tin, float>::value && std::is_same<T, float>::value) {
+        if (n1 == 1024) {
+            k_rfft1024<<<dim3((unsigned)((rows + kRows1k - 1) / kRows1k), nf), 256, 0, s>>>(p, out, rows, t.twM, t.twN);
+            return cudaGetLastError();
+        }
+    }
     const int RB = fft_rows_per_launch(n1 / 2, rows * nf);
     const size_t smem = row_fft_smem<T>(n1, RB);
     auto kern = k_rfft_rows<Tin, T>;
@@ -122,6 +265,12 @@ static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, i
 
 template <typename T, typename Tout>
 static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, int nf, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value && std::is_same<Tout, float>::value) {
+        if (n1 == 1024) {
+            k_irfft1024<<<dim3((unsigned)((rows + kRows1k - 1) / kRows1k), nf), 256, 0, s>>>(in, p, rows, t.twM, t.twN, f0);
+            return cudaGetLastError();
+        }
+    }
     const int RB = fft_rows_per_launch(n1 / 2, rows * nf);
     const size_t smem = row_fft_smem<T>(n1, RB);
     auto kern = k_irfft_rows<T, Tout>;

@@ -43,6 +43,16 @@ def test_three_pass_extreme_row_lengths(orc, prec, n1, n2):
     assert max(errs) < TOL[prec], errs
 
 
+def test_three_pass_3d_1024_rows_fp32(orc):
+    """The 3D benchmark's row length (the register-resident 1024-point row FFT) with a ragged row count."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("e31", 3, 1024, 6, 5, dx1=0.2, dx2=0.2, dx3=0.2, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2,
+                    seed=14)
+    errs = _run(orc, hyb, w, path=1)
+    assert max(errs) < TOL[32], errs
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_three_pass_3d_two_planes(orc, prec):
     need_gpu()
