@@ -110,15 +110,18 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
 // The 512-point complex FFT of z[j] = x[2j] + i x[2j+1], factored 8 x 8 x 8 over 64 threads per
 // row (8 points each), the exchanges through shared memory, then the real-input split in
 // (k, M - k) pairs:
-//   S1  thread t: z[t + 64 n], DFT8 over n -> k1, twiddle W_512^{t k1}          -> A[64 k1 + t]
-//   S2  (t0, k1) = (t & 7, t >> 3): A[64 k1 + t0 + 8 t1], DFT8 over t1 -> k2,
+//   S1  thread t: z[t + 64 n], DFT8 over n -> k1, twiddle W_512^{t k1}          -> A(k1, t)
+//   S2  (t0, k1) = (t & 7, t >> 3): A(k1, t0 + 8 t1), DFT8 over t1 -> k2,
 //       twiddle W_64^{t0 k2}                                                  -> B[9 (8 k1 + k2) + t0]
 //   S3  (k1, k2) = (t >> 3, t & 7): B[9 (8 k1 + k2) + t0], DFT8 over t0 -> Z[k1 + 8 k2 + 64 k3]
-// Z is stored at k + k / 8 (padding against bank conflicts).  The inverse runs the stages
+// A(k, t) is stored at 64 k + t and Z[k] at k + k / 8 (padding against bank conflicts).
+// The inverse runs the stages
 // transposed with conjugate twiddles.  Four rows per block, one named barrier per row.
 constexpr int kRows1k = 4;
 constexpr int kBuf1k = 576;
 __device__ __forceinline__ int zp1k(int k) { return k + (k >> 3); }
+// stage-1 output (k1, t) position
+__device__ __forceinline__ int ap1k(int k, int t) { return 64 * k + t; }
 __device__ __forceinline__ float2 cm(float2 a, float2 b) { return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
 __device__ __forceinline__ float2 cmc(float2 a, float2 b) { return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y)); }
 
@@ -142,12 +145,12 @@ __global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict
 #pragma unroll
     for (int k = 1; k < 8; k++) v[k] = cm(v[k], twM[t * k]);
 #pragma unroll
-    for (int k = 0; k < 8; k++) A[64 * k + t] = v[k];
+    for (int k = 0; k < 8; k++) A[ap1k(k, t)] = v[k];
     lsync();
     {
         const int t0 = t & 7, k1 = t >> 3;
 #pragma unroll
-        for (int n = 0; n < 8; n++) v[n] = A[64 * k1 + t0 + 8 * n];
+        for (int n = 0; n < 8; n++) v[n] = A[ap1k(k1, t0 + 8 * n)];
         dft8x<false>(v);
 #pragma unroll
         for (int k = 1; k < 8; k++) v[k] = cm(v[k], twM[8 * t0 * k]);
@@ -226,11 +229,11 @@ __global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in
         for (int k = 1; k < 8; k++) v[k] = cmc(v[k], twM[8 * t0 * k]);
         dft8x<true>(v);
 #pragma unroll
-        for (int n = 0; n < 8; n++) A[64 * k1 + t0 + 8 * n] = v[n];
+        for (int n = 0; n < 8; n++) A[ap1k(k1, t0 + 8 * n)] = v[n];
     }
     lsync();
 #pragma unroll
-    for (int k = 0; k < 8; k++) v[k] = A[64 * k + t];
+    for (int k = 0; k < 8; k++) v[k] = A[ap1k(k, t)];
 #pragma unroll
     for (int k = 1; k < 8; k++) v[k] = cmc(v[k], twM[t * k]);
     dft8x<true>(v);
@@ -249,6 +252,8 @@ template <typename Tin, typename T>
 static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
     if constexpr (std::is_same<Tin, float>::value && std::is_same<T, float>::value) {
         if (n1 == 1024) {
+            static bool carve = (cudaFuncSetAttribute(k_rfft1024, cudaFuncAttributePreferredSharedMemoryCarveout, 100), true);
+            (void)carve;
             k_rfft1024<<<dim3((unsigned)((rows + kRows1k - 1) / kRows1k), nf), 256, 0, s>>>(p, out, rows, t.twM, t.twN);
             return cudaGetLastError();
         }
@@ -267,6 +272,8 @@ template <typename T, typename Tout>
 static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, int nf, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
     if constexpr (std::is_same<T, float>::value && std::is_same<Tout, float>::value) {
         if (n1 == 1024) {
+            static bool carve = (cudaFuncSetAttribute(k_irfft1024, cudaFuncAttributePreferredSharedMemoryCarveout, 100), true);
+            (void)carve;
             k_irfft1024<<<dim3((unsigned)((rows + kRows1k - 1) / kRows1k), nf), 256, 0, s>>>(in, p, rows, t.twM, t.twN, f0);
             return cudaGetLastError();
         }
