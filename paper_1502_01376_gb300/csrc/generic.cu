@@ -3,6 +3,8 @@
 //   (2) per-k1-mode Faraday then Ampere updates with finite differences in
 //       x2 (and x3) (Eqs. hybrid2db1-hybrid2de3; Sec. 2.4 for 3D),
 //   (3) batched inverse real FFT of E, B back in place.
+// For FP32 rows of 1024 points the Ampere update of (2) is folded into (3),
+// which then reads the spectra of E, B, j and writes E, B (three launches).
 // It also provides the row FFTs used by the standalone current processing and
 // the diagnostics.  The x1 transform is a shared-memory Stockham FFT (radix 8,
 // then one radix-4 or radix-2 pass; several short rows per block)
@@ -183,23 +185,17 @@ __global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict
     }
 }
 
-__global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in, RowPtrsW out, int64_t rows,
-                                                   const float2* __restrict__ twM, const float2* __restrict__ twN,
-                                                   int in_field0) {
-    __shared__ float2 sbuf[kRows1k][2][kBuf1k];
-    const int L = threadIdx.x >> 6, t = threadIdx.x & 63;
-    const int64_t row = (int64_t)blockIdx.x * kRows1k + L;
-    const bool live = row < rows;
-    const int f = blockIdx.y;
-    float2* A = sbuf[L][0];
-    float2* B = sbuf[L][1];
+// Inverse of one row from its spectrum, X[k] = ld(k) for k = 0..M (the stages of k_rfft1024 in
+// reverse with conjugate twiddles); z_out receives the 1024 real samples (nullptr: dead row).
+template <class Ld>
+__device__ __forceinline__ void irfft1024_row(float2* A, float2* B, int L, int t, float2* __restrict__ z_out,
+                                              const float2* __restrict__ twM, const float2* __restrict__ twN, Ld ld) {
     auto lsync = [&]() { asm volatile("bar.sync %0, %1;" :: "r"(1 + L), "r"(64) : "memory"); };
     {
-        const float2* X = in + ((int64_t)(in_field0 + f) * rows + (live ? row : 0)) * 513;
         // Z[k] = E + iO, Z[M-k] = conj(E - iO), E = (X[k] + X*[M-k])/2, O = conj(W_N^k)(X[k] - X*[M-k])/2;
         // the imaginary parts of X[0] and X[M] are dropped
         auto pair = [&](int k) {
-            float2 xk = X[k], xm = X[512 - k];
+            float2 xk = ld(k), xm = ld(512 - k);
             if (k == 0) { xk.y = 0.f; xm.y = 0.f; }
             const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y - xm.y));
             const float2 o = cmc(make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y + xm.y)), twN[k]);
@@ -237,11 +233,79 @@ __global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in
 #pragma unroll
     for (int k = 1; k < 8; k++) v[k] = cmc(v[k], twM[t * k]);
     dft8x<true>(v);
-    if (live) {
-        float2* z = reinterpret_cast<float2*>(out.p[f]) + row * 512;
+    if (z_out) {
         const float inv = 1.f / 512.f;
 #pragma unroll
-        for (int n = 0; n < 8; n++) z[t + 64 * n] = make_float2(v[n].x * inv, v[n].y * inv);
+        for (int n = 0; n < 8; n++) z_out[t + 64 * n] = make_float2(v[n].x * inv, v[n].y * inv);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in, RowPtrsW out, int64_t rows,
+                                                   const float2* __restrict__ twM, const float2* __restrict__ twN,
+                                                   int in_field0) {
+    __shared__ float2 sbuf[kRows1k][2][kBuf1k];
+    const int L = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int64_t row = (int64_t)blockIdx.x * kRows1k + L;
+    const bool live = row < rows;
+    const int f = blockIdx.y;
+    const float2* X = in + ((int64_t)(in_field0 + f) * rows + (live ? row : 0)) * 513;
+    float2* z = live ? reinterpret_cast<float2*>(out.p[f]) + row * 512 : nullptr;
+    irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) { return X[k]; });
+}
+
+// Ampere (Eqs. hybrid2de1-hybrid2de3; the x3 differences of Sec. 2.4) fused into the inverse
+// transform of E, B: blocks of kRows1k rows of one field, the six fields of a row group in
+// consecutive blocks so that the B rows three of them read come from L2.  Fields 0-2 apply Ampere
+// to E_f mode by mode as they load it (Sm = -conj(S) = c dt sigma-):
+//   E1 += a2 d2-B3 - a3 d3-B2 - cj1 J1;  E2 += a3 d3-B1 - Sm B3 - cj J2;  E3 += Sm B2 - a2 d2-B1 - cj J3
+// fields 3-5 invert B.  The spectral scratch is only read.
+template <bool D3>
+__global__ void __launch_bounds__(256) k_ampere_irfft1024(const float2* __restrict__ spec, RowPtrsW out, int64_t rows, int n2, int n3,
+                                                          const float2* __restrict__ twM, const float2* __restrict__ twN,
+                                                          const float2* __restrict__ S, const float* __restrict__ cj1,
+                                                          const float* __restrict__ cj, float a2, float a3) {
+    __shared__ float2 sbuf[kRows1k][2][kBuf1k];
+    const int L = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int f = blockIdx.x % 6;
+    const int64_t row = (int64_t)(blockIdx.x / 6) * kRows1k + L;
+    const bool live = row < rows;
+    const int64_t r = live ? row : 0;
+    const int64_t i3 = r / n2;
+    const int i2 = (int)(r - i3 * n2);
+    const int64_t fs = rows * 513;
+    const float2* Xr = spec + r * 513;                                            // field 0 of row r
+    const float2* Xm2 = spec + (i3 * n2 + (i2 == 0 ? n2 - 1 : i2 - 1)) * 513;     // row i2 - 1
+    const float2* Xm3 = spec + ((D3 ? (i3 == 0 ? n3 - 1 : i3 - 1) : i3) * n2 + i2) * 513;   // row i3 - 1
+    float2* z = live ? reinterpret_cast<float2*>(out.p[f]) + row * 512 : nullptr;
+    auto sub = [](float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); };
+    auto axpy = [](float2 y, float s, float2 x) { return make_float2(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y)); };
+    if (f == 0) {
+        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) {
+            float2 e = axpy(Xr[k], a2, sub(Xr[5 * fs + k], Xm2[5 * fs + k]));
+            if (D3) e = axpy(e, -a3, sub(Xr[4 * fs + k], Xm3[4 * fs + k]));
+            return axpy(e, -cj1[k], Xr[6 * fs + k]);
+        });
+    } else if (f == 1) {
+        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) {
+            const float2 s = S[k], b3 = Xr[5 * fs + k];
+            // - Sm B3 = conj(S) B3
+            float2 e = Xr[fs + k];
+            e = make_float2(e.x + (s.x * b3.x + s.y * b3.y), e.y + (s.x * b3.y - s.y * b3.x));
+            if (D3) e = axpy(e, a3, sub(Xr[3 * fs + k], Xm3[3 * fs + k]));
+            return axpy(e, -cj[k], Xr[7 * fs + k]);
+        });
+    } else if (f == 2) {
+        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) {
+            const float2 s = S[k], b2 = Xr[4 * fs + k];
+            // + Sm B2 = - conj(S) B2
+            float2 e = Xr[2 * fs + k];
+            e = make_float2(e.x - (s.x * b2.x + s.y * b2.y), e.y - (s.x * b2.y - s.y * b2.x));
+            e = axpy(e, -a2, sub(Xr[3 * fs + k], Xm2[3 * fs + k]));
+            return axpy(e, -cj[k], Xr[8 * fs + k]);
+        });
+    } else {
+        const float2* X = Xr + f * fs;
+        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) { return X[k]; });
     }
 }
 
@@ -401,6 +465,9 @@ template <typename T> static const ModeTables<T>& tables(hyb_grid* g);
 template <> const ModeTables<float>& tables<float>(hyb_grid* g) { return g->tf; }
 template <> const ModeTables<double>& tables<double>(hyb_grid* g) { return g->td; }
 
+// FP32 n1 = 1024 off the DFT-GEMM path: Ampere runs inside the inverse transform
+static bool amp_fused(const hyb_grid* g) { return g->d.precision == 32 && g->d.n1 == 1024 && g->path != 3; }
+
 template <typename T>
 hyb_status generic_advance(hyb_grid* g, int nsteps) {
     using C = cplx<T>;
@@ -426,6 +493,22 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
             HYB_CUDA_TRY((launch_rfft<T, T>(fin, 9, spec, n1, rows, t, g->stream)));
         }
         const dim3 mgrid((unsigned)((int64_t)g->d.n3 * ((g->d.n2 + kModeRows - 1) / kModeRows) * ((nk + 31) / 32))), mblk(32, kModeRows);
+        if constexpr (std::is_same<T, float>::value) {
+            if (amp_fused(g)) {
+                const float2* sp = reinterpret_cast<const float2*>(spec);
+                const unsigned nb = (unsigned)((rows + kRows1k - 1) / kRows1k) * 6u;
+                if (d3) {
+                    k_faraday<T, true><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
+                    k_ampere_irfft1024<true><<<nb, 256, 0, g->stream>>>(sp, fout, rows, g->d.n2, g->d.n3, t.twM, t.twN, t.S, t.cj1, t.cj, a2, a3);
+                } else {
+                    k_faraday<T, false><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, a2, a3);
+                    k_ampere_irfft1024<false><<<nb, 256, 0, g->stream>>>(sp, fout, rows, g->d.n2, 1, t.twM, t.twN, t.S, t.cj1, t.cj, a2, a3);
+                }
+                HYB_CUDA_TRY(cudaGetLastError());
+                if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
+                continue;
+            }
+        }
         if (d3) {
             k_faraday<T, true><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
             k_ampere<T, true><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, t.cj1, t.cj, a2, a3);
@@ -472,7 +555,7 @@ hyb_status generic_process_current(hyb_grid* g, bool corr, bool filt) {
     return HYB_OK;
 }
 
-hyb_status generic_launches_per_step() { return (hyb_status)4; }
+int generic_launches_per_step(const hyb_grid* g) { return amp_fused(g) ? 3 : 4; }
 
 template hyb_status generic_advance<float>(hyb_grid*, int);
 template hyb_status generic_advance<double>(hyb_grid*, int);

@@ -361,7 +361,7 @@ int hyb_launches_per_step(const hyb_grid* g) {
     if (!g) return 0;
     if (g->path == 2) return fused_launches_per_step(g);
     if (g->path == 3) return 11;     // split + product (forward), Faraday, Ampere, split + 6 products (inverse)
-    return (int)generic_launches_per_step();
+    return generic_launches_per_step(g);
 }
 
 }  // extern "C"

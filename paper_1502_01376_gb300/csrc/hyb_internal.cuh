@@ -194,7 +194,7 @@ hyb_status cuda_fail(cudaError_t e, const char* what);
 // three-pass path (generic.cu)
 template <typename T> hyb_status generic_advance(hyb_grid* g, int nsteps);
 template <typename T> hyb_status generic_process_current(hyb_grid* g, bool corr, bool filt);
-hyb_status generic_launches_per_step();
+int generic_launches_per_step(const hyb_grid* g);
 
 // batched real FFT along x1 (generic.cu); in: rows of n1 reals of Tin;
 // out: rows of n1/2+1 complex of T (strides in elements)

@@ -338,3 +338,37 @@ def test_fused_full_size_drift_plasma_grid(orc):
     hyb = hyb_module()
     errs = _fused_case(orc, hyb, 4096, 1024, 3, seed=31)
     assert max(errs) < 1e-5
+
+
+def test_three_pass_3d_full_size_sampled_rows(orc):
+    """The 3D 1024 x 256 x 256 FP32 grid in the launch configuration the benchmark times, one step,
+    checked on sampled x1 rows: after one step a row depends only on the rows of its 3 x 3 (x2, x3)
+    neighbourhood (Faraday reads E one row ahead, Ampere reads B one row behind), so the oracle run on
+    that periodic 1024 x 3 x 3 window gives the exact centre row."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.DRIFT_PLASMA_3D
+    n3, n2, n1 = w.shape
+    rng = np.random.default_rng(77)
+    host = [rng.standard_normal(w.shape, dtype=np.float32) * np.float32(1e-3) for _ in range(9)]
+    dev = [torch.from_numpy(a).cuda() for a in host]
+    g = hyb.Grid(hyb.desc_from_workload(w, path=1))
+    g.bind(dev[0:3], dev[3:6], dev[6:9])
+    g.advance(1)
+    g.check()
+    torch.cuda.synchronize()
+    ww = w.scaled(n2=3, n3=3)
+    go = orc_grid(orc, ww)
+    samples = [(0, 0), (0, n2 - 1), (n3 - 1, 0), (n3 - 1, n2 - 1), (1, 3), (128, 127), (255, 128)]
+    samples += [tuple(int(v) for v in rng.integers(0, (n3, n2))) for _ in range(5)]
+    for i3, i2 in samples:
+        win = np.ix_([(i3 - 1) % n3, i3, (i3 + 1) % n3], [(i2 - 1) % n2, i2, (i2 + 1) % n2])
+        fw = [a[win].astype(np.float64) for a in host]
+        Eo, Bo = fw[0:3], fw[3:6]
+        orc.step(go, Eo, Bo, fw[6:9], nsteps=1)
+        for name, d, o in zip(("E1", "E2", "E3", "B1", "B2", "B3"), dev[0:6], Eo + Bo):
+            got = d[i3, i2].double().cpu().numpy()
+            ref = o[1, 1]
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err < TOL[32], (i3, i2, name, err)
+    g.close()

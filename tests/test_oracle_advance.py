@@ -350,6 +350,34 @@ def test_gauss_law_3d(orc):
         assert np.max(np.abs(G1 - G0)) < 1e-12 * np.max(np.abs(G0))
 
 
+def test_one_step_is_local_to_a_3x3_window(orc):
+    """One step moves information one row in x2 and x3 (Faraday reads E one row ahead, Ampere B one
+    row behind), so the step on the periodic 3 x 3 (x2, x3) window around a row gives that row's
+    result on the whole grid: the reduction the full-size GPU test samples with."""
+    n1, n2, n3 = 16, 6, 5
+    g = orc.grid(dims=3, n1=n1, n2=n2, n3=n3, dx1=0.2, dx2=0.2, dx3=0.25, dt=0.06, filt_kc=0.5, filt_w=0.2)
+    gw = orc.grid(dims=3, n1=n1, n2=3, n3=3, dx1=0.2, dx2=0.2, dx3=0.25, dt=0.06, filt_kc=0.5, filt_w=0.2)
+    rng = np.random.default_rng(21)
+    F = [rng.standard_normal((n3, n2, n1)) for _ in range(9)]
+    E, B = [a.copy() for a in F[0:3]], [a.copy() for a in F[3:6]]
+    orc.step(g, E, B, [a.copy() for a in F[6:9]], nsteps=1)
+    for i3 in range(n3):
+        for i2 in range(n2):
+            win = np.ix_([(i3 - 1) % n3, i3, (i3 + 1) % n3], [(i2 - 1) % n2, i2, (i2 + 1) % n2])
+            fw = [a[win] for a in F]
+            Ew, Bw = fw[0:3], fw[3:6]
+            orc.step(gw, Ew, Bw, fw[6:9], nsteps=1)
+            for full, part in zip(E + B, Ew + Bw):
+                np.testing.assert_allclose(part[1, 1], full[i3, i2], rtol=0, atol=1e-12)
+    # and a window too small to hold the neighbourhood is not exact
+    i3, i2 = 2, 3
+    fw = [a[np.ix_([i3 - 1, i3], [i2 - 1, i2])] for a in F]
+    g2 = orc.grid(dims=3, n1=n1, n2=2, n3=2, dx1=0.2, dx2=0.2, dx3=0.25, dt=0.06, filt_kc=0.5, filt_w=0.2)
+    Ew, Bw = fw[0:3], fw[3:6]
+    orc.step(g2, Ew, Bw, fw[6:9], nsteps=1)
+    assert np.max(np.abs(Ew[0][1, 1] - E[0][i3, i2])) > 1e-6
+
+
 # ---------------------------------------------------------------- tables
 def test_correction_and_filter_special_values(orc):
     n1 = 64
