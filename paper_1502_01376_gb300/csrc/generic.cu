@@ -10,6 +10,7 @@
 // then one radix-4 or radix-2 pass; several short rows per block)
 // of the n1/2-point complex sequence z[j] = x[2j] + i x[2j+1] followed by the
 // standard even/odd split into the n1/2+1 real-input coefficients.
+#include <algorithm>
 #include <type_traits>
 
 #include "hyb_internal.cuh"
@@ -116,61 +117,71 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
 //   S2  (t0, k1) = (t & 7, t >> 3): A(k1, t0 + 8 t1), DFT8 over t1 -> k2,
 //       twiddle W_64^{t0 k2}                                                  -> B[9 (8 k1 + k2) + t0]
 //   S3  (k1, k2) = (t >> 3, t & 7): B[9 (8 k1 + k2) + t0], DFT8 over t0 -> Z[k1 + 8 k2 + 64 k3]
-// A(k, t) is stored at 64 k + t and Z[k] at k + k / 8 (padding against bank conflicts).
+// A(k, t) is stored at 72 k + t and Z[k] at k + k / 8 (padding against bank conflicts); the
+// twiddles of S1 and S2 come from a table laid out in the order the threads read them.
 // The inverse runs the stages
 // transposed with conjugate twiddles.  Four rows per block, one named barrier per row.
 constexpr int kRows1k = 4;
 constexpr int kBuf1k = 576;
 __device__ __forceinline__ int zp1k(int k) { return k + (k >> 3); }
 // stage-1 output (k1, t) position
-__device__ __forceinline__ int ap1k(int k, int t) { return 64 * k + t; }
+__device__ __forceinline__ int ap1k(int k, int t) { return 72 * k + t; }
 __device__ __forceinline__ float2 cm(float2 a, float2 b) { return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
 __device__ __forceinline__ float2 cmc(float2 a, float2 b) { return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y)); }
 
-__global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict__ out, int64_t rows,
-                                                  const float2* __restrict__ twM, const float2* __restrict__ twN) {
+// Persistent: each 64-thread team (four per block) walks the rows j = team, team + teams, ... of all
+// fields (field j / rows), holding the next row's samples in registers while it transforms the
+// current one, so that every team keeps a row of loads in flight.
+__global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict__ out, int64_t rows, int nf,
+                                                  const float2* __restrict__ tw8, const float2* __restrict__ twN) {
     __shared__ float2 sbuf[kRows1k][2][kBuf1k];
     const int L = threadIdx.x >> 6, t = threadIdx.x & 63;
-    const int64_t row = (int64_t)blockIdx.x * kRows1k + L;
-    const bool live = row < rows;
-    const int f = blockIdx.y;
+    const int64_t total = rows * nf, teams = (int64_t)gridDim.x * kRows1k;
     float2* A = sbuf[L][0];
     float2* B = sbuf[L][1];
     auto lsync = [&]() { asm volatile("bar.sync %0, %1;" :: "r"(1 + L), "r"(64) : "memory"); };
-    float2 v[8];
-    {
-        const float2* z = reinterpret_cast<const float2*>(in.p[f]) + (live ? row : 0) * 512;
+    float2 nx[8];
+    auto fetch = [&](int64_t j) {
+        const int f = (int)(j / rows);
+        const float2* z = reinterpret_cast<const float2*>(in.p[f]) + (j - (int64_t)f * rows) * 512;
 #pragma unroll
-        for (int n = 0; n < 8; n++) v[n] = live ? z[t + 64 * n] : make_float2(0.f, 0.f);
-    }
-    dft8x<false>(v);
+        for (int n = 0; n < 8; n++) nx[n] = __ldcs(z + t + 64 * n);
+    };
+    int64_t j = (int64_t)blockIdx.x * kRows1k + L;
+    if (j < total) fetch(j);
+    for (; j < total; j += teams) {
+        float2 v[8];
 #pragma unroll
-    for (int k = 1; k < 8; k++) v[k] = cm(v[k], twM[t * k]);
-#pragma unroll
-    for (int k = 0; k < 8; k++) A[ap1k(k, t)] = v[k];
-    lsync();
-    {
-        const int t0 = t & 7, k1 = t >> 3;
-#pragma unroll
-        for (int n = 0; n < 8; n++) v[n] = A[ap1k(k1, t0 + 8 * n)];
+        for (int n = 0; n < 8; n++) v[n] = nx[n];
+        if (j + teams < total) fetch(j + teams);
         dft8x<false>(v);
 #pragma unroll
-        for (int k = 1; k < 8; k++) v[k] = cm(v[k], twM[8 * t0 * k]);
+        for (int k = 1; k < 8; k++) v[k] = cm(v[k], tw8[(k - 1) * 64 + t]);
+        lsync();                     // the previous row's split has read A
 #pragma unroll
-        for (int k = 0; k < 8; k++) B[9 * (8 * k1 + k) + t0] = v[k];
-    }
-    lsync();
-    {
-        const int k1 = t >> 3, k2 = t & 7;
+        for (int k = 0; k < 8; k++) A[ap1k(k, t)] = v[k];
+        lsync();
+        {
+            const int t0 = t & 7, k1 = t >> 3;
 #pragma unroll
-        for (int n = 0; n < 8; n++) v[n] = B[9 * (8 * k1 + k2) + n];
-        dft8x<false>(v);
+            for (int n = 0; n < 8; n++) v[n] = A[ap1k(k1, t0 + 8 * n)];
+            dft8x<false>(v);
 #pragma unroll
-        for (int k = 0; k < 8; k++) A[zp1k(k1 + 8 * k2 + 64 * k)] = v[k];
-    }
-    lsync();
-    if (live) {
-        float2* X = out + ((int64_t)f * rows + row) * 513;
+            for (int k = 1; k < 8; k++) v[k] = cm(v[k], tw8[448 + (k - 1) * 8 + t0]);
+#pragma unroll
+            for (int k = 0; k < 8; k++) B[9 * (8 * k1 + k) + t0] = v[k];
+        }
+        lsync();
+        {
+            const int k1 = t >> 3, k2 = t & 7;
+#pragma unroll
+            for (int n = 0; n < 8; n++) v[n] = B[9 * (8 * k1 + k2) + n];
+            dft8x<false>(v);
+#pragma unroll
+            for (int k = 0; k < 8; k++) A[zp1k(k1 + 8 * k2 + 64 * k)] = v[k];
+        }
+        lsync();
+        float2* X = out + j * 513;   // [field][row][513], j = field * rows + row
         // X[k] = e - u, X[M-k] = conj(e + u), e = (Z[k] + Z*[M-k])/2, u = (i/2) W_N^k (Z[k] - Z*[M-k])
         auto pair = [&](int k) {
             const float2 zk = A[zp1k(k)], zm = A[zp1k((512 - k) & 511)];
@@ -189,7 +200,7 @@ __global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict
 // reverse with conjugate twiddles); z_out receives the 1024 real samples (nullptr: dead row).
 template <class Ld>
 __device__ __forceinline__ void irfft1024_row(float2* A, float2* B, int L, int t, float2* __restrict__ z_out,
-                                              const float2* __restrict__ twM, const float2* __restrict__ twN, Ld ld) {
+                                              const float2* __restrict__ tw8, const float2* __restrict__ twN, Ld ld) {
     auto lsync = [&]() { asm volatile("bar.sync %0, %1;" :: "r"(1 + L), "r"(64) : "memory"); };
     {
         // Z[k] = E + iO, Z[M-k] = conj(E - iO), E = (X[k] + X*[M-k])/2, O = conj(W_N^k)(X[k] - X*[M-k])/2;
@@ -222,7 +233,7 @@ __device__ __forceinline__ void irfft1024_row(float2* A, float2* B, int L, int t
 #pragma unroll
         for (int k = 0; k < 8; k++) v[k] = B[9 * (8 * k1 + k) + t0];
 #pragma unroll
-        for (int k = 1; k < 8; k++) v[k] = cmc(v[k], twM[8 * t0 * k]);
+        for (int k = 1; k < 8; k++) v[k] = cmc(v[k], tw8[448 + (k - 1) * 8 + t0]);
         dft8x<true>(v);
 #pragma unroll
         for (int n = 0; n < 8; n++) A[ap1k(k1, t0 + 8 * n)] = v[n];
@@ -231,7 +242,7 @@ __device__ __forceinline__ void irfft1024_row(float2* A, float2* B, int L, int t
 #pragma unroll
     for (int k = 0; k < 8; k++) v[k] = A[ap1k(k, t)];
 #pragma unroll
-    for (int k = 1; k < 8; k++) v[k] = cmc(v[k], twM[t * k]);
+    for (int k = 1; k < 8; k++) v[k] = cmc(v[k], tw8[(k - 1) * 64 + t]);
     dft8x<true>(v);
     if (z_out) {
         const float inv = 1.f / 512.f;
@@ -241,7 +252,7 @@ __device__ __forceinline__ void irfft1024_row(float2* A, float2* B, int L, int t
 }
 
 __global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in, RowPtrsW out, int64_t rows,
-                                                   const float2* __restrict__ twM, const float2* __restrict__ twN,
+                                                   const float2* __restrict__ tw8, const float2* __restrict__ twN,
                                                    int in_field0) {
     __shared__ float2 sbuf[kRows1k][2][kBuf1k];
     const int L = threadIdx.x >> 6, t = threadIdx.x & 63;
@@ -250,7 +261,7 @@ __global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in
     const int f = blockIdx.y;
     const float2* X = in + ((int64_t)(in_field0 + f) * rows + (live ? row : 0)) * 513;
     float2* z = live ? reinterpret_cast<float2*>(out.p[f]) + row * 512 : nullptr;
-    irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) { return X[k]; });
+    irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, tw8, twN, [&](int k) { return X[k]; });
 }
 
 // Ampere (Eqs. hybrid2de1-hybrid2de3; the x3 differences of Sec. 2.4) fused into the inverse
@@ -261,7 +272,7 @@ __global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in
 // fields 3-5 invert B.  The spectral scratch is only read.
 template <bool D3>
 __global__ void __launch_bounds__(256) k_ampere_irfft1024(const float2* __restrict__ spec, RowPtrsW out, int64_t rows, int n2, int n3,
-                                                          const float2* __restrict__ twM, const float2* __restrict__ twN,
+                                                          const float2* __restrict__ tw8, const float2* __restrict__ twN,
                                                           const float2* __restrict__ S, const float* __restrict__ cj1,
                                                           const float* __restrict__ cj, float a2, float a3) {
     __shared__ float2 sbuf[kRows1k][2][kBuf1k];
@@ -280,13 +291,13 @@ __global__ void __launch_bounds__(256) k_ampere_irfft1024(const float2* __restri
     auto sub = [](float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); };
     auto axpy = [](float2 y, float s, float2 x) { return make_float2(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y)); };
     if (f == 0) {
-        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) {
+        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, tw8, twN, [&](int k) {
             float2 e = axpy(Xr[k], a2, sub(Xr[5 * fs + k], Xm2[5 * fs + k]));
             if (D3) e = axpy(e, -a3, sub(Xr[4 * fs + k], Xm3[4 * fs + k]));
             return axpy(e, -cj1[k], Xr[6 * fs + k]);
         });
     } else if (f == 1) {
-        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) {
+        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, tw8, twN, [&](int k) {
             const float2 s = S[k], b3 = Xr[5 * fs + k];
             // - Sm B3 = conj(S) B3
             float2 e = Xr[fs + k];
@@ -295,7 +306,7 @@ __global__ void __launch_bounds__(256) k_ampere_irfft1024(const float2* __restri
             return axpy(e, -cj[k], Xr[7 * fs + k]);
         });
     } else if (f == 2) {
-        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) {
+        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, tw8, twN, [&](int k) {
             const float2 s = S[k], b2 = Xr[4 * fs + k];
             // + Sm B2 = - conj(S) B2
             float2 e = Xr[2 * fs + k];
@@ -305,7 +316,7 @@ __global__ void __launch_bounds__(256) k_ampere_irfft1024(const float2* __restri
         });
     } else {
         const float2* X = Xr + f * fs;
-        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, twM, twN, [&](int k) { return X[k]; });
+        irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, tw8, twN, [&](int k) { return X[k]; });
     }
 }
 
@@ -316,9 +327,16 @@ template <typename Tin, typename T>
 static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
     if constexpr (std::is_same<Tin, float>::value && std::is_same<T, float>::value) {
         if (n1 == 1024) {
-            static bool carve = (cudaFuncSetAttribute(k_rfft1024, cudaFuncAttributePreferredSharedMemoryCarveout, 100), true);
-            (void)carve;
-            k_rfft1024<<<dim3((unsigned)((rows + kRows1k - 1) / kRows1k), nf), 256, 0, s>>>(p, out, rows, t.twM, t.twN);
+            static const int resident = [] {
+                cudaFuncSetAttribute(k_rfft1024, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+                int dev = 0, sms = 0, occ = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rfft1024, 256, 0);
+                return std::max(1, sms * occ);
+            }();
+            const int64_t blocks = std::min<int64_t>((rows * nf + kRows1k - 1) / kRows1k, resident);
+            k_rfft1024<<<(unsigned)blocks, 256, 0, s>>>(p, out, rows, nf, t.tw8, t.twN);
             return cudaGetLastError();
         }
     }
@@ -338,7 +356,7 @@ static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, in
         if (n1 == 1024) {
             static bool carve = (cudaFuncSetAttribute(k_irfft1024, cudaFuncAttributePreferredSharedMemoryCarveout, 100), true);
             (void)carve;
-            k_irfft1024<<<dim3((unsigned)((rows + kRows1k - 1) / kRows1k), nf), 256, 0, s>>>(in, p, rows, t.twM, t.twN, f0);
+            k_irfft1024<<<dim3((unsigned)((rows + kRows1k - 1) / kRows1k), nf), 256, 0, s>>>(in, p, rows, t.tw8, t.twN, f0);
             return cudaGetLastError();
         }
     }
@@ -499,10 +517,10 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
                 const unsigned nb = (unsigned)((rows + kRows1k - 1) / kRows1k) * 6u;
                 if (d3) {
                     k_faraday<T, true><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
-                    k_ampere_irfft1024<true><<<nb, 256, 0, g->stream>>>(sp, fout, rows, g->d.n2, g->d.n3, t.twM, t.twN, t.S, t.cj1, t.cj, a2, a3);
+                    k_ampere_irfft1024<true><<<nb, 256, 0, g->stream>>>(sp, fout, rows, g->d.n2, g->d.n3, t.tw8, t.twN, t.S, t.cj1, t.cj, a2, a3);
                 } else {
                     k_faraday<T, false><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, a2, a3);
-                    k_ampere_irfft1024<false><<<nb, 256, 0, g->stream>>>(sp, fout, rows, g->d.n2, 1, t.twM, t.twN, t.S, t.cj1, t.cj, a2, a3);
+                    k_ampere_irfft1024<false><<<nb, 256, 0, g->stream>>>(sp, fout, rows, g->d.n2, 1, t.tw8, t.twN, t.S, t.cj1, t.cj, a2, a3);
                 }
                 HYB_CUDA_TRY(cudaGetLastError());
                 if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));

@@ -134,6 +134,8 @@ __host__ __forceinline__ int fft_rows_per_launch(int M, int64_t total_rows) {
 
 // ---------------------------------------------------------------- tables
 // Per-mode tables for kappa = 0..n1/2, computed in FP64 on the host and rounded once.
+constexpr int kTw8 = 504;   // entries of ModeTables::tw8
+
 template <typename T>
 struct ModeTables {
     cplx<T>* S = nullptr;     // c dt sigma+ = c dt i [k]1 exp(+i k1 dx1/2)
@@ -144,6 +146,10 @@ struct ModeTables {
     cplx<T>* twM = nullptr;   // W_M^j = exp(-2 pi i j / M), j < M, M = n1/2
     cplx<T>* twN = nullptr;   // W_N^k = exp(-2 pi i k / n1), k < M
     cplx<T>* sgp = nullptr;   // sigma+ (without c dt), for diagnostics
+    // M = 512 only (n1 = 1024, factored 8 x 8 x 8): the twiddles of the first two stages in the
+    // order the threads read them, [(k - 1) 64 + t] = W_512^{t k} (k = 1..7, t < 64), then
+    // [448 + (k - 1) 8 + t0] = W_64^{t0 k} (t0 < 8)
+    cplx<T>* tw8 = nullptr;
 };
 
 struct FusedPlan;   // defined in fused_api.cuh
