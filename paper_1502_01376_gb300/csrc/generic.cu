@@ -117,13 +117,15 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
 //   S2  (t0, k1) = (t & 7, t >> 3): A(k1, t0 + 8 t1), DFT8 over t1 -> k2,
 //       twiddle W_64^{t0 k2}                                                  -> B[9 (8 k1 + k2) + t0]
 //   S3  (k1, k2) = (t >> 3, t & 7): B[9 (8 k1 + k2) + t0], DFT8 over t0 -> Z[k1 + 8 k2 + 64 k3]
-// A(k, t) is stored at 72 k + t and Z[k] at k + k / 8 (padding against bank conflicts); the
+// A(k, t) is stored at 72 k + t and Z[k] at a swizzled position (both against bank conflicts); the
 // twiddles of S1 and S2 come from a table laid out in the order the threads read them.
 // The inverse runs the stages
 // transposed with conjugate twiddles.  Four rows per block, one named barrier per row.
 constexpr int kRows1k = 4;
 constexpr int kBuf1k = 576;
-__device__ __forceinline__ int zp1k(int k) { return k + (k >> 3); }
+// Z[k] at k with bit 2 flipped by bit 4: the S3 accesses (lanes over bits 0, 1, 3, 4, 5 of k) and the
+// split's runs of 32 consecutive k both touch every bank pair exactly twice per warp
+__device__ __forceinline__ int zp1k(int k) { return k ^ (((k >> 4) & 1) << 2); }
 // stage-1 output (k1, t) position
 __device__ __forceinline__ int ap1k(int k, int t) { return 72 * k + t; }
 __device__ __forceinline__ float2 cm(float2 a, float2 b) { return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
@@ -132,7 +134,7 @@ __device__ __forceinline__ float2 cmc(float2 a, float2 b) { return make_float2(f
 // Persistent: each 64-thread team (four per block) walks the rows j = team, team + teams, ... of all
 // fields (field j / rows), holding the next row's samples in registers while it transforms the
 // current one, so that every team keeps a row of loads in flight.
-__global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict__ out, int64_t rows, int nf,
+__global__ void __launch_bounds__(256, 3) k_rfft1024(RowPtrs in, float2* __restrict__ out, int64_t rows, int nf,
                                                   const float2* __restrict__ tw8, const float2* __restrict__ twN) {
     __shared__ float2 sbuf[kRows1k][2][kBuf1k];
     const int L = threadIdx.x >> 6, t = threadIdx.x & 63;
@@ -140,7 +142,12 @@ __global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict
     float2* A = sbuf[L][0];
     float2* B = sbuf[L][1];
     auto lsync = [&]() { asm volatile("bar.sync %0, %1;" :: "r"(1 + L), "r"(64) : "memory"); };
-    float2 nx[8];
+    float2 nx[8], w1[8], w2[8];
+#pragma unroll
+    for (int k = 1; k < 8; k++) {
+        w1[k] = tw8[(k - 1) * 64 + t];
+        w2[k] = tw8[448 + (k - 1) * 8 + (t & 7)];
+    }
     auto fetch = [&](int64_t j) {
         const int f = (int)(j / rows);
         const float2* z = reinterpret_cast<const float2*>(in.p[f]) + (j - (int64_t)f * rows) * 512;
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict
         if (j + teams < total) fetch(j + teams);
         dft8x<false>(v);
 #pragma unroll
-        for (int k = 1; k < 8; k++) v[k] = cm(v[k], tw8[(k - 1) * 64 + t]);
+        for (int k = 1; k < 8; k++) v[k] = cm(v[k], w1[k]);
         lsync();                     // the previous row's split has read A
 #pragma unroll
         for (int k = 0; k < 8; k++) A[ap1k(k, t)] = v[k];
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(256) k_rfft1024(RowPtrs in, float2* __restrict
             for (int n = 0; n < 8; n++) v[n] = A[ap1k(k1, t0 + 8 * n)];
             dft8x<false>(v);
 #pragma unroll
-            for (int k = 1; k < 8; k++) v[k] = cm(v[k], tw8[448 + (k - 1) * 8 + t0]);
+            for (int k = 1; k < 8; k++) v[k] = cm(v[k], w2[k]);
 #pragma unroll
             for (int k = 0; k < 8; k++) B[9 * (8 * k1 + k) + t0] = v[k];
         }
