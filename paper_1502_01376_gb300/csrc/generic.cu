@@ -28,7 +28,7 @@ struct RowPtrsW { void* p[9]; };
 // A block transforms RB = fft_rows_per_block(M) consecutive rows of one field.
 template <typename Tin, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* __restrict__ out, int n1, int64_t rows,
-                                                           const cplx<T>* __restrict__ twM, const cplx<T>* __restrict__ twN, int RB) {
+                                                           const cplx<T>* __restrict__ twS, const cplx<T>* __restrict__ twN, int RB) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = n1 >> 1;
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* 
         for (int q = threadIdx.x; q < nrow * M; q += blockDim.x) src[fpad(q)] = mkc<C>((T)x[2 * q], (T)x[2 * q + 1]);
     }
     __syncthreads();
-    stockham_rows<C, false>(src, dst, M, nrow, twM);
+    stockham_rows<C, false>(src, dst, M, nrow, twS);
     C* X = out + ((int64_t)f * rows + row0) * (M + 1);
     const int lgH = 31 - __clz(M) - 1, H = M >> 1;
     // pairs (k, M - k) for k < M/2 of all rows (k = 0 gives X[0] and X[M]), then k = M/2 of each row:
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rfft_rows(RowPtrs in, cplx<T>* 
 // z = IDFT_M(Z) / M, x[2j] = Re z[j], x[2j+1] = Im z[j].  DC/Nyquist imaginary parts are dropped.
 template <typename T, typename Tout>
 __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __restrict__ in, RowPtrsW out, int n1, int64_t rows,
-                                                            const cplx<T>* __restrict__ twM, const cplx<T>* __restrict__ twN,
+                                                            const cplx<T>* __restrict__ twS, const cplx<T>* __restrict__ twN,
                                                             int in_field0, int RB) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
         if (k != 0 && k != H) src[fpad(r * M + M - k)] = mkc<C>(e.x + o.y, o.x - e.y);
     }
     __syncthreads();
-    stockham_rows<C, true>(src, dst, M, nrow, twM);
+    stockham_rows<C, true>(src, dst, M, nrow, twS);
     Tout* x = reinterpret_cast<Tout*>(out.p[f]) + row0 * n1;
     const T inv = (T)1 / (T)M;
     if constexpr (std::is_same<Tout, T>::value) {
@@ -353,7 +353,7 @@ static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, i
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fft_smem<T>(n1, fft_rows_per_block(n1 / 2)));
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
-    kern<<<grid, kRowThreads, smem, s>>>(p, out, n1, rows, t.twM, t.twN, RB);
+    kern<<<grid, kRowThreads, smem, s>>>(p, out, n1, rows, t.twS, t.twN, RB);
     return cudaGetLastError();
 }
 
@@ -373,7 +373,7 @@ static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, in
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fft_smem<T>(n1, fft_rows_per_block(n1 / 2)));
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
-    kern<<<grid, kRowThreads, smem, s>>>(in, p, n1, rows, t.twM, t.twN, f0, RB);
+    kern<<<grid, kRowThreads, smem, s>>>(in, p, n1, rows, t.twS, t.twN, f0, RB);
     return cudaGetLastError();
 }
 

@@ -109,21 +109,9 @@ static hyb_status upload_tables(hyb_grid* g, const HostModes& h, ModeTables<T>& 
         const double b = -2.0 * kPi * (double)j / (double)d.n1;
         twN[j] = mkc<C>((T)cos(b), (T)sin(b));
     }
-    std::vector<C> tw8;
-    if (M == 512) {
-        tw8.resize(kTw8);
-        for (int k = 1; k < 8; k++) {
-            for (int t = 0; t < 64; t++) {
-                const double a = -2.0 * kPi * (double)(t * k) / 512.0;
-                tw8[(k - 1) * 64 + t] = mkc<C>((T)cos(a), (T)sin(a));
-            }
-            for (int t0 = 0; t0 < 8; t0++) {
-                const double a = -2.0 * kPi * (double)(t0 * k) / 64.0;
-                tw8[448 + (k - 1) * 8 + t0] = mkc<C>((T)cos(a), (T)sin(a));
-            }
-        }
-    }
-    const size_t bytes = sizeof(C) * (4 * (size_t)nk + 2 * (size_t)M + tw8.size()) + sizeof(T) * 4 * (size_t)nk + 256;
+    const std::vector<C> tw8 = M == 512 ? tw8_table<C>() : std::vector<C>();
+    const std::vector<C> twS = stockham_twiddles<C>(M);
+    const size_t bytes = sizeof(C) * (4 * (size_t)nk + 3 * (size_t)M + tw8.size()) + sizeof(T) * 4 * (size_t)nk + 256;
     char* base = nullptr;
     HYB_CUDA_TRY(cudaMalloc(&base, bytes));
     char* p = base;
@@ -137,6 +125,7 @@ static hyb_status upload_tables(hyb_grid* g, const HostModes& h, ModeTables<T>& 
     t.corr = (T*)take(sizeof(T) * nk);
     t.filt = (T*)take(sizeof(T) * nk);
     if (!tw8.empty()) t.tw8 = (C*)take(sizeof(C) * tw8.size());
+    t.twS = (C*)take(sizeof(C) * M);
     HYB_CUDA_TRY(cudaMemcpy(t.S, S.data(), sizeof(C) * nk, cudaMemcpyHostToDevice));
     HYB_CUDA_TRY(cudaMemcpy(t.sgp, sgp.data(), sizeof(C) * nk, cudaMemcpyHostToDevice));
     HYB_CUDA_TRY(cudaMemcpy(t.twM, twM.data(), sizeof(C) * M, cudaMemcpyHostToDevice));
@@ -146,6 +135,7 @@ static hyb_status upload_tables(hyb_grid* g, const HostModes& h, ModeTables<T>& 
     HYB_CUDA_TRY(cudaMemcpy(t.corr, corr.data(), sizeof(T) * nk, cudaMemcpyHostToDevice));
     HYB_CUDA_TRY(cudaMemcpy(t.filt, filt.data(), sizeof(T) * nk, cudaMemcpyHostToDevice));
     if (!tw8.empty()) HYB_CUDA_TRY(cudaMemcpy(t.tw8, tw8.data(), sizeof(C) * tw8.size(), cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMemcpy(t.twS, twS.data(), sizeof(C) * M, cudaMemcpyHostToDevice));
     return HYB_OK;
 }
 

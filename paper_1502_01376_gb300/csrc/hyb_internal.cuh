@@ -4,7 +4,10 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cmath>
 #include <string>
+#include <vector>
 
 #include "../../include/hyb.h"
 
@@ -64,13 +67,15 @@ __host__ __device__ __forceinline__ size_t fpad_size(size_t n) { return n + n / 
 
 // One radix-R Stockham pass over nrow rows of M points (rows contiguous): butterfly j of a
 // row (0 <= j < M/R, k = j mod Ns) takes src[j + r M/R] W_{R Ns}^{r k}, r = 0..R-1, does an
-// R-point DFT over r and writes output r to dst[(j - k) R + k + r Ns].
+// R-point DFT over r and writes output r to dst[(j - k) R + k + r Ns].  The twiddles come from
+// the pass-ordered table of stockham_twiddles, W_{R Ns}^{r k} at Ns - 1 + (r - 1) Ns + k, so that
+// the lanes of a warp (consecutive k) read consecutive entries.
 template <typename C, int R, bool INV>
 __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __restrict__ dst, int lgM, int lgNs, int nrow,
                                               const C* __restrict__ tw) {
     constexpr int lgR = (R == 8) ? 3 : (R == 4) ? 2 : 1;
     const int M = 1 << lgM, Ns = 1 << lgNs;
-    const int lgnb = lgM - lgR, nb = 1 << lgnb, lgts = lgM - lgR - lgNs;
+    const int lgnb = lgM - lgR, nb = 1 << lgnb;
     // padded positions: when the element stride is a multiple of 16, fpad(a + r s) = fpad(a) + r (s + s / 16)
     const bool rstride = (nb & 15) == 0, wstride = (Ns & 15) == 0;
     const int nbp = nb + (nb >> 4), nsp = Ns + (Ns >> 4);
@@ -83,7 +88,7 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __re
         for (int r = 0; r < R; r++) {
             x[r] = src[rstride ? ra + r * nbp : fpad(base + j + r * nb)];
             if (r > 0 && Ns > 1) {
-                const C w = tw[(r * k) << lgts];
+                const C w = tw[Ns - 1 + (r - 1) * Ns + k];
                 x[r] = INV ? cmulc(x[r], w) : cmul(x[r], w);
             }
         }
@@ -100,7 +105,7 @@ __device__ __forceinline__ void stockham_pass(const C* __restrict__ src, C* __re
 // natural-order in, natural-order out FFT of nrow rows of M = 2^m points held in shared
 // memory (src, padded positions fpad(row * M + j)); radix-8 passes then one radix-4 or
 // radix-2 pass; one __syncthreads per pass.  On return src points at the result.
-// tw[j] = W_M^j, j < M.
+// tw: stockham_twiddles(M).
 template <typename C, bool INV>
 __device__ __forceinline__ void stockham_rows(C*& src, C*& dst, int M, int nrow, const C* __restrict__ tw) {
     const int lgM = 31 - __clz(M);
@@ -120,6 +125,47 @@ __device__ __forceinline__ void stockham_rows(C*& src, C*& dst, int M, int nrow,
         __syncthreads();
         C* t = src; src = dst; dst = t;
     }
+}
+
+// The twiddles of the passes stockham_rows makes for M points, in pass order: the pass with span
+// Ns and radix R holds W_{R Ns}^{r k} (r = 1..R-1, k < Ns) at Ns - 1 + (r - 1) Ns + k, so the
+// passes fill entries 0..M-2 (computed in FP64, rounded once).
+template <typename C>
+inline std::vector<C> stockham_twiddles(int M) {
+    std::vector<C> tw((size_t)M, mkc<C>(1, 0));
+    int lgM = 0;
+    while ((1 << lgM) < M) lgM++;
+    int lgNs = 0;
+    auto pass = [&](int lgR) {
+        const int Ns = 1 << lgNs, R = 1 << lgR;
+        for (int r = 1; r < R; r++)
+            for (int k = 0; k < Ns; k++) {
+                const double a = -2.0 * 3.14159265358979323846 * (double)(r * k) / (double)(R * Ns);
+                tw[(size_t)(Ns - 1 + (r - 1) * Ns + k)] = mkc<C>((decltype(C::x))std::cos(a), (decltype(C::x))std::sin(a));
+            }
+        lgNs += lgR;
+    };
+    while (lgNs + 3 <= lgM) pass(3);
+    if (lgNs + 2 <= lgM) pass(2);
+    else if (lgNs + 1 <= lgM) pass(1);
+    return tw;
+}
+
+// ModeTables::tw8 for M = 512 (computed in FP64, rounded once)
+template <typename C>
+inline std::vector<C> tw8_table() {
+    std::vector<C> tw(504);
+    for (int k = 1; k < 8; k++) {
+        for (int t = 0; t < 64; t++) {
+            const double a = -2.0 * 3.14159265358979323846 * (double)(t * k) / 512.0;
+            tw[(size_t)((k - 1) * 64 + t)] = mkc<C>((decltype(C::x))std::cos(a), (decltype(C::x))std::sin(a));
+        }
+        for (int t0 = 0; t0 < 8; t0++) {
+            const double a = -2.0 * 3.14159265358979323846 * (double)(t0 * k) / 64.0;
+            tw[(size_t)(448 + (k - 1) * 8 + t0)] = mkc<C>((decltype(C::x))std::cos(a), (decltype(C::x))std::sin(a));
+        }
+    }
+    return tw;
 }
 
 // rows of M points one block of 256 threads transforms together (one radix-8 pass then
@@ -146,6 +192,7 @@ struct ModeTables {
     cplx<T>* twM = nullptr;   // W_M^j = exp(-2 pi i j / M), j < M, M = n1/2
     cplx<T>* twN = nullptr;   // W_N^k = exp(-2 pi i k / n1), k < M
     cplx<T>* sgp = nullptr;   // sigma+ (without c dt), for diagnostics
+    cplx<T>* twS = nullptr;   // stockham_twiddles(M): the shared-memory row FFTs
     // M = 512 only (n1 = 1024, factored 8 x 8 x 8): the twiddles of the first two stages in the
     // order the threads read them, [(k - 1) 64 + t] = W_512^{t k} (k = 1..7, t < 64), then
     // [448 + (k - 1) 8 + t0] = W_64^{t0 k} (t0 < 8)

@@ -54,9 +54,10 @@ static hyb_status run(const hyb_grid_desc& d, T* j1, cudaStream_t s) {
     using C = cplx<T>;
     const int n1 = d.n1, M = n1 / 2, nk = M + 1;
     const int64_t rows = (int64_t)d.n2 * (d.dims == 3 ? d.n3 : 1);
-    // tables in the head of the array: corr[nk], twM[M], twN[M]; then row blocks
+    // tables in the head of the array: corr[nk], twS[M], twN[M] and, for n1 = 1024, tw8; then row blocks
     auto up16 = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t tab_bytes = up16(sizeof(T) * nk) + up16(sizeof(C) * M) * 2;
+    const size_t n8 = M == 512 ? (size_t)kTw8 : 0;
+    const size_t tab_bytes = up16(sizeof(T) * nk) + up16(sizeof(C) * M) * 2 + up16(sizeof(C) * n8);
     const size_t row_bytes = sizeof(C) * (size_t)nk;
     if (tab_bytes + row_bytes > kNoallocBytes) {
         set_error("hyb_correct_current_noalloc: n1 = %d needs %zu bytes of working memory, more than the %zu available",
@@ -68,15 +69,18 @@ static hyb_status run(const hyb_grid_desc& d, T* j1, cudaStream_t s) {
     if (st != HYB_OK) return st;
     char* p = (char*)base;
     T* corr = (T*)p;
-    C* twM = (C*)(p + up16(sizeof(T) * nk));
+    C* twS = (C*)(p + up16(sizeof(T) * nk));
     C* twN = (C*)(p + up16(sizeof(T) * nk) + up16(sizeof(C) * M));
+    C* tw8 = (C*)(p + up16(sizeof(T) * nk) + 2 * up16(sizeof(C) * M));
     C* spec = (C*)(p + tab_bytes);
     const int64_t rows_per_block = (int64_t)((kNoallocBytes - tab_bytes) / row_bytes);
 
     // FP64 tables on the host, rounded once (the same quantities hyb_create_grid computes)
     const double pi = 3.14159265358979323846;
     std::vector<T> hc(nk);
-    std::vector<C> hm(M), hn(M);
+    const std::vector<C> hm = stockham_twiddles<C>(M);
+    std::vector<C> hn(M);
+    const std::vector<C> h8 = n8 ? tw8_table<C>() : std::vector<C>();
     for (int k = 0; k < nk; k++) {
         const double k1 = 2.0 * pi * k / (n1 * d.dx1);
         const double kfd = sin(0.5 * k1 * d.dx1) / (0.5 * d.dx1);
@@ -89,17 +93,18 @@ static hyb_status run(const hyb_grid_desc& d, T* j1, cudaStream_t s) {
         hc[k] = (T)(k == 0 ? 1.0 : kfd / ke);
     }
     for (int j = 0; j < M; j++) {
-        const double a = -2.0 * pi * j / M, b = -2.0 * pi * j / n1;
-        hm[j] = mkc<C>((T)cos(a), (T)sin(a));
+        const double b = -2.0 * pi * j / n1;
         hn[j] = mkc<C>((T)cos(b), (T)sin(b));
     }
     // pageable source: the copies are staged before cudaMemcpyAsync returns
     HYB_CUDA_TRY(cudaMemcpyAsync(corr, hc.data(), sizeof(T) * nk, cudaMemcpyHostToDevice, s));
-    HYB_CUDA_TRY(cudaMemcpyAsync(twM, hm.data(), sizeof(C) * M, cudaMemcpyHostToDevice, s));
+    HYB_CUDA_TRY(cudaMemcpyAsync(twS, hm.data(), sizeof(C) * M, cudaMemcpyHostToDevice, s));
     HYB_CUDA_TRY(cudaMemcpyAsync(twN, hn.data(), sizeof(C) * M, cudaMemcpyHostToDevice, s));
+    if (n8) HYB_CUDA_TRY(cudaMemcpyAsync(tw8, h8.data(), sizeof(C) * n8, cudaMemcpyHostToDevice, s));
     ModeTables<T> t;
-    t.twM = twM;
+    t.twS = twS;
     t.twN = twN;
+    t.tw8 = n8 ? tw8 : nullptr;
     // the row blocks are overwritten completely by the forward transform, so
     // nothing left by an earlier call needs clearing
     for (int64_t r0 = 0; r0 < rows; r0 += rows_per_block) {

@@ -29,7 +29,7 @@ struct QTab {
 template <typename T>
 struct QPlan {
     QTab<T>* tab = nullptr;
-    cplx<T>* tw = nullptr;    // W_nz^j, j < nz
+    cplx<T>* tw = nullptr;    // stockham_twiddles(nz)
     cplx<T>* spec = nullptr;  // [9][nr][nz]
 };
 
@@ -168,8 +168,7 @@ static hyb_status create_t(hyb_grid* g) {
         tab[k].cjz = (T)(d.ampere * d.dt * F * corr);
         tab[k].cj = (T)(d.ampere * d.dt * F);
     }
-    std::vector<C> tw(nz);
-    for (int j = 0; j < nz; j++) { const double a = -2.0 * pi * j / nz; tw[j] = mkc<C>((T)cos(a), (T)sin(a)); }
+    const std::vector<C> tw = stockham_twiddles<C>(nz);
     HYB_CUDA_TRY(cudaMalloc(&P->tab, sizeof(QTab<T>) * nz));
     HYB_CUDA_TRY(cudaMemcpy(P->tab, tab.data(), sizeof(QTab<T>) * nz, cudaMemcpyHostToDevice));
     HYB_CUDA_TRY(cudaMalloc(&P->tw, sizeof(C) * nz));

@@ -13,11 +13,11 @@ pytestmark = pytest.mark.gpu
 TOL = {64: 1e-12, 32: 1e-5}
 
 
-@pytest.mark.parametrize("prec", [64, 32])
-def test_noalloc_correction_matches_regular_entry_point(prec):
+@pytest.mark.parametrize("n1,n2", [(4096, 600), (1024, 2100)])   # several row blocks of the static array,
+@pytest.mark.parametrize("prec", [64, 32])                           # the last one ragged
+def test_noalloc_correction_matches_regular_entry_point(prec, n1, n2):
     need_gpu()
     hyb = hyb_module()
-    n1, n2 = 4096, 600                     # several row blocks of the static array, the last one ragged
     dt = torch.float64 if prec == 64 else torch.float32
     desc = hyb.make_desc(n1=n1, n2=n2, dx1=0.2, dx2=0.2, dt=0.1, precision=prec, path=1)
     g = hyb.Grid(desc)
