@@ -123,9 +123,10 @@ __global__ void __launch_bounds__(kRowThreads) k_irfft_rows(const cplx<T>* __res
 // transposed with conjugate twiddles.  Four rows per block, one named barrier per row.
 constexpr int kRows1k = 4;
 constexpr int kBuf1k = 576;
-// Z[k] at k with bit 2 flipped by bit 4: the S3 accesses (lanes over bits 0, 1, 3, 4, 5 of k) and the
-// split's runs of 32 consecutive k both touch every bank pair exactly twice per warp
-__device__ __forceinline__ int zp1k(int k) { return k ^ (((k >> 4) & 1) << 2); }
+// Z[k] at k with bits 2 and 1 flipped by bits 4 and 5: a half-warp's 8-byte accesses of the S3
+// scatter (lanes over bits 0, 3, 4, 5 of k) and of the split (16 consecutive k) both reach 16
+// different bank pairs
+__device__ __forceinline__ int zp1k(int k) { return k ^ (((k >> 4) & 1) << 2) ^ (((k >> 5) & 1) << 1); }
 // stage-1 output (k1, t) position
 __device__ __forceinline__ int ap1k(int k, int t) { return 72 * k + t; }
 __device__ __forceinline__ float2 cm(float2 a, float2 b) { return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
