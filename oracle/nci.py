@@ -39,10 +39,13 @@ extra root, at the resonance itself, is rejected.
 Pins (tests/test_oracle_nci_mlp.py, tests/test_golden_paper_values.py): the
 vacuum limit factorises into the hybrid EM modes and the beam resonance; the
 resonance roots scale with sqrt(wp2); the (0,0) modes grow far more slowly
-than the (0,+-1) modes; and the value Sec. 4 prints: zero (0,0) growth at the
+than the (0,+-1) modes; the value Sec. 4 prints: zero (0,0) growth at the
 Table 1 parameters with the printed k1 modification, positive growth without
-it.  The growth rates of other individual modes live in the paper's absent
-figures: beyond those properties their values are parity unpinned.
+it; and the root finding: the growth from the cubic seeds and Newton steps
+equals the one from a brute-force scan of |F| around the resonance.  The
+growth rates of other individual modes live in the paper's absent figures:
+the coupled relation's values there rest on these properties only, so they
+are parity unpinned.
 """
 from __future__ import annotations
 

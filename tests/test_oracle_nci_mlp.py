@@ -6,8 +6,10 @@ resonance roots move away as sqrt(wp2); the (0,0) modes grow far more slowly
 than the fastest (0,+-1) modes (Sec. 3, Sec. 6).  Quantitative growth rates of
 the paper live in absent figures, and the printed cubic (Eq. asym1) disagrees
 with the full relation in character for some modes (garbled coefficients), so
-parity of the growth values themselves is unpinned by the paper; the cubic is
-used only to seed Newton's method on the full relation.
+the growth values of the coupled relation are pinned by the paper only through
+the Sec. 4 statement; the cubic is used only to seed Newton's method on the
+full relation, and the root finding itself is pinned by a brute-force scan of
+|F| over the complex plane around the resonance.
 
 MLP: the FP64 backward pass equals central finite differences of the loss.
 """
@@ -53,6 +55,63 @@ def test_zero_zero_modes_slower_than_pm1():
     gpm = max(nci.growth_scan(P, 0, -1, 16, 16)[2].max(), nci.growth_scan(P, 0, 1, 16, 16)[2].max())
     assert gpm > 0.0
     assert g00 < 0.5 * gpm
+
+
+def _brute_roots(P, m, center, boxes=((2.0, 401), (0.06, 241))):
+    """Roots of F in square boxes around `center` found without the oracle's seeds or Newton
+    iteration: every local minimum of |F| on a grid of the box, refined by the secant method,
+    kept if F vanishes there (relative to a point 1e-3 away) and it is not the resonance point."""
+    from numpy.lib.stride_tricks import sliding_window_view
+    out = []
+    for R, n in boxes:
+        x = np.linspace(-R, R, n)
+        X, Y = np.meshgrid(x, x, indexing="ij")
+        W = center + X + 1j * Y
+        L = np.log(np.abs(nci.F_of(P, m, W)) + 1e-300)
+        ismin = L[1:-1, 1:-1] <= sliding_window_view(L, (3, 3)).min(axis=(2, 3))
+        h = x[1] - x[0]
+        for i, j in np.argwhere(ismin):
+            a = complex(W[i + 1, j + 1])
+            b = a + h * (0.3 + 0.2j)
+            fa, fb = nci.F_of(P, m, a), nci.F_of(P, m, b)
+            r = None
+            for _ in range(200):
+                if fb == fa:
+                    break
+                c = b - fb * (b - a) / (fb - fa)
+                a, fa, b, fb = b, fb, c, nci.F_of(P, m, c)
+                if abs(b - a) < 1e-14 * max(1.0, abs(b)):
+                    r = b
+                    break
+            if r is None or abs(r - center) > R or abs(r - center) < 1e-9:
+                continue
+            if abs(nci.F_of(P, m, r)) > 1e-9 * abs(nci.F_of(P, m, r + 1e-3)):
+                continue
+            if all(abs(r - u) > 1e-8 for u in out):
+                out.append(r)
+    return out
+
+
+# the fastest-growing (k1, k2) of a 16 x 16 scan of each alias at the Table 1 parameters, and
+# modes of other aliases, stable and unstable
+@pytest.mark.parametrize("mu,nu,k1,k2", [(0, 0, 6.381360077604267, 0.4908738521234052),
+                                         (0, -1, 14.23534171157875, 10.30835089459151),
+                                         (0, 1, 15.21708941582556, 9.326603190344699),
+                                         (1, -1, 10.0, 8.0), (1, 0, 3.0, 5.0), (0, 0, 2.0, 12.0), (0, -1, 5.0, 3.0)])
+def test_growth_equals_brute_force_root_scan(mu, nu, k1, k2):
+    """The growth rate (max Im w over the roots near the beam resonance) from the oracle's cubic
+    seeds and Newton steps equals the one from a brute-force scan of |F| over the complex plane
+    around the resonance, and every growing root the scan finds is among the oracle's roots."""
+    P = nci.NciParams()
+    m = nci.symbols(P, k1, k2, mu, nu)
+    w_res = m.k1a * P.v0 - mu * 2.0 * math.pi / P.dt
+    brute = _brute_roots(P, m, w_res)
+    oracle_roots = nci.roots(P, k1, k2, mu, nu)
+    g_brute = max([r.imag for r in brute] + [0.0])
+    assert abs(nci.growth(P, k1, k2, mu, nu) - g_brute) < 1e-9
+    for r in brute:
+        if r.imag > 1e-9:
+            assert min(abs(r - u) for u in oracle_roots) < 1e-7, r
 
 
 @pytest.mark.parametrize("width,depth", [(8, 2), (16, 3)])
