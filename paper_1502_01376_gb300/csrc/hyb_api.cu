@@ -7,12 +7,31 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "hyb_internal.cuh"
 #include "fused_api.cuh"
 
 namespace hyb {
+
+int resident_grid(const void* kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, size_t>, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(kernel, smem * 4096 + (size_t)threads);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+    const int r = sms * occ > 0 ? sms * occ : 1;
+    cache[key] = r;
+    return r;
+}
 
 static thread_local char g_err[512] = "";
 

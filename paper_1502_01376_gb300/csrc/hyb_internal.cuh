@@ -178,6 +178,15 @@ __host__ __forceinline__ int fft_rows_per_launch(int M, int64_t total_rows) {
     return rb;
 }
 
+// Persistent launches of the shared-memory complex row FFTs (quasi-3D): a block takes the
+// row blocks i = blockIdx.x, blockIdx.x + gridDim.x, ... and, when a row block is at most
+// kPrefetchPts points per thread, holds the next block's points in registers while it
+// transforms the current one.
+constexpr int kPrefetchPts = 8;
+// blocks of `threads` threads with `smem` bytes of dynamic shared memory that fit on the
+// current device at once (cached per kernel and size)
+int resident_grid(const void* kernel, int threads, size_t smem);
+
 // ---------------------------------------------------------------- tables
 // Per-mode tables for kappa = 0..n1/2, computed in FP64 on the host and rounded once.
 constexpr int kTw8 = 504;   // entries of ModeTables::tw8

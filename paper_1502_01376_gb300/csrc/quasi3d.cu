@@ -14,6 +14,8 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "hyb_internal.cuh"
 
 namespace hyb {
@@ -37,45 +39,67 @@ struct QPtrs { void* p[9]; };
 
 constexpr int kQThreads = 256;
 
-// complex transforms along z of RB = fft_rows_per_block(nz) rows per block
-template <typename T>
-__global__ void __launch_bounds__(kQThreads) k_qfft_fwd(QPtrs in, cplx<T>* __restrict__ spec, int nz, int nr,
-                                                       const cplx<T>* __restrict__ tw, int RB) {
-    using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + fpad_size((size_t)RB * nz);
-    const int row0 = blockIdx.x * RB, f = blockIdx.y;
-    const int nrow = (nr - row0) < RB ? (nr - row0) : RB;
-    const C* x = reinterpret_cast<const C*>(in.p[f]) + (int64_t)row0 * nz;
-    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) src[fpad(q)] = x[q];
-    __syncthreads();
-    stockham_rows<C, false>(src, dst, nz, nrow, tw);
-    C* X = spec + ((int64_t)f * nr + row0) * nz;
-    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) X[q] = src[fpad(q)];
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kQThreads) k_qfft_inv(const cplx<T>* __restrict__ spec, QPtrs out, int nz, int nr,
-                                                       const cplx<T>* __restrict__ tw, int RB) {
-    using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* src = reinterpret_cast<C*>(smem_raw);
-    C* dst = src + fpad_size((size_t)RB * nz);
-    const int row0 = blockIdx.x * RB, f = blockIdx.y;
-    const int nrow = (nr - row0) < RB ? (nr - row0) : RB;
-    const C* X = spec + ((int64_t)f * nr + row0) * nz;
-    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) src[fpad(q)] = X[q];
-    __syncthreads();
-    stockham_rows<C, true>(src, dst, nz, nrow, tw);
-    C* x = reinterpret_cast<C*>(out.p[f]) + (int64_t)row0 * nz;
-    const T inv = (T)1 / (T)nz;
-    for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) x[q] = cscale(src[fpad(q)], inv);
-}
-
 // i m / r times a
 template <typename C>
 __device__ __forceinline__ C imr(C a, decltype(C::x) m_over_r) { return mkc<C>(-m_over_r * a.y, m_over_r * a.x); }
+
+// complex transforms along z of row blocks of RB rows (block i: field i / nblk); persistent, the
+// next block's points held in registers while the current one is transformed (RB nz <= 2048)
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kQThreads) k_qfft(QPtrs io, cplx<T>* __restrict__ spec, int nz, int nr, int nf,
+                                                   const cplx<T>* __restrict__ tw, int RB) {
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* const src0 = reinterpret_cast<C*>(smem_raw);
+    C* const dst0 = src0 + fpad_size((size_t)RB * nz);
+    const int nblk = (nr + RB - 1) / RB, total = nblk * nf;
+    const bool pf = RB * nz <= kPrefetchPts * kQThreads;
+    // forward: fields -> spectral scratch; inverse: scratch -> fields (scaled by 1/nz)
+    auto in_of = [&](int f, int row0) -> const C* {
+        return INV ? spec + ((int64_t)f * nr + row0) * nz : reinterpret_cast<const C*>(io.p[f]) + (int64_t)row0 * nz;
+    };
+    C nx[kPrefetchPts];
+    auto fetch = [&](int i) {
+        const int f = i / nblk, row0 = (i - f * nblk) * RB;
+        const int cnt = ((nr - row0) < RB ? (nr - row0) : RB) * nz;
+        const C* x = in_of(f, row0);
+#pragma unroll
+        for (int u = 0; u < kPrefetchPts; u++) {
+            const int q = threadIdx.x + u * kQThreads;
+            if (q < cnt) nx[u] = x[q];
+        }
+    };
+    int i = blockIdx.x;
+    if (pf && i < total) fetch(i);
+    for (; i < total; i += gridDim.x) {
+        const int f = i / nblk, row0 = (i - f * nblk) * RB;
+        const int nrow = (nr - row0) < RB ? (nr - row0) : RB;
+        __syncthreads();                                   // the previous block has read its result
+        if (pf) {
+#pragma unroll
+            for (int u = 0; u < kPrefetchPts; u++) {
+                const int q = threadIdx.x + u * kQThreads;
+                if (q < nrow * nz) src0[fpad(q)] = nx[u];
+            }
+            if (i + gridDim.x < total) fetch(i + gridDim.x);
+        } else {
+            const C* x = in_of(f, row0);
+            for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) src0[fpad(q)] = x[q];
+        }
+        __syncthreads();
+        C* src = src0;
+        C* dst = dst0;
+        stockham_rows<C, INV>(src, dst, nz, nrow, tw);
+        if (INV) {
+            C* x = reinterpret_cast<C*>(io.p[f]) + (int64_t)row0 * nz;
+            const T inv = (T)1 / (T)nz;
+            for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) x[q] = cscale(src[fpad(q)], inv);
+        } else {
+            C* X = spec + ((int64_t)f * nr + row0) * nz;
+            for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) X[q] = src[fpad(q)];
+        }
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kQThreads) k_qfaraday(cplx<T>* __restrict__ spec, int nz, int nr, const QTab<T>* __restrict__ tab,
@@ -175,8 +199,8 @@ static hyb_status create_t(hyb_grid* g) {
     HYB_CUDA_TRY(cudaMemcpy(P->tw, tw.data(), sizeof(C) * nz, cudaMemcpyHostToDevice));
     HYB_CUDA_TRY(cudaMalloc(&P->spec, sizeof(C) * 9 * (size_t)nr * nz));
     const size_t smem = sizeof(C) * 2 * fpad_size((size_t)fft_rows_per_block(nz) * nz);
-    HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return HYB_OK;
 }
 
@@ -191,12 +215,14 @@ static hyb_status advance_t(hyb_grid* g, int nsteps) {
     QPtrs fin{}, fout{};
     for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; fin.p[6 + c] = g->J[c]; }
     for (int c = 0; c < 3; c++) { fout.p[c] = g->E[c]; fout.p[3 + c] = g->B[c]; }
+    const int gf = std::min(9 * nblk, resident_grid((const void*)k_qfft<T, false>, kQThreads, smem));
+    const int gi = std::min(6 * nblk, resident_grid((const void*)k_qfft<T, true>, kQThreads, smem));
     for (int s = 0; s < nsteps; s++) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
-        k_qfft_fwd<T><<<dim3(nblk, 9), kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, P->tw, RB);
+        k_qfft<T, false><<<gf, kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, 9, P->tw, RB);
         k_qfaraday<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
         k_qampere<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
-        k_qfft_inv<T><<<dim3(nblk, 6), kQThreads, smem, g->stream>>>(P->spec, fout, nz, nr, P->tw, RB);
+        k_qfft<T, true><<<gi, kQThreads, smem, g->stream>>>(fout, P->spec, nz, nr, 6, P->tw, RB);
         HYB_CUDA_TRY(cudaGetLastError());
         if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
     }
