@@ -47,16 +47,15 @@ constexpr int N = 4096, M = 2048, T = 256, NT = 768;
 constexpr int XS = 64 * 34;                              // exchange buffer (float2): the S2 -> S3 layout is 64 x 34
 constexpr int OFF_STAGE = 0;                             // [3][M] float2
 constexpr int OFF_XB = OFF_STAGE + 3 * M * 8;            // [3][2][XS] float2
-// twiddle tables as pairs: entry [m][i] = (W^{i (2m+1)}, W^{i (2m+2)}), m = 0..3 (k = 1..8, k = 8 unused)
-constexpr int OFF_TW1 = OFF_XB + 3 * 2 * XS * 8;         // [4][256] float4  W_2048^{t k1}
-constexpr int OFF_TW2 = OFF_TW1 + 4 * 256 * 16;          // [4][32] float4   W_256^{t0 k2}
-constexpr int OFF_TW3 = OFF_TW2 + 4 * 32 * 16;           // [4][4] float4    W_32^{u0 k3}
-constexpr int OFF_SYMN = OFF_TW3 + 4 * 4 * 16;           // float4: the Nyquist mode's symbols
+constexpr int OFF_SYMN = OFF_XB + 3 * 2 * XS * 8;        // float4: the Nyquist mode's symbols
 constexpr int OFF_BAR = OFF_SYMN + 16;                   // [3] mbarrier
 constexpr int OFF_MISC = OFF_BAR + 3 * 8;                // TMEM base address, abort flag
 constexpr int SMEM = OFF_MISC + 16;
-constexpr uint32_t TMEM_COLS = 512;                      // slots 2 x 160, symbols 2 x 32
+constexpr uint32_t TMEM_COLS = 512;                      // slots 2 x 160, symbols 2 x 32, twiddles 2 x 64
 constexpr int SYM_COL = 320;                             // per-mode symbols: S (16 words), cj1 (8), cj (8)
+// per-thread twiddles (the same for the three groups' thread t): W_2048^{t k} at +0, W_256^{t0 k}
+// at +16, W_32^{u0 k} at +32 (k = 1..7, two words each), the split's W_4096^{cA} W_8^{k4} at +48
+constexpr int TW_COL = 384;
 constexpr long long WAIT_CYCLES = kWaitCycles;            // about 2 s at 2 GHz
 }  // namespace tmk
 
@@ -80,6 +79,15 @@ __device__ __forceinline__ void tm_ld8(uint32_t ta, float (&r)[8]) {
                  : "r"(ta));
 #pragma unroll
     for (int i = 0; i < 8; i++) r[i] = __uint_as_float(u[i]);
+}
+__device__ __forceinline__ void tm_ld16(uint32_t ta, float (&r)[16]) {
+    uint32_t u[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                   "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+                 : "r"(ta));
+#pragma unroll
+    for (int i = 0; i < 16; i++) r[i] = __uint_as_float(u[i]);
 }
 __device__ __forceinline__ void tm_st8(uint32_t ta, const float (&r)[8]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
@@ -214,22 +222,13 @@ __device__ __forceinline__ const float* tm_src(const FusedInst& a, int N, int st
 __device__ __forceinline__ int x3base(int k1, int k2, int k3, int u0odd) {
     return k1 * 256 + 8 * (k3 ^ ((k2 ^ u0odd) & 1)) + (k2 ^ k1);
 }
-// the twiddles (W^{i k}, k = 1..7) of row i of a pair table: W^i .. W^{4i} are
-// read, W^{5i}, W^{6i}, W^{7i} are products with W^{4i} (a few ulp, far below
-// the path's error budget)
-__device__ __forceinline__ void tw_row(const float4* tab, int stride, int i, float2 (&w)[8]) {
-    const float4 q0 = tab[i], q1 = tab[stride + i];
-    w[1] = f2(q0.x, q0.y); w[2] = f2(q0.z, q0.w); w[3] = f2(q1.x, q1.y); w[4] = f2(q1.z, q1.w);
-    w[5] = mul(w[4], w[1]); w[6] = mul(w[4], w[2]); w[7] = mul(w[4], w[3]);
-}
-// all four pairs read from the table (for the small, broadcast-read tables)
-__device__ __forceinline__ void tw_row_full(const float4* tab, int stride, int i, float2 (&w)[8]) {
+// the seven twiddles W^{k}, k = 1..7, of a stage from this thread's TMEM words
+__device__ __forceinline__ void tw_tmem(uint32_t ta, float2 (&w)[8]) {
+    float r[16];
+    tm_ld16(ta, r);
+    tm_wait_ld();
 #pragma unroll
-    for (int m = 0; m < 4; m++) {
-        const float4 q = tab[m * stride + i];
-        w[2 * m + 1] = f2(q.x, q.y);
-        if (m < 3) w[2 * m + 2] = f2(q.z, q.w);
-    }
+    for (int k = 1; k < 8; k++) w[k] = f2(r[2 * k - 2], r[2 * k - 1]);
 }
 
 // forward split of one pair: X[k] = e - u, X[M-k] = conj(e + u), e = (a + conj b)/2,
@@ -259,9 +258,6 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
     extern __shared__ __align__(128) unsigned char sm[];
     float2* stage = reinterpret_cast<float2*>(sm + OFF_STAGE);
     float2* xbuf = reinterpret_cast<float2*>(sm + OFF_XB);
-    float4* tw1 = reinterpret_cast<float4*>(sm + OFF_TW1);
-    float4* tw2 = reinterpret_cast<float4*>(sm + OFF_TW2);
-    float4* tw3 = reinterpret_cast<float4*>(sm + OFF_TW3);
     float4* symN = reinterpret_cast<float4*>(sm + OFF_SYMN);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
     uint32_t* s_taddr = reinterpret_cast<uint32_t*>(sm + OFF_MISC);
@@ -272,7 +268,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
     const bool fm = fb.flags != nullptr;
     if ((int)blockIdx.x >= fb.n_items) return;
 
-    // ---- one-time set-up: TMEM, barriers, twiddle tables
+    // ---- one-time set-up: TMEM, barriers, twiddles
     if (warp == 0) {
         tm_alloc(smem_addr(s_taddr), TMEM_COLS);
         tm_relinquish();
@@ -283,15 +279,6 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
         *s_abort = 0;
     }
     const FusedInst& i0 = fb.inst[fb.items[blockIdx.x].x];
-    // W_2048^{j} for j < 2048; the k = 8 half of the last pair is never used (set to 1)
-    auto twp = [&](int step, int i, int m) {
-        const float2 lo = i0.twM[(step * i * (2 * m + 1)) & (M - 1)];
-        const float2 hi = (m < 3) ? i0.twM[(step * i * (2 * m + 2)) & (M - 1)] : f2(1.f, 0.f);
-        return make_float4(lo.x, lo.y, hi.x, hi.y);
-    };
-    for (int q = tid; q < 4 * 256; q += NT) tw1[q] = twp(1, q & 255, q >> 8);
-    for (int q = tid; q < 4 * 32; q += NT) tw2[q] = twp(8, q & 31, q >> 5);
-    for (int q = tid; q < 4 * 4; q += NT) tw3[q] = twp(64, q & 3, q >> 2);
     tm_fence_before();
     __syncthreads();
     tm_fence_after();
@@ -318,6 +305,38 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
     auto s3_pos = [&](int k3) { return ((k3 & 1) ? s3_w1 : s3_w0) + 16 * (k3 >> 1); };
     auto x3_pos = [&](int q0, int q1, int u0) { return ((u0 & 1) ? q1 : q0) + 64 * u0; };
     constexpr float inv2M = 0.5f / (float)M;
+
+    // this thread's twiddles into TMEM (written by group 0; thread t of every group reads them)
+    const uint32_t twc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(TW_COL + (t >> 7) * 64);
+    if (g == 0) {
+        float r[16];
+        auto put = [&](int step, int i, uint32_t col) {      // W_2048^{step i k}, k = 1..7
+#pragma unroll
+            for (int k = 1; k < 8; k++) {
+                const float2 w = i0.twM[(step * i * k) & (M - 1)];
+                r[2 * k - 2] = w.x;
+                r[2 * k - 1] = w.y;
+            }
+            r[14] = 0.f;
+            r[15] = 0.f;
+            tm_st16(twc + col, r);
+        };
+        put(1, t, 0);
+        put(8, s2_t0, 16);
+        put(64, s3_u0, 32);
+        float q[8];
+#pragma unroll
+        for (int k4 = 0; k4 < 4; k4++) {
+            const float2 w = mul(wA, wr(8, k4));
+            q[2 * k4] = w.x;
+            q[2 * k4 + 1] = w.y;
+        }
+        tm_st8(twc + 48, q);
+        tm_wait_st();
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
 
     const uint32_t bar = smem_addr(bars + g);
     float2* stg = stage + g * M;
@@ -408,7 +427,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
             dft8x<false>(v);
             {
                 float2 w[8];
-                tw_row(tw1, 256, t, w);
+                tw_tmem(twc, w);
 #pragma unroll
                 for (int k = 1; k < 8; k++) v[k] = mul(v[k], w[k]);
             }
@@ -430,7 +449,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
             dft8x<false>(v);
             {
                 float2 w[8];
-                tw_row(tw2, 32, s2_t0, w);
+                tw_tmem(twc + 16, w);
 #pragma unroll
                 for (int k = 1; k < 8; k++) v[k] = mul(v[k], w[k]);
             }
@@ -443,7 +462,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
             dft8x<false>(v);
             {
                 float2 w[8];
-                tw_row_full(tw3, 4, s3_u0, w);
+                tw_tmem(twc + 32, w);
 #pragma unroll
                 for (int k = 1; k < 8; k++) v[k] = mul(v[k], w[k]);
             }
@@ -459,8 +478,13 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
             tc++;
             // even/odd split into the real-input coefficients of this thread's modes
             float2 x[8];
+            {
+                float ws[8];
+                tm_ld8(twc + 48, ws);
+                tm_wait_ld();
 #pragma unroll
-            for (int k4 = 0; k4 < 4; k4++) split_fwd(A[k4], Bc[3 - k4], mul(wA, wr(8, k4)), x[2 * k4], x[2 * k4 + 1]);
+                for (int k4 = 0; k4 < 4; k4++) split_fwd(A[k4], Bc[3 - k4], f2(ws[2 * k4], ws[2 * k4 + 1]), x[2 * k4], x[2 * k4 + 1]);
+            }
             if (t == 0) {
                 // columns 0 and 256 pair with themselves: Z[0] gives (X_0, X_M), Z[512] with
                 // Z[1536], Z[1024] with itself, Z[256] with Z[1792], Z[768] with Z[1280]
@@ -597,8 +621,13 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
                 for (int i = 0; i < 4; i++) x[4 * c + i] = f2(r[2 * i], r[2 * i + 1]);
             }
             float2 A[4], Bc[4];
+            {
+                float ws[8];
+                tm_ld8(twc + 48, ws);
+                tm_wait_ld();
 #pragma unroll
-            for (int k4 = 0; k4 < 4; k4++) split_inv(x[2 * k4], x[2 * k4 + 1], mul(wA, wr(8, k4)), inv2M, A[k4], Bc[3 - k4]);
+                for (int k4 = 0; k4 < 4; k4++) split_inv(x[2 * k4], x[2 * k4 + 1], f2(ws[2 * k4], ws[2 * k4 + 1]), inv2M, A[k4], Bc[3 - k4]);
+            }
             if (t == 0) {
                 A[0] = f2((x[0].x + x[0].y) * inv2M, (x[0].x - x[0].y) * inv2M);
                 split_inv(x[2], x[6], wconst<8, 1, false>(), inv2M, A[1], A[3]);
@@ -618,7 +647,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
             for (int k = 0; k < 8; k++) v[k] = X[s3_pos(k)];
             {
                 float2 w[8];
-                tw_row_full(tw3, 4, s3_u0, w);
+                tw_tmem(twc + 32, w);
 #pragma unroll
                 for (int k = 1; k < 8; k++) v[k] = mulc(v[k], w[k]);
             }
@@ -631,7 +660,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
             for (int k = 0; k < 8; k++) v[k] = Y[(s2_k1 * 8 + k) * 34 + s2_t0];
             {
                 float2 w[8];
-                tw_row(tw2, 32, s2_t0, w);
+                tw_tmem(twc + 16, w);
 #pragma unroll
                 for (int k = 1; k < 8; k++) v[k] = mulc(v[k], w[k]);
             }
@@ -644,7 +673,7 @@ __global__ void __launch_bounds__(tmk::NT, 1) k_fused_tm(FusedBatch fb) {
             for (int k = 0; k < 8; k++) v[k] = X[k * 256 + t];
             {
                 float2 w[8];
-                tw_row(tw1, 256, t, w);
+                tw_tmem(twc, w);
 #pragma unroll
                 for (int k = 1; k < 8; k++) v[k] = mulc(v[k], w[k]);
             }
