@@ -75,7 +75,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fused_tm.cu", "fused_dev.cuh", "fused_api.cuh"):
+    for f in ("fused_tm.cu", "fused_dev.cuh", "fused_api.cuh", "packed_dev.cuh"):
         with open(os.path.join(ROOT, "paper_1502_01376_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
