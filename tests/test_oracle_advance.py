@@ -350,6 +350,56 @@ def test_gauss_law_3d(orc):
         assert np.max(np.abs(G1 - G0)) < 1e-12 * np.max(np.abs(G0))
 
 
+def _dense_x1_operator(n1, dx1, symbol):
+    """Real n1 x n1 matrix of the x1 operator whose Fourier symbol is symbol(k), from the DFT
+    definition with no FFT: D[j, l] = (1/n1) sum_kappa symbol(k_kappa) e^{2 pi i kappa (j - l) / n1},
+    k_kappa = 2 pi kappa / (n1 dx1) for kappa <= n1/2 and 2 pi (kappa - n1) / (n1 dx1) above."""
+    kap = np.arange(n1)
+    k = 2 * np.pi * np.where(kap <= n1 // 2, kap, kap - n1) / (n1 * dx1)
+    W = np.exp(2j * np.pi * np.outer(np.arange(n1), kap) / n1)
+    D = (W * symbol(k)) @ W.conj().T / n1
+    assert np.max(np.abs(D.imag)) < 1e-12          # Hermitian symbols give a real operator
+    return D.real
+
+
+@pytest.mark.parametrize("n1,n2", [(8, 4), (16, 6)])
+def test_dense_real_space_step_matches_oracle(orc, n1, n2):
+    """One step of the scheme written in real space with dense x1 operators built from the
+    Fourier symbols (sigma+- = i k e^{+-i k dx1/2}, the Eq. currentcorrection factor, the filter
+    table) and the finite differences of Eqs. hybrid2db1-hybrid2de3, no FFT anywhere, equals the
+    oracle's FFT-based step (Faraday first, then Ampere with the new B)."""
+    dx1, dx2, dt, A = 0.2, 0.25, 0.05, 4 * np.pi
+    g = orc.grid(n1=n1, n2=n2, dx1=dx1, dx2=dx2, dt=dt, filt_kc=0.5, filt_w=0.3)
+    _, _, filt = orc.mode_tables(g)
+    kstored = 2 * np.pi * np.arange(n1 // 2 + 1) / (n1 * dx1)
+    f_of = lambda k: np.interp(np.abs(k), kstored, filt)           # the filter table at |k|
+    corr_of = lambda k: np.where(k == 0, 1.0, np.sin(k * dx1 / 2) / np.where(k == 0, 1.0, k * dx1 / 2))
+    Dp = _dense_x1_operator(n1, dx1, lambda k: 1j * k * np.exp(1j * k * dx1 / 2))
+    Dm = _dense_x1_operator(n1, dx1, lambda k: 1j * k * np.exp(-1j * k * dx1 / 2))
+    C1 = _dense_x1_operator(n1, dx1, lambda k: corr_of(k) * f_of(k) + 0j)
+    Cf = _dense_x1_operator(n1, dx1, lambda k: f_of(k) + 0j)
+    rng = np.random.default_rng(n1)
+    E = [rng.standard_normal((n2, n1)) for _ in range(3)]
+    B = [rng.standard_normal((n2, n1)) for _ in range(3)]
+    J = [rng.standard_normal((n2, n1)) for _ in range(3)]
+    x1 = lambda D, f: f @ D.T                                      # apply along x1
+    up = lambda f: np.roll(f, -1, axis=0)                          # f[i2 + 1]
+    dn = lambda f: np.roll(f, 1, axis=0)                           # f[i2 - 1]
+    E1, E2, E3 = [a.copy() for a in E]
+    B1, B2, B3 = [a.copy() for a in B]
+    J1, J2, J3 = x1(C1, J[0]), x1(Cf, J[1]), x1(Cf, J[2])
+    B1 = B1 - dt * (up(E3) - E3) / dx2
+    B2 = B2 + dt * x1(Dp, E3)
+    B3 = B3 + dt * ((up(E1) - E1) / dx2 - x1(Dp, E2))
+    E1 = E1 + dt * (B3 - dn(B3)) / dx2 - A * dt * J1
+    E2 = E2 - dt * x1(Dm, B3) - A * dt * J2
+    E3 = E3 + dt * (x1(Dm, B2) - (B1 - dn(B1)) / dx2) - A * dt * J3
+    Eo, Bo = [a.copy() for a in E], [a.copy() for a in B]
+    orc.step(g, Eo, Bo, [a.copy() for a in J], nsteps=1)
+    for got, want in zip(Eo + Bo, [E1, E2, E3, B1, B2, B3]):
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
+
+
 def test_one_step_is_local_to_a_3x3_window(orc):
     """One step moves information one row in x2 and x3 (Faraday reads E one row ahead, Ampere B one
     row behind), so the step on the periodic 3 x 3 (x2, x3) window around a row gives that row's
