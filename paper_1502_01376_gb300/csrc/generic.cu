@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in
 //   E1 += a2 d2-B3 - a3 d3-B2 - cj1 J1;  E2 += a3 d3-B1 - Sm B3 - cj J2;  E3 += Sm B2 - a2 d2-B1 - cj J3
 // fields 3-5 invert B.  The spectral scratch is only read.
 template <bool D3>
-__global__ void __launch_bounds__(256) k_ampere_irfft1024(const float2* __restrict__ spec, RowPtrsW out, int64_t rows, int n2, int n3,
+__global__ void __launch_bounds__(256, 3) k_ampere_irfft1024(const float2* __restrict__ spec, RowPtrsW out, int64_t rows, int n2, int n3,
                                                           const float2* __restrict__ tw8, const float2* __restrict__ twN,
                                                           const float2* __restrict__ S, const float* __restrict__ cj1,
                                                           const float* __restrict__ cj, float a2, float a3) {

@@ -50,6 +50,22 @@ def test_quasi3d_matches_oracle(m, prec):
     grid.close()
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("nz,nr", [(16, 5), (2048, 9), (4096, 3)])
+def test_quasi3d_row_lengths(nz, nr, prec):
+    """Short rows (many rows per block), the batched workload's z length (one row per block, next
+    block prefetched) and rows longer than the prefetch holds (direct loads)."""
+    need_gpu()
+    hyb = hyb_module()
+    g, grid, (Eo, Bo, Jo), (Et, Bt, Jt), _ = _run_pair(hyb, 1, prec, nz=nz, nr=nr, nsteps=3, seed=nz + nr)
+    q.step(g, Eo, Bo, Jo, 3)
+    grid.advance(3)
+    for a, b in zip(Et + Bt, Eo + Bo):
+        assert rel_err(a.cpu().numpy().view(np.float64 if prec == 64 else np.float32).astype(np.float64),
+                       b.view(np.float64)) < TOL[prec]
+    grid.close()
+
+
 def test_quasi3d_in_batch_with_2d_grids():
     need_gpu()
     hyb = hyb_module()
