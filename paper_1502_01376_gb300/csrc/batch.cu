@@ -3,8 +3,8 @@
 // group is one persistent launch of k_fused2d<n1> over a table of work items
 // (grid, strip, first row, end row) from all its grids, preceded by one halo
 // launch.  Other grids (FP64, 3D, unsupported n1) run their three-pass step.
-// Groups are forked onto side streams inside the captured graph so that they
-// overlap.  hyb_batch_tune times candidate strip heights per group on scratch
+// Groups, and each of the other grids, are forked onto side streams inside the
+// captured graph so that they overlap.  hyb_batch_tune times candidate strip heights per group on scratch
 // fields and keeps the fastest (the autotuner).
 #include <algorithm>
 #include <vector>
@@ -26,6 +26,8 @@ struct hyb_batch {
     };
     std::vector<Group> groups;
     std::vector<int> others;               // grids on the three-pass path
+    std::vector<cudaStream_t> oside;       // one side stream (and fork/join events) per other grid
+    std::vector<cudaEvent_t> ofork, ojoin;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;
@@ -80,16 +82,20 @@ static hyb_status enqueue_step(hyb_batch* b, cudaStream_t s) {
         HYB_CUDA_TRY(fused_launch(G.n1, group_args(b, G), G.grid, G.side, nullptr, nullptr));
         HYB_CUDA_TRY(cudaEventRecord(G.join, G.side));
     }
-    for (int i : b->others) {
-        hyb_grid* g = b->grids[i];
+    for (size_t o = 0; o < b->others.size(); o++) {
+        hyb_grid* g = b->grids[b->others[o]];
+        HYB_CUDA_TRY(cudaEventRecord(b->ofork[o], s));
+        HYB_CUDA_TRY(cudaStreamWaitEvent(b->oside[o], b->ofork[o], 0));
         cudaStream_t keep = g->stream;
-        g->stream = s;
+        g->stream = b->oside[o];
         hyb_status st = g->d.dims == 20 ? quasi3d_advance(g, 1)
                        : g->d.precision == 32 ? generic_advance<float>(g, 1) : generic_advance<double>(g, 1);
         g->stream = keep;
         if (st != HYB_OK) return st;
+        HYB_CUDA_TRY(cudaEventRecord(b->ojoin[o], b->oside[o]));
     }
     for (auto& G : b->groups) HYB_CUDA_TRY(cudaStreamWaitEvent(s, G.join, 0));
+    for (cudaEvent_t e : b->ojoin) HYB_CUDA_TRY(cudaStreamWaitEvent(s, e, 0));
     return HYB_OK;
 }
 
@@ -148,7 +154,19 @@ hyb_status hyb_batch_create(const hyb_grid_desc* descs, int n, void* stream, hyb
         hyb_status st = group_plan(b, G);
         if (st != HYB_OK) { hyb_batch_destroy(b); return st; }
     }
-    b->launches_per_step = 2 * (int)b->groups.size() + 4 * (int)b->others.size();
+    for (size_t o = 0; o < b->others.size(); o++) {
+        cudaStream_t st_ = nullptr;
+        cudaEvent_t f = nullptr, j = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        b->oside.push_back(st_);
+        b->ofork.push_back(f);
+        b->ojoin.push_back(j);
+        if (e != cudaSuccess) { hyb_status st = cuda_fail(e, "stream/event creation"); hyb_batch_destroy(b); return st; }
+    }
+    b->launches_per_step = 2 * (int)b->groups.size();
+    for (int i : b->others) b->launches_per_step += hyb_launches_per_step(b->grids[i]);
     *out = b;
     return HYB_OK;
 }
@@ -268,6 +286,11 @@ hyb_status hyb_batch_destroy(hyb_batch* b) {
         if (G.side) cudaStreamDestroy(G.side);
         if (G.fork) cudaEventDestroy(G.fork);
         if (G.join) cudaEventDestroy(G.join);
+    }
+    for (size_t o = 0; o < b->oside.size(); o++) {
+        if (b->oside[o]) cudaStreamDestroy(b->oside[o]);
+        if (b->ofork[o]) cudaEventDestroy(b->ofork[o]);
+        if (b->ojoin[o]) cudaEventDestroy(b->ojoin[o]);
     }
     for (auto* g : b->grids) hyb_destroy_grid(g);
     delete b;

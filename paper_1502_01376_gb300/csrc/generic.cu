@@ -492,7 +492,7 @@ template <> const ModeTables<float>& tables<float>(hyb_grid* g) { return g->tf; 
 template <> const ModeTables<double>& tables<double>(hyb_grid* g) { return g->td; }
 
 // FP32 n1 = 1024 off the DFT-GEMM path: Ampere runs inside the inverse transform
-static bool amp_fused(const hyb_grid* g) { return g->d.precision == 32 && g->d.n1 == 1024 && g->path != 3; }
+static bool amp_fused(const hyb_grid* g) { return g->d.precision == 32 && g->d.n1 == 1024 && g->path != 3 && g->d.dims != 20; }
 
 template <typename T>
 hyb_status generic_advance(hyb_grid* g, int nsteps) {
