@@ -151,7 +151,9 @@ HYB_API hyb_status hyb_advance(hyb_grid* g, int nsteps);
 
 /* The same as hyb_advance, but E, B, J are HOST arrays (pinned memory
  * recommended): they are copied into the bound device arrays, advanced, and
- * E, B are copied back.  Synchronises the grid's stream. */
+ * E, B are copied back.  Synchronises the grid's stream.  On the fused path
+ * with nsteps = 1 the copies and the step are pipelined over chunks of rows
+ * (the device arrays end up holding the same values). */
 HYB_API hyb_status hyb_advance_host(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3], int nsteps);
 
 /* FP64 diagnostics of the bound fields, synchronous:

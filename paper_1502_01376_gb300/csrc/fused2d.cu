@@ -36,6 +36,7 @@
 // DC and Nyquist coefficients (both real) are packed into one complex slot.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "fused_dev.cuh"
@@ -437,10 +438,10 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::MINB) k_fused2d(FusedBatch
 }
 
 // copies the 7 halo rows of every work item: E1,E2,E3,B1,B3 of row p0-1 and E1,E3 of row p1
-__global__ void k_halo(FusedBatch fb, int n1) {
+__global__ void k_halo(FusedBatch fb, int n1, int k0) {
     const int4 it = fb.items[blockIdx.x];
     const FusedInst& a = fb.inst[it.x];
-    const int k = blockIdx.y;
+    const int k = k0 + blockIdx.y;
     const int n2 = a.n2, p0 = it.z, p1 = it.w;
     const int rl = (p0 - 1 + n2) % n2, rn = p1 % n2;
     const float* src;
@@ -508,11 +509,25 @@ static cudaError_t launch_n(const FusedBatch& fb, int grid, cudaStream_t s) {
 
 // one step for the work items of a launch: halo copy (unless the kernel exchanges
 // halos itself), then the persistent fused kernel
+cudaError_t halo_parts(int n1, const FusedBatch& fb, int k0, int nk, cudaStream_t s) {
+    if (fb.n_items < 1 || nk < 1) return cudaSuccess;
+    k_halo<<<dim3(fb.n_items, nk), 256, 0, s>>>(fb, n1, k0);
+    return cudaGetLastError();
+}
+
+cudaError_t fused_kernel_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s) {
+    switch (n1) {
+    case 512: return launch_n<512>(fb, grid, s);
+    case 1024: return launch_n<1024>(fb, grid, s);
+    case 2048: return launch_n<2048>(fb, grid, s);
+    default: return fused_tm_launch(fb, grid, s);
+    }
+}
+
 cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
     cudaError_t e;
     if (!fb.flags) {
-        k_halo<<<dim3(fb.n_items, 7), 256, 0, s>>>(fb, n1);
-        e = cudaGetLastError();
+        e = halo_parts(n1, fb, 0, 7, s);
         if (e != cudaSuccess) return e;
     }
     if (ev0) { e = cudaEventRecord(ev0, s); if (e != cudaSuccess) return e; }
@@ -623,6 +638,10 @@ hyb_status fused_create(hyb_grid* g) {
 void fused_destroy(hyb_grid* g) {
     FusedPlan* P = g->fused;
     if (!P) return;
+    if (P->hp_items) cudaFree(P->hp_items);
+    if (P->hp_halo) cudaFree(P->hp_halo);
+    for (cudaStream_t q : P->hp_s) if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t e : P->hp_ev) if (e) cudaEventDestroy(e);
     if (P->items) cudaFree(P->items);
     if (P->halo) cudaFree(P->halo);
     if (P->flags) cudaFree(P->flags);
@@ -649,5 +668,115 @@ hyb_status fused_advance(hyb_grid* g, int nsteps) {
 }
 
 int fused_launches_per_step(const hyb_grid* g) { return (g->fused && g->fused->flags) ? 1 : 2; }
+
+// ------------------------------------------------------------------ one step from and to host arrays
+// The copies over the host link dominate this step, so it is pipelined over chunks of rows:
+// stream 0 copies the rows in (the last row first, then chunk by chunk), stream 1 fills the
+// halo buffer and runs the fused kernel on chunk c as soon as chunks c and c + 1 have landed,
+// stream 2 copies chunk c's E and B back once it is computed, while later chunks still come in.
+// Halo rows must be taken before the rows they come from are updated in place: the lower
+// parts of chunk c + 1 (row p0 - 1 of its strips, the first of which is the last row of chunk
+// c) before chunk c runs, and the upper part of the very last strip (row 0) before chunk 0 runs.
+static hyb_status hp_plan(hyb_grid* g) {
+    FusedPlan* P = g->fused;
+    if (P->hp_chunks) return HYB_OK;
+    const int n2 = g->d.n2;
+    const int C = std::max(1, std::min(8, n2 / 8));
+    std::vector<int4> items;
+    P->hp_first.assign(1, 0);
+    P->hp_row0.assign(1, 0);
+    for (int c = 0; c < C; c++) {
+        const int r0 = (int)((int64_t)c * n2 / C), r1 = (int)((int64_t)(c + 1) * n2 / C);
+        const int ns = std::max(1, (r1 - r0) / 2);
+        for (int s = 0; s < ns; s++) {
+            const int p0 = r0 + (int)((int64_t)s * (r1 - r0) / ns), p1 = r0 + (int)((int64_t)(s + 1) * (r1 - r0) / ns);
+            items.push_back(make_int4(0, (int)items.size(), p0, p1));
+        }
+        P->hp_first.push_back((int)items.size());
+        P->hp_row0.push_back(r1);
+    }
+    HYB_CUDA_TRY(cudaMalloc(&P->hp_items, sizeof(int4) * items.size()));
+    HYB_CUDA_TRY(cudaMemcpy(P->hp_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    HYB_CUDA_TRY(cudaMalloc(&P->hp_halo, sizeof(float) * items.size() * 7 * (size_t)g->d.n1));
+    for (auto& q : P->hp_s) HYB_CUDA_TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+    P->hp_ev.assign(2 + 2 * (size_t)C, nullptr);
+    for (auto& e : P->hp_ev) HYB_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    P->hp_chunks = C;
+    return HYB_OK;
+}
+
+hyb_status fused_host_advance(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3]) {
+    hyb_status st = hp_plan(g);
+    if (st != HYB_OK) return st;
+    FusedPlan* P = g->fused;
+    const int n1 = g->d.n1, n2 = g->d.n2, C = P->hp_chunks;
+    const size_t rowb = sizeof(float) * (size_t)n1;
+    cudaStream_t in = P->hp_s[0], cmp = P->hp_s[1], out = P->hp_s[2];
+    cudaEvent_t fork = P->hp_ev[0], join = P->hp_ev[1];
+    auto ev_in = [&](int c) { return P->hp_ev[2 + c]; };
+    auto ev_cmp = [&](int c) { return P->hp_ev[2 + C + c]; };
+    void* const* hf[3] = {E, B, J};
+    void* df[3][3];
+    for (int c = 0; c < 3; c++) { df[0][c] = g->E[c]; df[1][c] = g->B[c]; df[2][c] = g->J[c]; }
+    auto rows_copy = [&](int kind, int comp, int r0, int r1, cudaMemcpyKind dir, cudaStream_t s) {
+        char* d = (char*)df[kind][comp] + (size_t)r0 * rowb;
+        char* h = (char*)hf[kind][comp] + (size_t)r0 * rowb;
+        return dir == cudaMemcpyHostToDevice ? cudaMemcpyAsync(d, h, (size_t)(r1 - r0) * rowb, dir, s)
+                                             : cudaMemcpyAsync(h, d, (size_t)(r1 - r0) * rowb, dir, s);
+    };
+    FusedBatch fb;
+    fb.inst[0] = fused_inst(g);
+    fb.inst[0].halo = P->hp_halo;
+    fb.flags = nullptr;
+    fb.epoch = 0;
+    fb.n_strips = 0;
+    fb.err = g->dflag;
+    auto sub = [&](int i0, int i1) {
+        FusedBatch b = fb;
+        b.items = P->hp_items + i0;
+        b.n_items = i1 - i0;
+        return b;
+    };
+    int occ = 0, sms = 0;
+    HYB_CUDA_TRY(fused_occupancy(n1, &occ));
+    HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+    const int last = P->hp_first[C] - 1;                   // the strip that ends at row n2 (wraps to row 0)
+    auto copy_in = [&](int ch) -> cudaError_t {
+        for (int k = 0; k < 3; k++)
+            for (int c = 0; c < 3; c++) {
+                cudaError_t e = rows_copy(k, c, P->hp_row0[ch], P->hp_row0[ch + 1], cudaMemcpyHostToDevice, in);
+                if (e != cudaSuccess) return e;
+            }
+        return cudaEventRecord(ev_in(ch), in);
+    };
+    HYB_CUDA_TRY(cudaEventRecord(fork, g->stream));
+    for (cudaStream_t q : P->hp_s) HYB_CUDA_TRY(cudaStreamWaitEvent(q, fork, 0));
+    // enqueued chunk by chunk so that each stream gets work as early as possible:
+    // copy in the last row, chunks 0 and 1; then per chunk c: copy in c + 2, compute c, copy out c
+    for (int k = 0; k < 3; k++)
+        for (int c = 0; c < 3; c++) HYB_CUDA_TRY(rows_copy(k, c, n2 - 1, n2, cudaMemcpyHostToDevice, in));
+    HYB_CUDA_TRY(copy_in(0));
+    if (C > 1) HYB_CUDA_TRY(copy_in(1));
+    HYB_CUDA_TRY(cudaStreamWaitEvent(cmp, ev_in(0), 0));
+    if (C > 1) HYB_CUDA_TRY(cudaStreamWaitEvent(cmp, ev_in(1), 0));
+    HYB_CUDA_TRY(halo_parts(n1, sub(last, last + 1), 5, 2, cmp));          // row 0, before chunk 0 runs
+    HYB_CUDA_TRY(halo_parts(n1, sub(P->hp_first[0], P->hp_first[1]), 0, 5, cmp));
+    for (int ch = 0; ch < C; ch++) {
+        if (ch + 2 < C) HYB_CUDA_TRY(copy_in(ch + 2));
+        if (ch + 1 < C) HYB_CUDA_TRY(cudaStreamWaitEvent(cmp, ev_in(ch + 1), 0));
+        const int i0 = P->hp_first[ch], i1 = P->hp_first[ch + 1];
+        HYB_CUDA_TRY(halo_parts(n1, sub(i0, ch + 1 == C ? i1 - 1 : i1), 5, 2, cmp));
+        if (ch + 1 < C) HYB_CUDA_TRY(halo_parts(n1, sub(i1, P->hp_first[ch + 2]), 0, 5, cmp));
+        const FusedBatch b = sub(i0, i1);
+        HYB_CUDA_TRY(fused_kernel_launch(n1, b, std::min(b.n_items, sms * occ), cmp));
+        HYB_CUDA_TRY(cudaEventRecord(ev_cmp(ch), cmp));
+        HYB_CUDA_TRY(cudaStreamWaitEvent(out, ev_cmp(ch), 0));
+        for (int k = 0; k < 2; k++)
+            for (int c = 0; c < 3; c++) HYB_CUDA_TRY(rows_copy(k, c, P->hp_row0[ch], P->hp_row0[ch + 1], cudaMemcpyDeviceToHost, out));
+    }
+    HYB_CUDA_TRY(cudaEventRecord(join, out));
+    HYB_CUDA_TRY(cudaStreamWaitEvent(g->stream, join, 0));
+    return HYB_OK;
+}
 
 }  // namespace hyb

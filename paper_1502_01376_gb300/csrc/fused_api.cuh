@@ -44,6 +44,15 @@ struct FusedPlan {
     float4* sym = nullptr;        // [M + 1] {Re S, Im S, cj1, cj}, S = c dt sigma+
     float2* twM = nullptr;        // [M] W_M^j (the grid's FP32 table)
     float2* twC = nullptr;        // [256] W_N^c
+    // host-array step (fused_host_advance): the rows in chunks, each chunk in short strips,
+    // with their own halo buffer, work items and three streams (copy in, compute, copy out)
+    int hp_chunks = 0;
+    int4* hp_items = nullptr;     // strips of all chunks in row order {0, strip, p0, p1}
+    std::vector<int> hp_first;    // first item of chunk c (hp_chunks + 1 entries)
+    std::vector<int> hp_row0;     // first row of chunk c (hp_chunks + 1 entries)
+    float* hp_halo = nullptr;     // [strips][7][n1]
+    cudaStream_t hp_s[3] = {nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> hp_ev;   // fork, join, then per chunk: input landed, chunk computed
 };
 
 size_t fused_smem_bytes(int n1);
@@ -55,6 +64,12 @@ cudaError_t wait_probe(int* dflag, int* derr, long long limit, int which, cudaSt
 int fused_threads(int n1);
 cudaError_t fused_occupancy(int n1, int* occ);
 cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+// the fused kernel alone (halo buffer already filled, or flag mode)
+cudaError_t fused_kernel_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s);
+// copies halo parts k0 .. k0 + nk - 1 (0-4: E1 E2 E3 B1 B3 of row p0 - 1; 5, 6: E1 E3 of row p1)
+// of the work items into the halo buffer
+cudaError_t halo_parts(int n1, const FusedBatch& fb, int k0, int nk, cudaStream_t s);
+hyb_status fused_host_advance(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3]);
 std::vector<int4> fused_items(int inst, int n2, int n_strips);
 FusedInst fused_inst(const hyb_grid* g);
 hyb_status fused_set_strips(hyb_grid* g, int n_strips);

@@ -300,6 +300,15 @@ hyb_status hyb_advance(hyb_grid* g, int nsteps) {
 hyb_status hyb_advance_host(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3], int nsteps) {
     if (!g || !E || !B || !J) { set_error("hyb_advance_host: null argument"); return HYB_EINVAL; }
     if (!g->bound) { set_error("hyb_advance_host: device fields not bound"); return HYB_ESTATE; }
+    for (int c = 0; c < 3; c++)
+        if (!E[c] || !B[c] || !J[c]) { set_error("hyb_advance_host: null field pointer"); return HYB_EINVAL; }
+    if (g->path == 2 && nsteps == 1) {
+        // one fused step: copies in, compute and copies out pipelined over chunks of rows
+        hyb_status st = fused_host_advance(g, E, B, J);
+        if (st != HYB_OK) return st;
+        HYB_CUDA_TRY(cudaStreamSynchronize(g->stream));
+        return HYB_OK;
+    }
     const size_t bytes = (size_t)g->cells * (g->d.precision == 32 ? 4 : 8) * (g->d.dims == 20 ? 2 : 1);
     for (int c = 0; c < 3; c++) {
         HYB_CUDA_TRY(cudaMemcpyAsync(g->E[c], E[c], bytes, cudaMemcpyHostToDevice, g->stream));

@@ -254,6 +254,37 @@ def test_advance_host_matches_device(orc):
         assert rel_err(a.numpy(), b) < 1e-12
 
 
+@pytest.mark.parametrize("n1,n2", [(4096, 1024), (1024, 37), (512, 4), (2048, 70)])
+def test_fused_host_step_matches_device_step(n1, n2):
+    """One fused step from and to host arrays (copies and compute pipelined over chunks of rows,
+    halo rows taken before the rows they come from are updated) equals the device-array step."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("hp", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.1, precision=32, filt_kc=0.5, filt_w=0.2, seed=17)
+    rng = np.random.default_rng(n1 + n2)
+    F0 = [rng.standard_normal(w.shape).astype(np.float32) * np.float32(1e-3) for _ in range(9)]
+    gd = hyb.Grid(hyb.desc_from_workload(w))
+    assert gd.path == 2
+    D = [torch.from_numpy(a.copy()).cuda() for a in F0]
+    gd.bind(D[0:3], D[3:6], D[6:9])
+    gd.advance(1)
+    gh = hyb.Grid(hyb.desc_from_workload(w))
+    Dh = [torch.zeros(w.shape, device="cuda") for _ in range(9)]
+    gh.bind(Dh[0:3], Dh[3:6], Dh[6:9])
+    H = [torch.from_numpy(a.copy()).pin_memory() for a in F0]
+    for _ in range(2):                      # twice: the second call reuses the pipeline's plan
+        for h, a in zip(H, F0):
+            h.copy_(torch.from_numpy(a))
+        gh.advance_host(H[0:3], H[3:6], H[6:9], 1)
+    gh.check()
+    torch.cuda.synchronize()
+    for a, b, dev in zip(H[:6], D[:6], Dh[:6]):
+        assert torch.equal(a, b.cpu()), float((a - b.cpu()).abs().max())
+        assert torch.equal(dev.cpu(), a)
+    gd.close()
+    gh.close()
+
+
 def test_courant_rejected_and_alignment():
     need_gpu()
     hyb = hyb_module()
