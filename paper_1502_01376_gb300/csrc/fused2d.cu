@@ -635,13 +635,21 @@ hyb_status fused_create(hyb_grid* g) {
     return HYB_OK;
 }
 
+static void hp_release(FusedPlan* P) {
+    if (P->hp_items) cudaFree(P->hp_items);
+    if (P->hp_halo) cudaFree(P->hp_halo);
+    for (cudaStream_t& q : P->hp_s) { if (q) cudaStreamDestroy(q); q = nullptr; }
+    for (cudaEvent_t e : P->hp_ev) if (e) cudaEventDestroy(e);
+    P->hp_items = nullptr;
+    P->hp_halo = nullptr;
+    P->hp_ev.clear();
+    P->hp_chunks = 0;
+}
+
 void fused_destroy(hyb_grid* g) {
     FusedPlan* P = g->fused;
     if (!P) return;
-    if (P->hp_items) cudaFree(P->hp_items);
-    if (P->hp_halo) cudaFree(P->hp_halo);
-    for (cudaStream_t q : P->hp_s) if (q) cudaStreamDestroy(q);
-    for (cudaEvent_t e : P->hp_ev) if (e) cudaEventDestroy(e);
+    hp_release(P);
     if (P->items) cudaFree(P->items);
     if (P->halo) cudaFree(P->halo);
     if (P->flags) cudaFree(P->flags);
@@ -680,6 +688,7 @@ int fused_launches_per_step(const hyb_grid* g) { return (g->fused && g->fused->f
 static hyb_status hp_plan(hyb_grid* g) {
     FusedPlan* P = g->fused;
     if (P->hp_chunks) return HYB_OK;
+    hp_release(P);                                 // whatever an earlier, failed plan left
     const int n2 = g->d.n2;
     const int C = std::max(1, std::min(8, n2 / 8));
     std::vector<int4> items;
