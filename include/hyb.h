@@ -79,8 +79,8 @@ typedef struct {
                              3: three-pass with the x1 transform as a dense DFT matrix product on
                                 the tensor cores, FP32 split into BF16 hi + lo (3 products),
                                 FP32 accumulation (precision 32, dims 2 or 3, 16 <= n1 <= 1024) */
-    int azimuthal_m;      /* dims 20 only: azimuthal mode number m >= 0.  The grid is then
-                             (z, r) = (x1, x2) with n1 = nz, n2 = nr, dx1 = dz, dx2 = dr, a
+    int azimuthal_m;      /* dims 20 only: azimuthal mode number 0 <= m <= 64.  The grid is then
+                             (z, r) = (x1, x2) with n1 = nz, n2 = nr <= 65535, dx1 = dz, dx2 = dr, a
                              perfectly conducting wall at r = n2 dx2, the axis at r = 0, and
                              every field and current is COMPLEX (interleaved re, im) of the
                              grid's precision: the amplitude of exp(i m phi) (Sec. 5). */

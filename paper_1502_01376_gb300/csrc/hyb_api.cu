@@ -184,6 +184,7 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
     if (d.dims != 2 && d.dims != 3 && d.dims != 20) { set_error("dims must be 2, 3 or 20 (got %d)", d.dims); return HYB_EINVAL; }
     if (d.dims != 3) { d.n3 = 1; d.dx3 = d.dx3 > 0 ? d.dx3 : 1.0; }
     if (d.dims == 20 && (d.azimuthal_m < 0 || d.azimuthal_m > 64)) { set_error("azimuthal_m must be in [0, 64]"); return HYB_EINVAL; }
+    if (d.dims == 20 && d.n2 > 65535) { set_error("quasi-3D grids take at most 65535 radial rows (got %d)", d.n2); return HYB_EINVAL; }
     if (!is_pow2(d.n1) || d.n1 < 8 || d.n1 > 8192) { set_error("n1 must be a power of two in [8, 8192] (got %d)", d.n1); return HYB_EINVAL; }
     if (d.n2 < 2 || (d.dims == 3 && d.n3 < 2)) { set_error("n2 (and n3 in 3D) must be >= 2"); return HYB_EINVAL; }
     if ((int64_t)d.n2 * d.n3 > (int64_t)1 << 30) { set_error("too many rows"); return HYB_EINVAL; }

@@ -105,13 +105,15 @@ template <typename T>
 __global__ void __launch_bounds__(kQThreads) k_qfaraday(cplx<T>* __restrict__ spec, int nz, int nr, const QTab<T>* __restrict__ tab,
                                                        T dt, T dr, int m) {
     using C = cplx<T>;
-    const int j = blockIdx.x;
+    const int j = blockIdx.y;                                        // radial row
     const int64_t fs = (int64_t)nr * nz;
     C* Ez = spec; C* Er = spec + fs; C* Ep = spec + 2 * fs;
     C* Bz = spec + 3 * fs; C* Br = spec + 4 * fs; C* Bp = spec + 5 * fs;
     const T ri = (T)j * dr, rh = ((T)j + (T)0.5) * dr, rup = (T)(j + 1) * dr;
     const T mT = (T)m;
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    {
+        const int k = blockIdx.x * blockDim.x + threadIdx.x;          // axial mode
+        if (k >= nz) return;
         const int64_t i = (int64_t)j * nz + k, iu = i + nz;
         const C sp = tab[k].sp;
         const C ez = Ez[i], er = Er[i], ep = Ep[i];
@@ -133,14 +135,16 @@ template <typename T>
 __global__ void __launch_bounds__(kQThreads) k_qampere(cplx<T>* __restrict__ spec, int nz, int nr, const QTab<T>* __restrict__ tab,
                                                       T dt, T dr, int m) {
     using C = cplx<T>;
-    const int j = blockIdx.x;
+    const int j = blockIdx.y;                                        // radial row
     const int64_t fs = (int64_t)nr * nz;
     C* Ez = spec; C* Er = spec + fs; C* Ep = spec + 2 * fs;
     const C* Bz = spec + 3 * fs; const C* Br = spec + 4 * fs; const C* Bp = spec + 5 * fs;
     const C* Jz = spec + 6 * fs; const C* Jr = spec + 7 * fs; const C* Jp = spec + 8 * fs;
     const T ri = (T)j * dr, rh = ((T)j + (T)0.5) * dr, rd = ((T)j - (T)0.5) * dr;
     const T mT = (T)m;
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    {
+        const int k = blockIdx.x * blockDim.x + threadIdx.x;          // axial mode
+        if (k >= nz) return;
         const int64_t i = (int64_t)j * nz + k, idn = i - nz;
         const QTab<T> q = tab[k];
         const C bz = Bz[i], br = Br[i], bp = Bp[i];
@@ -220,8 +224,9 @@ static hyb_status advance_t(hyb_grid* g, int nsteps) {
     for (int s = 0; s < nsteps; s++) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
         k_qfft<T, false><<<gf, kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, 9, P->tw, RB);
-        k_qfaraday<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
-        k_qampere<T><<<nr, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
+        const dim3 mgrid((unsigned)((nz + kQThreads - 1) / kQThreads), (unsigned)nr);   // one thread per (mode, row)
+        k_qfaraday<T><<<mgrid, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
+        k_qampere<T><<<mgrid, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
         k_qfft<T, true><<<gi, kQThreads, smem, g->stream>>>(fout, P->spec, nz, nr, 6, P->tw, RB);
         HYB_CUDA_TRY(cudaGetLastError());
         if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
