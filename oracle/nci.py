@@ -22,7 +22,7 @@ with w' = w + mu 2 pi/dt, k1' = k1 + nu1 2 pi/dx1, [w] = sin(w dt/2)/(dt/2),
 and for the hybrid solver [k]E1 = [k]B1 = k1 (plus the Sec. 4 bump when
 used), [k]E2 = [k]B2 = sin(k2 dx2/2)/(dx2/2).
 
-Readings of garbled or silent points (listed in the design doc):
+Readings of garbled or silent points:
   * s_{l,i} = (sin(k'_i dx_i/2) / (k'_i dx_i/2))^(l+1) with k' the aliased
     wavenumber (the printed form lacks the denominator's k');
   * the repeated "S_E1" of the interpolation list is S_E3 (unused in 2D);
