@@ -251,6 +251,7 @@ hyb_status hyb_set_stream(hyb_grid* g, void* stream) {
 
 hyb_status hyb_bind_fields(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3], void* rho) {
     if (!g || !E || !B || !J) { set_error("hyb_bind_fields: null argument"); return HYB_EINVAL; }
+    g->step_dirty = true;
     for (int c = 0; c < 3; c++) {
         if (!E[c] || !B[c] || !J[c]) { set_error("hyb_bind_fields: null field pointer"); return HYB_EINVAL; }
         if (!aligned16(E[c]) || !aligned16(B[c]) || !aligned16(J[c])) { set_error("hyb_bind_fields: field not 16-byte aligned"); return HYB_EALIGN; }
@@ -288,14 +289,57 @@ hyb_status hyb_filter(hyb_grid* g) {
     return g->d.precision == 32 ? generic_process_current<float>(g, false, true) : generic_process_current<double>(g, false, true);
 }
 
+// one step of the three-pass or quasi-3D path enqueued on g->stream
+static hyb_status step_once(hyb_grid* g) {
+    if (g->d.dims == 20) return quasi3d_advance(g, 1);
+    return g->d.precision == 32 ? generic_advance<float>(g, 1) : generic_advance<double>(g, 1);
+}
+
+// captures one step on a private stream (launches only: the step's kernels read and write the
+// bound arrays and the grid's scratch) into g->step_exec
+static hyb_status capture_step(hyb_grid* g) {
+    if (g->step_exec) { cudaGraphExecDestroy(g->step_exec); g->step_exec = nullptr; }
+    cudaStream_t cs = nullptr;
+    HYB_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t keep = g->stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    hyb_status st = HYB_OK;
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) {
+        g->stream = cs;
+        st = step_once(g);
+        g->stream = keep;
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    cudaStreamDestroy(cs);
+    if (st != HYB_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "step capture"); }
+    e = cudaGraphInstantiate(&g->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { g->step_exec = nullptr; return cuda_fail(e, "step graph instantiation"); }
+    g->step_dirty = false;
+    return HYB_OK;
+}
+
 hyb_status hyb_advance(hyb_grid* g, int nsteps) {
     if (!g) { set_error("null grid"); return HYB_EINVAL; }
     if (!g->bound) { set_error("hyb_advance: fields not bound"); return HYB_ESTATE; }
     if (nsteps < 0) { set_error("nsteps < 0"); return HYB_EINVAL; }
     if (nsteps == 0) return HYB_OK;
-    if (g->d.dims == 20) return quasi3d_advance(g, nsteps);
     if (g->path == 2) return fused_advance(g, nsteps);
-    return g->d.precision == 32 ? generic_advance<float>(g, nsteps) : generic_advance<double>(g, nsteps);
+    if (g->ev_start) {   // per-step kernel events requested: plain launches
+        for (int s = 0; s < nsteps; s++) {
+            hyb_status st = step_once(g);
+            if (st != HYB_OK) return st;
+        }
+        return HYB_OK;
+    }
+    if (g->step_dirty || !g->step_exec) {
+        hyb_status st = capture_step(g);
+        if (st != HYB_OK) return st;
+    }
+    for (int s = 0; s < nsteps; s++) HYB_CUDA_TRY(cudaGraphLaunch(g->step_exec, g->stream));
+    return HYB_OK;
 }
 
 hyb_status hyb_advance_host(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3], int nsteps) {
@@ -369,6 +413,7 @@ hyb_status hyb_wait_selftest(int which, double seconds, void* stream) {
 hyb_status hyb_destroy_grid(hyb_grid* g) {
     if (!g) return HYB_OK;
     if (g->stream) cudaStreamSynchronize(g->stream); else cudaDeviceSynchronize();
+    if (g->step_exec) cudaGraphExecDestroy(g->step_exec);
     if (g->fused) fused_destroy(g);
     if (g->qtab) quasi3d_destroy(g);
     if (g->dft) dftgemm_destroy(g);

@@ -240,6 +240,10 @@ struct hyb_grid {
     void* qtab = nullptr;          // quasi-3D per-mode tables (device)
     void* dft = nullptr;           // path 3: DFT-GEMM matrices and buffers
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional kernel timing events
+    // one three-pass (or quasi-3D) step captured as a CUDA graph and replayed per step, so
+    // that small grids do not pay a launch per kernel; re-captured after hyb_bind_fields
+    cudaGraphExec_t step_exec = nullptr;
+    bool step_dirty = true;
 };
 
 namespace hyb {
