@@ -330,6 +330,12 @@ __global__ void __launch_bounds__(256, 3) k_ampere_irfft1024(const float2* __res
 
 template <typename T>
 static size_t row_fft_smem(int n1, int RB) { return sizeof(cplx<T>) * 2 * fpad_size((size_t)RB * (n1 / 2)); }
+template <typename T>
+static size_t max_row_fft_smem() {
+    size_t m = 0;
+    for (int n1 = 8; n1 <= 8192; n1 *= 2) m = std::max(m, row_fft_smem<T>(n1, fft_rows_per_block(n1 / 2)));
+    return m;
+}
 
 template <typename Tin, typename T>
 static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
@@ -351,8 +357,9 @@ static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, i
     const int RB = fft_rows_per_launch(n1 / 2, rows * nf);
     const size_t smem = row_fft_smem<T>(n1, RB);
     auto kern = k_rfft_rows<Tin, T>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fft_smem<T>(n1, fft_rows_per_block(n1 / 2)));
-    if (e != cudaSuccess) return e;
+    // once per kernel: room for the largest row block any n1 up to 8192 asks for
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_row_fft_smem<T>());
+    if (attr != cudaSuccess) return attr;
     dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
     kern<<<grid, kRowThreads, smem, s>>>(p, out, n1, rows, t.twS, t.twN, RB);
     return cudaGetLastError();
@@ -371,8 +378,9 @@ static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, in
     const int RB = fft_rows_per_launch(n1 / 2, rows * nf);
     const size_t smem = row_fft_smem<T>(n1, RB);
     auto kern = k_irfft_rows<T, Tout>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_fft_smem<T>(n1, fft_rows_per_block(n1 / 2)));
-    if (e != cudaSuccess) return e;
+    // once per kernel: room for the largest row block any n1 up to 8192 asks for
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_row_fft_smem<T>());
+    if (attr != cudaSuccess) return attr;
     dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
     kern<<<grid, kRowThreads, smem, s>>>(in, p, n1, rows, t.twS, t.twN, f0, RB);
     return cudaGetLastError();

@@ -327,7 +327,10 @@ hyb_status hyb_advance(hyb_grid* g, int nsteps) {
     if (nsteps < 0) { set_error("nsteps < 0"); return HYB_EINVAL; }
     if (nsteps == 0) return HYB_OK;
     if (g->path == 2) return fused_advance(g, nsteps);
-    if (g->ev_start) {   // per-step kernel events requested: plain launches
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    HYB_CUDA_TRY(cudaStreamIsCapturing(g->stream, &cap));
+    if (g->ev_start || cap != cudaStreamCaptureStatusNone) {
+        // per-step kernel events requested, or the caller is capturing its own graph: plain launches
         for (int s = 0; s < nsteps; s++) {
             hyb_status st = step_once(g);
             if (st != HYB_OK) return st;

@@ -403,3 +403,39 @@ def test_three_pass_3d_full_size_sampled_rows(orc):
             err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
             assert err < TOL[32], (i3, i2, name, err)
     g.close()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_three_pass_step_inside_a_caller_graph(prec):
+    """hyb_advance on the three-pass path replays its own captured step graph; called while the
+    caller captures a CUDA graph of its own it launches plainly into that capture, and replaying
+    the caller's graph advances the fields exactly like direct calls."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("cg", 3, 64, 6, 5, dx1=0.2, dx2=0.2, dx3=0.25, dt=0.06, precision=prec, filt_kc=0.5,
+                    filt_w=0.2, seed=23)
+    dt = torch.float64 if prec == 64 else torch.float32
+    rng = np.random.default_rng(5)
+    F0 = [rng.standard_normal(w.shape) * 1e-3 for _ in range(9)]
+    ga = hyb.Grid(hyb.desc_from_workload(w, path=1))
+    A = [to_dev(a, dt) for a in F0]
+    ga.bind(A[0:3], A[3:6], A[6:9])
+    ga.advance(1)                           # warm: tables, launch attributes, the grid's own step graph
+    gb = hyb.Grid(hyb.desc_from_workload(w, path=1))
+    Bt = [to_dev(a, dt) for a in F0]
+    gb.bind(Bt[0:3], Bt[3:6], Bt[6:9])
+    gb.advance(1)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    hyb.hyb_set_stream(gb.h, s.cuda_stream)
+    with torch.cuda.graph(graph, stream=s):
+        gb.advance(1)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        graph.replay()
+    ga.advance(3)
+    torch.cuda.synchronize()
+    for a, b in zip(A[:6], Bt[:6]):
+        assert torch.equal(a, b)
+    ga.close()
+    gb.close()
