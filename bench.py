@@ -298,9 +298,11 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler.mark(True)
+    n_launch0 = net.launch_count()
     ev0.record()
     hist = sg.train(net, X, y, steps=steps, batch=batch, lr=2e-3, seed=1)
     ev1.record()
+    n_launches = net.launch_count() - n_launch0
     torch.cuda.synchronize()
     sampler.mark(False)
     train_ms = ev0.elapsed_time(ev1)
@@ -330,7 +332,7 @@ def run_surrogate(args):
             "value": steps * batch / (train_ms / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": train_ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "gpu_launches": None, "clocks": sampler.summary(),
+            "gpu_launches": n_launches, "clocks": sampler.summary(),
             "config": {"workload": "nci_surrogate_200k", "samples": n, "kept_below_courant": kept,
                        "label_seconds": t_data, "batch": batch, "loss_first": float(hist[:10].mean()),
                        "loss_last": float(hist[-50:].mean()), "val_mse_over_var": mse / var,

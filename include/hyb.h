@@ -275,6 +275,9 @@ HYB_API hyb_status hyb_mlp_gradients(hyb_mlp* m, const float* x, const float* ta
  * the loss before the step is written to loss_dev (device FP32, nullable). */
 HYB_API hyb_status hyb_mlp_train_step(hyb_mlp* m, const float* x, const float* target, int64_t B, float lr, float* loss_dev,
                                       void* stream);
+/* Kernels this network has launched so far (instrumentation: nine per layer
+ * plus one per training step, fewer for a forward pass alone). */
+HYB_API int64_t hyb_mlp_launch_count(const hyb_mlp* m);
 HYB_API hyb_status hyb_mlp_destroy(hyb_mlp* m);
 
 /* Which advance path a grid runs: 1 three-pass, 2 fused, 3 three-pass with DFT-GEMM. */

@@ -34,6 +34,7 @@ struct hyb_mlp {
     float* dx = nullptr;                  // [cap][256] FP32 dX
     float* loss = nullptr;                // device scalar
     int64_t step = 0;
+    int64_t launches = 0;                 // kernels launched so far (hyb_mlp_launch_count)
 };
 
 namespace hyb {
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, int kmax
 // Few output tiles and a long K (the weight gradients: K = batch) are split along K
 // over up to 64 blocks per tile, the partial sums added atomically into C.
 static void gemm(int M, int N, int K, const __nv_bfloat16* a, int64_t sam, int64_t sak, const __nv_bfloat16* b, int64_t sbk,
-                 int64_t sbn, float* c, int64_t scm, int acc, cudaStream_t s) {
+                 int64_t sbn, float* c, int64_t scm, int acc, cudaStream_t s, int64_t& launches) {
     const int Kp = (K + 15) & ~15;
     const int tiles = ((N + TN - 1) / TN) * ((M + TM - 1) / TM);
     int split = 1;
@@ -139,6 +140,7 @@ static void gemm(int M, int N, int K, const __nv_bfloat16* a, int64_t sam, int64
     if (split > 1 && !acc) cudaMemsetAsync(c, 0, sizeof(float) * (size_t)M * scm, s);   // rows of stride scm >= N
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, split);
     k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, Kp, K, a, sam, sak, b, sbk, sbn, c, scm, acc, kchunk);
+    launches++;
 }
 
 // x (FP32 [B][n_in]) -> BF16 [B][kin] with zero padding
@@ -245,6 +247,7 @@ static hyb_status refresh(hyb_mlp* m, cudaStream_t s) {
     for (int l = 0; l < m->L; l++) {
         const int fo = layer_out(m, l), fi = layer_in(m, l), fop = pad16(fo), fip = pad16(fi);
         k_refresh<<<(fop * fip + 255) / 256, 256, 0, s>>>(m->master + m->w_off[l], fo, fi, fop, fip, m->wbf + m->wb_off[l]);
+        m->launches++;
     }
     HYB_CUDA_TRY(cudaGetLastError());
     return HYB_OK;
@@ -271,15 +274,17 @@ static hyb_status forward(hyb_mlp* m, const float* x, int64_t B, float* y, cudaS
     if (st != HYB_OK) return st;
     const int64_t cap = m->cap;
     k_pack_input<<<(unsigned)((B * m->kin + 255) / 256), 256, 0, s>>>(x, B, m->n_in, m->kin, m->act);
+    m->launches++;
     for (int l = 0; l < m->L; l++) {
         const int fi = pad16(layer_in(m, l)), fo = pad16(layer_out(m, l));
         const __nv_bfloat16* X = m->act + (size_t)l * cap * 256;
         float* H = m->pre + (size_t)l * cap * 256;
         // H[B][fo] = X[B][fi] W^T, W stored [fo][fi]
-        gemm((int)B, fo, fi, X, 256, 1, m->wbf + m->wb_off[l], 1, fi, H, 256, 0, s);
+        gemm((int)B, fo, fi, X, 256, 1, m->wbf + m->wb_off[l], 1, fi, H, 256, 0, s, m->launches);
         const bool hidden = l < m->L - 1;
         k_bias_act<<<(unsigned)((B * fo + 255) / 256), 256, 0, s>>>(H, m->master + m->b_off[l], B, layer_out(m, l), fo, hidden,
                                                                   m->act + (size_t)(l + 1) * cap * 256, y);
+        m->launches++;
     }
     HYB_CUDA_TRY(cudaGetLastError());
     return HYB_OK;
@@ -289,18 +294,23 @@ static hyb_status backward(hyb_mlp* m, const float* tgt, int64_t B, cudaStream_t
     const int64_t cap = m->cap;
     HYB_CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
     k_loss<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(m->pre + (size_t)(m->L - 1) * cap * 256, tgt, B, m->dh, m->loss);
+    m->launches++;
     for (int l = m->L - 1; l >= 0; l--) {
         const int fi = pad16(layer_in(m, l)), fo = pad16(layer_out(m, l));
         const int ni = layer_in(m, l), no = layer_out(m, l);
         k_to_bf16<<<(unsigned)((B * 256 + 255) / 256), 256, 0, s>>>(m->dh, B * 256, m->dhb);
+        m->launches++;
         // dW[fo][fi] = dH^T X: M = fo, N = fi, K = B (B padded to 16 with zero rows)
-        gemm(fo, fi, (int)B, m->dhb, 1, 256, m->act + (size_t)l * cap * 256, 256, 1, m->dx, 256, 0, s);
+        gemm(fo, fi, (int)B, m->dhb, 1, 256, m->act + (size_t)l * cap * 256, 256, 1, m->dx, 256, 0, s, m->launches);
         k_copy_grad<<<(no * ni + 255) / 256, 256, 0, s>>>(m->dx, no, ni, 256, m->grad + m->w_off[l]);
+        m->launches++;
         k_colsum<<<no, 256, 0, s>>>(m->dh, B, no, m->grad + m->b_off[l]);
+        m->launches++;
         if (l > 0) {
             // dX[B][fi] = dH[B][fo] W[fo][fi]
-            gemm((int)B, fi, fo, m->dhb, 256, 1, m->wbf + m->wb_off[l], fi, 1, m->dx, 256, 0, s);
+            gemm((int)B, fi, fo, m->dhb, 256, 1, m->wbf + m->wb_off[l], fi, 1, m->dx, 256, 0, s, m->launches);
             k_act_back<<<(unsigned)((B * fi + 255) / 256), 256, 0, s>>>(m->dx, m->pre + (size_t)(l - 1) * cap * 256, B, ni, fi, m->dh);
+            m->launches++;
         }
     }
     HYB_CUDA_TRY(cudaGetLastError());
@@ -392,12 +402,15 @@ hyb_status hyb_mlp_train_step(hyb_mlp* m, const float* x, const float* target, i
     const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
     k_adam<<<(unsigned)((m->n_params + 255) / 256), 256, 0, s>>>(m->master, m->grad, m->adam_m, m->adam_v, (int64_t)m->n_params,
                                                                 lr, b1, b2, 1e-8f, c1, c2);
+    m->launches++;
     HYB_CUDA_TRY(cudaGetLastError());
     st = refresh(m, s);
     if (st != HYB_OK) return st;
     if (loss_dev) HYB_CUDA_TRY(cudaMemcpyAsync(loss_dev, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
     return HYB_OK;
 }
+
+int64_t hyb_mlp_launch_count(const hyb_mlp* m) { return m ? m->launches : 0; }
 
 hyb_status hyb_mlp_destroy(hyb_mlp* m) {
     if (!m) return HYB_OK;

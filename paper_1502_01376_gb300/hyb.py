@@ -123,6 +123,8 @@ def lib():
             L.hyb_mlp_train_step.restype = S
             L.hyb_mlp_destroy.argtypes = [_V]
             L.hyb_mlp_destroy.restype = S
+            L.hyb_mlp_launch_count.argtypes = [_V]
+            L.hyb_mlp_launch_count.restype = ctypes.c_int64
             L.hyb_launches_per_step.argtypes = [_V]
             L.hyb_launches_per_step.restype = ctypes.c_int
             L.hyb_wait_selftest.argtypes = [ctypes.c_int, ctypes.c_double, _V]
@@ -458,6 +460,9 @@ class MLP:
                                        g.ctypes.data_as(_V), loss.ctypes.data_as(_V),
                                        _V(torch.cuda.current_stream().cuda_stream)))
         return g, float(loss[0])
+
+    def launch_count(self) -> int:
+        return int(lib().hyb_mlp_launch_count(_V(self.h)))
 
     def train_step(self, x, t, lr, loss_out=None):
         import torch
