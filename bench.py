@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and fp64 comparison")
     ap.add_argument("--quick", action="store_true",
                     help="profiling mode: random band-limited J instead of the particle deposit, no extras")
+    ap.add_argument("--n1", type=int, default=4096,
+                    help="drift_plasma with another row length at the same 4096 x 1024 cells (4096 is the "
+                         "benchmark; others show the n1 = 512 .. 2048 kernels and the three-pass path)")
     ap.add_argument("--rows3d", type=int, default=256,
                     help="3d workload: n2 = n3 = this (256 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--workload", default="drift_plasma",
@@ -491,6 +494,8 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     w = wl.DRIFT_PLASMA
+    if args.n1 != w.n1:
+        w = w.scaled(n1=args.n1, n2=w.cells // args.n1, name=f"drift_plasma_2d_{args.n1}x{w.cells // args.n1}_f32")
     stream = torch.cuda.current_stream()
     grid = hyb.Grid(hyb.desc_from_workload(w, path=0), stream)
     E0, B0 = wl.band_limited_fields(w)
@@ -620,7 +625,8 @@ def main():
     if rank == 0:
         peak, src = peaks()
         achieved = BYTES_PER_CELL_STEP * cells / (kms / 1e3) / 1e9
-        traffic = profiled_traffic(cells)
+        traffic = profiled_traffic(cells) if (grid.path == 2 and w.n1 == 4096) else None
+        kname = ("k_fused_tm" if w.n1 == 4096 else f"k_fused2d<{w.n1}>") if grid.path == 2 else "three-pass step"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -632,7 +638,7 @@ def main():
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": src,
-                         "kernel": "k_fused_tm" if grid.path == 2 else "three-pass step",
+                         "kernel": kname,
                          "kernel_ms": kms, "bytes_per_launch": BYTES_PER_CELL_STEP * cells,
                          "kernel_timing": "events around the kernel on its stream, a second pass of K steps"},
             "gpu_launches": launches,
