@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--n1", type=int, default=4096,
                     help="drift_plasma with another row length at the same 4096 x 1024 cells (4096 is the "
                          "benchmark; others show the n1 = 512 .. 2048 kernels and the three-pass path)")
+    ap.add_argument("--batch-strips", default="",
+                    help="batched workload: rows per strip per n1 as '512:3,1024:2,...' instead of the autotuner")
     ap.add_argument("--rows3d", type=int, default=256,
                     help="3d workload: n2 = n3 = this (256 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--workload", default="drift_plasma",
@@ -392,12 +394,19 @@ def run_other(args):
         for i, (E, B, J) in enumerate(bufs):
             b.bind(i, E, B, J)
         t0 = time.perf_counter()
-        b.tune(3)
+        if args.batch_strips:
+            for kv in args.batch_strips.split(","):
+                n1_, h_ = (int(v) for v in kv.split(":"))
+                b.set_rows_per_strip(n1_, h_)
+        else:
+            b.tune(3)
         tune_s = time.perf_counter() - t0
         ms = time_steps(lambda: b.advance(1), args.steps, args.warmup, stream, flush, sampler)
         launches = b.launches_per_step * args.steps
         extra["config"] = {"workload": "batched_16x2d_uneven_plus_quasi3d_m012_2048x512", "instances_2d": sizes,
-                           "quasi3d_modes": [0, 1, 2], "quasi3d_grid": [nz, nr], "autotune_s": tune_s,
+                           "quasi3d_modes": [0, 1, 2], "quasi3d_grid": [nz, nr],
+                           "strips": "set by --batch-strips" if args.batch_strips else "autotuned",
+                           "autotune_s": tune_s,
                            "rows_per_strip": {n1: b.rows_per_strip(n1) for n1 in (512, 1024, 2048, 4096)},
                            "current": "band-limited random J (no deposit in the timed step)",
                            "l2": "flushed between timed steps (256 MB write)"}

@@ -222,6 +222,11 @@ HYB_API hyb_status hyb_batch_advance(hyb_batch* b, int nsteps);
 /* Tuned rows per strip of the group with this n1 (0 if none). */
 HYB_API int hyb_batch_rows_per_strip(const hyb_batch* b, int n1);
 
+/* Sets the rows per strip of the group with this n1 (as the autotuner would),
+ * e.g. to reuse a height found by an earlier hyb_batch_tune.  h >= 1.
+ * HYB_EINVAL if no group has this n1.  Synchronous (uploads the work items). */
+HYB_API hyb_status hyb_batch_set_rows_per_strip(hyb_batch* b, int n1, int h);
+
 /* Kernel launches in one step of the batch (the nodes of its graph). */
 HYB_API int hyb_batch_launches_per_step(const hyb_batch* b);
 

@@ -274,6 +274,18 @@ int hyb_batch_rows_per_strip(const hyb_batch* b, int n1) {
     return 0;
 }
 
+hyb_status hyb_batch_set_rows_per_strip(hyb_batch* b, int n1, int h) {
+    if (!b) { set_error("null batch"); return HYB_EINVAL; }
+    if (h < 1) { set_error("rows per strip must be >= 1"); return HYB_EINVAL; }
+    for (auto& G : b->groups)
+        if (G.n1 == n1) {
+            G.rows_per_strip = h;
+            return group_plan(b, G);
+        }
+    set_error("no fused group with this n1");
+    return HYB_EINVAL;
+}
+
 int hyb_batch_launches_per_step(const hyb_batch* b) { return b ? b->launches_per_step : 0; }
 
 hyb_status hyb_batch_destroy(hyb_batch* b) {

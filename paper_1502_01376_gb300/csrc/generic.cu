@@ -589,7 +589,7 @@ hyb_status generic_process_current(hyb_grid* g, bool corr, bool filt) {
     return HYB_OK;
 }
 
-int generic_launches_per_step(const hyb_grid* g) { return amp_fused(g) ? 3 : 4; }
+int generic_launches_per_step(const hyb_grid* g) { return (amp_fused(g) || g->d.dims == 20) ? 3 : 4; }
 
 template hyb_status generic_advance<float>(hyb_grid*, int);
 template hyb_status generic_advance<double>(hyb_grid*, int);

@@ -8,8 +8,9 @@
 // in the E1..B3 slots), r_j = j dr.  Axis: E_z(0) from the circulation of
 // B_phi round a disc of radius dr/2 for m = 0, else 0; E_phi(0), B_r(0) only
 // for m = 1 (with dB_z/dr(0) = 2 B_z(dr/2)/dr and (i m/r) E_z -> i m E_z(dr)/dr),
-// else 0.  A perfect conductor at r = n_r dr.  Three passes per step: complex
-// FFT along z of the nine arrays, Faraday then Ampere per (r, k_z), inverse FFT.
+// else 0.  A perfect conductor at r = n_r dr.  Three launches per step: complex
+// FFT along z of the nine arrays, the leapfrog (Faraday then Ampere) per (r, k_z)
+// in one kernel, inverse FFT of the six advanced spectra.
 #include <math.h>
 
 #include <vector>
@@ -32,7 +33,7 @@ template <typename T>
 struct QPlan {
     QTab<T>* tab = nullptr;
     cplx<T>* tw = nullptr;    // stockham_twiddles(nz)
-    cplx<T>* spec = nullptr;  // [9][nr][nz]
+    cplx<T>* spec = nullptr;  // [12][nr][nz]: E, B, J spectra, then the advanced B (E^{n+1} replaces J)
 };
 
 struct QPtrs { void* p[9]; };
@@ -102,70 +103,75 @@ __global__ void __launch_bounds__(kQThreads) k_qfft(QPtrs io, cplx<T>* __restric
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kQThreads) k_qfaraday(cplx<T>* __restrict__ spec, int nz, int nr, const QTab<T>* __restrict__ tab,
-                                                       T dt, T dr, int m) {
+struct QB { cplx<T> z, r, p; };
+
+// Faraday for axial mode k at radial row j: B^{n+1/2} from B^{n-1/2} at j and E^n at rows j and j+1
+// (tangential E vanishes on the conducting wall r = nr dr; on the axis B_r follows the m rules)
+template <typename T>
+__device__ __forceinline__ QB<T> qfaraday_at(const cplx<T>* __restrict__ spec, int64_t fs, int nz, int nr, int j, int k,
+                                             cplx<T> sp, T dt, T dr, int m) {
     using C = cplx<T>;
-    const int j = blockIdx.y;                                        // radial row
-    const int64_t fs = (int64_t)nr * nz;
-    C* Ez = spec; C* Er = spec + fs; C* Ep = spec + 2 * fs;
-    C* Bz = spec + 3 * fs; C* Br = spec + 4 * fs; C* Bp = spec + 5 * fs;
+    const C* Ez = spec; const C* Er = spec + fs; const C* Ep = spec + 2 * fs;
+    const C* Bz = spec + 3 * fs; const C* Br = spec + 4 * fs; const C* Bp = spec + 5 * fs;
     const T ri = (T)j * dr, rh = ((T)j + (T)0.5) * dr, rup = (T)(j + 1) * dr;
     const T mT = (T)m;
-    {
-        const int k = blockIdx.x * blockDim.x + threadIdx.x;          // axial mode
-        if (k >= nz) return;
-        const int64_t i = (int64_t)j * nz + k, iu = i + nz;
-        const C sp = tab[k].sp;
-        const C ez = Ez[i], er = Er[i], ep = Ep[i];
-        const C ezu = (j + 1 < nr) ? Ez[iu] : mkc<C>((T)0, (T)0);       // wall: tangential E = 0
-        const C epu = (j + 1 < nr) ? Ep[iu] : mkc<C>((T)0, (T)0);
-        C cr;
-        if (j > 0) cr = csub(imr(ez, mT / ri), cmul(sp, ep));
-        else if (m == 1) cr = csub(imr(Ez[nz + k], mT / dr), cmul(sp, ep));
-        else cr = mkc<C>((T)0, (T)0);
-        const C cp = csub(cmul(sp, er), cscale(csub(ezu, ez), (T)1 / dr));
-        const C cz = csub(cscale(csub(cscale(epu, rup), cscale(ep, ri)), (T)1 / (rh * dr)), imr(er, mT / rh));
-        Bz[i] = csub(Bz[i], cscale(cz, dt));
-        Br[i] = (j == 0 && m != 1) ? mkc<C>((T)0, (T)0) : csub(Br[i], cscale(cr, dt));
-        Bp[i] = csub(Bp[i], cscale(cp, dt));
-    }
+    const int64_t i = (int64_t)j * nz + k, iu = i + nz;
+    const C ez = Ez[i], er = Er[i], ep = Ep[i];
+    const C ezu = (j + 1 < nr) ? Ez[iu] : mkc<C>((T)0, (T)0);
+    const C epu = (j + 1 < nr) ? Ep[iu] : mkc<C>((T)0, (T)0);
+    C cr;
+    if (j > 0) cr = csub(imr(ez, mT / ri), cmul(sp, ep));
+    else if (m == 1) cr = csub(imr(Ez[nz + k], mT / dr), cmul(sp, ep));
+    else cr = mkc<C>((T)0, (T)0);
+    const C cp = csub(cmul(sp, er), cscale(csub(ezu, ez), (T)1 / dr));
+    const C cz = csub(cscale(csub(cscale(epu, rup), cscale(ep, ri)), (T)1 / (rh * dr)), imr(er, mT / rh));
+    QB<T> b;
+    b.z = csub(Bz[i], cscale(cz, dt));
+    b.r = (j == 0 && m != 1) ? mkc<C>((T)0, (T)0) : csub(Br[i], cscale(cr, dt));
+    b.p = csub(Bp[i], cscale(cp, dt));
+    return b;
 }
 
+// one leapfrog step per (axial mode k, radial row j) on the spectra [E, B, J] (slots 0..8): Faraday at
+// rows j and j-1 (the latter recomputed, so no launch boundary is needed between the halves), then
+// Ampere at row j.  E^{n+1} goes to the J slots 6..8 (J at row j is read by this thread only) and
+// B^{n+1/2} to slots 9..11; slots 0..5 are only read, so neighbouring threads see the old values.
 template <typename T>
-__global__ void __launch_bounds__(kQThreads) k_qampere(cplx<T>* __restrict__ spec, int nz, int nr, const QTab<T>* __restrict__ tab,
-                                                      T dt, T dr, int m) {
+__global__ void __launch_bounds__(kQThreads) k_qleap(cplx<T>* __restrict__ spec, int nz, int nr, const QTab<T>* __restrict__ tab,
+                                                    T dt, T dr, int m) {
     using C = cplx<T>;
     const int j = blockIdx.y;                                        // radial row
-    const int64_t fs = (int64_t)nr * nz;
-    C* Ez = spec; C* Er = spec + fs; C* Ep = spec + 2 * fs;
-    const C* Bz = spec + 3 * fs; const C* Br = spec + 4 * fs; const C* Bp = spec + 5 * fs;
-    const C* Jz = spec + 6 * fs; const C* Jr = spec + 7 * fs; const C* Jp = spec + 8 * fs;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;             // axial mode
+    if (k >= nz) return;
+    const int64_t fs = (int64_t)nr * nz, i = (int64_t)j * nz + k;
+    const C* Ez = spec; const C* Er = spec + fs; const C* Ep = spec + 2 * fs;
+    C* Jz = spec + 6 * fs; C* Jr = spec + 7 * fs; C* Jp = spec + 8 * fs;
+    C* Bn = spec + 9 * fs;
     const T ri = (T)j * dr, rh = ((T)j + (T)0.5) * dr, rd = ((T)j - (T)0.5) * dr;
     const T mT = (T)m;
-    {
-        const int k = blockIdx.x * blockDim.x + threadIdx.x;          // axial mode
-        if (k >= nz) return;
-        const int64_t i = (int64_t)j * nz + k, idn = i - nz;
-        const QTab<T> q = tab[k];
-        const C bz = Bz[i], br = Br[i], bp = Bp[i];
-        const C cr = csub(imr(bz, mT / rh), cmul(q.sm, bp));
-        C cp, cz;
-        if (j > 0) {
-            cp = csub(cmul(q.sm, br), cscale(csub(bz, Bz[idn]), (T)1 / dr));
-            cz = csub(cscale(csub(cscale(bp, rh), cscale(Bp[idn], rd)), (T)1 / (ri * dr)), imr(br, mT / ri));
-        } else {
-            cp = (m == 1) ? csub(cmul(q.sm, br), cscale(bz, (T)2 / dr)) : mkc<C>((T)0, (T)0);
-            cz = (m == 0) ? cscale(bp, (T)4 / dr) : mkc<C>((T)0, (T)0);
-        }
-        C er = csub(cadd(Er[i], cscale(cr, dt)), cscale(Jr[i], q.cj));
-        C ep = csub(cadd(Ep[i], cscale(cp, dt)), cscale(Jp[i], q.cj));
-        C ez = csub(cadd(Ez[i], cscale(cz, dt)), cscale(Jz[i], q.cjz));
-        if (j == 0 && m != 0) ez = mkc<C>((T)0, (T)0);
-        if (j == 0 && m != 1) ep = mkc<C>((T)0, (T)0);
-        Er[i] = er;
-        Ep[i] = ep;
-        Ez[i] = ez;
+    const QTab<T> q = tab[k];
+    const QB<T> b = qfaraday_at<T>(spec, fs, nz, nr, j, k, q.sp, dt, dr, m);
+    const C cr = csub(imr(b.z, mT / rh), cmul(q.sm, b.p));
+    C cp, cz;
+    if (j > 0) {
+        const QB<T> bd = qfaraday_at<T>(spec, fs, nz, nr, j - 1, k, q.sp, dt, dr, m);
+        cp = csub(cmul(q.sm, b.r), cscale(csub(b.z, bd.z), (T)1 / dr));
+        cz = csub(cscale(csub(cscale(b.p, rh), cscale(bd.p, rd)), (T)1 / (ri * dr)), imr(b.r, mT / ri));
+    } else {
+        cp = (m == 1) ? csub(cmul(q.sm, b.r), cscale(b.z, (T)2 / dr)) : mkc<C>((T)0, (T)0);
+        cz = (m == 0) ? cscale(b.p, (T)4 / dr) : mkc<C>((T)0, (T)0);
     }
+    C er = csub(cadd(Er[i], cscale(cr, dt)), cscale(Jr[i], q.cj));
+    C ep = csub(cadd(Ep[i], cscale(cp, dt)), cscale(Jp[i], q.cj));
+    C ez = csub(cadd(Ez[i], cscale(cz, dt)), cscale(Jz[i], q.cjz));
+    if (j == 0 && m != 0) ez = mkc<C>((T)0, (T)0);
+    if (j == 0 && m != 1) ep = mkc<C>((T)0, (T)0);
+    Jz[i] = ez;
+    Jr[i] = er;
+    Jp[i] = ep;
+    Bn[i] = b.z;
+    Bn[fs + i] = b.r;
+    Bn[2 * fs + i] = b.p;
 }
 
 template <typename T>
@@ -201,7 +207,7 @@ static hyb_status create_t(hyb_grid* g) {
     HYB_CUDA_TRY(cudaMemcpy(P->tab, tab.data(), sizeof(QTab<T>) * nz, cudaMemcpyHostToDevice));
     HYB_CUDA_TRY(cudaMalloc(&P->tw, sizeof(C) * nz));
     HYB_CUDA_TRY(cudaMemcpy(P->tw, tw.data(), sizeof(C) * nz, cudaMemcpyHostToDevice));
-    HYB_CUDA_TRY(cudaMalloc(&P->spec, sizeof(C) * 9 * (size_t)nr * nz));
+    HYB_CUDA_TRY(cudaMalloc(&P->spec, sizeof(C) * 12 * (size_t)nr * nz));
     const size_t smem = sizeof(C) * 2 * fpad_size((size_t)fft_rows_per_block(nz) * nz);
     HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -225,9 +231,8 @@ static hyb_status advance_t(hyb_grid* g, int nsteps) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
         k_qfft<T, false><<<gf, kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, 9, P->tw, RB);
         const dim3 mgrid((unsigned)((nz + kQThreads - 1) / kQThreads), (unsigned)nr);   // one thread per (mode, row)
-        k_qfaraday<T><<<mgrid, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
-        k_qampere<T><<<mgrid, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
-        k_qfft<T, true><<<gi, kQThreads, smem, g->stream>>>(fout, P->spec, nz, nr, 6, P->tw, RB);
+        k_qleap<T><<<mgrid, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
+        k_qfft<T, true><<<gi, kQThreads, smem, g->stream>>>(fout, P->spec + 6 * (int64_t)nr * nz, nz, nr, 6, P->tw, RB);
         HYB_CUDA_TRY(cudaGetLastError());
         if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
     }

@@ -100,6 +100,8 @@ def lib():
             L.hyb_batch_advance.restype = S
             L.hyb_batch_rows_per_strip.argtypes = [_V, ctypes.c_int]
             L.hyb_batch_rows_per_strip.restype = ctypes.c_int
+            L.hyb_batch_set_rows_per_strip.argtypes = [_V, ctypes.c_int, ctypes.c_int]
+            L.hyb_batch_set_rows_per_strip.restype = ctypes.c_int
             L.hyb_batch_launches_per_step.argtypes = [_V]
             L.hyb_batch_launches_per_step.restype = ctypes.c_int
             L.hyb_batch_destroy.argtypes = [_V]
@@ -255,6 +257,10 @@ def hyb_batch_rows_per_strip(b: int, n1: int) -> int:
     return lib().hyb_batch_rows_per_strip(_V(b), n1)
 
 
+def hyb_batch_set_rows_per_strip(b: int, n1: int, h: int) -> None:
+    _check(lib().hyb_batch_set_rows_per_strip(_V(b), n1, h))
+
+
 def hyb_batch_launches_per_step(b: int) -> int:
     return lib().hyb_batch_launches_per_step(_V(b))
 
@@ -390,6 +396,9 @@ class Batch:
 
     def advance(self, nsteps=1):
         hyb_batch_advance(self.h, nsteps)
+
+    def set_rows_per_strip(self, n1, h):
+        hyb_batch_set_rows_per_strip(self.h, n1, h)
 
     def rows_per_strip(self, n1):
         return hyb_batch_rows_per_strip(self.h, n1)
