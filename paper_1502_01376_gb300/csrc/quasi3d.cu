@@ -13,11 +13,13 @@
 // in one kernel, inverse FFT of the six advanced spectra.
 #include <math.h>
 
+#include <type_traits>
 #include <vector>
 
 #include <algorithm>
 
 #include "hyb_internal.cuh"
+#include "packed_dev.cuh"
 
 namespace hyb {
 
@@ -33,6 +35,7 @@ template <typename T>
 struct QPlan {
     QTab<T>* tab = nullptr;
     cplx<T>* tw = nullptr;    // stockham_twiddles(nz)
+    float2* tw2k = nullptr;   // stage twiddles of k_cfft2048 (FP32, nz = 2048 only)
     cplx<T>* spec = nullptr;  // [12][nr][nz]: E, B, J spectra, then the advanced B (E^{n+1} replaces J)
 };
 
@@ -100,6 +103,129 @@ __global__ void __launch_bounds__(kQThreads) k_qfft(QPtrs io, cplx<T>* __restric
             for (int q = threadIdx.x; q < nrow * nz; q += blockDim.x) X[q] = src[fpad(q)];
         }
     }
+}
+
+// ---------------------------------------------------------------- nz = 2048, FP32: register-resident rows
+// X[k] = sum_j x[j] W^{jk}, W = exp(-2 pi i / 2048), factored 8 x 8 x 8 x 4 with k = k1 + 8 k2 + 64 k3 + 512 k4:
+//   S1  thread t:            DFT8 over n of x[t + 256 n] -> k1, times W_2048^{t k1}      -> A(k1, t)
+//   S2  (t0, k1) = (t & 31, t >> 5):  DFT8 over t1 of A(k1, t0 + 32 t1) -> k2, times W_256^{t0 k2}
+//   S3  (u0, k1, k2) = (t & 3, (t >> 2) & 7, t >> 5):  DFT8 over u1 of A'(k1, k2, u0 + 4 u1) -> k3,
+//       times W_32^{u0 k3}
+//   S4  the 512 (k1, k2, k3) in two halves:  DFT4 over u0 -> k4, written to X[k1 + 8 k2 + 64 k3 + 512 k4]
+// Exchange layouts (float2 units): A(k1, t) at 256 k1 + t; A'(k1, k2, t0) at 260 k1 + 32 k2 + t0;
+// A''(k1, k2, k3, u0) at 516 u0 + 64 k3 + k1 + 8 k2 (in the A buffer).  With 8-byte accesses a half-warp
+// of every exchange reaches 16 different bank pairs; global loads and stores are row-contiguous per warp.
+// The inverse uses the conjugate twiddles and scales by 1/2048.  One row per 256-thread block
+// iteration; persistent, the next row's points held in registers while the current one is transformed.
+constexpr int kQ2k = 2048;
+constexpr int kQ2kA = 2064, kQ2kB = 2080;
+constexpr int kQ2kTw = 7 * 256 + 7 * 32 + 7 * 4;     // stage twiddles, in the order the threads read them
+
+template <bool INV>
+__device__ __forceinline__ float2 q2k_tw(float2 a, float2 w) {
+    return INV ? make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y))
+               : make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(256, 2) k_cfft2048(const __grid_constant__ QPtrs io, float2* __restrict__ spec, int nr, int nf,
+                                                     const float2* __restrict__ tw) {
+    __shared__ __align__(16) float2 bufA[kQ2kA];
+    __shared__ __align__(16) float2 bufB[kQ2kB];
+    const int t = threadIdx.x;
+    const int64_t total = (int64_t)nr * nf;
+    float2 w1[8], w2[8], w3[8], nx[8];
+#pragma unroll
+    for (int k = 1; k < 8; k++) {
+        w1[k] = tw[(k - 1) * 256 + t];
+        w2[k] = tw[1792 + (k - 1) * 32 + (t & 31)];
+        w3[k] = tw[2016 + (k - 1) * 4 + (t & 3)];
+    }
+    auto src_of = [&](int64_t j) -> const float2* {
+        const int f = (int)(j / nr);
+        const int64_t r = j - (int64_t)f * nr;
+        return INV ? spec + j * kQ2k : reinterpret_cast<const float2*>(io.p[f]) + r * kQ2k;
+    };
+    auto fetch = [&](int64_t j) {
+        const float2* x = src_of(j);
+#pragma unroll
+        for (int n = 0; n < 8; n++) nx[n] = __ldcs(x + t + 256 * n);
+    };
+    int64_t j = blockIdx.x;
+    if (j < total) fetch(j);
+    for (; j < total; j += gridDim.x) {
+        float2 v[8];
+#pragma unroll
+        for (int n = 0; n < 8; n++) v[n] = nx[n];
+        if (j + gridDim.x < total) fetch(j + gridDim.x);
+        // S1
+        dft8x<INV>(v);
+#pragma unroll
+        for (int k = 1; k < 8; k++) v[k] = q2k_tw<INV>(v[k], w1[k]);
+        __syncthreads();                 // the previous row's S4 has read the A buffer
+#pragma unroll
+        for (int k = 0; k < 8; k++) bufA[256 * k + t] = v[k];
+        __syncthreads();
+        // S2
+        {
+            const int t0 = t & 31, k1 = t >> 5;
+#pragma unroll
+            for (int n = 0; n < 8; n++) v[n] = bufA[256 * k1 + t0 + 32 * n];
+            dft8x<INV>(v);
+#pragma unroll
+            for (int k = 1; k < 8; k++) v[k] = q2k_tw<INV>(v[k], w2[k]);
+#pragma unroll
+            for (int k = 0; k < 8; k++) bufB[260 * k1 + 32 * k + t0] = v[k];
+        }
+        __syncthreads();
+        // S3
+        {
+            const int u0 = t & 3, k1 = (t >> 2) & 7, k2 = t >> 5;
+#pragma unroll
+            for (int n = 0; n < 8; n++) v[n] = bufB[260 * k1 + 32 * k2 + u0 + 4 * n];
+            dft8x<INV>(v);
+#pragma unroll
+            for (int k = 1; k < 8; k++) v[k] = q2k_tw<INV>(v[k], w3[k]);
+#pragma unroll
+            for (int k = 0; k < 8; k++) bufA[516 * u0 + 64 * k + k1 + 8 * k2] = v[k];
+        }
+        __syncthreads();
+        // S4
+        float2* X;
+        {
+            const int f = (int)(j / nr);
+            const int64_t r = j - (int64_t)f * nr;
+            X = INV ? reinterpret_cast<float2*>(io.p[f]) + r * kQ2k : spec + j * kQ2k;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int it = t + 256 * h;      // k1 + 8 k2 + 64 k3
+            float2 a0 = bufA[it], a1 = bufA[516 + it], a2 = bufA[1032 + it], a3 = bufA[1548 + it];
+            dft4x<INV>(a0, a1, a2, a3);
+            if (INV) {
+                const float s = 1.0f / (float)kQ2k;
+                a0 = vmul(a0, make_float2(s, s)); a1 = vmul(a1, make_float2(s, s));
+                a2 = vmul(a2, make_float2(s, s)); a3 = vmul(a3, make_float2(s, s));
+            }
+            __stcs(X + it, a0);
+            __stcs(X + it + 512, a1);
+            __stcs(X + it + 1024, a2);
+            __stcs(X + it + 1536, a3);
+        }
+    }
+}
+
+// stage twiddles of k_cfft2048, W_N^e = exp(-2 pi i e / N), in the order above
+static std::vector<float2> cfft2048_twiddles() {
+    std::vector<float2> w(kQ2kTw);
+    const double pi = 3.14159265358979323846;
+    auto W = [&](int e, int N) { const double a = 2.0 * pi * e / N; return make_float2((float)cos(a), (float)-sin(a)); };
+    for (int k = 1; k < 8; k++) {
+        for (int t = 0; t < 256; t++) w[(k - 1) * 256 + t] = W(t * k, 2048);
+        for (int t = 0; t < 32; t++) w[1792 + (k - 1) * 32 + t] = W(t * k, 256);
+        for (int t = 0; t < 4; t++) w[2016 + (k - 1) * 4 + t] = W(t * k, 32);
+    }
+    return w;
 }
 
 template <typename T>
@@ -208,6 +334,11 @@ static hyb_status create_t(hyb_grid* g) {
     HYB_CUDA_TRY(cudaMalloc(&P->tw, sizeof(C) * nz));
     HYB_CUDA_TRY(cudaMemcpy(P->tw, tw.data(), sizeof(C) * nz, cudaMemcpyHostToDevice));
     HYB_CUDA_TRY(cudaMalloc(&P->spec, sizeof(C) * 12 * (size_t)nr * nz));
+    if (std::is_same<T, float>::value && nz == kQ2k) {
+        const std::vector<float2> w2k = cfft2048_twiddles();
+        HYB_CUDA_TRY(cudaMalloc(&P->tw2k, sizeof(float2) * w2k.size()));
+        HYB_CUDA_TRY(cudaMemcpy(P->tw2k, w2k.data(), sizeof(float2) * w2k.size(), cudaMemcpyHostToDevice));
+    }
     const size_t smem = sizeof(C) * 2 * fpad_size((size_t)fft_rows_per_block(nz) * nz);
     HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     HYB_CUDA_TRY(cudaFuncSetAttribute(k_qfft<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -229,10 +360,22 @@ static hyb_status advance_t(hyb_grid* g, int nsteps) {
     const int gi = std::min(6 * nblk, resident_grid((const void*)k_qfft<T, true>, kQThreads, smem));
     for (int s = 0; s < nsteps; s++) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
-        k_qfft<T, false><<<gf, kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, 9, P->tw, RB);
+        if (P->tw2k) {
+            static const int res = resident_grid((const void*)k_cfft2048<false>, 256, 0);
+            k_cfft2048<false><<<(unsigned)std::min<int64_t>(res, 9 * (int64_t)nr), 256, 0, g->stream>>>(
+                fin, reinterpret_cast<float2*>(P->spec), nr, 9, P->tw2k);
+        } else {
+            k_qfft<T, false><<<gf, kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, 9, P->tw, RB);
+        }
         const dim3 mgrid((unsigned)((nz + kQThreads - 1) / kQThreads), (unsigned)nr);   // one thread per (mode, row)
         k_qleap<T><<<mgrid, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
-        k_qfft<T, true><<<gi, kQThreads, smem, g->stream>>>(fout, P->spec + 6 * (int64_t)nr * nz, nz, nr, 6, P->tw, RB);
+        if (P->tw2k) {
+            static const int res = resident_grid((const void*)k_cfft2048<true>, 256, 0);
+            k_cfft2048<true><<<(unsigned)std::min<int64_t>(res, 6 * (int64_t)nr), 256, 0, g->stream>>>(
+                fout, reinterpret_cast<float2*>(P->spec + 6 * (int64_t)nr * nz), nr, 6, P->tw2k);
+        } else {
+            k_qfft<T, true><<<gi, kQThreads, smem, g->stream>>>(fout, P->spec + 6 * (int64_t)nr * nz, nz, nr, 6, P->tw, RB);
+        }
         HYB_CUDA_TRY(cudaGetLastError());
         if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
     }
@@ -247,10 +390,10 @@ void quasi3d_destroy(hyb_grid* g) {
     if (!g->qtab) return;
     if (g->d.precision == 32) {
         QPlan<float>* P = reinterpret_cast<QPlan<float>*>(g->qtab);
-        cudaFree(P->tab); cudaFree(P->tw); cudaFree(P->spec); delete P;
+        cudaFree(P->tab); cudaFree(P->tw); cudaFree(P->tw2k); cudaFree(P->spec); delete P;
     } else {
         QPlan<double>* P = reinterpret_cast<QPlan<double>*>(g->qtab);
-        cudaFree(P->tab); cudaFree(P->tw); cudaFree(P->spec); delete P;
+        cudaFree(P->tab); cudaFree(P->tw); cudaFree(P->tw2k); cudaFree(P->spec); delete P;
     }
     g->qtab = nullptr;
 }
