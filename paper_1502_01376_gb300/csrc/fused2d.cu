@@ -476,8 +476,6 @@ size_t fused_smem_bytes(int n1) {
     }
 }
 
-int fused_threads(int n1) { return n1 == 4096 ? 768 : 3 * (n1 / 32); }
-
 template <int N>
 static cudaError_t fused_attr(int* occ) {
     const size_t smem = fused_smem<N>();

@@ -61,7 +61,6 @@ size_t fused_tm_smem_bytes();
 cudaError_t fused_tm_occupancy(int* occ);
 cudaError_t fused_tm_launch(const FusedBatch& fb, int grid, cudaStream_t s);
 cudaError_t wait_probe(int* dflag, int* derr, long long limit, int which, cudaStream_t s);
-int fused_threads(int n1);
 cudaError_t fused_occupancy(int n1, int* occ);
 cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
 // the fused kernel alone (halo buffer already filled, or flag mode)

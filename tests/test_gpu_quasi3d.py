@@ -51,7 +51,7 @@ def test_quasi3d_matches_oracle(m, prec):
 
 
 @pytest.mark.parametrize("prec", [64, 32])
-@pytest.mark.parametrize("nz,nr", [(16, 5), (2048, 9), (4096, 3)])
+@pytest.mark.parametrize("nz,nr", [(16, 5), (2048, 2), (2048, 9), (4096, 3)])
 def test_quasi3d_row_lengths(nz, nr, prec):
     """Short rows (many rows per block), the batched workload's z length (one row per block, next
     block prefetched) and rows longer than the prefetch holds (direct loads)."""
@@ -86,4 +86,28 @@ def test_quasi3d_in_batch_with_2d_grids():
     for a, c in zip(Eq + Bq, Et + Bt):
         assert torch.equal(a, c)
     b.close()
+    grid.close()
+
+
+@pytest.mark.parametrize("m", [0, 1, 2])
+def test_quasi3d_batched_workload_size(m):
+    """The batched benchmark's quasi-3D modes at full size (nz x nr = 2048 x 512, FP32, dz = dr = 0.2,
+    filtered): every output element against the oracle after two steps."""
+    need_gpu()
+    hyb = hyb_module()
+    nz, nr, dz = 2048, 512, 0.2
+    dt = min(0.08, 0.9 * 2 / np.sqrt(np.pi ** 2 / dz ** 2 + (4 * m * m + 6) / dz ** 2))
+    g = q.QGrid(nz=nz, nr=nr, dz=dz, dr=dz, dt=dt, m=m, filt_kc=0.5, filt_w=0.2)
+    E, B, J = _fields(nr, nz, 500 + m), _fields(nr, nz, 600 + m), _fields(nr, nz, 700 + m, 1e-2)
+    rnd = lambda a: a.astype(np.complex64).astype(np.complex128)
+    Eo, Bo, Jo = [rnd(a) for a in E], [rnd(a) for a in B], [rnd(a) for a in J]
+    desc = hyb.make_desc(dims=20, n1=nz, n2=nr, dx1=dz, dx2=dz, dt=dt, precision=32, filt_kc=0.5, filt_w=0.2,
+                         azimuthal_m=m)
+    grid = hyb.Grid(desc)
+    Et, Bt, Jt = ([torch.from_numpy(a).to("cuda", torch.complex64) for a in X] for X in (E, B, J))
+    grid.bind(Et, Bt, Jt)
+    q.step(g, Eo, Bo, Jo, 2)
+    grid.advance(2)
+    for a, b in zip(Et + Bt, Eo + Bo):
+        assert rel_err(a.cpu().numpy().view(np.float32).astype(np.float64), b.view(np.float64)) < TOL[32]
     grid.close()
