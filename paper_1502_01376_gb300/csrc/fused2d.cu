@@ -688,7 +688,7 @@ static hyb_status hp_plan(hyb_grid* g) {
     if (P->hp_chunks) return HYB_OK;
     hp_release(P);                                 // whatever an earlier, failed plan left
     const int n2 = g->d.n2;
-    const int C = std::max(1, std::min(8, n2 / 8));
+    const int C = std::max(1, std::min(4, n2 / 8));
     std::vector<int4> items;
     P->hp_first.assign(1, 0);
     P->hp_row0.assign(1, 0);
@@ -748,32 +748,36 @@ hyb_status fused_host_advance(hyb_grid* g, void* const E[3], void* const B[3], v
     HYB_CUDA_TRY(fused_occupancy(n1, &occ));
     HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
     const int last = P->hp_first[C] - 1;                   // the strip that ends at row n2 (wraps to row 0)
+    // chunk ch's rows of all nine arrays, plus the first row of chunk ch + 1 for E1 and E3 (the
+    // upper halo of the chunk's last strip), so that compute ch waits for its own copy only
     auto copy_in = [&](int ch) -> cudaError_t {
         for (int k = 0; k < 3; k++)
             for (int c = 0; c < 3; c++) {
-                cudaError_t e = rows_copy(k, c, P->hp_row0[ch], P->hp_row0[ch + 1], cudaMemcpyHostToDevice, in);
+                const int extra = (k == 0 && c != 1 && ch + 1 < C) ? 1 : 0;
+                cudaError_t e = rows_copy(k, c, P->hp_row0[ch], P->hp_row0[ch + 1] + extra, cudaMemcpyHostToDevice, in);
                 if (e != cudaSuccess) return e;
             }
         return cudaEventRecord(ev_in(ch), in);
     };
     HYB_CUDA_TRY(cudaEventRecord(fork, g->stream));
     for (cudaStream_t q : P->hp_s) HYB_CUDA_TRY(cudaStreamWaitEvent(q, fork, 0));
-    // enqueued chunk by chunk so that each stream gets work as early as possible:
-    // copy in the last row, chunks 0 and 1; then per chunk c: copy in c + 2, compute c, copy out c
+    // the copy-in stream runs ahead chunk by chunk; compute ch waits for copy ch, copy-out ch for compute ch.
+    // Halo rows are taken into the halo buffer before the chunk that holds them is updated.
     for (int k = 0; k < 3; k++)
         for (int c = 0; c < 3; c++) HYB_CUDA_TRY(rows_copy(k, c, n2 - 1, n2, cudaMemcpyHostToDevice, in));
     HYB_CUDA_TRY(copy_in(0));
-    if (C > 1) HYB_CUDA_TRY(copy_in(1));
     HYB_CUDA_TRY(cudaStreamWaitEvent(cmp, ev_in(0), 0));
-    if (C > 1) HYB_CUDA_TRY(cudaStreamWaitEvent(cmp, ev_in(1), 0));
     HYB_CUDA_TRY(halo_parts(n1, sub(last, last + 1), 5, 2, cmp));          // row 0, before chunk 0 runs
     HYB_CUDA_TRY(halo_parts(n1, sub(P->hp_first[0], P->hp_first[1]), 0, 5, cmp));
     for (int ch = 0; ch < C; ch++) {
-        if (ch + 2 < C) HYB_CUDA_TRY(copy_in(ch + 2));
-        if (ch + 1 < C) HYB_CUDA_TRY(cudaStreamWaitEvent(cmp, ev_in(ch + 1), 0));
+        if (ch + 1 < C) HYB_CUDA_TRY(copy_in(ch + 1));
         const int i0 = P->hp_first[ch], i1 = P->hp_first[ch + 1];
+        if (ch > 0) {
+            HYB_CUDA_TRY(cudaStreamWaitEvent(cmp, ev_in(ch), 0));
+            HYB_CUDA_TRY(halo_parts(n1, sub(i0 + 1, i1), 0, 5, cmp));      // lower halos inside chunk ch
+        }
         HYB_CUDA_TRY(halo_parts(n1, sub(i0, ch + 1 == C ? i1 - 1 : i1), 5, 2, cmp));
-        if (ch + 1 < C) HYB_CUDA_TRY(halo_parts(n1, sub(i1, P->hp_first[ch + 2]), 0, 5, cmp));
+        if (ch + 1 < C) HYB_CUDA_TRY(halo_parts(n1, sub(i1, i1 + 1), 0, 5, cmp));   // row r1 - 1, for chunk ch + 1
         const FusedBatch b = sub(i0, i1);
         HYB_CUDA_TRY(fused_kernel_launch(n1, b, std::min(b.n_items, sms * occ), cmp));
         HYB_CUDA_TRY(cudaEventRecord(ev_cmp(ch), cmp));
