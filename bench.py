@@ -50,15 +50,18 @@ def parse():
                          "benchmark; others show the n1 = 512 .. 2048 kernels and the three-pass path)")
     ap.add_argument("--batch-strips", default="",
                     help="batched workload: rows per strip per n1 as '512:3,1024:2,...' instead of the autotuner")
+    ap.add_argument("--ppc", type=int, default=8,
+                    help="push workload: particles per cell per species (8 is the benchmark; fewer for profiling)")
     ap.add_argument("--rows3d", type=int, default=256,
                     help="3d workload: n2 = n3 = this (256 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--workload", default="drift_plasma",
-                    choices=["drift_plasma", "batched", "3d", "vacuum_beam", "x1_sweep", "surrogate"],
+                    choices=["drift_plasma", "batched", "3d", "vacuum_beam", "x1_sweep", "surrogate", "push"],
                     help="drift_plasma (default, the headline): 2D 4096 x 1024 FP32; batched: 16 uneven 2D grids "
                          "+ quasi-3D modes m = 0, 1, 2 (2048 x 512 complex) in one CUDA-graph step; 3d: 1024 x 256 x 256 "
                          "FP32, radix FFT vs DFT-GEMM x1 transform; vacuum_beam: 2D 128 x 64 FP64; x1_sweep: both x1 "
                          "transforms for n1 = 16 .. 1024 at 2^25 cells; surrogate: NCI surrogate trained on 200k "
-                         "root-solver samples, then the pick of cutoff and dt judged by the solver")
+                         "root-solver samples, then the pick of cutoff and dt judged by the solver; push: field gather "
+                         "and Boris push of the drifting plasma's 67 M particles")
     return ap.parse_args()
 
 
@@ -351,6 +354,74 @@ def run_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+def run_push(args):
+    """The particle step that feeds the deposit (field gather with momentum-conserving
+    interpolation, relativistic Boris push) on the drifting-plasma grid: 8 + 8 particles
+    per cell (67 M), quadratic shapes, band-limited random E and B; each step pushes
+    every particle once and its x^{n+1} offsets become the next step's x^n."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_1502_01376_gb300 import build, hyb, workloads as wl
+    build.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.5)
+    peak, src = peaks()
+    w = wl.DRIFT_PLASMA.scaled(ppc=args.ppc)
+    E0, B0 = wl.band_limited_fields(w)
+    fields = [a.astype(np.float32) for a in list(E0) + list(B0)]
+    g = hyb.Grid(hyb.desc_from_workload(w), stream)
+    E = [torch.from_numpy(f).to(dev) for f in fields[:3]]
+    B = [torch.from_numpy(f).to(dev) for f in fields[3:]]
+    J = [torch.zeros(w.shape, device=dev) for _ in range(3)]
+    g.bind(E, B, J)
+    cell, off, u, qm = wl.plasma_push_particles_torch(w, dev)
+    n = qm.numel()
+    buf = [off, torch.empty_like(off)]
+    v3 = torch.empty_like(qm)
+    state = {"i": 0}
+
+    def step():
+        a, b = buf[state["i"]], buf[1 - state["i"]]
+        g.push(cell, a, u, qm, b, v3, order=w.shape_order)
+        state["i"] = 1 - state["i"]
+
+    ms = time_steps(step, args.steps, args.warmup, stream, flush, sampler)
+    g.check()
+    sampler.stop()
+    per_particle = 2 * 4 + 2 * 4 + 3 * 4 + 4 + 2 * 4 + 2 * 4 + 3 * 4 + 2 * 4 + 4     # read cell, off, u, q/m; write cell, off, u, off_new, v3
+    alg_bytes = per_particle * n + 6 * 4 * w.cells
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    line = {"metric": "particle pushes/s (field gather, momentum-conserving quadratic shapes, relativistic Boris) on 1 GB300",
+            "value": n / (ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": src, "kernel": "k_push2d<float, 2>",
+                         "bytes_per_launch": alg_bytes,
+                         "bytes_per_unit": f"{per_particle} B per particle + 24 B per cell of fields"},
+            "gpu_launches": args.steps, "clocks": sampler.summary(),
+            "config": {"workload": f"drift_plasma_2d_4096x1024_push_{w.ppc}+{w.ppc}ppc_f32", "particles": n, "shape_order": w.shape_order,
+                       "fields": "band-limited random E, B", "order": "particles stored in cell order",
+                       "l2": "flushed between timed steps (256 MB write)"}}
+    if not args.no_extras:
+        from oracle import push as P
+        k = 200000
+        sel = torch.from_numpy(np.random.default_rng(1).choice(n, k, replace=False)).to(dev)
+        ins = [t[sel].cpu().numpy() for t in (cell, buf[state["i"]], u, qm)]
+        t0 = time.perf_counter()
+        P.push(fields, ins[0], ins[1], ins[2], ins[3], w.dt, np.array([w.dx1, w.dx2]), w.shape_order)
+        cpu_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": k / cpu_s, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{k} particles of the workload, one oracle push ({cpu_s:.1f} s, numpy)"}
+    g.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_other(args):
     """Measurement lines for the non-headline configurations (same JSON keys)."""
     import numpy as np
@@ -485,6 +556,8 @@ def main():
         return run_reference(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "push":
+        return run_push(args)
     if args.workload != "drift_plasma":
         return run_other(args)
     import numpy as np

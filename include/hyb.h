@@ -119,6 +119,35 @@ HYB_API hyb_status hyb_bind_fields(hyb_grid* g, void* const E[3], void* const B[
 HYB_API hyb_status hyb_deposit(hyb_grid* g, const int32_t* cell, const void* off_old, const void* off_new,
                        const void* v3, const void* q, int64_t np, int shape_order);
 
+/* Field gather and relativistic Boris push of np particles, the step that feeds
+ * hyb_deposit.  Gather: the momentum-conserving interpolation of the Appendix
+ * (Eqs. for S_E and S_B): each component of E and B is interpolated with the
+ * order-l shape s_l along every axis, from its own staggered grid (2D: E1 at
+ * (i1+1/2, i2), E2 (i1, i2+1/2), E3 (i1, i2), B1 (i1, i2+1/2), B2 (i1+1/2, i2),
+ * B3 (i1+1/2, i2+1/2); 3D as in the 3D Yee cell).  Push (c = 1, Gaussian units,
+ * u = gamma v): the Boris rotation, h = (q/m) dt/2,
+ *   u- = u + h E;  t = h B / gamma(u-);  s = 2 t / (1 + t.t);
+ *   u+ = u- + (u- + u- x t) x s;  u^{n+1/2} = u+ + h E;
+ *   x^{n+1} = x^n + dt u^{n+1/2} / gamma(u^{n+1/2}).
+ * E and B are read from the bound arrays, which the caller holds at the
+ * particles' time level n (E^n and, e.g., the mean of B^{n-1/2} and B^{n+1/2}).
+ *   cell    int32 [np][dims] in/out: the cell the offsets refer to (0 <= c < n);
+ *   off     real  [np][dims] in/out: x^n - cell in cell units, in [-1, 2) on entry
+ *           (a previous step's off_new); the call first moves each particle to
+ *           the cell that holds it (periodic), so that on exit 0 <= off < 1;
+ *   u       real  [np][3] in/out: u^{n-1/2} on entry, u^{n+1/2} on exit;
+ *   qm      real  [np]: charge-to-mass ratio q/m;
+ *   off_new real  [np][dims] out: x^{n+1} - cell (cell units), hyb_deposit's off_new;
+ *   v3      real  [np] out, nullable, 2D only: u3/gamma, hyb_deposit's v3;
+ *   shape_order 1, 2 or 3.
+ * Real arrays are of the grid's precision, device resident; fields periodic.
+ * 2D: cell, off and off_new must be aligned to one particle's pair (8 bytes,
+ * 2 reals), else HYB_EALIGN.
+ * Particles with a cell out of range or an offset outside [-1, 2) are left
+ * unchanged (off_new = off) and flagged (hyb_check -> HYB_EDATA). */
+HYB_API hyb_status hyb_push(hyb_grid* g, int32_t* cell, void* off, void* u, const void* qm, void* off_new, void* v3,
+                            int64_t np, int shape_order);
+
 /* Eq. currentcorrection alone, in place on the bound J1:
  * j1 <- IFFT_x1[ sin(k1 dx1/2)/(k1 dx1/2) FFT_x1[j1] ]. */
 HYB_API hyb_status hyb_correct_current(hyb_grid* g);

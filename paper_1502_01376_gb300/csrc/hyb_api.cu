@@ -275,6 +275,23 @@ hyb_status hyb_deposit(hyb_grid* g, const int32_t* cell, const void* off_old, co
     return deposit<double>(g, cell, (const double*)off_old, (const double*)off_new, (const double*)v3, (const double*)q, np, shape_order);
 }
 
+hyb_status hyb_push(hyb_grid* g, int32_t* cell, void* off, void* u, const void* qm, void* off_new, void* v3,
+                    int64_t np, int shape_order) {
+    if (!g) { set_error("null grid"); return HYB_EINVAL; }
+    if (!g->bound) { set_error("hyb_push: fields not bound"); return HYB_ESTATE; }
+    if (np < 0 || shape_order < 1 || shape_order > 3) { set_error("hyb_push: bad np or shape_order"); return HYB_EINVAL; }
+    if (np > 0 && (!cell || !off || !u || !qm || !off_new)) { set_error("hyb_push: null particle array"); return HYB_EINVAL; }
+    if (g->d.dims == 20) { set_error("hyb_push: quasi-3D grids carry no particles"); return HYB_EINVAL; }
+    const size_t real = g->d.precision == 32 ? 4 : 8;
+    if (g->d.dims == 2 && ((uintptr_t)cell % 8 || (uintptr_t)off % (2 * real) || (uintptr_t)off_new % (2 * real))) {
+        set_error("hyb_push: 2D cell (8 bytes) and off, off_new (2 reals) must be aligned to one particle's pair");
+        return HYB_EALIGN;
+    }
+    if (g->d.precision == 32)
+        return push<float>(g, cell, (float*)off, (float*)u, (const float*)qm, (float*)off_new, (float*)v3, np, shape_order);
+    return push<double>(g, cell, (double*)off, (double*)u, (const double*)qm, (double*)off_new, (double*)v3, np, shape_order);
+}
+
 hyb_status hyb_correct_current(hyb_grid* g) {
     if (!g) { set_error("null grid"); return HYB_EINVAL; }
     if (!g->bound) { set_error("fields not bound"); return HYB_ESTATE; }

@@ -292,6 +292,10 @@ template <typename T>
 hyb_status deposit(hyb_grid* g, const int32_t* cell, const T* off_old, const T* off_new, const T* v3,
                    const T* q, int64_t np, int order);
 
+// field gather and Boris push (push.cu)
+template <typename T>
+hyb_status push(hyb_grid* g, int32_t* cell, T* off, T* u, const T* qm, T* off_new, T* v3, int64_t np, int order);
+
 // diagnostics (diag.cu)
 template <typename T> hyb_status diag(hyb_grid* g, double out[9]);
 

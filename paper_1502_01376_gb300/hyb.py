@@ -75,6 +75,8 @@ def lib():
             L.hyb_bind_fields.restype = S
             L.hyb_deposit.argtypes = [_V, _V, _V, _V, _V, _V, ctypes.c_int64, ctypes.c_int]
             L.hyb_deposit.restype = S
+            L.hyb_push.argtypes = [_V, _V, _V, _V, _V, _V, _V, ctypes.c_int64, ctypes.c_int]
+            L.hyb_push.restype = S
             for fn in ("hyb_correct_current", "hyb_filter", "hyb_check", "hyb_destroy_grid"):
                 getattr(L, fn).argtypes = [_V]
                 getattr(L, fn).restype = S
@@ -175,6 +177,10 @@ def hyb_bind_fields(g: int, E, B, J, rho=0):
 
 def hyb_deposit(g: int, cell: int, off_old: int, off_new: int, v3: int, q: int, np_: int, order: int):
     _check(lib().hyb_deposit(_V(g), _V(cell), _V(off_old), _V(off_new), _V(v3 or 0), _V(q), np_, order))
+
+
+def hyb_push(g: int, cell: int, off: int, u: int, qm: int, off_new: int, v3: int, np_: int, order: int):
+    _check(lib().hyb_push(_V(g), _V(cell), _V(off), _V(u), _V(qm), _V(off_new), _V(v3 or 0), np_, order))
 
 
 def hyb_correct_current(g: int):
@@ -331,6 +337,10 @@ class Grid:
     def deposit(self, cell, off_old, off_new, v3, q, order):
         n = q.numel()
         hyb_deposit(self.h, _ptr(cell), _ptr(off_old), _ptr(off_new), _ptr(v3), _ptr(q), n, order)
+
+    def push(self, cell, off, u, qm, off_new, v3=None, order=2):
+        """Gather and Boris push (hyb_push): cell, off, u updated in place; off_new (and v3) written."""
+        hyb_push(self.h, _ptr(cell), _ptr(off), _ptr(u), _ptr(qm), _ptr(off_new), _ptr(v3), qm.numel(), order)
 
     def correct_current(self):
         hyb_correct_current(self.h)

@@ -218,3 +218,33 @@ def plasma_move_torch(w: Workload, device, seed: int | None = None, step: int = 
         del x, v, c, o0, o1
     return (torch.cat(cells).contiguous(), torch.cat(off0s).contiguous(), torch.cat(off1s).contiguous(),
             torch.cat(v3s).contiguous(), torch.cat(qs).contiguous())
+
+
+def plasma_push_particles_torch(w: Workload, device, seed: int | None = None):
+    """Both species of the drifting plasma for the particle push, drawn on a CUDA
+    device (seeded torch generator), w.ppc per cell per species, stored in cell
+    order (as a PIC code keeps them sorted): int32 cell [np, dims], float32
+    offsets in [0, 1) [np, dims], float32 u = gamma v [np, 3] (drift gamma along
+    x1 plus a Gaussian spread u_th), float32 q/m = -1 (electrons) or +1 [np]."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(w.seed + 3000 if seed is None else seed)
+    d = w.dims
+    n = w.cells * w.ppc
+    idx = torch.arange(w.cells, device=device, dtype=torch.int64).repeat_interleave(w.ppc)
+    if d == 2:
+        cell = torch.stack([idx % w.n1, idx // w.n1], dim=1)
+    else:
+        cell = torch.stack([idx % w.n1, (idx // w.n1) % w.n2, idx // (w.n1 * w.n2)], dim=1)
+    cell = cell.to(torch.int32)
+    del idx
+    cells, offs, us, qms = [], [], [], []
+    for sign in (-1.0, +1.0):
+        cells.append(cell)
+        offs.append(torch.rand(n, d, generator=gen, device=device, dtype=torch.float32))
+        u = torch.randn(n, 3, generator=gen, device=device, dtype=torch.float32) * w.u_th
+        u[:, 0] += float(np.sqrt(w.gamma ** 2 - 1.0))
+        us.append(u)
+        qms.append(torch.full((n,), sign, device=device, dtype=torch.float32))
+    return (torch.cat(cells).contiguous(), torch.cat(offs).contiguous(), torch.cat(us).contiguous(),
+            torch.cat(qms).contiguous())
