@@ -100,9 +100,20 @@ __global__ void __launch_bounds__(256, 3) k_push2d(PushFields F, int n1, int n2,
     const T* E1 = (const T*)F.E[0]; const T* E2 = (const T*)F.E[1]; const T* E3 = (const T*)F.E[2];
     const T* B1 = (const T*)F.B[0]; const T* B2 = (const T*)F.B[1]; const T* B3 = (const T*)F.B[2];
     using V2 = cplx<T>;                      // a particle's two offsets, one 8- or 16-byte access
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-        const int2 cc = reinterpret_cast<const int2*>(cell)[p];
-        const V2 oo = reinterpret_cast<const V2*>(off)[p];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // the next particle's cell and offsets are loaded while this one is gathered and pushed
+    int2 ncc = make_int2(0, 0);
+    V2 noo;
+    noo.x = noo.y = (T)0;
+    if (p < np) { ncc = reinterpret_cast<const int2*>(cell)[p]; noo = reinterpret_cast<const V2*>(off)[p]; }
+    for (; p < np; p += stride) {
+        const int2 cc = ncc;
+        const V2 oo = noo;
+        if (p + stride < np) {
+            ncc = reinterpret_cast<const int2*>(cell)[p + stride];
+            noo = reinterpret_cast<const V2*>(off)[p + stride];
+        }
         int cx = cc.x, cy = cc.y;
         T ox = oo.x, oy = oo.y;
         T uu[3] = {u[3 * p], u[3 * p + 1], u[3 * p + 2]};
