@@ -10,6 +10,8 @@
 // Push (c = 1, u = gamma v): u- = u + h E, t = h B / gamma(u-), s = 2 t / (1 + t.t),
 // u' = u- + u- x t, u+ = u- + u' x s, u_new = u+ + h E with h = (q/m) dt / 2, then
 // x_new = x + dt u_new / gamma(u_new).  One thread per particle.
+#include <climits>
+
 #include "hyb_internal.cuh"
 
 namespace hyb {
@@ -92,22 +94,38 @@ __device__ __forceinline__ void boris(T (&u)[3], const T (&E)[3], const T (&B)[3
 
 struct PushFields { const void* E[3]; const void* B[3]; };
 
+// The block's particles are usually neighbours (a PIC code keeps them sorted by cell): the block
+// takes the bounding box of their cells, and when the box widened by the stencil reach (2 points
+// each side, every order and staggering) fits the shared tile, it stages the six components there
+// with row-contiguous loads and gathers from the tile; otherwise every particle gathers from global
+// memory.  Both paths take the same weights and points.
+constexpr int kPushThreads = 256;
+constexpr int kReach = 2;
+
 template <typename T, int L>
-__global__ void __launch_bounds__(256, 3) k_push2d(PushFields F, int n1, int n2, int32_t* __restrict__ cell,
-                                               T* __restrict__ off, T* __restrict__ u, const T* __restrict__ qm,
-                                               T* __restrict__ off_new, T* __restrict__ v3, int64_t np, T hdt,
-                                               T s1, T s2, int* __restrict__ flag) {
-    const T* E1 = (const T*)F.E[0]; const T* E2 = (const T*)F.E[1]; const T* E3 = (const T*)F.E[2];
-    const T* B1 = (const T*)F.B[0]; const T* B2 = (const T*)F.B[1]; const T* B3 = (const T*)F.B[2];
+__global__ void __launch_bounds__(kPushThreads, 3) k_push2d(PushFields F, int n1, int n2, int32_t* __restrict__ cell,
+                                                          T* __restrict__ off, T* __restrict__ u, const T* __restrict__ qm,
+                                                          T* __restrict__ off_new, T* __restrict__ v3, int64_t np, T hdt,
+                                                          T s1, T s2, int* __restrict__ flag) {
+    constexpr int kTile = sizeof(T) == 4 ? 1024 : 512;        // points per component in the shared tile
+    __shared__ T tile[6][kTile];
+    __shared__ int red[kPushThreads / 32][4];
+    const T* src[6] = {(const T*)F.E[0], (const T*)F.E[1], (const T*)F.E[2],
+                       (const T*)F.B[0], (const T*)F.B[1], (const T*)F.B[2]};
     using V2 = cplx<T>;                      // a particle's two offsets, one 8- or 16-byte access
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * kPushThreads;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // the next particle's cell and offsets are loaded while this one is gathered and pushed
     int2 ncc = make_int2(0, 0);
     V2 noo;
     noo.x = noo.y = (T)0;
-    if (p < np) { ncc = reinterpret_cast<const int2*>(cell)[p]; noo = reinterpret_cast<const V2*>(off)[p]; }
-    for (; p < np; p += stride) {
+    {
+        const int64_t p = blockIdx.x * (int64_t)kPushThreads + threadIdx.x;
+        if (p < np) { ncc = reinterpret_cast<const int2*>(cell)[p]; noo = reinterpret_cast<const V2*>(off)[p]; }
+    }
+    for (int64_t base = blockIdx.x * (int64_t)kPushThreads; base < np; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        const bool live = p < np;
         const int2 cc = ncc;
         const V2 oo = noo;
         if (p + stride < np) {
@@ -116,50 +134,96 @@ __global__ void __launch_bounds__(256, 3) k_push2d(PushFields F, int n1, int n2,
         }
         int cx = cc.x, cy = cc.y;
         T ox = oo.x, oy = oo.y;
-        T uu[3] = {u[3 * p], u[3 * p + 1], u[3 * p + 2]};
-        if (cx < 0 || cx >= n1 || cy < 0 || cy >= n2 || !renormalise(cx, ox, n1) || !renormalise(cy, oy, n2)) {
+        const bool ok = live && cx >= 0 && cx < n1 && cy >= 0 && cy < n2 && renormalise(cx, ox, n1) &&
+                        renormalise(cy, oy, n2);
+        if (live && !ok) {
             atomicOr(flag, 1);
             reinterpret_cast<V2*>(off_new)[p] = oo;
             if (v3) v3[p] = (T)0;
-            continue;
         }
-        // weights for the integer (0) and half (1) positions along each axis
-        T wx[2][L + 1], wy[2][L + 1];
-        const int ix0 = pweights<L>(ox, wx[0]), ix1 = pweights<L>(ox - (T)0.5, wx[1]);
-        const int iy0 = pweights<L>(oy, wy[0]), iy1 = pweights<L>(oy - (T)0.5, wy[1]);
-        int cx0[L + 1], cx1[L + 1];
+        // bounding box of the block's cells
+        int bx0 = __reduce_min_sync(0xffffffffu, ok ? cx : INT_MAX), bx1 = __reduce_max_sync(0xffffffffu, ok ? cx : INT_MIN);
+        int by0 = __reduce_min_sync(0xffffffffu, ok ? cy : INT_MAX), by1 = __reduce_max_sync(0xffffffffu, ok ? cy : INT_MIN);
+        if (lane == 0) { red[warp][0] = bx0; red[warp][1] = bx1; red[warp][2] = by0; red[warp][3] = by1; }
+        __syncthreads();
 #pragma unroll
-        for (int k = 0; k <= L; k++) { cx0[k] = pwrap(cx + ix0 + k, n1); cx1[k] = pwrap(cx + ix1 + k, n1); }
-        T e1 = 0, e2 = 0, e3 = 0, b1 = 0, b2 = 0, b3 = 0;
+        for (int w = 0; w < kPushThreads / 32; w++) {
+            bx0 = min(bx0, red[w][0]); bx1 = max(bx1, red[w][1]);
+            by0 = min(by0, red[w][2]); by1 = max(by1, red[w][3]);
+        }
+        const bool any = bx0 <= bx1;
+        const int W = any ? bx1 - bx0 + 1 + 2 * kReach : 0, H = any ? by1 - by0 + 1 + 2 * kReach : 0;
+        const bool tiled = any && W <= kTile && H <= kTile && W * H <= kTile;
+        const int tx0 = bx0 - kReach, ty0 = by0 - kReach;
+        if (tiled) {
+            for (int q = threadIdx.x; q < W * H; q += kPushThreads) {
+                const int yy = q / W, xx = q - yy * W;
+                const int64_t gq = (int64_t)pwrap(ty0 + yy, n2) * n1 + pwrap(tx0 + xx, n1);
 #pragma unroll
-        for (int j = 0; j <= L; j++) {
-            const int64_t r0 = (int64_t)pwrap(cy + iy0 + j, n2) * n1, r1 = (int64_t)pwrap(cy + iy1 + j, n2) * n1;
-            const T *e1r = E1 + r0, *b2r = B2 + r0, *e3r = E3 + r0, *e2r = E2 + r1, *b1r = B1 + r1, *b3r = B3 + r1;
-            T a10 = 0, a01 = 0, a00 = 0, b01 = 0, b10 = 0, b11 = 0;
-#pragma unroll
-            for (int i = 0; i <= L; i++) {
-                a10 += wx[1][i] * __ldg(e1r + cx1[i]);       // E1 at (1/2, 0)
-                b10 += wx[1][i] * __ldg(b2r + cx1[i]);       // B2 at (1/2, 0)
-                a01 += wx[0][i] * __ldg(e2r + cx0[i]);       // E2 at (0, 1/2)
-                b01 += wx[0][i] * __ldg(b1r + cx0[i]);       // B1 at (0, 1/2)
-                a00 += wx[0][i] * __ldg(e3r + cx0[i]);       // E3 at (0, 0)
-                b11 += wx[1][i] * __ldg(b3r + cx1[i]);       // B3 at (1/2, 1/2)
+                for (int f = 0; f < 6; f++) tile[f][q] = __ldg(src[f] + gq);
             }
-            e1 += wy[0][j] * a10; b2 += wy[0][j] * b10; e3 += wy[0][j] * a00;
-            e2 += wy[1][j] * a01; b1 += wy[1][j] * b01; b3 += wy[1][j] * b11;
         }
-        const T Ev[3] = {e1, e2, e3}, Bv[3] = {b1, b2, b3};
-        boris(uu, Ev, Bv, hdt * qm[p]);
-        const T gi = prsqrt((T)1 + uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
-        reinterpret_cast<int2*>(cell)[p] = make_int2(cx, cy);
-        V2 on;
-        on.x = ox; on.y = oy;
-        reinterpret_cast<V2*>(off)[p] = on;
-        u[3 * p] = uu[0]; u[3 * p + 1] = uu[1]; u[3 * p + 2] = uu[2];
-        on.x = ox + s1 * uu[0] * gi;
-        on.y = oy + s2 * uu[1] * gi;
-        reinterpret_cast<V2*>(off_new)[p] = on;
-        if (v3) v3[p] = uu[2] * gi;
+        __syncthreads();
+        if (ok) {
+            T uu[3] = {u[3 * p], u[3 * p + 1], u[3 * p + 2]};
+            // weights for the integer (0) and half (1) positions along each axis
+            T wx[2][L + 1], wy[2][L + 1];
+            const int ix0 = pweights<L>(ox, wx[0]), ix1 = pweights<L>(ox - (T)0.5, wx[1]);
+            const int iy0 = pweights<L>(oy, wy[0]), iy1 = pweights<L>(oy - (T)0.5, wy[1]);
+            T e1 = 0, e2 = 0, e3 = 0, b1 = 0, b2 = 0, b3 = 0;
+            if (tiled) {
+                const int lx = cx - tx0, ly = cy - ty0;
+#pragma unroll
+                for (int j = 0; j <= L; j++) {
+                    const int r0 = (ly + iy0 + j) * W + lx, r1 = (ly + iy1 + j) * W + lx;
+                    T a10 = 0, a01 = 0, a00 = 0, b01 = 0, b10 = 0, b11 = 0;
+#pragma unroll
+                    for (int i = 0; i <= L; i++) {
+                        a10 += wx[1][i] * tile[0][r0 + ix1 + i];     // E1 at (1/2, 0)
+                        b10 += wx[1][i] * tile[4][r0 + ix1 + i];     // B2 at (1/2, 0)
+                        a01 += wx[0][i] * tile[1][r1 + ix0 + i];     // E2 at (0, 1/2)
+                        b01 += wx[0][i] * tile[3][r1 + ix0 + i];     // B1 at (0, 1/2)
+                        a00 += wx[0][i] * tile[2][r0 + ix0 + i];     // E3 at (0, 0)
+                        b11 += wx[1][i] * tile[5][r1 + ix1 + i];     // B3 at (1/2, 1/2)
+                    }
+                    e1 += wy[0][j] * a10; b2 += wy[0][j] * b10; e3 += wy[0][j] * a00;
+                    e2 += wy[1][j] * a01; b1 += wy[1][j] * b01; b3 += wy[1][j] * b11;
+                }
+            } else {
+                int cx0[L + 1], cx1[L + 1];
+#pragma unroll
+                for (int k = 0; k <= L; k++) { cx0[k] = pwrap(cx + ix0 + k, n1); cx1[k] = pwrap(cx + ix1 + k, n1); }
+#pragma unroll
+                for (int j = 0; j <= L; j++) {
+                    const int64_t r0 = (int64_t)pwrap(cy + iy0 + j, n2) * n1, r1 = (int64_t)pwrap(cy + iy1 + j, n2) * n1;
+                    T a10 = 0, a01 = 0, a00 = 0, b01 = 0, b10 = 0, b11 = 0;
+#pragma unroll
+                    for (int i = 0; i <= L; i++) {
+                        a10 += wx[1][i] * __ldg(src[0] + r0 + cx1[i]);
+                        b10 += wx[1][i] * __ldg(src[4] + r0 + cx1[i]);
+                        a01 += wx[0][i] * __ldg(src[1] + r1 + cx0[i]);
+                        b01 += wx[0][i] * __ldg(src[3] + r1 + cx0[i]);
+                        a00 += wx[0][i] * __ldg(src[2] + r0 + cx0[i]);
+                        b11 += wx[1][i] * __ldg(src[5] + r1 + cx1[i]);
+                    }
+                    e1 += wy[0][j] * a10; b2 += wy[0][j] * b10; e3 += wy[0][j] * a00;
+                    e2 += wy[1][j] * a01; b1 += wy[1][j] * b01; b3 += wy[1][j] * b11;
+                }
+            }
+            const T Ev[3] = {e1, e2, e3}, Bv[3] = {b1, b2, b3};
+            boris(uu, Ev, Bv, hdt * qm[p]);
+            const T gi = prsqrt((T)1 + uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
+            reinterpret_cast<int2*>(cell)[p] = make_int2(cx, cy);
+            V2 on;
+            on.x = ox; on.y = oy;
+            reinterpret_cast<V2*>(off)[p] = on;
+            u[3 * p] = uu[0]; u[3 * p + 1] = uu[1]; u[3 * p + 2] = uu[2];
+            on.x = ox + s1 * uu[0] * gi;
+            on.y = oy + s2 * uu[1] * gi;
+            reinterpret_cast<V2*>(off_new)[p] = on;
+            if (v3) v3[p] = uu[2] * gi;
+        }
+        __syncthreads();                     // the tile has been read before the next one is staged
     }
 }
 
@@ -237,7 +301,7 @@ hyb_status push(hyb_grid* g, int32_t* cell, T* off, T* u, const T* qm, T* off_ne
     if (np == 0) return HYB_OK;
     PushFields F;
     for (int c = 0; c < 3; c++) { F.E[c] = g->E[c]; F.B[c] = g->B[c]; }
-    const int threads = 256;
+    const int threads = kPushThreads;
     int sms = 0;
     HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
     const int64_t want = (np + threads - 1) / threads;

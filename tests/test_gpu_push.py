@@ -34,10 +34,13 @@ def _check(res, ref, prec, dims):
         assert np.max(np.abs(v3 - v3o)) <= tol
 
 
+@pytest.mark.parametrize("sort", [False, True])
 @pytest.mark.parametrize("prec", [32, 64])
 @pytest.mark.parametrize("order", [1, 2, 3])
 @pytest.mark.parametrize("dims", [2, 3])
-def test_push_matches_oracle(dims, order, prec):
+def test_push_matches_oracle(dims, order, prec, sort):
+    """Random particles (each block's cells spread over the grid: gathers from global memory) and
+    the same particles sorted by cell (2D blocks stage their fields in a shared tile)."""
     need_gpu()
     hyb = hyb_module()
     shape = (128, 40) if dims == 2 else (32, 12, 10)
@@ -46,13 +49,19 @@ def test_push_matches_oracle(dims, order, prec):
     tdt = torch.float32 if prec == 32 else torch.float64
     g = _grid(hyb, dims, prec, shape)
     fields = [rng.standard_normal(shape[::-1]).astype(dt_np) for _ in range(6)]
-    n = 6000
+    n = 40000 if sort else 6000          # sorted: about 8 particles per 2D cell, as in the workload
     cell = np.stack([rng.integers(0, s, n) for s in shape], axis=1).astype(np.int32)
     off = rng.uniform(0.0, 1.0, (n, dims))
     off[: n // 3] = rng.uniform(-1.0, 2.0, (n // 3, dims))      # a previous step's off_new
     off = off.astype(dt_np)
     u = (rng.standard_normal((n, 3)) * 20.0).astype(dt_np)
     qm = rng.choice([-1.0, 1.0], n).astype(dt_np)
+    if sort:
+        key = np.zeros(n, dtype=np.int64)
+        for a in reversed(range(dims)):
+            key = key * shape[a] + cell[:, a]
+        o = np.argsort(key, kind="stable")
+        cell, off, u, qm = cell[o], off[o], u[o], qm[o]
     E = [torch.from_numpy(f).cuda() for f in fields[:3]]
     B = [torch.from_numpy(f).cuda() for f in fields[3:]]
     J = [torch.zeros(shape[::-1], dtype=tdt, device="cuda") for _ in range(3)]
