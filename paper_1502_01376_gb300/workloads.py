@@ -182,7 +182,8 @@ def position_at(w: Workload, p: Particles, step: int, real=np.float64):
 
 def plasma_move_torch(w: Workload, device, seed: int | None = None, step: int = 0):
     """Drifting-plasma particles drawn directly on a CUDA device (seeded
-    torch generator; same distributions as make_particles), returned as the
+    torch generator; same distributions as make_particles), each species
+    stored in cell order, returned as the
     deposit interface takes them for step `step`: int32 cell [np, dims],
     float32 offsets of x^n and x^{n+1}, float32 v3 and q."""
     import torch
@@ -210,10 +211,18 @@ def plasma_move_torch(w: Workload, device, seed: int | None = None, step: int = 
         c = torch.where(up, c + 1, c)
         o1 = torch.where(up, o1 - 1.0, o1)
         o0f = torch.where(up, torch.zeros_like(o0f), o0f)
-        cells.append(torch.remainder(c, ext).to(torch.int32))
-        off0s.append(o0f)
-        off1s.append(o1.to(torch.float32))
-        v3s.append(v[:, 2].to(torch.float32))
+        c = torch.remainder(c, ext)
+        # stored in cell order, as a PIC code keeps its particles
+        key = c[:, d - 1].to(torch.int64)
+        for a in range(d - 2, -1, -1):
+            key = key * int(ext[a].item()) + c[:, a].to(torch.int64)
+        order = torch.argsort(key, stable=True)
+        del key
+        cells.append(c[order].to(torch.int32))
+        off0s.append(o0f[order])
+        off1s.append(o1[order].to(torch.float32))
+        v3s.append(v[order, 2].to(torch.float32))
+        del order
         qs.append(torch.full((n,), sign * rho0 * dV / w.ppc, device=device, dtype=torch.float32))
         del x, v, c, o0, o1
     return (torch.cat(cells).contiguous(), torch.cat(off0s).contiguous(), torch.cat(off1s).contiguous(),

@@ -116,10 +116,13 @@ def test_yee_mode_and_bump(orc, yee):
     _compare(E, B, Eo, Bo, TOL[64])
 
 
+@pytest.mark.parametrize("sort", [False, True])
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("order", [1, 2, 3])
 @pytest.mark.parametrize("dims", [2, 3])
-def test_deposit_matches_oracle(orc, prec, order, dims):
+def test_deposit_matches_oracle(orc, prec, order, dims, sort):
+    """Random particle order (contributions added to J directly) and cell order (2D blocks add
+    into a shared tile first)."""
     need_gpu()
     hyb = hyb_module()
     if dims == 2:
@@ -134,6 +137,12 @@ def test_deposit_matches_oracle(orc, prec, order, dims):
     p = wl.make_particles(w)
     cell, off0, off1, v3 = wl.ballistic_move(w, p, 2, real=real)
     q = p.q.astype(real)
+    if sort:
+        key = np.zeros(len(q), dtype=np.int64)
+        for a in reversed(range(dims)):
+            key = key * (w.n1, w.n2, w.n3)[a] + cell[:, a]
+        o = np.argsort(key, kind="stable")
+        cell, off0, off1, v3, q = cell[o], off0[o], off1[o], v3[o], q[o]
     g.deposit(torch.from_numpy(cell).cuda(), to_dev(off0, dt), to_dev(off1, dt),
               to_dev(v3, dt) if dims == 2 else None, to_dev(q, dt), order)
     g.check()
