@@ -597,6 +597,7 @@ def main():
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        grid.deposit(cell, off0, off1, v3, q, w.shape_order)       # first call loads the kernel
         t0.record()
         grid.deposit(cell, off0, off1, v3, q, w.shape_order)
         t1.record()

@@ -26,8 +26,8 @@ __device__ __forceinline__ T bspline(T d) {
         if (a < (T)1.5) { T t = (T)1.5 - a; return (T)0.5 * t * t; }
         return (T)0;
     }
-    if (a <= (T)1) return ((T)4 - (T)6 * a * a + (T)3 * a * a * a) / (T)6;
-    if (a < (T)2) { T t = (T)2 - a; return t * t * t / (T)6; }
+    if (a <= (T)1) return ((T)4 - (T)6 * a * a + (T)3 * a * a * a) * ((T)1 / (T)6);
+    if (a < (T)2) { T t = (T)2 - a; return t * t * t * ((T)1 / (T)6); }
     return (T)0;
 }
 
@@ -54,7 +54,9 @@ __global__ void __launch_bounds__(kDepThreads) k_deposit2d(T* __restrict__ J1, T
     T* const Jc[3] = {J1, J2, J3};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t base = blockIdx.x * (int64_t)kDepThreads; base < np; base += (int64_t)gridDim.x * kDepThreads) {
-        const int64_t p = base + threadIdx.x;
+        // lanes take particles 8 apart, so that the lanes of a warp (which add to the same window
+        // offsets in lockstep) sit in different cells of a sorted chunk
+        const int64_t p = base + lane * (kDepThreads / 32) + warp;
         const bool live = p < np;
         int cx = 0, cy = 0;
         T x0 = 0, y0 = 0, x1 = 0, y1 = 0;
@@ -125,13 +127,16 @@ __global__ void __launch_bounds__(kDepThreads) k_deposit2d(T* __restrict__ J1, T
                 }
             }
             if (c3 != (T)0) {
+                // S1^0 S2^0/3 + S1^1 S2^0/6 + S1^0 S2^1/6 + S1^1 S2^1/3 = S1^0 a_j + S1^1 b_j
 #pragma unroll
-                for (int j = 0; j < W; j++)
+                for (int j = 0; j < W; j++) {
+                    const T aj = (Sy0[j] + Sy0[j] + Sy1[j]) * ((T)1 / (T)6), bj = (Sy0[j] + Sy1[j] + Sy1[j]) * ((T)1 / (T)6);
 #pragma unroll
                     for (int i = 0; i < W; i++) {
-                        const T w3 = Sx0[i] * Sy0[j] / (T)3 + Sx1[i] * Sy0[j] / (T)6 + Sx0[i] * Sy1[j] / (T)6 + Sx1[i] * Sy1[j] / (T)3;
+                        const T w3 = Sx0[i] * aj + Sx1[i] * bj;
                         if (w3 != (T)0) add(2, i, j, c3 * w3);
                     }
+                }
             }
         }
         __syncthreads();
@@ -191,7 +196,7 @@ __global__ void k_deposit3d(T* __restrict__ J1, T* __restrict__ J2, T* __restric
             for (int u = 0; u < W; u++)
                 for (int v = 0; v < W; v++) {
                     const T tw = S0[b][u] * S0[e][v] + (T)0.5 * dS[b][u] * S0[e][v] + (T)0.5 * S0[b][u] * dS[e][v]
-                               + dS[b][u] * dS[e][v] / (T)3;
+                               + dS[b][u] * dS[e][v] * ((T)1 / (T)3);
                     if (tw == (T)0) continue;
                     T acc = (T)0;
                     for (int i = 0; i < W; i++) {
