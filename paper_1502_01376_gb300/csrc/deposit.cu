@@ -85,43 +85,50 @@ __global__ void __launch_bounds__(kDepThreads) k_deposit2d(T* __restrict__ J1, T
             for (int t = threadIdx.x; t < TW * TH; t += kDepThreads) { tile[0][t] = (T)0; tile[1][t] = (T)0; tile[2][t] = (T)0; }
         __syncthreads();
         if (ok) {
-            T Sx0[W], Sx1[W], Sy0[W], Sy1[W];
+            // along each axis only the points where the shape at x^n or at x^{n+1} is non-zero: at most
+            // ORDER + 2 consecutive points (|x^{n+1} - x^n| < 1 cell), starting at gx, gy (relative to the
+            // cell, inside the full window LO .. LO + W - 1); beyond them the cumulative sums are back to 0
+            constexpr int WN = ORDER + 2;
+            // (clamped into the full window: a start rounded one point up only drops a point of weight 0)
+            const int gx = min(max((int)floor((x0 < x1 ? x0 : x1) - (T)0.5 * (T)(ORDER + 1)) + 1, LO), LO + W - WN);
+            const int gy = min(max((int)floor((y0 < y1 ? y0 : y1) - (T)0.5 * (T)(ORDER + 1)) + 1, LO), LO + W - WN);
+            T Sx0[WN], Sx1[WN], Sy0[WN], Sy1[WN];
 #pragma unroll
-            for (int w = 0; w < W; w++) {
-                const T gp = (T)(w + LO);
-                Sx0[w] = bspline<ORDER>(x0 - gp); Sx1[w] = bspline<ORDER>(x1 - gp);
-                Sy0[w] = bspline<ORDER>(y0 - gp); Sy1[w] = bspline<ORDER>(y1 - gp);
+            for (int w = 0; w < WN; w++) {
+                const T px = (T)(gx + w), py = (T)(gy + w);
+                Sx0[w] = bspline<ORDER>(x0 - px); Sx1[w] = bspline<ORDER>(x1 - px);
+                Sy0[w] = bspline<ORDER>(y0 - py); Sy1[w] = bspline<ORDER>(y1 - py);
             }
             const T qp = q[p];
             const T c1 = c1s * qp, c2 = c2s * qp;
             const T c3 = v3 ? c3s * qp * v3[p] : (T)0;
             // window point (i, j) -> tile index, or global index
-            const int lx = cx - bx0, ly = cy - by0;
-            int col[W], row[W];
+            const int lx = cx - bx0 + gx - LO, ly = cy - by0 + gy - LO;
+            int col[WN], row[WN];
 #pragma unroll
-            for (int w = 0; w < W; w++) { col[w] = wrapi(cx + LO + w, n1); row[w] = wrapi(cy + LO + w, n2); }
+            for (int w = 0; w < WN; w++) { col[w] = wrapi(cx + gx + w, n1); row[w] = wrapi(cy + gy + w, n2); }
             auto add = [&](int c, int i, int j, T v) {
                 if (tiled) atomicAdd(&tile[c][(ly + j) * TW + lx + i], v);
                 else atomicAdd(Jc[c] + (int64_t)row[j] * n1 + col[i], v);
             };
 #pragma unroll
-            for (int j = 0; j < W; j++) {
+            for (int j = 0; j < WN; j++) {
                 const T sy = (T)0.5 * (Sy0[j] + Sy1[j]);
                 if (sy == (T)0) continue;
                 T acc = (T)0;
 #pragma unroll
-                for (int i = 0; i < W; i++) {
+                for (int i = 0; i < WN; i++) {
                     acc += (Sx1[i] - Sx0[i]) * sy;
                     if (acc != (T)0) add(0, i, j, c1 * acc);
                 }
             }
 #pragma unroll
-            for (int i = 0; i < W; i++) {
+            for (int i = 0; i < WN; i++) {
                 const T sx = (T)0.5 * (Sx0[i] + Sx1[i]);
                 if (sx == (T)0) continue;
                 T acc = (T)0;
 #pragma unroll
-                for (int j = 0; j < W; j++) {
+                for (int j = 0; j < WN; j++) {
                     acc += (Sy1[j] - Sy0[j]) * sx;
                     if (acc != (T)0) add(1, i, j, c2 * acc);
                 }
@@ -129,10 +136,10 @@ __global__ void __launch_bounds__(kDepThreads) k_deposit2d(T* __restrict__ J1, T
             if (c3 != (T)0) {
                 // S1^0 S2^0/3 + S1^1 S2^0/6 + S1^0 S2^1/6 + S1^1 S2^1/3 = S1^0 a_j + S1^1 b_j
 #pragma unroll
-                for (int j = 0; j < W; j++) {
+                for (int j = 0; j < WN; j++) {
                     const T aj = (Sy0[j] + Sy0[j] + Sy1[j]) * ((T)1 / (T)6), bj = (Sy0[j] + Sy1[j] + Sy1[j]) * ((T)1 / (T)6);
 #pragma unroll
-                    for (int i = 0; i < W; i++) {
+                    for (int i = 0; i < WN; i++) {
                         const T w3 = Sx0[i] * aj + Sx1[i] * bj;
                         if (w3 != (T)0) add(2, i, j, c3 * w3);
                     }
