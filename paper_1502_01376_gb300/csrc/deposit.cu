@@ -10,8 +10,6 @@
 //       j_a = -q/(dt dV/dx_a) cumulative sum of W_a along axis a.
 // S are B-spline shape factors of order 1, 2 or 3 (grid points at integers).
 // One thread per particle; contributions are added with atomics.
-#include <climits>
-
 #include "hyb_internal.cuh"
 
 namespace hyb {
