@@ -144,3 +144,35 @@ def test_renormalise_moves_particles_and_keeps_precision():
     # -tiny + 1 rounds to 1 in FP32: the particle stays in its cell at offset 0
     c, o, ok = P.renormalise(np.array([[3, 1]]), np.array([[-1e-9, 0.0]], dtype=np.float32), (8, 4))
     assert c.tolist() == [[3, 1]] and o.tolist() == [[0.0, 0.0]]
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_gather_reproduces_linear_fields_3d(order):
+    """3D staggering: each component holding x1 + 2 x2 - x3 at its own points returns that
+    combination at the particle (linear reproduction along every axis)."""
+    rng = np.random.default_rng(30 + order)
+    n1, n2, n3 = 16, 12, 10
+    i3, i2, i1 = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    st = P.STAGGER[3]
+    fields = [(i1 + 0.5 * s[0]) + 2.0 * (i2 + 0.5 * s[1]) - (i3 + 0.5 * s[2]) for s in st]
+    cell = np.stack([rng.integers(3, n - 3, 200) for n in (n1, n2, n3)], axis=1)
+    off = rng.uniform(0.0, 1.0, (200, 3))
+    x = cell + off
+    want = x[:, 0] + 2.0 * x[:, 1] - x[:, 2]
+    out = P.gather(fields, cell, off, order)
+    assert np.max(np.abs(out - want[:, None])) < 1e-11
+
+
+def test_push_moves_particles_by_v_dt():
+    """No fields: u is kept and x^{n+1} - x^n = dt u / gamma / dx per axis (cell units)."""
+    rng = np.random.default_rng(4)
+    shape = (16, 8)
+    fields = [np.zeros(shape[::-1]) for _ in range(6)]
+    cell, off = _particles(rng, 100, shape)
+    u = rng.standard_normal((100, 3)) * 5.0
+    dt, dx = 0.1, np.array([0.2, 0.25])
+    c2, o2, un, on, v3, ok = P.push(fields, cell, off, u, np.ones(100), dt, dx, 2)
+    g = np.sqrt(1.0 + np.sum(u * u, axis=1))
+    assert ok.all() and np.array_equal(un, u)
+    assert np.max(np.abs(on - o2 - dt * u[:, :2] / g[:, None] / dx[None, :])) < 1e-15
+    assert np.max(np.abs(v3 - u[:, 2] / g)) < 1e-15
