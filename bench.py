@@ -708,6 +708,12 @@ def main():
                          "ms_median": 1e3 * statistics.median(e2e_t), "ms_max": 1e3 * max(e2e_t), "calls": len(e2e_t)}
         if ws == 1:
             extras["cpu_baseline"] = cpu_baseline_sample(w)
+    # FP64 diagnostics of the final state (energies, max |div B|, Gauss residual): synchronous call,
+    # the first one allocates its scratch
+    grid.diag()
+    tt = time.perf_counter()
+    grid.diag()
+    diag_ms = 1e3 * (time.perf_counter() - tt)
     if rank == 0:
         peak, src = peaks()
         achieved = BYTES_PER_CELL_STEP * cells / (kms / 1e3) / 1e9
@@ -719,7 +725,7 @@ def main():
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "n1": w.n1, "n2": w.n2, "dx": w.dx1, "dt": w.dt,
                        "correct_j1": True, "filter_kc": w.filt_kc, "filter_w": w.filt_w,
-                       "particles_deposited": n_particles, "deposit_ms": deposit_ms,
+                       "particles_deposited": n_particles, "deposit_ms": deposit_ms, "diag_ms": diag_ms,
                        "path": "fused" if grid.path == 2 else "three-pass",
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
