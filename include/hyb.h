@@ -155,12 +155,13 @@ HYB_API hyb_status hyb_correct_current(hyb_grid* g);
 /* The same j1 correction as hyb_correct_current, for callers that cannot
  * allocate device memory (the paper has no counterpart; this is a library
  * convenience).  It needs no grid: desc gives the sizes and cell size (dims,
- * n1, n2, n3, dx1, precision, yee_mode and the Sec. 4 bump are read), j1 is
- * the caller's device array (in place), stream a cudaStream_t.  It allocates
- * nothing: its tables and the k1-space copy of a block of rows live in one
- * static 8 MiB device array of the library, which every GPU that loads the
- * library keeps until the process exits.  Rows are processed in blocks that
- * fit the array; an n1 whose single row does not fit is rejected with
+ * n1, n2, n3, dx1, precision, yee_mode, kmod_l, kmod_u and kmod_max are read),
+ * j1 is the caller's device array (in place), stream a cudaStream_t.  It
+ * allocates nothing: its tables and the k1-space copy of a block of rows live
+ * in one static 8 MiB device array of the library, which every GPU that loads
+ * the library keeps until the process exits.  The tables are computed by a
+ * kernel on the stream (no host-to-device copy).  Rows are processed in blocks
+ * that fit the array; an n1 whose single row does not fit is rejected with
  * HYB_EINVAL.  The first call on a device looks up the array's address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call reuses the same array, so calls whose work overlaps on the GPU

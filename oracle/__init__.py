@@ -16,8 +16,9 @@ Parity status per function (pins in ``tests/test_oracle_*.py``):
   mode tables          pinned: special values of the correction and filter
   diag                 pinned through the invariants above
 The sibling modules carry their own status: ``quasi3d`` (Bessel modes of a
-conducting cylinder), ``nci`` (brute-force root scan; the coupled relation's
-values are parity unpinned), ``mlp`` (finite differences), ``push`` (B-spline
+conducting cylinder), ``nci`` (the printed cubic as the relation's expansion,
+the cold-beam continuum limit, Sec. 4's printed zero growth, a brute-force root
+scan), ``mlp`` (finite differences), ``push`` (B-spline
 identities, exact uniform-field solutions, second-order convergence).
 """
 from __future__ import annotations

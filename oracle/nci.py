@@ -26,26 +26,36 @@ Readings of garbled or silent points:
   * s_{l,i} = (sin(k'_i dx_i/2) / (k'_i dx_i/2))^(l+1) with k' the aliased
     wavenumber (the printed form lacks the denominator's k');
   * the repeated "S_E1" of the interpolation list is S_E3 (unused in 2D);
-  * S'_B3 in the cubic coefficients is S_B3;
+  * S_B3 of the full relation carries B's time centring: S_B3(w) = S'_B3
+    cos(w dt/2), with S'_B3 the printed spatial factor; the cubic's
+    zeta0 + zeta1 dw' is exactly the expansion of cos(w dt/2) about the
+    resonance, and only with this factor are the cubic's D2 and C2 the Taylor
+    coefficients of xi0^2 D (pinned);
   * the current filter F(k1) and the j1 correction multiply S_j1
     (S_j1 <- S_j1 F corr) and the filter multiplies S_j2;
   * momentum-conserving interpolation, shape order l = 2 unless given;
-  * the growth rate is max Im(w) over the roots, 0 if all are real.
+  * the growth rate of an alias is max Im(w) over the roots in the disk
+    |w - w_res| < (wp2/gamma)^(1/3) around the beam resonance w_res (the scale
+    at which the cubic's cubic and constant terms balance; the fastest NCI
+    roots lie within a tenth of it), 0 if none grows.
 
-The cubic asym1 (expansion about w' = k1' v0 with v0 -> 1) gives seeds; each
-seed is refined by Newton's method on F(w) = D(w) (w' - k1' v0), whose only
-extra root, at the resonance itself, is rejected.
+Root finding: the zeros of [w] F(w) (entire: the same zeros as F without its
+poles) in the disk, by recursive subdivision of an enclosing rectangle with
+the argument principle counting the zeros of each piece, and Newton's method
+inside pieces that hold one zero.  The count over the whole region makes the
+set complete by construction.
 
 Pins (tests/test_oracle_nci_mlp.py, tests/test_golden_paper_values.py): the
-vacuum limit factorises into the hybrid EM modes and the beam resonance; the
-resonance roots scale with sqrt(wp2); the (0,0) modes grow far more slowly
-than the (0,+-1) modes; the value Sec. 4 prints: zero (0,0) growth at the
-Table 1 parameters with the printed k1 modification, positive growth without
-it; and the root finding: the growth from the cubic seeds and Newton steps
-equals the one from a brute-force scan of |F| around the resonance.  The
-growth rates of other individual modes live in the paper's absent figures:
-the coupled relation's values there rest on these properties only, so they
-are parity unpinned.
+printed cubic's D2 and C2 equal the Taylor coefficients of xi0^2 D at v0 -> 1
+(this fixes the coupling term C and every symbol's place); the continuum limit
+equals the eigenfrequencies of an independently written linearised cold
+relativistic beam; planted sign errors in each group of C fail these; the
+vacuum limit factorises; the resonance roots scale with sqrt(wp2); the (0,0)
+modes grow far more slowly than the (0,+-1) modes and more slowly at smaller
+dt (Sec. 4); the value Sec. 4 prints: zero (0,0) growth at the Table 1
+parameters with the printed k1 modification, positive growth without it; the
+root set's completeness (argument principle on the region's circle) and its
+growth against a brute-force scan of |F|.
 """
 from __future__ import annotations
 
@@ -147,31 +157,48 @@ def symbols(P: NciParams, k1: float, k2: float, mu: int, nu1: int) -> ModeSymbol
     return ModeSymbols(k1, k2, k1a, kE1, kE2, SE1, SE2, SB3, Sj1, Sj2, mu, nu1)
 
 
-def wbracket(P: NciParams, w: complex) -> complex:
+def wbracket(P: NciParams, w):
+    """[w] = sin(w dt/2)/(dt/2), the leapfrog's time-difference symbol (numpy, complex)."""
     return np.sin(0.5 * w * P.dt) / (0.5 * P.dt)
 
 
-def F_of(P: NciParams, m: ModeSymbols, w: complex) -> complex:
-    """D(w) (w' - k1' v0): the dispersion function without the resonance pole."""
+def sb3_of(P: NciParams, m: ModeSymbols, w):
+    """S_B3 of the full relation: the spatial interpolation factor times cos(w dt/2),
+    the time centring of B (half a step away from E) at the particles' time level;
+    the printed cubic's zeta0 + zeta1 dw' is exactly the expansion of this factor."""
+    return m.SB3 * np.cos(0.5 * w * P.dt)
+
+
+def F_of(P: NciParams, m: ModeSymbols, w):
+    """D(w) (w' - k1' v0): the dispersion function (Eq. 2dmodesres with the coupling
+    term) times the resonance factor, which removes D's pole at w' = k1' v0."""
     v0 = P.v0
     wg = 2.0 * math.pi / P.dt
     wp = w + m.mu * wg
     Delta = wp - m.k1a * v0
     wb = wbracket(P, w)
+    SB3 = sb3_of(P, m, w)
     sgn = -1.0 if (m.mu % 2) else 1.0
     a = P.wp2 / P.gamma ** 3 * sgn
     b = P.wp2 / P.gamma * sgn
     K2 = m.kE1 * m.kE1 + m.kE2 * m.kE2
     first = Delta * Delta - a * m.Sj1 * m.SE1 * wp / wb
-    second = (wb * wb - K2) * Delta - b * m.Sj2 * (m.SE2 * wb - m.SB3 * m.kE1 * v0)
+    second = (wb * wb - K2) * Delta - b * m.Sj2 * (m.SE2 * wb - SB3 * m.kE1 * v0)
     C = b / wb * (m.Sj1 * m.SE1 * wp * m.kE2 * m.kE2 * (v0 * v0 - 1.0)
                   + m.Sj2 * m.SE2 * m.kE2 * m.kE2 * Delta
-                  + m.Sj1 * m.kE2 * (m.SE2 * m.kE1 * m.k2 * v0 - m.SB3 * m.k2 * v0 * v0 * wb))
+                  + m.Sj1 * m.kE2 * (m.SE2 * m.kE1 * m.k2 * v0 - SB3 * m.k2 * v0 * v0 * wb))
     return first * second + C * Delta
 
 
+def G_of(P: NciParams, m: ModeSymbols, w):
+    """[w] F(w): the same zeros as F, without F's poles where [w] = 0 (an entire function
+    of w, so the argument principle counts its zeros)."""
+    return wbracket(P, w) * F_of(P, m, w)
+
+
 def cubic_coeffs(P: NciParams, m: ModeSymbols):
-    """A2, B2, C2, D2 of Eq. asym1 (v0 -> 1 in k~1, S'_B3 read as S_B3)."""
+    """A2, B2, C2, D2 of Eq. asym1 (v0 -> 1 in k~1; S'_B3 is the spatial factor m.SB3,
+    zeta0 and zeta1 the expansion of B's time centring cos(w dt/2))."""
     wg = 2.0 * math.pi / P.dt
     kt = m.k1 + m.nu1 * (2.0 * math.pi / P.dx1) - m.mu * wg
     h = 0.5 * P.dt
@@ -190,49 +217,122 @@ def cubic_coeffs(P: NciParams, m: ModeSymbols):
     return A2, B2, C2, D2
 
 
-def newton(P: NciParams, m: ModeSymbols, w0: complex, tol: float = 1e-13, maxit: int = 60):
-    """Newton's method on F with a central complex difference for F'."""
-    w = complex(w0)
+def region_radius(P: NciParams) -> float:
+    """Radius of the disk around the beam resonance whose roots define the growth:
+    (wp2/gamma)^(1/3), the scale at which the cubic's leading and constant terms
+    balance (the NCI roots lie well inside it)."""
+    return (P.wp2 / P.gamma) ** (1.0 / 3.0)
+
+
+class _OnBoundary(Exception):
+    pass
+
+
+def _winding(f, x0, x1, y0, y1):
+    """Number of zeros of f inside the rectangle (argument principle): the change of
+    arg f around the boundary, sampled until no step exceeds 0.5 rad."""
+    n = 32
+    while n <= 1 << 14:
+        t = np.arange(n) / n
+        z = np.concatenate([x0 + (x1 - x0) * t + 1j * y0, x1 + 1j * (y0 + (y1 - y0) * t),
+                            x1 - (x1 - x0) * t + 1j * y1, x0 + 1j * (y1 - (y1 - y0) * t), [x0 + 1j * y0]])
+        g = f(z)
+        if np.all(g != 0):
+            d = np.angle(g[1:] / g[:-1])
+            if np.max(np.abs(d)) <= 0.5:
+                return int(round(np.sum(d) / (2.0 * math.pi)))
+        n *= 4
+    raise _OnBoundary()
+
+
+def _newton(f, w, tol=1e-14, maxit=100):
+    """Newton's method with a central-difference derivative."""
     for _ in range(maxit):
-        f = F_of(P, m, w)
+        fw = f(w)
         h = 1e-7 * max(1.0, abs(w))
-        d = (F_of(P, m, w + h) - F_of(P, m, w - h)) / (2.0 * h)
-        if d == 0:
+        d = (f(w + h) - f(w - h)) / (2.0 * h)
+        if d == 0 or not np.isfinite(d):
             return None
-        step = f / d
-        w -= step
+        step = fw / d
+        w = w - step
+        if not np.isfinite(w):
+            return None
         if abs(step) <= tol * max(1.0, abs(w)):
-            return w
+            return complex(w)
     return None
 
 
-def roots(P: NciParams, k1: float, k2: float, mu: int, nu1: int):
-    """Refined roots of the full relation near the beam resonance."""
-    m = symbols(P, k1, k2, mu, nu1)
-    wg = 2.0 * math.pi / P.dt
-    w_res = m.k1a * P.v0 - mu * wg
-    A2, B2, C2, D2 = cubic_coeffs(P, m)
-    seeds = []
-    if A2 != 0.0:
-        seeds += [w_res + complex(r) for r in np.roots([A2, B2, C2, D2])]
-    r0 = (P.wp2 / P.gamma) ** (1.0 / 3.0) * 0.05
-    seeds += [w_res + r0 * complex(math.cos(t), math.sin(t)) for t in (math.pi / 6, math.pi / 2, 5 * math.pi / 6)]
-    out = []
-    for s in seeds:
-        w = newton(P, m, s)
-        if w is None:
-            continue
-        if abs(w + mu * wg - m.k1a * P.v0) < 1e-9 * max(1.0, abs(w)):
-            continue                       # the removed pole
-        if all(abs(w - u) > 1e-9 * max(1.0, abs(w)) for u in out):
+# split fractions of the subdivision, away from 1/2 so that the real axis (where the real
+# roots lie) and the resonance do not fall on a split line; the next pair is tried when a
+# zero lies too close to a split line for its count to be resolved
+_SPLITS = ((0.4871, 0.5317), (0.4413, 0.5689), (0.5593, 0.4231), (0.3917, 0.6143))
+
+
+def _zeros_in_rect(f, x0, x1, y0, y1, hmin, N, out):
+    if N == 0:
+        return
+    if N == 1:
+        w = _newton(f, complex(x0 + _SPLITS[0][0] * (x1 - x0), y0 + _SPLITS[0][1] * (y1 - y0)))
+        if w is not None and x0 <= w.real <= x1 and y0 <= w.imag <= y1:
             out.append(w)
-    return out
+            return
+    if max(x1 - x0, y1 - y0) < hmin:            # a cluster below resolution: its centre, N times
+        out.extend([complex(0.5 * (x0 + x1), 0.5 * (y0 + y1))] * N)
+        return
+    for fx, fy in _SPLITS:
+        xm, ym = x0 + fx * (x1 - x0), y0 + fy * (y1 - y0)
+        kids = [(x0, xm, y0, ym), (xm, x1, y0, ym), (x0, xm, ym, y1), (xm, x1, ym, y1)]
+        try:
+            ns = [_winding(f, *k) for k in kids]
+        except _OnBoundary:
+            continue
+        if sum(ns) != N:
+            raise RuntimeError("argument principle: inconsistent zero counts")
+        for k, nk in zip(kids, ns):
+            _zeros_in_rect(f, *k, hmin, nk, out)
+        return
+    raise RuntimeError("argument principle: zeros on every split line tried")
+
+
+def zeros_in_disk(f, c: complex, rho: float):
+    """All zeros of the entire function f with |w - c| < rho: a rectangle enclosing the
+    disk is split into four until each piece holds one zero (counted by the argument
+    principle), which Newton's method then locates inside it."""
+    if not rho > 0.0:
+        return []
+    for e in (1.0, 1.013, 1.029):
+        x0, x1 = c.real - e * rho, c.real + 1.0007 * e * rho
+        y0, y1 = c.imag - 1.0003 * e * rho, c.imag + 1.0011 * e * rho
+        try:
+            N = _winding(f, x0, x1, y0, y1)
+        except _OnBoundary:
+            continue
+        out = []
+        # resolution: zeros closer than this are returned as one point, N times (below it,
+        # rounding in w and in f decides the phase of f)
+        hmin = max(1e-12 * rho, 1e-9 * max(1.0, abs(c)))
+        _zeros_in_rect(f, x0, x1, y0, y1, hmin, N, out)
+        return [w for w in out if abs(w - c) < rho]
+    raise RuntimeError("argument principle: zeros on the enclosing rectangle")
+
+
+def resonance(P: NciParams, m: ModeSymbols) -> float:
+    """w at the beam resonance w' = k1' v0."""
+    return m.k1a * P.v0 - m.mu * 2.0 * math.pi / P.dt
+
+
+def roots(P: NciParams, k1: float, k2: float, mu: int, nu1: int, rho: float | None = None):
+    """All roots of the full relation within rho (default region_radius) of the beam resonance."""
+    m = symbols(P, k1, k2, mu, nu1)
+    r = region_radius(P) if rho is None else rho
+    return zeros_in_disk(lambda w: G_of(P, m, w), complex(resonance(P, m)), r)
 
 
 def growth(P: NciParams, k1: float, k2: float, mu: int, nu1: int) -> float:
+    """NCI growth rate of alias (mu, nu1) at (k1, k2): the largest Im w over the roots in the
+    region around the beam resonance, 0 if none grows."""
     rs = roots(P, k1, k2, mu, nu1)
-    g = max([r.imag for r in rs], default=0.0)
-    return max(g, 0.0)
+    return max([r.imag for r in rs] + [0.0])
 
 
 def growth_scan(P: NciParams, mu: int, nu1: int, n1: int = 64, n2: int = 64):

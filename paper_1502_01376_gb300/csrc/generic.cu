@@ -341,14 +341,9 @@ template <typename Tin, typename T>
 static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
     if constexpr (std::is_same<Tin, float>::value && std::is_same<T, float>::value) {
         if (n1 == 1024) {
-            static const int resident = [] {
-                cudaFuncSetAttribute(k_rfft1024, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-                int dev = 0, sms = 0, occ = 0;
-                cudaGetDevice(&dev);
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rfft1024, 256, 0);
-                return std::max(1, sms * occ);
-            }();
+            const cudaError_t carve = func_attr_once((const void*)k_rfft1024, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (carve != cudaSuccess) return carve;
+            const int resident = resident_grid((const void*)k_rfft1024, 256, 0);
             const int64_t blocks = std::min<int64_t>((rows * nf + kRows1k - 1) / kRows1k, resident);
             k_rfft1024<<<(unsigned)blocks, 256, 0, s>>>(p, out, rows, nf, t.tw8, t.twN);
             return cudaGetLastError();
@@ -357,8 +352,8 @@ static cudaError_t launch_rfft(const RowPtrs& p, int nf, cplx<T>* out, int n1, i
     const int RB = fft_rows_per_launch(n1 / 2, rows * nf);
     const size_t smem = row_fft_smem<T>(n1, RB);
     auto kern = k_rfft_rows<Tin, T>;
-    // once per kernel: room for the largest row block any n1 up to 8192 asks for
-    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_row_fft_smem<T>());
+    // once per kernel and device: room for the largest row block any n1 up to 8192 asks for
+    const cudaError_t attr = func_attr_once((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_row_fft_smem<T>());
     if (attr != cudaSuccess) return attr;
     dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
     kern<<<grid, kRowThreads, smem, s>>>(p, out, n1, rows, t.twS, t.twN, RB);
@@ -369,8 +364,8 @@ template <typename T, typename Tout>
 static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, int nf, int n1, int64_t rows, const ModeTables<T>& t, cudaStream_t s) {
     if constexpr (std::is_same<T, float>::value && std::is_same<Tout, float>::value) {
         if (n1 == 1024) {
-            static bool carve = (cudaFuncSetAttribute(k_irfft1024, cudaFuncAttributePreferredSharedMemoryCarveout, 100), true);
-            (void)carve;
+            const cudaError_t carve = func_attr_once((const void*)k_irfft1024, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (carve != cudaSuccess) return carve;
             k_irfft1024<<<dim3((unsigned)((rows + kRows1k - 1) / kRows1k), nf), 256, 0, s>>>(in, p, rows, t.tw8, t.twN, f0);
             return cudaGetLastError();
         }
@@ -378,8 +373,8 @@ static cudaError_t launch_irfft(const cplx<T>* in, int f0, const RowPtrsW& p, in
     const int RB = fft_rows_per_launch(n1 / 2, rows * nf);
     const size_t smem = row_fft_smem<T>(n1, RB);
     auto kern = k_irfft_rows<T, Tout>;
-    // once per kernel: room for the largest row block any n1 up to 8192 asks for
-    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_row_fft_smem<T>());
+    // once per kernel and device: room for the largest row block any n1 up to 8192 asks for
+    const cudaError_t attr = func_attr_once((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_row_fft_smem<T>());
     if (attr != cudaSuccess) return attr;
     dim3 grid((unsigned)((rows + RB - 1) / RB), nf);
     kern<<<grid, kRowThreads, smem, s>>>(in, p, n1, rows, t.twS, t.twN, f0, RB);

@@ -9,6 +9,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -19,18 +20,33 @@ namespace hyb {
 
 int resident_grid(const void* kernel, int threads, size_t smem) {
     static std::mutex mu;
-    static std::map<std::pair<const void*, size_t>, int> cache;
-    std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_pair(kernel, smem * 4096 + (size_t)threads);
-    const auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
+    static std::map<std::tuple<int, const void*, size_t>, int> cache;
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(dev, kernel, smem * 4096 + (size_t)threads);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
     const int r = sms * occ > 0 ? sms * occ : 1;
     cache[key] = r;
     return r;
+}
+
+cudaError_t func_attr_once(const void* kernel, cudaFuncAttribute attr, int value) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int>, int> done;   // value set per (device, kernel, attribute)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(dev, kernel, (int)attr);
+    const auto it = done.find(key);
+    if (it != done.end() && it->second == value) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, attr, value);
+    if (e == cudaSuccess) done[key] = value;
+    return e;
 }
 
 static thread_local char g_err[512] = "";
@@ -72,23 +88,13 @@ static HostModes host_modes(const hyb_grid_desc& d) {
     HostModes h;
     h.keff.resize(M + 1); h.corr.resize(M + 1); h.filt.resize(M + 1);
     h.sgp_re.resize(M + 1); h.sgp_im.resize(M + 1);
-    const double kn = kPi / d.dx1, kg = 2.0 * kPi / d.dx1;
+    const double kn = kPi / d.dx1;
     const bool filt_on = d.filt_kc > 0.0 && d.filt_kc < 1.0;
     for (int k = 0; k <= M; k++) {
-        const double k1 = kg * (double)k / (double)d.n1;               // 2 pi kappa / (n1 dx1)
-        const double kfd = sin(0.5 * k1 * d.dx1) / (0.5 * d.dx1);        // Yee symbol [k]1
-        double ke = k1;                                                  // hybrid: [k]1 -> k1
-        if (d.yee_mode) {
-            ke = kfd;
-        } else if (d.kmod_max != 0.0) {                                  // Sec. 4 bump
-            const double kl = d.kmod_l * kg, ku = d.kmod_u * kg, km = 0.5 * (kl + ku);
-            if (k1 >= kl && k1 <= ku) {
-                const double c = cos(0.5 * kPi * (k1 - km) / (kl - km));
-                ke += d.kmod_max * kg * c * c;
-            }
-        }
+        const ModeK mk = mode_k(k, d.n1, d.dx1, d.yee_mode, d.kmod_l, d.kmod_u, d.kmod_max);
+        const double k1 = mk.k1, ke = mk.keff;                           // hybrid: [k]1 -> k1 (or Yee, or bump)
         h.keff[k] = ke;
-        h.corr[k] = (k == 0) ? 1.0 : kfd / ke;                           // Eq. currentcorrection
+        h.corr[k] = mode_corr(k, mk);                                    // Eq. currentcorrection
         double f = 1.0;
         if (filt_on) {
             const double kc = d.filt_kc * kn, w = d.filt_w * kn, a = fabs(k1);

@@ -127,43 +127,87 @@ __device__ __forceinline__ void stockham_rows(C*& src, C*& dst, int M, int nrow,
     }
 }
 
+constexpr int kTw8 = 504;   // entries of ModeTables::tw8
+
+// x1 wavenumbers of mode kappa in FP64: k1 = 2 pi kappa / (n1 dx1); the Yee symbol
+// [k]1 = sin(k1 dx1/2)/(dx1/2); and the wavenumber the advance differentiates with
+// (Sec. 2.1: [k]1 replaced by k1; the Yee symbol itself in Yee-recovery mode; k1 plus the
+// raised-cosine bump of Sec. 4 between kmod_l and kmod_u, fractions of k_g1 = 2 pi/dx1).
+// One definition for the host tables and for tables built on the device.
+struct ModeK { double k1, kfd, keff; };
+__host__ __device__ inline ModeK mode_k(int kappa, int n1, double dx1, int yee_mode, double kmod_l, double kmod_u,
+                                        double kmod_max) {
+    const double pi = 3.14159265358979323846, kg = 2.0 * pi / dx1;
+    ModeK m;
+    m.k1 = kg * (double)kappa / (double)n1;
+    m.kfd = sin(0.5 * m.k1 * dx1) / (0.5 * dx1);
+    m.keff = m.k1;
+    if (yee_mode) {
+        m.keff = m.kfd;
+    } else if (kmod_max != 0.0) {
+        const double kl = kmod_l * kg, ku = kmod_u * kg, km = 0.5 * (kl + ku);
+        if (m.k1 >= kl && m.k1 <= ku) {
+            const double c = cos(0.5 * pi * (m.k1 - km) / (kl - km));
+            m.keff += kmod_max * kg * c * c;
+        }
+    }
+    return m;
+}
+// Eq. currentcorrection factor of mode kappa ([k]1 of the finite difference over the
+// advance's wavenumber; 1 at kappa = 0)
+__host__ __device__ inline double mode_corr(int kappa, const ModeK& m) { return kappa == 0 ? 1.0 : m.kfd / m.keff; }
+
+// Entry i of stockham_twiddles(M) as W = exp(-2 pi i num/den): the pass with span Ns and
+// radix R holds W_{R Ns}^{r k} at Ns - 1 + (r - 1) Ns + k.  Returns num = 0, den = 1 for
+// the one entry no pass uses.
+__host__ __device__ inline void stockham_tw_frac(int M, int i, int* num, int* den) {
+    int lgM = 0;
+    while ((1 << lgM) < M) lgM++;
+    int lgNs = 0;
+    *num = 0;
+    *den = 1;
+    while (lgNs < lgM) {
+        const int lgR = (lgNs + 3 <= lgM) ? 3 : (lgNs + 2 <= lgM) ? 2 : 1;
+        const int Ns = 1 << lgNs, R = 1 << lgR;
+        if (i >= Ns - 1 && i < R * Ns - 1) {
+            const int q = i - (Ns - 1), r = 1 + q / Ns, k = q % Ns;
+            *num = r * k;
+            *den = R * Ns;
+            return;
+        }
+        lgNs += lgR;
+    }
+}
+// Entry i of ModeTables::tw8 as W = exp(-2 pi i num/den)
+__host__ __device__ inline void tw8_frac(int i, int* num, int* den) {
+    if (i < 448) { *num = (i % 64) * (1 + i / 64); *den = 512; }
+    else { *num = ((i - 448) % 8) * (1 + (i - 448) / 8); *den = 64; }
+}
+
 // The twiddles of the passes stockham_rows makes for M points, in pass order: the pass with span
 // Ns and radix R holds W_{R Ns}^{r k} (r = 1..R-1, k < Ns) at Ns - 1 + (r - 1) Ns + k, so the
 // passes fill entries 0..M-2 (computed in FP64, rounded once).
 template <typename C>
 inline std::vector<C> stockham_twiddles(int M) {
-    std::vector<C> tw((size_t)M, mkc<C>(1, 0));
-    int lgM = 0;
-    while ((1 << lgM) < M) lgM++;
-    int lgNs = 0;
-    auto pass = [&](int lgR) {
-        const int Ns = 1 << lgNs, R = 1 << lgR;
-        for (int r = 1; r < R; r++)
-            for (int k = 0; k < Ns; k++) {
-                const double a = -2.0 * 3.14159265358979323846 * (double)(r * k) / (double)(R * Ns);
-                tw[(size_t)(Ns - 1 + (r - 1) * Ns + k)] = mkc<C>((decltype(C::x))std::cos(a), (decltype(C::x))std::sin(a));
-            }
-        lgNs += lgR;
-    };
-    while (lgNs + 3 <= lgM) pass(3);
-    if (lgNs + 2 <= lgM) pass(2);
-    else if (lgNs + 1 <= lgM) pass(1);
+    std::vector<C> tw((size_t)M);
+    for (int i = 0; i < M; i++) {
+        int num, den;
+        stockham_tw_frac(M, i, &num, &den);
+        const double a = -2.0 * 3.14159265358979323846 * (double)num / (double)den;
+        tw[(size_t)i] = mkc<C>((decltype(C::x))std::cos(a), (decltype(C::x))std::sin(a));
+    }
     return tw;
 }
 
 // ModeTables::tw8 for M = 512 (computed in FP64, rounded once)
 template <typename C>
 inline std::vector<C> tw8_table() {
-    std::vector<C> tw(504);
-    for (int k = 1; k < 8; k++) {
-        for (int t = 0; t < 64; t++) {
-            const double a = -2.0 * 3.14159265358979323846 * (double)(t * k) / 512.0;
-            tw[(size_t)((k - 1) * 64 + t)] = mkc<C>((decltype(C::x))std::cos(a), (decltype(C::x))std::sin(a));
-        }
-        for (int t0 = 0; t0 < 8; t0++) {
-            const double a = -2.0 * 3.14159265358979323846 * (double)(t0 * k) / 64.0;
-            tw[(size_t)(448 + (k - 1) * 8 + t0)] = mkc<C>((decltype(C::x))std::cos(a), (decltype(C::x))std::sin(a));
-        }
+    std::vector<C> tw(kTw8);
+    for (int i = 0; i < kTw8; i++) {
+        int num, den;
+        tw8_frac(i, &num, &den);
+        const double a = -2.0 * 3.14159265358979323846 * (double)num / (double)den;
+        tw[(size_t)i] = mkc<C>((decltype(C::x))std::cos(a), (decltype(C::x))std::sin(a));
     }
     return tw;
 }
@@ -184,13 +228,14 @@ __host__ __forceinline__ int fft_rows_per_launch(int M, int64_t total_rows) {
 // transforms the current one.
 constexpr int kPrefetchPts = 8;
 // blocks of `threads` threads with `smem` bytes of dynamic shared memory that fit on the
-// current device at once (cached per kernel and size)
+// current device at once (cached per device, kernel and size)
 int resident_grid(const void* kernel, int threads, size_t smem);
+// cudaFuncSetAttribute(kernel, attr, value) on the current device, once per device (a
+// function attribute set on one device does not carry over to another)
+cudaError_t func_attr_once(const void* kernel, cudaFuncAttribute attr, int value);
 
 // ---------------------------------------------------------------- tables
 // Per-mode tables for kappa = 0..n1/2, computed in FP64 on the host and rounded once.
-constexpr int kTw8 = 504;   // entries of ModeTables::tw8
-
 template <typename T>
 struct ModeTables {
     cplx<T>* S = nullptr;     // c dt sigma+ = c dt i [k]1 exp(+i k1 dx1/2)

@@ -9,9 +9,12 @@
 // memory (the per-mode tables and the k1-space copy of a block of rows) is the
 // file-scope array g_noalloc_scratch below, which every GPU that loads the
 // library holds until the process exits.  Rows are processed in blocks that
-// fit the array, so any grid size is accepted as long as one row fits.
+// fit the array, so any grid size is accepted as long as one row fits.  The
+// tables are computed by a kernel on the call's stream, not copied from the
+// host, so a call makes no host-to-device copy and does not block the host on
+// the stream.
+#include <algorithm>
 #include <mutex>
-#include <vector>
 
 #include "hyb_internal.cuh"
 
@@ -43,10 +46,38 @@ static hyb_status noalloc_address(void** out) {
     return HYB_OK;
 }
 
+// The tables of one call, written on the device into the head of the static array (no
+// host copies): corr[nk] (Eq. currentcorrection, from the same mode_k the grid tables use),
+// twS[M] (stockham_twiddles), twN[M] = W_n1^j and, for n1 = 1024, tw8[kTw8]; FP64, rounded once.
 template <typename T>
-__global__ void k_noalloc_scale(cplx<T>* __restrict__ spec, int nk, const T* __restrict__ fac) {
-    cplx<T>* X = spec + (int64_t)blockIdx.x * nk;
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) X[k] = cscale(X[k], fac[k]);
+__global__ void k_noalloc_tables(T* __restrict__ corr, cplx<T>* __restrict__ twS, cplx<T>* __restrict__ twN,
+                                 cplx<T>* __restrict__ tw8, int n1, double dx1, int yee_mode, double kmod_l,
+                                 double kmod_u, double kmod_max, int n8) {
+    using C = cplx<T>;
+    const int M = n1 / 2, nk = M + 1;
+    const int total = nk + 2 * M + n8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        if (i < nk) {
+            corr[i] = (T)mode_corr(i, mode_k(i, n1, dx1, yee_mode, kmod_l, kmod_u, kmod_max));
+            continue;
+        }
+        int j = i - nk, num, den;
+        C* dst;
+        if (j < M) { stockham_tw_frac(M, j, &num, &den); dst = twS + j; }
+        else if (j < 2 * M) { j -= M; num = j; den = n1; dst = twN + j; }
+        else { j -= 2 * M; tw8_frac(j, &num, &den); dst = tw8 + j; }
+        double sn, cs;
+        sincospi(-2.0 * (double)num / (double)den, &sn, &cs);   // exp(-2 pi i num/den)
+        *dst = mkc<C>((T)cs, (T)sn);
+    }
+}
+
+// X[r][k] *= fac[k] over nr rows of nk modes (grid-stride over all nr * nk entries)
+template <typename T>
+__global__ void k_noalloc_scale(cplx<T>* __restrict__ spec, int nk, int64_t nr, const T* __restrict__ fac) {
+    const int64_t n = nr * nk;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        spec[i] = cscale(spec[i], fac[i % nk]);
 }
 
 template <typename T>
@@ -55,9 +86,9 @@ static hyb_status run(const hyb_grid_desc& d, T* j1, cudaStream_t s) {
     const int n1 = d.n1, M = n1 / 2, nk = M + 1;
     const int64_t rows = (int64_t)d.n2 * (d.dims == 3 ? d.n3 : 1);
     // tables in the head of the array: corr[nk], twS[M], twN[M] and, for n1 = 1024, tw8; then row blocks
-    auto up16 = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t n8 = M == 512 ? (size_t)kTw8 : 0;
-    const size_t tab_bytes = up16(sizeof(T) * nk) + up16(sizeof(C) * M) * 2 + up16(sizeof(C) * n8);
+    auto up256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const int n8 = M == 512 ? kTw8 : 0;
+    const size_t tab_bytes = up256(sizeof(T) * nk) + up256(sizeof(C) * M) * 2 + up256(sizeof(C) * n8);
     const size_t row_bytes = sizeof(C) * (size_t)nk;
     if (tab_bytes + row_bytes > kNoallocBytes) {
         set_error("hyb_correct_current_noalloc: n1 = %d needs %zu bytes of working memory, more than the %zu available",
@@ -69,38 +100,20 @@ static hyb_status run(const hyb_grid_desc& d, T* j1, cudaStream_t s) {
     if (st != HYB_OK) return st;
     char* p = (char*)base;
     T* corr = (T*)p;
-    C* twS = (C*)(p + up16(sizeof(T) * nk));
-    C* twN = (C*)(p + up16(sizeof(T) * nk) + up16(sizeof(C) * M));
-    C* tw8 = (C*)(p + up16(sizeof(T) * nk) + 2 * up16(sizeof(C) * M));
+    C* twS = (C*)(p + up256(sizeof(T) * nk));
+    C* twN = (C*)(p + up256(sizeof(T) * nk) + up256(sizeof(C) * M));
+    C* tw8 = (C*)(p + up256(sizeof(T) * nk) + 2 * up256(sizeof(C) * M));
     C* spec = (C*)(p + tab_bytes);
     const int64_t rows_per_block = (int64_t)((kNoallocBytes - tab_bytes) / row_bytes);
 
-    // FP64 tables on the host, rounded once (the same quantities hyb_create_grid computes)
-    const double pi = 3.14159265358979323846;
-    std::vector<T> hc(nk);
-    const std::vector<C> hm = stockham_twiddles<C>(M);
-    std::vector<C> hn(M);
-    const std::vector<C> h8 = n8 ? tw8_table<C>() : std::vector<C>();
-    for (int k = 0; k < nk; k++) {
-        const double k1 = 2.0 * pi * k / (n1 * d.dx1);
-        const double kfd = sin(0.5 * k1 * d.dx1) / (0.5 * d.dx1);
-        double ke = k1;
-        if (d.yee_mode) ke = kfd;
-        else if (d.kmod_max != 0.0) {
-            const double kg = 2.0 * pi / d.dx1, kl = d.kmod_l * kg, ku = d.kmod_u * kg, km = 0.5 * (kl + ku);
-            if (k1 >= kl && k1 <= ku) { const double c = cos(0.5 * pi * (k1 - km) / (kl - km)); ke += d.kmod_max * kg * c * c; }
-        }
-        hc[k] = (T)(k == 0 ? 1.0 : kfd / ke);
+    // every table entry is rewritten, so an earlier call's tables (other n1, dx1 or mode
+    // switches) leave nothing behind; stream-ordered before the transforms that read them
+    {
+        const int total = nk + 2 * M + n8;
+        k_noalloc_tables<T><<<(total + 255) / 256, 256, 0, s>>>(corr, twS, twN, tw8, n1, d.dx1, d.yee_mode, d.kmod_l,
+                                                               d.kmod_u, d.kmod_max, n8);
+        HYB_CUDA_TRY(cudaGetLastError());
     }
-    for (int j = 0; j < M; j++) {
-        const double b = -2.0 * pi * j / n1;
-        hn[j] = mkc<C>((T)cos(b), (T)sin(b));
-    }
-    // pageable source: the copies are staged before cudaMemcpyAsync returns
-    HYB_CUDA_TRY(cudaMemcpyAsync(corr, hc.data(), sizeof(T) * nk, cudaMemcpyHostToDevice, s));
-    HYB_CUDA_TRY(cudaMemcpyAsync(twS, hm.data(), sizeof(C) * M, cudaMemcpyHostToDevice, s));
-    HYB_CUDA_TRY(cudaMemcpyAsync(twN, hn.data(), sizeof(C) * M, cudaMemcpyHostToDevice, s));
-    if (n8) HYB_CUDA_TRY(cudaMemcpyAsync(tw8, h8.data(), sizeof(C) * n8, cudaMemcpyHostToDevice, s));
     ModeTables<T> t;
     t.twS = twS;
     t.twN = twN;
@@ -111,7 +124,9 @@ static hyb_status run(const hyb_grid_desc& d, T* j1, cudaStream_t s) {
         const int64_t nr = (rows - r0 < rows_per_block) ? rows - r0 : rows_per_block;
         T* rowp = j1 + r0 * n1;
         HYB_CUDA_TRY((rfft_rows<T, T>(rowp, spec, n1, nr, t, s)));
-        k_noalloc_scale<T><<<(unsigned)nr, 256, 0, s>>>(spec, nk, corr);
+        const int64_t n = nr * nk;
+        const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
+        k_noalloc_scale<T><<<blocks, 256, 0, s>>>(spec, nk, nr, corr);
         HYB_CUDA_TRY(cudaGetLastError());
         HYB_CUDA_TRY((irfft_rows<T, T>(spec, rowp, n1, nr, t, s)));
     }

@@ -361,7 +361,7 @@ static hyb_status advance_t(hyb_grid* g, int nsteps) {
     for (int s = 0; s < nsteps; s++) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
         if (P->tw2k) {
-            static const int res = resident_grid((const void*)k_cfft2048<false>, 256, 0);
+            const int res = resident_grid((const void*)k_cfft2048<false>, 256, 0);
             k_cfft2048<false><<<(unsigned)std::min<int64_t>(res, 9 * (int64_t)nr), 256, 0, g->stream>>>(
                 fin, reinterpret_cast<float2*>(P->spec), nr, 9, P->tw2k);
         } else {
@@ -370,7 +370,7 @@ static hyb_status advance_t(hyb_grid* g, int nsteps) {
         const dim3 mgrid((unsigned)((nz + kQThreads - 1) / kQThreads), (unsigned)nr);   // one thread per (mode, row)
         k_qleap<T><<<mgrid, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
         if (P->tw2k) {
-            static const int res = resident_grid((const void*)k_cfft2048<true>, 256, 0);
+            const int res = resident_grid((const void*)k_cfft2048<true>, 256, 0);
             k_cfft2048<true><<<(unsigned)std::min<int64_t>(res, 6 * (int64_t)nr), 256, 0, g->stream>>>(
                 fout, reinterpret_cast<float2*>(P->spec + 6 * (int64_t)nr * nz), nr, 6, P->tw2k);
         } else {
