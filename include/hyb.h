@@ -267,21 +267,40 @@ HYB_API hyb_status hyb_batch_destroy(hyb_batch* b);
  * NCI analysis (Sec. 3 and the Appendix): growth rate of the numerical
  * Cerenkov instability of a cold plasma drifting along x1 on the hybrid
  * solver's grid, from the roots of the numerical dispersion relation
- * (Eq. 2dmodesres with its coupling term; hybrid operators [k]E1 = [k]B1 = k1,
- * [k]E2 = [k]B2 = sin(k2 dx2/2)/(dx2/2)), seeded by the roots of the cubic
- * Eq. asym1 and refined by Newton's method, in FP64 on the GPU.
- *   samples  device double [n][9]: dt, dx1, dx2, gamma, wp2 (plasma frequency^2,
+ * (Eq. 2dmodesres with its coupling term; hybrid operators [k]E1 = [k]B1 = k1
+ * plus the Sec. 4 bump, [k]E2 = [k]B2 = sin(k2 dx2/2)/(dx2/2); B time-centred,
+ * S_B3 = S'_B3 cos(omega dt/2), as the cubic Eq. asym1 implies), in FP64 on the
+ * GPU.  The roots of an alias are ALL zeros of [omega] D(omega) (omega' - k1' v0)
+ * in the disk |omega - omega_res| < (wp2/gamma)^(1/3) about the beam resonance
+ * omega' = k1' v0: counted by the argument principle on the disk's circle,
+ * located by deflated Newton iterations from the cubic's roots and rings of
+ * seeds, and, when seeds leave some unfound, by argument-principle subdivision.
+ *   samples  device double [n][12]: dt, dx1, dx2, gamma, wp2 (plasma frequency^2,
  *            n/n_p), filt_kc, filt_w (current filter, fractions of pi/dx1;
- *            kc outside (0,1) = off), k1, k2;
+ *            kc outside (0,1) = off), k1, k2, kmod_l, kmod_u, kmod_max (Sec. 4
+ *            k1 modification, fractions of 2 pi/dx1; kmod_max = 0 = off);
  *   order    particle shape order l (1..3), momentum-conserving interpolation;
  *   correct_j1  1: the Eq. currentcorrection factor multiplies S_j1;
  *   alias    device int [n_alias][2]: (mu, nu1) pairs;
- *   growth   device double [n][n_alias]: max Im(omega) over the refined roots
- *            of that alias (0 if none grows);
+ *   growth   device double [n][n_alias]: max Im(omega) over the roots of that
+ *            alias (0 if none grows);
  *   root     device double [n][n_alias][2] (nullable): the root that gives it.
  * Asynchronous on stream. */
 HYB_API hyb_status hyb_nci_growth(const double* samples, int64_t n, int order, int correct_j1,
                                   const int* alias, int n_alias, double* growth, double* root, void* stream);
+
+/* The same root sets in full (the Appendix relation, as hyb_nci_growth):
+ *   roots    device double [n][n_alias][max_roots][2]: the zeros in the disk,
+ *            unordered, zero-filled after count;
+ *   count    device int [n][n_alias]: how many were found;
+ *   growth   device double [n][n_alias] as in hyb_nci_growth;
+ *   err      device int (nullable), OR-ed: 1 = more than 16 zeros in a disk
+ *            (the rest dropped), 2 = a count the argument principle could not
+ *            resolve (a zero on a contour after every refinement).
+ * Asynchronous on stream. */
+HYB_API hyb_status hyb_nci_roots(const double* samples, int64_t n, int order, int correct_j1, const int* alias,
+                                 int n_alias, int max_roots, double* roots, int* count, double* growth, int* err,
+                                 void* stream);
 
 /* ---------------------------------------------------------------------------
  * NCI surrogate: a small MLP (n_in -> width x depth tanh layers -> 1) trained

@@ -112,6 +112,9 @@ def lib():
             L.hyb_correct_current_noalloc.restype = S
             L.hyb_nci_growth.argtypes = [_V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _V, ctypes.c_int, _V, _V, _V]
             L.hyb_nci_growth.restype = S
+            L.hyb_nci_roots.argtypes = [_V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _V, ctypes.c_int, ctypes.c_int,
+                                        _V, _V, _V, _V, _V]
+            L.hyb_nci_roots.restype = S
             L.hyb_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _V, ctypes.POINTER(_V)]
             L.hyb_mlp_create.restype = S
             L.hyb_mlp_num_params.argtypes = [_V]
@@ -281,11 +284,30 @@ def hyb_nci_growth(samples: int, n: int, order: int, correct_j1: bool, alias: in
                                 _V(growth), _V(root or 0), _V(stream)))
 
 
-def nci_growth(samples, aliases=((0, -1), (0, 0), (0, 1)), order=2, correct_j1=True, want_roots=False):
-    """samples: CUDA float64 tensor [n, 9]; returns growth [n, n_alias] (and roots [n, n_alias] complex)."""
+NCI_ROW = 12     # dt, dx1, dx2, gamma, wp2, filt_kc, filt_w, k1, k2, kmod_l, kmod_u, kmod_max
+
+
+def hyb_nci_roots(samples: int, n: int, order: int, correct_j1: bool, alias: int, n_alias: int, max_roots: int,
+                  roots: int, count: int, growth: int, err: int = 0, stream: int = 0):
+    _check(lib().hyb_nci_roots(_V(samples), n, order, int(bool(correct_j1)), _V(alias), n_alias, max_roots,
+                               _V(roots), _V(count), _V(growth), _V(err or 0), _V(stream)))
+
+
+def nci_rows(samples):
+    """[n, 9] (no k1 modification) or [n, 12] float64 CUDA rows -> contiguous [n, 12]."""
     import torch
-    assert samples.is_cuda and samples.dtype == torch.float64 and samples.shape[1] == 9
-    samples = samples.contiguous()
+    assert samples.is_cuda and samples.dtype == torch.float64 and samples.shape[1] in (9, NCI_ROW)
+    if samples.shape[1] == 9:
+        samples = torch.cat([samples, torch.zeros((samples.shape[0], 3), dtype=samples.dtype,
+                                                  device=samples.device)], dim=1)
+    return samples.contiguous()
+
+
+def nci_growth(samples, aliases=((0, -1), (0, 0), (0, 1)), order=2, correct_j1=True, want_roots=False):
+    """samples: CUDA float64 tensor [n, 9] or [n, 12]; returns growth [n, n_alias]
+    (and the growing roots [n, n_alias] complex)."""
+    import torch
+    samples = nci_rows(samples)
     n = samples.shape[0]
     al = torch.tensor(list(aliases), dtype=torch.int32, device=samples.device).contiguous()
     g = torch.empty((n, len(aliases)), dtype=torch.float64, device=samples.device)
@@ -296,6 +318,24 @@ def nci_growth(samples, aliases=((0, -1), (0, 0), (0, 1)), order=2, correct_j1=T
     if want_roots:
         return g, torch.view_as_complex(r)
     return g
+
+
+def nci_roots(samples, aliases=((0, -1), (0, 0), (0, 1)), order=2, correct_j1=True, max_roots=16):
+    """All roots in each alias's disk: (roots [n, n_alias, max_roots] complex, count [n, n_alias],
+    growth [n, n_alias], err flags)."""
+    import torch
+    samples = nci_rows(samples)
+    n = samples.shape[0]
+    dev = samples.device
+    al = torch.tensor(list(aliases), dtype=torch.int32, device=dev).contiguous()
+    r = torch.zeros((n, len(aliases), max_roots, 2), dtype=torch.float64, device=dev)
+    c = torch.zeros((n, len(aliases)), dtype=torch.int32, device=dev)
+    g = torch.empty((n, len(aliases)), dtype=torch.float64, device=dev)
+    e = torch.zeros(1, dtype=torch.int32, device=dev)
+    hyb_nci_roots(int(samples.data_ptr()), n, order, correct_j1, int(al.data_ptr()), len(aliases), max_roots,
+                  int(r.data_ptr()), int(c.data_ptr()), int(g.data_ptr()), int(e.data_ptr()),
+                  torch.cuda.current_stream().cuda_stream)
+    return torch.view_as_complex(r), c, g, int(e.item())
 
 
 # ---- tensor convenience ----------------------------------------------------------
