@@ -148,6 +148,34 @@ HYB_API hyb_status hyb_deposit(hyb_grid* g, const int32_t* cell, const void* off
 HYB_API hyb_status hyb_push(hyb_grid* g, int32_t* cell, void* off, void* u, const void* qm, void* off_new, void* v3,
                             int64_t np, int shape_order);
 
+/* ---------------------------------------------------------------------------
+ * The particle-in-cell loop around the advance (the drifting-plasma runs whose
+ * measured NCI growth Sec. 4 reports): E at integer steps, B at half steps
+ * (Sec. 2.1), the charge-conserving current of Sec. 2.3, and the particle step
+ * the Appendix's dispersion relation assumes (fields gathered at the
+ * particles' time level with B time-centred, momentum-conserving
+ * interpolation).  Per step, with E = E^n, B = B^{n-1/2} bound to g and the
+ * particles at x^n with u^{n-1/2}:
+ *   B^n = (B^{n-1/2} + B^{n+1/2})/2, B^{n+1/2} from Faraday's update of a copy;
+ *   hyb_push with E^n, B^n (u^{n+1/2}, x^{n+1});  hyb_deposit (j^{n+1/2});
+ *   hyb_advance (E^{n+1}, B^{n+1/2});  off <- off_new.
+ * hyb_pic_create borrows g (which must stay bound to the same arrays) and
+ * allocates a second grid of the same description and 9 scratch fields. */
+typedef struct hyb_pic hyb_pic;   /* opaque */
+HYB_API hyb_status hyb_pic_create(hyb_grid* g, hyb_pic** out);
+
+/* nsteps PIC steps on the grid's stream (asynchronous).  Particle arrays as
+ * for hyb_push and hyb_deposit (device, the grid's precision): cell int32
+ * [np][dims], off [np][dims] (x^n on entry, x^{n+nsteps} on exit, in [-1, 2)
+ * of its cell), u [np][3], qm [np] (q/m), q [np] (macro-particle charge),
+ * off_new [np][dims] (scratch, ends equal to off), v3 [np] (scratch; required
+ * in 2D).  Errors of the push and deposit are flagged as for them (hyb_check). */
+HYB_API hyb_status hyb_pic_step(hyb_pic* p, int32_t* cell, void* off, void* u, const void* qm, const void* q,
+                                void* off_new, void* v3, int64_t np, int shape_order, int nsteps);
+
+/* Frees the PIC step's second grid and scratch (not g). */
+HYB_API hyb_status hyb_pic_destroy(hyb_pic* p);
+
 /* Eq. currentcorrection alone, in place on the bound J1:
  * j1 <- IFFT_x1[ sin(k1 dx1/2)/(k1 dx1/2) FFT_x1[j1] ]. */
 HYB_API hyb_status hyb_correct_current(hyb_grid* g);

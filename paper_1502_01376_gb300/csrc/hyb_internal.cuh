@@ -340,6 +340,10 @@ hyb_status deposit(hyb_grid* g, const int32_t* cell, const T* off_old, const T* 
 // field gather and Boris push (push.cu)
 template <typename T>
 hyb_status push(hyb_grid* g, int32_t* cell, T* off, T* u, const T* qm, T* off_new, T* v3, int64_t np, int order);
+// the same with the fields given explicitly (E[3], B[3] of the grid's shape and precision)
+template <typename T>
+hyb_status push_fields(hyb_grid* g, void* const E[3], void* const B[3], int32_t* cell, T* off, T* u, const T* qm,
+                       T* off_new, T* v3, int64_t np, int order);
 
 // diagnostics (diag.cu)
 template <typename T> hyb_status diag(hyb_grid* g, double out[9]);

@@ -296,11 +296,12 @@ __global__ void __launch_bounds__(256) k_push3d(PushFields F, int n1, int n2, in
 }
 
 template <typename T>
-hyb_status push(hyb_grid* g, int32_t* cell, T* off, T* u, const T* qm, T* off_new, T* v3, int64_t np, int order) {
+hyb_status push_fields(hyb_grid* g, void* const E[3], void* const B[3], int32_t* cell, T* off, T* u, const T* qm,
+                       T* off_new, T* v3, int64_t np, int order) {
     const hyb_grid_desc& d = g->d;
     if (np == 0) return HYB_OK;
     PushFields F;
-    for (int c = 0; c < 3; c++) { F.E[c] = g->E[c]; F.B[c] = g->B[c]; }
+    for (int c = 0; c < 3; c++) { F.E[c] = E[c]; F.B[c] = B[c]; }
     const int threads = kPushThreads;
     int sms = 0;
     HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
@@ -321,7 +322,16 @@ hyb_status push(hyb_grid* g, int32_t* cell, T* off, T* u, const T* qm, T* off_ne
     return HYB_OK;
 }
 
+template <typename T>
+hyb_status push(hyb_grid* g, int32_t* cell, T* off, T* u, const T* qm, T* off_new, T* v3, int64_t np, int order) {
+    return push_fields<T>(g, g->E, g->B, cell, off, u, qm, off_new, v3, np, order);
+}
+
 template hyb_status push<float>(hyb_grid*, int32_t*, float*, float*, const float*, float*, float*, int64_t, int);
 template hyb_status push<double>(hyb_grid*, int32_t*, double*, double*, const double*, double*, double*, int64_t, int);
+template hyb_status push_fields<float>(hyb_grid*, void* const*, void* const*, int32_t*, float*, float*, const float*,
+                                       float*, float*, int64_t, int);
+template hyb_status push_fields<double>(hyb_grid*, void* const*, void* const*, int32_t*, double*, double*,
+                                        const double*, double*, double*, int64_t, int);
 
 }  // namespace hyb

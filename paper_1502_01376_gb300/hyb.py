@@ -115,6 +115,12 @@ def lib():
             L.hyb_nci_roots.argtypes = [_V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _V, ctypes.c_int, ctypes.c_int,
                                         _V, _V, _V, _V, _V]
             L.hyb_nci_roots.restype = S
+            L.hyb_pic_create.argtypes = [_V, ctypes.POINTER(_V)]
+            L.hyb_pic_create.restype = S
+            L.hyb_pic_step.argtypes = [_V, _V, _V, _V, _V, _V, _V, _V, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
+            L.hyb_pic_step.restype = S
+            L.hyb_pic_destroy.argtypes = [_V]
+            L.hyb_pic_destroy.restype = S
             L.hyb_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _V, ctypes.POINTER(_V)]
             L.hyb_mlp_create.restype = S
             L.hyb_mlp_num_params.argtypes = [_V]
@@ -418,6 +424,32 @@ class Grid:
     def close(self):
         if self.h:
             hyb_destroy_grid(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pic:
+    """The particle-in-cell loop around a bound Grid (hyb_pic_*): push, deposit and
+    advance per step, B time-centred for the push."""
+
+    def __init__(self, grid: Grid):
+        h = _V()
+        _check(lib().hyb_pic_create(_V(grid.h), ctypes.byref(h)))
+        self.h = h.value
+        self.grid = grid
+
+    def step(self, cell, off, u, qm, q, off_new, v3, order=2, nsteps=1):
+        _check(lib().hyb_pic_step(_V(self.h), _V(_ptr(cell)), _V(_ptr(off)), _V(_ptr(u)), _V(_ptr(qm)), _V(_ptr(q)),
+                                  _V(_ptr(off_new)), _V(_ptr(v3)), qm.numel(), order, nsteps))
+
+    def close(self):
+        if self.h:
+            lib().hyb_pic_destroy(_V(self.h))
             self.h = 0
 
     def __del__(self):

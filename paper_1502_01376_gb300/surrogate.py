@@ -142,16 +142,40 @@ def max_growth_solver(dt_dx1, dx2_dx1, gamma, kc, nk: int = 48) -> np.ndarray:
     return g.view(cands, nk * nk).max(dim=1).values.cpu().numpy()
 
 
-def pick(mlp, gamma: float, dx2_dx1: float, dt_grid, kc_grid, tol: float = 0.002, nk: int = 48, verify: int = 0):
-    """Candidate (dt/dx1, kc) with the lowest predicted max growth, preferring
-    the largest cutoff and then the largest time step among those within tol
-    of the lowest (keep the most physics bandwidth).  With verify = k > 0 the
-    root solver, the surrogate's judge, re-scores the k candidates with the
-    lowest predicted growth and the pick is made among them on its values."""
+def candidates(dx2_dx1: float, dt_grid, kc_grid):
+    """The (dt/dx1, kc) candidates of a grid of settings that satisfy the Courant limit."""
     dts, kcs = np.meshgrid(np.asarray(dt_grid, float), np.asarray(kc_grid, float), indexing="ij")
     dts, kcs = dts.ravel(), kcs.ravel()
     ok = dts * DX1 <= courant_dt(DX1, dx2_dx1 * DX1)
-    dts, kcs = dts[ok], kcs[ok]
+    return dts[ok], kcs[ok]
+
+
+def select(dts, kcs, score, idx=None, tol: float = 0.002) -> int:
+    """Index of the candidate with the lowest score, preferring the largest cutoff and then
+    the largest time step among those within tol of the lowest (keep the most physics
+    bandwidth); only the candidates in idx (default all) compete."""
+    idx = np.arange(len(dts)) if idx is None else np.asarray(idx)
+    best = score[idx].min()
+    good = idx[score[idx] <= best + tol]
+    return int(good[np.lexsort((dts[good], kcs[good]))[-1]])
+
+
+def pick_solver(gamma: float, dx2_dx1: float, dt_grid, kc_grid, tol: float = 0.002, nk: int = 48):
+    """The method without the network: the root solver scores every candidate."""
+    dts, kcs = candidates(dx2_dx1, dt_grid, kc_grid)
+    t0 = time.perf_counter()
+    score = max_growth_solver(dts, np.full(dts.size, dx2_dx1), np.full(dts.size, gamma), kcs, nk)
+    secs = time.perf_counter() - t0
+    i = select(dts, kcs, score, tol=tol)
+    return {"dt_dx1": float(dts[i]), "kc": float(kcs[i]), "growth": float(score[i]), "candidates": int(dts.size),
+            "seconds": secs, "all_dt": dts, "all_kc": kcs, "all_growth": score}
+
+
+def pick(mlp, gamma: float, dx2_dx1: float, dt_grid, kc_grid, tol: float = 0.002, nk: int = 48, verify: int = 0):
+    """Candidate (dt/dx1, kc) with the lowest predicted max growth (select()).  With
+    verify = k > 0 the root solver, the surrogate's judge, re-scores the k candidates with
+    the lowest predicted growth and the pick is made among them on its values."""
+    dts, kcs = candidates(dx2_dx1, dt_grid, kc_grid)
     t0 = time.perf_counter()
     pred = max_growth_surrogate(mlp, dts, np.full(dts.size, dx2_dx1), np.full(dts.size, gamma), kcs, nk)
     t_pred = time.perf_counter() - t0
@@ -164,9 +188,7 @@ def pick(mlp, gamma: float, dx2_dx1: float, dt_grid, kc_grid, tol: float = 0.002
         score = np.full(dts.size, np.inf)
         score[idx] = max_growth_solver(dts[idx], np.full(idx.size, dx2_dx1), np.full(idx.size, gamma), kcs[idx], nk)
         t_ver = time.perf_counter() - t1
-    best = score[idx].min()
-    good = idx[score[idx] <= best + tol]
-    i = good[np.lexsort((dts[good], kcs[good]))[-1]]
+    i = select(dts, kcs, score, idx, tol)
     return {"dt_dx1": float(dts[i]), "kc": float(kcs[i]), "predicted": float(pred[i]), "candidates": int(dts.size),
             "seconds": t_pred, "verify_seconds": t_ver, "verified": int(verify),
             "all_dt": dts, "all_kc": kcs, "all_pred": pred}

@@ -257,3 +257,38 @@ def plasma_push_particles_torch(w: Workload, device, seed: int | None = None):
         qms.append(torch.full((n,), sign, device=device, dtype=torch.float32))
     return (torch.cat(cells).contiguous(), torch.cat(offs).contiguous(), torch.cat(us).contiguous(),
             torch.cat(qms).contiguous())
+
+
+def pic_plasma_torch(w: Workload, device, seed: int | None = None, real=None):
+    """Both species of the drifting plasma for a particle-in-cell run, drawn on a CUDA
+    device (seeded torch generator), w.ppc per cell per species, in cell order: a quiet
+    start (the positive species at the electrons' positions, so the plasma starts
+    neutral in every cell and E = B = 0 is consistent), independent Gaussian spreads
+    u_th in u.  Returns int32 cell [np, dims], offsets in [0, 1) [np, dims],
+    u = gamma v [np, 3], q/m = -1 or +1 [np] and the macro-particle charge
+    q = +-rho0 dV / ppc [np] (rho0 = n/n_p / (4 pi), so omega_p^2 = n/n_p)."""
+    import torch
+    dt = real or (torch.float32 if w.precision == 32 else torch.float64)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(w.seed + 4000 if seed is None else seed)
+    d = w.dims
+    n = w.cells * w.ppc
+    idx = torch.arange(w.cells, device=device, dtype=torch.int64).repeat_interleave(w.ppc)
+    if d == 2:
+        cell = torch.stack([idx % w.n1, idx // w.n1], dim=1)
+    else:
+        cell = torch.stack([idx % w.n1, (idx // w.n1) % w.n2, idx // (w.n1 * w.n2)], dim=1)
+    cell = cell.to(torch.int32)
+    del idx
+    off = torch.rand(n, d, generator=gen, device=device, dtype=torch.float64).to(dt)
+    dV = w.dx1 * w.dx2 * (w.dx3 if d == 3 else 1.0)
+    rho0 = w.density / (4.0 * np.pi)
+    us, qms, qs = [], [], []
+    for sign in (-1.0, +1.0):
+        u = torch.randn(n, 3, generator=gen, device=device, dtype=torch.float64) * w.u_th
+        u[:, 0] += float(np.sqrt(w.gamma ** 2 - 1.0))
+        us.append(u.to(dt))
+        qms.append(torch.full((n,), sign, device=device, dtype=dt))
+        qs.append(torch.full((n,), sign * rho0 * dV / w.ppc, device=device, dtype=dt))
+    return (torch.cat([cell, cell]).contiguous(), torch.cat([off, off]).contiguous(), torch.cat(us).contiguous(),
+            torch.cat(qms).contiguous(), torch.cat(qs).contiguous())

@@ -1,7 +1,7 @@
 """Surrogate network kernels (forward, backward, Adam) against the FP64
 oracle, training on the GPU root solver's data, and what the trained network
-gains: the filter cutoff and time step it picks give less NCI growth (checked
-by the root solver) than the unfiltered run, and it scans settings faster."""
+gains over the root solver alone: the same pick of the filter cutoff and time
+step at a fraction of the scan time, confirmed by a measured PIC run."""
 import time
 
 import numpy as np
@@ -56,35 +56,53 @@ def test_adam_step_matches_oracle_update():
     net.close()
 
 
-def test_surrogate_trains_and_picks_settings_with_less_growth():
+def test_surrogate_pick_against_the_solver_and_a_measured_run():
+    """What the trained network gains over the method without it, for the cutoff and time step
+    of the drifting-plasma run (gamma 50, square cells; 56 candidates x 48^2 modes): its own
+    pick is far below the unfiltered growth at under a quarter of the root solver's scan time;
+    with the root solver judging the network's 16 most promising candidates (the solver stays
+    the judge), the pick is the exhaustive scan's (within a stated growth tolerance) with 2/7
+    of its solver work.  A PIC run with those settings grows no faster than the root solver
+    predicts for its modes."""
     need_gpu()
     hyb = hyb_module()
-    from paper_1502_01376_gb300 import surrogate as sg
+    from paper_1502_01376_gb300 import pic, surrogate as sg
     X, y, kept, n = sg.dataset(60000, seed=11)
     assert kept < n                                # Courant-unstable samples are flagged out
     Xv, yv, _, _ = sg.dataset(8000, seed=12)
     net = hyb.MLP(6, 256, 4, seed=5)
-    hist = sg.train(net, X, y, steps=1500, batch=8192, lr=2e-3, seed=1)
+    hist = sg.train(net, X, y, steps=3000, batch=8192, lr=2e-3, seed=1)
     assert hist[-50:].mean() < 0.3 * hist[:10].mean()
     pred = net.forward(Xv)
-    mse = float(torch.mean((pred - yv) ** 2))
-    var = float(torch.var(yv))
-    assert mse < 0.5 * var, (mse, var)
-    # pick the cutoff and dt for the drifting-plasma run (gamma 50, square cells)
+    r2 = 1.0 - float(torch.mean((pred - yv) ** 2)) / float(torch.var(yv))
     dts = np.arange(0.2, 0.51, 0.05)
     kcs = np.arange(0.3, 1.01, 0.1)
+    sg.pick(net, 50.0, 1.0, dts, kcs)              # first call sizes the activation buffers
+    sg.pick_solver(50.0, 1.0, dts[:1], kcs[:1])    # and loads the solver
     res = sg.pick(net, 50.0, 1.0, dts, kcs)
-    confirmed = sg.max_growth_solver([res["dt_dx1"]], [1.0], [50.0], [res["kc"]])[0]
-    unfiltered = sg.max_growth_solver([0.5], [1.0], [50.0], [1.0])[0]
-    assert confirmed <= unfiltered
-    # pruned by the surrogate, judged by the root solver on the 8 most promising candidates
-    resv = sg.pick(net, 50.0, 1.0, dts, kcs, verify=8)
-    confirmed_v = sg.max_growth_solver([resv["dt_dx1"]], [1.0], [50.0], [resv["kc"]])[0]
-    assert confirmed_v <= unfiltered
-    assert confirmed_v <= confirmed + 2e-3
-    t0 = time.perf_counter()
-    sg.max_growth_solver(res["all_dt"], np.ones(res["candidates"]), np.full(res["candidates"], 50.0), res["all_kc"])
-    t_solver = time.perf_counter() - t0
-    print(f"pick {res['dt_dx1']:.2f} {res['kc']:.2f} predicted {res['predicted']:.4f} confirmed {confirmed:.4f} "
-          f"unfiltered {unfiltered:.4f}; scan {res['seconds']:.4f} s vs root solver {t_solver:.4f} s")
+    ex = sg.pick_solver(50.0, 1.0, dts, kcs)
+    confirmed = float(sg.max_growth_solver([res["dt_dx1"]], [1.0], [50.0], [res["kc"]])[0])
+    resv = sg.pick(net, 50.0, 1.0, dts, kcs, verify=16)
+    confirmed_v = float(sg.max_growth_solver([resv["dt_dx1"]], [1.0], [50.0], [resv["kc"]])[0])
+    unfiltered = float(sg.max_growth_solver([0.5], [1.0], [50.0], [1.0])[0])
+    print(f"R2 {r2:.3f}; pick {res['dt_dx1']:.2f} {res['kc']:.2f} solver growth {confirmed:.4f}; verified pick "
+          f"{resv['dt_dx1']:.2f} {resv['kc']:.2f} {confirmed_v:.4f}; exhaustive {ex['dt_dx1']:.2f} {ex['kc']:.2f} "
+          f"{ex['growth']:.4f}; unfiltered {unfiltered:.4f}; scan {res['seconds']:.4f} s vs {ex['seconds']:.4f} s")
+    assert r2 > 0.7, r2
+    # the network alone (56 candidates scored in one forward pass): far below the unfiltered growth
+    assert confirmed < 0.25 * unfiltered
+    assert res["seconds"] < 0.25 * ex["seconds"]
+    # pruned by the network, judged by the solver on 16 candidates: the exhaustive pick's growth
+    # (within 0.002) with 16/56 of the solver's work, in under 3/4 of its time (the solver's
+    # time does not fall in proportion: its slowest threads set it)
+    assert confirmed_v <= ex["growth"] + 0.002
+    assert resv["verified"] * 3.5 <= ex["candidates"]
+    assert resv["seconds"] + resv["verify_seconds"] < 0.75 * ex["seconds"]
+    # the picked settings in a PIC run of the Table 1 plasma: no growth above the prediction
+    w = pic.TABLE1.scaled(dt=resv["dt_dx1"] * pic.TABLE1.dx1, filt_kc=resv["kc"])
+    h = pic.run(w, steps=int(round(480.0 / w.dt)), every=10)
+    meas = pic.growth_rate(h.t, h.energy[:, 1])
+    pred_run = pic.predicted(w, aliases=pic.ALL_ALIASES)[0]
+    print(f"PIC at the pick: measured {meas:.4f}, predicted {pred_run:.4f}")
+    assert meas <= 1.5 * pred_run + 2e-3
     net.close()
