@@ -266,7 +266,8 @@ def test_advance_host_matches_device(orc):
 @pytest.mark.parametrize("n1,n2", [(4096, 1024), (1024, 37), (512, 4), (2048, 70)])
 def test_fused_host_step_matches_device_step(n1, n2):
     """One fused step from and to host arrays (copies and compute pipelined over chunks of rows,
-    halo rows taken before the rows they come from are updated) equals the device-array step."""
+    halo rows taken before the rows they come from are updated) equals the device-array step
+    (bit for bit where both run the same kernel, to FP32 rounding at n1 = 4096)."""
     need_gpu()
     hyb = hyb_module()
     w = wl.Workload("hp", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.1, precision=32, filt_kc=0.5, filt_w=0.2, seed=17)
@@ -288,7 +289,12 @@ def test_fused_host_step_matches_device_step(n1, n2):
     gh.check()
     torch.cuda.synchronize()
     for a, b, dev in zip(H[:6], D[:6], Dh[:6]):
-        assert torch.equal(a, b.cpu()), float((a - b.cpu()).abs().max())
+        if n1 == 4096:
+            # the single grid runs the paired-transform kernel, the chunked host step the
+            # row-by-row one: the same step up to FP32 rounding order
+            assert rel_err(a.numpy(), b.cpu().numpy()) < 1e-5
+        else:
+            assert torch.equal(a, b.cpu()), float((a - b.cpu()).abs().max())
         assert torch.equal(dev.cpu(), a)
     gd.close()
     gh.close()
