@@ -332,6 +332,8 @@ __global__ void __launch_bounds__(pq::NT, 1) k_fused_pair(PairArgs P) {
         if (is_fwd(job)) {
             if (staged_round != r) issue_stage(r);
             float b1v[16];
+            if (job == PJ_A && s == 0)           // B1(p), which the next A job reads, into L2 now
+                bulk_prefetch_l2(a.B[0] + (size_t)rowp(rr) * N, 4 * N);
             if (job == PJ_A && rr >= 1) {        // B1(p-1) + a2 E3(p-1), loaded while the rows land
                 const float* b1 = a.B[0] + (size_t)rowp(rr - 1) * N;
                 const float* e3 = a.E[2] + (size_t)rowp(rr - 1) * N;

@@ -132,4 +132,10 @@ __device__ __forceinline__ void tm_st8_at(uint32_t ta, const float (&r)[NN]) {
     tm_st8(ta, t);
 }
 
+
+// bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) of global memory into L2
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(src), "r"(bytes) : "memory");
+}
+
 }  // namespace hyb
