@@ -365,6 +365,11 @@ HYB_API hyb_status hyb_mlp_destroy(hyb_mlp* m);
 /* Which advance path a grid runs: 1 three-pass, 2 fused, 3 three-pass with DFT-GEMM. */
 HYB_API int hyb_grid_path(const hyb_grid* g);
 
+/* Name of the kernel that does a step's work on this grid's path (the fused kernel's name
+ * on path 2; a description of the step on the others).  A static string owned by the
+ * library; "" for a null grid. */
+HYB_API const char* hyb_step_kernel(const hyb_grid* g);
+
 /* Number of kernel launches one hyb_advance step of this grid issues. */
 HYB_API int hyb_launches_per_step(const hyb_grid* g);
 

@@ -680,6 +680,22 @@ hyb_status fused_advance(hyb_grid* g, int nsteps) {
 
 int fused_launches_per_step(const hyb_grid* g) { return (g->fused && g->fused->flags) ? 1 : 2; }
 
+const char* fused_step_kernel(const hyb_grid* g) {
+    switch (g->d.n1) {
+    case 512: return "k_fused2d<512>";
+    case 1024: return "k_fused2d<1024>";
+    case 2048: return "k_fused2d<2048>";
+    default: break;
+    }
+    const FusedPlan* P = g->fused;
+    FusedBatch fb;
+    fb.inst[0] = fused_inst(g);
+    fb.n_items = P->n_items;
+    fb.flags = P->flags;
+    fb.n_strips = P->n_strips;
+    return fused_pair_applies(fb) ? "k_fused_pair" : "k_fused_tm";
+}
+
 // ------------------------------------------------------------------ one step from and to host arrays
 // The copies over the host link dominate this step, so it is pipelined over chunks of rows:
 // stream 0 copies the rows in (the last row first, then chunk by chunk), stream 1 fills the

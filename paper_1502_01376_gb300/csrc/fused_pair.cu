@@ -29,9 +29,10 @@
 // kept doubled (2F); the inverse scales by 1/(2 N).
 //
 // A CTA has two groups of 256 threads.  A strip's work is a list of jobs,
-// each a pair of transforms (or an epilogue alone), run in rounds (one job
-// per group per round, a CTA barrier between rounds) from a schedule the host
-// computes from the jobs' dependencies:
+// each a pair of transforms (or an epilogue alone), split between the groups
+// by a list schedule the host computes from the jobs' dependencies and costs;
+// a group runs its list in order and, before a job that reads what the other
+// group writes, waits for that job's done flag in shared memory:
 //   P1  F(E1(p0), E1(p0-1))            P2  F(E2(p0-1), B3(p0-1))
 //   P3  B3'(p0-1) from P1, P2; B1'(p0-1)            (the strip's prologue)
 //   A   F(E2, E3)(p)          -> slot EA(p)

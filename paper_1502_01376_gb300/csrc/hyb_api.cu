@@ -463,6 +463,13 @@ hyb_status hyb_set_kernel_events(hyb_grid* g, void* start, void* stop) {
 
 int hyb_grid_path(const hyb_grid* g) { return g ? g->path : 0; }
 
+const char* hyb_step_kernel(const hyb_grid* g) {
+    if (!g) return "";
+    if (g->path == 2) return fused_step_kernel(g);
+    if (g->path == 3) return "dft-gemm three-pass step";
+    return g->d.dims == 20 ? "quasi-3D step" : "three-pass step";
+}
+
 int hyb_launches_per_step(const hyb_grid* g) {
     if (!g) return 0;
     if (g->path == 2) return fused_launches_per_step(g);

@@ -138,6 +138,8 @@ def lib():
             L.hyb_mlp_destroy.restype = S
             L.hyb_mlp_launch_count.argtypes = [_V]
             L.hyb_mlp_launch_count.restype = ctypes.c_int64
+            L.hyb_step_kernel.argtypes = [_V]
+            L.hyb_step_kernel.restype = ctypes.c_char_p
             L.hyb_launches_per_step.argtypes = [_V]
             L.hyb_launches_per_step.restype = ctypes.c_int
             L.hyb_wait_selftest.argtypes = [ctypes.c_int, ctypes.c_double, _V]
@@ -243,6 +245,10 @@ def hyb_set_kernel_events(g: int, start: int, stop: int):
 
 def hyb_grid_path(g: int) -> int:
     return lib().hyb_grid_path(_V(g))
+
+
+def hyb_step_kernel(g: int) -> str:
+    return lib().hyb_step_kernel(_V(g)).decode()
 
 
 def hyb_launches_per_step(g: int) -> int:
@@ -420,6 +426,10 @@ class Grid:
     @property
     def launches_per_step(self):
         return hyb_launches_per_step(self.h)
+
+    @property
+    def step_kernel(self):
+        return hyb_step_kernel(self.h)
 
     def close(self):
         if self.h:

@@ -47,9 +47,18 @@ def test_batch_equals_single_grids_and_oracle(orc):
     for g in singles:
         g.advance(nst)
     torch.cuda.synchronize()
-    for i in range(len(ws)):
-        for a, b in zip(bt[i][0] + bt[i][1], st[i][0] + st[i][1]):
-            assert torch.equal(a, b), (SIZES[i])
+    def same_as_singles(what):
+        for i in range(len(ws)):
+            # a single 4096-wide grid with one strip per SM runs the paired-transform kernel, the
+            # batch the per-field one: the same arithmetic in another rounding order
+            exact = singles[i].step_kernel != "k_fused_pair"
+            for a, b in zip(bt[i][0] + bt[i][1], st[i][0] + st[i][1]):
+                if exact:
+                    assert torch.equal(a, b), (SIZES[i], what)
+                else:
+                    assert float((a - b).abs().max() / b.abs().max()) < 1e-5, (SIZES[i], what)
+
+    same_as_singles("first steps")
     # oracle on two of them
     for i in (1, 5):
         w = ws[i]
@@ -60,7 +69,7 @@ def test_batch_equals_single_grids_and_oracle(orc):
         tol = 1e-5 if w.precision == 32 else 1e-12
         for a, b in zip(bt[i][0] + bt[i][1], Eo + Bo):
             assert rel_err(to_np(a), b) < tol
-    # autotune, then the batch still reproduces the single grids exactly
+    # autotune, then the batch still reproduces the single grids
     batch.tune(2)
     for n1 in (512, 1024, 2048, 4096):
         assert 2 <= batch.rows_per_strip(n1) <= 64
@@ -68,9 +77,7 @@ def test_batch_equals_single_grids_and_oracle(orc):
     for g in singles:
         g.advance(3)
     torch.cuda.synchronize()
-    for i in range(len(ws)):
-        for a, b in zip(bt[i][0] + bt[i][1], st[i][0] + st[i][1]):
-            assert torch.equal(a, b), (SIZES[i], "after tune")
+    same_as_singles("after tune")
     # heights set by hand (odd ones, and one row, clamped to two-row strips) give the same results
     for n1, h in ((512, 7), (1024, 5), (2048, 17), (4096, 1)):
         batch.set_rows_per_strip(n1, h)
@@ -82,7 +89,5 @@ def test_batch_equals_single_grids_and_oracle(orc):
     for g in singles:
         g.advance(2)
     torch.cuda.synchronize()
-    for i in range(len(ws)):
-        for a, b in zip(bt[i][0] + bt[i][1], st[i][0] + st[i][1]):
-            assert torch.equal(a, b), (SIZES[i], "after set_rows_per_strip")
+    same_as_singles("after set_rows_per_strip")
     batch.close()
