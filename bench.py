@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and fp64 comparison")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the short batched, 3D and surrogate measurements of the default run")
     ap.add_argument("--quick", action="store_true",
                     help="profiling mode: random band-limited J instead of the particle deposit, no extras")
     ap.add_argument("--n1", type=int, default=4096,
@@ -82,16 +84,14 @@ def peaks():
 
 
 KERNEL_SOURCES = {
-    "k_fused_pair": ("fused_pair.cu", "tm_dev.cuh", "fused_dev.cuh", "fused_api.cuh", "packed_dev.cuh"),
     "k_fused_tm": ("fused_tm.cu", "tm_dev.cuh", "fused_dev.cuh", "fused_api.cuh", "packed_dev.cuh"),
 }
 KERNEL_PROFILES = {
-    "k_fused_pair": "fused_pair_drift_plasma_4096x1024.md",
     "k_fused_tm": "fused_tm_drift_plasma_4096x1024.md",
 }
 
 
-def kernel_source_hash(kernel="k_fused_pair"):
+def kernel_source_hash(kernel="k_fused_tm"):
     """Hash of the kernel's sources with line comments and blank lines dropped, so that the
     profile summary stays matched to the code through comment-only edits."""
     h = hashlib.sha256()
@@ -142,6 +142,7 @@ class ClockSampler:
         self.rows = []
         self.proc = None
         self.t0 = self.t1 = None
+        self.spans = []                 # every marked (begin, end) interval
 
     def start(self):
         try:
@@ -162,6 +163,8 @@ class ClockSampler:
             self.t0 = time.time()
         else:
             self.t1 = time.time()
+            if self.t0:
+                self.spans.append((self.t0, self.t1))
 
     def stop(self):
         if self.proc:
@@ -175,7 +178,7 @@ class ClockSampler:
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        inside = [r for t, r in self.rows if self.t0 and self.t1 and self.t0 <= t <= self.t1]
+        inside = [r for t, r in self.rows if any(a <= t <= b for a, b in self.spans)]
         use = inside if inside else [r for _, r in self.rows]
         sm = [float(r[0]) for r in use if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in use if r[1].replace(".", "").isdigit()]
@@ -278,7 +281,7 @@ def time_steps(step_fn, K, W, stream, flush, sampler):
     return statistics.mean(a.elapsed_time(b) for a, b in ev)
 
 
-def x1_compare(hyb, w, arrs, stream, flush, sampler, args, dev):
+def x1_compare(hyb, w, arrs, stream, flush, sampler, steps_, warmup, dev):
     """Time the three-pass advance with the radix x1 FFT (path 1) and with the
     DFT-GEMM (path 3) on the same inputs; per-field relative L2 error of each
     after 3 steps against the FP64 GPU path (parity-tested against the oracle)."""
@@ -295,8 +298,8 @@ def x1_compare(hyb, w, arrs, stream, flush, sampler, args, dev):
         torch.cuda.synchronize()
         fin[path] = [f.double() if path != 64 else f for f in F[:6]]
         if path != 64:
-            steps = args.steps if path == 1 else max(3, min(args.steps, 20))
-            out[f"ms_path{path}"] = time_steps(lambda: g.advance(1), steps, args.warmup, stream, flush, sampler)
+            steps = steps_ if path == 1 else max(3, min(steps_, 20))
+            out[f"ms_path{path}"] = time_steps(lambda: g.advance(1), steps, warmup, stream, flush, sampler)
             out[f"launches_path{path}"] = g.launches_per_step
         g.close()
         del F
@@ -306,38 +309,34 @@ def x1_compare(hyb, w, arrs, stream, flush, sampler, args, dev):
     return out
 
 
-def run_surrogate(args):
-    """The learned part: 200k (dt/dx1, dx2/dx1, gamma, kc, k1, k2) samples labelled by
+def measure_surrogate(hyb, sg, steps, warmup, sampler=None, n_samples=200000):
+    """The learned part: n_samples (dt/dx1, dx2/dx1, gamma, kc, k1, k2) samples labelled by
     the FP64 GPU root solver of the NCI dispersion relation, the MLP 6 -> 256 x 4 -> 1
     trained by the library's own kernels, then the pick of filter cutoff and dt for
     the drifting-plasma run (gamma 50, square cells), judged by the root solver."""
     import numpy as np
     import torch
-    torch.cuda.set_device(0)
-    from paper_1502_01376_gb300 import build, hyb, surrogate as sg
-    build.build()
-    sampler = ClockSampler(0)
-    sampler.start()
-    time.sleep(0.5)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    X, y, kept, n = sg.dataset(200000, seed=21)
+    X, y, kept, n = sg.dataset(n_samples, seed=21)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     Xv, yv, _, _ = sg.dataset(20000, seed=22)
     net = hyb.MLP(6, 256, 4, seed=5)
-    steps, batch = max(args.steps, 500), 8192
-    sg.train(net, X, y, steps=args.warmup, batch=batch, lr=2e-3, seed=0)       # warm-up steps (not timed)
+    batch = 8192
+    sg.train(net, X, y, steps=warmup, batch=batch, lr=2e-3, seed=0)       # warm-up steps (not timed)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler.mark(True)
+    if sampler:
+        sampler.mark(True)
     n_launch0 = net.launch_count()
     ev0.record()
     hist = sg.train(net, X, y, steps=steps, batch=batch, lr=2e-3, seed=1)
     ev1.record()
     n_launches = net.launch_count() - n_launch0
     torch.cuda.synchronize()
-    sampler.mark(False)
+    if sampler:
+        sampler.mark(False)
     train_ms = ev0.elapsed_time(ev1)
     pred = net.forward(Xv)
     mse = float(torch.mean((pred - yv) ** 2))
@@ -347,35 +346,43 @@ def run_surrogate(args):
     sg.pick(net, 50.0, 1.0, dts, kcs)                   # first call sizes the activation buffers
     res = sg.pick(net, 50.0, 1.0, dts, kcs)
     confirmed = float(sg.max_growth_solver([res["dt_dx1"]], [1.0], [50.0], [res["kc"]])[0])
-    # the surrogate prunes, the root solver judges the 8 most promising candidates
-    resv = sg.pick(net, 50.0, 1.0, dts, kcs, verify=8)
+    # the surrogate prunes, the root solver judges the 16 most promising candidates
+    resv = sg.pick(net, 50.0, 1.0, dts, kcs, verify=16)
     confirmed_v = float(sg.max_growth_solver([resv["dt_dx1"]], [1.0], [50.0], [resv["kc"]])[0])
     unfiltered = float(sg.max_growth_solver([0.5], [1.0], [50.0], [1.0])[0])
-    sg.max_growth_solver(res["all_dt"][:1], np.ones(1), np.full(1, 50.0), res["all_kc"][:1])   # warm
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    solver_all = sg.max_growth_solver(res["all_dt"], np.ones(res["candidates"]), np.full(res["candidates"], 50.0),
-                                      res["all_kc"])
-    torch.cuda.synchronize()
-    t_solver = time.perf_counter() - t1
-    best_solver = float(np.min(solver_all))
-    sampler.stop()
+    ex = sg.pick_solver(50.0, 1.0, dts[:1], kcs[:1])    # warm
+    ex = sg.pick_solver(50.0, 1.0, dts, kcs)
     net.close()
-    line = {"metric": "NCI surrogate training samples/s (MLP 6->256x4->1, BF16 operands, FP32 accumulation)",
-            "value": steps * batch / (train_ms / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": train_ms / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "gpu_launches": n_launches, "clocks": sampler.summary(),
-            "config": {"workload": "nci_surrogate_200k", "samples": n, "kept_below_courant": kept,
+    return {"value": steps * batch / (train_ms / 1e3), "unit": "samples/s", "steps": steps,
+            "ms_per_step": train_ms / steps, "gpu_launches": n_launches,
+            "config": {"workload": f"nci_surrogate_{n_samples // 1000}k", "samples": n, "kept_below_courant": kept,
                        "label_seconds": t_data, "batch": batch, "loss_first": float(hist[:10].mean()),
-                       "loss_last": float(hist[-50:].mean()), "val_mse_over_var": mse / var,
+                       "loss_last": float(hist[-50:].mean()), "val_r2": 1.0 - mse / var,
                        "pick": {"dt_dx1": res["dt_dx1"], "kc": res["kc"], "predicted": res["predicted"],
-                                "solver_at_pick": confirmed, "solver_best_candidate": best_solver,
-                                "solver_unfiltered_dt0.5": unfiltered, "candidates": res["candidates"],
-                                "surrogate_scan_s": res["seconds"], "solver_scan_s": t_solver,
+                                "solver_at_pick": confirmed, "solver_unfiltered_dt0.5": unfiltered,
+                                "candidates": res["candidates"], "surrogate_scan_s": res["seconds"],
+                                "exhaustive_solver": {"dt_dx1": ex["dt_dx1"], "kc": ex["kc"], "growth": ex["growth"],
+                                                      "seconds": ex["seconds"]},
                                 "verified_pick": {"dt_dx1": resv["dt_dx1"], "kc": resv["kc"], "solver": confirmed_v,
                                                   "candidates_solved": resv["verified"],
                                                   "seconds": resv["seconds"] + resv["verify_seconds"]}}}}
+
+
+def run_surrogate(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1502_01376_gb300 import build, hyb, surrogate as sg
+    build.build()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.5)
+    r = measure_surrogate(hyb, sg, max(args.steps, 500), args.warmup, sampler)
+    sampler.stop()
+    line = {"metric": "NCI surrogate training samples/s (MLP 6->256x4->1, BF16 operands, FP32 accumulation)",
+            "value": r["value"], "unit": r["unit"], "n_gpus": 1, "steps": r["steps"],
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "gpu_launches": r["gpu_launches"], "clocks": sampler.summary(), "config": r["config"]}
     print(json.dumps(line), flush=True)
 
 
@@ -447,6 +454,84 @@ def run_push(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_batched(hyb, wl, steps, warmup, stream, flush, sampler, dev, strips=""):
+    """16 uneven 2D FP32 grids (sizes drawn with seed 3) plus the quasi-3D modes m = 0, 1, 2
+    on 2048 x 512 complex fields, advanced together as one batch (CUDA-graph step)."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(3)
+    descs, bufs, cells, alg_bytes = [], [], 0, 0
+    sizes = [(int(rng.choice([512, 1024, 2048, 4096])), int(rng.choice([128, 256, 512, 1024]))) for _ in range(16)]
+    for i, (n1, n2) in enumerate(sizes):
+        w = wl.Workload(f"b{i}", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2,
+                        seed=100 + i)
+        descs.append(hyb.desc_from_workload(w))
+        E0, B0 = wl.band_limited_fields(w)
+        J0, _ = wl.band_limited_fields(w.scaled(seed=w.seed + 50))
+        mk = lambda arrs: [torch.from_numpy(a.astype(np.float32)).to(dev) for a in arrs]
+        bufs.append((mk(E0), mk(B0), mk(J0)))
+        cells += n1 * n2
+        alg_bytes += 60 * n1 * n2
+    nz, nr = 2048, 512
+    for m in (0, 1, 2):
+        dt = 0.9 * 2 / np.sqrt(np.pi ** 2 / 0.2 ** 2 + (4 * m * m + 6) / 0.2 ** 2)
+        descs.append(hyb.make_desc(dims=20, n1=nz, n2=nr, dx1=0.2, dx2=0.2, dt=min(0.08, dt), precision=32,
+                                   filt_kc=0.5, filt_w=0.2, azimuthal_m=m))
+        cf = lambda s_: [(torch.randn(nr, nz, device=dev) + 1j * torch.randn(nr, nz, device=dev)).to(torch.complex64) * s_
+                         for _ in range(3)]
+        bufs.append((cf(1e-3), cf(1e-3), cf(1e-3)))
+        cells += nz * nr
+        alg_bytes += 120 * nz * nr
+    b = hyb.Batch(descs, stream)
+    for i, (E, B, J) in enumerate(bufs):
+        b.bind(i, E, B, J)
+    t0 = time.perf_counter()
+    if strips:
+        for kv in strips.split(","):
+            n1_, h_ = (int(v) for v in kv.split(":"))
+            b.set_rows_per_strip(n1_, h_)
+    else:
+        b.tune(3)
+    tune_s = time.perf_counter() - t0
+    ms = time_steps(lambda: b.advance(1), steps, warmup, stream, flush, sampler)
+    lps = b.launches_per_step
+    config = {"workload": "batched_16x2d_uneven_plus_quasi3d_m012_2048x512", "instances_2d": sizes,
+              "quasi3d_modes": [0, 1, 2], "quasi3d_grid": [nz, nr],
+              "strips": "set by --batch-strips" if strips else "autotuned", "autotune_s": tune_s,
+              "rows_per_strip": {n1: b.rows_per_strip(n1) for n1 in (512, 1024, 2048, 4096)},
+              "current": "band-limited random J (no deposit in the timed step)",
+              "l2": "flushed between timed steps (256 MB write)"}
+    b.close()
+    return ms, cells, alg_bytes, lps, config
+
+
+def measure_3d(hyb, wl, steps, warmup, stream, flush, sampler, dev, rows3d=256):
+    """3D FP32 drifting-plasma grid: the x1 transform as radix FFT (path 1) and as split-BF16
+    DFT-GEMM (path 3), both timed, per-field error of each after 3 steps against the FP64 GPU
+    path from the same initial state; and the radix path with k1-resident E, B."""
+    import torch
+    w = wl.DRIFT_PLASMA_3D
+    if rows3d != w.n2:
+        w = w.scaled(n2=rows3d, n3=rows3d, name=f"drift_plasma_3d_1024x{rows3d}x{rows3d}_f32")
+    E0, B0 = wl.band_limited_fields(w)
+    J0, _ = wl.band_limited_fields(w.scaled(seed=w.seed + 50))
+    arrs = list(E0) + list(B0) + list(J0)
+    x1 = x1_compare(hyb, w, arrs, stream, flush, sampler, steps, warmup, dev)
+    g = hyb.Grid(hyb.desc_from_workload(w, path=1), stream)
+    F = [torch.from_numpy(a).to(device=dev, dtype=torch.float32) for a in arrs]
+    g.bind(F[0:3], F[3:6], F[6:9])
+    g.set_resident(True)
+    x1["ms_path1_resident"] = time_steps(lambda: g.advance(1), steps, warmup, stream, flush, sampler)
+    x1["launches_path1_resident"] = g.launches_per_step
+    g.close()
+    del F
+    best = min((1, 3), key=lambda p_: x1[f"ms_path{p_}"])
+    config = {"workload": w.name, "path": {1: "three-pass radix FFT", 3: "three-pass DFT-GEMM"}[best],
+              "x1_transform": x1, "current": "band-limited random J",
+              "l2": "flushed between timed steps (256 MB write)"}
+    return x1[f"ms_path{best}"], w.cells, 60 * w.cells, x1[f"launches_path{best}"], config
+
+
 def run_other(args):
     """Measurement lines for the non-headline configurations (same JSON keys)."""
     import numpy as np
@@ -461,70 +546,16 @@ def run_other(args):
     sampler.start()
     time.sleep(0.5)
     peak, src = peaks()
-    rng = np.random.default_rng(3)
     extra = {}
     if args.workload == "batched":
-        descs, bufs, cells, alg_bytes = [], [], 0, 0
-        sizes = [(int(rng.choice([512, 1024, 2048, 4096])), int(rng.choice([128, 256, 512, 1024]))) for _ in range(16)]
-        for i, (n1, n2) in enumerate(sizes):
-            w = wl.Workload(f"b{i}", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2,
-                            seed=100 + i)
-            descs.append(hyb.desc_from_workload(w))
-            E0, B0 = wl.band_limited_fields(w)
-            J0, _ = wl.band_limited_fields(w.scaled(seed=w.seed + 50))
-            mk = lambda arrs: [torch.from_numpy(a.astype(np.float32)).to(dev) for a in arrs]
-            bufs.append((mk(E0), mk(B0), mk(J0)))
-            cells += n1 * n2
-            alg_bytes += 60 * n1 * n2
-        nz, nr = 2048, 512
-        for m in (0, 1, 2):
-            dt = 0.9 * 2 / np.sqrt(np.pi ** 2 / 0.2 ** 2 + (4 * m * m + 6) / 0.2 ** 2)
-            descs.append(hyb.make_desc(dims=20, n1=nz, n2=nr, dx1=0.2, dx2=0.2, dt=min(0.08, dt), precision=32,
-                                       filt_kc=0.5, filt_w=0.2, azimuthal_m=m))
-            cf = lambda s_: [(torch.randn(nr, nz, device=dev) + 1j * torch.randn(nr, nz, device=dev)).to(torch.complex64) * s_
-                             for _ in range(3)]
-            bufs.append((cf(1e-3), cf(1e-3), cf(1e-3)))
-            cells += nz * nr
-            alg_bytes += 120 * nz * nr
-        b = hyb.Batch(descs, stream)
-        for i, (E, B, J) in enumerate(bufs):
-            b.bind(i, E, B, J)
-        t0 = time.perf_counter()
-        if args.batch_strips:
-            for kv in args.batch_strips.split(","):
-                n1_, h_ = (int(v) for v in kv.split(":"))
-                b.set_rows_per_strip(n1_, h_)
-        else:
-            b.tune(3)
-        tune_s = time.perf_counter() - t0
-        ms = time_steps(lambda: b.advance(1), args.steps, args.warmup, stream, flush, sampler)
-        launches = b.launches_per_step * args.steps
-        extra["config"] = {"workload": "batched_16x2d_uneven_plus_quasi3d_m012_2048x512", "instances_2d": sizes,
-                           "quasi3d_modes": [0, 1, 2], "quasi3d_grid": [nz, nr],
-                           "strips": "set by --batch-strips" if args.batch_strips else "autotuned",
-                           "autotune_s": tune_s,
-                           "rows_per_strip": {n1: b.rows_per_strip(n1) for n1 in (512, 1024, 2048, 4096)},
-                           "current": "band-limited random J (no deposit in the timed step)",
-                           "l2": "flushed between timed steps (256 MB write)"}
+        ms, cells, alg_bytes, lps, extra["config"] = measure_batched(hyb, wl, args.steps, args.warmup, stream, flush,
+                                                                     sampler, dev, args.batch_strips)
+        launches = lps * args.steps
         dtype = "f32"
-        b.close()
     elif args.workload == "3d":
-        # x1 transform as radix FFT (path 1) and as split-BF16 DFT-GEMM (path 3):
-        # both timed, per-field error of each after 3 steps against the FP64 GPU
-        # path from the same initial state, the faster one reported as the value
-        w = wl.DRIFT_PLASMA_3D
-        if args.rows3d != w.n2:
-            w = w.scaled(n2=args.rows3d, n3=args.rows3d, name=f"drift_plasma_3d_1024x{args.rows3d}x{args.rows3d}_f32")
-        E0, B0 = wl.band_limited_fields(w)
-        J0, _ = wl.band_limited_fields(w.scaled(seed=w.seed + 50))
-        cells, alg_bytes = w.cells, 60 * w.cells
-        x1 = x1_compare(hyb, w, list(E0) + list(B0) + list(J0), stream, flush, sampler, args, dev)
-        best = min((1, 3), key=lambda p_: x1[f"ms_path{p_}"])
-        ms = x1[f"ms_path{best}"]
-        launches = x1[f"launches_path{best}"] * args.steps
-        extra["config"] = {"workload": w.name, "path": {1: "three-pass radix FFT", 3: "three-pass DFT-GEMM"}[best],
-                           "x1_transform": x1, "current": "band-limited random J",
-                           "l2": "flushed between timed steps (256 MB write)"}
+        ms, cells, alg_bytes, lps, extra["config"] = measure_3d(hyb, wl, args.steps, args.warmup, stream, flush,
+                                                                sampler, dev, args.rows3d)
+        launches = lps * args.steps
         dtype = "f32"
     elif args.workload == "x1_sweep":
         rows_out = []
@@ -534,7 +565,7 @@ def run_other(args):
                             filt_w=0.2, seed=3)
             gen = np.random.default_rng(n1)
             arrs = [gen.standard_normal(w.shape) * 1e-3 for _ in range(9)]
-            r = x1_compare(hyb, w, arrs, stream, flush, None, args, dev)
+            r = x1_compare(hyb, w, arrs, stream, flush, None, args.steps, args.warmup, dev)
             r["n1"], r["n2"] = n1, n2
             rows_out.append(r)
         best_row = rows_out[0]
@@ -573,6 +604,55 @@ def run_other(args):
             "gpu_launches": launches, "clocks": sampler.summary()}
     line.update(extra)
     print(json.dumps(line), flush=True)
+
+
+def measure_resident(hyb, w, E, B, J, steps, warmup, stream, flush, fused_kms, peak):
+    """The same workload with k1-resident E, B (hyb_set_resident): per step the forward FFT of
+    j only, the k1-space updates and the inverse FFT of E, B into the real arrays (the fields a
+    particle gather reads), against the fused single pass that transforms E, B, j every step."""
+    Ec, Bc, Jc = [t.clone() for t in E], [t.clone() for t in B], [t.clone() for t in J]
+    g = hyb.Grid(hyb.desc_from_workload(w, path=0), stream)
+    g.bind(Ec, Bc, Jc)
+    g.set_resident(True)
+    ms = time_steps(lambda: g.advance(1), steps, warmup, stream, flush, None)
+    out = {"value": w.cells / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "kernel": g.step_kernel, "launches_per_step": g.launches_per_step,
+           "row_transforms_per_step": {"resident": "3 forward (j) + 6 inverse (E, B)",
+                                       "fused_single_pass": "8 forward + 5 inverse (E1..3, B2, B3, j1..3; B1 "
+                                                            "in real space)"},
+           "algorithmic_bytes_per_cell": {"resident_three_pass": 156, "fused_single_pass": BYTES_PER_CELL_STEP},
+           "fused_kernel_ms": fused_kms,
+           "achieved_gbs": 156 * w.cells / (ms / 1e3) / 1e9}
+    out["frac"] = out["achieved_gbs"] / peak
+    g.close()
+    return out
+
+
+def measure_configs(hyb, wl, stream, flush, dev):
+    """Short measurements of the batched, 3D and surrogate configurations in the same run
+    (each also has its own --workload mode with the full step count)."""
+    import torch
+    from paper_1502_01376_gb300 import surrogate as sg
+    peak, src = peaks()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    out = {}
+    for name, fn in (("batched", lambda: measure_batched(hyb, wl, 20, 3, stream, flush, sampler, dev)),
+                     ("3d", lambda: measure_3d(hyb, wl, 10, 3, stream, flush, sampler, dev))):
+        ms, cells, alg_bytes, lps, config = fn()
+        achieved = alg_bytes / (ms / 1e3) / 1e9
+        out[name] = {"value": cells / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "dtype": "f32",
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak, "peak_source": src, "kernel": "whole step",
+                                  "bytes_per_launch": alg_bytes},
+                     "launches_per_step": lps, "config": config}
+        torch.cuda.empty_cache()
+    out["surrogate"] = measure_surrogate(hyb, sg, 3000, 20, sampler)
+    out["surrogate"]["metric"] = "NCI surrogate training samples/s (MLP 6->256x4->1, BF16 operands, FP32 accumulation)"
+    sampler.stop()
+    out["clocks"] = sampler.summary()
+    return out
 
 
 def main():
@@ -743,6 +823,10 @@ def main():
                          "ms_median": 1e3 * statistics.median(e2e_t), "ms_max": 1e3 * max(e2e_t), "calls": len(e2e_t)}
         if ws == 1:
             extras["cpu_baseline"] = cpu_baseline_sample(w)
+        extras["k1_resident"] = measure_resident(hyb, w, E, B, J, min(K, 200), max(3, args.warmup), stream, flush,
+                                                 kms, peaks()[0])
+        if not args.no_configs:
+            extras["configs"] = measure_configs(hyb, wl, stream, flush, dev)
     # FP64 diagnostics of the final state (energies, max |div B|, Gauss residual): synchronous call,
     # the first one allocates its scratch
     grid.diag()

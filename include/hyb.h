@@ -207,6 +207,25 @@ HYB_API hyb_status hyb_filter(hyb_grid* g);
  * finite differences in x2 (and x3); inverse FFT. */
 HYB_API hyb_status hyb_advance(hyb_grid* g, int nsteps);
 
+/* k1-resident fields (on = 1) or not (on = 0, the default).  The method
+ * applies every curl update to the x1-spectra of the fields (Sec. 2.1), and
+ * the real-space fields are needed only where particles gather them, so with
+ * on = 1 the grid keeps the k1-space E and B of its last step in its own
+ * scratch and the next step transforms only j: per step one forward FFT of
+ * the three j components, the same k1-space correction, filter, Faraday and
+ * Ampere updates, and the inverse FFT of E and B into the bound arrays, which
+ * thereby become an output (the fields to gather) rather than the input.  The
+ * first step after this call, after hyb_bind_fields or inside
+ * hyb_advance_host imports E and B from the bound (or host) arrays as a
+ * normal step does; to feed changed real-space fields in later, call
+ * hyb_set_resident(g, 1) again.  Results are those of hyb_advance up to the
+ * rounding of the dropped inverse/forward round trip.  Resident grids run the
+ * three-pass kernels (the fused single pass keeps no spectra); on a grid made
+ * for the fused path the first call with on = 1 synchronises the grid's
+ * stream and allocates the spectral state (9 n2 n3 (n1/2 + 1) complex values).
+ * HYB_EINVAL for quasi-3D grids or on outside {0, 1}. */
+HYB_API hyb_status hyb_set_resident(hyb_grid* g, int on);
+
 /* The same as hyb_advance, but E, B, J are HOST arrays (pinned memory
  * recommended): they are copied into the bound device arrays, advanced, and
  * E, B are copied back.  Synchronises the grid's stream.  On the fused path

@@ -71,7 +71,6 @@ static FusedBatch group_args(hyb_batch* b, const hyb_batch::Group& G) {
     fb.epoch = 0;
     fb.n_strips = 0;
     fb.err = b->grids[G.members[0]]->dflag;   // a device wait that gives up is reported by hyb_check of this grid
-    fb.plan = nullptr;
     return fb;
 }
 
@@ -247,7 +246,6 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
             fb.epoch = 0;
             fb.n_strips = 0;
             fb.err = b->grids[G.members[0]]->dflag;
-            fb.plan = nullptr;
             fused_launch(G.n1, fb, G.grid, b->stream, nullptr, nullptr);       // warm
             cudaEventRecord(e0, b->stream);
             for (int t = 0; t < trials; t++) fused_launch(G.n1, fb, G.grid, b->stream, nullptr, nullptr);

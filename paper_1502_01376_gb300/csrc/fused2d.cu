@@ -533,10 +533,7 @@ cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s,
     case 512: e = launch_n<512>(fb, grid, s); break;
     case 1024: e = launch_n<1024>(fb, grid, s); break;
     case 2048: e = launch_n<2048>(fb, grid, s); break;
-    default:
-        e = (fb.plan && fused_pair_applies(fb)) ? fused_pair_launch(fb, (const FusedPlan*)fb.plan, grid, s)
-                                                : fused_tm_launch(fb, grid, s);
-        break;
+    default: e = fused_tm_launch(fb, grid, s); break;
     }
     if (e != cudaSuccess) return e;
     if (ev1) e = cudaEventRecord(ev1, s);
@@ -650,7 +647,6 @@ static void hp_release(FusedPlan* P) {
 void fused_destroy(hyb_grid* g) {
     FusedPlan* P = g->fused;
     if (!P) return;
-    fused_pair_release(P);
     hp_release(P);
     if (P->items) cudaFree(P->items);
     if (P->halo) cudaFree(P->halo);
@@ -670,7 +666,6 @@ hyb_status fused_advance(hyb_grid* g, int nsteps) {
     fb.flags = P->flags;          // in-kernel halo exchange: one co-resident CTA per strip
     fb.n_strips = P->n_strips;
     fb.err = g->dflag;
-    fb.plan = P;
     for (int s = 0; s < nsteps; s++) {
         fb.epoch = ++P->epoch;
         HYB_CUDA_TRY(fused_launch(g->d.n1, fb, P->grid, g->stream, g->ev_start, g->ev_stop));
@@ -685,15 +680,8 @@ const char* fused_step_kernel(const hyb_grid* g) {
     case 512: return "k_fused2d<512>";
     case 1024: return "k_fused2d<1024>";
     case 2048: return "k_fused2d<2048>";
-    default: break;
+    default: return "k_fused_tm";
     }
-    const FusedPlan* P = g->fused;
-    FusedBatch fb;
-    fb.inst[0] = fused_inst(g);
-    fb.n_items = P->n_items;
-    fb.flags = P->flags;
-    fb.n_strips = P->n_strips;
-    return fused_pair_applies(fb) ? "k_fused_pair" : "k_fused_tm";
 }
 
 // ------------------------------------------------------------------ one step from and to host arrays
@@ -759,7 +747,6 @@ hyb_status fused_host_advance(hyb_grid* g, void* const E[3], void* const B[3], v
     fb.epoch = 0;
     fb.n_strips = 0;
     fb.err = g->dflag;
-    fb.plan = nullptr;
     auto sub = [&](int i0, int i1) {
         FusedBatch b = fb;
         b.items = P->hp_items + i0;

@@ -31,7 +31,6 @@ struct FusedBatch {
     int epoch;
     int n_strips;
     int* err;
-    const void* plan;    // the single grid's FusedPlan (host pointer; nullptr in batches)
 };
 
 struct FusedPlan {
@@ -62,11 +61,6 @@ size_t fused_tm_smem_bytes();
 cudaError_t fused_tm_occupancy(int* occ);
 cudaError_t fused_tm_launch(const FusedBatch& fb, int grid, cudaStream_t s);
 cudaError_t wait_probe(int* dflag, int* derr, long long limit, int which, cudaStream_t s);
-// n1 = 4096, one strip per co-resident CTA (flag mode): the paired-transform kernel (fused_pair.cu)
-bool fused_pair_applies(const FusedBatch& fb);
-cudaError_t fused_pair_occupancy(int* occ);
-cudaError_t fused_pair_launch(const FusedBatch& fb, const FusedPlan* FP, int grid, cudaStream_t s);
-void fused_pair_release(const FusedPlan* P);
 cudaError_t fused_occupancy(int n1, int* occ);
 cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
 // the fused kernel alone (halo buffer already filled, or flag mode)

@@ -148,9 +148,6 @@ __device__ __forceinline__ void wait_flag(const int* f, int epoch, int* err, lon
         __nanosleep(256);
     }
 }
-__device__ __forceinline__ void stg_stream1(float* p, float v) {
-    asm volatile("st.global.L1::no_allocate.f32 [%0], %1;" :: "l"(p), "f"(v) : "memory");
-}
 __device__ __forceinline__ void stg_stream(float2* p, float2 v) {
     asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(v.x), "f"(v.y) : "memory");
 }

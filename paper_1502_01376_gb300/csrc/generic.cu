@@ -214,7 +214,8 @@ __device__ __forceinline__ void irfft1024_row(float2* A, float2* B, int L, int t
         // Z[k] = E + iO, Z[M-k] = conj(E - iO), E = (X[k] + X*[M-k])/2, O = conj(W_N^k)(X[k] - X*[M-k])/2;
         // the imaginary parts of X[0] and X[M] are dropped
         auto pair = [&](int k) {
-            float2 xk = ld(k), xm = ld(512 - k);
+            float2 xk = ld(k);
+            float2 xm = k == 256 ? xk : ld(512 - k);        // each mode loaded once
             if (k == 0) { xk.y = 0.f; xm.y = 0.f; }
             const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y - xm.y));
             const float2 o = cmc(make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y + xm.y)), twN[k]);
@@ -277,9 +278,11 @@ __global__ void __launch_bounds__(256) k_irfft1024(const float2* __restrict__ in
 // consecutive blocks so that the B rows three of them read come from L2.  Fields 0-2 apply Ampere
 // to E_f mode by mode as they load it (Sm = -conj(S) = c dt sigma-):
 //   E1 += a2 d2-B3 - a3 d3-B2 - cj1 J1;  E2 += a3 d3-B1 - Sm B3 - cj J2;  E3 += Sm B2 - a2 d2-B1 - cj J3
-// fields 3-5 invert B.  The spectral scratch is only read.
-template <bool D3>
-__global__ void __launch_bounds__(256, 3) k_ampere_irfft1024(const float2* __restrict__ spec, RowPtrsW out, int64_t rows, int n2, int n3,
+// fields 3-5 invert B.  Without WB the spectral scratch is only read; with WB (k1-resident
+// state) the updated E spectrum is also stored back in place (each mode of a row is loaded once,
+// by the block of that row and field).
+template <bool D3, bool WB>
+__global__ void __launch_bounds__(256, 3) k_ampere_irfft1024(float2* __restrict__ spec, RowPtrsW out, int64_t rows, int n2, int n3,
                                                           const float2* __restrict__ tw8, const float2* __restrict__ twN,
                                                           const float2* __restrict__ S, const float* __restrict__ cj1,
                                                           const float* __restrict__ cj, float a2, float a3) {
@@ -292,17 +295,21 @@ __global__ void __launch_bounds__(256, 3) k_ampere_irfft1024(const float2* __res
     const int64_t i3 = r / n2;
     const int i2 = (int)(r - i3 * n2);
     const int64_t fs = rows * 513;
-    const float2* Xr = spec + r * 513;                                            // field 0 of row r
+    float2* Xr = spec + r * 513;                                                  // field 0 of row r
     const float2* Xm2 = spec + (i3 * n2 + (i2 == 0 ? n2 - 1 : i2 - 1)) * 513;     // row i2 - 1
     const float2* Xm3 = spec + ((D3 ? (i3 == 0 ? n3 - 1 : i3 - 1) : i3) * n2 + i2) * 513;   // row i3 - 1
     float2* z = live ? reinterpret_cast<float2*>(out.p[f]) + row * 512 : nullptr;
     auto sub = [](float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); };
     auto axpy = [](float2 y, float s, float2 x) { return make_float2(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y)); };
+    auto keep = [&](float2* at, float2 e) {
+        if (WB && live) *at = e;
+        return e;
+    };
     if (f == 0) {
         irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, tw8, twN, [&](int k) {
             float2 e = axpy(Xr[k], a2, sub(Xr[5 * fs + k], Xm2[5 * fs + k]));
             if (D3) e = axpy(e, -a3, sub(Xr[4 * fs + k], Xm3[4 * fs + k]));
-            return axpy(e, -cj1[k], Xr[6 * fs + k]);
+            return keep(Xr + k, axpy(e, -cj1[k], Xr[6 * fs + k]));
         });
     } else if (f == 1) {
         irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, tw8, twN, [&](int k) {
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(256, 3) k_ampere_irfft1024(const float2* __res
             float2 e = Xr[fs + k];
             e = make_float2(e.x + (s.x * b3.x + s.y * b3.y), e.y + (s.x * b3.y - s.y * b3.x));
             if (D3) e = axpy(e, a3, sub(Xr[3 * fs + k], Xm3[3 * fs + k]));
-            return axpy(e, -cj[k], Xr[7 * fs + k]);
+            return keep(Xr + fs + k, axpy(e, -cj[k], Xr[7 * fs + k]));
         });
     } else if (f == 2) {
         irfft1024_row(sbuf[L][0], sbuf[L][1], L, t, z, tw8, twN, [&](int k) {
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(256, 3) k_ampere_irfft1024(const float2* __res
             float2 e = Xr[2 * fs + k];
             e = make_float2(e.x - (s.x * b2.x + s.y * b2.y), e.y - (s.x * b2.y - s.y * b2.x));
             e = axpy(e, -a2, sub(Xr[3 * fs + k], Xm2[3 * fs + k]));
-            return axpy(e, -cj[k], Xr[8 * fs + k]);
+            return keep(Xr + 2 * fs + k, axpy(e, -cj[k], Xr[8 * fs + k]));
         });
     } else {
         const float2* X = Xr + f * fs;
@@ -504,8 +511,8 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
     const int n1 = g->d.n1, nk = g->nk;
     const int64_t rows = g->rows;
     C* spec = reinterpret_cast<C*>(g->spec);
-    RowPtrs fin{};
-    for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; fin.p[6 + c] = g->J[c]; }
+    const void* src9[9];
+    for (int c = 0; c < 3; c++) { src9[c] = g->E[c]; src9[3 + c] = g->B[c]; src9[6 + c] = g->J[c]; }
     RowPtrsW fout{};
     for (int c = 0; c < 3; c++) { fout.p[c] = g->E[c]; fout.p[3 + c] = g->B[c]; }
     const T a2 = (T)(g->d.dt / g->d.dx2);
@@ -513,26 +520,32 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
     const bool d3 = g->d.dims == 3;
     for (int s = 0; s < nsteps; s++) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
+        // k1-resident state: the spectra of E and B left by the previous step are this step's
+        // input, so only j is transformed (the first step after hyb_set_resident imports E, B)
+        const int f0 = (g->resident && !g->res_stale) ? 6 : 0;
+        RowPtrs fin{};
+        for (int c = f0; c < 9; c++) fin.p[c - f0] = src9[c];
+        C* spec_in = spec + (int64_t)f0 * rows * nk;
         if (g->path == 3) {
-            const float* f9[9];
-            for (int c = 0; c < 9; c++) f9[c] = (const float*)fin.p[c];
-            hyb_status st = dftgemm_forward(g, f9, 9, reinterpret_cast<float2*>(spec));
+            const float* fsrc[9];
+            for (int c = f0; c < 9; c++) fsrc[c - f0] = (const float*)src9[c];
+            hyb_status st = dftgemm_forward(g, fsrc, 9 - f0, reinterpret_cast<float2*>(spec_in));
             if (st != HYB_OK) return st;
         } else {
-            HYB_CUDA_TRY((launch_rfft<T, T>(fin, 9, spec, n1, rows, t, g->stream)));
+            HYB_CUDA_TRY((launch_rfft<T, T>(fin, 9 - f0, spec_in, n1, rows, t, g->stream)));
         }
+        if (g->resident) g->res_stale = false;
         const dim3 mgrid((unsigned)((int64_t)g->d.n3 * ((g->d.n2 + kModeRows - 1) / kModeRows) * ((nk + 31) / 32))), mblk(32, kModeRows);
         if constexpr (std::is_same<T, float>::value) {
             if (amp_fused(g)) {
-                const float2* sp = reinterpret_cast<const float2*>(spec);
+                float2* sp = reinterpret_cast<float2*>(spec);
                 const unsigned nb = (unsigned)((rows + kRows1k - 1) / kRows1k) * 6u;
-                if (d3) {
-                    k_faraday<T, true><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
-                    k_ampere_irfft1024<true><<<nb, 256, 0, g->stream>>>(sp, fout, rows, g->d.n2, g->d.n3, t.tw8, t.twN, t.S, t.cj1, t.cj, a2, a3);
-                } else {
-                    k_faraday<T, false><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, a2, a3);
-                    k_ampere_irfft1024<false><<<nb, 256, 0, g->stream>>>(sp, fout, rows, g->d.n2, 1, t.tw8, t.twN, t.S, t.cj1, t.cj, a2, a3);
-                }
+                const int n3 = d3 ? g->d.n3 : 1;
+                if (d3) k_faraday<T, true><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, n3, rows, t.S, a2, a3);
+                else k_faraday<T, false><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, a2, a3);
+                auto amp = d3 ? (g->resident ? k_ampere_irfft1024<true, true> : k_ampere_irfft1024<true, false>)
+                              : (g->resident ? k_ampere_irfft1024<false, true> : k_ampere_irfft1024<false, false>);
+                amp<<<nb, 256, 0, g->stream>>>(sp, fout, rows, g->d.n2, n3, t.tw8, t.twN, t.S, t.cj1, t.cj, a2, a3);
                 HYB_CUDA_TRY(cudaGetLastError());
                 if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
                 continue;
@@ -565,7 +578,8 @@ hyb_status generic_process_current(hyb_grid* g, bool corr, bool filt) {
     const ModeTables<T>& t = tables<T>(g);
     const int n1 = g->d.n1, nk = g->nk;
     const int64_t rows = g->rows;
-    C* spec = reinterpret_cast<C*>(g->spec);
+    // the j part of the scratch (its last three fields), so that a k1-resident E, B survives
+    C* spec = reinterpret_cast<C*>(g->spec) + (int64_t)(g->spec_fields - 3) * rows * nk;
     int nf = filt ? 3 : 1;
     RowPtrs fin{};
     RowPtrsW fout{};

@@ -238,6 +238,7 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
     if (st == HYB_OK && d.dims != 20) {
         const size_t csz = d.precision == 32 ? sizeof(float2) : sizeof(double2);
         const int nf = (g->path == 1 || g->path == 3) ? 9 : 3;
+        g->spec_fields = nf;
         g->spec_bytes = (size_t)nf * g->rows * g->nk * csz;
         ce = cudaMalloc(&g->spec, g->spec_bytes);
         if (ce != cudaSuccess) { g->spec = nullptr; st = cuda_fail(ce, "cudaMalloc(spectral scratch)"); }
@@ -246,6 +247,28 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
     if (st == HYB_OK && g->path == 3) st = dftgemm_create(g);
     if (st != HYB_OK) { hyb_destroy_grid(g); return st; }
     *out = g;
+    return HYB_OK;
+}
+
+hyb_status hyb_set_resident(hyb_grid* g, int on) {
+    if (!g) { set_error("null grid"); return HYB_EINVAL; }
+    if (on != 0 && on != 1) { set_error("hyb_set_resident: on must be 0 or 1"); return HYB_EINVAL; }
+    if (on && g->d.dims == 20) { set_error("hyb_set_resident: quasi-3D grids keep no k1-resident state"); return HYB_EINVAL; }
+    if (on && g->spec_fields < 9) {
+        // a fused-path grid keeps only j's spectra: room for E, B too
+        const size_t csz = g->d.precision == 32 ? sizeof(float2) : sizeof(double2);
+        const size_t bytes = (size_t)9 * g->rows * g->nk * csz;
+        void* p = nullptr;
+        HYB_CUDA_TRY(cudaStreamSynchronize(g->stream));
+        HYB_CUDA_TRY(cudaMalloc(&p, bytes));
+        if (g->spec) cudaFree(g->spec);
+        g->spec = p;
+        g->spec_bytes = bytes;
+        g->spec_fields = 9;
+    }
+    g->resident = on != 0;
+    g->res_stale = true;
+    g->step_dirty = true;
     return HYB_OK;
 }
 
@@ -266,6 +289,7 @@ hyb_status hyb_bind_fields(hyb_grid* g, void* const E[3], void* const B[3], void
     for (int c = 0; c < 3; c++) { g->E[c] = E[c]; g->B[c] = B[c]; g->J[c] = J[c]; }
     g->rho = rho;
     g->bound = true;
+    g->res_stale = true;
     return HYB_OK;
 }
 
@@ -349,9 +373,16 @@ hyb_status hyb_advance(hyb_grid* g, int nsteps) {
     if (!g->bound) { set_error("hyb_advance: fields not bound"); return HYB_ESTATE; }
     if (nsteps < 0) { set_error("nsteps < 0"); return HYB_EINVAL; }
     if (nsteps == 0) return HYB_OK;
-    if (g->path == 2) return fused_advance(g, nsteps);
+    if (g->path == 2 && !g->resident) return fused_advance(g, nsteps);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     HYB_CUDA_TRY(cudaStreamIsCapturing(g->stream, &cap));
+    if (g->resident && g->res_stale && cap == cudaStreamCaptureStatusNone && !g->ev_start) {
+        // the importing step (E, B transformed too) runs as plain launches; the step graph
+        // captured afterwards is the resident one
+        hyb_status st = step_once(g);
+        if (st != HYB_OK) return st;
+        if (--nsteps == 0) return HYB_OK;
+    }
     if (g->ev_start || cap != cudaStreamCaptureStatusNone) {
         // per-step kernel events requested, or the caller is capturing its own graph: plain launches
         for (int s = 0; s < nsteps; s++) {
@@ -373,7 +404,8 @@ hyb_status hyb_advance_host(hyb_grid* g, void* const E[3], void* const B[3], voi
     if (!g->bound) { set_error("hyb_advance_host: device fields not bound"); return HYB_ESTATE; }
     for (int c = 0; c < 3; c++)
         if (!E[c] || !B[c] || !J[c]) { set_error("hyb_advance_host: null field pointer"); return HYB_EINVAL; }
-    if (g->path == 2 && nsteps == 1) {
+    if (g->resident) g->res_stale = true;      // E, B come from the host arrays
+    if (g->path == 2 && nsteps == 1 && !g->resident) {
         // one fused step: copies in, compute and copies out pipelined over chunks of rows
         hyb_status st = fused_host_advance(g, E, B, J);
         if (st != HYB_OK) return st;
@@ -465,6 +497,7 @@ int hyb_grid_path(const hyb_grid* g) { return g ? g->path : 0; }
 
 const char* hyb_step_kernel(const hyb_grid* g) {
     if (!g) return "";
+    if (g->resident) return g->path == 3 ? "k1-resident dft-gemm three-pass step" : "k1-resident three-pass step";
     if (g->path == 2) return fused_step_kernel(g);
     if (g->path == 3) return "dft-gemm three-pass step";
     return g->d.dims == 20 ? "quasi-3D step" : "three-pass step";
@@ -472,7 +505,7 @@ const char* hyb_step_kernel(const hyb_grid* g) {
 
 int hyb_launches_per_step(const hyb_grid* g) {
     if (!g) return 0;
-    if (g->path == 2) return fused_launches_per_step(g);
+    if (g->path == 2 && !g->resident) return fused_launches_per_step(g);
     if (g->path == 3) return 11;     // split + product (forward), Faraday, Ampere, split + 6 products (inverse)
     return generic_launches_per_step(g);
 }

@@ -277,6 +277,11 @@ struct hyb_grid {
     // scratch (library-owned)
     void* spec = nullptr;          // three-pass path: 9 spectral arrays [9][rows][nk] complex of run precision
     size_t spec_bytes = 0;
+    int spec_fields = 0;           // 9 (three-pass or k1-resident) or 3 (fused path: j only)
+    // k1-resident state (hyb_set_resident): the spectra of E, B in spec carry over between steps;
+    // res_stale: the next step first imports them from the bound real arrays
+    bool resident = false;
+    bool res_stale = true;
     double* diag_work = nullptr;   // diagnostics: 2 spectral FP64 arrays + 1 real FP64 array
     size_t diag_bytes = 0;
     double* diag_acc = nullptr;    // 16 FP64 accumulators

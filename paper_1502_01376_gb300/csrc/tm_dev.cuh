@@ -101,41 +101,4 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int* er
     }
 }
 
-
-
-
-
-// the same on 16 (8) consecutive elements of a larger register array, from element OFF: the
-// array is passed by reference with constant indices only, so it stays in registers
-template <int OFF, int NN>
-__device__ __forceinline__ void tm_ld16_at(uint32_t ta, float (&r)[NN]) {
-    static_assert(OFF + 16 <= NN, "range");
-    float t[16];
-    tm_ld16(ta, t);
-#pragma unroll
-    for (int i = 0; i < 16; i++) r[OFF + i] = t[i];
-}
-template <int OFF, int NN>
-__device__ __forceinline__ void tm_st16_at(uint32_t ta, const float (&r)[NN]) {
-    static_assert(OFF + 16 <= NN, "range");
-    float t[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) t[i] = r[OFF + i];
-    tm_st16(ta, t);
-}
-template <int OFF, int NN>
-__device__ __forceinline__ void tm_st8_at(uint32_t ta, const float (&r)[NN]) {
-    static_assert(OFF + 8 <= NN, "range");
-    float t[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++) t[i] = r[OFF + i];
-    tm_st8(ta, t);
-}
-
-
-// bulk prefetch of `bytes` (multiple of 16, 16-byte aligned) of global memory into L2
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(src), "r"(bytes) : "memory");
-}
-
 }  // namespace hyb

@@ -138,6 +138,8 @@ def lib():
             L.hyb_mlp_destroy.restype = S
             L.hyb_mlp_launch_count.argtypes = [_V]
             L.hyb_mlp_launch_count.restype = ctypes.c_int64
+            L.hyb_set_resident.argtypes = [_V, ctypes.c_int]
+            L.hyb_set_resident.restype = ctypes.c_int
             L.hyb_step_kernel.argtypes = [_V]
             L.hyb_step_kernel.restype = ctypes.c_char_p
             L.hyb_launches_per_step.argtypes = [_V]
@@ -430,6 +432,11 @@ class Grid:
     @property
     def step_kernel(self):
         return hyb_step_kernel(self.h)
+
+    def set_resident(self, on=True):
+        """k1-resident E, B between steps (hyb_set_resident); calling it again with on=True
+        re-imports the bound real-space fields at the next step."""
+        _check(lib().hyb_set_resident(_V(self.h), 1 if on else 0))
 
     def close(self):
         if self.h:

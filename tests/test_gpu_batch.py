@@ -49,14 +49,8 @@ def test_batch_equals_single_grids_and_oracle(orc):
     torch.cuda.synchronize()
     def same_as_singles(what):
         for i in range(len(ws)):
-            # a single 4096-wide grid with one strip per SM runs the paired-transform kernel, the
-            # batch the per-field one: the same arithmetic in another rounding order
-            exact = singles[i].step_kernel != "k_fused_pair"
             for a, b in zip(bt[i][0] + bt[i][1], st[i][0] + st[i][1]):
-                if exact:
-                    assert torch.equal(a, b), (SIZES[i], what)
-                else:
-                    assert float((a - b).abs().max() / b.abs().max()) < 1e-5, (SIZES[i], what)
+                assert torch.equal(a, b), (SIZES[i], what)
 
     same_as_singles("first steps")
     # oracle on two of them
@@ -69,7 +63,7 @@ def test_batch_equals_single_grids_and_oracle(orc):
         tol = 1e-5 if w.precision == 32 else 1e-12
         for a, b in zip(bt[i][0] + bt[i][1], Eo + Bo):
             assert rel_err(to_np(a), b) < tol
-    # autotune, then the batch still reproduces the single grids
+    # autotune, then the batch still reproduces the single grids exactly
     batch.tune(2)
     for n1 in (512, 1024, 2048, 4096):
         assert 2 <= batch.rows_per_strip(n1) <= 64

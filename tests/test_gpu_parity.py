@@ -266,8 +266,7 @@ def test_advance_host_matches_device(orc):
 @pytest.mark.parametrize("n1,n2", [(4096, 1024), (1024, 37), (512, 4), (2048, 70)])
 def test_fused_host_step_matches_device_step(n1, n2):
     """One fused step from and to host arrays (copies and compute pipelined over chunks of rows,
-    halo rows taken before the rows they come from are updated) equals the device-array step
-    (bit for bit where both run the same kernel, to FP32 rounding at n1 = 4096)."""
+    halo rows taken before the rows they come from are updated) equals the device-array step."""
     need_gpu()
     hyb = hyb_module()
     w = wl.Workload("hp", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.1, precision=32, filt_kc=0.5, filt_w=0.2, seed=17)
@@ -289,12 +288,7 @@ def test_fused_host_step_matches_device_step(n1, n2):
     gh.check()
     torch.cuda.synchronize()
     for a, b, dev in zip(H[:6], D[:6], Dh[:6]):
-        if n1 == 4096:
-            # the single grid runs the paired-transform kernel, the chunked host step the
-            # row-by-row one: the same step up to FP32 rounding order
-            assert rel_err(a.numpy(), b.cpu().numpy()) < 1e-5
-        else:
-            assert torch.equal(a, b.cpu()), float((a - b.cpu()).abs().max())
+        assert torch.equal(a, b.cpu()), float((a - b.cpu()).abs().max())
         assert torch.equal(dev.cpu(), a)
     gd.close()
     gh.close()
@@ -342,6 +336,31 @@ def test_fused_matches_oracle(orc, n1, n2):
     need_gpu()
     hyb = hyb_module()
     _fused_case(orc, hyb, n1, n2, 10)
+
+
+@pytest.mark.parametrize("n1,n2,path", [(4096, 64, 2), (2048, 24, 2), (1024, 21, 2), (512, 16, 2), (1024, 12, 1),
+                                       (256, 12, 1)])
+def test_per_field_accuracy_with_components_of_unequal_size(orc, n1, n2, path):
+    """Per-field relative error stays at FP32 level when the components differ by orders of
+    magnitude, as in the drifting plasma, where the drive j1 is large and the TE fields
+    (E3, B1, B2) are far weaker than E2, B3: a transform that mixed two fields would give the
+    weak one an error on the scale of the strong one."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("mix", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.1, precision=32, filt_kc=0.5, filt_w=0.2, seed=41)
+    g, E0, B0, E, B, J = _setup(hyb, w, path=path)
+    scale_e, scale_b = (1.0, 1.0, 1e-5), (1e-5, 1e-5, 1.0)
+    E0 = [a * s for a, s in zip(E0, scale_e)]
+    B0 = [a * s for a, s in zip(B0, scale_b)]
+    rng = np.random.default_rng(42)
+    J0 = [rng.standard_normal(w.shape) * s for s in (1e-1, 1e-3, 1e-9)]
+    for t, a in zip(E + B + J, E0 + B0 + J0):
+        t.copy_(to_dev(a, torch.float32))
+    rnd = lambda a: a.astype(np.float32).astype(np.float64)
+    Eo, Bo, Jo = [rnd(a) for a in E0], [rnd(a) for a in B0], [rnd(a) for a in J0]
+    orc.step(orc_grid(orc, w), Eo, Bo, Jo, nsteps=5)
+    g.advance(5)
+    _compare(E, B, Eo, Bo, TOL[32], f"unequal components {n1}x{n2} path {path}")
 
 
 def test_fused_without_filter_and_correction(orc):
