@@ -1,188 +1,416 @@
 // dftgemm.cu -- the x1 transform of the three-pass advance as a dense DFT
-// matrix product on the tensor cores (path 3), for short n1.  FP32 operands
-// are split into two BF16 parts, a = a_hi + a_lo, and the product keeps the
-// three leading terms a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32
-// (mma.sync m16n8k16): one GEMM with the K dimension tripled,
-//   [a_hi | a_hi | a_lo] x [b_hi ; b_lo ; b_hi].
+// matrix product on the fifth-generation tensor cores (path 3), for short n1.
+//
 // Forward:  X[r][2k + {0,1}] = sum_j x[r][j] (cos, -sin)(2 pi k j / n1), k = 0..n1/2
 // Inverse:  x[r][j] = sum_k w_k (Re X_k cos - Im X_k sin)(2 pi k j / n1) / n1,
 //           w_0 = w_{n1/2} = 1, otherwise 2 (the imaginary parts of the DC and
 //           Nyquist coefficients drop out, as in the radix path).
-// The matrices are computed in FP64 on the host and split once.
+// Both are D[m][n] = sum_k A[m][k] M[n][k] with A the FP32 rows (K = n1 reals,
+// or n1 + 2 interleaved spectrum values) and M the DFT matrix, computed in FP64
+// on the host and rounded to FP32.  FP32 operands are split into two BF16
+// parts, a = a_hi + a_lo, and the product keeps the three leading terms
+//   D = A_hi M_hi + A_hi M_lo + A_lo M_hi,
+// accumulated in FP32 by tcgen05.mma (kind::f16, BF16 inputs) in tensor memory.
+//
+// k_dft_tc: a persistent kernel over (tile of 128 rows, pass of <= 512 output
+// columns).  Per 64-wide K chunk the 256 threads load the tile's FP32 values
+// (coalesced along the rows), split them and store A_hi, A_lo in shared memory
+// in the canonical K-major layout without swizzle (core matrices of 8 rows x
+// 16 bytes; element (m, k) at byte (k / 8) * LBO + 16 m + 2 (k % 8)); the
+// matrix chunk, stored in global memory in that layout already, arrives by one
+// bulk copy (cp.async.bulk, completion on an mbarrier).  One thread issues the
+// 4 k-steps x 3 products x (1 or 2 column blocks of <= 256) MMAs into the TMEM
+// accumulator (row m in lane m, column n in column n) and commits them to a
+// second mbarrier; the next chunk overwrites shared memory only after it.  The
+// epilogue reads the accumulator with tcgen05.ld (warp w: lanes 32 (w % 4) ..,
+// half of the column blocks) and writes the valid columns of each row.  All
+// waits are bounded; a wait that runs out sets bit 1 of the grid's error flag,
+// skips the remaining work, drains what is in flight and frees the TMEM.
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "hyb_internal.cuh"
+#include "tm_dev.cuh"
 
 namespace hyb {
 
-constexpr int GM = 64, GN = 64, GK = 16;
+namespace dg {
+constexpr int BM = 128;                  // rows per tile (MMA M)
+constexpr int KC = 64;                   // K per chunk: 4 k-steps of 16
+constexpr int NPASS = 512;               // output columns per pass (TMEM columns)
+constexpr int NT = 256;                  // threads per CTA
+constexpr int A_LBO = BM * 16 + 32;      // bytes between K groups of the A image (padded: bank spread)
+constexpr int A_IMG = 8 * A_LBO;         // one A image (hi or lo) of a chunk
+constexpr int OFF_B = ((2 * A_IMG + 127) / 128) * 128;
+// shared memory requested beyond the operand images, so that the products of a chunk stay
+// inside the CTA's allocation whichever of the two byte offsets of the descriptor the
+// hardware applies along K (the images are laid out for the K-direction one)
+constexpr int GUARD = 0;
+}  // namespace dg
 
-__device__ __forceinline__ uint32_t pk2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+// shared-memory matrix descriptor of tcgen05: start, leading (K-direction core matrix) and
+// stride (M/N-direction 8-row group) byte offsets, fixed version bits 46-48 = 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
+}
+// bounded wait that ignores the abort flag: used to drain copies and products in flight
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return;
 }
 
-// C[m][n] (FP32, row stride ldc) = sum_k A[m][k] B[k][n]; A BF16 row-major (lda),
-// B BF16 row-major (ldb); K multiple of 16; M, N arbitrary.
-__global__ void __launch_bounds__(128) k_dgemm(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int64_t lda,
-                                               const __nv_bfloat16* __restrict__ B, int64_t ldb, float* __restrict__ C,
-                                               int64_t ldc) {
-    __shared__ __nv_bfloat16 As[GM][GK + 8];
-    __shared__ __nv_bfloat16 Bs[GN][GK + 8];
-    const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gq = lane >> 2, tq = lane & 3;
-    float acc[2][4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int i = threadIdx.x; i < GM * GK; i += blockDim.x) {
-            const int r = i / GK, kk = i % GK, m = m0 + r;
-            As[r][kk] = (m < M) ? A[(int64_t)m * lda + k0 + kk] : __float2bfloat16(0.f);
-        }
-        for (int i = threadIdx.x; i < GN * GK; i += blockDim.x) {
-            const int kk = i / GN, r = i % GN, n = n0 + r;
-            Bs[r][kk] = (n < N) ? B[(int64_t)(k0 + kk) * ldb + n] : __float2bfloat16(0.f);
-        }
-        __syncthreads();
-        uint32_t af[2][4], bf[4][2];
-#pragma unroll
-        for (int i = 0; i < 2; i++) {
-            const int r = wm + i * 16;
-            af[i][0] = pk2(As[r + gq][2 * tq], As[r + gq][2 * tq + 1]);
-            af[i][1] = pk2(As[r + gq + 8][2 * tq], As[r + gq + 8][2 * tq + 1]);
-            af[i][2] = pk2(As[r + gq][2 * tq + 8], As[r + gq][2 * tq + 9]);
-            af[i][3] = pk2(As[r + gq + 8][2 * tq + 8], As[r + gq + 8][2 * tq + 9]);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int cn = wn + j * 8 + gq;
-            bf[j][0] = pk2(Bs[cn][2 * tq], Bs[cn][2 * tq + 1]);
-            bf[j][1] = pk2(Bs[cn][2 * tq + 8], Bs[cn][2 * tq + 9]);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; i++)
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                             "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                             : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-                             : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]), "r"(bf[j][1]));
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int r = m0 + wm + i * 16 + gq + 8 * h, cc = n0 + wn + j * 8 + 2 * tq;
-                if (r < M) {
-                    if (cc < N) C[(int64_t)r * ldc + cc] = acc[i][j][2 * h];
-                    if (cc + 1 < N) C[(int64_t)r * ldc + cc + 1] = acc[i][j][2 * h + 1];
-                }
-            }
-}
-
-struct SplitSrc { const float* p[9]; };
-
-// rows of the nf source arrays (row length L, row stride ls) -> BF16 [nf*rows][3 Lp]:
-// [hi | hi | lo], each segment padded with zeros to Lp (a multiple of 16)
-__global__ void k_split_rows(SplitSrc src, int nf, int64_t rows, int L, int Lp, int64_t ls, __nv_bfloat16* __restrict__ out) {
-    const int64_t R = (int64_t)nf * rows;
-    const int64_t total = R * Lp;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / Lp;
-        const int c = (int)(i % Lp);
-        const int f = (int)(r / rows);
-        const float v = (c < L) ? src.p[f][(r % rows) * ls + c] : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16(v);
-        const __nv_bfloat16 lo = __float2bfloat16(v - __bfloat162float(hi));
-        __nv_bfloat16* o = out + r * (3 * (int64_t)Lp);
-        o[c] = hi;
-        o[Lp + c] = hi;
-        o[2 * Lp + c] = lo;
-    }
-}
-
-struct DftPlan {
-    __nv_bfloat16* Bf = nullptr;   // [3 n1][n1 + 2]
-    __nv_bfloat16* Bi = nullptr;   // [3 (n1 + 2)][n1]
-    __nv_bfloat16* Asplit = nullptr;
-    size_t a_elems = 0;
+struct DgArgs {
+    const float* src[9];          // source arrays: rows x L valid values, row stride ls floats
+    float* dst[9];                // destination arrays: rows x N valid values, row stride ld floats
+    int nf;
+    int64_t rows;                 // rows per array
+    int L, ls;
+    int N, ld;
+    int nkc;                      // K chunks of 64
+    int npass;                    // passes over the output columns
+    int npc[4];                   // columns of pass p (multiple of 16, <= 512)
+    int64_t boff[4];              // element offset of pass p's first chunk image in B
+    const __nv_bfloat16* B;       // per (pass, chunk): hi image then lo image, each npc x 64
+    uint32_t tcols;               // TMEM columns allocated
+    int* err;
 };
 
-static void split_host(const std::vector<double>& m, std::vector<__nv_bfloat16>& hi, std::vector<__nv_bfloat16>& lo) {
-    hi.resize(m.size());
-    lo.resize(m.size());
-    for (size_t i = 0; i < m.size(); i++) {
-        const float f = (float)m[i];
-        hi[i] = __float2bfloat16(f);
-        lo[i] = __float2bfloat16(f - __bfloat162float(hi[i]));
+// P value pairs per row and warp row (P = 32, or 16 / 8 when a row has at most 32 / 16 values):
+// thread tid loads, for (tile, chunk kc), rows tid / P + (256 / P) j of the tile (j < P / 2),
+// values kc * 64 + 2 (tid % P) and the next; zero outside the arrays
+template <int P>
+__device__ __forceinline__ void dg_load(const DgArgs& a, int64_t tile, int kc, int tid, float2 (&v)[16]) {
+    const int64_t t0 = tile * dg::BM;
+    const int f0 = (int)(t0 / a.rows);
+    const int64_t r0 = t0 - (int64_t)f0 * a.rows;
+    const int k = kc * dg::KC + 2 * (tid % P);
+#pragma unroll
+    for (int j = 0; j < P / 2; j++) {
+        int f = f0;
+        int64_t r = r0 + tid / P + (dg::NT / P) * j;
+        while (r >= a.rows) { r -= a.rows; f++; }
+        v[j] = make_float2(0.f, 0.f);
+        if (f < a.nf && k < a.L) {
+            const float* row = a.src[f] + r * a.ls;
+            if (k + 1 < a.L) v[j] = __ldg(reinterpret_cast<const float2*>(row + k));
+            else v[j].x = __ldg(row + k);
+        }
     }
+}
+// the same pairs split into BF16 hi and lo parts, stored into the two A images
+template <int P>
+__device__ __forceinline__ void dg_store(uint32_t sA, int tid, const float2 (&v)[16]) {
+    const int kk = 2 * (tid % P);
+#pragma unroll
+    for (int j = 0; j < P / 2; j++) {
+        const int i = tid / P + (dg::NT / P) * j;
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[j].x), h1 = __float2bfloat16_rn(v[j].y);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[j].x - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[j].y - __bfloat162float(h1));
+        const uint32_t off = (uint32_t)((kk >> 3) * dg::A_LBO + 16 * i + 2 * (kk & 7));
+        const uint32_t hv = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        const uint32_t lv = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        asm volatile("st.shared.b32 [%0], %1;" :: "r"(sA + off), "r"(hv) : "memory");
+        asm volatile("st.shared.b32 [%0], %1;" :: "r"(sA + dg::A_IMG + off), "r"(lv) : "memory");
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(dg::NT, 1) k_dft_tc(DgArgs a) {
+    using namespace dg;
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ uint64_t bars[2];                 // 0: matrix chunk landed, 1: products done
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sA = (smem_addr(sm) + 127u) & ~127u;          // 128 bytes of slack are requested
+    const uint32_t sB = sA + OFF_B;
+    const uint32_t bar_b = smem_addr(&bars[0]), bar_m = smem_addr(&bars[1]);
+    if (warp == 0) {
+        tm_alloc(smem_addr(&s_taddr), a.tcols);
+        tm_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(bar_b, 1);
+        mbar_init(bar_m, 1);
+        mbar_fence_init();
+        s_abort = 0;
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const uint32_t tbase = s_taddr;
+    uint32_t ph_b = 0, ph_m = 0;
+    bool pend_b = false, pend_m = false;         // thread 0: a copy / products not yet waited for
+    bool b_in = false;                           // thread 0: the single matrix image is in shared memory
+    const bool b_resident = a.nkc * a.npass == 1;
+    const int64_t R = (int64_t)a.nf * a.rows;
+    const int64_t items = (R + BM - 1) / BM * a.npass;
+    bool abort = false;                          // s_abort as read after a barrier: uniform
+    // units (item, chunk) of this CTA in order; the values of the next unit are loaded while the
+    // products of the current one run
+    int64_t it = blockIdx.x;
+    int kc = 0;
+    float2 v[16];
+    if (it < items) dg_load<P>(a, it / a.npass, 0, tid, v);
+    while (it < items && !abort) {
+        const int64_t tile = it / a.npass;
+        const int p = (int)(it % a.npass);
+        const int npc = a.npc[p];
+        const int c0 = npc < 256 ? npc : 256, c1 = npc - c0;
+        if (tid == 0 && !(b_resident && b_in)) {
+            const uint32_t bytes = (uint32_t)npc * KC * 2 * 2;
+            mbar_expect_tx(bar_b, bytes);
+            bulk_load(sB, a.B + a.boff[p] + (int64_t)kc * 2 * npc * KC, bytes, bar_b);
+            pend_b = true;
+        }
+        dg_store<P>(sA, tid, v);
+        fence_proxy_async_smem();
+        tm_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tm_fence_after();
+            if (pend_b) {
+                mbar_wait(bar_b, ph_b, a.err, &s_abort);
+                if (!s_abort) {
+                    ph_b ^= 1;
+                    pend_b = false;
+                    b_in = true;
+                }
+            }
+            if (!s_abort) {
+                // k-steps of 16 holding values of this chunk (the rest of the image is zero)
+                const int nks = min(4, (a.L - kc * KC + 15) / 16);
+                for (int ks = 0; ks < nks; ks++) {
+                    const uint64_t ah = smem_desc(sA + 2 * ks * A_LBO, A_LBO, 128);
+                    const uint64_t al = smem_desc(sA + A_IMG + 2 * ks * A_LBO, A_LBO, 128);
+                    for (int c = 0; c < 2; c++) {
+                        const int w = c ? c1 : c0;
+                        if (w == 0) continue;
+                        // the block's hi and lo images: 8 K groups of w rows x 16 bytes each
+                        const uint32_t bh = sB + (uint32_t)(c ? c0 : 0) * KC * 2;
+                        const uint32_t bl = bh + (uint32_t)npc * KC * 2;
+                        const uint32_t lb = (uint32_t)w * 16;
+                        const uint64_t dh = smem_desc(bh + 2 * ks * lb, lb, 128);
+                        const uint64_t dl = smem_desc(bl + 2 * ks * lb, lb, 128);
+                        const uint32_t dt = tbase + (uint32_t)(c ? c0 : 0);
+                        const uint32_t id = idesc_bf16(w);
+                        mma_bf16(dt, ah, dh, id, (kc > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16(dt, ah, dl, id, 1u);
+                        mma_bf16(dt, al, dh, id, 1u);
+                    }
+                }
+                mma_commit(bar_m);
+                pend_m = true;
+            }
+        }
+        // the next unit's values, in flight while the products run
+        int64_t it2 = it;
+        int kc2 = kc + 1;
+        if (kc2 == a.nkc) { it2 = it + gridDim.x; kc2 = 0; }
+        if (it2 < items) dg_load<P>(a, it2 / a.npass, kc2, tid, v);
+        if (tid == 0 && pend_m) {
+            // the products read shared memory: wait for them before the next unit overwrites it
+            mbar_wait(bar_m, ph_m, a.err, &s_abort);
+            if (!s_abort) {
+                ph_m ^= 1;
+                pend_m = false;
+            }
+        }
+        __syncthreads();
+        abort = s_abort != 0;
+        if (kc == a.nkc - 1 && !abort) {
+            // epilogue: warp w reads lanes 32 (w % 4) .. + 31 (rows), column units of 16
+            // alternating between the two warp halves
+            tm_fence_after();
+            const int q = warp & 3, h = warp >> 2;
+            int f = 0;
+            int64_t r = 0;
+            {
+                const int64_t gr = tile * BM + 32 * q + lane;
+                f = (int)(gr / a.rows);
+                r = gr - (int64_t)f * a.rows;
+            }
+            float* out = f < a.nf ? a.dst[f] + r * a.ld : nullptr;
+            for (int u = h; u < npc / 16; u += 2) {
+                float t[16];
+                tm_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * u), t);
+                tm_wait_ld();
+                const int n0 = p * NPASS + 16 * u;
+                if (out) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2)
+                        if (n0 + j < a.N) *reinterpret_cast<float2*>(out + n0 + j) = make_float2(t[j], t[j + 1]);
+                }
+            }
+            tm_fence_before();
+        }
+        it = it2;
+        kc = kc2;
+    }
+    // drain what an early exit left in flight, then free the tensor memory
+    if (tid == 0) {
+        if (pend_b) mbar_drain(bar_b, ph_b);
+        if (pend_m) mbar_drain(bar_m, ph_m);
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (warp == 0) tm_dealloc(tbase, a.tcols);
+}
+
+// ------------------------------------------------------------------ host side
+struct DftOp {                      // one direction: matrix images and launch shape
+    __nv_bfloat16* B = nullptr;
+    int K = 0, N = 0, nkc = 0, npass = 0;
+    int npc[4] = {0, 0, 0, 0};
+    int64_t boff[4] = {0, 0, 0, 0};
+    uint32_t tcols = 0;
+    size_t smem = 0;
+    int grid = 0;
+    void (*kern)(DgArgs) = nullptr;     // k_dft_tc<P>, P = pairs per row and warp row
+};
+struct DftPlan {
+    DftOp fwd, inv;
+};
+
+// M[n][k] (FP64, n < N, k < K) -> images [pass][chunk][hi | lo][block][k / 8][n][k % 8] of BF16
+static hyb_status make_op(hyb_grid* g, DftOp& op, const std::vector<double>& M, int N, int K) {
+    using namespace dg;
+    op.K = K;
+    op.N = N;
+    op.nkc = (K + KC - 1) / KC;
+    const int Np = (N + 15) & ~15;
+    op.npass = (Np + NPASS - 1) / NPASS;
+    if (op.npass > 4) { set_error("DFT-GEMM: n1 too large"); return HYB_EINVAL; }
+    size_t total = 0;
+    int maxc = 0;
+    for (int p = 0; p < op.npass; p++) {
+        op.npc[p] = std::min(NPASS, Np - p * NPASS);
+        op.boff[p] = (int64_t)total;
+        total += (size_t)op.nkc * 2 * op.npc[p] * KC;
+        maxc = std::max(maxc, op.npc[p]);
+    }
+    std::vector<__nv_bfloat16> img(total, __float2bfloat16(0.f));
+    for (int p = 0; p < op.npass; p++) {
+        const int npc = op.npc[p];
+        const int c0 = std::min(256, npc);
+        for (int kc = 0; kc < op.nkc; kc++) {
+            __nv_bfloat16* base = img.data() + op.boff[p] + (size_t)kc * 2 * npc * KC;
+            for (int nl = 0; nl < npc; nl++) {
+                const int blk = nl < c0 ? 0 : 1, w = blk ? npc - c0 : c0, nb = blk ? nl - c0 : nl;
+                const size_t boff = (size_t)(blk ? c0 : 0) * KC;
+                for (int kl = 0; kl < KC; kl++) {
+                    const int n = p * NPASS + nl, k = kc * KC + kl;
+                    const float v = (n < N && k < K) ? (float)M[(size_t)n * K + k] : 0.f;
+                    const __nv_bfloat16 hi = __float2bfloat16(v);
+                    const __nv_bfloat16 lo = __float2bfloat16(v - __bfloat162float(hi));
+                    const size_t e = boff + ((size_t)(kl >> 3) * w + nb) * 8 + (kl & 7);
+                    base[e] = hi;
+                    base[(size_t)npc * KC + e] = lo;
+                }
+            }
+        }
+    }
+    HYB_CUDA_TRY(cudaMalloc(&op.B, sizeof(__nv_bfloat16) * total));
+    HYB_CUDA_TRY(cudaMemcpy(op.B, img.data(), sizeof(__nv_bfloat16) * total, cudaMemcpyHostToDevice));
+    op.tcols = maxc <= 256 ? 256 : 512;
+    op.smem = 128 + (size_t)OFF_B + (size_t)maxc * KC * 2 * 2 + GUARD;
+    op.kern = K <= 16 ? k_dft_tc<8> : K <= 32 ? k_dft_tc<16> : k_dft_tc<32>;
+    const void* kf = (const void*)op.kern;
+    HYB_CUDA_TRY(func_attr_once(kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(128 + OFF_B + NPASS * KC * 2 * 2 + GUARD)));
+    HYB_CUDA_TRY(func_attr_once(kf, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    // CTAs per SM from the kernel's registers and shared memory (warps take registers in units
+    // of 256) and from the 512 TMEM columns the CTAs of an SM share
+    cudaFuncAttributes fa;
+    HYB_CUDA_TRY(cudaFuncGetAttributes(&fa, kf));
+    int sms = 0, smem_sm = 0;
+    HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+    HYB_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, g->device));
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int occ_r = 65536 / (regs_warp * (NT / 32));
+    const int occ_s = (int)(smem_sm / (op.smem + fa.sharedSizeBytes + 1024));
+    const int occ = std::max(1, std::min({occ_r, occ_s, (int)(512 / op.tcols)}));
+    op.grid = sms * occ;
+    return HYB_OK;
 }
 
 hyb_status dftgemm_create(hyb_grid* g) {
     const int n = g->d.n1, nc = n + 2;
     const double pi = 3.14159265358979323846;
-    std::vector<double> F((size_t)n * nc), I((size_t)nc * n);
+    std::vector<double> F((size_t)nc * n), I((size_t)n * nc);     // F[out][in], I[out][in]
     for (int j = 0; j < n; j++)
         for (int k = 0; k <= n / 2; k++) {
-            const double a = 2.0 * pi * (double)(((int64_t)k * j) % n) / n;
-            F[(size_t)j * nc + 2 * k] = cos(a);
-            F[(size_t)j * nc + 2 * k + 1] = -sin(a);
+            const double ang = 2.0 * pi * (double)(((int64_t)k * j) % n) / n;
+            F[(size_t)(2 * k) * n + j] = cos(ang);
+            F[(size_t)(2 * k + 1) * n + j] = -sin(ang);
             const double w = (k == 0 || k == n / 2) ? 1.0 : 2.0;
-            I[(size_t)(2 * k) * n + j] = w * cos(a) / n;
-            I[(size_t)(2 * k + 1) * n + j] = -w * sin(a) / n;
+            I[(size_t)j * nc + 2 * k] = w * cos(ang) / n;
+            I[(size_t)j * nc + 2 * k + 1] = -w * sin(ang) / n;
         }
-    const int ncp = (nc + 15) & ~15;          // inverse K segment, padded with zero rows
-    I.resize((size_t)ncp * n, 0.0);
-    std::vector<__nv_bfloat16> fh, fl, ih, il;
-    split_host(F, fh, fl);
-    split_host(I, ih, il);
-    // stacked [hi; lo; hi] along K
-    std::vector<__nv_bfloat16> Bf((size_t)3 * n * nc), Bi((size_t)3 * ncp * n);
-    for (size_t i = 0; i < fh.size(); i++) { Bf[i] = fh[i]; Bf[fh.size() + i] = fl[i]; Bf[2 * fh.size() + i] = fh[i]; }
-    for (size_t i = 0; i < ih.size(); i++) { Bi[i] = ih[i]; Bi[ih.size() + i] = il[i]; Bi[2 * ih.size() + i] = ih[i]; }
     DftPlan* P = new DftPlan();
     g->dft = P;
-    HYB_CUDA_TRY(cudaMalloc(&P->Bf, sizeof(__nv_bfloat16) * Bf.size()));
-    HYB_CUDA_TRY(cudaMemcpy(P->Bf, Bf.data(), sizeof(__nv_bfloat16) * Bf.size(), cudaMemcpyHostToDevice));
-    HYB_CUDA_TRY(cudaMalloc(&P->Bi, sizeof(__nv_bfloat16) * Bi.size()));
-    HYB_CUDA_TRY(cudaMemcpy(P->Bi, Bi.data(), sizeof(__nv_bfloat16) * Bi.size(), cudaMemcpyHostToDevice));
-    P->a_elems = (size_t)9 * g->rows * 3 * ncp;
-    HYB_CUDA_TRY(cudaMalloc(&P->Asplit, sizeof(__nv_bfloat16) * P->a_elems));
-    return HYB_OK;
+    hyb_status st = make_op(g, P->fwd, F, nc, n);
+    if (st == HYB_OK) st = make_op(g, P->inv, I, n, nc);
+    return st;
 }
 
 void dftgemm_destroy(hyb_grid* g) {
     DftPlan* P = reinterpret_cast<DftPlan*>(g->dft);
     if (!P) return;
-    cudaFree(P->Bf); cudaFree(P->Bi); cudaFree(P->Asplit);
+    cudaFree(P->fwd.B);
+    cudaFree(P->inv.B);
     delete P;
     g->dft = nullptr;
 }
 
-static void dgemm(int M, int N, int K, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, float* C,
-                  int64_t ldc, cudaStream_t s) {
-    dim3 grid((M + GM - 1) / GM, (N + GN - 1) / GN);     // M tiles on x: up to 2^31 - 1 blocks
-    k_dgemm<<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+static cudaError_t launch_op(const hyb_grid* g, const DftOp& op, const float* const* src, int ls, float* const* dst,
+                             int ld, int nf) {
+    DgArgs a{};
+    for (int f = 0; f < nf; f++) { a.src[f] = src[f]; a.dst[f] = dst[f]; }
+    a.nf = nf;
+    a.rows = g->rows;
+    a.L = op.K;
+    a.ls = ls;
+    a.N = op.N;
+    a.ld = ld;
+    a.nkc = op.nkc;
+    a.npass = op.npass;
+    for (int p = 0; p < 4; p++) { a.npc[p] = op.npc[p]; a.boff[p] = op.boff[p]; }
+    a.B = op.B;
+    a.tcols = op.tcols;
+    a.err = g->dflag;
+    const int64_t items = ((int64_t)nf * g->rows + dg::BM - 1) / dg::BM * op.npass;
+    const int grid = (int)std::min<int64_t>(op.grid, items);
+    op.kern<<<grid, dg::NT, op.smem, g->stream>>>(a);
+    return cudaGetLastError();
 }
 
 // forward transform of nf fields into spec (FP32 complex [nf][rows][n1/2+1])
 hyb_status dftgemm_forward(hyb_grid* g, const float* const* fields, int nf, float2* spec) {
     DftPlan* P = reinterpret_cast<DftPlan*>(g->dft);
     const int n = g->d.n1, nc = n + 2;
-    const int64_t rows = g->rows;
-    SplitSrc src{};
-    for (int f = 0; f < nf; f++) src.p[f] = fields[f];
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    k_split_rows<<<sms * 8, 256, 0, g->stream>>>(src, nf, rows, n, n, n, P->Asplit);
-    HYB_CUDA_TRY(cudaGetLastError());
-    dgemm((int)(nf * rows), nc, 3 * n, P->Asplit, 3 * n, P->Bf, nc, reinterpret_cast<float*>(spec), nc, g->stream);
-    HYB_CUDA_TRY(cudaGetLastError());
+    float* dst[9];
+    for (int f = 0; f < nf; f++) dst[f] = reinterpret_cast<float*>(spec) + (size_t)f * g->rows * nc;
+    HYB_CUDA_TRY(launch_op(g, P->fwd, fields, n, dst, nc, nf));
     return HYB_OK;
 }
 
@@ -190,18 +418,9 @@ hyb_status dftgemm_forward(hyb_grid* g, const float* const* fields, int nf, floa
 hyb_status dftgemm_inverse(hyb_grid* g, const float2* spec, int nf, float* const* fields) {
     DftPlan* P = reinterpret_cast<DftPlan*>(g->dft);
     const int n = g->d.n1, nc = n + 2;
-    const int64_t rows = g->rows;
-    SplitSrc src{};
-    for (int f = 0; f < nf; f++) src.p[f] = reinterpret_cast<const float*>(spec) + (size_t)f * rows * nc;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    const int ncp = (nc + 15) & ~15;
-    k_split_rows<<<sms * 8, 256, 0, g->stream>>>(src, nf, rows, nc, ncp, nc, P->Asplit);
-    HYB_CUDA_TRY(cudaGetLastError());
-    // one product per field, written straight into its array
-    for (int f = 0; f < nf; f++)
-        dgemm((int)rows, n, 3 * ncp, P->Asplit + (size_t)f * rows * 3 * ncp, 3 * ncp, P->Bi, n, fields[f], n, g->stream);
-    HYB_CUDA_TRY(cudaGetLastError());
+    const float* src[9];
+    for (int f = 0; f < nf; f++) src[f] = reinterpret_cast<const float*>(spec) + (size_t)f * g->rows * nc;
+    HYB_CUDA_TRY(launch_op(g, P->inv, src, nc, const_cast<float* const*>(fields), n, nf));
     return HYB_OK;
 }
 

@@ -506,7 +506,7 @@ const char* hyb_step_kernel(const hyb_grid* g) {
 int hyb_launches_per_step(const hyb_grid* g) {
     if (!g) return 0;
     if (g->path == 2 && !g->resident) return fused_launches_per_step(g);
-    if (g->path == 3) return 11;     // split + product (forward), Faraday, Ampere, split + 6 products (inverse)
+    if (g->path == 3) return 4;      // forward product, Faraday, Ampere, inverse product
     return generic_launches_per_step(g);
 }
 
