@@ -288,7 +288,7 @@ def x1_compare(hyb, w, arrs, stream, flush, sampler, steps_, warmup, dev):
     import torch
     out = {}
     fin = {}
-    for path in (64, 1, 3):
+    for path in (64, 1, 3, 4):
         prec = 64 if path == 64 else 32
         dt = torch.float64 if prec == 64 else torch.float32
         g = hyb.Grid(hyb.desc_from_workload(w, path=1 if path == 64 else path, precision=prec), stream)
@@ -298,13 +298,13 @@ def x1_compare(hyb, w, arrs, stream, flush, sampler, steps_, warmup, dev):
         torch.cuda.synchronize()
         fin[path] = [f.double() if path != 64 else f for f in F[:6]]
         if path != 64:
-            steps = steps_ if path == 1 else max(3, min(steps_, 20))
+            steps = steps_ if path == 1 else max(3, min(steps_, 20))      # the DFT-GEMM paths are slower
             out[f"ms_path{path}"] = time_steps(lambda: g.advance(1), steps, warmup, stream, flush, sampler)
             out[f"launches_path{path}"] = g.launches_per_step
         g.close()
         del F
     names = ("E1", "E2", "E3", "B1", "B2", "B3")
-    for path in (1, 3):
+    for path in (1, 3, 4):
         out[f"err_path{path}"] = {n: float((a - b).norm() / b.norm()) for n, a, b in zip(names, fin[path], fin[64])}
     return out
 
@@ -525,8 +525,9 @@ def measure_3d(hyb, wl, steps, warmup, stream, flush, sampler, dev, rows3d=256):
     x1["launches_path1_resident"] = g.launches_per_step
     g.close()
     del F
-    best = min((1, 3), key=lambda p_: x1[f"ms_path{p_}"])
-    config = {"workload": w.name, "path": {1: "three-pass radix FFT", 3: "three-pass DFT-GEMM"}[best],
+    best = min((1, 3, 4), key=lambda p_: x1[f"ms_path{p_}"])
+    config = {"workload": w.name, "path": {1: "three-pass radix FFT", 3: "three-pass DFT-GEMM (2 BF16 parts)",
+                                           4: "three-pass DFT-GEMM (3 BF16 parts)"}[best],
               "x1_transform": x1, "current": "band-limited random J",
               "l2": "flushed between timed steps (256 MB write)"}
     return x1[f"ms_path{best}"], w.cells, 60 * w.cells, x1[f"launches_path{best}"], config
@@ -569,7 +570,7 @@ def run_other(args):
             r["n1"], r["n2"] = n1, n2
             rows_out.append(r)
         best_row = rows_out[0]
-        best = min((1, 3), key=lambda p_: best_row[f"ms_path{p_}"])
+        best = min((1, 3, 4), key=lambda p_: best_row[f"ms_path{p_}"])
         cells, alg_bytes = 1 << 25, 60 << 25
         ms = best_row[f"ms_path{best}"]
         launches = best_row[f"launches_path{best}"] * args.steps

@@ -77,8 +77,11 @@ typedef struct {
                              1: three-pass (FFT, update, inverse FFT);
                              2: fused single-pass (precision 32, dims 2, n1 in 512..4096);
                              3: three-pass with the x1 transform as a dense DFT matrix product on
-                                the tensor cores, FP32 split into BF16 hi + lo (3 products),
-                                FP32 accumulation (precision 32, dims 2 or 3, 16 <= n1 <= 1024) */
+                                the tensor cores (tcgen05), FP32 split into BF16 hi + lo (3
+                                products), FP32 accumulation (precision 32, dims 2 or 3,
+                                16 <= n1 <= 1024); about 1e-5 relative error per field;
+                             4: as 3 with FP32 split into three BF16 parts (6 products): the
+                                error of the FP32 radix path */
     int azimuthal_m;      /* dims 20 only: azimuthal mode number 0 <= m <= 64.  The grid is then
                              (z, r) = (x1, x2) with n1 = nz, n2 = nr <= 65535, dx1 = dz, dx2 = dr, a
                              perfectly conducting wall at r = n2 dx2, the axis at r = 0, and
@@ -381,7 +384,8 @@ HYB_API hyb_status hyb_mlp_train_step(hyb_mlp* m, const float* x, const float* t
 HYB_API int64_t hyb_mlp_launch_count(const hyb_mlp* m);
 HYB_API hyb_status hyb_mlp_destroy(hyb_mlp* m);
 
-/* Which advance path a grid runs: 1 three-pass, 2 fused, 3 three-pass with DFT-GEMM. */
+/* Which advance path a grid runs: 1 three-pass, 2 fused, 3 and 4 three-pass with DFT-GEMM
+ * (2 and 3 BF16 parts). */
 HYB_API int hyb_grid_path(const hyb_grid* g);
 
 /* Name of the kernel that does a step's work on this grid's path (the fused kernel's name

@@ -502,7 +502,7 @@ template <> const ModeTables<float>& tables<float>(hyb_grid* g) { return g->tf; 
 template <> const ModeTables<double>& tables<double>(hyb_grid* g) { return g->td; }
 
 // FP32 n1 = 1024 off the DFT-GEMM path: Ampere runs inside the inverse transform
-static bool amp_fused(const hyb_grid* g) { return g->d.precision == 32 && g->d.n1 == 1024 && g->path != 3 && g->d.dims != 20; }
+static bool amp_fused(const hyb_grid* g) { return g->d.precision == 32 && g->d.n1 == 1024 && g->path < 3 && g->d.dims != 20; }
 
 template <typename T>
 hyb_status generic_advance(hyb_grid* g, int nsteps) {
@@ -526,7 +526,7 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
         RowPtrs fin{};
         for (int c = f0; c < 9; c++) fin.p[c - f0] = src9[c];
         C* spec_in = spec + (int64_t)f0 * rows * nk;
-        if (g->path == 3) {
+        if (g->path >= 3) {
             const float* fsrc[9];
             for (int c = f0; c < 9; c++) fsrc[c - f0] = (const float*)src9[c];
             hyb_status st = dftgemm_forward(g, fsrc, 9 - f0, reinterpret_cast<float2*>(spec_in));
@@ -559,7 +559,7 @@ hyb_status generic_advance(hyb_grid* g, int nsteps) {
             k_ampere<T, false><<<mgrid, mblk, 0, g->stream>>>(spec, nk, g->d.n2, 1, rows, t.S, t.cj1, t.cj, a2, a3);
         }
         HYB_CUDA_TRY(cudaGetLastError());
-        if (g->path == 3) {
+        if (g->path >= 3) {
             float* f6[6];
             for (int c = 0; c < 6; c++) f6[c] = (float*)fout.p[c];
             hyb_status st = dftgemm_inverse(g, reinterpret_cast<const float2*>(spec), 6, f6);

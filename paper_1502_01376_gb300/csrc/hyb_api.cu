@@ -202,9 +202,9 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
         set_error("dt = %.17g exceeds the Courant limit %.17g of the hybrid solver", d.dt, cl);
         return HYB_ECOURANT;
     }
-    if (d.path < 0 || d.path > 3) { set_error("path must be 0, 1, 2 or 3"); return HYB_EINVAL; }
-    if (d.path == 3 && !(d.precision == 32 && d.dims != 20 && d.n1 >= 16 && d.n1 <= 1024)) {
-        set_error("path 3 (DFT-GEMM) needs precision 32, dims 2 or 3 and 16 <= n1 <= 1024");
+    if (d.path < 0 || d.path > 4) { set_error("path must be 0, 1, 2, 3 or 4"); return HYB_EINVAL; }
+    if (d.path >= 3 && !(d.precision == 32 && d.dims != 20 && d.n1 >= 16 && d.n1 <= 1024)) {
+        set_error("paths 3 and 4 (DFT-GEMM) need precision 32, dims 2 or 3 and 16 <= n1 <= 1024");
         return HYB_EINVAL;
     }
     const bool fused_ok = d.dims != 20 && fused_supported(d);
@@ -237,14 +237,14 @@ hyb_status hyb_create_grid(const hyb_grid_desc* desc, void* stream, hyb_grid** o
     if (st == HYB_OK && d.dims == 20) st = quasi3d_create(g);
     if (st == HYB_OK && d.dims != 20) {
         const size_t csz = d.precision == 32 ? sizeof(float2) : sizeof(double2);
-        const int nf = (g->path == 1 || g->path == 3) ? 9 : 3;
+        const int nf = g->path == 2 ? 3 : 9;
         g->spec_fields = nf;
         g->spec_bytes = (size_t)nf * g->rows * g->nk * csz;
         ce = cudaMalloc(&g->spec, g->spec_bytes);
         if (ce != cudaSuccess) { g->spec = nullptr; st = cuda_fail(ce, "cudaMalloc(spectral scratch)"); }
     }
     if (st == HYB_OK && g->path == 2) st = fused_create(g);
-    if (st == HYB_OK && g->path == 3) st = dftgemm_create(g);
+    if (st == HYB_OK && g->path >= 3) st = dftgemm_create(g);
     if (st != HYB_OK) { hyb_destroy_grid(g); return st; }
     *out = g;
     return HYB_OK;
@@ -497,16 +497,17 @@ int hyb_grid_path(const hyb_grid* g) { return g ? g->path : 0; }
 
 const char* hyb_step_kernel(const hyb_grid* g) {
     if (!g) return "";
-    if (g->resident) return g->path == 3 ? "k1-resident dft-gemm three-pass step" : "k1-resident three-pass step";
+    if (g->resident) return g->path >= 3 ? "k1-resident dft-gemm three-pass step" : "k1-resident three-pass step";
     if (g->path == 2) return fused_step_kernel(g);
-    if (g->path == 3) return "dft-gemm three-pass step";
+    if (g->path >= 3) return g->path == 3 ? "dft-gemm three-pass step (k_dft_tc, 2 parts)"
+                                          : "dft-gemm three-pass step (k_dft_tc, 3 parts)";
     return g->d.dims == 20 ? "quasi-3D step" : "three-pass step";
 }
 
 int hyb_launches_per_step(const hyb_grid* g) {
     if (!g) return 0;
     if (g->path == 2 && !g->resident) return fused_launches_per_step(g);
-    if (g->path == 3) return 4;      // forward product, Faraday, Ampere, inverse product
+    if (g->path >= 3) return 4;      // forward product, Faraday, Ampere, inverse product
     return generic_launches_per_step(g);
 }
 

@@ -5,7 +5,12 @@ hi*hi + hi*lo + lo*hi of the BF16 split; the dropped lo*lo term and the BF16
 rounding of lo leave about 2^-17 relative error per matrix entry, so after
 forward + inverse transforms over five steps the per-field relative L2 error is
 1.1e-5 to 1.4e-5 for n1 <= 256 and 2.9e-5 at n1 = 1024 (measured); the bound
-here is 1e-4."""
+here is 6e-5.  Path 4 splits FP32 into three BF16 parts and keeps the six
+products A_i M_j with i + j < 3: the dropped terms are about 2^-25 relative,
+which leaves the FP32 accumulation of the K = n1 (n1 + 2) terms in the tensor
+core as the error, growing with n1 (measured after 5 steps: 1.0e-6 at n1 = 16,
+6.6e-6 at 128, 1.2e-5 at 256, 4.6e-5 at 1024), so path 4 meets the 1e-5
+per-field bound for the short rows (n1 <= 128) the DFT-GEMM is meant for."""
 import numpy as np
 import pytest
 
@@ -15,7 +20,8 @@ from gpu_util import hyb_module, need_gpu, orc_grid, rel_err, to_dev, to_np, tor
 
 pytestmark = pytest.mark.gpu
 
-TOL_DFT = 1e-4
+TOL_DFT = {3: 6e-5, 4: 6e-5}
+TOL_SHORT = 1e-5          # path 4, n1 <= 128
 
 
 def _run(orc, w, path, nst):
@@ -38,32 +44,36 @@ def _run(orc, w, path, nst):
     return [rel_err(to_np(a), b) for a, b in zip(E + B, Eo + Bo)]
 
 
-@pytest.mark.parametrize("n1,n2", [(16, 9), (64, 37), (128, 20), (256, 33), (1024, 3)])
-def test_dftgemm_2d_per_field(orc, n1, n2):
+@pytest.mark.parametrize("path", [3, 4])
+@pytest.mark.parametrize("n1,n2", [(16, 9), (32, 300), (64, 37), (128, 20), (256, 33), (1024, 3)])
+def test_dftgemm_2d_per_field(orc, n1, n2, path):
     need_gpu()
     w = wl.Workload("t", 2, n1, n2, dx1=0.2, dx2=0.25, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2, seed=5)
-    errs = _run(orc, w, 3, 5)
-    print(f"n1 {n1}: per-field error after 5 steps {max(errs):.2e}")
-    assert max(errs) < TOL_DFT, errs
+    errs = _run(orc, w, path, 5)
+    print(f"path {path} n1 {n1}: per-field error after 5 steps {max(errs):.2e}")
+    assert max(errs) < (TOL_SHORT if path == 4 and n1 <= 128 else TOL_DFT[path]), errs
 
 
-def test_dftgemm_3d_per_field(orc):
+@pytest.mark.parametrize("path", [3, 4])
+def test_dftgemm_3d_per_field(orc, path):
     need_gpu()
     w = wl.Workload("t", 3, 64, 12, 10, dx1=0.2, dx2=0.25, dx3=0.3, dt=0.05, precision=32, filt_kc=0.6,
                     filt_w=0.2, seed=6)
-    errs = _run(orc, w, 3, 4)
-    assert max(errs) < TOL_DFT, errs
+    errs = _run(orc, w, path, 4)
+    assert max(errs) < (TOL_SHORT if path == 4 else TOL_DFT[path]), errs
 
 
 def test_dftgemm_tracks_radix_path(orc):
     """Both FP32 paths on the same inputs: the DFT-GEMM error stays within a
     small factor of the radix FFT's FP32 error plus the split-BF16 bound."""
     need_gpu()
-    w = wl.Workload("t", 2, 128, 40, dx1=0.2, dx2=0.25, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2, seed=8)
+    w = wl.Workload("t", 2, 32, 160, dx1=0.2, dx2=0.25, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2, seed=8)
     e3 = _run(orc, w, 3, 8)
     e1 = _run(orc, w, 1, 8)
     assert max(e1) < 1e-5, e1
-    assert all(a < 10 * b + TOL_DFT for a, b in zip(e3, e1)), (e3, e1)
+    assert all(a < 10 * b + TOL_DFT[3] for a, b in zip(e3, e1)), (e3, e1)
+    e4 = _run(orc, w, 4, 8)
+    assert max(e4) < 0.5 * max(e3), (e4, e3)          # the third part buys accuracy (short rows)
 
 
 def test_dftgemm_rejects_unsupported():
@@ -71,8 +81,9 @@ def test_dftgemm_rejects_unsupported():
     hyb = hyb_module()
     for bad in (dict(precision=64, n1=64), dict(precision=32, n1=2048), dict(precision=32, n1=8)):
         w = wl.Workload("t", 2, bad["n1"], 8, dx1=0.2, dx2=0.25, dt=0.05, precision=bad["precision"], seed=1)
-        with pytest.raises(Exception):
-            hyb.Grid(hyb.desc_from_workload(w, path=3))
+        for path in (3, 4):
+            with pytest.raises(Exception):
+                hyb.Grid(hyb.desc_from_workload(w, path=path))
 
 
 def test_auto_path_picks_measured_transform():
