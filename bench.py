@@ -54,6 +54,10 @@ def parse():
                     help="batched workload: rows per strip per n1 as '512:3,1024:2,...' instead of the autotuner")
     ap.add_argument("--ppc", type=int, default=8,
                     help="push workload: particles per cell per species (8 is the benchmark; fewer for profiling)")
+    ap.add_argument("--sweep-n1", default="16,32,64,128,256,512,1024",
+                    help="x1_sweep workload: the row lengths to run (comma-separated)")
+    ap.add_argument("--sweep-cells", type=int, default=1 << 25,
+                    help="x1_sweep workload: cells per grid (2^25 is the sweep; smaller sizes are for profiling)")
     ap.add_argument("--rows3d", type=int, default=256,
                     help="3d workload: n2 = n3 = this (256 is the benchmark; smaller sizes are for profiling)")
     ap.add_argument("--workload", default="drift_plasma",
@@ -560,8 +564,8 @@ def run_other(args):
         dtype = "f32"
     elif args.workload == "x1_sweep":
         rows_out = []
-        for n1 in (16, 32, 64, 128, 256, 512, 1024):
-            n2 = (1 << 25) // n1
+        for n1 in (int(v) for v in args.sweep_n1.split(",")):
+            n2 = args.sweep_cells // n1
             w = wl.Workload(f"sweep_{n1}", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.08, precision=32, filt_kc=0.5,
                             filt_w=0.2, seed=3)
             gen = np.random.default_rng(n1)
@@ -571,10 +575,11 @@ def run_other(args):
             rows_out.append(r)
         best_row = rows_out[0]
         best = min((1, 3, 4), key=lambda p_: best_row[f"ms_path{p_}"])
-        cells, alg_bytes = 1 << 25, 60 << 25
+        cells, alg_bytes = args.sweep_cells, 60 * args.sweep_cells
         ms = best_row[f"ms_path{best}"]
         launches = best_row[f"launches_path{best}"] * args.steps
-        extra["config"] = {"workload": "x1_transform_sweep_2d_2^25_cells_f32", "value_at": "n1 = 16",
+        extra["config"] = {"workload": f"x1_transform_sweep_2d_{args.sweep_cells}_cells_f32",
+                           "value_at": f"n1 = {rows_out[0]['n1']}",
                            "sweep": rows_out, "current": "random J", "l2": "flushed between timed steps"}
         dtype = "f32"
     else:
