@@ -61,31 +61,6 @@ __host__ __device__ constexpr int off_b(int S) { return ((S * A_IMG + 127) / 128
 __host__ __device__ constexpr int pass_cols(int S) { return S == 2 ? 512 : 256; }
 }  // namespace dg
 
-// shared-memory matrix descriptor of tcgen05: start, leading (K-direction core matrix) and
-// stride (M/N-direction 8-row group) byte offsets, fixed version bits 46-48 = 1, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
-}
-// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                 :: "r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate) : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
-}
-// bounded wait that ignores the abort flag: used to drain copies and products in flight
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return;
-}
-
 struct DgArgs {
     const float* src[9];          // source arrays: rows x L valid values, row stride ls floats
     float* dst[9];                // destination arrays: rows x N valid values, row stride ld floats

@@ -3,9 +3,11 @@
 // activations as tensor-core operands, FP32 accumulation, FP32 master
 // weights).  Architecture: n_in -> width x depth (tanh) -> 1 (linear).
 //
-// The GEMMs use the BF16 tensor-core instruction mma.sync.m16n8k16 with FP32
-// accumulation on 64 x 64 output tiles staged through shared memory; the
-// network is small (widths 16..256), so this is not a roofline-bound path.
+// The GEMMs run on the fifth-generation tensor cores: tcgen05.mma (kind::f16,
+// BF16 operands) into FP32 accumulators in tensor memory, 128 x 64 output tiles
+// per CTA, operands gathered into shared memory from any strides (the weight
+// gradients read the activations transposed); the network is small (widths
+// 16..256), so this is not a roofline-bound path.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -13,6 +15,7 @@
 #include <vector>
 
 #include "hyb_internal.cuh"
+#include "tm_dev.cuh"
 
 struct hyb_mlp {
     int n_in = 0, width = 0, depth = 0;   // hidden layers of `width`
@@ -33,105 +36,136 @@ struct hyb_mlp {
     __nv_bfloat16* dhb = nullptr;         // BF16 copy of dH
     float* dx = nullptr;                  // [cap][256] FP32 dX
     float* loss = nullptr;                // device scalar
+    int* err = nullptr;                   // device flag: bit 1 = a bounded wait in a GEMM gave up
     int64_t step = 0;
     int64_t launches = 0;                 // kernels launched so far (hyb_mlp_launch_count)
 };
 
 namespace hyb {
 
-constexpr int TM = 64, TN = 64, TK = 16;
-
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
+// GEMM tiles: 128 x 64 outputs per CTA (tcgen05.mma M = 128, N = 64), K in chunks of 64
+constexpr int TM = 128, TN = 64, TKC = 64, GT = 128;
+constexpr int LBO_A = TM * 16 + 16, LBO_B = TN * 16 + 16;     // K-group strides (16-byte slots spread)
 
 // C[m][n] (FP32) = sum_k A(m,k) B(k,n), A(m,k) = a[m*sam + k*sak], B(k,n) = b[k*sbk + n*sbn]
-// (BF16), M, N, K multiples of 16; accumulate into C if acc != 0.  Split K: block z
-// handles k in [z*kchunk, (z+1)*kchunk) and, when gridDim.z > 1, adds its partial sums
-// atomically (C then holds the caller's zero or previous values).
-__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, int kmax, const __nv_bfloat16* __restrict__ a, int64_t sam, int64_t sak,
-                                                   const __nv_bfloat16* __restrict__ b, int64_t sbk, int64_t sbn,
-                                                   float* __restrict__ c, int64_t scm, int acc, int kchunk) {
-    __shared__ __nv_bfloat16 As[TM][TK + 8];
-    __shared__ __nv_bfloat16 Bs[TN][TK + 8];      // stored as [n][k]
-    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gq = lane >> 2, tq = lane & 3;
-    float accf[2][4][4];
+// (BF16), K a multiple of 16, entries with k >= kmax read as zero; accumulate into C if
+// acc != 0.  Split K: block z handles k in [z*kchunk, (z+1)*kchunk) and, when gridDim.z > 1,
+// adds its partial sums atomically (C then holds the caller's zero or previous values).
+// Per 64-wide K chunk the 128 threads gather the A and B tiles into shared memory in the
+// canonical K-major layout without swizzle (8 x 16-byte core matrices; 16-byte slots (row, k/8),
+// filled along whichever index of the source is contiguous), one thread issues the k-steps of
+// tcgen05.mma into the 128 x 64 FP32 accumulator in TMEM and commits them to an mbarrier, and
+// after the last chunk each warp reads its 32 rows with tcgen05.ld.  Waits are bounded: on
+// time-out bit 1 of *err is set and the CTA skips the rest, drains and frees its TMEM.
+__device__ __forceinline__ void gemm_fill(uint32_t dst, int lbo, int rows, int rmax, int r0, int k0, int kmax,
+                                          const __nv_bfloat16* __restrict__ src, int64_t sr, int64_t sk, int tid) {
+    // 16-byte slots (row r, group g of 8 k values): rows x 8 slots
+    const bool kfast = sk == 1 && (sr & 7) == 0;
+    for (int i = tid; i < rows * 8; i += GT) {
+        const int r = kfast ? i >> 3 : i % rows, g = kfast ? i & 7 : i / rows;
+        const int row = r0 + r, k = k0 + 8 * g;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row < rmax) {
+            if (kfast && k + 8 <= kmax) {
+                v = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)row * sr + k));
+            } else {
+                uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int r = 0; r < 4; r++) accf[i][j][r] = 0.f;
-    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    // tile fills walk the unit-stride index fastest (coalesced global reads)
-    const bool a_m_fast = (sam == 1), b_n_fast = (sbn == 1);
-    for (int k0 = kb; k0 < ke; k0 += TK) {
-        for (int i = threadIdx.x; i < TM * TK; i += blockDim.x) {
-            const int r = a_m_fast ? i % TM : i / TK, kk = a_m_fast ? i / TM : i % TK;
-            const int m = m0 + r, k = k0 + kk;
-            As[r][kk] = (m < M && k < kmax) ? a[(int64_t)m * sam + (int64_t)k * sak] : __float2bfloat16(0.f);
+                for (int e = 0; e < 8; e++) {
+                    const uint32_t x = (k + e < kmax) ? (uint32_t)__bfloat16_as_ushort(src[(int64_t)row * sr + (int64_t)(k + e) * sk]) : 0u;
+                    w[e >> 1] |= x << (16 * (e & 1));
+                }
+                v = make_uint4(w[0], w[1], w[2], w[3]);
+            }
         }
-        for (int i = threadIdx.x; i < TN * TK; i += blockDim.x) {
-            const int r = b_n_fast ? i % TN : i / TK, kk = b_n_fast ? i / TN : i % TK;
-            const int n = n0 + r, k = k0 + kk;
-            Bs[r][kk] = (n < N && k < kmax) ? b[(int64_t)k * sbk + (int64_t)n * sbn] : __float2bfloat16(0.f);
-        }
-        __syncthreads();
-        uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-        for (int i = 0; i < 2; i++) {
-            const int r = wm + i * 16;
-            af[i][0] = pack_bf16(As[r + gq][2 * tq], As[r + gq][2 * tq + 1]);
-            af[i][1] = pack_bf16(As[r + gq + 8][2 * tq], As[r + gq + 8][2 * tq + 1]);
-            af[i][2] = pack_bf16(As[r + gq][2 * tq + 8], As[r + gq][2 * tq + 9]);
-            af[i][3] = pack_bf16(As[r + gq + 8][2 * tq + 8], As[r + gq + 8][2 * tq + 9]);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int cn = wn + j * 8 + gq;
-            bfr[j][0] = pack_bf16(Bs[cn][2 * tq], Bs[cn][2 * tq + 1]);
-            bfr[j][1] = pack_bf16(Bs[cn][2 * tq + 8], Bs[cn][2 * tq + 9]);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; i++)
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                             "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                             : "+f"(accf[i][j][0]), "+f"(accf[i][j][1]), "+f"(accf[i][j][2]), "+f"(accf[i][j][3])
-                             : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
-        __syncthreads();
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                     :: "r"(dst + (uint32_t)(g * lbo + 16 * r)), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
     }
+}
+
+__global__ void __launch_bounds__(GT) k_gemm_tc(int M, int N, int K, int kmax, const __nv_bfloat16* __restrict__ a, int64_t sam, int64_t sak,
+                                                const __nv_bfloat16* __restrict__ b, int64_t sbk, int64_t sbn,
+                                                float* __restrict__ c, int64_t scm, int acc, int kchunk, int* err) {
+    __shared__ __align__(128) unsigned char sbuf[8 * LBO_A + 8 * LBO_B];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sA = smem_addr(sbuf), sB = sA + 8 * LBO_A, mb = smem_addr(&bar);
+    if (warp == 0) {
+        tm_alloc(smem_addr(&s_taddr), TN);
+        tm_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(mb, 1);
+        mbar_fence_init();
+        s_abort = 0;
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    const uint32_t tbase = s_taddr;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    uint32_t ph = 0;
+    bool pend = false, abort = false, any = false;
+    for (int k0 = kb; k0 < ke && !abort; k0 += TKC) {
+        gemm_fill(sA, LBO_A, TM, M, m0, k0, kmax, a, sam, sak, tid);
+        gemm_fill(sB, LBO_B, TN, N, n0, k0, kmax, b, sbn, sbk, tid);
+        fence_proxy_async_smem();
+        tm_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tm_fence_after();
+            const int nks = min(TKC, ke - k0) / 16;
+            for (int ks = 0; ks < nks; ks++)
+                mma_bf16(tbase, smem_desc(sA + 2 * ks * LBO_A, LBO_A, 128), smem_desc(sB + 2 * ks * LBO_B, LBO_B, 128),
+                         idesc_bf16(TN), (k0 > kb || ks > 0) ? 1u : 0u);
+            mma_commit(mb);
+            pend = true;
+            mbar_wait(mb, ph, err, &s_abort);
+            if (!s_abort) {
+                ph ^= 1;
+                pend = false;
+            }
+        }
+        __syncthreads();
+        abort = s_abort != 0;
+        any = true;
+    }
+    if (any && !abort) {
+        tm_fence_after();
+        const int row = m0 + 32 * warp + lane;
 #pragma unroll
-    for (int i = 0; i < 2; i++)
+        for (int u = 0; u < TN / 16; u++) {
+            float t[16];
+            tm_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * u), t);
+            tm_wait_ld();
+            if (row < M) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int r = m0 + wm + i * 16 + gq, cc = n0 + wn + j * 8 + 2 * tq;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int rr = r + 8 * h;
-                if (rr < M) {
-#pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        if (cc + q < N) {
-                            float* p = c + (int64_t)rr * scm + cc + q;
-                            if (gridDim.z > 1) atomicAdd(p, accf[i][j][2 * h + q]);
-                            else *p = acc ? *p + accf[i][j][2 * h + q] : accf[i][j][2 * h + q];
-                        }
+                for (int j = 0; j < 16; j++) {
+                    const int col = n0 + 16 * u + j;
+                    if (col < N) {
+                        float* p = c + (int64_t)row * scm + col;
+                        if (gridDim.z > 1) atomicAdd(p, t[j]);
+                        else *p = acc ? *p + t[j] : t[j];
                     }
                 }
             }
         }
+    }
+    if (tid == 0 && pend) mbar_drain(mb, ph);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (warp == 0) tm_dealloc(tbase, TN);
 }
 
-// K is rounded up to 16 (the tile depth); entries with k >= K read as zero
+// K is rounded up to 16 (the MMA depth); entries with k >= K read as zero
 // Few output tiles and a long K (the weight gradients: K = batch) are split along K
 // over up to 64 blocks per tile, the partial sums added atomically into C.
 static void gemm(int M, int N, int K, const __nv_bfloat16* a, int64_t sam, int64_t sak, const __nv_bfloat16* b, int64_t sbk,
-                 int64_t sbn, float* c, int64_t scm, int acc, cudaStream_t s, int64_t& launches) {
+                 int64_t sbn, float* c, int64_t scm, int acc, cudaStream_t s, int64_t& launches, int* err) {
     const int Kp = (K + 15) & ~15;
     const int tiles = ((N + TN - 1) / TN) * ((M + TM - 1) / TM);
     int split = 1;
@@ -139,7 +173,7 @@ static void gemm(int M, int N, int K, const __nv_bfloat16* a, int64_t sam, int64
     const int kchunk = ((Kp / split + 15) & ~15);
     if (split > 1 && !acc) cudaMemsetAsync(c, 0, sizeof(float) * (size_t)M * scm, s);   // rows of stride scm >= N
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, split);
-    k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, Kp, K, a, sam, sak, b, sbk, sbn, c, scm, acc, kchunk);
+    k_gemm_tc<<<grid, GT, 0, s>>>(M, N, Kp, K, a, sam, sak, b, sbk, sbn, c, scm, acc, kchunk, err);
     launches++;
 }
 
@@ -280,7 +314,7 @@ static hyb_status forward(hyb_mlp* m, const float* x, int64_t B, float* y, cudaS
         const __nv_bfloat16* X = m->act + (size_t)l * cap * 256;
         float* H = m->pre + (size_t)l * cap * 256;
         // H[B][fo] = X[B][fi] W^T, W stored [fo][fi]
-        gemm((int)B, fo, fi, X, 256, 1, m->wbf + m->wb_off[l], 1, fi, H, 256, 0, s, m->launches);
+        gemm((int)B, fo, fi, X, 256, 1, m->wbf + m->wb_off[l], 1, fi, H, 256, 0, s, m->launches, m->err);
         const bool hidden = l < m->L - 1;
         k_bias_act<<<(unsigned)((B * fo + 255) / 256), 256, 0, s>>>(H, m->master + m->b_off[l], B, layer_out(m, l), fo, hidden,
                                                                   m->act + (size_t)(l + 1) * cap * 256, y);
@@ -301,14 +335,14 @@ static hyb_status backward(hyb_mlp* m, const float* tgt, int64_t B, cudaStream_t
         k_to_bf16<<<(unsigned)((B * 256 + 255) / 256), 256, 0, s>>>(m->dh, B * 256, m->dhb);
         m->launches++;
         // dW[fo][fi] = dH^T X: M = fo, N = fi, K = B (B padded to 16 with zero rows)
-        gemm(fo, fi, (int)B, m->dhb, 1, 256, m->act + (size_t)l * cap * 256, 256, 1, m->dx, 256, 0, s, m->launches);
+        gemm(fo, fi, (int)B, m->dhb, 1, 256, m->act + (size_t)l * cap * 256, 256, 1, m->dx, 256, 0, s, m->launches, m->err);
         k_copy_grad<<<(no * ni + 255) / 256, 256, 0, s>>>(m->dx, no, ni, 256, m->grad + m->w_off[l]);
         m->launches++;
         k_colsum<<<no, 256, 0, s>>>(m->dh, B, no, m->grad + m->b_off[l]);
         m->launches++;
         if (l > 0) {
             // dX[B][fi] = dH[B][fo] W[fo][fi]
-            gemm((int)B, fi, fo, m->dhb, 256, 1, m->wbf + m->wb_off[l], fi, 1, m->dx, 256, 0, s, m->launches);
+            gemm((int)B, fi, fo, m->dhb, 256, 1, m->wbf + m->wb_off[l], fi, 1, m->dx, 256, 0, s, m->launches, m->err);
             k_act_back<<<(unsigned)((B * fi + 255) / 256), 256, 0, s>>>(m->dx, m->pre + (size_t)(l - 1) * cap * 256, B, ni, fi, m->dh);
             m->launches++;
         }
@@ -345,6 +379,8 @@ hyb_status hyb_mlp_create(int n_in, int width, int depth, const float* init_para
     if (e == cudaSuccess) e = cudaMalloc(&m->grad, sizeof(float) * off);
     if (e == cudaSuccess) e = cudaMalloc(&m->wbf, sizeof(__nv_bfloat16) * woff);
     if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * off);
     if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * off);
     if (e == cudaSuccess && init_params) e = cudaMemcpy(m->master, init_params, sizeof(float) * off, cudaMemcpyHostToDevice);
@@ -369,6 +405,13 @@ hyb_status hyb_mlp_get_params(hyb_mlp* m, float* params_host) {
     if (!m || !params_host) { set_error("null argument"); return HYB_EINVAL; }
     HYB_CUDA_TRY(cudaDeviceSynchronize());
     HYB_CUDA_TRY(cudaMemcpy(params_host, m->master, sizeof(float) * m->n_params, cudaMemcpyDeviceToHost));
+    int h = 0;
+    HYB_CUDA_TRY(cudaMemcpy(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        cudaMemset(m->err, 0, sizeof(int));
+        set_error("a bounded device-side wait in the surrogate's GEMMs gave up");
+        return HYB_ETIMEOUT;
+    }
     return HYB_OK;
 }
 
@@ -416,6 +459,7 @@ hyb_status hyb_mlp_destroy(hyb_mlp* m) {
     if (!m) return HYB_OK;
     cudaDeviceSynchronize();
     cudaFree(m->master); cudaFree(m->adam_m); cudaFree(m->adam_v); cudaFree(m->grad); cudaFree(m->wbf); cudaFree(m->loss);
+    cudaFree(m->err);
     if (m->act) { cudaFree(m->act); cudaFree(m->pre); cudaFree(m->dh); cudaFree(m->dhb); cudaFree(m->dx); }
     delete m;
     return HYB_OK;
