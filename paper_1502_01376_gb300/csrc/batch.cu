@@ -1,8 +1,12 @@
 // batch.cu -- many independent grids advanced together, one CUDA-graph launch
 // per step.  Grids that run the fused FP32 kernel are grouped by n1; each
-// group is one persistent launch of k_fused2d<n1> over a table of work items
-// (grid, strip, first row, end row) from all its grids, preceded by one halo
-// launch.  Other grids (FP64, 3D, unsupported n1) run their three-pass step.
+// group is one persistent launch of k_fused2d<n1> (k_fused_tm for n1 = 4096)
+// over a table of work items (grid, strip, first row, end row) from all its
+// grids, after one launch that copies the halo rows of every group's items.
+// Quasi-3D modes with nz = 2048 and a common radial grid are advanced together
+// (z transform of all their arrays, leapfrog of all modes, inverse: three
+// launches for up to eight modes).  Other grids (FP64, 3D, unsupported n1, other
+// quasi-3D modes) run their own step.
 // Groups, and each of the other grids, are forked onto side streams inside the
 // captured graph so that they overlap.  hyb_batch_tune times candidate strip heights per group on scratch
 // fields and keeps the fastest (the autotuner).
@@ -21,13 +25,19 @@ struct hyb_batch {
         int4* items = nullptr;             // device work items
         int n_items = 0;
         int grid = 0;
+        std::vector<int4> h_items;         // host copy of the work items
         cudaStream_t side = nullptr;
         cudaEvent_t fork = nullptr, join = nullptr;
     };
     std::vector<Group> groups;
-    std::vector<int> others;               // grids on the three-pass path
+    std::vector<int> q3;                   // quasi-3D modes advanced together (quasi3d_advance_many)
+    cudaStream_t q3side = nullptr;
+    cudaEvent_t q3fork = nullptr, q3join = nullptr;
+    std::vector<int> others;               // other grids (three-pass path, other quasi-3D modes)
     std::vector<cudaStream_t> oside;       // one side stream (and fork/join events) per other grid
     std::vector<cudaEvent_t> ofork, ojoin;
+    hyb::RowCopy* halo_tasks = nullptr;    // device: the halo rows of all groups' items
+    int n_halo = 0, halo_cap = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;
@@ -54,6 +64,7 @@ static hyb_status group_plan(hyb_batch* b, hyb_batch::Group& G) {
     HYB_CUDA_TRY(cudaMalloc(&G.items, sizeof(int4) * items.size()));
     HYB_CUDA_TRY(cudaMemcpy(G.items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
     G.n_items = (int)items.size();
+    G.h_items = items;
     int occ = 0, sms = 0;
     HYB_CUDA_TRY(fused_occupancy(G.n1, &occ));
     HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->grids[0]->device));
@@ -74,13 +85,46 @@ static FusedBatch group_args(hyb_batch* b, const hyb_batch::Group& G) {
     return fb;
 }
 
-// enqueue one step of every group (forked onto side streams) and of the others
-static hyb_status enqueue_step(hyb_batch* b, cudaStream_t s) {
+// the halo rows of every group's work items (E1, E2, E3, B1, B3 of row p0 - 1; E1, E3 of row p1),
+// from the bound arrays into each grid's halo buffer: the task table of the one copy launch
+static hyb_status halo_plan(hyb_batch* b) {
+    std::vector<RowCopy> tasks;
     for (auto& G : b->groups) {
-        HYB_CUDA_TRY(cudaEventRecord(G.fork, s));
-        HYB_CUDA_TRY(cudaStreamWaitEvent(G.side, G.fork, 0));
-        HYB_CUDA_TRY(fused_launch(G.n1, group_args(b, G), G.grid, G.side, nullptr, nullptr));
-        HYB_CUDA_TRY(cudaEventRecord(G.join, G.side));
+        for (const int4& it : G.h_items) {
+            const hyb_grid* g = b->grids[G.members[it.x]];
+            const FusedInst a = fused_inst(g);
+            const int n1 = G.n1, n2 = a.n2, rl = (it.z - 1 + n2) % n2, rn = it.w % n2;
+            const float* src[7] = {a.E[0] + (size_t)rl * n1, a.E[1] + (size_t)rl * n1, a.E[2] + (size_t)rl * n1,
+                                   a.B[0] + (size_t)rl * n1, a.B[2] + (size_t)rl * n1, a.E[0] + (size_t)rn * n1,
+                                   a.E[2] + (size_t)rn * n1};
+            for (int k = 0; k < 7; k++)
+                tasks.push_back(RowCopy{src[k], const_cast<float*>(a.halo) + ((size_t)it.y * 7 + k) * n1, n1, 0});
+        }
+    }
+    if ((int)tasks.size() > b->halo_cap) {
+        if (b->halo_tasks) cudaFree(b->halo_tasks);
+        b->halo_tasks = nullptr;
+        b->halo_cap = 0;
+        HYB_CUDA_TRY(cudaMalloc(&b->halo_tasks, sizeof(RowCopy) * tasks.size()));
+        b->halo_cap = (int)tasks.size();
+    }
+    if (!tasks.empty())
+        HYB_CUDA_TRY(cudaMemcpy(b->halo_tasks, tasks.data(), sizeof(RowCopy) * tasks.size(), cudaMemcpyHostToDevice));
+    b->n_halo = (int)tasks.size();
+    return HYB_OK;
+}
+
+// enqueue one step: the others forked onto side streams, the halo copy of all groups, then
+// every group (forked onto side streams)
+static hyb_status enqueue_step(hyb_batch* b, cudaStream_t s) {
+    if (!b->q3.empty()) {
+        std::vector<hyb_grid*> gs;
+        for (int i : b->q3) gs.push_back(b->grids[i]);
+        HYB_CUDA_TRY(cudaEventRecord(b->q3fork, s));
+        HYB_CUDA_TRY(cudaStreamWaitEvent(b->q3side, b->q3fork, 0));
+        hyb_status st = quasi3d_advance_many(gs.data(), (int)gs.size(), b->q3side);
+        if (st != HYB_OK) return st;
+        HYB_CUDA_TRY(cudaEventRecord(b->q3join, b->q3side));
     }
     for (size_t o = 0; o < b->others.size(); o++) {
         hyb_grid* g = b->grids[b->others[o]];
@@ -94,12 +138,22 @@ static hyb_status enqueue_step(hyb_batch* b, cudaStream_t s) {
         if (st != HYB_OK) return st;
         HYB_CUDA_TRY(cudaEventRecord(b->ojoin[o], b->oside[o]));
     }
+    HYB_CUDA_TRY(copy_rows(b->halo_tasks, b->n_halo, s));
+    for (auto& G : b->groups) {
+        HYB_CUDA_TRY(cudaEventRecord(G.fork, s));
+        HYB_CUDA_TRY(cudaStreamWaitEvent(G.side, G.fork, 0));
+        HYB_CUDA_TRY(fused_kernel_launch(G.n1, group_args(b, G), G.grid, G.side));
+        HYB_CUDA_TRY(cudaEventRecord(G.join, G.side));
+    }
     for (auto& G : b->groups) HYB_CUDA_TRY(cudaStreamWaitEvent(s, G.join, 0));
     for (cudaEvent_t e : b->ojoin) HYB_CUDA_TRY(cudaStreamWaitEvent(s, e, 0));
+    if (!b->q3.empty()) HYB_CUDA_TRY(cudaStreamWaitEvent(s, b->q3join, 0));
     return HYB_OK;
 }
 
 static hyb_status capture(hyb_batch* b) {
+    hyb_status hs = halo_plan(b);
+    if (hs != HYB_OK) return hs;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     cudaStream_t cs = nullptr;
@@ -136,6 +190,10 @@ hyb_status hyb_batch_create(const hyb_grid_desc* descs, int n, void* stream, hyb
     }
     for (int i = 0; i < n; i++) {
         hyb_grid* g = b->grids[i];
+        if (g->d.dims == 20 && (b->q3.empty() ? quasi3d_can_batch(g, g) : quasi3d_can_batch(b->grids[b->q3[0]], g))) {
+            b->q3.push_back(i);
+            continue;
+        }
         if (g->path != 2) { b->others.push_back(i); continue; }
         auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const hyb_batch::Group& G) { return G.n1 == g->d.n1; });
         if (it == b->groups.end()) {
@@ -154,6 +212,12 @@ hyb_status hyb_batch_create(const hyb_grid_desc* descs, int n, void* stream, hyb
         hyb_status st = group_plan(b, G);
         if (st != HYB_OK) { hyb_batch_destroy(b); return st; }
     }
+    if (!b->q3.empty()) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->q3side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->q3fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->q3join, cudaEventDisableTiming);
+        if (e != cudaSuccess) { hyb_status st = cuda_fail(e, "stream/event creation"); hyb_batch_destroy(b); return st; }
+    }
     for (size_t o = 0; o < b->others.size(); o++) {
         cudaStream_t st_ = nullptr;
         cudaEvent_t f = nullptr, j = nullptr;
@@ -165,7 +229,8 @@ hyb_status hyb_batch_create(const hyb_grid_desc* descs, int n, void* stream, hyb
         b->ojoin.push_back(j);
         if (e != cudaSuccess) { hyb_status st = cuda_fail(e, "stream/event creation"); hyb_batch_destroy(b); return st; }
     }
-    b->launches_per_step = 2 * (int)b->groups.size();
+    b->launches_per_step = (int)b->groups.size() + (b->groups.empty() ? 0 : 1);
+    if (!b->q3.empty()) b->launches_per_step += 3 * (((int)b->q3.size() + 7) / 8);
     for (int i : b->others) b->launches_per_step += hyb_launches_per_step(b->grids[i]);
     *out = b;
     return HYB_OK;
@@ -293,6 +358,10 @@ hyb_status hyb_batch_destroy(hyb_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->halo_tasks) cudaFree(b->halo_tasks);
+    if (b->q3side) cudaStreamDestroy(b->q3side);
+    if (b->q3fork) cudaEventDestroy(b->q3fork);
+    if (b->q3join) cudaEventDestroy(b->q3join);
     for (auto& G : b->groups) {
         if (G.items) cudaFree(G.items);
         if (G.side) cudaStreamDestroy(G.side);

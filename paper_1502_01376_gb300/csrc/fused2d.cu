@@ -513,6 +513,19 @@ cudaError_t halo_parts(int n1, const FusedBatch& fb, int k0, int nk, cudaStream_
     return cudaGetLastError();
 }
 
+__global__ void k_copy_rows(const RowCopy* __restrict__ tasks) {
+    const RowCopy t = tasks[blockIdx.x];
+    const float4* s4 = reinterpret_cast<const float4*>(t.src);
+    float4* d4 = reinterpret_cast<float4*>(t.dst);
+    for (int i = threadIdx.x; i < t.n / 4; i += blockDim.x) d4[i] = s4[i];
+}
+
+cudaError_t copy_rows(const RowCopy* tasks, int n, cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    k_copy_rows<<<n, 256, 0, s>>>(tasks);
+    return cudaGetLastError();
+}
+
 cudaError_t fused_kernel_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s) {
     switch (n1) {
     case 512: return launch_n<512>(fb, grid, s);

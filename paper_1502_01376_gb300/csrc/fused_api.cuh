@@ -68,6 +68,10 @@ cudaError_t fused_kernel_launch(int n1, const FusedBatch& fb, int grid, cudaStre
 // copies halo parts k0 .. k0 + nk - 1 (0-4: E1 E2 E3 B1 B3 of row p0 - 1; 5, 6: E1 E3 of row p1)
 // of the work items into the halo buffer
 cudaError_t halo_parts(int n1, const FusedBatch& fb, int k0, int nk, cudaStream_t s);
+// one launch copying n rows (row i: tasks[i].n floats, a multiple of 4, 16-byte aligned) from
+// src to dst: the halo rows of every work item of a batch's fused groups at once
+struct RowCopy { const float* src; float* dst; int n; int pad; };
+cudaError_t copy_rows(const RowCopy* tasks, int n, cudaStream_t s);
 hyb_status fused_host_advance(hyb_grid* g, void* const E[3], void* const B[3], void* const J[3]);
 std::vector<int4> fused_items(int inst, int n2, int n_strips);
 FusedInst fused_inst(const hyb_grid* g);

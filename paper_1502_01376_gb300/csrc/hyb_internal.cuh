@@ -331,6 +331,10 @@ const char* fused_step_kernel(const hyb_grid* g);   // name of the kernel one st
 hyb_status quasi3d_create(hyb_grid* g);
 void quasi3d_destroy(hyb_grid* g);
 hyb_status quasi3d_advance(hyb_grid* g, int nsteps);
+// one step of several FP32 modes with nz = 2048 and equal nr, dr (quasi3d_can_batch pairwise
+// with the first) in three launches on stream st
+bool quasi3d_can_batch(const hyb_grid* a, const hyb_grid* b);
+hyb_status quasi3d_advance_many(hyb_grid* const* gs, int n, cudaStream_t st);
 
 // x1 transform as a split-BF16 DFT-GEMM on the tensor cores (dftgemm.cu)
 hyb_status dftgemm_create(hyb_grid* g);

@@ -40,6 +40,10 @@ struct QPlan {
 };
 
 struct QPtrs { void* p[9]; };
+// the arrays of up to kQModes modes advanced by one launch (modes of equal nz = 2048, nr, dr):
+// mode q's field f at p[9 q + f], its spectra at spec[q]
+constexpr int kQModes = 8;
+struct QMulti { void* p[kQModes * 9]; float2* spec[kQModes]; int nm; };
 
 constexpr int kQThreads = 256;
 
@@ -128,12 +132,12 @@ __device__ __forceinline__ float2 q2k_tw(float2 a, float2 w) {
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(256, 2) k_cfft2048(const __grid_constant__ QPtrs io, float2* __restrict__ spec, int nr, int nf,
+__global__ void __launch_bounds__(256, 2) k_cfft2048(const __grid_constant__ QMulti io, int nr, int nf,
                                                      const float2* __restrict__ tw) {
     __shared__ __align__(16) float2 bufA[kQ2kA];
     __shared__ __align__(16) float2 bufB[kQ2kB];
     const int t = threadIdx.x;
-    const int64_t total = (int64_t)nr * nf;
+    const int64_t per = (int64_t)nr * nf, total = per * io.nm;
     float2 w1[8], w2[8], w3[8], nx[8];
 #pragma unroll
     for (int k = 1; k < 8; k++) {
@@ -141,10 +145,13 @@ __global__ void __launch_bounds__(256, 2) k_cfft2048(const __grid_constant__ QPt
         w2[k] = tw[1792 + (k - 1) * 32 + (t & 31)];
         w3[k] = tw[2016 + (k - 1) * 4 + (t & 3)];
     }
+    // row j of the launch: mode q, field f, radial row r; its spectrum row is jj of mode q
     auto src_of = [&](int64_t j) -> const float2* {
-        const int f = (int)(j / nr);
-        const int64_t r = j - (int64_t)f * nr;
-        return INV ? spec + j * kQ2k : reinterpret_cast<const float2*>(io.p[f]) + r * kQ2k;
+        const int q = (int)(j / per);
+        const int64_t jj = j - q * per;
+        const int f = (int)(jj / nr);
+        const int64_t r = jj - (int64_t)f * nr;
+        return INV ? io.spec[q] + jj * kQ2k : reinterpret_cast<const float2*>(io.p[9 * q + f]) + r * kQ2k;
     };
     auto fetch = [&](int64_t j) {
         const float2* x = src_of(j);
@@ -193,9 +200,11 @@ __global__ void __launch_bounds__(256, 2) k_cfft2048(const __grid_constant__ QPt
         // S4
         float2* X;
         {
-            const int f = (int)(j / nr);
-            const int64_t r = j - (int64_t)f * nr;
-            X = INV ? reinterpret_cast<float2*>(io.p[f]) + r * kQ2k : spec + j * kQ2k;
+            const int q = (int)(j / per);
+            const int64_t jj = j - q * per;
+            const int f = (int)(jj / nr);
+            const int64_t r = jj - (int64_t)f * nr;
+            X = INV ? reinterpret_cast<float2*>(io.p[9 * q + f]) + r * kQ2k : io.spec[q] + jj * kQ2k;
         }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -263,9 +272,15 @@ __device__ __forceinline__ QB<T> qfaraday_at(const cplx<T>* __restrict__ spec, i
 // Ampere at row j.  E^{n+1} goes to the J slots 6..8 (J at row j is read by this thread only) and
 // B^{n+1/2} to slots 9..11; slots 0..5 are only read, so neighbouring threads see the old values.
 template <typename T>
-__global__ void __launch_bounds__(kQThreads) k_qleap(cplx<T>* __restrict__ spec, int nz, int nr, const QTab<T>* __restrict__ tab,
-                                                    T dt, T dr, int m) {
+struct QLeap { cplx<T>* spec[kQModes]; const QTab<T>* tab[kQModes]; T dt[kQModes]; int m[kQModes]; };
+
+template <typename T>
+__global__ void __launch_bounds__(kQThreads) k_qleap(const __grid_constant__ QLeap<T> ql, int nz, int nr, T dr) {
     using C = cplx<T>;
+    cplx<T>* __restrict__ spec = ql.spec[blockIdx.z];               // mode of this block
+    const QTab<T>* __restrict__ tab = ql.tab[blockIdx.z];
+    const T dt = ql.dt[blockIdx.z];
+    const int m = ql.m[blockIdx.z];
     const int j = blockIdx.y;                                        // radial row
     const int k = blockIdx.x * blockDim.x + threadIdx.x;             // axial mode
     if (k >= nz) return;
@@ -345,39 +360,79 @@ static hyb_status create_t(hyb_grid* g) {
     return HYB_OK;
 }
 
+// one step of the modes gs[0 .. n - 1] (n = 1, or modes that qualify for quasi3d_advance_many)
+// on stream st: z transform of E, B, j, the leapfrog, inverse of the advanced E, B
 template <typename T>
-static hyb_status advance_t(hyb_grid* g, int nsteps) {
+static hyb_status step_modes(hyb_grid* const* gs, int n, cudaStream_t st) {
     using C = cplx<T>;
+    hyb_grid* g = gs[0];
     QPlan<T>* P = reinterpret_cast<QPlan<T>*>(g->qtab);
     const hyb_grid_desc& d = g->d;
     const int nz = d.n1, nr = d.n2;
-    const int RB = fft_rows_per_launch(nz, (int64_t)nr * 6), nblk = (nr + RB - 1) / RB;
-    const size_t smem = sizeof(C) * 2 * fpad_size((size_t)RB * nz);
-    QPtrs fin{}, fout{};
-    for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; fin.p[6 + c] = g->J[c]; }
-    for (int c = 0; c < 3; c++) { fout.p[c] = g->E[c]; fout.p[3 + c] = g->B[c]; }
-    const int gf = std::min(9 * nblk, resident_grid((const void*)k_qfft<T, false>, kQThreads, smem));
-    const int gi = std::min(6 * nblk, resident_grid((const void*)k_qfft<T, true>, kQThreads, smem));
+    QLeap<T> ql{};
+    for (int q = 0; q < n; q++) {
+        QPlan<T>* Pq = reinterpret_cast<QPlan<T>*>(gs[q]->qtab);
+        ql.spec[q] = Pq->spec;
+        ql.tab[q] = Pq->tab;
+        ql.dt[q] = (T)gs[q]->d.dt;
+        ql.m[q] = gs[q]->d.azimuthal_m;
+    }
+    if (P->tw2k) {
+        QMulti fin{}, fout{};
+        for (int q = 0; q < n; q++) {
+            for (int c = 0; c < 3; c++) {
+                fin.p[9 * q + c] = gs[q]->E[c]; fin.p[9 * q + 3 + c] = gs[q]->B[c]; fin.p[9 * q + 6 + c] = gs[q]->J[c];
+                fout.p[9 * q + c] = gs[q]->E[c]; fout.p[9 * q + 3 + c] = gs[q]->B[c];
+            }
+            QPlan<T>* Pq = reinterpret_cast<QPlan<T>*>(gs[q]->qtab);
+            fin.spec[q] = reinterpret_cast<float2*>(Pq->spec);
+            fout.spec[q] = reinterpret_cast<float2*>(Pq->spec + 6 * (int64_t)nr * nz);
+        }
+        fin.nm = fout.nm = n;
+        const int res = resident_grid((const void*)k_cfft2048<false>, 256, 0);
+        k_cfft2048<false><<<(unsigned)std::min<int64_t>(res, (int64_t)n * 9 * nr), 256, 0, st>>>(fin, nr, 9, P->tw2k);
+        const dim3 mgrid((unsigned)((nz + kQThreads - 1) / kQThreads), (unsigned)nr, (unsigned)n);
+        k_qleap<T><<<mgrid, kQThreads, 0, st>>>(ql, nz, nr, (T)d.dx2);
+        const int res2 = resident_grid((const void*)k_cfft2048<true>, 256, 0);
+        k_cfft2048<true><<<(unsigned)std::min<int64_t>(res2, (int64_t)n * 6 * nr), 256, 0, st>>>(fout, nr, 6, P->tw2k);
+    } else {
+        const int RB = fft_rows_per_launch(nz, (int64_t)nr * 6), nblk = (nr + RB - 1) / RB;
+        const size_t smem = sizeof(C) * 2 * fpad_size((size_t)RB * nz);
+        QPtrs fin{}, fout{};
+        for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; fin.p[6 + c] = g->J[c]; }
+        for (int c = 0; c < 3; c++) { fout.p[c] = g->E[c]; fout.p[3 + c] = g->B[c]; }
+        const int gf = std::min(9 * nblk, resident_grid((const void*)k_qfft<T, false>, kQThreads, smem));
+        const int gi = std::min(6 * nblk, resident_grid((const void*)k_qfft<T, true>, kQThreads, smem));
+        k_qfft<T, false><<<gf, kQThreads, smem, st>>>(fin, P->spec, nz, nr, 9, P->tw, RB);
+        const dim3 mgrid((unsigned)((nz + kQThreads - 1) / kQThreads), (unsigned)nr, 1u);
+        k_qleap<T><<<mgrid, kQThreads, 0, st>>>(ql, nz, nr, (T)d.dx2);
+        k_qfft<T, true><<<gi, kQThreads, smem, st>>>(fout, P->spec + 6 * (int64_t)nr * nz, nz, nr, 6, P->tw, RB);
+    }
+    HYB_CUDA_TRY(cudaGetLastError());
+    return HYB_OK;
+}
+
+template <typename T>
+static hyb_status advance_t(hyb_grid* g, int nsteps) {
     for (int s = 0; s < nsteps; s++) {
         if (g->ev_start) HYB_CUDA_TRY(cudaEventRecord(g->ev_start, g->stream));
-        if (P->tw2k) {
-            const int res = resident_grid((const void*)k_cfft2048<false>, 256, 0);
-            k_cfft2048<false><<<(unsigned)std::min<int64_t>(res, 9 * (int64_t)nr), 256, 0, g->stream>>>(
-                fin, reinterpret_cast<float2*>(P->spec), nr, 9, P->tw2k);
-        } else {
-            k_qfft<T, false><<<gf, kQThreads, smem, g->stream>>>(fin, P->spec, nz, nr, 9, P->tw, RB);
-        }
-        const dim3 mgrid((unsigned)((nz + kQThreads - 1) / kQThreads), (unsigned)nr);   // one thread per (mode, row)
-        k_qleap<T><<<mgrid, kQThreads, 0, g->stream>>>(P->spec, nz, nr, P->tab, (T)d.dt, (T)d.dx2, d.azimuthal_m);
-        if (P->tw2k) {
-            const int res = resident_grid((const void*)k_cfft2048<true>, 256, 0);
-            k_cfft2048<true><<<(unsigned)std::min<int64_t>(res, 6 * (int64_t)nr), 256, 0, g->stream>>>(
-                fout, reinterpret_cast<float2*>(P->spec + 6 * (int64_t)nr * nz), nr, 6, P->tw2k);
-        } else {
-            k_qfft<T, true><<<gi, kQThreads, smem, g->stream>>>(fout, P->spec + 6 * (int64_t)nr * nz, nz, nr, 6, P->tw, RB);
-        }
-        HYB_CUDA_TRY(cudaGetLastError());
+        hyb_status st = step_modes<T>(&g, 1, g->stream);
+        if (st != HYB_OK) return st;
         if (g->ev_stop) HYB_CUDA_TRY(cudaEventRecord(g->ev_stop, g->stream));
+    }
+    return HYB_OK;
+}
+
+bool quasi3d_can_batch(const hyb_grid* a, const hyb_grid* b) {
+    return a->d.dims == 20 && b->d.dims == 20 && a->d.precision == 32 && b->d.precision == 32 && a->d.n1 == 2048 &&
+           b->d.n1 == 2048 && a->d.n2 == b->d.n2 && a->d.dx2 == b->d.dx2;
+}
+
+hyb_status quasi3d_advance_many(hyb_grid* const* gs, int n, cudaStream_t st) {
+    for (int i = 0; i < n; i += kQModes) {
+        const int m = std::min(kQModes, n - i);
+        hyb_status r = step_modes<float>(gs + i, m, st);
+        if (r != HYB_OK) return r;
     }
     return HYB_OK;
 }

@@ -89,6 +89,41 @@ def test_quasi3d_in_batch_with_2d_grids():
     grid.close()
 
 
+def test_quasi3d_modes_advanced_together_in_a_batch():
+    """Modes with nz = 2048 and a common radial grid run as one set of launches in a batch (their
+    arrays in one z transform, all modes in one leapfrog launch): each mode's result equals its
+    own grid's, and one mode against the oracle."""
+    need_gpu()
+    hyb = hyb_module()
+    from paper_1502_01376_gb300 import workloads as wl
+    runs = [_run_pair(hyb, m, 32, nz=2048, nr=24, seed=90 + m) for m in (0, 1, 2)]
+    w = wl.Workload("b", 2, 1024, 16, dx1=0.2, dx2=0.2, dt=0.08, precision=32, filt_kc=0.5, filt_w=0.2, seed=5)
+    E0, B0 = wl.band_limited_fields(w)
+    mk = lambda arrs: [torch.from_numpy(a.astype(np.float32)).cuda() for a in arrs]
+    b = hyb.Batch([r[4] for r in runs] + [hyb.desc_from_workload(w)])
+    assert b.launches_per_step == 3 + 2        # modes: z transform, leapfrog, inverse; the 2D grid: halo, fused
+    copies = []
+    for i, (_, grid, _, (Et, Bt, Jt), _) in enumerate(runs):
+        Eq, Bq = [t.clone() for t in Et], [t.clone() for t in Bt]
+        b.bind(i, Eq, Bq, Jt)
+        copies.append((Eq, Bq))
+    b.bind(3, mk(E0), mk(B0), [torch.zeros(w.shape, device="cuda") for _ in range(3)])
+    b.advance(3)
+    for _, grid, _, _, _ in runs:
+        grid.advance(3)
+    torch.cuda.synchronize()
+    for (Eq, Bq), (_, _, _, (Et, Bt, _), _) in zip(copies, runs):
+        for a, c in zip(Eq + Bq, Et + Bt):
+            assert torch.equal(a, c)
+    g, _, (Eo, Bo, Jo), (Et, Bt, _), _ = runs[1]
+    q.step(g, Eo, Bo, Jo, 3)
+    for a, c in zip(Et + Bt, Eo + Bo):
+        assert rel_err(a.cpu().numpy().view(np.float32).astype(np.float64), c.view(np.float64)) < TOL[32]
+    b.close()
+    for r in runs:
+        r[1].close()
+
+
 @pytest.mark.parametrize("m", [0, 1, 2])
 def test_quasi3d_batched_workload_size(m):
     """The batched benchmark's quasi-3D modes at full size (nz x nr = 2048 x 512, FP32, dz = dr = 0.2,
