@@ -23,6 +23,7 @@ CASES = [
     (2, 256, 20, 1, 64, 1, 1e-12),
     (3, 64, 6, 5, 64, 1, 1e-12),
     (2, 64, 16, 1, 32, 3, 1e-4),     # DFT-GEMM transform: the split-BF16 error bound of its own tests
+    (3, 32, 8, 6, 32, 4, 1e-5),      # DFT-GEMM with three BF16 parts
 ]
 
 
