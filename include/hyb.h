@@ -163,7 +163,11 @@ HYB_API hyb_status hyb_push(hyb_grid* g, int32_t* cell, void* off, void* u, cons
  *   hyb_push with E^n, B^n (u^{n+1/2}, x^{n+1});  hyb_deposit (j^{n+1/2});
  *   hyb_advance (E^{n+1}, B^{n+1/2});  off <- off_new.
  * hyb_pic_create borrows g (which must stay bound to the same arrays) and
- * allocates a second grid of the same description and 9 scratch fields. */
+ * allocates a second grid of the same description and 9 scratch fields.
+ * When g is k1-resident (hyb_set_resident) the step takes B^n from the
+ * resident spectra instead (B^{n-1/2} + Faraday(E^n)/2 per mode, transformed
+ * into scratch), and its advance transforms only j forward: 12 row transforms
+ * per step instead of two full advances. */
 typedef struct hyb_pic hyb_pic;   /* opaque */
 HYB_API hyb_status hyb_pic_create(hyb_grid* g, hyb_pic** out);
 

@@ -448,6 +448,39 @@ __global__ void __launch_bounds__(kRowThreads) k_faraday(cplx<T>* __restrict__ s
     }
 }
 
+// B^n = B^{n-1/2} + (1/2) Faraday(E^n) per mode, from the resident spectra into out (3 spectral
+// fields): the time-centred B a particle push gathers, without advancing the state
+template <typename T, bool D3>
+__global__ void __launch_bounds__(kRowThreads) k_faraday_half(const cplx<T>* __restrict__ spec, cplx<T>* __restrict__ out, int nk,
+                                                              int n2, int n3, int64_t rows, const cplx<T>* __restrict__ S, T a2, T a3) {
+    using C = cplx<T>;
+    const int g2 = (n2 + kModeRows - 1) / kModeRows, nch = (nk + 31) / 32;
+    const int rg = blockIdx.x / nch, ch = blockIdx.x - rg * nch;
+    const int i3 = rg / g2, i2 = (rg - i3 * g2) * kModeRows + threadIdx.y;
+    const int k = ch * 32 + threadIdx.x;
+    if (i2 >= n2 || k >= nk) return;
+    const int64_t r = (int64_t)i3 * n2 + i2;
+    const int64_t rp2 = (int64_t)i3 * n2 + (i2 + 1 == n2 ? 0 : i2 + 1);
+    const int64_t rp3 = D3 ? (int64_t)(i3 + 1 == n3 ? 0 : i3 + 1) * n2 + i2 : r;
+    const int64_t fs = rows * nk;
+    const C* E1 = spec; const C* E2 = spec + fs; const C* E3 = spec + 2 * fs;
+    const C* B1 = spec + 3 * fs; const C* B2 = spec + 4 * fs; const C* B3 = spec + 5 * fs;
+    const int64_t i = r * nk + k, ip2 = rp2 * nk + k, ip3 = rp3 * nk + k;
+    const C e1 = E1[i], e2 = E2[i], e3 = E3[i], s = S[k];
+    const T h = (T)0.5;
+    // the increments of k_faraday, halved
+    C d1 = cscale(csub(E3[ip2], e3), -a2);
+    C d2 = cmul(s, e3);
+    C d3 = csub(cscale(csub(E1[ip2], e1), a2), cmul(s, e2));
+    if (D3) {
+        d1 = cadd(d1, cscale(csub(E2[ip3], e2), a3));
+        d2 = csub(d2, cscale(csub(E1[ip3], e1), a3));
+    }
+    out[i] = cadd(B1[i], cscale(d1, h));
+    out[fs + i] = cadd(B2[i], cscale(d2, h));
+    out[2 * fs + i] = cadd(B3[i], cscale(d3, h));
+}
+
 // Ampere (Sm = c dt sigma- = -conj(S)):
 //   E1 += a2 d2-B3 - a3 d3-B2 - cj1 J1;  E2 += a3 d3-B1 - Sm B3 - cj J2;  E3 += Sm B2 - a2 d2-B1 - cj J3
 template <typename T, bool D3>
@@ -597,6 +630,46 @@ hyb_status generic_process_current(hyb_grid* g, bool corr, bool filt) {
     HYB_CUDA_TRY((launch_irfft<T, T>(spec, 0, fout, nf, n1, rows, t, g->stream)));
     return HYB_OK;
 }
+
+// k1-resident state: transform the bound E, B into their spectra (the import a resident step
+// does when its state is stale)
+template <typename T>
+hyb_status generic_resident_import(hyb_grid* g) {
+    using C = cplx<T>;
+    const ModeTables<T>& t = tables<T>(g);
+    RowPtrs fin{};
+    for (int c = 0; c < 3; c++) { fin.p[c] = g->E[c]; fin.p[3 + c] = g->B[c]; }
+    HYB_CUDA_TRY((launch_rfft<T, T>(fin, 6, reinterpret_cast<C*>(g->spec), g->d.n1, g->rows, t, g->stream)));
+    g->res_stale = false;
+    return HYB_OK;
+}
+
+// B^n = B^{n-1/2} + (1/2) Faraday(E^n) from the resident spectra, into the real arrays Bh (the
+// spectral j slots serve as scratch: the next step transforms j again)
+template <typename T>
+hyb_status generic_b_half(hyb_grid* g, void* const Bh[3]) {
+    using C = cplx<T>;
+    const ModeTables<T>& t = tables<T>(g);
+    const int nk = g->nk;
+    const int64_t rows = g->rows;
+    C* spec = reinterpret_cast<C*>(g->spec);
+    C* out = spec + 6 * rows * nk;
+    const T a2 = (T)(g->d.dt / g->d.dx2);
+    const T a3 = (T)(g->d.dims == 3 ? g->d.dt / g->d.dx3 : 0.0);
+    const dim3 mgrid((unsigned)((int64_t)g->d.n3 * ((g->d.n2 + kModeRows - 1) / kModeRows) * ((nk + 31) / 32))), mblk(32, kModeRows);
+    if (g->d.dims == 3) k_faraday_half<T, true><<<mgrid, mblk, 0, g->stream>>>(spec, out, nk, g->d.n2, g->d.n3, rows, t.S, a2, a3);
+    else k_faraday_half<T, false><<<mgrid, mblk, 0, g->stream>>>(spec, out, nk, g->d.n2, 1, rows, t.S, a2, a3);
+    HYB_CUDA_TRY(cudaGetLastError());
+    RowPtrsW fout{};
+    for (int c = 0; c < 3; c++) fout.p[c] = Bh[c];
+    HYB_CUDA_TRY((launch_irfft<T, T>(out, 0, fout, 3, g->d.n1, rows, t, g->stream)));
+    return HYB_OK;
+}
+
+template hyb_status generic_resident_import<float>(hyb_grid*);
+template hyb_status generic_resident_import<double>(hyb_grid*);
+template hyb_status generic_b_half<float>(hyb_grid*, void* const*);
+template hyb_status generic_b_half<double>(hyb_grid*, void* const*);
 
 int generic_launches_per_step(const hyb_grid* g) { return (amp_fused(g) || g->d.dims == 20) ? 3 : 4; }
 

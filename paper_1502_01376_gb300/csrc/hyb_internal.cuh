@@ -310,6 +310,10 @@ hyb_status cuda_fail(cudaError_t e, const char* what);
 // three-pass path (generic.cu)
 template <typename T> hyb_status generic_advance(hyb_grid* g, int nsteps);
 template <typename T> hyb_status generic_process_current(hyb_grid* g, bool corr, bool filt);
+// k1-resident state (three-pass path): import E, B into the spectra; B^n = B^{n-1/2} + Faraday/2
+// from the spectra into the real arrays Bh (the PIC step's gather)
+template <typename T> hyb_status generic_resident_import(hyb_grid* g);
+template <typename T> hyb_status generic_b_half(hyb_grid* g, void* const Bh[3]);
 int generic_launches_per_step(const hyb_grid* g);
 
 // batched real FFT along x1 (generic.cu); in: rows of n1 reals of Tin;

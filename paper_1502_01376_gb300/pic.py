@@ -33,9 +33,11 @@ class History:
     steps: int
 
 
-def run(w: wl.Workload = TABLE1, steps: int = 4000, every: int = 20, kmod=None, device="cuda") -> History:
+def run(w: wl.Workload = TABLE1, steps: int = 4000, every: int = 20, kmod=None, device="cuda",
+        resident: bool = False) -> History:
     """A PIC run of workload w (its dt, filter, shape order) with an optional Sec. 4 k1
-    modification kmod = (k1l, k1u, dk_max) in units of kg1; energies every `every` steps."""
+    modification kmod = (k1l, k1u, dk_max) in units of kg1; energies every `every` steps.
+    resident: keep E, B in k1 space between steps (hyb_set_resident)."""
     import time
 
     import torch
@@ -47,6 +49,8 @@ def run(w: wl.Workload = TABLE1, steps: int = 4000, every: int = 20, kmod=None, 
     B = [torch.zeros(w.shape, dtype=dt_, device=device) for _ in range(3)]
     J = [torch.zeros(w.shape, dtype=dt_, device=device) for _ in range(3)]
     g.bind(E, B, J)
+    if resident:
+        g.set_resident(True)
     cell, off, u, qm, q = wl.pic_plasma_torch(w, device)
     off_new = torch.empty_like(off)
     v3 = torch.empty_like(qm)

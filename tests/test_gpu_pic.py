@@ -2,7 +2,8 @@
 same steps: B^{n+1/2} from the oracle's advance of a copy with zero current, B^n the
 mean of B^{n-1/2} and B^{n+1/2}, the oracle's gather and Boris push with E^n, B^n,
 its charge-conserving deposit, its advance; particles and fields compared element
-by element (FP64 over three steps, FP32 over one)."""
+by element (FP64 over three steps, FP32 over one).  The same with k1-resident
+fields, where the step forms B^n from the resident spectra instead."""
 import numpy as np
 import pytest
 
@@ -30,8 +31,9 @@ def _oracle_pic(orc, g, E, B, cell, off, u, qm, q, order, dt, dx, steps):
     return E, B, cell, off, u
 
 
+@pytest.mark.parametrize("resident", [False, True])
 @pytest.mark.parametrize("prec,steps,order", [(64, 3, 2), (64, 2, 3), (64, 2, 1), (32, 1, 2)])
-def test_pic_steps_match_oracle(prec, steps, order, orc):
+def test_pic_steps_match_oracle(prec, steps, order, resident, orc):
     need_gpu()
     hyb = hyb_module()
     # FP32: a warm, mildly relativistic plasma, so that the two species' currents do not cancel
@@ -49,6 +51,8 @@ def test_pic_steps_match_oracle(prec, steps, order, orc):
     B = [torch.from_numpy(a).to("cuda", tdt) for a in B0]
     J = [torch.zeros(w.shape, dtype=tdt, device="cuda") for _ in range(3)]
     g.bind(E, B, J)
+    if resident:
+        g.set_resident(True)
     cell, off, u, qm, q = wl.pic_plasma_torch(w, "cuda")
     ins = [t.cpu().numpy() for t in (cell, off, u, qm, q)]
     pic = hyb.Pic(g)
