@@ -654,6 +654,17 @@ def measure_configs(hyb, wl, stream, flush, dev):
                                   "bytes_per_launch": alg_bytes},
                      "launches_per_step": lps, "config": config}
         torch.cuda.empty_cache()
+    # PIC step (push, deposit, advance with B time-centred) on the Table 1 box, with the fields
+    # in real space (two advances per step) and k1-resident (B^n from the spectra)
+    from paper_1502_01376_gb300 import pic
+    out["pic_table1"] = {}
+    for res in (False, True):
+        pic.run(pic.TABLE1, steps=20, every=20, resident=res)                  # warm
+        h = pic.run(pic.TABLE1, steps=400, every=400, resident=res)
+        out["pic_table1"]["resident" if res else "real_space"] = {"ms_per_step": 1e3 * h.seconds / h.steps,
+                                                                  "steps": h.steps}
+    out["pic_table1"]["config"] = {"grid": [pic.TABLE1.n1, pic.TABLE1.n2], "particles_per_cell": 2 * pic.TABLE1.ppc,
+                                   "timing": "wall clock over 400 steps on the host (one diagnostics call at the end)"}
     out["surrogate"] = measure_surrogate(hyb, sg, 3000, 20, sampler)
     out["surrogate"]["metric"] = "NCI surrogate training samples/s (MLP 6->256x4->1, BF16 operands, FP32 accumulation)"
     sampler.stop()
