@@ -56,7 +56,8 @@ static hyb_status pic_step(hyb_pic* p, int32_t* cell, T* off, T* u, const T* qm,
         if (st == HYB_OK) st = hyb_deposit(g, cell, off, off_new, v3, q, np, order);
         if (st == HYB_OK) st = hyb_advance(g, 1);                               // j forward only
         if (st != HYB_OK) return st;
-        HYB_CUDA_TRY(cudaMemcpyAsync(off, off_new, sizeof(T) * (size_t)np * g->d.dims, cudaMemcpyDeviceToDevice, g->stream));
+        if (np > 0)
+            HYB_CUDA_TRY(cudaMemcpyAsync(off, off_new, sizeof(T) * (size_t)np * g->d.dims, cudaMemcpyDeviceToDevice, g->stream));
         return HYB_OK;
     }
     hyb_grid* s = p->shadow;
@@ -86,7 +87,7 @@ static hyb_status pic_step(hyb_pic* p, int32_t* cell, T* off, T* u, const T* qm,
     st = hyb_advance(g, 1);                                      // E^{n+1}, B^{n+1/2}
     if (st != HYB_OK) return st;
     const int dims = g->d.dims;
-    HYB_CUDA_TRY(cudaMemcpyAsync(off, off_new, sizeof(T) * (size_t)np * dims, cudaMemcpyDeviceToDevice, g->stream));
+    if (np > 0) HYB_CUDA_TRY(cudaMemcpyAsync(off, off_new, sizeof(T) * (size_t)np * dims, cudaMemcpyDeviceToDevice, g->stream));
     return HYB_OK;
 }
 

@@ -1,6 +1,8 @@
 """Edge cases of the boundary: the smallest and largest row lengths, the
-fewest rows, one-row-per-strip fused grids, ragged strips, an empty particle
-set, a batch of one grid, and the sizes the ABI rejects."""
+fewest rows, one-row-per-strip fused grids, ragged strips, the DFT-GEMM's
+fewest rows and ragged tiles, k1-resident fields on the smallest grids, an
+empty particle set (deposit and PIC step), a batch of one grid, and the sizes
+the ABI rejects."""
 import numpy as np
 import pytest
 
@@ -71,6 +73,70 @@ def test_fused_fewest_rows(orc, n1, n2):
     w = wl.Workload("ef", 2, n1, n2, dx1=0.2, dx2=0.2, dt=0.1, precision=32, filt_kc=0.5, filt_w=0.2, seed=11)
     errs = _run(orc, hyb, w, path=2)
     assert max(errs) < TOL[32], errs
+
+
+@pytest.mark.parametrize("path", [3, 4])
+@pytest.mark.parametrize("n1,n2", [(16, 2), (1024, 2), (32, 129)])
+def test_dftgemm_fewest_rows_and_ragged_tiles(orc, n1, n2, path):
+    """The tensor-core DFT-GEMM with the fewest rows a grid has (one 128-row tile mostly empty), the
+    longest rows it takes (several passes over the output columns and K chunks) and a row count
+    one past a tile boundary."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("ed", 2, n1, n2, dx1=0.2, dx2=0.25, dt=0.05, precision=32, filt_kc=0.5, filt_w=0.2, seed=19)
+    errs = _run(orc, hyb, w, path=path)
+    assert max(errs) < 6e-5, errs
+
+
+@pytest.mark.parametrize("n1,n2", [(8, 2), (4096, 4)])
+def test_resident_fewest_rows(orc, n1, n2):
+    """k1-resident fields on the smallest grids: the step equals the oracle's."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("er", 2, n1, n2, dx1=0.2, dx2=0.25, dt=0.05, precision=64, filt_kc=0.5, filt_w=0.2, seed=23)
+    g = hyb.Grid(hyb.desc_from_workload(w))
+    E0, B0 = wl.band_limited_fields(w)
+    rng = np.random.default_rng(24)
+    J0 = [rng.standard_normal(w.shape) * 1e-3 for _ in range(3)]
+    T = [to_dev(a, torch.float64) for a in list(E0) + list(B0) + J0]
+    g.bind(T[0:3], T[3:6], T[6:9])
+    g.set_resident(True)
+    g.advance(0)                                 # no step: nothing imported or written
+    g.advance(3)
+    g.check()
+    Eo, Bo, Jo = [a.copy() for a in E0], [a.copy() for a in B0], [a.copy() for a in J0]
+    orc.step(orc_grid(orc, w), Eo, Bo, Jo, nsteps=3)
+    errs = [rel_err(to_np(a), b) for a, b in zip(T[:6], Eo + Bo)]
+    assert max(errs) < TOL[64], errs
+    g.close()
+
+
+def test_pic_step_without_particles(orc):
+    """A PIC step with no particles (both modes): the fields advance as hyb_advance with zero current."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("ep", 2, 64, 8, dx1=0.2, dx2=0.2, dt=0.08, precision=64, seed=29)
+    E0, B0 = wl.band_limited_fields(w)
+    for resident in (False, True):
+        g = hyb.Grid(hyb.desc_from_workload(w))
+        T = [to_dev(a, torch.float64) for a in list(E0) + list(B0)] + [torch.zeros(w.shape, dtype=torch.float64,
+                                                                                     device="cuda") for _ in range(3)]
+        g.bind(T[0:3], T[3:6], T[6:9])
+        if resident:
+            g.set_resident(True)
+        pic = hyb.Pic(g)
+        e_i = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+        e_f = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
+        e_1 = torch.zeros(0, dtype=torch.float64, device="cuda")
+        e_3 = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+        pic.step(e_i, e_f, e_3, e_1, e_1, e_f, e_1, order=2, nsteps=2)
+        g.check()
+        Eo, Bo = [a.copy() for a in E0], [a.copy() for a in B0]
+        orc.step(orc_grid(orc, w), Eo, Bo, [np.zeros(w.shape) for _ in range(3)], nsteps=2)
+        errs = [rel_err(to_np(a), b) for a, b in zip(T[:6], Eo + Bo)]
+        assert max(errs) < TOL[64], (resident, errs)
+        pic.close()
+        g.close()
 
 
 def test_deposit_without_particles_zeroes_j(orc):
