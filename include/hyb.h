@@ -360,7 +360,7 @@ HYB_API hyb_status hyb_nci_roots(const double* samples, int64_t n, int order, in
  * NCI surrogate: a small MLP (n_in -> width x depth tanh layers -> 1) trained
  * on the root solver's growth rates to pick the filter cutoff and time step
  * before a run.  Forward, backward and Adam are this library's kernels: BF16
- * weights and activations as tensor-core operands (mma m16n8k16), FP32
+ * weights and activations as tensor-core operands (tcgen05.mma), FP32
  * accumulation, FP32 master weights.  Parameters are laid out per layer as
  * W[out][in] then b[out] (FP32).  x is device FP32 [B][n_in]; targets, outputs
  * device FP32 [B].
@@ -383,8 +383,9 @@ HYB_API hyb_status hyb_mlp_gradients(hyb_mlp* m, const float* x, const float* ta
  * the loss before the step is written to loss_dev (device FP32, nullable). */
 HYB_API hyb_status hyb_mlp_train_step(hyb_mlp* m, const float* x, const float* target, int64_t B, float lr, float* loss_dev,
                                       void* stream);
-/* Kernels this network has launched so far (instrumentation: nine per layer
- * plus one per training step, fewer for a forward pass alone). */
+/* Kernels this network has launched so far (instrumentation: a training step
+ * of L = depth + 1 layers launches 3 L (one GEMM per layer forward, two per
+ * layer backward but one for the first layer, the Adam step), a forward pass L). */
 HYB_API int64_t hyb_mlp_launch_count(const hyb_mlp* m);
 HYB_API hyb_status hyb_mlp_destroy(hyb_mlp* m);
 

@@ -7,7 +7,12 @@
 // BF16 operands) into FP32 accumulators in tensor memory, 128 x 64 output tiles
 // per CTA, operands gathered into shared memory from any strides (the weight
 // gradients read the activations transposed); the network is small (widths
-// 16..256), so this is not a roofline-bound path.
+// 16..256), so this is not a roofline-bound path.  The elementwise work sits in
+// the GEMM epilogues (bias and tanh; loss, output dH and its bias gradient;
+// tanh' and the bias gradient of the layer below), the weight gradients are
+// written straight into the gradient array, and the Adam step writes the BF16
+// weight copies: a training step is 3 launches per layer (forward, dW, dX; no
+// dX below the first layer) plus the Adam step.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -17,11 +22,20 @@
 #include "hyb_internal.cuh"
 #include "tm_dev.cuh"
 
+namespace hyb {
+// per-layer offsets and sizes for the fused Adam step (passed by value)
+constexpr int kMaxLayers = 17;
+struct LayerTab {
+    int L;
+    int64_t w_off[kMaxLayers], wb_off[kMaxLayers];
+    int fo[kMaxLayers], fi[kMaxLayers], fip[kMaxLayers];
+};
+}  // namespace hyb
+
 struct hyb_mlp {
     int n_in = 0, width = 0, depth = 0;   // hidden layers of `width`
-    int kin = 0;                          // n_in padded to 16
     int L = 0;                            // layers = depth + 1
-    std::vector<int> fin, fout;           // per layer, padded to 16
+    hyb::LayerTab tab{};
     float* master = nullptr;              // FP32 weights and biases, all layers
     float* adam_m = nullptr;
     float* adam_v = nullptr;
@@ -30,11 +44,9 @@ struct hyb_mlp {
     std::vector<size_t> w_off, b_off, wb_off;
     size_t n_params = 0;
     int64_t cap = 0;                      // batch capacity of the activations
-    __nv_bfloat16* act = nullptr;         // [L+1][cap][256] BF16 layer inputs (X_l)
+    __nv_bfloat16* act = nullptr;         // [L-1][cap][256] BF16 inputs X_l of layers l >= 1
     float* pre = nullptr;                 // [L][cap][256] FP32 pre-activations
-    float* dh = nullptr;                  // [cap][256] FP32 dH of the current layer
-    __nv_bfloat16* dhb = nullptr;         // BF16 copy of dH
-    float* dx = nullptr;                  // [cap][256] FP32 dX
+    __nv_bfloat16* dhb = nullptr;         // [2][cap][256] BF16 dH (two layers' worth)
     float* loss = nullptr;                // device scalar
     int* err = nullptr;                   // device flag: bit 1 = a bounded wait in a GEMM gave up
     int64_t step = 0;
@@ -47,32 +59,60 @@ namespace hyb {
 constexpr int TM = 128, TN = 64, TKC = 64, GT = 128;
 constexpr int LBO_A = TM * 16 + 16, LBO_B = TN * 16 + 16;     // K-group strides (16-byte slots spread)
 
+// Epilogues of the GEMM (what happens to an accumulator value v of output (row, col)):
+//   EP_STORE   C[row][col] = v (split K: added atomically; C zeroed by the caller)
+//   EP_HIDDEN  h = v + b[col]; pre[row][col] = h; act[row][col] = BF16(tanh h) (0 for col >= n)
+//   EP_OUTPUT  y = v + b[0] (column 0); out[row] = y; with a target t: d = 2 (y - t) / B,
+//              dH[row] = (d, 0, ..., 0) in BF16, loss += (y - t)^2 / B, db[0] += d
+//   EP_DX      dH'[row][col] = v (1 - tanh(pre[row][col])^2) for col < n (else 0), in BF16,
+//              and db[col] += sum over rows of dH' (the bias gradient of the layer below)
+enum : int { EP_STORE = 0, EP_HIDDEN, EP_OUTPUT, EP_DX };
+struct Epi {
+    float* c = nullptr;                  // EP_STORE output, row stride scm
+    int64_t scm = 0;
+    const float* bias = nullptr;         // EP_HIDDEN, EP_OUTPUT
+    float* pre = nullptr;                // EP_HIDDEN: written; EP_DX: read (pre-activations below)
+    __nv_bfloat16* act = nullptr;        // EP_HIDDEN: activations; EP_OUTPUT, EP_DX: dH out (row stride 256)
+    float* out = nullptr;                // EP_OUTPUT: y (nullable)
+    const float* tgt = nullptr;          // EP_OUTPUT: targets (nullable: forward only)
+    float* loss = nullptr;               // EP_OUTPUT
+    float* db = nullptr;                 // EP_OUTPUT, EP_DX: bias gradient, added atomically
+    int n = 0;                           // live columns
+    float invB = 0.f;
+};
+
 // C[m][n] (FP32) = sum_k A(m,k) B(k,n), A(m,k) = a[m*sam + k*sak], B(k,n) = b[k*sbk + n*sbn]
-// (BF16), K a multiple of 16, entries with k >= kmax read as zero; accumulate into C if
-// acc != 0.  Split K: block z handles k in [z*kchunk, (z+1)*kchunk) and, when gridDim.z > 1,
-// adds its partial sums atomically (C then holds the caller's zero or previous values).
+// (BF16, or FP32 rounded to BF16 on the way in: the network input), K a multiple of 16, entries with
+// k >= kmax read as zero.  Split K (EP_STORE only): block z handles k in [z*kchunk,
+// (z+1)*kchunk) and, when gridDim.z > 1, adds its partial sums atomically.
 // Per 64-wide K chunk the 128 threads gather the A and B tiles into shared memory in the
 // canonical K-major layout without swizzle (8 x 16-byte core matrices; 16-byte slots (row, k/8),
 // filled along whichever index of the source is contiguous), one thread issues the k-steps of
 // tcgen05.mma into the 128 x 64 FP32 accumulator in TMEM and commits them to an mbarrier, and
-// after the last chunk each warp reads its 32 rows with tcgen05.ld.  Waits are bounded: on
-// time-out bit 1 of *err is set and the CTA skips the rest, drains and frees its TMEM.
+// after the last chunk each warp reads its 32 rows with tcgen05.ld into the epilogue.  Waits
+// are bounded: on time-out bit 1 of *err is set and the CTA skips the rest, drains and frees
+// its TMEM.
+__device__ __forceinline__ uint32_t bf16_bits(float x) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16(x)); }
+__device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 x) { return (uint32_t)__bfloat16_as_ushort(x); }
+
+template <typename TA>
 __device__ __forceinline__ void gemm_fill(uint32_t dst, int lbo, int rows, int rmax, int r0, int k0, int kmax,
-                                          const __nv_bfloat16* __restrict__ src, int64_t sr, int64_t sk, int tid) {
+                                          const TA* __restrict__ src, int64_t sr, int64_t sk, int tid) {
     // 16-byte slots (row r, group g of 8 k values): rows x 8 slots
+    constexpr bool kBF = sizeof(TA) == 2;
     const bool kfast = sk == 1 && (sr & 7) == 0;
     for (int i = tid; i < rows * 8; i += GT) {
         const int r = kfast ? i >> 3 : i % rows, g = kfast ? i & 7 : i / rows;
         const int row = r0 + r, k = k0 + 8 * g;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (row < rmax) {
-            if (kfast && k + 8 <= kmax) {
+            if (kBF && kfast && k + 8 <= kmax) {
                 v = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)row * sr + k));
             } else {
                 uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
                 for (int e = 0; e < 8; e++) {
-                    const uint32_t x = (k + e < kmax) ? (uint32_t)__bfloat16_as_ushort(src[(int64_t)row * sr + (int64_t)(k + e) * sk]) : 0u;
+                    const uint32_t x = (k + e < kmax) ? bf16_bits(src[(int64_t)row * sr + (int64_t)(k + e) * sk]) : 0u;
                     w[e >> 1] |= x << (16 * (e & 1));
                 }
                 v = make_uint4(w[0], w[1], w[2], w[3]);
@@ -83,9 +123,16 @@ __device__ __forceinline__ void gemm_fill(uint32_t dst, int lbo, int rows, int r
     }
 }
 
-__global__ void __launch_bounds__(GT) k_gemm_tc(int M, int N, int K, int kmax, const __nv_bfloat16* __restrict__ a, int64_t sam, int64_t sak,
-                                                const __nv_bfloat16* __restrict__ b, int64_t sbk, int64_t sbn,
-                                                float* __restrict__ c, int64_t scm, int acc, int kchunk, int* err) {
+// sum of v over the 32 lanes of a warp
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int EP, typename TA, typename TB>
+__global__ void __launch_bounds__(GT) k_gemm_tc(int M, int N, int K, int kmax, const TA* __restrict__ a, int64_t sam, int64_t sak,
+                                                const TB* __restrict__ b, int64_t sbk, int64_t sbn, Epi ep, int kchunk, int* err) {
     __shared__ __align__(128) unsigned char sbuf[8 * LBO_A + 8 * LBO_B];
     __shared__ uint64_t bar;
     __shared__ uint32_t s_taddr;
@@ -110,8 +157,8 @@ __global__ void __launch_bounds__(GT) k_gemm_tc(int M, int N, int K, int kmax, c
     uint32_t ph = 0;
     bool pend = false, abort = false, any = false;
     for (int k0 = kb; k0 < ke && !abort; k0 += TKC) {
-        gemm_fill(sA, LBO_A, TM, M, m0, k0, kmax, a, sam, sak, tid);
-        gemm_fill(sB, LBO_B, TN, N, n0, k0, kmax, b, sbn, sbk, tid);
+        gemm_fill<TA>(sA, LBO_A, TM, M, m0, k0, kmax, a, sam, sak, tid);
+        gemm_fill<TB>(sB, LBO_B, TN, N, n0, k0, kmax, b, sbn, sbk, tid);
         fence_proxy_async_smem();
         tm_fence_before();
         __syncthreads();
@@ -136,19 +183,88 @@ __global__ void __launch_bounds__(GT) k_gemm_tc(int M, int N, int K, int kmax, c
     if (any && !abort) {
         tm_fence_after();
         const int row = m0 + 32 * warp + lane;
-#pragma unroll
-        for (int u = 0; u < TN / 16; u++) {
+        const bool live = row < M;
+        const int nchunk = EP == EP_OUTPUT ? 1 : TN / 16;
+        for (int u = 0; u < nchunk; u++) {
             float t[16];
             tm_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * u), t);
             tm_wait_ld();
-            if (row < M) {
+            const int c0 = n0 + 16 * u;
+            if (EP == EP_STORE) {
+                if (live) {
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const int col = n0 + 16 * u + j;
-                    if (col < N) {
-                        float* p = c + (int64_t)row * scm + col;
-                        if (gridDim.z > 1) atomicAdd(p, t[j]);
-                        else *p = acc ? *p + t[j] : t[j];
+                    for (int j = 0; j < 16; j++) {
+                        const int col = c0 + j;
+                        if (col < N) {
+                            float* p = ep.c + (int64_t)row * ep.scm + col;
+                            if (gridDim.z > 1) atomicAdd(p, t[j]);
+                            else *p = t[j];
+                        }
+                    }
+                }
+            } else if (EP == EP_HIDDEN) {
+                if (live && c0 < N) {
+                    float h[16];
+                    uint32_t q[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const int col = c0 + j;
+                        h[j] = t[j] + (col < ep.n ? __ldg(ep.bias + col) : 0.f);
+                        q[j >> 1] |= (col < ep.n ? bf16_bits(tanhf(h[j])) : 0u) << (16 * (j & 1));
+                    }
+                    float4* pp = reinterpret_cast<float4*>(ep.pre + (int64_t)row * 256 + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; j++) pp[j] = make_float4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
+                    uint4* pa = reinterpret_cast<uint4*>(ep.act + (int64_t)row * 256 + c0);
+                    pa[0] = make_uint4(q[0], q[1], q[2], q[3]);
+                    pa[1] = make_uint4(q[4], q[5], q[6], q[7]);
+                }
+            } else if (EP == EP_OUTPUT) {
+                const float y = t[0] + __ldg(ep.bias);
+                if (live && ep.out) ep.out[row] = y;
+                if (ep.tgt) {
+                    const float dd = live ? y - ep.tgt[row] : 0.f;
+                    const float d = 2.f * dd * ep.invB;
+                    if (live) {
+                        uint4* pa = reinterpret_cast<uint4*>(ep.act + (int64_t)row * 256);
+                        pa[0] = make_uint4(bf16_bits(d), 0u, 0u, 0u);
+                        pa[1] = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                    const float l = warp_sum(dd * dd * ep.invB), s = warp_sum(d);
+                    if (lane == 0) {
+                        atomicAdd(ep.loss, l);
+                        atomicAdd(ep.db, s);
+                    }
+                }
+            } else {   // EP_DX
+                if (c0 < N) {
+                    float d[16];
+                    uint32_t q[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                    if (live) {
+                        const float4* pp = reinterpret_cast<const float4*>(ep.pre + (int64_t)row * 256 + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            const float4 h = pp[j];
+                            const float hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+                            for (int i = 0; i < 4; i++) {
+                                const float th = tanhf(hv[i]);
+                                d[4 * j + i] = (c0 + 4 * j + i < ep.n) ? t[4 * j + i] * (1.f - th * th) : 0.f;
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; j++) q[j >> 1] |= bf16_bits(d[j]) << (16 * (j & 1));
+                        uint4* pa = reinterpret_cast<uint4*>(ep.act + (int64_t)row * 256 + c0);
+                        pa[0] = make_uint4(q[0], q[1], q[2], q[3]);
+                        pa[1] = make_uint4(q[4], q[5], q[6], q[7]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; j++) d[j] = 0.f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const float s = warp_sum(d[j]);
+                        if (lane == 0 && c0 + j < ep.n) atomicAdd(ep.db + c0 + j, s);
                     }
                 }
             }
@@ -161,99 +277,28 @@ __global__ void __launch_bounds__(GT) k_gemm_tc(int M, int N, int K, int kmax, c
     if (warp == 0) tm_dealloc(tbase, TN);
 }
 
-// K is rounded up to 16 (the MMA depth); entries with k >= K read as zero
+// K is rounded up to 16 (the MMA depth); entries with k >= K read as zero.
 // Few output tiles and a long K (the weight gradients: K = batch) are split along K
-// over up to 64 blocks per tile, the partial sums added atomically into C.
-static void gemm(int M, int N, int K, const __nv_bfloat16* a, int64_t sam, int64_t sak, const __nv_bfloat16* b, int64_t sbk,
-                 int64_t sbn, float* c, int64_t scm, int acc, cudaStream_t s, int64_t& launches, int* err) {
+// over up to 64 blocks per tile, the partial sums added atomically into C (zeroed by the caller).
+template <int EP, typename TA, typename TB>
+static void gemm(int M, int N, int K, const TA* a, int64_t sam, int64_t sak, const TB* b, int64_t sbk, int64_t sbn,
+                 const Epi& ep, cudaStream_t s, int64_t& launches, int* err) {
     const int Kp = (K + 15) & ~15;
     const int tiles = ((N + TN - 1) / TN) * ((M + TM - 1) / TM);
     int split = 1;
-    while (split < 64 && tiles * split < 600 && Kp / (split * 2) >= 256) split *= 2;
+    if (EP == EP_STORE)
+        while (split < 64 && tiles * split < 600 && Kp / (split * 2) >= 256) split *= 2;
     const int kchunk = ((Kp / split + 15) & ~15);
-    if (split > 1 && !acc) cudaMemsetAsync(c, 0, sizeof(float) * (size_t)M * scm, s);   // rows of stride scm >= N
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, split);
-    k_gemm_tc<<<grid, GT, 0, s>>>(M, N, Kp, K, a, sam, sak, b, sbk, sbn, c, scm, acc, kchunk, err);
+    k_gemm_tc<EP, TA, TB><<<grid, GT, 0, s>>>(M, N, Kp, K, a, sam, sak, b, sbk, sbn, ep, kchunk, err);
     launches++;
 }
 
-// x (FP32 [B][n_in]) -> BF16 [B][kin] with zero padding
-__global__ void k_pack_input(const float* __restrict__ x, int64_t B, int n_in, int kin, __nv_bfloat16* __restrict__ out) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= B * kin) return;
-    const int64_t r = i / kin;
-    const int c = (int)(i % kin);
-    out[r * 256 + c] = __float2bfloat16(c < n_in ? x[r * n_in + c] : 0.f);
-}
-
-// pre += bias; act = tanh(pre) (BF16) for hidden layers
-__global__ void k_bias_act(float* __restrict__ pre, const float* __restrict__ bias, int64_t B, int n, int fout, int hidden,
-                           __nv_bfloat16* __restrict__ act, float* __restrict__ yout) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= B * fout) return;
-    const int64_t r = i / fout;
-    const int c = (int)(i % fout);
-    float v = pre[r * 256 + c] + (c < n ? bias[c] : 0.f);
-    pre[r * 256 + c] = v;
-    if (hidden) act[r * 256 + c] = __float2bfloat16(c < n ? tanhf(v) : 0.f);
-    else if (c == 0 && yout) yout[r] = v;
-}
-
-// output layer: dH = 2 (y - t) / B, loss += (y - t)^2 / B
-__global__ void k_loss(const float* __restrict__ pre, const float* __restrict__ tgt, int64_t B, float* __restrict__ dh,
-                       float* __restrict__ loss) {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    float l = 0.f;
-    if (r < B) {
-        const float d = pre[r * 256] - tgt[r];
-        for (int c = 0; c < 16; c++) dh[r * 256 + c] = (c == 0) ? 2.f * d / (float)B : 0.f;
-        l = d * d / (float)B;
-    }
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
-}
-
-// dH_{l-1} = dX_l * (1 - tanh(pre)^2), only the first n columns are live
-__global__ void k_act_back(const float* __restrict__ dx, const float* __restrict__ pre, int64_t B, int n, int fout,
-                           float* __restrict__ dh) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= B * fout) return;
-    const int64_t r = i / fout;
-    const int c = (int)(i % fout);
-    const float th = tanhf(pre[r * 256 + c]);
-    dh[r * 256 + c] = (c < n) ? dx[r * 256 + c] * (1.f - th * th) : 0.f;
-}
-
-__global__ void k_to_bf16(const float* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ dst) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = __float2bfloat16(src[i]);
-}
-
-// db[c] = sum_r dh[r][c]
-__global__ void k_colsum(const float* __restrict__ dh, int64_t B, int n, float* __restrict__ db) {
-    const int c = blockIdx.x;
-    float s = 0.f;
-    for (int64_t r = threadIdx.x; r < B; r += blockDim.x) s += dh[r * 256 + c];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ float part[8];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
-        if (c < n) db[c] = t;
-    }
-}
-
-// copy a [fout][fin] FP32 gradient block out of a [fout_pad][256]-strided product
-__global__ void k_copy_grad(const float* __restrict__ src, int rows, int cols, int64_t sstride, float* __restrict__ dst) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows * cols) return;
-    dst[i] = src[(int64_t)(i / cols) * sstride + i % cols];
-}
-
-__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+// The Adam step on every parameter, fused with the BF16 copy of the updated weights
+// (zero-padded [fout_pad][fin_pad] per layer; the padding was written by refresh()).
+__global__ void k_adam_bf16(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                            int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, LayerTab tab,
+                            __nv_bfloat16* __restrict__ wb) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -261,10 +306,18 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    int l = 0;
+    while (l + 1 < tab.L && i >= tab.w_off[l + 1]) l++;
+    const int64_t loc = i - tab.w_off[l];
+    if (loc < (int64_t)tab.fo[l] * tab.fi[l]) {
+        const int r = (int)(loc / tab.fi[l]), c = (int)(loc % tab.fi[l]);
+        wb[tab.wb_off[l] + (int64_t)r * tab.fip[l] + c] = __float2bfloat16(wi);
+    }
 }
 
-// BF16 copies of the weights, zero-padded to [fout_pad][fin_pad]
+// BF16 copies of the weights, zero-padded to [fout_pad][fin_pad] (at creation and on new parameters)
 __global__ void k_refresh(const float* __restrict__ w, int fout, int fin, int fout_p, int fin_p, __nv_bfloat16* __restrict__ wb) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= fout_p * fin_p) return;
@@ -289,66 +342,94 @@ static hyb_status refresh(hyb_mlp* m, cudaStream_t s) {
 
 static hyb_status ensure_cap(hyb_mlp* m, int64_t B) {
     if (B <= m->cap) return HYB_OK;
-    if (m->act) { cudaFree(m->act); cudaFree(m->pre); cudaFree(m->dh); cudaFree(m->dhb); cudaFree(m->dx); }
+    if (m->act) { cudaFree(m->act); cudaFree(m->pre); cudaFree(m->dhb); }
     m->act = nullptr;
-    // at least 256 rows: dx also holds the weight gradient of a layer (up to 256 x 256)
-    const int64_t cap = std::max<int64_t>(256, ((B + 63) / 64) * 64);
-    HYB_CUDA_TRY(cudaMalloc(&m->act, sizeof(__nv_bfloat16) * (size_t)(m->L + 1) * cap * 256));
+    const int64_t cap = ((B + 63) / 64) * 64;
+    const size_t na = (size_t)std::max(1, m->L - 1) * cap * 256;
+    HYB_CUDA_TRY(cudaMalloc(&m->act, sizeof(__nv_bfloat16) * na));
     HYB_CUDA_TRY(cudaMalloc(&m->pre, sizeof(float) * (size_t)m->L * cap * 256));
-    HYB_CUDA_TRY(cudaMalloc(&m->dh, sizeof(float) * (size_t)cap * 256));
-    HYB_CUDA_TRY(cudaMalloc(&m->dhb, sizeof(__nv_bfloat16) * (size_t)cap * 256));
-    HYB_CUDA_TRY(cudaMalloc(&m->dx, sizeof(float) * (size_t)cap * 256));
-    HYB_CUDA_TRY(cudaMemset(m->act, 0, sizeof(__nv_bfloat16) * (size_t)(m->L + 1) * cap * 256));
+    HYB_CUDA_TRY(cudaMalloc(&m->dhb, sizeof(__nv_bfloat16) * 2 * (size_t)cap * 256));
+    HYB_CUDA_TRY(cudaMemset(m->act, 0, sizeof(__nv_bfloat16) * na));
     m->cap = cap;
     return HYB_OK;
 }
 
-static hyb_status forward(hyb_mlp* m, const float* x, int64_t B, float* y, cudaStream_t s) {
+// input of layer l >= 1 (BF16 activations of layer l - 1, row stride 256)
+static __nv_bfloat16* act_in(const hyb_mlp* m, int l) { return m->act + (size_t)(l - 1) * m->cap * 256; }
+// dH of layer l (BF16, row stride 256): two buffers, so that the dX product of layer l reads
+// one while its epilogue writes dH of layer l - 1 into the other
+static __nv_bfloat16* dh_of(const hyb_mlp* m, int l) { return m->dhb + (size_t)((m->L - 1 - l) & 1) * m->cap * 256; }
+
+// forward pass: one GEMM per layer, bias and tanh in its epilogue; with a target the output
+// layer's epilogue also forms the loss, dH of the output layer and its bias gradient
+static hyb_status forward(hyb_mlp* m, const float* x, int64_t B, float* y, const float* tgt, cudaStream_t s) {
     hyb_status st = ensure_cap(m, B);
     if (st != HYB_OK) return st;
     const int64_t cap = m->cap;
-    k_pack_input<<<(unsigned)((B * m->kin + 255) / 256), 256, 0, s>>>(x, B, m->n_in, m->kin, m->act);
-    m->launches++;
     for (int l = 0; l < m->L; l++) {
         const int fi = pad16(layer_in(m, l)), fo = pad16(layer_out(m, l));
-        const __nv_bfloat16* X = m->act + (size_t)l * cap * 256;
-        float* H = m->pre + (size_t)l * cap * 256;
+        const __nv_bfloat16* W = m->wbf + m->wb_off[l];
+        Epi ep;
+        ep.bias = m->master + m->b_off[l];
+        ep.n = layer_out(m, l);
+        ep.invB = 1.f / (float)B;
+        int64_t n_launch = 0;
         // H[B][fo] = X[B][fi] W^T, W stored [fo][fi]
-        gemm((int)B, fo, fi, X, 256, 1, m->wbf + m->wb_off[l], 1, fi, H, 256, 0, s, m->launches, m->err);
-        const bool hidden = l < m->L - 1;
-        k_bias_act<<<(unsigned)((B * fo + 255) / 256), 256, 0, s>>>(H, m->master + m->b_off[l], B, layer_out(m, l), fo, hidden,
-                                                                  m->act + (size_t)(l + 1) * cap * 256, y);
-        m->launches++;
+        if (l < m->L - 1) {
+            ep.pre = m->pre + (size_t)l * cap * 256;
+            ep.act = act_in(m, l + 1);
+            if (l == 0) gemm<EP_HIDDEN>((int)B, fo, fi, x, m->n_in, 1, W, 1, fi, ep, s, n_launch, m->err);
+            else gemm<EP_HIDDEN>((int)B, fo, fi, act_in(m, l), 256, 1, W, 1, fi, ep, s, n_launch, m->err);
+        } else {
+            ep.out = y;
+            ep.tgt = tgt;
+            ep.loss = m->loss;
+            ep.db = m->grad + m->b_off[l];
+            ep.act = dh_of(m, l);
+            if (l == 0) gemm<EP_OUTPUT>((int)B, fo, fi, x, m->n_in, 1, W, 1, fi, ep, s, n_launch, m->err);
+            else gemm<EP_OUTPUT>((int)B, fo, fi, act_in(m, l), 256, 1, W, 1, fi, ep, s, n_launch, m->err);
+        }
+        m->launches += n_launch;
     }
     HYB_CUDA_TRY(cudaGetLastError());
     return HYB_OK;
 }
 
-static hyb_status backward(hyb_mlp* m, const float* tgt, int64_t B, cudaStream_t s) {
+// backward pass after forward(.., tgt): per layer the weight gradient dW = dH^T X (split K,
+// written into the gradient array) and, below the first layer, dX = dH W with tanh' and the
+// bias gradient of the layer below in the epilogue.  grad and loss are zeroed before forward.
+static hyb_status backward(hyb_mlp* m, const float* x, int64_t B, cudaStream_t s) {
     const int64_t cap = m->cap;
-    HYB_CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
-    k_loss<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(m->pre + (size_t)(m->L - 1) * cap * 256, tgt, B, m->dh, m->loss);
-    m->launches++;
     for (int l = m->L - 1; l >= 0; l--) {
         const int fi = pad16(layer_in(m, l)), fo = pad16(layer_out(m, l));
         const int ni = layer_in(m, l), no = layer_out(m, l);
-        k_to_bf16<<<(unsigned)((B * 256 + 255) / 256), 256, 0, s>>>(m->dh, B * 256, m->dhb);
-        m->launches++;
-        // dW[fo][fi] = dH^T X: M = fo, N = fi, K = B (B padded to 16 with zero rows)
-        gemm(fo, fi, (int)B, m->dhb, 1, 256, m->act + (size_t)l * cap * 256, 256, 1, m->dx, 256, 0, s, m->launches, m->err);
-        k_copy_grad<<<(no * ni + 255) / 256, 256, 0, s>>>(m->dx, no, ni, 256, m->grad + m->w_off[l]);
-        m->launches++;
-        k_colsum<<<no, 256, 0, s>>>(m->dh, B, no, m->grad + m->b_off[l]);
-        m->launches++;
+        const __nv_bfloat16* dH = dh_of(m, l);
+        Epi ep;
+        ep.c = m->grad + m->w_off[l];
+        ep.scm = ni;
+        // dW[no][ni] = dH^T X: M = no, N = ni, K = B
+        if (l == 0) gemm<EP_STORE>(no, ni, (int)B, dH, 1, 256, x, m->n_in, 1, ep, s, m->launches, m->err);
+        else gemm<EP_STORE>(no, ni, (int)B, dH, 1, 256, act_in(m, l), 256, 1, ep, s, m->launches, m->err);
         if (l > 0) {
-            // dX[B][fi] = dH[B][fo] W[fo][fi]
-            gemm((int)B, fi, fo, m->dhb, 256, 1, m->wbf + m->wb_off[l], fi, 1, m->dx, 256, 0, s, m->launches, m->err);
-            k_act_back<<<(unsigned)((B * fi + 255) / 256), 256, 0, s>>>(m->dx, m->pre + (size_t)(l - 1) * cap * 256, B, ni, fi, m->dh);
-            m->launches++;
+            // dX[B][fi] = dH[B][fo] W[fo][fi], then dH of layer l - 1
+            Epi ed;
+            ed.pre = m->pre + (size_t)(l - 1) * cap * 256;
+            ed.act = dh_of(m, l - 1);
+            ed.db = m->grad + m->b_off[l - 1];
+            ed.n = ni;
+            gemm<EP_DX>((int)B, fi, fo, dH, 256, 1, m->wbf + m->wb_off[l], fi, 1, ed, s, m->launches, m->err);
         }
     }
     HYB_CUDA_TRY(cudaGetLastError());
     return HYB_OK;
+}
+
+static hyb_status forward_backward(hyb_mlp* m, const float* x, const float* tgt, int64_t B, cudaStream_t s) {
+    HYB_CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * m->n_params, s));
+    HYB_CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
+    hyb_status st = forward(m, x, B, nullptr, tgt, s);
+    if (st == HYB_OK) st = backward(m, x, B, s);
+    return st;
 }
 
 }  // namespace hyb
@@ -364,7 +445,7 @@ hyb_status hyb_mlp_create(int n_in, int width, int depth, const float* init_para
     }
     *out = nullptr;
     hyb_mlp* m = new hyb_mlp();
-    m->n_in = n_in; m->width = width; m->depth = depth; m->kin = pad16(n_in); m->L = depth + 1;
+    m->n_in = n_in; m->width = width; m->depth = depth; m->L = depth + 1;
     size_t off = 0, woff = 0;
     for (int l = 0; l < m->L; l++) {
         const int fi = layer_in(m, l), fo = layer_out(m, l);
@@ -373,6 +454,14 @@ hyb_status hyb_mlp_create(int n_in, int width, int depth, const float* init_para
         m->wb_off.push_back(woff); woff += (size_t)pad16(fo) * pad16(fi);
     }
     m->n_params = off;
+    m->tab.L = m->L;
+    for (int l = 0; l < m->L; l++) {
+        m->tab.w_off[l] = (int64_t)m->w_off[l];
+        m->tab.wb_off[l] = (int64_t)m->wb_off[l];
+        m->tab.fo[l] = layer_out(m, l);
+        m->tab.fi[l] = layer_in(m, l);
+        m->tab.fip[l] = pad16(layer_in(m, l));
+    }
     cudaError_t e = cudaMalloc(&m->master, sizeof(float) * off);
     if (e == cudaSuccess) e = cudaMalloc(&m->adam_m, sizeof(float) * off);
     if (e == cudaSuccess) e = cudaMalloc(&m->adam_v, sizeof(float) * off);
@@ -417,15 +506,14 @@ hyb_status hyb_mlp_get_params(hyb_mlp* m, float* params_host) {
 
 hyb_status hyb_mlp_forward(hyb_mlp* m, const float* x, int64_t B, float* y, void* stream) {
     if (!m || !x || !y || B < 1) { set_error("hyb_mlp_forward: bad arguments"); return HYB_EINVAL; }
-    return forward(m, x, B, y, (cudaStream_t)stream);
+    return forward(m, x, B, y, nullptr, (cudaStream_t)stream);
 }
 
 hyb_status hyb_mlp_gradients(hyb_mlp* m, const float* x, const float* target, int64_t B, float* grad_host, float* loss_host,
                              void* stream) {
     if (!m || !x || !target || B < 1) { set_error("hyb_mlp_gradients: bad arguments"); return HYB_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
-    hyb_status st = forward(m, x, B, nullptr, s);
-    if (st == HYB_OK) st = backward(m, target, B, s);
+    hyb_status st = forward_backward(m, x, target, B, s);
     if (st != HYB_OK) return st;
     HYB_CUDA_TRY(cudaStreamSynchronize(s));
     if (grad_host) HYB_CUDA_TRY(cudaMemcpy(grad_host, m->grad, sizeof(float) * m->n_params, cudaMemcpyDeviceToHost));
@@ -437,18 +525,15 @@ hyb_status hyb_mlp_train_step(hyb_mlp* m, const float* x, const float* target, i
                               void* stream) {
     if (!m || !x || !target || B < 1) { set_error("hyb_mlp_train_step: bad arguments"); return HYB_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
-    hyb_status st = forward(m, x, B, nullptr, s);
-    if (st == HYB_OK) st = backward(m, target, B, s);
+    hyb_status st = forward_backward(m, x, target, B, s);
     if (st != HYB_OK) return st;
     m->step++;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
-    k_adam<<<(unsigned)((m->n_params + 255) / 256), 256, 0, s>>>(m->master, m->grad, m->adam_m, m->adam_v, (int64_t)m->n_params,
-                                                                lr, b1, b2, 1e-8f, c1, c2);
+    k_adam_bf16<<<(unsigned)((m->n_params + 255) / 256), 256, 0, s>>>(m->master, m->grad, m->adam_m, m->adam_v,
+                                                                     (int64_t)m->n_params, lr, b1, b2, 1e-8f, c1, c2, m->tab, m->wbf);
     m->launches++;
     HYB_CUDA_TRY(cudaGetLastError());
-    st = refresh(m, s);
-    if (st != HYB_OK) return st;
     if (loss_dev) HYB_CUDA_TRY(cudaMemcpyAsync(loss_dev, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
     return HYB_OK;
 }
@@ -460,7 +545,7 @@ hyb_status hyb_mlp_destroy(hyb_mlp* m) {
     cudaDeviceSynchronize();
     cudaFree(m->master); cudaFree(m->adam_m); cudaFree(m->adam_v); cudaFree(m->grad); cudaFree(m->wbf); cudaFree(m->loss);
     cudaFree(m->err);
-    if (m->act) { cudaFree(m->act); cudaFree(m->pre); cudaFree(m->dh); cudaFree(m->dhb); cudaFree(m->dx); }
+    if (m->act) { cudaFree(m->act); cudaFree(m->pre); cudaFree(m->dhb); }
     delete m;
     return HYB_OK;
 }

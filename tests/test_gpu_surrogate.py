@@ -56,6 +56,35 @@ def test_adam_step_matches_oracle_update():
     net.close()
 
 
+@pytest.mark.parametrize("depth", [1, 4])
+def test_training_step_launch_count_and_repeatability(depth):
+    """A training step is 3 launches per layer (forward GEMM, dW, dX; no dX below the first
+    layer) plus the Adam step, the elementwise work living in the GEMM epilogues; and two
+    identical networks stepped on the same batches stay together (the gradients are summed
+    atomically, so they agree to FP32 rounding, not bit for bit)."""
+    need_gpu()
+    hyb = hyb_module()
+    rng = np.random.default_rng(depth)
+    p = hyb.mlp_init_params(6, 64, depth, seed=depth)
+    nets = [hyb.MLP(6, 64, depth, params=p) for _ in range(2)]
+    x = torch.from_numpy(rng.uniform(-1, 1, (1000, 6)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.uniform(0, 2, 1000).astype(np.float32)).cuda()
+    n0 = nets[0].launch_count()
+    nets[0].train_step(x, t, 1e-3)
+    assert nets[0].launch_count() - n0 == 3 * (depth + 1)
+    n0 = nets[0].launch_count()
+    nets[0].forward(x)
+    assert nets[0].launch_count() - n0 == depth + 1
+    for _ in range(4):
+        nets[1].train_step(x, t, 1e-3)
+    for _ in range(3):
+        nets[0].train_step(x, t, 1e-3)
+    a, b = nets[0].get_params(), nets[1].get_params()
+    assert np.linalg.norm(a - b) < 1e-4 * np.linalg.norm(a)
+    for n in nets:
+        n.close()
+
+
 def test_surrogate_pick_against_the_solver_and_a_measured_run():
     """What the trained network gains over the method without it, for the cutoff and time step
     of the drifting-plasma run (gamma 50, square cells; 56 candidates x 48^2 modes): its own
