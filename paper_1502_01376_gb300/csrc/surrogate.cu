@@ -343,7 +343,7 @@ static void gemm(int M, int N, int K, const TA* a, int64_t sam, int64_t sak, con
                  const Epi& ep, cudaStream_t s, int64_t& launches, int* err) {
     const int Kp = (K + 15) & ~15;
     const int split = EP == EP_PART ? split_of(M, N, K) : 1;
-    const int kchunk = ((Kp / split + 15) & ~15);
+    const int kchunk = (((Kp + split - 1) / split + 15) & ~15);     // the parts cover all of K
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, split);
     k_gemm_tc<EP, TA, TB><<<grid, GT, 0, s>>>(M, N, Kp, K, a, sam, sak, b, sbk, sbn, ep, kchunk, err);
     launches++;

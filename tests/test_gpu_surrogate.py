@@ -14,8 +14,12 @@ from gpu_util import hyb_module, need_gpu, torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("width,depth,B", [(32, 2, 100), (256, 4, 128)])
+@pytest.mark.parametrize("width,depth,B", [(32, 2, 100), (256, 4, 128), (16, 1, 1), (64, 2, 1000), (48, 3, 8200)])
 def test_mlp_forward_and_gradients_match_oracle(width, depth, B):
+    """Forward pass, loss and every gradient against the oracle with the same BF16 roundings.
+    The batch sizes cover one row, a ragged single row block, many row blocks with a ragged
+    last one (bias and loss parts of 8 and 65 blocks), and a weight-gradient K of 8200 split
+    into parts of which the last has an empty K range (it must contribute zeros)."""
     need_gpu()
     hyb = hyb_module()
     rng = np.random.default_rng(width)
