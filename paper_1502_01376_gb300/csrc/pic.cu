@@ -25,9 +25,20 @@ struct hyb_pic {
     hyb_grid* shadow = nullptr;   // the same description, bound to the scratch copy and zero current
     void* scratch = nullptr;      // E'[3], B'[3], J'[3] = 0
     size_t field_bytes = 0;
+    // one step captured as a CUDA graph, replayed for the later steps of a call (and of later calls
+    // with the same arguments): its own stream, fork/join events, and the arguments it was taken with
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* key[12] = {};
+    int64_t key_np = -1;
+    int key_order = 0, key_path = 0;
+    bool key_res = false;
 };
 
 namespace hyb {
+
+constexpr int kPicGraphMinSteps = 4;   // calls of at least this many steps replay a captured step
 
 // B'[c] <- (B'[c] + B[c]) / 2 over the three components
 template <typename T>
@@ -136,18 +147,86 @@ hyb_status hyb_pic_step(hyb_pic* p, int32_t* cell, void* off, void* u, const voi
         return HYB_EINVAL;
     }
     if (!p->g->bound) { set_error("hyb_pic_step: fields not bound"); return HYB_ESTATE; }
-    for (int s = 0; s < nsteps; s++) {
-        hyb_status st = p->g->d.precision == 32
+    hyb_grid* g = p->g;
+    auto step = [&]() {
+        return g->d.precision == 32
             ? pic_step<float>(p, cell, (float*)off, (float*)u, (const float*)qm, (const float*)q, (float*)off_new, (float*)v3, np, shape_order)
             : pic_step<double>(p, cell, (double*)off, (double*)u, (const double*)qm, (const double*)q, (double*)off_new, (double*)v3, np, shape_order);
-        if (st != HYB_OK) return st;
+    };
+    // A step is some twenty small launches and copies, so a call of several steps runs the first
+    // one as plain launches (it imports k1-resident state if stale) and replays the rest as one
+    // captured graph.  Not on the single-grid fused path, whose kernels exchange halo rows under
+    // a fresh epoch each launch, nor while the caller is capturing its own graph.
+    cudaStreamCaptureStatus outer = cudaStreamCaptureStatusNone;
+    HYB_CUDA_TRY(cudaStreamIsCapturing(g->stream, &outer));
+    const bool graphs = nsteps >= kPicGraphMinSteps && !(g->path == 2 && !g->resident) && !g->ev_start &&
+                        outer == cudaStreamCaptureStatusNone;
+    if (!graphs) {
+        for (int s = 0; s < nsteps; s++) {
+            hyb_status st = step();
+            if (st != HYB_OK) return st;
+        }
+        return HYB_OK;
     }
+    hyb_status st = step();
+    if (st != HYB_OK) return st;
+    const void* key[12] = {cell, off, u, qm, q, off_new, v3, g->E[0], g->E[1], g->E[2], g->B[0], g->J[0]};
+    bool same = p->exec && np == p->key_np && shape_order == p->key_order && g->path == p->key_path && g->resident == p->key_res;
+    for (int i = 0; i < 12 && same; i++) same = key[i] == p->key[i];
+    if (!p->cs) {
+        HYB_CUDA_TRY(cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking));
+        HYB_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+        HYB_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    }
+    cudaStream_t orig = g->stream;
+    HYB_CUDA_TRY(cudaEventRecord(p->ev_fork, orig));
+    HYB_CUDA_TRY(cudaStreamWaitEvent(p->cs, p->ev_fork, 0));
+    if (!same) {
+        if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+        cudaGraph_t graph = nullptr;
+        g->stream = p->cs;
+        cudaError_t ce = cudaStreamBeginCapture(p->cs, cudaStreamCaptureModeRelaxed);
+        if (ce == cudaSuccess) {
+            st = step();
+            ce = cudaStreamEndCapture(p->cs, &graph);
+        }
+        g->stream = orig;
+        if (p->shadow) p->shadow->stream = orig;    // the captured step pointed it at the private stream
+        if (st == HYB_OK && ce == cudaSuccess) ce = cudaGraphInstantiate(&p->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (st != HYB_OK || ce != cudaSuccess) {
+            // the captured step did not run: the remaining steps as plain launches
+            if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+            cudaGetLastError();
+            for (int s = 1; s < nsteps; s++) {
+                st = step();
+                if (st != HYB_OK) return st;
+            }
+            return HYB_OK;
+        }
+        for (int i = 0; i < 12; i++) p->key[i] = key[i];
+        p->key_np = np;
+        p->key_order = shape_order;
+        p->key_path = g->path;
+        p->key_res = g->resident;
+    }
+    for (int s = 1; s < nsteps; s++) HYB_CUDA_TRY(cudaGraphLaunch(p->exec, p->cs));
+    HYB_CUDA_TRY(cudaEventRecord(p->ev_join, p->cs));
+    HYB_CUDA_TRY(cudaStreamWaitEvent(orig, p->ev_join, 0));
     return HYB_OK;
 }
 
 hyb_status hyb_pic_destroy(hyb_pic* p) {
     if (!p) return HYB_OK;
-    if (p->shadow) hyb_destroy_grid(p->shadow);
+    if (p->cs) cudaStreamSynchronize(p->cs);
+    if (p->shadow) {
+        p->shadow->stream = nullptr;      // never the private stream destroyed below (the caller's grid may be gone)
+        hyb_destroy_grid(p->shadow);
+    }
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->cs) cudaStreamDestroy(p->cs);
     if (p->scratch) cudaFree(p->scratch);
     delete p;
     return HYB_OK;

@@ -70,3 +70,44 @@ def test_pic_steps_match_oracle(prec, steps, order, resident, orc):
     assert np.max(np.abs(u.cpu().numpy().astype(np.float64) - uo)) < tol * np.max(np.abs(uo))
     pic.close()
     g.close()
+
+
+@pytest.mark.parametrize("resident", [False, True])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_pic_graph_replay_matches_plain_steps(prec, resident):
+    """A call of several steps replays one captured step as a CUDA graph; the fields and
+    particles it leaves are those of the same steps taken one call at a time (plain
+    launches), also on a second call with the same arguments (the graph reused).  The
+    deposit adds with atomics, so two runs agree to rounding, not bit for bit: cells
+    exactly, fields and particle offsets and momenta to the parity bound."""
+    need_gpu()
+    hyb = hyb_module()
+    w = wl.Workload("pic_graph", 2, 64, 32, dx1=0.2, dx2=0.2, dt=0.08, precision=prec, filt_kc=0.5, filt_w=0.2,
+                    shape_order=2, seed=5, kind="plasma", ppc=2, gamma=3.0, u_th=0.2, field_amp=0.05)
+    tdt = torch.float64 if prec == 64 else torch.float32
+    E0, B0 = wl.band_limited_fields(w)
+    runs = []
+    for chunks in ([1] * 12, [6, 6]):
+        g = hyb.Grid(hyb.desc_from_workload(w))
+        E = [torch.from_numpy(a).to("cuda", tdt) for a in E0]
+        B = [torch.from_numpy(a).to("cuda", tdt) for a in B0]
+        J = [torch.zeros(w.shape, dtype=tdt, device="cuda") for _ in range(3)]
+        g.bind(E, B, J)
+        if resident:
+            g.set_resident(True)
+        cell, off, u, qm, q = wl.pic_plasma_torch(w, "cuda")
+        off_new, v3 = torch.empty_like(off), torch.empty_like(qm)
+        pic = hyb.Pic(g)
+        for k in chunks:
+            pic.step(cell, off, u, qm, q, off_new, v3, order=2, nsteps=k)
+        g.check()
+        torch.cuda.synchronize()
+        runs.append([t.cpu().numpy().copy() for t in E + B + [cell, off, u]])
+        pic.close()
+        g.close()
+    tol = 1e-12 if prec == 64 else 1e-5
+    for a, b in zip(runs[0][:6], runs[1][:6]):
+        assert rel_err(a, b.astype(np.float64)) < tol
+    assert np.array_equal(runs[0][6], runs[1][6])
+    for a, b in zip(runs[0][7:], runs[1][7:]):
+        assert np.max(np.abs(a.astype(np.float64) - b)) < tol * max(1.0, float(np.max(np.abs(b))))
