@@ -88,7 +88,7 @@ def peaks():
 
 
 KERNEL_SOURCES = {
-    "k_fused_tm": ("fused_tm.cu", "tm_dev.cuh", "fused_dev.cuh", "fused_api.cuh", "packed_dev.cuh"),
+    "k_fused_tm": ("fused_tm.cu", "tm_sched.cuh", "tm_dev.cuh", "fused_dev.cuh", "fused_api.cuh", "packed_dev.cuh"),
 }
 KERNEL_PROFILES = {
     "k_fused_tm": "fused_tm_drift_plasma_4096x1024.md",

@@ -467,14 +467,7 @@ bool fused_supported(const hyb_grid_desc& d) {
 template <int N>
 static size_t fused_smem() { return sizeof(float2) * ((size_t)kSlots * Geo<N>::M + 3 * (size_t)Geo<N>::XB + 16 * Geo<N>::P3); }
 
-size_t fused_smem_bytes(int n1) {
-    switch (n1) {
-    case 512: return fused_smem<512>();
-    case 1024: return fused_smem<1024>();
-    case 2048: return fused_smem<2048>();
-    default: return fused_tm_smem_bytes();
-    }
-}
+size_t fused_smem_bytes(int n1) { return n1 == 4096 ? fused_tm_smem_bytes() : fused_tmt_smem_bytes(n1); }
 
 template <int N>
 static cudaError_t fused_attr(int* occ) {
@@ -485,14 +478,7 @@ static cudaError_t fused_attr(int* occ) {
 }
 
 // resident CTAs per SM of the fused kernel for n1
-cudaError_t fused_occupancy(int n1, int* occ) {
-    switch (n1) {
-    case 512: return fused_attr<512>(occ);
-    case 1024: return fused_attr<1024>(occ);
-    case 2048: return fused_attr<2048>(occ);
-    default: return fused_tm_occupancy(occ);
-    }
-}
+cudaError_t fused_occupancy(int n1, int* occ) { return n1 == 4096 ? fused_tm_occupancy(occ) : fused_tmt_occupancy(n1, occ); }
 
 template <int N>
 static cudaError_t launch_n(const FusedBatch& fb, int grid, cudaStream_t s) {
@@ -527,12 +513,7 @@ cudaError_t copy_rows(const RowCopy* tasks, int n, cudaStream_t s) {
 }
 
 cudaError_t fused_kernel_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s) {
-    switch (n1) {
-    case 512: return launch_n<512>(fb, grid, s);
-    case 1024: return launch_n<1024>(fb, grid, s);
-    case 2048: return launch_n<2048>(fb, grid, s);
-    default: return fused_tm_launch(fb, grid, s);
-    }
+    return n1 == 4096 ? fused_tm_launch(fb, grid, s) : fused_tmt_launch(n1, fb, grid, s);
 }
 
 cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
@@ -542,12 +523,7 @@ cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s,
         if (e != cudaSuccess) return e;
     }
     if (ev0) { e = cudaEventRecord(ev0, s); if (e != cudaSuccess) return e; }
-    switch (n1) {
-    case 512: e = launch_n<512>(fb, grid, s); break;
-    case 1024: e = launch_n<1024>(fb, grid, s); break;
-    case 2048: e = launch_n<2048>(fb, grid, s); break;
-    default: e = fused_tm_launch(fb, grid, s); break;
-    }
+    e = fused_kernel_launch(n1, fb, grid, s);
     if (e != cudaSuccess) return e;
     if (ev1) e = cudaEventRecord(ev1, s);
     return e;
@@ -690,9 +666,9 @@ int fused_launches_per_step(const hyb_grid* g) { return (g->fused && g->fused->f
 
 const char* fused_step_kernel(const hyb_grid* g) {
     switch (g->d.n1) {
-    case 512: return "k_fused2d<512>";
-    case 1024: return "k_fused2d<1024>";
-    case 2048: return "k_fused2d<2048>";
+    case 512: return "k_fused_tmt<32>";
+    case 1024: return "k_fused_tmt<64>";
+    case 2048: return "k_fused_tmt<128>";
     default: return "k_fused_tm";
     }
 }

@@ -60,6 +60,10 @@ size_t fused_smem_bytes(int n1);
 size_t fused_tm_smem_bytes();
 cudaError_t fused_tm_occupancy(int* occ);
 cudaError_t fused_tm_launch(const FusedBatch& fb, int grid, cudaStream_t s);
+// n1 = 512, 1024, 2048 (fused_tmt.cu): occupancy and launches count work units (teams), not CTAs
+size_t fused_tmt_smem_bytes(int n1);
+cudaError_t fused_tmt_occupancy(int n1, int* units);
+cudaError_t fused_tmt_launch(int n1, const FusedBatch& fb, int units, cudaStream_t s);
 cudaError_t wait_probe(int* dflag, int* derr, long long limit, int which, cudaStream_t s);
 cudaError_t fused_occupancy(int n1, int* occ);
 cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
