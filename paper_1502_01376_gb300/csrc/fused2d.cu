@@ -570,7 +570,7 @@ hyb_status fused_set_strips(hyb_grid* g, int n_strips) {
     HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
     P->grid = P->n_items < sms * occ ? P->n_items : sms * occ;
     if (P->flags) { cudaFree(P->flags); P->flags = nullptr; }
-    if (P->n_items <= sms * occ) {
+    if (P->n_items <= sms * occ && fused_in_kernel_halo(g->d.n1)) {
         HYB_CUDA_TRY(cudaMalloc(&P->flags, sizeof(int) * 2 * (size_t)n_strips));
         HYB_CUDA_TRY(cudaMemset(P->flags, 0, sizeof(int) * 2 * (size_t)n_strips));
         P->epoch = 0;
@@ -599,6 +599,12 @@ FusedInst fused_inst(const hyb_grid* g) {
     return a;
 }
 
+// The halo rows of a single grid's strips are exchanged inside the kernel (one co-resident
+// CTA per strip, cooperative launch) for n1 = 4096.  The n1 = 512 .. 2048 kernel runs two CTAs
+// per SM, which the runtime's cooperative launch does not admit (it counts one per SM), so those
+// grids copy their halo rows in a small launch before the step instead.
+bool fused_in_kernel_halo(int n1) { return n1 == 4096; }
+
 hyb_status fused_create(hyb_grid* g) {
     FusedPlan* P = new FusedPlan();
     g->fused = P;
@@ -616,8 +622,10 @@ hyb_status fused_create(hyb_grid* g) {
     HYB_CUDA_TRY(cudaMemcpy(P->items, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
     P->n_items = (int)it.size();
     P->grid = (int)it.size();
-    HYB_CUDA_TRY(cudaMalloc(&P->flags, sizeof(int) * 2 * (size_t)ns));
-    HYB_CUDA_TRY(cudaMemset(P->flags, 0, sizeof(int) * 2 * (size_t)ns));
+    if (fused_in_kernel_halo(g->d.n1)) {
+        HYB_CUDA_TRY(cudaMalloc(&P->flags, sizeof(int) * 2 * (size_t)ns));
+        HYB_CUDA_TRY(cudaMemset(P->flags, 0, sizeof(int) * 2 * (size_t)ns));
+    }
     P->epoch = 0;
     return HYB_OK;
 }

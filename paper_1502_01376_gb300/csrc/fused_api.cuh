@@ -66,6 +66,7 @@ cudaError_t fused_tmt_occupancy(int n1, int* units);
 cudaError_t fused_tmt_launch(int n1, const FusedBatch& fb, int units, cudaStream_t s);
 cudaError_t wait_probe(int* dflag, int* derr, long long limit, int which, cudaStream_t s);
 cudaError_t fused_occupancy(int n1, int* occ);
+bool fused_in_kernel_halo(int n1);
 cudaError_t fused_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
 // the fused kernel alone (halo buffer already filled, or flag mode)
 cudaError_t fused_kernel_launch(int n1, const FusedBatch& fb, int grid, cudaStream_t s);

@@ -30,6 +30,8 @@
 // is conflict-free except the S3 reads (T = 64) and writes (T = 64, 128), 2-way.
 #include <math.h>
 
+#include <algorithm>
+
 #include "fused_api.cuh"
 #include "fused_dev.cuh"
 #include "packed_dev.cuh"
@@ -429,10 +431,21 @@ template <int T>
 static cudaError_t tmt_occ(int* units) {
     cudaError_t e = cudaFuncSetAttribute(k_fused_tmt<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tmt<T>::SMEM);
     if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_tmt<T>, Tmt<T>::NT, Tmt<T>::SMEM);
+    e = cudaFuncSetAttribute(k_fused_tmt<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    if (occ > 2) occ = 2;                                  // TMEM holds two CTAs' lines per SM
+    // CTAs per SM from the kernel's registers (warps take them in units of 256) and shared memory,
+    // and at most two (the 512 TMEM columns of an SM); the runtime's occupancy query answers one
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_fused_tmt<T>);
+    if (e != cudaSuccess) return e;
+    int dev = 0, smem_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return e;
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int occ_r = 65536 / (regs_warp * (Tmt<T>::NT / 32));
+    const int occ_s = smem_sm / (Tmt<T>::SMEM + (int)fa.sharedSizeBytes + 1024);
+    const int occ = std::max(1, std::min(std::min(occ_r, occ_s), 2));
     *units = occ * Tmt<T>::NTM;
     return cudaSuccess;
 }
