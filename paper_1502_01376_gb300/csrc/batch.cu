@@ -1,6 +1,6 @@
 // batch.cu -- many independent grids advanced together, one CUDA-graph launch
 // per step.  Grids that run the fused FP32 kernel are grouped by n1; each
-// group is one persistent launch of k_fused2d<n1> (k_fused_tm for n1 = 4096)
+// group is one persistent launch of k_fused_tmt (k_fused_tm for n1 = 4096)
 // over a table of work items (grid, strip, first row, end row) from all its
 // grids, after one launch that copies the halo rows of every group's items.
 // Quasi-3D modes with nz = 2048 and a common radial grid are advanced together

@@ -173,101 +173,8 @@ constexpr int sE2 = 4;
 __device__ __forceinline__ int sB1(int r) { return 5 + (r & 1); }
 __device__ __forceinline__ int sB3(int r) { return 7 + (r & 1); }
 constexpr int sB2 = 9;
-constexpr int kSlots = 10;
 
 
-// job of group g in round index ri of a strip [p0, p1)
-__device__ __forceinline__ Job job_of(const FusedInst& a, int N, int strip, int p0, int p1, int ri, int g) {
-    Job j{J_IDLE, X_STORE, 0, 0, nullptr, nullptr};
-    const float* halo = a.halo + (size_t)strip * 7 * N;
-    const int h = p0 - 1;
-    if (ri < 3) {
-        if (ri == 0) {
-            j.kind = J_FWD; j.epi = X_STORE;
-            if (g == 0) { j.src = a.E[0] + (size_t)p0 * N; j.slot = sE1(p0); }
-            else if (g == 1) { j.src = a.E[2] + (size_t)p0 * N; j.slot = sE3(p0); }
-            else { j.src = halo + 1 * N; j.slot = sE2; }
-        } else if (ri == 1) {
-            if (g == 0) { j.kind = J_FWD; j.epi = X_STORE; j.src = halo + 0 * N; j.slot = sE1(h); }
-            else if (g == 1) { j.kind = J_FWD; j.epi = X_STORE; j.src = halo + 2 * N; j.slot = sE3(h); }
-        } else {
-            if (g == 0) { j.kind = J_FWD; j.epi = X_B1; j.src = halo + 3 * N; j.slot = sB1(h); j.row = h; }
-            else if (g == 2) { j.kind = J_FWD; j.epi = X_B3; j.src = halo + 4 * N; j.slot = sB3(h); j.row = h; }
-        }
-        return j;
-    }
-    const int r = (ri - 3) % 5;
-    const int p = p0 + (ri - 3) / 5;
-    if (p >= p1) return j;
-    j.row = p;
-    switch (r) {
-    case 0:
-        j.kind = J_FWD; j.epi = X_STORE;
-        if (g == 0) { j.src = (p + 1 < p1) ? a.E[0] + (size_t)(p + 1) * N : halo + 5 * N; j.slot = sE1(p + 1); }
-        else if (g == 1) { j.src = (p + 1 < p1) ? a.E[2] + (size_t)(p + 1) * N : halo + 6 * N; j.slot = sE3(p + 1); }
-        else { j.src = a.E[1] + (size_t)p * N; j.slot = sE2; }
-        break;
-    case 1:
-        j.kind = J_FWD;
-        if (g == 0) { j.epi = X_B1; j.src = a.B[0] + (size_t)p * N; j.slot = sB1(p); }
-        else if (g == 1) { j.epi = X_B2; j.src = a.B[1] + (size_t)p * N; j.slot = sB2; }
-        else { j.epi = X_B3; j.src = a.B[2] + (size_t)p * N; j.slot = sB3(p); }
-        break;
-    case 2:
-        j.kind = J_FWD;
-        if (g == 0) { j.epi = X_J1; j.src = a.J[0] + (size_t)p * N; j.slot = sE1(p); }
-        else if (g == 1) { j.epi = X_J2; j.src = a.J[1] + (size_t)p * N; j.slot = sE2; }
-        else { j.epi = X_J3; j.src = a.J[2] + (size_t)p * N; j.slot = sE3(p); }
-        break;
-    case 3:
-        j.kind = J_INV;
-        if (g == 0) { j.slot = sE1(p); j.dst = a.E[0] + (size_t)p * N; }
-        else if (g == 1) { j.slot = sE2; j.dst = a.E[1] + (size_t)p * N; }
-        else { j.slot = sE3(p); j.dst = a.E[2] + (size_t)p * N; }
-        break;
-    default:
-        j.kind = J_INV;
-        if (g == 0) { j.slot = sB1(p); j.dst = a.B[0] + (size_t)p * N; }
-        else if (g == 1) { j.slot = sB2; j.dst = a.B[1] + (size_t)p * N; }
-        else { j.slot = sB3(p); j.dst = a.B[2] + (size_t)p * N; }
-        break;
-    }
-    return j;
-}
-
-// source row of the idx-th forward transform of group g in a work item
-// (prologue: P1 all groups, P2 groups 0 and 1, P3 groups 0 and 2; then R1, R2, R3 per row).
-// Halo-buffer mode: rows outside the strip come from the buffer filled by k_halo.
-// Flag mode: the row before the strip is read from the fields directly, and the
-// row after it (E1, E3 only) from the copy published by the next strip.
-__device__ __forceinline__ const float* fwd_src(const FusedInst& a, int N, int strip, int p0, int p1, int g, int idx,
-                                                bool fm, int next) {
-    const float* halo = a.halo + (size_t)strip * 7 * N;
-    const int npro = (g == 0) ? 3 : 2;
-    if (idx < npro) {
-        if (fm) {
-            const int h = (p0 - 1 + a.n2) % a.n2;
-            if (idx == 0) return g == 0 ? a.E[0] + (size_t)p0 * N : g == 1 ? a.E[2] + (size_t)p0 * N : a.E[1] + (size_t)h * N;
-            if (idx == 1) return g == 0 ? a.E[0] + (size_t)h * N : g == 1 ? a.E[2] + (size_t)h * N : a.B[2] + (size_t)h * N;
-            return a.B[0] + (size_t)h * N;                                  // g == 0, P3
-        }
-        if (idx == 0) return g == 0 ? a.E[0] + (size_t)p0 * N : g == 1 ? a.E[2] + (size_t)p0 * N : halo + 1 * N;
-        if (idx == 1) return g == 0 ? halo + 0 * N : g == 1 ? halo + 2 * N : halo + 4 * N;
-        return halo + 3 * N;                                                // g == 0, P3
-    }
-    const int q = idx - npro;
-    const int p = p0 + q / 3, r = q % 3;
-    if (p >= p1) return nullptr;
-    if (r == 0) {
-        if (g == 2) return a.E[1] + (size_t)p * N;
-        const int c = g == 0 ? 0 : 2;
-        if (p + 1 < p1) return a.E[c] + (size_t)(p + 1) * N;
-        if (fm) return a.halo + (size_t)next * 7 * N + (g == 0 ? 0 : 1) * N;
-        return halo + (g == 0 ? 5 : 6) * N;
-    }
-    if (r == 1) return a.B[g] + (size_t)p * N;
-    return a.J[g] + (size_t)p * N;
-}
 
 
 }  // namespace hyb
