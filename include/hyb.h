@@ -177,8 +177,9 @@ HYB_API hyb_status hyb_pic_create(hyb_grid* g, hyb_pic** out);
  * of its cell), u [np][3], qm [np] (q/m), q [np] (macro-particle charge),
  * off_new [np][dims] (scratch, ends equal to off), v3 [np] (scratch; required
  * in 2D).  Errors of the push and deposit are flagged as for them (hyb_check).
- * With nsteps >= 4 (and unless g runs the single-grid fused path, or the
- * grid's stream is being captured by the caller) the first step runs as plain
+ * With nsteps >= 4 (and unless g's fused kernel exchanges halo rows inside
+ * the launch, as at n1 = 4096, or the grid's stream is being captured by the
+ * caller) the first step runs as plain
  * launches and the others replay one captured step as a CUDA graph on a
  * private stream ordered after and before the grid's stream; the graph is kept
  * for later calls with the same arrays.  Results agree with plain steps to

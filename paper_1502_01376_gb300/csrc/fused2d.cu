@@ -228,6 +228,9 @@ hyb_status fused_advance(hyb_grid* g, int nsteps) {
 
 int fused_launches_per_step(const hyb_grid* g) { return (g->fused && g->fused->flags) ? 1 : 2; }
 
+// the grid's fused kernel exchanges halo rows in the kernel under a per-launch epoch
+bool fused_epoch_launches(const hyb_grid* g) { return g->fused && g->fused->flags; }
+
 const char* fused_step_kernel(const hyb_grid* g) {
     switch (g->d.n1) {
     case 512: return "k_fused_tmt<32>";

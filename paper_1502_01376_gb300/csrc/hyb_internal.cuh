@@ -329,6 +329,7 @@ hyb_status fused_create(hyb_grid* g);
 void fused_destroy(hyb_grid* g);
 hyb_status fused_advance(hyb_grid* g, int nsteps);
 int fused_launches_per_step(const hyb_grid* g);
+bool fused_epoch_launches(const hyb_grid* g);
 const char* fused_step_kernel(const hyb_grid* g);   // name of the kernel one step launches
 
 // quasi-3D azimuthal-mode path (quasi3d.cu)

@@ -155,12 +155,12 @@ hyb_status hyb_pic_step(hyb_pic* p, int32_t* cell, void* off, void* u, const voi
     };
     // A step is some twenty small launches and copies, so a call of several steps runs the first
     // one as plain launches (it imports k1-resident state if stale) and replays the rest as one
-    // captured graph.  Not on the single-grid fused path, whose kernels exchange halo rows under
-    // a fresh epoch each launch, nor while the caller is capturing its own graph.
+    // captured graph.  Not when the grid's fused kernel exchanges halo rows under a fresh epoch
+    // each launch (n1 = 4096), nor while the caller is capturing its own graph.
     cudaStreamCaptureStatus outer = cudaStreamCaptureStatusNone;
     HYB_CUDA_TRY(cudaStreamIsCapturing(g->stream, &outer));
-    const bool graphs = nsteps >= kPicGraphMinSteps && !(g->path == 2 && !g->resident) && !g->ev_start &&
-                        outer == cudaStreamCaptureStatusNone;
+    const bool graphs = nsteps >= kPicGraphMinSteps && !(g->path == 2 && !g->resident && fused_epoch_launches(g)) &&
+                        !g->ev_start && outer == cudaStreamCaptureStatusNone;
     if (!graphs) {
         for (int s = 0; s < nsteps; s++) {
             hyb_status st = step();

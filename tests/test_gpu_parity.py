@@ -405,6 +405,17 @@ def test_fused_full_size_drift_plasma_grid(orc):
     assert max(errs) < 1e-5
 
 
+@pytest.mark.parametrize("n1,n2", [(2048, 2048), (512, 8192)])
+def test_fused_team_kernel_full_size_grid(orc, n1, n2):
+    """The same 4.19 M cells with rows of 2048 and 512 points, in the launch configuration of
+    `bench.py --n1`: the team kernel at two CTAs per SM (304 and 1216 strips of about 7 rows,
+    halo rows copied before each step), 3 steps against the oracle on every element."""
+    need_gpu()
+    hyb = hyb_module()
+    errs = _fused_case(orc, hyb, n1, n2, 3, seed=41)
+    assert max(errs) < 1e-5
+
+
 def test_three_pass_3d_full_size_sampled_rows(orc):
     """The 3D 1024 x 256 x 256 FP32 grid in the launch configuration the benchmark times, one step,
     checked on sampled x1 rows: after one step a row depends only on the rows of its 3 x 3 (x2, x3)

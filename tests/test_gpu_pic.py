@@ -72,17 +72,18 @@ def test_pic_steps_match_oracle(prec, steps, order, resident, orc):
     g.close()
 
 
-@pytest.mark.parametrize("resident", [False, True])
-@pytest.mark.parametrize("prec", [64, 32])
-def test_pic_graph_replay_matches_plain_steps(prec, resident):
+@pytest.mark.parametrize("resident,prec,n1", [(False, 64, 64), (True, 64, 64), (False, 32, 64), (True, 32, 64),
+                                               (False, 32, 512)])
+def test_pic_graph_replay_matches_plain_steps(prec, resident, n1):
     """A call of several steps replays one captured step as a CUDA graph; the fields and
     particles it leaves are those of the same steps taken one call at a time (plain
-    launches), also on a second call with the same arguments (the graph reused).  The
-    deposit adds with atomics, so two runs agree to rounding, not bit for bit: cells
+    launches), also on a second call with the same arguments (the graph reused), on the
+    three-pass path (n1 = 64) and on a fused grid whose halo rows are copied before each step
+    (n1 = 512).  The deposit adds with atomics, so two runs agree to rounding, not bit for bit: cells
     exactly, fields and particle offsets and momenta to the parity bound."""
     need_gpu()
     hyb = hyb_module()
-    w = wl.Workload("pic_graph", 2, 64, 32, dx1=0.2, dx2=0.2, dt=0.08, precision=prec, filt_kc=0.5, filt_w=0.2,
+    w = wl.Workload("pic_graph", 2, n1, 32, dx1=0.2, dx2=0.2, dt=0.08, precision=prec, filt_kc=0.5, filt_w=0.2,
                     shape_order=2, seed=5, kind="plasma", ppc=2, gamma=3.0, u_th=0.2, field_amp=0.05)
     tdt = torch.float64 if prec == 64 else torch.float32
     E0, B0 = wl.band_limited_fields(w)
