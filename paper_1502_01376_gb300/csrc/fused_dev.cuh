@@ -1,7 +1,7 @@
-// fused_dev.cuh -- device helpers shared by the fused FP32 2D kernels:
-// complex arithmetic, small DFTs with constant twiddles, streaming loads and
-// stores, release/acquire flags with bounded waits, and the round schedule
-// (which row, slot and epilogue each thread group handles in each round).
+// fused_dev.cuh -- device helpers shared by the fused FP32 2D kernels: complex
+// products, twiddles W_R^k as constants, streaming loads and stores,
+// release/acquire flags with bounded waits, the kernel arguments, and the job
+// record and slot numbers of the round schedule (tm_sched.cuh).
 #pragma once
 #include "fused_api.cuh"
 
@@ -10,13 +10,8 @@ namespace hyb {
 // ------------------------------------------------------------------ complex
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 add(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 sub(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 mul(float2 a, float2 b) { return f2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
 __device__ __forceinline__ float2 mulc(float2 a, float2 b) { return f2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y)); }  // a conj(b)
-__device__ __forceinline__ float2 scl(float2 a, float s) { return f2(a.x * s, a.y * s); }
-__device__ __forceinline__ float2 conjf2(float2 a) { return f2(a.x, -a.y); }
-// multiply by -i (forward) or +i (inverse)
-template <bool INV> __device__ __forceinline__ float2 rot(float2 a) { return INV ? f2(-a.y, a.x) : f2(a.y, -a.x); }
 
 // W_R^k as compile-time constants (forward sign); INV conjugates
 template <int R, int K, bool INV>
@@ -66,61 +61,6 @@ __device__ __forceinline__ float2 wr(int R, int k) {
     default: return f2(c1, s1);
     }
 }
-
-// ------------------------------------------------------------------ small DFTs (natural order in/out)
-template <bool INV> __device__ __forceinline__ void dft2(float2& a, float2& b) { float2 t = a; a = add(t, b); b = sub(t, b); }
-
-template <bool INV> __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
-    float2 a = add(x0, x2), b = sub(x0, x2), c = add(x1, x3), d = rot<INV>(sub(x1, x3));
-    x0 = add(a, c); x2 = sub(a, c); x1 = add(b, d); x3 = sub(b, d);
-}
-
-template <int R, bool INV> struct Dft;
-template <bool INV> struct Dft<1, INV> { template <typename A> __device__ static void run(A&) {} };
-template <bool INV> struct Dft<2, INV> { template <typename A> __device__ static void run(A& x) { dft2<INV>(x[0], x[1]); } };
-template <bool INV> struct Dft<4, INV> { template <typename A> __device__ static void run(A& x) { dft4<INV>(x[0], x[1], x[2], x[3]); } };
-template <bool INV> struct Dft<8, INV> {
-    template <typename A> __device__ static void run(A& x) {
-        // n = 2 n1 + n2, k = k1 + 4 k2
-        float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
-        float2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
-        dft4<INV>(e0, e1, e2, e3);
-        dft4<INV>(o0, o1, o2, o3);
-        o1 = mul(o1, wconst<8, 1, INV>());
-        o2 = rot<INV>(o2);
-        o3 = mul(o3, wconst<8, 3, INV>());
-        x[0] = add(e0, o0); x[4] = sub(e0, o0);
-        x[1] = add(e1, o1); x[5] = sub(e1, o1);
-        x[2] = add(e2, o2); x[6] = sub(e2, o2);
-        x[3] = add(e3, o3); x[7] = sub(e3, o3);
-    }
-};
-template <bool INV> struct Dft<16, INV> {
-    template <typename A> __device__ static void run(A& x) {
-        // n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W16^{n2 k1}, DFT4 over n2
-        float2 y[4][4];
-#pragma unroll
-        for (int n2 = 0; n2 < 4; n2++) {
-            y[n2][0] = x[n2]; y[n2][1] = x[4 + n2]; y[n2][2] = x[8 + n2]; y[n2][3] = x[12 + n2];
-            dft4<INV>(y[n2][0], y[n2][1], y[n2][2], y[n2][3]);
-        }
-        y[1][1] = mul(y[1][1], wconst<16, 1, INV>());
-        y[1][2] = mul(y[1][2], wconst<16, 2, INV>());
-        y[1][3] = mul(y[1][3], wconst<16, 3, INV>());
-        y[2][1] = mul(y[2][1], wconst<16, 2, INV>());
-        y[2][2] = rot<INV>(y[2][2]);
-        y[2][3] = mul(y[2][3], wconst<16, 6, INV>());
-        y[3][1] = mul(y[3][1], wconst<16, 3, INV>());
-        y[3][2] = mul(y[3][2], wconst<16, 6, INV>());
-        y[3][3] = mul(y[3][3], wconst<16, 9, INV>());
-#pragma unroll
-        for (int k1 = 0; k1 < 4; k1++) {
-            float2 a = y[0][k1], b = y[1][k1], c = y[2][k1], d = y[3][k1];
-            dft4<INV>(a, b, c, d);
-            x[k1] = a; x[k1 + 4] = b; x[k1 + 8] = c; x[k1 + 12] = d;
-        }
-    }
-};
 
 // ------------------------------------------------------------------ kernel args
 
