@@ -495,7 +495,7 @@ def measure_batched(hyb, wl, steps, warmup, stream, flush, sampler, dev, strips=
             n1_, h_ = (int(v) for v in kv.split(":"))
             b.set_rows_per_strip(n1_, h_)
     else:
-        b.tune(3)
+        b.tune(5)
     tune_s = time.perf_counter() - t0
     ms = time_steps(lambda: b.advance(1), steps, warmup, stream, flush, sampler)
     lps = b.launches_per_step

@@ -300,9 +300,10 @@ HYB_API hyb_status hyb_batch_create(const hyb_grid_desc* descs, int n, void* str
 /* Binds grid i of the batch to caller device arrays (as hyb_bind_fields; no rho). */
 HYB_API hyb_status hyb_batch_bind(hyb_batch* b, int i, void* const E[3], void* const B[3], void* const J[3]);
 
-/* Autotuner: for each group, times `trials` steps for each candidate strip
- * height (rows per work item) on scratch fields it allocates and frees, and
- * keeps the fastest.  Bound fields are not touched.  Synchronises. */
+/* Autotuner: for each group, times `trials` launches for each candidate strip
+ * height (rows per work item) on scratch fields it allocates and frees, each
+ * after a write larger than the L2 (a group's data arrives cold inside a
+ * step), and keeps the fastest.  Bound fields are not touched.  Synchronises. */
 HYB_API hyb_status hyb_batch_tune(hyb_batch* b, int trials);
 
 /* nsteps of every grid of the batch, one CUDA-graph launch per step, with the

@@ -258,6 +258,13 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
     cudaEvent_t e0, e1;
     HYB_CUDA_TRY(cudaEventCreate(&e0));
     HYB_CUDA_TRY(cudaEventCreate(&e1));
+    // each timed launch starts with a cold L2, as a group does inside a step (a write larger than
+    // the L2 between launches): a group small enough to stay in L2 would otherwise be tuned warm
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->grids[0]->device);
+    const size_t flush_bytes = (size_t)std::max(l2, 1 << 20) * 3 / 2;
+    void* flush = nullptr;
+    if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) { flush = nullptr; cudaGetLastError(); }
     hyb_status result = HYB_OK;
     for (auto& G : b->groups) {
         // scratch fields: timing does not depend on the values
@@ -312,13 +319,19 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
             fb.n_strips = 0;
             fb.err = b->grids[G.members[0]]->dflag;
             fused_launch(G.n1, fb, G.grid, b->stream, nullptr, nullptr);       // warm
-            cudaEventRecord(e0, b->stream);
-            for (int t = 0; t < trials; t++) fused_launch(G.n1, fb, G.grid, b->stream, nullptr, nullptr);
-            cudaEventRecord(e1, b->stream);
-            cudaError_t e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) { result = cuda_fail(e, "hyb_batch_tune"); break; }
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            cudaError_t e = cudaSuccess;
+            for (int t = 0; t < trials && e == cudaSuccess; t++) {
+                if (flush) cudaMemsetAsync(flush, t & 0xff, flush_bytes, b->stream);
+                cudaEventRecord(e0, b->stream);
+                fused_launch(G.n1, fb, G.grid, b->stream, nullptr, nullptr);
+                cudaEventRecord(e1, b->stream);
+                e = cudaEventSynchronize(e1);
+                float one = 0.f;
+                if (e == cudaSuccess) cudaEventElapsedTime(&one, e0, e1);
+                ms += one;
+            }
+            if (e != cudaSuccess) { result = cuda_fail(e, "hyb_batch_tune"); break; }
             if (ms < best) { best = ms; best_h = h; }
         }
         for (void* p : bufs) cudaFree(p);
@@ -329,6 +342,7 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (flush) cudaFree(flush);
     b->dirty = true;
     return result;
 }
