@@ -4,8 +4,8 @@
 // weights).  Architecture: n_in -> width x depth (tanh) -> 1 (linear).
 //
 // The GEMMs run on the fifth-generation tensor cores: tcgen05.mma (kind::f16,
-// BF16 operands) into FP32 accumulators in tensor memory, 128 x 64 output tiles
-// per CTA, operands loaded into the canonical K-major shared-memory layout with
+// BF16 operands) into FP32 accumulators in tensor memory, 128 x 32 output tiles
+// per CTA (narrow, so that the small products still give each SM a dozen warps), operands loaded into the canonical K-major shared-memory layout with
 // 16-byte vector loads: every operand is stored with its K index contiguous
 // (the epilogues write the activations and dH both batch-major and
 // feature-major, and the weights are kept in BF16 both ways).  The network is
@@ -67,8 +67,8 @@ struct hyb_mlp {
 
 namespace hyb {
 
-// GEMM tiles: 128 x 64 outputs per CTA (tcgen05.mma M = 128, N = 64), K in chunks of 64
-constexpr int TM = 128, TN = 64, TKC = 64, GT = 128;
+// GEMM tiles: 128 x 32 outputs per CTA (tcgen05.mma M = 128, N = 32), K in chunks of 64
+constexpr int TM = 128, TN = 32, TKC = 64, GT = 128;
 constexpr int LBO_A = TM * 16 + 16, LBO_B = TN * 16 + 16;     // K-group strides (16-byte slots spread)
 constexpr int kMaxSplit = 64;
 
