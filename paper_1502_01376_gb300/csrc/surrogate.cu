@@ -155,7 +155,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // [z*kchunk, (z+1)*kchunk).
 // Per 64-wide K chunk the 128 threads load the A and B tiles into shared memory in the
 // canonical K-major layout without swizzle (8 x 16-byte core matrices; 16-byte slots (row, k/8)),
-// one thread issues the k-steps of tcgen05.mma into the 128 x 64 FP32 accumulator in TMEM and
+// one thread issues the k-steps of tcgen05.mma into the 128 x 32 FP32 accumulator in TMEM and
 // commits them to an mbarrier, and after the last chunk each warp reads its 32 rows with
 // tcgen05.ld into the epilogue.  Waits are bounded: on time-out bit 1 of *err is set and the
 // CTA skips the rest, drains and frees its TMEM.
