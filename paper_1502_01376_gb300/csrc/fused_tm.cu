@@ -1,9 +1,9 @@
 // fused_tm.cu -- single-pass FP32 hybrid advance for n1 = 4096 with the
 // k1-space lines kept in tensor memory (TMEM) and the input rows brought in by
-// the bulk-copy engine (TMA).  Same schedule as the shared-memory kernel of
-// fused2d.cu (a CTA sweeps a strip of x2 rows; per row five rounds of three
-// real FFTs, one per thread group, with the Faraday and Ampere updates of
-// Eqs. hybrid2db1-hybrid2de3 as per-mode epilogues), re-laid for more warps:
+// the bulk-copy engine (TMA).  A CTA sweeps a strip of x2 rows; per row five
+// rounds of three real FFTs, one per thread group, with the Faraday and Ampere
+// updates of Eqs. hybrid2db1-hybrid2de3 as per-mode epilogues (the schedule of
+// tm_sched.cuh, shared with the n1 = 512 .. 2048 kernel of fused_tmt.cu):
 //
 //   * three groups of T = 256 threads (24 warps per SM); a thread holds 8
 //     complex points of a line;
