@@ -26,8 +26,9 @@
 //     three exchange buffers: A (S1 -> S2), Y (S2 -> S3, inside a warp), B (S3 -> S4);
 //     the inverse uses A and B the other way round (S4 -> S3 in A, S2 -> S1 in B),
 //     so that no transform's first write meets the last reads of the one before it.
-// The exchange paddings were chosen with a bank model of the accesses: every access
-// is conflict-free except the S3 reads (T = 64) and writes (T = 64, 128), 2-way.
+// The exchange paddings and the column permutation of the S3 -> S4 exchange were chosen
+// with a bank model of the accesses: every access is conflict-free except the S3 reads
+// (T = 64) and half of the S4 reads of the second column, 2-way.
 #include <math.h>
 
 #include <algorithm>
@@ -120,6 +121,12 @@ __global__ void __launch_bounds__(384, 2) k_fused_tmt(FusedBatch fb) {
     const int s3_u0 = lane & 3, s3_k2 = (lane >> 2) & 7, s3_w = t >> 5;
     constexpr int NK1 = (U1 > 1) ? 32 / T0 : 1;                     // k1 values per warp in S3
     constexpr float inv2M = 0.5f / (float)M;
+    // position of (u0, column c) in the S3 -> S4 exchange: for U > 1 bit 2 of c is flipped by its bits
+    // 4 and 5 (a permutation of the columns), which keeps the S3 writes free of bank conflicts
+    auto x3 = [&](int u0, int c) {
+        if constexpr (U1 > 1) c ^= (((c >> 4) ^ (c >> 5)) & 1) << 2;
+        return u0 * CR + c;
+    };
 
     // this thread's twiddles into TMEM (written by group 0 of each team)
     if (g == 0) {
@@ -268,7 +275,7 @@ __global__ void __launch_bounds__(384, 2) k_fused_tmt(FusedBatch fb) {
             }
             if constexpr (U1 == 1) {
 #pragma unroll
-                for (int k = 0; k < 8; k++) bB[s2_t0 * CR + s2_k1 + 8 * k] = v[k];
+                for (int k = 0; k < 8; k++) bB[x3(s2_t0, s2_k1 + 8 * k)] = v[k];
             } else {
 #pragma unroll
                 for (int k = 0; k < 8; k++) bY[(s2_k1 * 8 + k) * YR + s2_t0] = v[k];
@@ -286,14 +293,14 @@ __global__ void __launch_bounds__(384, 2) k_fused_tmt(FusedBatch fb) {
                     else dft2x<false>(u[0], u[1]);
 #pragma unroll
                     for (int k3 = 0; k3 < U1; k3++)
-                        bB[s3_u0 * CR + k1 + 8 * s3_k2 + 64 * k3] = (k3 == 0) ? u[0] : mul(u[k3], w3[k3]);
+                        bB[x3(s3_u0, k1 + 8 * s3_k2 + 64 * k3)] = (k3 == 0) ? u[0] : mul(u[k3], w3[k3]);
                 }
             }
             gsync();
             // ---------------- S4: columns cA, cB, 4-point DFT over u0
             float2 A4[4], B4[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) { A4[u] = bB[u * CR + cA]; B4[u] = bB[u * CR + cB]; }
+            for (int u = 0; u < 4; u++) { A4[u] = bB[x3(u, cA)]; B4[u] = bB[x3(u, cB)]; }
             dft4x<false>(A4[0], A4[1], A4[2], A4[3]);
             dft4x<false>(B4[0], B4[1], B4[2], B4[3]);
             // even/odd split into the real-input coefficients of this thread's modes
@@ -343,13 +350,13 @@ __global__ void __launch_bounds__(384, 2) k_fused_tmt(FusedBatch fb) {
                 dft4x<true>(A4[0], A4[1], A4[2], A4[3]);
                 dft4x<true>(B4[0], B4[1], B4[2], B4[3]);
 #pragma unroll
-                for (int u = 0; u < 4; u++) { bA[u * CR + cA] = A4[u]; bA[u * CR + cB] = B4[u]; }
+                for (int u = 0; u < 4; u++) { bA[x3(u, cA)] = A4[u]; bA[x3(u, cB)] = B4[u]; }
             }
             gsync();
             float2 v[8];
             if constexpr (U1 == 1) {
 #pragma unroll
-                for (int k = 0; k < 8; k++) v[k] = bA[s2_t0 * CR + s2_k1 + 8 * k];
+                for (int k = 0; k < 8; k++) v[k] = bA[x3(s2_t0, s2_k1 + 8 * k)];
             } else {
                 // ---------------- S3 inverse: twiddle, inverse U-point DFT over k3 -> u1 (into Y)
                 float2 w3[8];
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(384, 2) k_fused_tmt(FusedBatch fb) {
                     float2 u[U1];
 #pragma unroll
                     for (int k3 = 0; k3 < U1; k3++) {
-                        const float2 val = bA[s3_u0 * CR + k1 + 8 * s3_k2 + 64 * k3];
+                        const float2 val = bA[x3(s3_u0, k1 + 8 * s3_k2 + 64 * k3)];
                         u[k3] = (k3 == 0) ? val : mulc(val, w3[k3]);
                     }
                     if constexpr (U1 == 4) dft4x<true>(u[0], u[1], u[2], u[3]);
