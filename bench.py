@@ -108,6 +108,34 @@ def kernel_source_hash(kernel="k_fused_tm"):
     return h.hexdigest()[:16]
 
 
+# FP32 additions, multiplications and fused multiply-adds per cell-step of the n1 = 4096 fused
+# kernel, counted from its factorization: a 2048-point complex FFT of 8 x 8 x 8 x 4 costs about
+# 35.5 per complex point (an 8-point DFT 56 per 8 points, its seven twiddle products 28, three such
+# stages, then 4 per point for the radix-4 stage), the even/odd split of the real transform about 4
+# per real point, so a 4096-point real transform about 21.8 per point; 15 transforms per cell-step
+# and about 36 for the per-mode Faraday and Ampere updates.
+FP32_OPS_PER_CELL_STEP_N4096 = 15 * 21.8 + 36.0
+FP32_LANES_PER_SM = 128
+
+
+def fp32_view(cells, kernel_ms, sampler=None):
+    """The fused kernel's FP32 operation rate against the FP32 lanes' peak (SMs x 128 lanes x the
+    maximum SM clock seen by the clock sampler, else 2070 MHz): the kernel sits at the ridge point
+    between this peak and the HBM bandwidth, so both fractions describe it."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = 2070.0
+    if sampler is not None:
+        summ = sampler.summary() or {}
+        mhz = float(summ.get("sm_max_mhz") or mhz)
+    peak = sms * FP32_LANES_PER_SM * mhz * 1e6
+    ops = FP32_OPS_PER_CELL_STEP_N4096 * cells
+    achieved = ops / (kernel_ms / 1e3)
+    return {"ops_per_cell_step": FP32_OPS_PER_CELL_STEP_N4096, "ops_per_launch": ops, "achieved_ops_per_s": achieved,
+            "peak_ops_per_s": peak, "frac": achieved / peak,
+            "peak_from": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz"}
+
+
 def profiled_traffic(cells, kernel):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary, if it
     was taken on the current kernel source: the measured reads plus the writes, where
@@ -873,6 +901,9 @@ def main():
             "gpu_launches": launches,
             "wall_s_timed": wall,
         }
+        if kname == "k_fused_tm":
+            # the same kernel against the FP32 pipes: its arithmetic counted from the factorization
+            line["roofline"]["fp32_view"] = fp32_view(cells, kms, sampler)
         if sampler:
             line["clocks"] = sampler.summary()
         if "e2e" in extras:
