@@ -88,7 +88,8 @@ def peaks():
 
 
 KERNEL_SOURCES = {
-    "k_fused_tm": ("fused_tm.cu", "tm_sched.cuh", "tm_dev.cuh", "fused_dev.cuh", "fused_api.cuh", "packed_dev.cuh"),
+    "k_fused_tm": ("fused_tm.cu", "tm_body.cuh", "tm_sched.cuh", "tm_dev.cuh", "fused_dev.cuh", "fused_api.cuh",
+                   "packed_dev.cuh"),
 }
 KERNEL_PROFILES = {
     "k_fused_tm": "fused_tm_drift_plasma_4096x1024.md",
@@ -527,8 +528,24 @@ def measure_batched(hyb, wl, steps, warmup, stream, flush, sampler, dev, strips=
     tune_s = time.perf_counter() - t0
     ms = time_steps(lambda: b.advance(1), steps, warmup, stream, flush, sampler)
     lps = b.launches_per_step
+    single = b.single_launch
+    # the other form of the step (graph of launches vs one persistent launch), timed the same way
+    other = None
+    try:
+        b.single_launch = not single
+    except hyb.HybError:
+        pass
+    else:
+        ms_o = time_steps(lambda: b.advance(1), steps, warmup, stream, flush, sampler)
+        other = {"form": "single persistent launch" if not single else "graph of launches",
+                 "ms_per_step": ms_o, "launches_per_step": b.launches_per_step}
+        b.single_launch = single
     config = {"workload": "batched_16x2d_uneven_plus_quasi3d_m012_2048x512", "instances_2d": sizes,
               "quasi3d_modes": [0, 1, 2], "quasi3d_grid": [nz, nr],
+              "step": "single persistent launch" if single else "graph of launches",
+              "role_ctas": dict(zip(("n1=4096", "n1=512", "n1=1024", "n1=2048", "quasi3d"), b.role_ctas())),
+              "role_ms": dict(zip(("n1=4096", "n1=512", "n1=1024", "n1=2048", "quasi3d"), b.role_ms())),
+              "other_form": other,
               "strips": "set by --batch-strips" if strips else "autotuned", "autotune_s": tune_s,
               "rows_per_strip": {n1: b.rows_per_strip(n1) for n1 in (512, 1024, 2048, 4096)},
               "current": "band-limited random J (no deposit in the timed step)",

@@ -288,9 +288,21 @@ HYB_API hyb_status hyb_set_kernel_events(hyb_grid* g, void* start, void* stop);
 /* ---------------------------------------------------------------------------
  * Batches: many independent grids advanced together (the paper applies the
  * solver to many grid geometries; batching them is this library's design).
- * Grids on the fused path are grouped by n1 into one persistent launch per
- * group over a table of (grid, strip) work items; one step of all grids is
- * captured once in a CUDA graph and replayed by hyb_batch_advance.
+ * Grids on the fused path are grouped by n1 and cut into (grid, strip) work
+ * items; quasi-3D FP32 modes with nz = 2048 and a common radial grid are
+ * advanced together.  One step of all grids is captured once in a CUDA graph
+ * and replayed by hyb_batch_advance.  The step is either
+ *   - ONE persistent cooperative launch (one 768-thread CTA per SM) whose CTAs
+ *     are split into roles: one per n1 group (n1 = 512, 1024, 2048, 4096),
+ *     which copies its halo rows and sweeps its work items, and one for the
+ *     quasi-3D modes, which runs their z transforms, leapfrog and inverse
+ *     transforms with barriers of its own CTAs between them.  Available when
+ *     every grid of the batch belongs to such a role (at most 8 quasi-3D
+ *     modes); the default then.
+ *   - a graph of launches: per group one persistent launch after one copy of
+ *     all groups' halo rows, three launches per 8 quasi-3D modes, and each
+ *     other grid's own step, on forked streams.
+ * Both give the same bits.
  * ------------------------------------------------------------------------- */
 typedef struct hyb_batch hyb_batch;   /* opaque */
 
@@ -303,7 +315,13 @@ HYB_API hyb_status hyb_batch_bind(hyb_batch* b, int i, void* const E[3], void* c
 /* Autotuner: for each group, times `trials` launches for each candidate strip
  * height (rows per work item) on scratch fields it allocates and frees, each
  * after a write larger than the L2 (a group's data arrives cold inside a
- * step), and keeps the fastest.  Bound fields are not touched.  Synchronises. */
+ * step), and keeps the fastest.  Then, when the single launch is available
+ * and every grid is bound: splits its CTAs among the roles in proportion to
+ * the CTA time each role took in timed launches (up to 8 rounds, keeping the
+ * fastest split) and keeps the faster of the single launch and the graph of
+ * launches (each timed as a graph, `trials` steps after L2 flushes).  These
+ * runs advance the bound fields, which are saved first and restored after,
+ * so the fields end as they were.  Synchronises. */
 HYB_API hyb_status hyb_batch_tune(hyb_batch* b, int trials);
 
 /* nsteps of every grid of the batch, one CUDA-graph launch per step, with the
@@ -321,6 +339,23 @@ HYB_API hyb_status hyb_batch_set_rows_per_strip(hyb_batch* b, int n1, int h);
 
 /* Kernel launches in one step of the batch (the nodes of its graph). */
 HYB_API int hyb_batch_launches_per_step(const hyb_batch* b);
+
+/* Chooses the form of the step: on != 0 the single persistent launch
+ * (HYB_EINVAL if some grid has no role in it), 0 the graph of launches.
+ * Takes effect at the next hyb_batch_advance (re-capture). */
+HYB_API hyb_status hyb_batch_set_single_launch(hyb_batch* b, int on);
+
+/* 1 if a step is the single persistent launch, else 0. */
+HYB_API int hyb_batch_single_launch(const hyb_batch* b);
+
+/* CTAs of role r of the single launch (0: n1 = 4096, 1: 512, 2: 1024,
+ * 3: 2048, 4: the quasi-3D modes); 0 if the role is absent or the single
+ * launch is not available. */
+HYB_API int hyb_batch_role_ctas(const hyb_batch* b, int r);
+
+/* Duration (ms, first CTA start to last CTA end) of role r in the fastest
+ * single launch hyb_batch_tune timed; 0 before a tune or for an absent role. */
+HYB_API double hyb_batch_role_ms(const hyb_batch* b, int r);
 
 /* Frees the batch and its grids (not the caller's arrays). */
 HYB_API hyb_status hyb_batch_destroy(hyb_batch* b);

@@ -1,18 +1,22 @@
 // batch.cu -- many independent grids advanced together, one CUDA-graph launch
-// per step.  Grids that run the fused FP32 kernel are grouped by n1; each
-// group is one persistent launch of k_fused_tmt (k_fused_tm for n1 = 4096)
-// over a table of work items (grid, strip, first row, end row) from all its
-// grids, after one launch that copies the halo rows of every group's items.
-// Quasi-3D modes with nz = 2048 and a common radial grid are advanced together
-// (z transform of all their arrays, leapfrog of all modes, inverse: three
-// launches for up to eight modes).  Other grids (FP64, 3D, unsupported n1, other
-// quasi-3D modes) run their own step.
-// Groups, and each of the other grids, are forked onto side streams inside the
-// captured graph so that they overlap.  hyb_batch_tune times candidate strip heights per group on scratch
-// fields and keeps the fastest (the autotuner).
+// per step.  Grids that run the fused FP32 kernel are grouped by n1 and cut into
+// work items (grid, strip, first row, end row); quasi-3D modes with nz = 2048 and
+// a common radial grid are advanced together.  A step is either
+//   * one persistent launch (batch_step.cu) whose CTAs are split into one role per
+//     n1 group and one for the quasi-3D modes, when every grid belongs to one of
+//     them; or
+//   * a graph of launches: one copy of the halo rows of every group's items, one
+//     persistent launch of k_fused_tmt (k_fused_tm for n1 = 4096) per group, three
+//     launches for up to eight quasi-3D modes, and the own step of every other grid
+//     (FP64, 3D, unsupported n1, other quasi-3D modes), forked onto side streams so
+//     that they overlap.
+// hyb_batch_tune (the autotuner) times candidate strip heights per group on scratch
+// fields, then the split of the single launch's CTAs among its roles, and keeps the
+// faster of the two forms of the step.
 #include <algorithm>
 #include <vector>
 
+#include "batch_step.cuh"
 #include "fused_api.cuh"
 
 struct hyb_batch {
@@ -21,11 +25,14 @@ struct hyb_batch {
     struct Group {
         int n1 = 0;
         std::vector<int> members;          // indices into grids
-        int rows_per_strip = 8;            // tuned
+        int rows_per_strip = 8;            // tuned (graph of launches)
+        int rows_single = 0;               // tuned for the single launch (0: rows_per_strip)
+        int planned = 0;                   // the height the current work items were cut with
         int4* items = nullptr;             // device work items
         int n_items = 0;
         int grid = 0;
         std::vector<int4> h_items;         // host copy of the work items
+        int halo0 = 0, n_halo = 0;         // its halo rows in the task table
         cudaStream_t side = nullptr;
         cudaEvent_t fork = nullptr, join = nullptr;
     };
@@ -42,17 +49,32 @@ struct hyb_batch {
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;
     int launches_per_step = 0;
+    // the step as one persistent launch (batch_step.cu)
+    bool single_ok = false;                // every grid belongs to a role of the single launch
+    bool single = false;                   // steps use it
+    int step_ctas = 0;                     // CTAs of the launch
+    int role_ctas[hyb::kRoles] = {};       // CTAs of each role (0: no such role)
+    unsigned* d_sync = nullptr;            // role barriers
+    unsigned long long* d_stamp = nullptr; // per-role start and end times (autotuner)
+    double role_ms[hyb::kRoles] = {};      // each role's duration in the tuner's best single launch
 };
 
 namespace hyb {
 
-static hyb_status group_plan(hyb_batch* b, hyb_batch::Group& G) {
+// strips of a grid of n2 rows for strip height h (at least two rows a strip)
+static int strips_of(int n2, int h) { return std::max(1, std::min((n2 + h - 1) / h, n2 / 2)); }
+
+// the strip height of the group in the current form of the step
+static int form_height(const hyb_batch* b, const hyb_batch::Group& G) {
+    return b->single && G.rows_single > 0 ? G.rows_single : G.rows_per_strip;
+}
+
+// cuts the group's grids into work items of strip height h
+static hyb_status group_plan(hyb_batch* b, hyb_batch::Group& G, int h) {
     std::vector<int4> items;
     for (size_t k = 0; k < G.members.size(); k++) {
         hyb_grid* g = b->grids[G.members[k]];
-        int ns = (g->d.n2 + G.rows_per_strip - 1) / G.rows_per_strip;
-        if (ns > g->d.n2 / 2) ns = g->d.n2 / 2;
-        if (ns < 1) ns = 1;
+        const int ns = strips_of(g->d.n2, h);
         hyb_status st = fused_set_strips(g, ns);
         if (st != HYB_OK) return st;
         std::vector<int4> it = fused_items((int)k, g->d.n2, ns);
@@ -65,6 +87,7 @@ static hyb_status group_plan(hyb_batch* b, hyb_batch::Group& G) {
     HYB_CUDA_TRY(cudaMemcpy(G.items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
     G.n_items = (int)items.size();
     G.h_items = items;
+    G.planned = h;
     int occ = 0, sms = 0;
     HYB_CUDA_TRY(fused_occupancy(G.n1, &occ));
     HYB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->grids[0]->device));
@@ -90,6 +113,7 @@ static FusedBatch group_args(hyb_batch* b, const hyb_batch::Group& G) {
 static hyb_status halo_plan(hyb_batch* b) {
     std::vector<RowCopy> tasks;
     for (auto& G : b->groups) {
+        G.halo0 = (int)tasks.size();
         for (const int4& it : G.h_items) {
             const hyb_grid* g = b->grids[G.members[it.x]];
             const FusedInst a = fused_inst(g);
@@ -100,6 +124,7 @@ static hyb_status halo_plan(hyb_batch* b) {
             for (int k = 0; k < 7; k++)
                 tasks.push_back(RowCopy{src[k], const_cast<float*>(a.halo) + ((size_t)it.y * 7 + k) * n1, n1, 0});
         }
+        G.n_halo = (int)tasks.size() - G.halo0;
     }
     if ((int)tasks.size() > b->halo_cap) {
         if (b->halo_tasks) cudaFree(b->halo_tasks);
@@ -114,9 +139,88 @@ static hyb_status halo_plan(hyb_batch* b) {
     return HYB_OK;
 }
 
-// enqueue one step: the others forked onto side streams, the halo copy of all groups, then
-// every group (forked onto side streams)
+// the arguments of the single launch: roles in the order of kRoleTM .. kRoleQ3, each on the next
+// role_ctas[r] CTAs
+static StepArgs step_args(hyb_batch* b, unsigned long long* stamp) {
+    StepArgs a{};
+    int cta = 0;
+    for (auto& G : b->groups) {
+        const int r = role_of_n1(G.n1);
+        a.r2[r].fb = group_args(b, G);
+        a.r2[r].halo = b->halo_tasks + G.halo0;
+        a.r2[r].n_halo = G.n_halo;
+    }
+    for (int r = 0; r < 4; r++) {
+        a.r2[r].cta0 = cta;
+        a.r2[r].ncta = b->role_ctas[r];
+        cta += b->role_ctas[r];
+    }
+    if (!b->q3.empty()) {
+        std::vector<hyb_grid*> gs;
+        for (int i : b->q3) gs.push_back(b->grids[i]);
+        quasi3d_step_args(gs.data(), (int)gs.size(), &a.q3);
+        a.q3_err = gs[0]->dflag;
+    }
+    a.q3_cta0 = cta;
+    a.q3_ncta = b->role_ctas[kRoleQ3];
+    a.sync = b->d_sync;
+    a.stamp = stamp;
+    return a;
+}
+
+// CTAs per role in proportion to the work estimates w[r] (at least one CTA for a role with work)
+static void split_ctas(hyb_batch* b, const double* w) {
+    double tot = 0.0;
+    for (int r = 0; r < kRoles; r++) if (w[r] > 0.0) tot += w[r];
+    int used = 0, big = -1;
+    for (int r = 0; r < kRoles; r++) {
+        b->role_ctas[r] = 0;
+        if (w[r] <= 0.0) continue;
+        b->role_ctas[r] = std::max(1, (int)std::lround(b->step_ctas * w[r] / tot));
+        used += b->role_ctas[r];
+        if (big < 0 || b->role_ctas[r] > b->role_ctas[big]) big = r;
+    }
+    // the rounding error goes to the largest role; if the minimum of one CTA per role overshot,
+    // take the excess from the largest roles
+    if (big >= 0) b->role_ctas[big] += b->step_ctas - used;
+    while (big >= 0 && b->role_ctas[big] < 1) {
+        int donor = -1;
+        for (int r = 0; r < kRoles; r++)
+            if (r != big && b->role_ctas[r] > 1 && (donor < 0 || b->role_ctas[r] > b->role_ctas[donor])) donor = r;
+        if (donor < 0) break;
+        b->role_ctas[donor]--;
+        b->role_ctas[big]++;
+    }
+}
+
+// a first split from the bytes each role moves and the rates its kernels reach alone on the
+// whole GPU (TB/s): 60 B per 2D cell, 360 B per quasi-3D point over the three stages
+static void default_split(hyb_batch* b) {
+    double w[kRoles] = {0, 0, 0, 0, 0};
+    static const double rate[4] = {2.6, 1.9, 1.5, 2.1};
+    for (auto& G : b->groups) {
+        int64_t cells = 0;
+        for (int m : G.members) cells += b->grids[m]->cells;
+        w[role_of_n1(G.n1)] += 60.0 * (double)cells / rate[role_of_n1(G.n1)];
+    }
+    for (int i : b->q3) w[kRoleQ3] += 360.0 * (double)b->grids[i]->cells / 5.6;
+    split_ctas(b, w);
+}
+
+static void count_launches(hyb_batch* b) {
+    if (b->single) { b->launches_per_step = 1; return; }
+    b->launches_per_step = (int)b->groups.size() + (b->groups.empty() ? 0 : 1);
+    if (!b->q3.empty()) b->launches_per_step += 3 * (((int)b->q3.size() + 7) / 8);
+    for (int i : b->others) b->launches_per_step += hyb_launches_per_step(b->grids[i]);
+}
+
+// enqueue one step.  Single launch: the one persistent launch.  Otherwise the others forked onto
+// side streams, the halo copy of all groups, then every group (forked onto side streams)
 static hyb_status enqueue_step(hyb_batch* b, cudaStream_t s) {
+    if (b->single) {
+        HYB_CUDA_TRY(batch_step_launch(step_args(b, nullptr), b->step_ctas, s));
+        return HYB_OK;
+    }
     if (!b->q3.empty()) {
         std::vector<hyb_grid*> gs;
         for (int i : b->q3) gs.push_back(b->grids[i]);
@@ -151,11 +255,22 @@ static hyb_status enqueue_step(hyb_batch* b, cudaStream_t s) {
     return HYB_OK;
 }
 
+// work items cut for the current form of the step, and their halo rows
+static hyb_status plan(hyb_batch* b) {
+    for (auto& G : b->groups)
+        if (G.planned != form_height(b, G)) {
+            hyb_status st = group_plan(b, G, form_height(b, G));
+            if (st != HYB_OK) return st;
+        }
+    return halo_plan(b);
+}
+
 static hyb_status capture(hyb_batch* b) {
-    hyb_status hs = halo_plan(b);
+    hyb_status hs = plan(b);
     if (hs != HYB_OK) return hs;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    if (b->single) HYB_CUDA_TRY(cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned) * 2 * kRoles, b->stream));
     cudaStream_t cs = nullptr;
     HYB_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     HYB_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -169,6 +284,182 @@ static hyb_status capture(hyb_batch* b) {
     HYB_CUDA_TRY(cudaGraphInstantiate(&b->exec, graph, 0));
     b->dirty = false;
     return HYB_OK;
+}
+
+// mean time of `trials` steps of the current form, each after a write larger than the L2
+static hyb_status time_steps(hyb_batch* b, int trials, cudaEvent_t e0, cudaEvent_t e1, void* flush, size_t flush_bytes,
+                             float* ms_out) {
+    hyb_status st = capture(b);
+    if (st != HYB_OK) return st;
+    HYB_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));           // warm
+    float ms = 0.f;
+    for (int t = 0; t < trials; t++) {
+        if (flush) HYB_CUDA_TRY(cudaMemsetAsync(flush, t & 0xff, flush_bytes, b->stream));
+        HYB_CUDA_TRY(cudaEventRecord(e0, b->stream));
+        HYB_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+        HYB_CUDA_TRY(cudaEventRecord(e1, b->stream));
+        HYB_CUDA_TRY(cudaEventSynchronize(e1));
+        float one = 0.f;
+        HYB_CUDA_TRY(cudaEventElapsedTime(&one, e0, e1));
+        ms += one;
+    }
+    *ms_out = ms / (float)trials;
+    return HYB_OK;
+}
+
+// one single launch per trial, each after a write larger than the L2: the mean time and each
+// role's mean duration (first CTA start to last CTA end)
+static cudaError_t run_single(hyb_batch* b, int trials, cudaEvent_t e0, cudaEvent_t e1, void* flush, size_t flush_bytes,
+                              float* ms_out, double* dur) {
+    const StepArgs a = step_args(b, b->d_stamp);
+    for (int r = 0; r < kRoles; r++) dur[r] = 0.0;
+    cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned) * 2 * kRoles, b->stream);
+    if (e == cudaSuccess) e = batch_step_launch(a, b->step_ctas, b->stream);          // warm
+    float ms = 0.f;
+    for (int t = 0; t < trials && e == cudaSuccess; t++) {
+        unsigned long long init[2 * kRoles];
+        for (int r = 0; r < kRoles; r++) { init[2 * r] = ~0ull; init[2 * r + 1] = 0ull; }
+        e = cudaMemcpyAsync(b->d_stamp, init, sizeof(init), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess && flush) e = cudaMemsetAsync(flush, t & 0xff, flush_bytes, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = batch_step_launch(a, b->step_ctas, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float one = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&one, e0, e1);
+        ms += one;
+        unsigned long long st[2 * kRoles];
+        if (e == cudaSuccess) e = cudaMemcpy(st, b->d_stamp, sizeof(st), cudaMemcpyDeviceToHost);
+        for (int r = 0; r < kRoles && e == cudaSuccess; r++)
+            if (b->role_ctas[r] > 0 && st[2 * r + 1] > st[2 * r]) dur[r] += 1e-6 * (double)(st[2 * r + 1] - st[2 * r]);
+    }
+    *ms_out = ms / (float)trials;
+    for (int r = 0; r < kRoles; r++) dur[r] /= trials;
+    return e;
+}
+
+// candidate strip heights of a group whose work items share `units` strip sweepers: a fixed
+// ladder plus, for 1 to 4 waves of the sweepers, the smallest height whose items fit that many
+static std::vector<int> single_candidates(const hyb_batch* b, const hyb_batch::Group& G, int units) {
+    std::vector<int> hs = {2, 3, 4, 6, 8, 12, 16, 24, 32};
+    for (int w = 1; w <= 4; w++)
+        for (int h = 2; h <= 256; h++) {
+            int64_t items = 0;
+            for (int m : G.members) items += strips_of(b->grids[m]->d.n2, h);
+            if (items <= (int64_t)w * units) { hs.push_back(h); break; }
+        }
+    std::sort(hs.begin(), hs.end());
+    hs.erase(std::unique(hs.begin(), hs.end()), hs.end());
+    return hs;
+}
+
+// the autotuner's second part, on the bound fields (saved first and restored at the end, so that
+// tuning leaves them as they were).  Rounds of: for the current split of the single launch's CTAs,
+// each group's strip height (all groups' candidates timed together, each group judged by its own
+// role's duration); then a new split with CTAs in proportion to each role's CTA time (CTAs x
+// duration), until the split repeats.  The fastest (split, heights) is kept, then the faster of
+// the single launch and the graph of launches (each timed as its captured graph).
+static hyb_status tune_single(hyb_batch* b, int trials, cudaEvent_t e0, cudaEvent_t e1, void* flush, size_t flush_bytes) {
+    for (auto* g : b->grids) if (!g->bound) return HYB_OK;     // nothing to run on yet: keep the first split
+    struct Saved { void* dst; void* copy; size_t bytes; };
+    std::vector<Saved> saved;
+    hyb_status result = HYB_OK;
+    for (auto* g : b->grids) {
+        const size_t bytes = (size_t)g->cells * (g->d.dims == 20 ? 2 : 1) * (size_t)(g->d.precision / 8);
+        for (int c = 0; c < 6 && result == HYB_OK; c++) {
+            void* dst = c < 3 ? g->E[c] : g->B[c - 3];
+            void* copy = nullptr;
+            cudaError_t e = cudaMalloc(&copy, bytes);
+            if (e != cudaSuccess) { result = cuda_fail(e, "hyb_batch_tune copies"); break; }
+            saved.push_back(Saved{dst, copy, bytes});
+            e = cudaMemcpyAsync(copy, dst, bytes, cudaMemcpyDeviceToDevice, b->stream);
+            if (e != cudaSuccess) result = cuda_fail(e, "hyb_batch_tune copies");
+        }
+    }
+    const bool keep_single = b->single;
+    b->single = true;
+    static const int kTeams[4] = {1, 8, 4, 2};                   // strip sweepers per CTA of each 2D role
+    float best = 1e30f;
+    int best_split[kRoles];
+    std::vector<int> best_h(b->groups.size());
+    std::copy(b->role_ctas, b->role_ctas + kRoles, best_split);
+    for (size_t k = 0; k < b->groups.size(); k++) best_h[k] = b->groups[k].rows_single > 0 ? b->groups[k].rows_single : b->groups[k].rows_per_strip;
+    for (int iter = 0; iter < 6 && result == HYB_OK; iter++) {
+        std::vector<std::vector<int>> cand(b->groups.size());
+        size_t nc = 1;
+        for (size_t k = 0; k < b->groups.size(); k++) {
+            const int r = role_of_n1(b->groups[k].n1);
+            cand[k] = single_candidates(b, b->groups[k], kTeams[r] * b->role_ctas[r]);
+            nc = std::max(nc, cand[k].size());
+        }
+        std::vector<double> dbest(b->groups.size(), 1e30);
+        std::vector<int> hbest(b->groups.size(), 0);
+        cudaError_t e = cudaSuccess;
+        for (size_t c = 0; c < nc && e == cudaSuccess && result == HYB_OK; c++) {
+            for (size_t k = 0; k < b->groups.size() && result == HYB_OK; k++) {
+                b->groups[k].rows_single = cand[k][std::min(c, cand[k].size() - 1)];
+                result = group_plan(b, b->groups[k], b->groups[k].rows_single);
+            }
+            if (result == HYB_OK) result = halo_plan(b);
+            if (result != HYB_OK) break;
+            float ms = 0.f;
+            double dur[kRoles];
+            e = run_single(b, trials, e0, e1, flush, flush_bytes, &ms, dur);
+            for (size_t k = 0; k < b->groups.size() && e == cudaSuccess; k++) {
+                const double d = dur[role_of_n1(b->groups[k].n1)];
+                if (d < dbest[k]) { dbest[k] = d; hbest[k] = b->groups[k].rows_single; }
+            }
+        }
+        if (e != cudaSuccess) result = cuda_fail(e, "hyb_batch_tune (single launch)");
+        if (result != HYB_OK) break;
+        // this split with each group's best height
+        for (size_t k = 0; k < b->groups.size() && result == HYB_OK; k++) {
+            b->groups[k].rows_single = hbest[k];
+            result = group_plan(b, b->groups[k], hbest[k]);
+        }
+        if (result == HYB_OK) result = halo_plan(b);
+        if (result != HYB_OK) break;
+        float ms = 0.f;
+        double dur[kRoles];
+        e = run_single(b, trials, e0, e1, flush, flush_bytes, &ms, dur);
+        if (e != cudaSuccess) { result = cuda_fail(e, "hyb_batch_tune (single launch)"); break; }
+        if (ms < best) {
+            best = ms;
+            std::copy(b->role_ctas, b->role_ctas + kRoles, best_split);
+            best_h = hbest;
+            std::copy(dur, dur + kRoles, b->role_ms);
+        }
+        double w[kRoles];
+        for (int r = 0; r < kRoles; r++) w[r] = b->role_ctas[r] > 0 ? (double)b->role_ctas[r] * std::max(dur[r], 1e-3) : 0.0;
+        int prev[kRoles];
+        std::copy(b->role_ctas, b->role_ctas + kRoles, prev);
+        split_ctas(b, w);
+        if (std::equal(prev, prev + kRoles, b->role_ctas)) break;
+    }
+    std::copy(best_split, best_split + kRoles, b->role_ctas);
+    for (size_t k = 0; k < b->groups.size(); k++) b->groups[k].rows_single = best_h[k];
+    // the faster form of the step (each timed as its captured graph)
+    b->single = keep_single;
+    if (result == HYB_OK) {
+        float t_single = 0.f, t_multi = 0.f;
+        b->single = true;
+        result = time_steps(b, trials, e0, e1, flush, flush_bytes, &t_single);
+        if (result == HYB_OK) {
+            b->single = false;
+            result = time_steps(b, trials, e0, e1, flush, flush_bytes, &t_multi);
+        }
+        b->single = result == HYB_OK ? t_single <= t_multi : keep_single;
+    }
+    for (const Saved& sv : saved) {
+        cudaError_t e = cudaMemcpyAsync(sv.dst, sv.copy, sv.bytes, cudaMemcpyDeviceToDevice, b->stream);
+        if (e != cudaSuccess && result == HYB_OK) result = cuda_fail(e, "hyb_batch_tune restore");
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess && result == HYB_OK) result = cuda_fail(e, "hyb_batch_tune restore");
+    for (const Saved& sv : saved) cudaFree(sv.copy);
+    count_launches(b);
+    b->dirty = true;
+    return result;
 }
 
 }  // namespace hyb
@@ -209,7 +500,7 @@ hyb_status hyb_batch_create(const hyb_grid_desc* descs, int n, void* stream, hyb
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.join, cudaEventDisableTiming);
         if (e != cudaSuccess) { hyb_status st = cuda_fail(e, "stream/event creation"); hyb_batch_destroy(b); return st; }
-        hyb_status st = group_plan(b, G);
+        hyb_status st = group_plan(b, G, G.rows_per_strip);
         if (st != HYB_OK) { hyb_batch_destroy(b); return st; }
     }
     if (!b->q3.empty()) {
@@ -229,9 +520,32 @@ hyb_status hyb_batch_create(const hyb_grid_desc* descs, int n, void* stream, hyb
         b->ojoin.push_back(j);
         if (e != cudaSuccess) { hyb_status st = cuda_fail(e, "stream/event creation"); hyb_batch_destroy(b); return st; }
     }
-    b->launches_per_step = (int)b->groups.size() + (b->groups.empty() ? 0 : 1);
-    if (!b->q3.empty()) b->launches_per_step += 3 * (((int)b->q3.size() + 7) / 8);
-    for (int i : b->others) b->launches_per_step += hyb_launches_per_step(b->grids[i]);
+    // the single launch: every grid in a role, at most one launch's worth of quasi-3D modes,
+    // one CTA per SM for every role
+    {
+        bool ok = b->others.empty() && (int)b->q3.size() <= kQModes && !(b->groups.empty() && b->q3.empty());
+        for (auto& G : b->groups) ok = ok && role_of_n1(G.n1) >= 0;
+        if (ok && !b->q3.empty()) {
+            std::vector<hyb_grid*> gs;
+            for (int i : b->q3) gs.push_back(b->grids[i]);
+            Q3Args qa;
+            ok = quasi3d_step_args(gs.data(), (int)gs.size(), &qa) == HYB_OK;
+        }
+        int ctas = 0;
+        int roles = (int)b->groups.size() + (b->q3.empty() ? 0 : 1);
+        if (ok && (batch_step_ctas(&ctas) != cudaSuccess || ctas < roles)) { ok = false; cudaGetLastError(); }
+        if (ok) {
+            cudaError_t e = cudaMalloc(&b->d_sync, sizeof(unsigned) * 2 * kRoles);
+            if (e == cudaSuccess) e = cudaMalloc(&b->d_stamp, sizeof(unsigned long long) * 2 * kRoles);
+            if (e == cudaSuccess) e = cudaMemset(b->d_sync, 0, sizeof(unsigned) * 2 * kRoles);
+            if (e != cudaSuccess) { hyb_status st = cuda_fail(e, "hyb_batch_create"); hyb_batch_destroy(b); return st; }
+            b->step_ctas = ctas;
+            default_split(b);
+        }
+        b->single_ok = ok;
+        b->single = ok;
+    }
+    count_launches(b);
     *out = b;
     return HYB_OK;
 }
@@ -290,7 +604,7 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
             for (int w = 1; w <= 3; w++)
                 for (int h = 2; h <= 64; h++) {
                     int64_t items = 0;
-                    for (int m : G.members) items += (b->grids[m]->d.n2 + h - 1) / h;
+                    for (int m : G.members) items += strips_of(b->grids[m]->d.n2, h);
                     if (items <= (int64_t)w * sms * occ) { hs.push_back(h); break; }
                 }
             std::sort(hs.begin(), hs.end());
@@ -298,7 +612,7 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
         }
         for (int h : hs) {
             G.rows_per_strip = h;
-            hyb_status st = group_plan(b, G);
+            hyb_status st = group_plan(b, G, h);
             if (st != HYB_OK) { result = st; break; }
             FusedBatch fb;
             for (size_t k = 0; k < G.members.size(); k++) {
@@ -337,9 +651,10 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
         for (void* p : bufs) cudaFree(p);
         if (result != HYB_OK) break;
         G.rows_per_strip = best_h;
-        result = group_plan(b, G);
+        result = group_plan(b, G, best_h);
         if (result != HYB_OK) break;
     }
+    if (result == HYB_OK && b->single_ok) result = tune_single(b, trials, e0, e1, flush, flush_bytes);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (flush) cudaFree(flush);
@@ -349,7 +664,7 @@ hyb_status hyb_batch_tune(hyb_batch* b, int trials) {
 
 int hyb_batch_rows_per_strip(const hyb_batch* b, int n1) {
     if (!b) return 0;
-    for (auto& G : b->groups) if (G.n1 == n1) return G.rows_per_strip;
+    for (auto& G : b->groups) if (G.n1 == n1) return form_height(b, G);
     return 0;
 }
 
@@ -358,8 +673,8 @@ hyb_status hyb_batch_set_rows_per_strip(hyb_batch* b, int n1, int h) {
     if (h < 1) { set_error("rows per strip must be >= 1"); return HYB_EINVAL; }
     for (auto& G : b->groups)
         if (G.n1 == n1) {
-            G.rows_per_strip = h;
-            return group_plan(b, G);
+            G.rows_per_strip = G.rows_single = h;
+            return group_plan(b, G, h);
         }
     set_error("no fused group with this n1");
     return HYB_EINVAL;
@@ -367,12 +682,33 @@ hyb_status hyb_batch_set_rows_per_strip(hyb_batch* b, int n1, int h) {
 
 int hyb_batch_launches_per_step(const hyb_batch* b) { return b ? b->launches_per_step : 0; }
 
+hyb_status hyb_batch_set_single_launch(hyb_batch* b, int on) {
+    if (!b) { set_error("null batch"); return HYB_EINVAL; }
+    if (on && !b->single_ok) { set_error("hyb_batch_set_single_launch: some grid has no role in the single launch"); return HYB_EINVAL; }
+    b->single = on != 0;
+    count_launches(b);
+    b->dirty = true;
+    return HYB_OK;
+}
+
+int hyb_batch_single_launch(const hyb_batch* b) { return b && b->single ? 1 : 0; }
+
+int hyb_batch_role_ctas(const hyb_batch* b, int role) {
+    return b && role >= 0 && role < kRoles && b->single_ok ? b->role_ctas[role] : 0;
+}
+
+double hyb_batch_role_ms(const hyb_batch* b, int role) {
+    return b && role >= 0 && role < kRoles ? b->role_ms[role] : 0.0;
+}
+
 hyb_status hyb_batch_destroy(hyb_batch* b) {
     if (!b) return HYB_OK;
     if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->halo_tasks) cudaFree(b->halo_tasks);
+    if (b->d_sync) cudaFree(b->d_sync);
+    if (b->d_stamp) cudaFree(b->d_stamp);
     if (b->q3side) cudaStreamDestroy(b->q3side);
     if (b->q3fork) cudaEventDestroy(b->q3fork);
     if (b->q3join) cudaEventDestroy(b->q3join);

@@ -60,21 +60,7 @@ cudaError_t halo_parts(int n1, const FusedBatch& fb, int k0, int nk, cudaStream_
 __global__ void k_copy_rows(const RowCopy* __restrict__ tasks, int n) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += nw) {
-        const RowCopy t = tasks[w];
-        const float4* s4 = reinterpret_cast<const float4*>(t.src);
-        float4* d4 = reinterpret_cast<float4*>(t.dst);
-        const int n4 = t.n / 4;
-        int i = lane;
-        for (; i + 96 < n4; i += 128) {
-            const float4 a = s4[i], b = s4[i + 32], c = s4[i + 64], d = s4[i + 96];
-            d4[i] = a;
-            d4[i + 32] = b;
-            d4[i + 64] = c;
-            d4[i + 96] = d;
-        }
-        for (; i < n4; i += 32) d4[i] = s4[i];
-    }
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += nw) copy_row_warp(tasks[w], lane);
 }
 
 cudaError_t copy_rows(const RowCopy* tasks, int n, cudaStream_t s) {

@@ -88,6 +88,21 @@ __device__ __forceinline__ void wait_flag(const int* f, int epoch, int* err, lon
         __nanosleep(256);
     }
 }
+// one row copy by one warp (n a multiple of 4, both rows 16-byte aligned), four float4 in flight a lane
+__device__ __forceinline__ void copy_row_warp(const RowCopy& t, int lane) {
+    const float4* s4 = reinterpret_cast<const float4*>(t.src);
+    float4* d4 = reinterpret_cast<float4*>(t.dst);
+    const int n4 = t.n / 4;
+    int i = lane;
+    for (; i + 96 < n4; i += 128) {
+        const float4 a = s4[i], b = s4[i + 32], c = s4[i + 64], d = s4[i + 96];
+        d4[i] = a;
+        d4[i + 32] = b;
+        d4[i + 64] = c;
+        d4[i + 96] = d;
+    }
+    for (; i < n4; i += 32) d4[i] = s4[i];
+}
 __device__ __forceinline__ void stg_stream(float2* p, float2 v) {
     asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(v.x), "f"(v.y) : "memory");
 }

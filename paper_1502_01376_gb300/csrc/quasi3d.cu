@@ -18,18 +18,10 @@
 
 #include <algorithm>
 
-#include "hyb_internal.cuh"
-#include "packed_dev.cuh"
+#include "q3d_body.cuh"
 
 namespace hyb {
 
-template <typename T>
-struct QTab {
-    cplx<T> sp;   // sigma+ = i k e^{+i k dz/2}
-    cplx<T> sm;   // sigma- = i k e^{-i k dz/2}
-    T cjz;        // ampere dt F corr
-    T cj;         // ampere dt F
-};
 
 template <typename T>
 struct QPlan {
@@ -40,16 +32,6 @@ struct QPlan {
 };
 
 struct QPtrs { void* p[9]; };
-// the arrays of up to kQModes modes advanced by one launch (modes of equal nz = 2048, nr, dr):
-// mode q's field f at p[9 q + f], its spectra at spec[q]
-constexpr int kQModes = 8;
-struct QMulti { void* p[kQModes * 9]; float2* spec[kQModes]; int nm; };
-
-constexpr int kQThreads = 256;
-
-// i m / r times a
-template <typename C>
-__device__ __forceinline__ C imr(C a, decltype(C::x) m_over_r) { return mkc<C>(-m_over_r * a.y, m_over_r * a.x); }
 
 // complex transforms along z of row blocks of RB rows (block i: field i / nblk); persistent, the
 // next block's points held in registers while the current one is transformed (RB nz <= 2048)
@@ -109,119 +91,12 @@ __global__ void __launch_bounds__(kQThreads) k_qfft(QPtrs io, cplx<T>* __restric
     }
 }
 
-// ---------------------------------------------------------------- nz = 2048, FP32: register-resident rows
-// X[k] = sum_j x[j] W^{jk}, W = exp(-2 pi i / 2048), factored 8 x 8 x 8 x 4 with k = k1 + 8 k2 + 64 k3 + 512 k4:
-//   S1  thread t:            DFT8 over n of x[t + 256 n] -> k1, times W_2048^{t k1}      -> A(k1, t)
-//   S2  (t0, k1) = (t & 31, t >> 5):  DFT8 over t1 of A(k1, t0 + 32 t1) -> k2, times W_256^{t0 k2}
-//   S3  (u0, k1, k2) = (t & 3, (t >> 2) & 7, t >> 5):  DFT8 over u1 of A'(k1, k2, u0 + 4 u1) -> k3,
-//       times W_32^{u0 k3}
-//   S4  the 512 (k1, k2, k3) in two halves:  DFT4 over u0 -> k4, written to X[k1 + 8 k2 + 64 k3 + 512 k4]
-// Exchange layouts (float2 units): A(k1, t) at 256 k1 + t; A'(k1, k2, t0) at 260 k1 + 32 k2 + t0;
-// A''(k1, k2, k3, u0) at 516 u0 + 64 k3 + k1 + 8 k2 (in the A buffer).  With 8-byte accesses a half-warp
-// of every exchange reaches 16 different bank pairs; global loads and stores are row-contiguous per warp.
-// The inverse uses the conjugate twiddles and scales by 1/2048.  One row per 256-thread block
-// iteration; persistent, the next row's points held in registers while the current one is transformed.
-constexpr int kQ2k = 2048;
-constexpr int kQ2kA = 2064, kQ2kB = 2080;
-constexpr int kQ2kTw = 7 * 256 + 7 * 32 + 7 * 4;     // stage twiddles, in the order the threads read them
-
-template <bool INV>
-__device__ __forceinline__ float2 q2k_tw(float2 a, float2 w) {
-    return INV ? make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y))
-               : make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
-}
-
 template <bool INV>
 __global__ void __launch_bounds__(256, 2) k_cfft2048(const __grid_constant__ QMulti io, int nr, int nf,
                                                      const float2* __restrict__ tw) {
     __shared__ __align__(16) float2 bufA[kQ2kA];
     __shared__ __align__(16) float2 bufB[kQ2kB];
-    const int t = threadIdx.x;
-    const int64_t per = (int64_t)nr * nf, total = per * io.nm;
-    float2 w1[8], w2[8], w3[8], nx[8];
-#pragma unroll
-    for (int k = 1; k < 8; k++) {
-        w1[k] = tw[(k - 1) * 256 + t];
-        w2[k] = tw[1792 + (k - 1) * 32 + (t & 31)];
-        w3[k] = tw[2016 + (k - 1) * 4 + (t & 3)];
-    }
-    // row j of the launch: mode q, field f, radial row r; its spectrum row is jj of mode q
-    auto src_of = [&](int64_t j) -> const float2* {
-        const int q = (int)(j / per);
-        const int64_t jj = j - q * per;
-        const int f = (int)(jj / nr);
-        const int64_t r = jj - (int64_t)f * nr;
-        return INV ? io.spec[q] + jj * kQ2k : reinterpret_cast<const float2*>(io.p[9 * q + f]) + r * kQ2k;
-    };
-    auto fetch = [&](int64_t j) {
-        const float2* x = src_of(j);
-#pragma unroll
-        for (int n = 0; n < 8; n++) nx[n] = __ldcs(x + t + 256 * n);
-    };
-    int64_t j = blockIdx.x;
-    if (j < total) fetch(j);
-    for (; j < total; j += gridDim.x) {
-        float2 v[8];
-#pragma unroll
-        for (int n = 0; n < 8; n++) v[n] = nx[n];
-        if (j + gridDim.x < total) fetch(j + gridDim.x);
-        // S1
-        dft8x<INV>(v);
-#pragma unroll
-        for (int k = 1; k < 8; k++) v[k] = q2k_tw<INV>(v[k], w1[k]);
-        __syncthreads();                 // the previous row's S4 has read the A buffer
-#pragma unroll
-        for (int k = 0; k < 8; k++) bufA[256 * k + t] = v[k];
-        __syncthreads();
-        // S2
-        {
-            const int t0 = t & 31, k1 = t >> 5;
-#pragma unroll
-            for (int n = 0; n < 8; n++) v[n] = bufA[256 * k1 + t0 + 32 * n];
-            dft8x<INV>(v);
-#pragma unroll
-            for (int k = 1; k < 8; k++) v[k] = q2k_tw<INV>(v[k], w2[k]);
-#pragma unroll
-            for (int k = 0; k < 8; k++) bufB[260 * k1 + 32 * k + t0] = v[k];
-        }
-        __syncthreads();
-        // S3
-        {
-            const int u0 = t & 3, k1 = (t >> 2) & 7, k2 = t >> 5;
-#pragma unroll
-            for (int n = 0; n < 8; n++) v[n] = bufB[260 * k1 + 32 * k2 + u0 + 4 * n];
-            dft8x<INV>(v);
-#pragma unroll
-            for (int k = 1; k < 8; k++) v[k] = q2k_tw<INV>(v[k], w3[k]);
-#pragma unroll
-            for (int k = 0; k < 8; k++) bufA[516 * u0 + 64 * k + k1 + 8 * k2] = v[k];
-        }
-        __syncthreads();
-        // S4
-        float2* X;
-        {
-            const int q = (int)(j / per);
-            const int64_t jj = j - q * per;
-            const int f = (int)(jj / nr);
-            const int64_t r = jj - (int64_t)f * nr;
-            X = INV ? reinterpret_cast<float2*>(io.p[9 * q + f]) + r * kQ2k : io.spec[q] + jj * kQ2k;
-        }
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int it = t + 256 * h;      // k1 + 8 k2 + 64 k3
-            float2 a0 = bufA[it], a1 = bufA[516 + it], a2 = bufA[1032 + it], a3 = bufA[1548 + it];
-            dft4x<INV>(a0, a1, a2, a3);
-            if (INV) {
-                const float s = 1.0f / (float)kQ2k;
-                a0 = vmul(a0, make_float2(s, s)); a1 = vmul(a1, make_float2(s, s));
-                a2 = vmul(a2, make_float2(s, s)); a3 = vmul(a3, make_float2(s, s));
-            }
-            __stcs(X + it, a0);
-            __stcs(X + it + 512, a1);
-            __stcs(X + it + 1024, a2);
-            __stcs(X + it + 1536, a3);
-        }
-    }
+    cfft2048_body<INV, false>(io, nr, nf, tw, blockIdx.x, gridDim.x, threadIdx.x, bufA, bufB, 0);
 }
 
 // stage twiddles of k_cfft2048, W_N^e = exp(-2 pi i e / N), in the order above
@@ -237,82 +112,10 @@ static std::vector<float2> cfft2048_twiddles() {
     return w;
 }
 
-template <typename T>
-struct QB { cplx<T> z, r, p; };
-
-// Faraday for axial mode k at radial row j: B^{n+1/2} from B^{n-1/2} at j and E^n at rows j and j+1
-// (tangential E vanishes on the conducting wall r = nr dr; on the axis B_r follows the m rules)
-template <typename T>
-__device__ __forceinline__ QB<T> qfaraday_at(const cplx<T>* __restrict__ spec, int64_t fs, int nz, int nr, int j, int k,
-                                             cplx<T> sp, T dt, T dr, int m) {
-    using C = cplx<T>;
-    const C* Ez = spec; const C* Er = spec + fs; const C* Ep = spec + 2 * fs;
-    const C* Bz = spec + 3 * fs; const C* Br = spec + 4 * fs; const C* Bp = spec + 5 * fs;
-    const T ri = (T)j * dr, rh = ((T)j + (T)0.5) * dr, rup = (T)(j + 1) * dr;
-    const T mT = (T)m;
-    const int64_t i = (int64_t)j * nz + k, iu = i + nz;
-    const C ez = Ez[i], er = Er[i], ep = Ep[i];
-    const C ezu = (j + 1 < nr) ? Ez[iu] : mkc<C>((T)0, (T)0);
-    const C epu = (j + 1 < nr) ? Ep[iu] : mkc<C>((T)0, (T)0);
-    C cr;
-    if (j > 0) cr = csub(imr(ez, mT / ri), cmul(sp, ep));
-    else if (m == 1) cr = csub(imr(Ez[nz + k], mT / dr), cmul(sp, ep));
-    else cr = mkc<C>((T)0, (T)0);
-    const C cp = csub(cmul(sp, er), cscale(csub(ezu, ez), (T)1 / dr));
-    const C cz = csub(cscale(csub(cscale(epu, rup), cscale(ep, ri)), (T)1 / (rh * dr)), imr(er, mT / rh));
-    QB<T> b;
-    b.z = csub(Bz[i], cscale(cz, dt));
-    b.r = (j == 0 && m != 1) ? mkc<C>((T)0, (T)0) : csub(Br[i], cscale(cr, dt));
-    b.p = csub(Bp[i], cscale(cp, dt));
-    return b;
-}
-
-// one leapfrog step per (axial mode k, radial row j) on the spectra [E, B, J] (slots 0..8): Faraday at
-// rows j and j-1 (the latter recomputed, so no launch boundary is needed between the halves), then
-// Ampere at row j.  E^{n+1} goes to the J slots 6..8 (J at row j is read by this thread only) and
-// B^{n+1/2} to slots 9..11; slots 0..5 are only read, so neighbouring threads see the old values.
-template <typename T>
-struct QLeap { cplx<T>* spec[kQModes]; const QTab<T>* tab[kQModes]; T dt[kQModes]; int m[kQModes]; };
-
+// one leapfrog step per (axial mode, radial row, mode): grid (nz / kQThreads, nr, modes)
 template <typename T>
 __global__ void __launch_bounds__(kQThreads) k_qleap(const __grid_constant__ QLeap<T> ql, int nz, int nr, T dr) {
-    using C = cplx<T>;
-    cplx<T>* __restrict__ spec = ql.spec[blockIdx.z];               // mode of this block
-    const QTab<T>* __restrict__ tab = ql.tab[blockIdx.z];
-    const T dt = ql.dt[blockIdx.z];
-    const int m = ql.m[blockIdx.z];
-    const int j = blockIdx.y;                                        // radial row
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;             // axial mode
-    if (k >= nz) return;
-    const int64_t fs = (int64_t)nr * nz, i = (int64_t)j * nz + k;
-    const C* Ez = spec; const C* Er = spec + fs; const C* Ep = spec + 2 * fs;
-    C* Jz = spec + 6 * fs; C* Jr = spec + 7 * fs; C* Jp = spec + 8 * fs;
-    C* Bn = spec + 9 * fs;
-    const T ri = (T)j * dr, rh = ((T)j + (T)0.5) * dr, rd = ((T)j - (T)0.5) * dr;
-    const T mT = (T)m;
-    const QTab<T> q = tab[k];
-    const QB<T> b = qfaraday_at<T>(spec, fs, nz, nr, j, k, q.sp, dt, dr, m);
-    const C cr = csub(imr(b.z, mT / rh), cmul(q.sm, b.p));
-    C cp, cz;
-    if (j > 0) {
-        const QB<T> bd = qfaraday_at<T>(spec, fs, nz, nr, j - 1, k, q.sp, dt, dr, m);
-        cp = csub(cmul(q.sm, b.r), cscale(csub(b.z, bd.z), (T)1 / dr));
-        cz = csub(cscale(csub(cscale(b.p, rh), cscale(bd.p, rd)), (T)1 / (ri * dr)), imr(b.r, mT / ri));
-    } else {
-        cp = (m == 1) ? csub(cmul(q.sm, b.r), cscale(b.z, (T)2 / dr)) : mkc<C>((T)0, (T)0);
-        cz = (m == 0) ? cscale(b.p, (T)4 / dr) : mkc<C>((T)0, (T)0);
-    }
-    C er = csub(cadd(Er[i], cscale(cr, dt)), cscale(Jr[i], q.cj));
-    C ep = csub(cadd(Ep[i], cscale(cp, dt)), cscale(Jp[i], q.cj));
-    C ez = csub(cadd(Ez[i], cscale(cz, dt)), cscale(Jz[i], q.cjz));
-    if (j == 0 && m != 0) ez = mkc<C>((T)0, (T)0);
-    if (j == 0 && m != 1) ep = mkc<C>((T)0, (T)0);
-    Jz[i] = ez;
-    Jr[i] = er;
-    Jp[i] = ep;
-    Bn[i] = b.z;
-    Bn[fs + i] = b.r;
-    Bn[2 * fs + i] = b.p;
+    qleap_body<T>(ql, nz, nr, dr, (int)(blockIdx.x * blockDim.x + threadIdx.x), (int)blockIdx.y, (int)blockIdx.z);
 }
 
 template <typename T>
@@ -360,6 +163,37 @@ static hyb_status create_t(hyb_grid* g) {
     return HYB_OK;
 }
 
+// the arguments of the FP32 nz = 2048 stages for the modes gs[0 .. n - 1] (n <= kQModes, pairwise
+// quasi3d_can_batch): the forward transform reads E, B, j of every mode into its spectra, the
+// inverse writes the advanced E, B spectra (slots 6 .. 11) back to E, B
+hyb_status quasi3d_step_args(hyb_grid* const* gs, int n, Q3Args* out) {
+    if (n < 1 || n > kQModes || gs[0]->d.precision != 32) { set_error("quasi3d_step_args: bad modes"); return HYB_EINVAL; }
+    const QPlan<float>* P = reinterpret_cast<const QPlan<float>*>(gs[0]->qtab);
+    if (!P || !P->tw2k) { set_error("quasi3d_step_args: not the nz = 2048 FP32 path"); return HYB_EINVAL; }
+    const int nz = gs[0]->d.n1, nr = gs[0]->d.n2;
+    Q3Args a{};
+    for (int q = 0; q < n; q++) {
+        for (int c = 0; c < 3; c++) {
+            a.fin.p[9 * q + c] = gs[q]->E[c]; a.fin.p[9 * q + 3 + c] = gs[q]->B[c]; a.fin.p[9 * q + 6 + c] = gs[q]->J[c];
+            a.fout.p[9 * q + c] = gs[q]->E[c]; a.fout.p[9 * q + 3 + c] = gs[q]->B[c];
+        }
+        QPlan<float>* Pq = reinterpret_cast<QPlan<float>*>(gs[q]->qtab);
+        a.fin.spec[q] = reinterpret_cast<float2*>(Pq->spec);
+        a.fout.spec[q] = reinterpret_cast<float2*>(Pq->spec + 6 * (int64_t)nr * nz);
+        a.ql.spec[q] = Pq->spec;
+        a.ql.tab[q] = Pq->tab;
+        a.ql.dt[q] = (float)gs[q]->d.dt;
+        a.ql.m[q] = gs[q]->d.azimuthal_m;
+    }
+    a.fin.nm = a.fout.nm = n;
+    a.tw2k = P->tw2k;
+    a.nr = nr;
+    a.nm = n;
+    a.dr = (float)gs[0]->d.dx2;
+    *out = a;
+    return HYB_OK;
+}
+
 // one step of the modes gs[0 .. n - 1] (n = 1, or modes that qualify for quasi3d_advance_many)
 // on stream st: z transform of E, B, j, the leapfrog, inverse of the advanced E, B
 template <typename T>
@@ -378,23 +212,15 @@ static hyb_status step_modes(hyb_grid* const* gs, int n, cudaStream_t st) {
         ql.m[q] = gs[q]->d.azimuthal_m;
     }
     if (P->tw2k) {
-        QMulti fin{}, fout{};
-        for (int q = 0; q < n; q++) {
-            for (int c = 0; c < 3; c++) {
-                fin.p[9 * q + c] = gs[q]->E[c]; fin.p[9 * q + 3 + c] = gs[q]->B[c]; fin.p[9 * q + 6 + c] = gs[q]->J[c];
-                fout.p[9 * q + c] = gs[q]->E[c]; fout.p[9 * q + 3 + c] = gs[q]->B[c];
-            }
-            QPlan<T>* Pq = reinterpret_cast<QPlan<T>*>(gs[q]->qtab);
-            fin.spec[q] = reinterpret_cast<float2*>(Pq->spec);
-            fout.spec[q] = reinterpret_cast<float2*>(Pq->spec + 6 * (int64_t)nr * nz);
-        }
-        fin.nm = fout.nm = n;
+        Q3Args a{};
+        hyb_status hs = quasi3d_step_args(gs, n, &a);
+        if (hs != HYB_OK) return hs;
         const int res = resident_grid((const void*)k_cfft2048<false>, 256, 0);
-        k_cfft2048<false><<<(unsigned)std::min<int64_t>(res, (int64_t)n * 9 * nr), 256, 0, st>>>(fin, nr, 9, P->tw2k);
+        k_cfft2048<false><<<(unsigned)std::min<int64_t>(res, (int64_t)n * 9 * nr), 256, 0, st>>>(a.fin, nr, 9, a.tw2k);
         const dim3 mgrid((unsigned)((nz + kQThreads - 1) / kQThreads), (unsigned)nr, (unsigned)n);
         k_qleap<T><<<mgrid, kQThreads, 0, st>>>(ql, nz, nr, (T)d.dx2);
         const int res2 = resident_grid((const void*)k_cfft2048<true>, 256, 0);
-        k_cfft2048<true><<<(unsigned)std::min<int64_t>(res2, (int64_t)n * 6 * nr), 256, 0, st>>>(fout, nr, 6, P->tw2k);
+        k_cfft2048<true><<<(unsigned)std::min<int64_t>(res2, (int64_t)n * 6 * nr), 256, 0, st>>>(a.fout, nr, 6, a.tw2k);
     } else {
         const int RB = fft_rows_per_launch(nz, (int64_t)nr * 6), nblk = (nr + RB - 1) / RB;
         const size_t smem = sizeof(C) * 2 * fpad_size((size_t)RB * nz);

@@ -1,5 +1,5 @@
 // tm_sched.cuh -- the round schedule and the real-transform helpers shared by the
-// TMEM-resident fused kernels (fused_tm.cu for n1 = 4096, fused_tmt.cu for n1 =
+// TMEM-resident fused kernels (tm_body.cuh for n1 = 4096, tmt_body.cuh for n1 =
 // 512 .. 2048): which row each thread group transforms in each round, where its
 // forward rows come from, and the even/odd split of the real transform.
 #pragma once

@@ -106,6 +106,14 @@ def lib():
             L.hyb_batch_set_rows_per_strip.restype = ctypes.c_int
             L.hyb_batch_launches_per_step.argtypes = [_V]
             L.hyb_batch_launches_per_step.restype = ctypes.c_int
+            L.hyb_batch_set_single_launch.argtypes = [_V, ctypes.c_int]
+            L.hyb_batch_set_single_launch.restype = S
+            L.hyb_batch_single_launch.argtypes = [_V]
+            L.hyb_batch_single_launch.restype = ctypes.c_int
+            L.hyb_batch_role_ctas.argtypes = [_V, ctypes.c_int]
+            L.hyb_batch_role_ctas.restype = ctypes.c_int
+            L.hyb_batch_role_ms.argtypes = [_V, ctypes.c_int]
+            L.hyb_batch_role_ms.restype = ctypes.c_double
             L.hyb_batch_destroy.argtypes = [_V]
             L.hyb_batch_destroy.restype = S
             L.hyb_correct_current_noalloc.argtypes = [D, _V, _V]
@@ -286,6 +294,22 @@ def hyb_batch_set_rows_per_strip(b: int, n1: int, h: int) -> None:
 
 def hyb_batch_launches_per_step(b: int) -> int:
     return lib().hyb_batch_launches_per_step(_V(b))
+
+
+def hyb_batch_set_single_launch(b: int, on: bool) -> None:
+    _check(lib().hyb_batch_set_single_launch(_V(b), 1 if on else 0))
+
+
+def hyb_batch_single_launch(b: int) -> bool:
+    return lib().hyb_batch_single_launch(_V(b)) != 0
+
+
+def hyb_batch_role_ctas(b: int, r: int) -> int:
+    return lib().hyb_batch_role_ctas(_V(b), r)
+
+
+def hyb_batch_role_ms(b: int, r: int) -> float:
+    return lib().hyb_batch_role_ms(_V(b), r)
 
 
 def hyb_batch_destroy(b: int):
@@ -505,6 +529,23 @@ class Batch:
     @property
     def launches_per_step(self):
         return hyb_batch_launches_per_step(self.h)
+
+    @property
+    def single_launch(self):
+        """True if a step is one persistent launch (False: a graph of launches)."""
+        return hyb_batch_single_launch(self.h)
+
+    @single_launch.setter
+    def single_launch(self, on):
+        hyb_batch_set_single_launch(self.h, on)
+
+    def role_ctas(self):
+        """CTAs of the single launch's roles: n1 = 4096, 512, 1024, 2048, quasi-3D."""
+        return [hyb_batch_role_ctas(self.h, r) for r in range(5)]
+
+    def role_ms(self):
+        """Each role's duration in the tuner's fastest single launch (ms)."""
+        return [hyb_batch_role_ms(self.h, r) for r in range(5)]
 
     def close(self):
         if self.h:

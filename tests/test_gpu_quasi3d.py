@@ -101,6 +101,7 @@ def test_quasi3d_modes_advanced_together_in_a_batch():
     E0, B0 = wl.band_limited_fields(w)
     mk = lambda arrs: [torch.from_numpy(a.astype(np.float32)).cuda() for a in arrs]
     b = hyb.Batch([r[4] for r in runs] + [hyb.desc_from_workload(w)])
+    b.single_launch = False                    # the graph of launches (the single launch: test_gpu_batch_single.py)
     assert b.launches_per_step == 3 + 2        # modes: z transform, leapfrog, inverse; the 2D grid: halo, fused
     copies = []
     for i, (_, grid, _, (Et, Bt, Jt), _) in enumerate(runs):
