@@ -353,14 +353,63 @@ static std::vector<int> single_candidates(const hyb_batch* b, const hyb_batch::G
     return hs;
 }
 
+// cuts every group's work items with its single-launch height
+static hyb_status plan_single(hyb_batch* b) {
+    for (auto& G : b->groups) {
+        hyb_status st = group_plan(b, G, G.rows_single);
+        if (st != HYB_OK) return st;
+    }
+    return halo_plan(b);
+}
+
+// for the current split, each group of a role in `mask` takes the candidate strip height under
+// which its role finished first (the groups' candidates timed together, in the same launches)
+static hyb_status pick_heights(hyb_batch* b, unsigned mask, int trials, cudaEvent_t e0, cudaEvent_t e1, void* flush,
+                               size_t flush_bytes) {
+    static const int kTeams[4] = {1, 8, 4, 2};                   // strip sweepers per CTA of each 2D role
+    const size_t ng = b->groups.size();
+    std::vector<std::vector<int>> cand(ng);
+    std::vector<double> dbest(ng, 1e30);
+    std::vector<int> hbest(ng);
+    size_t nc = 0;
+    for (size_t k = 0; k < ng; k++) {
+        const int r = role_of_n1(b->groups[k].n1);
+        hbest[k] = b->groups[k].rows_single;
+        if (!((mask >> r) & 1u)) continue;
+        cand[k] = single_candidates(b, b->groups[k], kTeams[r] * b->role_ctas[r]);
+        nc = std::max(nc, cand[k].size());
+    }
+    for (size_t c = 0; c < nc; c++) {
+        for (size_t k = 0; k < ng; k++)
+            if (!cand[k].empty()) b->groups[k].rows_single = cand[k][std::min(c, cand[k].size() - 1)];
+        hyb_status st = plan_single(b);
+        if (st != HYB_OK) return st;
+        float ms = 0.f;
+        double dur[kRoles];
+        cudaError_t e = run_single(b, trials, e0, e1, flush, flush_bytes, &ms, dur);
+        if (e != cudaSuccess) return cuda_fail(e, "hyb_batch_tune (single launch)");
+        for (size_t k = 0; k < ng; k++) {
+            const double d = dur[role_of_n1(b->groups[k].n1)];
+            if (!cand[k].empty() && d < dbest[k]) { dbest[k] = d; hbest[k] = b->groups[k].rows_single; }
+        }
+    }
+    for (size_t k = 0; k < ng; k++) b->groups[k].rows_single = hbest[k];
+    return plan_single(b);
+}
+
 // the autotuner's second part, on the bound fields (saved first and restored at the end, so that
-// tuning leaves them as they were).  Rounds of: for the current split of the single launch's CTAs,
-// each group's strip height (all groups' candidates timed together, each group judged by its own
-// role's duration); then a new split with CTAs in proportion to each role's CTA time (CTAs x
-// duration), until the split repeats.  The fastest (split, heights) is kept, then the faster of
-// the single launch and the graph of launches (each timed as its captured graph).
+// tuning leaves them as they were).  (1) Rounds of: each group's strip height for the current split
+// of the single launch's CTAs (pick_heights), then a new split with CTAs in proportion to each
+// role's CTA time (CTAs x duration), until the split repeats.  (2) From the fastest of those, one
+// CTA at a time to the role that finished last from another role (tried in the order of the
+// duration it would have with one CTA less, in proportion, up to three of them), the two roles'
+// heights picked again, while the launch gets faster (the proportional split is coarse for roles
+// of a few CTAs, whose durations also step with the waves of their work items).  (3) The faster of
+// the single launch and the graph of launches, each timed as its captured graph.
 static hyb_status tune_single(hyb_batch* b, int trials, cudaEvent_t e0, cudaEvent_t e1, void* flush, size_t flush_bytes) {
     for (auto* g : b->grids) if (!g->bound) return HYB_OK;     // nothing to run on yet: keep the first split
+    hyb_status hs = halo_plan(b);
+    if (hs != HYB_OK) return hs;
     struct Saved { void* dst; void* copy; size_t bytes; };
     std::vector<Saved> saved;
     hyb_status result = HYB_OK;
@@ -378,57 +427,35 @@ static hyb_status tune_single(hyb_batch* b, int trials, cudaEvent_t e0, cudaEven
     }
     const bool keep_single = b->single;
     b->single = true;
-    static const int kTeams[4] = {1, 8, 4, 2};                   // strip sweepers per CTA of each 2D role
+    for (auto& G : b->groups) if (G.rows_single < 1) G.rows_single = G.rows_per_strip;
     float best = 1e30f;
     int best_split[kRoles];
     std::vector<int> best_h(b->groups.size());
+    auto keep_best = [&](float ms, const double* dur) {
+        best = ms;
+        std::copy(b->role_ctas, b->role_ctas + kRoles, best_split);
+        for (size_t k = 0; k < b->groups.size(); k++) best_h[k] = b->groups[k].rows_single;
+        std::copy(dur, dur + kRoles, b->role_ms);
+    };
+    auto restore_best = [&]() {
+        std::copy(best_split, best_split + kRoles, b->role_ctas);
+        for (size_t k = 0; k < b->groups.size(); k++) b->groups[k].rows_single = best_h[k];
+        return plan_single(b);
+    };
+    auto measure = [&](float* ms, double* dur) -> hyb_status {
+        cudaError_t e = run_single(b, trials, e0, e1, flush, flush_bytes, ms, dur);
+        return e == cudaSuccess ? HYB_OK : cuda_fail(e, "hyb_batch_tune (single launch)");
+    };
     std::copy(b->role_ctas, b->role_ctas + kRoles, best_split);
-    for (size_t k = 0; k < b->groups.size(); k++) best_h[k] = b->groups[k].rows_single > 0 ? b->groups[k].rows_single : b->groups[k].rows_per_strip;
+    for (size_t k = 0; k < b->groups.size(); k++) best_h[k] = b->groups[k].rows_single;
+    // (1)
     for (int iter = 0; iter < 6 && result == HYB_OK; iter++) {
-        std::vector<std::vector<int>> cand(b->groups.size());
-        size_t nc = 1;
-        for (size_t k = 0; k < b->groups.size(); k++) {
-            const int r = role_of_n1(b->groups[k].n1);
-            cand[k] = single_candidates(b, b->groups[k], kTeams[r] * b->role_ctas[r]);
-            nc = std::max(nc, cand[k].size());
-        }
-        std::vector<double> dbest(b->groups.size(), 1e30);
-        std::vector<int> hbest(b->groups.size(), 0);
-        cudaError_t e = cudaSuccess;
-        for (size_t c = 0; c < nc && e == cudaSuccess && result == HYB_OK; c++) {
-            for (size_t k = 0; k < b->groups.size() && result == HYB_OK; k++) {
-                b->groups[k].rows_single = cand[k][std::min(c, cand[k].size() - 1)];
-                result = group_plan(b, b->groups[k], b->groups[k].rows_single);
-            }
-            if (result == HYB_OK) result = halo_plan(b);
-            if (result != HYB_OK) break;
-            float ms = 0.f;
-            double dur[kRoles];
-            e = run_single(b, trials, e0, e1, flush, flush_bytes, &ms, dur);
-            for (size_t k = 0; k < b->groups.size() && e == cudaSuccess; k++) {
-                const double d = dur[role_of_n1(b->groups[k].n1)];
-                if (d < dbest[k]) { dbest[k] = d; hbest[k] = b->groups[k].rows_single; }
-            }
-        }
-        if (e != cudaSuccess) result = cuda_fail(e, "hyb_batch_tune (single launch)");
-        if (result != HYB_OK) break;
-        // this split with each group's best height
-        for (size_t k = 0; k < b->groups.size() && result == HYB_OK; k++) {
-            b->groups[k].rows_single = hbest[k];
-            result = group_plan(b, b->groups[k], hbest[k]);
-        }
-        if (result == HYB_OK) result = halo_plan(b);
-        if (result != HYB_OK) break;
+        result = pick_heights(b, ~0u, trials, e0, e1, flush, flush_bytes);
         float ms = 0.f;
         double dur[kRoles];
-        e = run_single(b, trials, e0, e1, flush, flush_bytes, &ms, dur);
-        if (e != cudaSuccess) { result = cuda_fail(e, "hyb_batch_tune (single launch)"); break; }
-        if (ms < best) {
-            best = ms;
-            std::copy(b->role_ctas, b->role_ctas + kRoles, best_split);
-            best_h = hbest;
-            std::copy(dur, dur + kRoles, b->role_ms);
-        }
+        if (result == HYB_OK) result = measure(&ms, dur);
+        if (result != HYB_OK) break;
+        if (ms < best) keep_best(ms, dur);
         double w[kRoles];
         for (int r = 0; r < kRoles; r++) w[r] = b->role_ctas[r] > 0 ? (double)b->role_ctas[r] * std::max(dur[r], 1e-3) : 0.0;
         int prev[kRoles];
@@ -436,9 +463,39 @@ static hyb_status tune_single(hyb_batch* b, int trials, cudaEvent_t e0, cudaEven
         split_ctas(b, w);
         if (std::equal(prev, prev + kRoles, b->role_ctas)) break;
     }
-    std::copy(best_split, best_split + kRoles, b->role_ctas);
-    for (size_t k = 0; k < b->groups.size(); k++) b->groups[k].rows_single = best_h[k];
-    // the faster form of the step (each timed as its captured graph)
+    // (2)
+    if (result == HYB_OK) result = restore_best();
+    for (int iter = 0; iter < 16 && result == HYB_OK; iter++) {
+        double dur[kRoles];
+        std::copy(b->role_ms, b->role_ms + kRoles, dur);
+        int slow = -1;
+        std::vector<std::pair<double, int>> donors;
+        for (int r = 0; r < kRoles; r++) {
+            if (b->role_ctas[r] < 1) continue;
+            if (slow < 0 || dur[r] > dur[slow]) slow = r;
+        }
+        for (int r = 0; r < kRoles; r++)
+            if (r != slow && b->role_ctas[r] > 1)
+                donors.push_back({dur[r] * b->role_ctas[r] / (b->role_ctas[r] - 1), r});
+        std::sort(donors.begin(), donors.end());
+        bool moved = false;
+        for (size_t d = 0; d < donors.size() && d < 3 && !moved && result == HYB_OK; d++) {
+            const int from = donors[d].second;
+            if (donors[d].first >= dur[slow]) break;
+            result = restore_best();
+            if (result != HYB_OK) break;
+            b->role_ctas[from]--;
+            b->role_ctas[slow]++;
+            result = pick_heights(b, (1u << slow) | (1u << from), trials, e0, e1, flush, flush_bytes);
+            float ms = 0.f;
+            double nd[kRoles];
+            if (result == HYB_OK) result = measure(&ms, nd);
+            if (result == HYB_OK && ms < best) { keep_best(ms, nd); moved = true; }
+        }
+        if (!moved) break;
+    }
+    if (result == HYB_OK) result = restore_best();
+    // (3)
     b->single = keep_single;
     if (result == HYB_OK) {
         float t_single = 0.f, t_multi = 0.f;

@@ -28,8 +28,9 @@ constexpr int kStepThreads = 768;
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int kQ3Part = (kQ2kA + kQ2kB + kQ2k) * 8;                // exchange buffers and staging row of a part
 constexpr int kTeamBytes = cmax(cmax(2 * Tmt<32>::SMEM_MEGA, 2 * Tmt<64>::SMEM_MEGA), 2 * Tmt<128>::SMEM_MEGA);
-constexpr int kQ3Bar = 3 * kQ3Part + kQ2kTw * 8;                    // quasi-3D role: 6 mbarriers, 3 abort flags
-constexpr int kStepSmem = cmax(cmax(tmk::SMEM, kTeamBytes + 16), kQ3Bar + 6 * 8 + 3 * 4);
+constexpr int kQ3Bar = 3 * kQ3Part + kQ2kTw * 8;                    // quasi-3D role: 12 mbarriers, 3 abort flags
+constexpr int kStepSmem = cmax(cmax(tmk::SMEM, kTeamBytes + 16), kQ3Bar + 12 * 8 + 3 * 4);
+static_assert(2 * 9 * 256 * 8 <= kQ3Part, "the leapfrog's two stages fit a part's transform buffers");
 }  // namespace
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -69,7 +70,9 @@ __device__ __forceinline__ void role_sync(unsigned* s, int ncta, int* err) {
 // transform's twiddle table: the L1 left beside the 2D roles' shared memory is small, and a part
 // has no registers to spare for holding the next row.  The leapfrog sweeps columns: a part takes
 // one (mode, block of 256 axial modes, chunk of radial rows), the chunks cut so that the columns
-// are at most as many as the parts (one round).
+// are at most as many as the parts (one round); its rows arrive by bulk copy into the part's
+// transform buffers, which the leapfrog does not otherwise use.  Spectra written by one stage are
+// read by bulk copy in the next: a proxy fence follows each role barrier.
 __device__ __forceinline__ void q3_role(const StepArgs& a, int vb, unsigned char* sm) {
     const int part = threadIdx.x >> 8, t = threadIdx.x & 255;
     const int n = a.q3_ncta, parts = 3 * n;
@@ -78,19 +81,21 @@ __device__ __forceinline__ void q3_role(const StepArgs& a, int vb, unsigned char
     float2* bufB = bufA + kQ2kA;
     float2* tws = reinterpret_cast<float2*>(sm + 3 * kQ3Part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kQ3Bar);
-    volatile int* aborts = reinterpret_cast<volatile int*>(sm + kQ3Bar + 6 * 8);
+    volatile int* aborts = reinterpret_cast<volatile int*>(sm + kQ3Bar + 12 * 8);
     for (int i = threadIdx.x; i < kQ2kTw; i += blockDim.x) tws[i] = q.tw2k[i];
     if (t == 0) {
-        mbar_init(smem_addr(bars + 2 * part), 1);
-        mbar_init(smem_addr(bars + 2 * part + 1), 1);
+        for (int b = 0; b < 4; b++) mbar_init(smem_addr(bars + 4 * part + b), 1);
         aborts[part] = 0;
         mbar_fence_init();
     }
     __syncthreads();
-    const QStage fwd{bufB + kQ2kB, smem_addr(bars + 2 * part), a.q3_err, aborts + part};
-    const QStage inv{bufB + kQ2kB, smem_addr(bars + 2 * part + 1), a.q3_err, aborts + part};
+    const QStage fwd{bufB + kQ2kB, smem_addr(bars + 4 * part), a.q3_err, aborts + part};
+    const QStage inv{bufB + kQ2kB, smem_addr(bars + 4 * part + 1), a.q3_err, aborts + part};
+    const uint32_t lbar0 = smem_addr(bars + 4 * part + 2), lbar1 = smem_addr(bars + 4 * part + 3);
+    uint32_t lph = 0;
     cfft2048_body<false, true>(q.fin, q.nr, 9, tws, 3 * vb + part, parts, t, bufA, bufB, 1 + part, fwd);
     role_sync(a.sync + 2 * kRoleQ3, n, a.q3_err);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     constexpr int nkb = kQ2k / 256;                                 // blocks of 256 axial modes per row
     const int ncol = nkb * q.nm;
     const int nch = max(1, min(q.nr, parts / ncol));                // row chunks per column
@@ -98,9 +103,17 @@ __device__ __forceinline__ void q3_role(const StepArgs& a, int vb, unsigned char
     for (int u = 3 * vb + part; u < ncol * nch; u += parts) {
         const int col = u % ncol, ch = u / ncol;
         const int j0 = ch * rows, j1 = min(q.nr, j0 + rows);
-        if (j0 < j1) qleap_column<float>(q.ql, kQ2k, q.nr, q.dr, (col % nkb) * 256 + t, col / nkb, j0, j1);
+        if (j0 < j1)
+            qleap_column<float>(q.ql, kQ2k, q.nr, q.dr, col % nkb, col / nkb, j0, j1, t, bufA, lbar0, lbar1, lph, 1 + part,
+                                a.q3_err, aborts + part);
+    }
+    // after a wait that gave up, the stages still in flight land before the buffers are reused
+    if (aborts[part] && t == 0) {
+        if (lph & 4u) mbar_drain(lbar0, (lph & 1u) ^ 1u);
+        if (lph & 8u) mbar_drain(lbar1, ((lph >> 1) & 1u) ^ 1u);
     }
     role_sync(a.sync + 2 * kRoleQ3, n, a.q3_err);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     cfft2048_body<true, true>(q.fout, q.nr, 6, tws, 3 * vb + part, parts, t, bufA, bufB, 1 + part, inv);
 }
 

@@ -310,58 +310,78 @@ __device__ __forceinline__ void qleap_body(const QLeap<T>& ql, int nz, int nr, T
     Bn[2 * fs + i] = b.p;
 }
 
-// the same for rows j0 .. j1 - 1 of axial mode k of mode qm, sweeping up the radius: E at rows j and
-// j + 1, B at row j and B^{n+1/2} at row j - 1 are carried in registers from row to row, and the
-// loads of the next row (E at j + 2, B at j + 1) are issued with those of j at row j before row j
-// is computed and stored, so every value is read from memory once and a thread keeps nine loads in
-// flight (for CTAs too large for the many resident threads the one-point form relies on)
+// The same for rows j0 .. j1 - 1 of the 256 axial modes kb * 256 .. + 255 of mode qm, one per thread
+// t of a 256-thread part of a CTA (80 registers a thread, inside the single-launch batched step),
+// sweeping up the radius.  E at row j and B^{n+1/2} at row j - 1 are carried in registers from row
+// to row; E at row j + 1 and B, j at row j arrive by bulk copy (nine 2 KB row segments, one stage)
+// into one of two stage buffers of st (2 x 9 x 256 complex, shared memory) two rows ahead, so that
+// every value is read once and the loads in flight do not take registers.  bar0, bar1: the two
+// stages' mbarriers (count 1); bit b of phases: the parity buffer b waits for next, bit 2 + b: buffer
+// b has been used; bar_id: the part's named barrier.
 template <typename T>
-__device__ __forceinline__ void qleap_column(const QLeap<T>& ql, int nz, int nr, T dr, int k, int qm, int j0, int j1) {
+__device__ __forceinline__ void qleap_column(const QLeap<T>& ql, int nz, int nr, T dr, int kb, int qm, int j0, int j1,
+                                             int t, cplx<T>* st, uint32_t bar0, uint32_t bar1, uint32_t& phases,
+                                             int bar_id, int* err, volatile int* abort) {
     using C = cplx<T>;
     cplx<T>* __restrict__ spec = ql.spec[qm];
     const T dt = ql.dt[qm];
     const int m = ql.m[qm];
     const int64_t fs = (int64_t)nr * nz;
-    const C* Ez = spec; const C* Er = spec + fs; const C* Ep = spec + 2 * fs;
-    const C* Bz = spec + 3 * fs; const C* Br = spec + 4 * fs; const C* Bp = spec + 5 * fs;
+    const int k = kb * 256 + t;
     C* Jz = spec + 6 * fs; C* Jr = spec + 7 * fs; C* Jp = spec + 8 * fs;
     C* Bn = spec + 9 * fs;
     const C zero = mkc<C>((T)0, (T)0);
     const QTab<T> q = ql.tab[qm][k];
-    auto at = [&](int j) { return (int64_t)j * nz + k; };
-    // E at rows j0 and j0 + 1, B and j at row j0, and B^{n+1/2} at row j0 - 1
-    int64_t i = at(j0);
-    C ez = Ez[i], er = Er[i], ep = Ep[i];
-    C ezu = zero, eru = zero, epu = zero;
-    if (j0 + 1 < nr) { ezu = Ez[i + nz]; eru = Er[i + nz]; epu = Ep[i + nz]; }
-    C bz = Bz[i], br = Br[i], bp = Bp[i];
+    constexpr uint32_t SEG = 256 * sizeof(C);
+    // stage of row r into buffer b: E (slots 0..2) at row r + 1 (none past the wall), B (3..5) and j
+    // (6..8) at row r
+    auto stage = [&](int r, int b) {
+        if (t == 0) {
+            fence_proxy_async_smem();
+            const bool e_up = r + 1 < nr;
+            const uint32_t bar = b ? bar1 : bar0;
+            mbar_expect_tx(bar, (e_up ? 9u : 6u) * SEG);
+            C* dst = st + b * 9 * 256;
+            for (int f = 0; f < 9; f++) {
+                if (f < 3 && !e_up) continue;
+                const int row = f < 3 ? r + 1 : r;
+                bulk_load(smem_addr(dst + f * 256), spec + f * fs + (int64_t)row * nz + kb * 256, SEG, bar);
+            }
+        }
+        phases |= 4u << b;
+    };
+    // E at row j0 and B^{n+1/2} at row j0 - 1 from memory
+    int64_t i = (int64_t)j0 * nz + k;
+    C ez = spec[i], er = spec[fs + i], ep = spec[2 * fs + i];
     QB<T> bd = {zero, zero, zero};
     if (j0 > 0) {
         const int64_t id = i - nz;
-        bd = qfaraday<T>(Ez[id], Er[id], Ep[id], ez, ep, Bz[id], Br[id], Bp[id], j0 - 1, q.sp, dt, dr, m);
+        bd = qfaraday<T>(spec[id], spec[fs + id], spec[2 * fs + id], ez, ep, spec[3 * fs + id], spec[4 * fs + id],
+                         spec[5 * fs + id], j0 - 1, q.sp, dt, dr, m);
     }
+    stage(j0, 0);
+    if (j0 + 1 < j1) stage(j0 + 1, 1);
     for (int j = j0; j < j1; j++) {
-        // j at row j; the next row's E at row j + 2 and B at row j + 1
-        const C jz = Jz[i], jr = Jr[i], jp = Jp[i];
-        C nez = zero, ner = zero, nep = zero, nbz = zero, nbr = zero, nbp = zero;
-        const int64_t in = i + nz;
-        if (j + 1 < j1) {
-            if (j + 2 < nr) { nez = Ez[in + nz]; ner = Er[in + nz]; nep = Ep[in + nz]; }
-            nbz = Bz[in]; nbr = Br[in]; nbp = Bp[in];
-        }
-        const QB<T> b = qfaraday<T>(ez, er, ep, ezu, epu, bz, br, bp, j, q.sp, dt, dr, m);
-        const QB<T> e = qampere<T>(b, bd, ez, er, ep, jz, jr, jp, q, j, dt, dr, m);
+        const int b = (j - j0) & 1;
+        mbar_wait(b ? bar1 : bar0, (phases >> b) & 1u, err, abort);
+        phases ^= 1u << b;
+        const C* sb = st + b * 9 * 256 + t;
+        const bool e_up = j + 1 < nr;
+        const C ezu = e_up ? sb[0] : zero, eru = e_up ? sb[256] : zero, epu = e_up ? sb[512] : zero;
+        const C bz = sb[768], br = sb[1024], bp = sb[1280], jz = sb[1536], jr = sb[1792], jp = sb[2048];
+        asm volatile("bar.sync %0, 256;" :: "r"(bar_id) : "memory");      // the part has read the buffer
+        if (j + 2 < j1) stage(j + 2, b);
+        const QB<T> bn = qfaraday<T>(ez, er, ep, ezu, epu, bz, br, bp, j, q.sp, dt, dr, m);
+        const QB<T> e = qampere<T>(bn, bd, ez, er, ep, jz, jr, jp, q, j, dt, dr, m);
         Jz[i] = e.z;
         Jr[i] = e.r;
         Jp[i] = e.p;
-        Bn[i] = b.z;
-        Bn[fs + i] = b.r;
-        Bn[2 * fs + i] = b.p;
-        bd = b;
+        Bn[i] = bn.z;
+        Bn[fs + i] = bn.r;
+        Bn[2 * fs + i] = bn.p;
+        bd = bn;
         ez = ezu; er = eru; ep = epu;
-        ezu = nez; eru = ner; epu = nep;
-        bz = nbz; br = nbr; bp = nbp;
-        i = in;
+        i += nz;
     }
 }
 
