@@ -52,6 +52,9 @@ def parse():
                          "benchmark; others show the n1 = 512 .. 2048 kernels and the three-pass path)")
     ap.add_argument("--batch-strips", default="",
                     help="batched workload: rows per strip per n1 as '512:3,1024:2,...' instead of the autotuner")
+    ap.add_argument("--batch-split", default="",
+                    help="batched workload with --batch-strips: CTAs of the single launch's roles (n1 = 4096, 512, "
+                         "1024, 2048, quasi-3D) as '64,6,7,18,57'")
     ap.add_argument("--ppc", type=int, default=8,
                     help="push workload: particles per cell per species (8 is the benchmark; fewer for profiling)")
     ap.add_argument("--sweep-n1", default="16,32,64,128,256,512,1024",
@@ -487,7 +490,7 @@ def run_push(args):
     print(json.dumps(line), flush=True)
 
 
-def measure_batched(hyb, wl, steps, warmup, stream, flush, sampler, dev, strips=""):
+def measure_batched(hyb, wl, steps, warmup, stream, flush, sampler, dev, strips="", split=""):
     """16 uneven 2D FP32 grids (sizes drawn with seed 3) plus the quasi-3D modes m = 0, 1, 2
     on 2048 x 512 complex fields, advanced together as one batch (CUDA-graph step)."""
     import numpy as np
@@ -523,6 +526,8 @@ def measure_batched(hyb, wl, steps, warmup, stream, flush, sampler, dev, strips=
         for kv in strips.split(","):
             n1_, h_ = (int(v) for v in kv.split(":"))
             b.set_rows_per_strip(n1_, h_)
+        if split:
+            b.set_role_ctas([int(v) for v in split.split(",")])
     else:
         b.tune(5)
     tune_s = time.perf_counter() - t0
@@ -546,7 +551,7 @@ def measure_batched(hyb, wl, steps, warmup, stream, flush, sampler, dev, strips=
               "role_ctas": dict(zip(("n1=4096", "n1=512", "n1=1024", "n1=2048", "quasi3d"), b.role_ctas())),
               "role_ms": dict(zip(("n1=4096", "n1=512", "n1=1024", "n1=2048", "quasi3d"), b.role_ms())),
               "other_form": other,
-              "strips": "set by --batch-strips" if strips else "autotuned", "autotune_s": tune_s,
+              "strips": "set by --batch-strips / --batch-split" if strips else "autotuned", "autotune_s": tune_s,
               "rows_per_strip": {n1: b.rows_per_strip(n1) for n1 in (512, 1024, 2048, 4096)},
               "current": "band-limited random J (no deposit in the timed step)",
               "l2": "flushed between timed steps (256 MB write)"}
@@ -599,7 +604,7 @@ def run_other(args):
     extra = {}
     if args.workload == "batched":
         ms, cells, alg_bytes, lps, extra["config"] = measure_batched(hyb, wl, args.steps, args.warmup, stream, flush,
-                                                                     sampler, dev, args.batch_strips)
+                                                                     sampler, dev, args.batch_strips, args.batch_split)
         launches = lps * args.steps
         dtype = "f32"
     elif args.workload == "3d":

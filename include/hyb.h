@@ -353,6 +353,12 @@ HYB_API int hyb_batch_single_launch(const hyb_batch* b);
  * launch is not available. */
 HYB_API int hyb_batch_role_ctas(const hyb_batch* b, int r);
 
+/* Sets the CTAs of the single launch's roles (ctas[0..4], as hyb_batch_role_ctas
+ * numbers them), e.g. to reuse a split found by an earlier hyb_batch_tune:
+ * at least one CTA for every role the batch has, zero for the others, at most
+ * one CTA per SM in all.  HYB_EINVAL otherwise or without a single launch. */
+HYB_API hyb_status hyb_batch_set_role_ctas(hyb_batch* b, const int* ctas);
+
 /* Duration (ms, first CTA start to last CTA end) of role r in the fastest
  * single launch hyb_batch_tune timed; 0 before a tune or for an absent role. */
 HYB_API double hyb_batch_role_ms(const hyb_batch* b, int r);

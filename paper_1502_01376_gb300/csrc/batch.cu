@@ -754,6 +754,24 @@ int hyb_batch_role_ctas(const hyb_batch* b, int role) {
     return b && role >= 0 && role < kRoles && b->single_ok ? b->role_ctas[role] : 0;
 }
 
+hyb_status hyb_batch_set_role_ctas(hyb_batch* b, const int* ctas) {
+    if (!b || !ctas) { set_error("hyb_batch_set_role_ctas: null argument"); return HYB_EINVAL; }
+    if (!b->single_ok) { set_error("hyb_batch_set_role_ctas: the batch has no single launch"); return HYB_EINVAL; }
+    int sum = 0;
+    for (int r = 0; r < kRoles; r++) {
+        const bool present = b->role_ctas[r] > 0;
+        if (present ? ctas[r] < 1 : ctas[r] != 0) {
+            set_error("hyb_batch_set_role_ctas: role %d needs %s", r, present ? "at least one CTA" : "zero CTAs");
+            return HYB_EINVAL;
+        }
+        sum += ctas[r];
+    }
+    if (sum > b->step_ctas) { set_error("hyb_batch_set_role_ctas: %d CTAs, more than the %d of the launch", sum, b->step_ctas); return HYB_EINVAL; }
+    std::copy(ctas, ctas + kRoles, b->role_ctas);
+    b->dirty = true;
+    return HYB_OK;
+}
+
 double hyb_batch_role_ms(const hyb_batch* b, int role) {
     return b && role >= 0 && role < kRoles ? b->role_ms[role] : 0.0;
 }

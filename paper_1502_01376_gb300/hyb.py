@@ -112,6 +112,8 @@ def lib():
             L.hyb_batch_single_launch.restype = ctypes.c_int
             L.hyb_batch_role_ctas.argtypes = [_V, ctypes.c_int]
             L.hyb_batch_role_ctas.restype = ctypes.c_int
+            L.hyb_batch_set_role_ctas.argtypes = [_V, ctypes.POINTER(ctypes.c_int)]
+            L.hyb_batch_set_role_ctas.restype = S
             L.hyb_batch_role_ms.argtypes = [_V, ctypes.c_int]
             L.hyb_batch_role_ms.restype = ctypes.c_double
             L.hyb_batch_destroy.argtypes = [_V]
@@ -306,6 +308,11 @@ def hyb_batch_single_launch(b: int) -> bool:
 
 def hyb_batch_role_ctas(b: int, r: int) -> int:
     return lib().hyb_batch_role_ctas(_V(b), r)
+
+
+def hyb_batch_set_role_ctas(b: int, ctas) -> None:
+    arr = (ctypes.c_int * 5)(*[int(c) for c in ctas])
+    _check(lib().hyb_batch_set_role_ctas(_V(b), arr))
 
 
 def hyb_batch_role_ms(b: int, r: int) -> float:
@@ -542,6 +549,10 @@ class Batch:
     def role_ctas(self):
         """CTAs of the single launch's roles: n1 = 4096, 512, 1024, 2048, quasi-3D."""
         return [hyb_batch_role_ctas(self.h, r) for r in range(5)]
+
+    def set_role_ctas(self, ctas):
+        """Sets the CTAs of the single launch's roles (as role_ctas() lists them)."""
+        hyb_batch_set_role_ctas(self.h, ctas)
 
     def role_ms(self):
         """Each role's duration in the tuner's fastest single launch (ms)."""

@@ -163,3 +163,32 @@ def test_single_launch_needs_every_grid_in_a_role():
     with pytest.raises(hyb.HybError):
         b.single_launch = True
     b.close()
+
+
+def test_role_split_set_by_hand():
+    """A split set by hand (every role at least one CTA, at most one CTA per SM) gives the same bits;
+    a split that leaves a role without CTAs, or gives one to an absent role, is refused."""
+    need_gpu()
+    hyb = hyb_module()
+    descs, inputs, _ = _setup(hyb)
+    one = hyb.Batch(descs)
+    many = hyb.Batch(descs)
+    many.single_launch = False
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    with pytest.raises(hyb.HybError):
+        one.set_role_ctas([0, 10, 10, 10, 10])
+    with pytest.raises(hyb.HybError):
+        one.set_role_ctas([sms, 1, 1, 1, 1])
+    one.set_role_ctas([1, 2, 3, 4, 5])                    # far from balanced, most CTAs idle
+    ba, bb = _bind(one, inputs), _bind(many, inputs)
+    one.advance(3)
+    many.advance(3)
+    torch.cuda.synchronize()
+    _same(ba, bb, "split by hand")
+    one.close()
+    many.close()
+    q3_only = hyb.Batch(_setup(hyb, with_2d=False)[0])
+    with pytest.raises(hyb.HybError):
+        q3_only.set_role_ctas([1, 0, 0, 0, 10])
+    q3_only.set_role_ctas([0, 0, 0, 0, 3])
+    q3_only.close()
