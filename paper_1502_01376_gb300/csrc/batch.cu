@@ -193,17 +193,18 @@ static void split_ctas(hyb_batch* b, const double* w) {
     }
 }
 
-// a first split from the bytes each role moves and the rates its kernels reach alone on the
-// whole GPU (TB/s): 60 B per 2D cell, 360 B per quasi-3D point over the three stages
+// a first split (before hyb_batch_tune) from the bytes each role moves, 60 B per 2D cell and 360 B
+// per quasi-3D point over the three stages, and the rate each role reached in the tuned single
+// launch of a 16-grid + 3-mode batch, per CTA, scaled to 152 CTAs (TB/s)
 static void default_split(hyb_batch* b) {
     double w[kRoles] = {0, 0, 0, 0, 0};
-    static const double rate[4] = {2.6, 1.9, 1.5, 2.1};
+    static const double rate[4] = {2.6, 3.4, 2.9, 2.8};
     for (auto& G : b->groups) {
         int64_t cells = 0;
         for (int m : G.members) cells += b->grids[m]->cells;
         w[role_of_n1(G.n1)] += 60.0 * (double)cells / rate[role_of_n1(G.n1)];
     }
-    for (int i : b->q3) w[kRoleQ3] += 360.0 * (double)b->grids[i]->cells / 5.6;
+    for (int i : b->q3) w[kRoleQ3] += 360.0 * (double)b->grids[i]->cells / 6.2;
     split_ctas(b, w);
 }
 
