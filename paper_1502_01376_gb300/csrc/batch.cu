@@ -402,11 +402,11 @@ static hyb_status pick_heights(hyb_batch* b, unsigned mask, int trials, cudaEven
 // tuning leaves them as they were).  (1) Rounds of: each group's strip height for the current split
 // of the single launch's CTAs (pick_heights), then a new split with CTAs in proportion to each
 // role's CTA time (CTAs x duration), until the split repeats.  (2) From the fastest of those, one
-// CTA at a time to the role that finished last from another role (tried in the order of the
-// duration it would have with one CTA less, in proportion, up to three of them), the two roles'
-// heights picked again, while the launch gets faster (the proportional split is coarse for roles
-// of a few CTAs, whose durations also step with the waves of their work items).  (3) The faster of
-// the single launch and the graph of launches, each timed as its captured graph.
+// CTA each to the roles that finished last (within 1 % of the last) from other roles (tried in the
+// order of the duration they would have with one CTA less, in proportion; up to three choices),
+// the changed roles' heights picked again, while the launch gets faster (the proportional split is
+// coarse for roles of a few CTAs, whose durations also step with the waves of their work items).
+// (3) The faster of the single launch and the graph of launches, each timed as its captured graph.
 static hyb_status tune_single(hyb_batch* b, int trials, cudaEvent_t e0, cudaEvent_t e1, void* flush, size_t flush_bytes) {
     for (auto* g : b->grids) if (!g->bound) return HYB_OK;     // nothing to run on yet: keep the first split
     hyb_status hs = halo_plan(b);
@@ -469,25 +469,30 @@ static hyb_status tune_single(hyb_batch* b, int trials, cudaEvent_t e0, cudaEven
     for (int iter = 0; iter < 16 && result == HYB_OK; iter++) {
         double dur[kRoles];
         std::copy(b->role_ms, b->role_ms + kRoles, dur);
-        int slow = -1;
-        std::vector<std::pair<double, int>> donors;
+        double top = 0.0;
+        for (int r = 0; r < kRoles; r++) if (b->role_ctas[r] > 0) top = std::max(top, dur[r]);
+        std::vector<int> slow;                                    // the roles that finish last
+        std::vector<std::pair<double, int>> donors;               // the others, by their duration with one CTA less
         for (int r = 0; r < kRoles; r++) {
             if (b->role_ctas[r] < 1) continue;
-            if (slow < 0 || dur[r] > dur[slow]) slow = r;
+            if (dur[r] >= 0.99 * top) slow.push_back(r);
+            else if (b->role_ctas[r] > 1) donors.push_back({dur[r] * b->role_ctas[r] / (b->role_ctas[r] - 1), r});
         }
-        for (int r = 0; r < kRoles; r++)
-            if (r != slow && b->role_ctas[r] > 1)
-                donors.push_back({dur[r] * b->role_ctas[r] / (b->role_ctas[r] - 1), r});
         std::sort(donors.begin(), donors.end());
         bool moved = false;
-        for (size_t d = 0; d < donors.size() && d < 3 && !moved && result == HYB_OK; d++) {
-            const int from = donors[d].second;
-            if (donors[d].first >= dur[slow]) break;
+        // choice c: the slow roles take one CTA each from the donors c, c + 1, ... (a donor gives one)
+        for (size_t c = 0; c < 3 && c + slow.size() <= donors.size() && !moved && result == HYB_OK; c++) {
+            if (donors[c + slow.size() - 1].first >= top) break;
             result = restore_best();
             if (result != HYB_OK) break;
-            b->role_ctas[from]--;
-            b->role_ctas[slow]++;
-            result = pick_heights(b, (1u << slow) | (1u << from), trials, e0, e1, flush, flush_bytes);
+            unsigned mask = 0;
+            for (size_t i = 0; i < slow.size(); i++) {
+                const int from = donors[c + i].second;
+                b->role_ctas[from]--;
+                b->role_ctas[slow[i]]++;
+                mask |= (1u << from) | (1u << slow[i]);
+            }
+            result = pick_heights(b, mask, trials, e0, e1, flush, flush_bytes);
             float ms = 0.f;
             double nd[kRoles];
             if (result == HYB_OK) result = measure(&ms, nd);
