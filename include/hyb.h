@@ -265,11 +265,13 @@ HYB_API hyb_status hyb_check(hyb_grid* g);
  * Runs one probe kernel that waits on a condition nothing satisfies, with the
  * same wait code the fused advance uses: which = 0, the release/acquire flag
  * wait of the in-kernel halo exchange; which = 1, the mbarrier wait of the row
- * staging.  The limit is `seconds` at the device's clock rate.  Returns
- * HYB_ETIMEOUT when the wait gave up as designed (the expected result), HYB_OK
- * if the condition was met, HYB_EINVAL for which not in {0, 1} or seconds not
- * in (0, 10], HYB_ECUDA on a CUDA error.  Synchronous on `stream`; allocates
- * and frees two ints of device memory. */
+ * staging; which = 2, the barrier between the CTAs of a role of the
+ * single-launch batched step (a role of two CTAs, one of which never arrives).
+ * The limit is `seconds` at the device's clock rate.  Returns HYB_ETIMEOUT
+ * when the wait gave up as designed (the expected result), HYB_OK if the
+ * condition was met, HYB_EINVAL for which not in {0, 1, 2} or seconds not in
+ * (0, 10], HYB_ECUDA on a CUDA error.  Synchronous on `stream`; allocates and
+ * frees three ints of device memory. */
 HYB_API hyb_status hyb_wait_selftest(int which, double seconds, void* stream);
 
 /* Frees the grid's tables and scratch (not the caller's arrays). NULL is a no-op. */

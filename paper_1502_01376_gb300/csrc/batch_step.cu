@@ -41,9 +41,10 @@ __device__ __forceinline__ unsigned long long gtimer() {
 
 // barrier of the ncta CTAs of one role: s[0] counts arrivals, s[1] is the generation.  The last CTA
 // to arrive resets the count and then advances the generation; the others wait for the generation
-// they saw before arriving to change (bounded: after kWaitCycles bit 1 of *err is set and the CTA
-// goes on).  Global writes of the CTA before the barrier are visible to the role's CTAs after it.
-__device__ __forceinline__ void role_sync(unsigned* s, int ncta, int* err) {
+// they saw before arriving to change (bounded: after `limit` cycles, about 2 s by default, bit 1 of
+// *err is set and the CTA goes on).  Global writes of the CTA before the barrier are visible to the
+// role's CTAs after it.
+__device__ __forceinline__ void role_sync(unsigned* s, int ncta, int* err, long long limit = kWaitCycles) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned* gen = s + 1;
@@ -56,7 +57,7 @@ __device__ __forceinline__ void role_sync(unsigned* s, int ncta, int* err) {
         } else {
             const long long t0 = clock64();
             while (*gen == g0) {
-                if (clock64() - t0 > kWaitCycles) { if (err) atomicOr(err, 2); break; }
+                if (clock64() - t0 > limit) { if (err) atomicOr(err, 2); break; }
                 __nanosleep(64);
             }
         }
@@ -170,6 +171,10 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_batch_step(const __grid_con
     }
 }
 
+// self-test of the role barrier: a role of two CTAs of which only this one arrives; the wait must
+// give up after `limit` cycles and report through *err
+__global__ void k_role_probe(unsigned* s, int* err, long long limit) { role_sync(s, 2, err, limit); }
+
 // ------------------------------------------------------------------ host side
 size_t batch_step_smem_bytes() { return (size_t)kStepSmem; }
 
@@ -183,6 +188,11 @@ cudaError_t batch_step_ctas(int* n) {
     if (e != cudaSuccess) return e;
     *n = occ >= 1 ? sms : 0;           // one CTA per SM (TMEM: 512 columns per CTA)
     return cudaSuccess;
+}
+
+cudaError_t role_probe(unsigned* sync, int* err, long long limit, cudaStream_t s) {
+    k_role_probe<<<1, 32, 0, s>>>(sync, err, limit);
+    return cudaGetLastError();
 }
 
 cudaError_t batch_step_launch(const StepArgs& a, int grid, cudaStream_t s) {

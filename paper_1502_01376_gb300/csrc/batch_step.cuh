@@ -36,5 +36,7 @@ size_t batch_step_smem_bytes();
 // CTAs of the launch: one per SM (every CTA must be resident: the roles have grid-wide barriers)
 cudaError_t batch_step_ctas(int* n);
 cudaError_t batch_step_launch(const StepArgs& a, int grid, cudaStream_t s);
+// self-test of the role barrier's bounded wait (sync: two zeroed words)
+cudaError_t role_probe(unsigned* sync, int* err, long long limit, cudaStream_t s);
 
 }  // namespace hyb

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "hyb_internal.cuh"
+#include "batch_step.cuh"
 #include "fused_api.cuh"
 
 namespace hyb {
@@ -447,20 +448,22 @@ hyb_status hyb_check(hyb_grid* g) {
 }
 
 hyb_status hyb_wait_selftest(int which, double seconds, void* stream) {
-    if ((which != 0 && which != 1) || !(seconds > 0.0 && seconds <= 10.0)) {
-        set_error("hyb_wait_selftest: which must be 0 or 1 and seconds in (0, 10]");
+    if (which < 0 || which > 2 || !(seconds > 0.0 && seconds <= 10.0)) {
+        set_error("hyb_wait_selftest: which must be 0, 1 or 2 and seconds in (0, 10]");
         return HYB_EINVAL;
     }
     int dev = 0, khz = 0;
     HYB_CUDA_TRY(cudaGetDevice(&dev));
     HYB_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
     int* d = nullptr;
-    HYB_CUDA_TRY(cudaMalloc(&d, 2 * sizeof(int)));
+    HYB_CUDA_TRY(cudaMalloc(&d, 3 * sizeof(int)));
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(int), s);
-    if (e == cudaSuccess) e = wait_probe(d, d + 1, (long long)(seconds * 1e3 * (double)khz), which, s);
+    cudaError_t e = cudaMemsetAsync(d, 0, 3 * sizeof(int), s);
+    const long long limit = (long long)(seconds * 1e3 * (double)khz);
+    if (e == cudaSuccess)
+        e = which == 2 ? role_probe(reinterpret_cast<unsigned*>(d), d + 2, limit, s) : wait_probe(d, d + 2, limit, which, s);
     int h = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d + 2, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e, "hyb_wait_selftest");

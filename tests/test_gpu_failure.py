@@ -1,5 +1,6 @@
 """Failure detection without a GPU fault: the bounded device waits of the fused
-advance (the halo-exchange flag and the row-staging mbarrier) give up on a
+advance (the halo-exchange flag and the row-staging mbarrier) and of the
+single-launch batched step (the barrier between a role's CTAs) give up on a
 condition nothing satisfies and report HYB_ETIMEOUT to the host; the context
 stays usable (a parity-checked advance runs right after)."""
 import numpy as np
@@ -12,7 +13,7 @@ from gpu_util import hyb_module, need_gpu, orc_grid, rel_err, to_dev, to_np, tor
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_wait_gives_up_and_reports(orc, which):
     need_gpu()
     hyb = hyb_module()
@@ -39,6 +40,6 @@ def test_bounded_wait_gives_up_and_reports(orc, which):
 def test_selftest_rejects_bad_arguments():
     need_gpu()
     hyb = hyb_module()
-    assert hyb.hyb_wait_selftest(2, 0.1) == hyb.HYB_EINVAL
+    assert hyb.hyb_wait_selftest(3, 0.1) == hyb.HYB_EINVAL
     assert hyb.hyb_wait_selftest(0, 0.0) == hyb.HYB_EINVAL
     assert hyb.hyb_wait_selftest(0, 60.0) == hyb.HYB_EINVAL
