@@ -1,6 +1,7 @@
 // q3d_body.cuh -- device parts of the quasi-3D step shared by its kernels (quasi3d.cu) and the
-// single-launch batched step (batch_step.cu): the per-mode tables, the register-resident
-// 2048-point z transform of a row, and the leapfrog of one (axial mode, radial row).
+// single-launch batched step (batch_step.cu): the per-mode tables, the 2048-point z transform of
+// a row (next row in registers, or staged by bulk copy inside the single launch), and the
+// leapfrog, per (axial mode, radial row) or per column of radial rows.
 #pragma once
 #include <math.h>
 
@@ -25,7 +26,6 @@ struct QMulti { void* p[kQModes * 9]; float2* spec[kQModes]; int nm; };
 
 constexpr int kQThreads = 256;
 
-
 // ---------------------------------------------------------------- nz = 2048, FP32: register-resident rows
 // X[k] = sum_j x[j] W^{jk}, W = exp(-2 pi i / 2048), factored 8 x 8 x 8 x 4 with k = k1 + 8 k2 + 64 k3 + 512 k4:
 //   S1  thread t:            DFT8 over n of x[t + 256 n] -> k1, times W_2048^{t k1}      -> A(k1, t)
@@ -37,7 +37,8 @@ constexpr int kQThreads = 256;
 // A''(k1, k2, k3, u0) at 516 u0 + 64 k3 + k1 + 8 k2 (in the A buffer).  With 8-byte accesses a half-warp
 // of every exchange reaches 16 different bank pairs; global loads and stores are row-contiguous per warp.
 // The inverse uses the conjugate twiddles and scales by 1/2048.  One row per 256-thread block
-// iteration; persistent, the next row's points held in registers while the current one is transformed.
+// iteration; persistent, the next row's points on their way (registers, or a bulk copy) while the
+// current one is transformed.
 constexpr int kQ2k = 2048;
 constexpr int kQ2kA = 2064, kQ2kB = 2080;
 constexpr int kQ2kTw = 7 * 256 + 7 * 32 + 7 * 4;     // stage twiddles, in the order the threads read them
