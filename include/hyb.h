@@ -318,12 +318,14 @@ HYB_API hyb_status hyb_batch_bind(hyb_batch* b, int i, void* const E[3], void* c
  * height (rows per work item) on scratch fields it allocates and frees, each
  * after a write larger than the L2 (a group's data arrives cold inside a
  * step), and keeps the fastest.  Then, when the single launch is available
- * and every grid is bound: splits its CTAs among the roles in proportion to
- * the CTA time each role took in timed launches (up to 8 rounds, keeping the
- * fastest split) and keeps the faster of the single launch and the graph of
- * launches (each timed as a graph, `trials` steps after L2 flushes).  These
- * runs advance the bound fields, which are saved first and restored after,
- * so the fields end as they were.  Synchronises. */
+ * and every grid is bound: rounds of (each group's strip height for the
+ * current split, then CTAs in proportion to the CTA time each role took in
+ * timed launches, up to 6 rounds), then one-CTA moves to the roles that
+ * finish last while the launch gets faster, keeping the fastest split and
+ * heights; finally the faster of the single launch and the graph of launches
+ * (each timed as a graph, `trials` steps after L2 flushes).  These runs
+ * advance the bound fields, which are saved first and restored after, so the
+ * fields end as they were.  Synchronises. */
 HYB_API hyb_status hyb_batch_tune(hyb_batch* b, int trials);
 
 /* nsteps of every grid of the batch, one CUDA-graph launch per step, with the
