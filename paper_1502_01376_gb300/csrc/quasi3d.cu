@@ -118,6 +118,39 @@ __global__ void __launch_bounds__(kQThreads) k_qleap(const __grid_constant__ QLe
     qleap_body<T>(ql, nz, nr, dr, (int)(blockIdx.x * blockDim.x + threadIdx.x), (int)blockIdx.y, (int)blockIdx.z);
 }
 
+// the same for FP32 modes with nz = 2048 in columns (qleap_column: a block takes 256 axial modes of a
+// chunk of `rows` radial rows of one mode, the rows staged by bulk copy); persistent over the
+// ncol x nch columns
+constexpr int kQColSmem = 2 * 9 * 256 * 8 + 2 * 8 + 4;
+__global__ void __launch_bounds__(256) k_qleap_col(const __grid_constant__ QLeap<float> ql, int nr, float dr, int nm,
+                                                   int nch, int rows, int* err) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    float2* st = reinterpret_cast<float2*>(sm);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * 9 * 256 * 8);
+    volatile int* abort = reinterpret_cast<volatile int*>(sm + 2 * 9 * 256 * 8 + 16);
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(bars), 1);
+        mbar_init(smem_addr(bars + 1), 1);
+        *abort = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    constexpr int nkb = kQ2k / 256;
+    const int ncol = nkb * nm;
+    uint32_t ph = 0;
+    for (int u = blockIdx.x; u < ncol * nch; u += gridDim.x) {
+        const int col = u % ncol, ch = u / ncol;
+        const int j0 = ch * rows, j1 = min(nr, j0 + rows);
+        if (j0 < j1)
+            qleap_column<float>(ql, kQ2k, nr, dr, col % nkb, col / nkb, j0, j1, threadIdx.x, st, smem_addr(bars),
+                                smem_addr(bars + 1), ph, 1, err, abort);
+    }
+    if (*abort && threadIdx.x == 0) {
+        if (ph & 4u) mbar_drain(smem_addr(bars), (ph & 1u) ^ 1u);
+        if (ph & 8u) mbar_drain(smem_addr(bars + 1), ((ph >> 1) & 1u) ^ 1u);
+    }
+}
+
 template <typename T>
 static hyb_status create_t(hyb_grid* g) {
     using C = cplx<T>;
@@ -217,8 +250,11 @@ static hyb_status step_modes(hyb_grid* const* gs, int n, cudaStream_t st) {
         if (hs != HYB_OK) return hs;
         const int res = resident_grid((const void*)k_cfft2048<false>, 256, 0);
         k_cfft2048<false><<<(unsigned)std::min<int64_t>(res, (int64_t)n * 9 * nr), 256, 0, st>>>(a.fin, nr, 9, a.tw2k);
-        const dim3 mgrid((unsigned)((nz + kQThreads - 1) / kQThreads), (unsigned)nr, (unsigned)n);
-        k_qleap<T><<<mgrid, kQThreads, 0, st>>>(ql, nz, nr, (T)d.dx2);
+        // the leapfrog in columns, about as many as the resident blocks
+        HYB_CUDA_TRY(func_attr_once((const void*)k_qleap_col, cudaFuncAttributeMaxDynamicSharedMemorySize, kQColSmem));
+        const int resl = resident_grid((const void*)k_qleap_col, 256, kQColSmem);
+        const int ncol = (kQ2k / 256) * n, nch = std::max(1, std::min(nr, resl / ncol)), rows = (nr + nch - 1) / nch;
+        k_qleap_col<<<(unsigned)std::min(resl, ncol * nch), 256, kQColSmem, st>>>(a.ql, nr, a.dr, n, nch, rows, g->dflag);
         const int res2 = resident_grid((const void*)k_cfft2048<true>, 256, 0);
         k_cfft2048<true><<<(unsigned)std::min<int64_t>(res2, (int64_t)n * 6 * nr), 256, 0, st>>>(a.fout, nr, 6, a.tw2k);
     } else {
