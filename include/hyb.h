@@ -352,6 +352,13 @@ HYB_API hyb_status hyb_batch_set_single_launch(hyb_batch* b, int on);
 /* 1 if a step is the single persistent launch, else 0. */
 HYB_API int hyb_batch_single_launch(const hyb_batch* b);
 
+/* hyb_check of every grid of the batch (synchronises the batch's stream, reads
+ * and clears each grid's device-side flag): HYB_ETIMEOUT when a bounded wait of
+ * a step gave up (a role barrier of the single launch, a row staging or halo
+ * wait), HYB_EDATA for a deposit's skipped particles; the first error found is
+ * returned and described by hyb_last_error. */
+HYB_API hyb_status hyb_batch_check(hyb_batch* b);
+
 /* CTAs of role r of the single launch (0: n1 = 4096, 1: 512, 2: 1024,
  * 3: 2048, 4: the quasi-3D modes); 0 if the role is absent or the single
  * launch is not available. */

@@ -14,6 +14,7 @@
 // fields, then the split of the single launch's CTAs among its roles, and keeps the
 // faster of the two forms of the step.
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "batch_step.cuh"
@@ -755,6 +756,19 @@ hyb_status hyb_batch_set_single_launch(hyb_batch* b, int on) {
 }
 
 int hyb_batch_single_launch(const hyb_batch* b) { return b && b->single ? 1 : 0; }
+
+hyb_status hyb_batch_check(hyb_batch* b) {
+    if (!b) { set_error("null batch"); return HYB_EINVAL; }
+    // every grid's flag is read and cleared; the first error found is the one reported
+    hyb_status first = HYB_OK;
+    std::string msg;
+    for (auto* g : b->grids) {
+        const hyb_status st = hyb_check(g);
+        if (st != HYB_OK && first == HYB_OK) { first = st; msg = hyb_last_error(); }
+    }
+    if (first != HYB_OK) set_error("%s", msg.c_str());
+    return first;
+}
 
 int hyb_batch_role_ctas(const hyb_batch* b, int role) {
     return b && role >= 0 && role < kRoles && b->single_ok ? b->role_ctas[role] : 0;

@@ -108,6 +108,8 @@ def lib():
             L.hyb_batch_launches_per_step.restype = ctypes.c_int
             L.hyb_batch_set_single_launch.argtypes = [_V, ctypes.c_int]
             L.hyb_batch_set_single_launch.restype = S
+            L.hyb_batch_check.argtypes = [_V]
+            L.hyb_batch_check.restype = S
             L.hyb_batch_single_launch.argtypes = [_V]
             L.hyb_batch_single_launch.restype = ctypes.c_int
             L.hyb_batch_role_ctas.argtypes = [_V, ctypes.c_int]
@@ -300,6 +302,10 @@ def hyb_batch_launches_per_step(b: int) -> int:
 
 def hyb_batch_set_single_launch(b: int, on: bool) -> None:
     _check(lib().hyb_batch_set_single_launch(_V(b), 1 if on else 0))
+
+
+def hyb_batch_check(b: int) -> None:
+    _check(lib().hyb_batch_check(_V(b)))
 
 
 def hyb_batch_single_launch(b: int) -> bool:
@@ -536,6 +542,10 @@ class Batch:
     @property
     def launches_per_step(self):
         return hyb_batch_launches_per_step(self.h)
+
+    def check(self):
+        """Raises if a device-side wait of a step gave up (or a deposit skipped particles)."""
+        hyb_batch_check(self.h)
 
     @property
     def single_launch(self):

@@ -86,7 +86,8 @@ def test_single_launch_equals_graph_of_launches(with_2d, with_q3):
     ba, bb = _bind(one, inputs), _bind(many, inputs)
     one.advance(5)
     many.advance(5)
-    torch.cuda.synchronize()
+    one.check()
+    many.check()
     _same(ba, bb, "5 steps")
     one.close()
     many.close()
