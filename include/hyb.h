@@ -324,8 +324,9 @@ HYB_API hyb_status hyb_batch_bind(hyb_batch* b, int i, void* const E[3], void* c
  * finish last while the launch gets faster, keeping the fastest split and
  * heights; finally the faster of the single launch and the graph of launches
  * (each timed as a graph, `trials` steps after L2 flushes).  These runs
- * advance the bound fields, which are saved first and restored after, so the
- * fields end as they were.  Synchronises. */
+ * advance the bound fields, which are saved first (device copies of every
+ * grid's E and B, allocated and freed here) and restored after, so the fields
+ * end as they were.  Synchronises. */
 HYB_API hyb_status hyb_batch_tune(hyb_batch* b, int trials);
 
 /* nsteps of every grid of the batch, one CUDA-graph launch per step, with the
